@@ -1,0 +1,162 @@
+/*
+ * tref.h -- the ORACLE: a plain, slow, serial-per-block CPU reference of the
+ * per-MeshBlock finite-volume hydro stage of "An End-to-End Numerical
+ * Framework for Tidal Disruption Events with AthenaK" (arxiv 2609.37859).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant with the CUDA library (include/tde.h) and the CUDA library
+ * never calls it.
+ *
+ * Everything is IEEE double precision, compiled with -ffp-contract=off so that
+ * every operation is rounded exactly as written.  Each function names the
+ * passage of the paper it follows; where the paper is silent the reading that
+ * is implemented is stated at the function.
+ *
+ * Parity status: every function in this file is pinned by a CPU test
+ * (tests/test_oracle_*.py) against something other than itself (a closed
+ * form, an exact Riemann solution, an invariant or brute force), except the
+ * PPM reconstruction, whose absolute accuracy is pinned only by its measured
+ * convergence order and by conservation.
+ *
+ * State layout (all hydro calls):  a mesh is a set of MeshBlocks, each a box of
+ * nx*ny*nz interior cells padded by ng ghost cells on each side of every
+ * active direction (a direction whose global extent is 1 cell is inactive and
+ * carries no ghosts and no flux).  A state is one double array
+ *     U[v * ntot + off_b + (k * Py + j) * Px + i]
+ * with v the conserved variable (rho, m_x, m_y, m_z, E_tot[, U_aux]), ntot the
+ * total number of padded cells of all blocks, off_b the first padded cell of
+ * block b and (i, j, k) padded indices (interior cells start at ng).
+ */
+#ifndef TREF_H
+#define TREF_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { TREF_EOS_IDEAL = 0, TREF_EOS_TABLE = 1 };
+enum { TREF_PLM = 0, TREF_PPM = 1 };
+enum { TREF_OUTFLOW = 0, TREF_PERIODIC = 1 };
+enum { TREF_RHO = 0, TREF_MX = 1, TREF_MY = 2, TREF_MZ = 3, TREF_EN = 4, TREF_AUX = 5 };
+
+/* Tabulated EOS on a uniform (log10 rho, log10 T) grid (Sec. 4.2).  Arrays are
+ * [n_rho][n_T], T fastest, in cgs.  The oracle does not own them. */
+typedef struct {
+  int n_rho, n_T;
+  double lrho_min, lrho_max, lT_min, lT_max;
+  const double *log10_e, *log10_P, *log10_cs2;
+} tref_table;
+
+/* Physics and scheme parameters (Table 1 lists the production values). */
+typedef struct {
+  int eos;              /* TREF_EOS_IDEAL or TREF_EOS_TABLE */
+  int recon;            /* TREF_PLM or TREF_PPM */
+  int dual;             /* dual-energy auxiliary variable on (1) / off (0), Sec. 6 */
+  double gamma;         /* ideal-gas adiabatic index */
+  double eta1, eta2;    /* dual-energy switch and resync thresholds, Eqs. dual-primitive-switch, dual-sync */
+  double rho_floor, p_floor, u_floor;   /* floors (Table 1); u_floor = internal energy density of the floor state */
+  double unit_rho, unit_e;              /* code -> cgs factors used for table lookups */
+  int bh_on, excision_on;               /* softened moving point mass, one-way sink (Sec. 3.1) */
+  double GM, r_soft, r_exc;
+  double bh_t0, bh_x0[3], bh_v0[3], bh_a0[3];   /* r_bh(t) = x0 + v0 (t-t0) + a0 (t-t0)^2 / 2 */
+} tref_params;
+
+/* Mesh: a uniform-cell global grid covered by MeshBlocks (no AMR). */
+typedef struct {
+  int nb;               /* number of MeshBlocks */
+  const int *blocks;    /* nb * 6 ints: i0, j0, k0, nx, ny, nz (global cell index of the first interior cell, size) */
+  int N[3];             /* global cells per direction */
+  double xmin[3];       /* lower domain corner */
+  double dx[3];         /* cell widths */
+  int bc[3];            /* TREF_OUTFLOW or TREF_PERIODIC per direction */
+  int ng;               /* ghost width (2 for PLM, 3 for PPM) */
+} tref_mesh_desc;
+
+/* Event counters (floors applied, table clamps, excised cells). */
+typedef struct {
+  int64_t rho_floor, p_floor, u_floor, table_clamp, excised, dual_aux_used, synced;
+} tref_counts;
+
+typedef struct tref_mesh tref_mesh;
+
+/* ---- EOS (oracle/tref_eos.c) ---------------------------------------------- */
+
+/* Saha H/He mixture with radiation at (rho, T) in cgs.  out[0..8] =
+ * P, e (specific internal energy incl. ionisation and radiation), n_e, x_H+,
+ * y_He+, y_He2+, mu, P_gas, n_nuc. */
+void tref_saha_state(double rho, double T, double X, double Y, double *out);
+/* Pure-hydrogen Saha ionised fraction from the closed-form quadratic (pin). */
+double tref_saha_pure_h_xe(double rho, double T);
+/* Fill the table: log10 e, log10 P, log10 cs^2 and Gamma_1 on the grid. */
+void tref_eos_build(int n_rho, int n_T, double lrho_min, double lrho_max, double lT_min,
+                    double lT_max, double X, double Y, double *log10_e, double *log10_P,
+                    double *log10_cs2, double *gamma1);
+/* Bilinear evaluation at (rho, T) (cgs): out P, e, cs2. */
+void tref_eos_eval_rhoT(const tref_table *t, double rho, double T, double *P, double *e, double *cs2);
+/* Inversion (rho, e) -> (T, P, cs2), cgs.  Returns 1 if clamped to the table edge. */
+int tref_eos_invert(const tref_table *t, double rho, double e, double *T, double *P, double *cs2,
+                    double *e_used);
+/* Inversion (rho, P) -> T on the pressure column (initial data only). */
+double tref_eos_T_from_P(const tref_table *t, double rho, double P);
+
+/* ---- mesh and hydro (oracle/tref_hydro.c) ---------------------------------- */
+
+tref_mesh *tref_mesh_new(const tref_mesh_desc *d, const tref_params *p, const tref_table *t);
+void tref_mesh_free(tref_mesh *m);
+int64_t tref_mesh_ntot(const tref_mesh *m);            /* padded cells of all blocks */
+int64_t tref_mesh_block_offset(const tref_mesh *m, int b);
+int tref_nvar(const tref_mesh *m);
+void tref_set_params(tref_mesh *m, const tref_params *p);
+
+/* a1: copy neighbour interior cells (periodic wrap or zero-gradient outflow)
+ * into the ghost cells of the listed blocks (all blocks if ids == NULL). */
+void tref_ghost_fill(const tref_mesh *m, double *U, int nvar, int nact, const int *ids);
+/* a1 under LAT: mode[o] of the source block o selects the ghost value:
+ * 0 copy from Udst, 1 copy from Ucur, 2 Uold + s_block[o] (Ucur - Uold). */
+void tref_ghost_fill_modes(const tref_mesh *m, double *Udst, const double *Ucur, const double *Uold,
+                           const int *mode, const double *s_block, int nact, const int *ids);
+/* size (doubles) of one block's flux register: 6 sides x nvar x face cells */
+int64_t tref_freg_block_size(const tref_mesh *m, int b);
+
+/* a2 + a3: conserved -> primitive for one cell.  w[0..7] = rho, vx, vy, vz, P,
+ * Gamma_e (= 1 + P/U), Gamma_1 (= rho cs^2 / P), U_aux. */
+void tref_cons_to_prim(const tref_mesh *m, const double *u, double *w, tref_counts *c);
+
+/* One Runge-Kutta stage (a2-a6) on the listed blocks.  stage 0:
+ * Uout = U0 + dt L(U0); stage 1: Uout = (U0 + Uin + dt L(Uin)) / 2.  Uin must
+ * have filled ghosts.  dt_b[], t_b[] are indexed by block id (t_b = time at the
+ * start of the block's step).  If flux_reg != NULL the face fluxes of block
+ * boundary faces are accumulated into it (LAT refluxing, a9). */
+void tref_stage(const tref_mesh *m, int stage, int nact, const int *ids, const double *U0,
+                const double *Uin, double *Uout, const double *dt_b, const double *t_b,
+                double *flux_reg, tref_counts *c);
+/* a8: excision reset of the listed blocks at time t_b[b] (+ dt_b[b]). */
+void tref_excise(const tref_mesh *m, double *U, int nact, const int *ids, const double *t_end_b,
+                 tref_counts *c);
+/* a8: dual-energy resync (Eq. dual-sync) of the listed blocks; E ghosts must be filled. */
+void tref_dual_sync(const tref_mesh *m, double *U, int nact, const int *ids, tref_counts *c);
+/* a7: per-block CFL time step from state U at time t_b[b] (no ghosts needed). */
+void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *t_b, double *dt_b,
+                 tref_counts *c);
+/* Full synchronised RK2 step of every block with one dt (ghost fill, two
+ * stages, excision, ghost fill, resync).  Uscr is a second state buffer. */
+void tref_step(const tref_mesh *m, double *U, double *Uscr, double dt, double t, tref_counts *c);
+/* Primitive (rho, vx, vy, vz, P) per interior cell -> conserved state, U_aux = U. */
+void tref_prim_to_cons(const tref_mesh *m, const double *W, double *U);
+/* Softened point-mass potential at position x (Eq. bh-softened-gravity). */
+double tref_phi_bh(const tref_params *p, const double *x, double t);
+
+/* ---- learned EOS guess: MLP 2 -> 64 -> 64 -> 2 with SiLU (oracle/tref_mlp.c) */
+
+enum { TREF_MLP_H = 64, TREF_MLP_NPARAM = 2 * 64 + 64 + 64 * 64 + 64 + 64 * 2 + 2 };
+/* y = MLP(x) for n inputs x[n][2] -> y[n][2]. */
+void tref_mlp_forward(const double *params, int64_t n, const double *x, double *y);
+/* Mean-squared-error loss over n samples and its gradient w.r.t. params. */
+double tref_mlp_loss_grad(const double *params, int64_t n, const double *x, const double *target,
+                          double *grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,189 @@
+"""Seeded synthetic workloads: MeshBlock layouts and primitive initial fields.
+
+This module holds geometry, random numbers and closed-form primitive profiles
+only -- none of the hydro method's arithmetic.  The conversion of primitives to
+conserved variables (which needs the equation of state) is done separately by
+the CUDA library (``tde_prim_to_cons``) and by the CPU oracle, each with its own
+code.  Thermodynamic constants a profile needs (a pressure level, a sound speed)
+are passed in by the caller.
+
+State layout shared by every consumer: a state is ``[nvar][ntot]`` float64 with
+MeshBlock ``b`` occupying padded cells ``off[b] .. off[b+1]``, padded index
+``(k * Py + j) * Px + i`` (x fastest), interior cells starting at ``ng`` in
+every active direction (a direction with one global cell is inactive and has no
+ghost cells).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+OUTFLOW, PERIODIC = 0, 1
+
+
+@dataclass
+class MeshLayout:
+    blocks: np.ndarray          # [nb, 6] int32: i0, j0, k0, nx, ny, nz
+    N: tuple                    # global cells per direction
+    xmin: tuple
+    dx: tuple
+    bc: tuple                   # OUTFLOW / PERIODIC per direction
+    ng: int
+    off: np.ndarray = field(init=False)
+    pd: np.ndarray = field(init=False)
+
+    def __post_init__(self):
+        self.blocks = np.ascontiguousarray(self.blocks, dtype=np.int32).reshape(-1, 6)
+        act = np.array([n > 1 for n in self.N])
+        self.active = act
+        self.pd = self.blocks[:, 3:6] + 2 * self.ng * act[None, :]
+        sizes = self.pd.prod(axis=1).astype(np.int64)
+        self.off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+    @property
+    def nb(self):
+        return len(self.blocks)
+
+    @property
+    def ntot(self):
+        return int(self.off[-1])
+
+    @property
+    def ncells(self):
+        return int(np.prod(self.N))
+
+    def gofs(self, a):
+        return self.ng if self.active[a] else 0
+
+    def interior_index(self, b):
+        """(flat padded indices into the state, global (gk, gj, gi)) of block b's interior."""
+        i0, j0, k0, nx, ny, nz = self.blocks[b]
+        px, py, _ = self.pd[b]
+        gx, gy, gz = self.gofs(0), self.gofs(1), self.gofs(2)
+        k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        flat = self.off[b] + ((k + gz) * py + (j + gy)) * px + (i + gx)
+        return flat, (k + k0, j + j0, i + i0)
+
+    def to_global(self, U):
+        """[nvar, ntot] state -> [nvar, Nz, Ny, Nx] interior grid."""
+        U = np.asarray(U)
+        out = np.zeros((U.shape[0], self.N[2], self.N[1], self.N[0]), dtype=U.dtype)
+        for b in range(self.nb):
+            flat, (gk, gj, gi) = self.interior_index(b)
+            out[:, gk, gj, gi] = U[:, flat]
+        return out
+
+    def from_global(self, G):
+        """[nvar, Nz, Ny, Nx] -> [nvar, ntot] state (ghost cells zero)."""
+        G = np.asarray(G)
+        U = np.zeros((G.shape[0], self.ntot), dtype=G.dtype)
+        for b in range(self.nb):
+            flat, (gk, gj, gi) = self.interior_index(b)
+            U[:, flat] = G[:, gk, gj, gi]
+        return U
+
+    def cell_centres(self):
+        """x, y, z of the global interior grid, each [Nz, Ny, Nx]."""
+        ax = [self.xmin[a] + (np.arange(self.N[a]) + 0.5) * self.dx[a] for a in range(3)]
+        z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        return x, y, z
+
+
+def uniform_layout(N, block, domain=((0.0, 1.0),) * 3, bc=(OUTFLOW,) * 3, ng=2):
+    """Uniform grid of N[a] cells per direction split into blocks of block[a] cells
+    (the last block of a direction takes the remainder: ragged tails allowed)."""
+    starts = []
+    for a in range(3):
+        s = list(range(0, N[a], block[a]))
+        starts.append([(x, min(block[a], N[a] - x)) for x in s])
+    blocks = []
+    for k0, nz in starts[2]:
+        for j0, ny in starts[1]:
+            for i0, nx in starts[0]:
+                blocks.append((i0, j0, k0, nx, ny, nz))
+    dx = tuple((domain[a][1] - domain[a][0]) / N[a] for a in range(3))
+    return MeshLayout(np.array(blocks), tuple(N), tuple(d[0] for d in domain), dx, tuple(bc), ng)
+
+
+def mixed_layout(root_N, root_block, split, domain, bc, ng):
+    """Uniform-cell grid of root blocks; the root blocks whose index is in `split`
+    are replaced by eight half-size blocks (same cell size, no refinement)."""
+    nbx = [root_N[a] // root_block for a in range(3)]
+    blocks = []
+    h = root_block // 2
+    for bk in range(nbx[2]):
+        for bj in range(nbx[1]):
+            for bi in range(nbx[0]):
+                i0, j0, k0 = bi * root_block, bj * root_block, bk * root_block
+                if (bi, bj, bk) in split:
+                    for dk in (0, h):
+                        for dj in (0, h):
+                            for di in (0, h):
+                                blocks.append((i0 + di, j0 + dj, k0 + dk, h, h, h))
+                else:
+                    blocks.append((i0, j0, k0, root_block, root_block, root_block))
+    dx = tuple((domain[a][1] - domain[a][0]) / root_N[a] for a in range(3))
+    return MeshLayout(np.array(blocks), tuple(root_N), tuple(d[0] for d in domain), dx, tuple(bc), ng)
+
+
+def prim_state(layout, rho, vx, vy, vz, P):
+    """Pack global [Nz, Ny, Nx] primitive fields into the padded layout, 5 fields."""
+    G = np.stack([np.broadcast_to(np.asarray(f, dtype=np.float64), (layout.N[2], layout.N[1], layout.N[0]))
+                  for f in (rho, vx, vy, vz, P)])
+    return layout.from_global(G)
+
+
+# --------------------------------------------------------------------- profiles
+
+def sod(layout, axis=0, rho=(1.0, 0.125), P=(1.0, 0.1), x0=0.5):
+    """Sod shock tube along `axis` (rho 1/0.125, P 1/0.1, at rest)."""
+    c = layout.cell_centres()[axis]
+    left = c < x0
+    r = np.where(left, rho[0], rho[1])
+    p = np.where(left, P[0], P[1])
+    z = np.zeros_like(r)
+    return prim_state(layout, r, z, z, z, p)
+
+
+def sound_wave(layout, amp=1e-6, rho0=1.0, P0=None, gamma=5.0 / 3.0, axis=0, wavelength=1.0):
+    """Linear right-moving sound wave; rho0, P0 background, c_s = sqrt(gamma P0 / rho0)."""
+    P0 = 1.0 / gamma if P0 is None else P0
+    cs = np.sqrt(gamma * P0 / rho0)
+    x = layout.cell_centres()[axis]
+    s = np.sin(2 * np.pi * (x - layout.xmin[axis]) / wavelength)
+    r = rho0 * (1 + amp * s)
+    v = cs * amp * s
+    p = P0 * (1 + gamma * amp * s)
+    z = np.zeros_like(r)
+    vel = [z, z, z]
+    vel[axis] = v
+    return prim_state(layout, r, *vel, p)
+
+
+def entropy_wave(layout, rho0, P0, v_adv, amp=1e-3, seed=0, axis=0, wavelength=1.0):
+    """Entropy wave rho = rho0 (1 + amp sin(2 pi x / wavelength + phi)), uniform P and v
+    along `axis`; phi drawn from the seed."""
+    phi = np.random.default_rng(seed).uniform(0.0, 2 * np.pi)
+    x = layout.cell_centres()[axis]
+    r = rho0 * (1 + amp * np.sin(2 * np.pi * (x - layout.xmin[axis]) / wavelength + phi))
+    z = np.zeros_like(r)
+    vel = [z, z, z]
+    vel[axis] = np.full_like(r, v_adv)
+    return prim_state(layout, r, *vel, np.full_like(r, P0)), phi
+
+
+def random_smooth(layout, seed=0, rho0=1.0, P0=1.0, drho=0.2, dv=0.3, dP=0.2, modes=3):
+    """Seeded smooth periodic fields (sums of low Fourier modes)."""
+    rng = np.random.default_rng(seed)
+    x, y, z = layout.cell_centres()
+    L = [layout.dx[a] * layout.N[a] for a in range(3)]
+
+    def field_(amp):
+        f = np.zeros_like(x)
+        for _ in range(modes):
+            k = rng.integers(0, 3, size=3)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += np.sin(2 * np.pi * (k[0] * x / L[0] + k[1] * y / L[1] + k[2] * z / L[2]) + ph)
+        return amp * f / modes
+
+    r = rho0 * (1 + field_(drho))
+    return prim_state(layout, r, field_(dv), field_(dv), field_(dv), P0 * (1 + field_(dP)))
