@@ -1,0 +1,251 @@
+/*
+ * tde.h -- C ABI of libtde.so, the GB300 (sm_103a) implementation of the
+ * per-MeshBlock finite-volume hydro stage of "An End-to-End Numerical Framework
+ * for Tidal Disruption Events with AthenaK" (arxiv 2609.37859).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a tde_status code.  No C++ exception, abort or device trap
+ *    crosses this boundary; tde_last_error() gives a one-line message for the
+ *    last failing call on a context.
+ *  - "device" pointers are CUDA global-memory pointers on the context's device
+ *    (e.g. from torch tensors); "host" pointers are ordinary CPU memory.
+ *  - The library never frees memory it did not allocate.  Objects it creates
+ *    (context, EOS, mesh, including their device workspaces) are released by the
+ *    matching *_destroy / tde_finalize call.
+ *  - Work is enqueued asynchronously on the context's CUDA stream.  Calls that
+ *    return host data (tde_counts_read, tde_mesh_info) synchronise that stream.
+ *    Every launch sequence of tde_hydro_stage / tde_step / tde_dual_energy_sync
+ *    is free of host synchronisation and may be captured in a CUDA graph.
+ *
+ * State layout.  A MeshBlock is a box of nx*ny*nz interior cells padded with
+ * ng ghost cells on both sides of every active direction (a direction whose
+ * global extent is one cell is inactive: no ghosts, no flux).  A state is one
+ * device array of nvar * ntot doubles,
+ *     U[v * ntot + off_b + (k * py + j) * px + i],
+ * v = 0..nvar-1 the conserved variables (rho, m_x, m_y, m_z, E_tot[, U_aux])
+ * (Eq. remap-state-vector), off_b the first padded cell of block b (blocks in
+ * the order given to tde_mesh_create), (px, py, pz) the padded block size and
+ * (i, j, k) padded indices; interior cells start at ng.
+ */
+#ifndef TDE_H
+#define TDE_H
+#include <stddef.h>
+#include <stdint.h>
+#if defined(__GNUC__)
+#define TDE_API __attribute__((visibility("default")))
+#else
+#define TDE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TDE_OK = 0,
+  TDE_EINVAL = 1,    /* invalid argument (null pointer, bad size, inconsistent layout) */
+  TDE_ENOMEM = 2,    /* device or host allocation failed */
+  TDE_ECUDA = 3,     /* a CUDA runtime call failed (message in tde_last_error) */
+  TDE_ERANGE = 4,    /* table input out of range (only where the call says so) */
+  TDE_ENUMERIC = 5,  /* non-finite or non-positive density after floors */
+  TDE_ETIMEOUT = 6   /* a bounded device wait expired */
+} tde_status;
+
+enum { TDE_EOS_IDEAL = 0, TDE_EOS_TABLE = 1 };
+enum { TDE_RECON_PLM = 0, TDE_RECON_PPM = 1 };
+enum { TDE_BC_OUTFLOW = 0, TDE_BC_PERIODIC = 1 };
+enum { TDE_INVERT_BISECT = 0, TDE_INVERT_SURROGATE = 1 };
+
+typedef struct tde_ctx tde_ctx;
+typedef struct tde_eos tde_eos;
+typedef struct tde_mesh tde_mesh;
+
+/* Scheme and physics parameters (Table 1 of the paper lists the production
+ * values: RK2, PLM, CFL, floors, eta_1 = 1e-3, eta_2 = 1e-4). */
+typedef struct {
+  int eos;              /* TDE_EOS_IDEAL or TDE_EOS_TABLE (Sec. 4) */
+  int recon;            /* TDE_RECON_PLM (ng >= 2) or TDE_RECON_PPM (ng >= 3) */
+  int dual;             /* 1: evolve the auxiliary internal energy U_aux (Sec. 6) */
+  double gamma;         /* ideal-gas adiabatic index (TDE_EOS_IDEAL) */
+  double eta1, eta2;    /* Eq. dual-primitive-switch and Eq. dual-sync thresholds */
+  double rho_floor, p_floor, u_floor;  /* floors; u_floor = internal energy density of the floor state */
+  double unit_rho, unit_e;             /* code -> cgs factors applied before table lookups */
+} tde_params;
+
+/* Softened point-mass potential on the trajectory
+ * r_bh(t) = x0 + v0 (t - t0) + a0 (t - t0)^2 / 2 (Eq. bh-softened-gravity, Sec. 3.1). */
+typedef struct {
+  int on;               /* gravity source terms on */
+  int excise;           /* one-way sink of radius r_exc */
+  double GM, r_soft, r_exc;
+  double t0, x0[3], v0[3], a0[3];
+} tde_bh_state;
+
+/* One MeshBlock: global index of its first interior cell and its size. */
+typedef struct {
+  int i0, j0, k0, nx, ny, nz;
+} tde_block_desc;
+
+/* Uniform-cell global grid covered by the MeshBlocks (no refinement). */
+typedef struct {
+  int N[3];             /* global cells per direction (1 = inactive direction) */
+  double xmin[3];       /* lower domain corner */
+  double dx[3];         /* cell widths */
+  int bc[3];            /* TDE_BC_OUTFLOW / TDE_BC_PERIODIC per direction */
+  int ng;               /* ghost width */
+} tde_grid_desc;
+
+/* Device-side event counters (cumulative until reset). */
+typedef struct {
+  uint64_t rho_floor, p_floor, u_floor, table_clamp, excised, dual_aux_used, synced, nonfinite;
+} tde_counts;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+TDE_API int tde_init(tde_ctx **out, int device, void *cuda_stream);
+TDE_API int tde_set_stream(tde_ctx *ctx, void *cuda_stream);
+/* One-line description of the last error on this context ("" if none). */
+TDE_API const char *tde_last_error(const tde_ctx *ctx);
+TDE_API int tde_finalize(tde_ctx *ctx);
+
+/* ---- equation of state (Sec. 4.2) --------------------------------------- */
+
+/* Load a tabulated EOS sampled on a uniform grid in (log10 rho, log10 T)
+ * (Eq. eos-table-range: the paper's table is 640 x 640 on ln rho, ln T; any
+ * n_rho, n_T >= 2 is accepted).  Host arrays [n_rho][n_T] (T fastest) of
+ * log10 e_th (erg/g), log10 P (dyn/cm^2) and log10 c_s^2 (cm^2/s^2) are COPIED
+ * to the device; the caller keeps ownership.  The runtime map (rho, U_EOS) ->
+ * (T, P, c_s) interpolates bilinearly in the table (Sec. 4.2, last paragraph).
+ * TDE_EINVAL if a log10 e column is not strictly increasing in T (the
+ * inversion needs it) or a value is not finite. */
+TDE_API int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double log10_rho_min,
+                       double log10_rho_max, double log10_T_min, double log10_T_max,
+                       const double *log10_e, const double *log10_P, const double *log10_cs2,
+                       tde_eos **out);
+TDE_API int tde_eos_destroy(tde_eos *eos);
+
+/* Invert n cells (rho, e) -> (T, P, cs2), all cgs, device arrays of n doubles.
+ * mode TDE_INVERT_BISECT: binary search of the interpolated log10 e column.
+ * T, P or cs2 may be NULL.  Inputs outside the table are clamped to its edge and
+ * counted (counts may be NULL; reading it synchronises the stream). */
+TDE_API int tde_eos_invert(tde_eos *eos, int mode, int64_t n, const double *rho, const double *e,
+                   double *T, double *P, double *cs2, tde_counts *counts);
+/* Forward evaluation at (rho, T), cgs, device arrays; outputs may be NULL. */
+TDE_API int tde_eos_eval_rhoT(tde_eos *eos, int64_t n, const double *rho, const double *T, double *P,
+                      double *e, double *cs2);
+
+/* ---- mesh (MeshBlocks with ghost zones: Sec. 2, Sec. 3.2) ---------------- */
+
+/* Build a mesh of nblocks MeshBlocks (host array) covering `grid` exactly once,
+ * with the ghost map (periodic wrap / zero-gradient outflow copy).  eos may be
+ * NULL for TDE_EOS_IDEAL.  TDE_EINVAL for overlaps, gaps, ng below the
+ * reconstruction's stencil (PLM 2, PPM 3), more than 2^31 padded cells or a
+ * block edge above 64 cells. */
+TDE_API int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *blocks,
+                    const tde_grid_desc *grid, const tde_params *params, tde_eos *eos,
+                    tde_mesh **out);
+TDE_API int tde_mesh_destroy(tde_mesh *mesh);
+/* ntot (padded cells of all blocks), nvar, and optionally the nblocks + 1 block
+ * offsets (host array; may be NULL). */
+TDE_API int tde_mesh_info(const tde_mesh *mesh, int64_t *ntot, int *nvar, int64_t *block_offsets);
+/* Replace the scheme parameters (same eos kind and dual flag). */
+TDE_API int tde_mesh_set_params(tde_mesh *mesh, const tde_params *params);
+
+/* Bind the caller-owned device states: U (the evolved state) and U1 (the
+ * intermediate Runge-Kutta state), nvar * ntot doubles each. */
+TDE_API int tde_mesh_bind_state(tde_mesh *mesh, double *U, double *U1);
+
+/* Primitive fields W (device, 5 * ntot: rho, vx, vy, vz, P) -> conserved state U
+ * on the interior cells (U_aux = the thermal energy density).  The tabulated
+ * EOS finds T from (rho, P) by bisection of the interpolated pressure. */
+TDE_API int tde_prim_to_cons(tde_mesh *mesh, const double *W, double *U);
+
+/* Fill the ghost cells of the first nvar fields of a state (a1). */
+TDE_API int tde_ghost_fill(tde_mesh *mesh, double *state, int nvar);
+
+/* One stage of the SSP-RK2 update (a1-a6 of the hydro stage) on nblk blocks:
+ *   stage 0:  U1 = U + dt L(U)
+ *   stage 1:  U  = (U_start + U1 + dt L(U1)) / 2   (U holds U_start on entry)
+ * L is the finite-volume operator of Eqs. frame-momentum and frame-energy with
+ * PLM/PPM reconstruction, the HLLC solver, the dual-energy flux and compression
+ * (Eqs. dual-flux .. dual-tabulated-compression) and the point-mass source
+ * (Eqs. lat-grav-momentum, lat-grav-energy) at the stage time (t_n, then
+ * t_n + dt).  Ghost cells of the stage input are refreshed inside the call.
+ * block_ids: device int32[nblk], or NULL for all blocks in order (nblk ignored).
+ * dt_block, t_block: device double arrays indexed by block id (per-block step
+ * and step start time, as LAT needs).  bh: host struct, may be NULL (no gravity). */
+TDE_API int tde_hydro_stage(tde_mesh *mesh, int stage, int nblk, const int32_t *block_ids,
+                    const double *dt_block, const double *t_block, const tde_bh_state *bh);
+
+/* Per-block CFL step (a7, Sec. 7.1 "local CFL limit from hydrodynamic and source
+ * terms"): dt_b = cfl * min over interior cells outside the excision sphere of
+ * min_d dx_d / (|v_d| + c_s) and sqrt(dx_min / |g_bh|).  t_block (device, may be
+ * NULL = 0) gives the BH time per block.  dt_block: device out [nblocks];
+ * dt_min: device out [1] (may be NULL), the minimum over blocks (Eq. lat-base-dt). */
+TDE_API int tde_compute_dt(tde_mesh *mesh, double cfl, const double *t_block, const tde_bh_state *bh,
+                   double *dt_block, double *dt_min);
+
+/* Excision reset (a8, Sec. 3.1): interior cells with |r - r_bh(t_end_b)| < r_exc
+ * of the listed blocks become rho_floor, zero momentum, U = u_floor. */
+TDE_API int tde_excise(tde_mesh *mesh, int nblk, const int32_t *block_ids, const double *t_end_block,
+               const tde_bh_state *bh);
+
+/* Dual-energy resynchronisation (a8, Eq. dual-sync): refreshes the E ghosts of
+ * U, then U_aux <- U_cons where U_cons > 0 and U_cons > eta2 * max of E_tot
+ * over the 3x3x3 neighbourhood.  eta2 < 0 uses the mesh parameter. */
+TDE_API int tde_dual_energy_sync(tde_mesh *mesh, int nblk, const int32_t *block_ids, double eta2);
+
+/* The mesh keeps its simulation time t in device memory (0 after creation).
+ * tde_step advances it by the step's dt without a host round trip. */
+TDE_API int tde_mesh_set_time(tde_mesh *mesh, double t);
+TDE_API int tde_mesh_get_time(tde_mesh *mesh, double *t);   /* synchronises the stream */
+
+/* One synchronised SSP-RK2 step of every block from the mesh time t: dt from the
+ * CFL condition if cfl > 0 (else dt_fixed), stage 0, stage 1, excision (at
+ * t + dt), resync if dual energy is on; then t += dt.  The step's dt is also
+ * written to dt_out (device double, may be NULL). */
+TDE_API int tde_step(tde_mesh *mesh, double cfl, double dt_fixed, const tde_bh_state *bh, double *dt_out);
+
+/* Copy the cumulative device counters to *out (synchronises the stream) and
+ * optionally reset them. */
+TDE_API int tde_counts_read(tde_mesh *mesh, tde_counts *out, int reset);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Kernel classes counted and (optionally) timed by the context. */
+enum {
+  TDE_K_C2P = 0,      /* conserved -> primitive (+ CFL minimum) */
+  TDE_K_DT = 1,       /* per-block dt finalisation */
+  TDE_K_GHOST = 2,    /* ghost-layer gather */
+  TDE_K_SWEEP_X = 3,  /* reconstruction + HLLC + divergence along x */
+  TDE_K_SWEEP_Y = 4,
+  TDE_K_SWEEP_Z = 5,  /* ... along z, with the final update of the stage */
+  TDE_K_SYNC = 6,     /* dual-energy resync */
+  TDE_K_EXCISE = 7,
+  TDE_K_SCALAR = 8,   /* device scalar bookkeeping (time, dt) */
+  TDE_K_P2C = 9,      /* primitive -> conserved */
+  TDE_K_EOS = 10,     /* batch EOS inversion / evaluation */
+  TDE_K_PROBE = 11,   /* peak-rate probe */
+  TDE_K_NKIND = 16
+};
+
+/* Every kernel the context launches is counted per class.  With timing on, a
+ * CUDA event pair on the context's stream brackets each launch and
+ * tde_profile_read() accumulates the elapsed times.  enable: 1 on, 0 off;
+ * both reset the counters. */
+TDE_API int tde_profile(tde_ctx *ctx, int enable);
+/* Per-class launch counts and summed device milliseconds since the last reset
+ * (arrays of TDE_K_NKIND entries, either may be NULL).  Synchronises the stream. */
+TDE_API int tde_profile_read(tde_ctx *ctx, uint64_t *launches, double *ms);
+
+/* Measured FP64 fused multiply-add throughput of the device (FLOP/s, an FMA
+ * counted as 2), from a kernel of independent FMA chains on every SM.  The
+ * hydro stage is bound by this rate on sm_103a.  Synchronises the stream. */
+TDE_API int tde_probe_fp64(tde_ctx *ctx, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

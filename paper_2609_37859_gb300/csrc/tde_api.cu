@@ -1,0 +1,661 @@
+// tde_api.cu -- the C ABI of libtde.so (declared in include/tde.h): object
+// lifetimes, argument checking, the ghost map and the launch sequences of a
+// stage and of a step.  No exception or abort leaves this file.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "tde_internal.h"
+
+namespace tde {
+size_t sweep_smem_max(const tde_mesh *m);
+cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids);
+}
+
+using namespace tde;
+
+namespace {
+
+int fail(tde_ctx *c, int code, const char *msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(tde_ctx *c, cudaError_t e, const char *where) {
+  if (c) {
+    c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return TDE_ECUDA;
+}
+
+#define CK(ctx, call)                                             \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return cuda_fail((ctx), _e, #call);    \
+  } while (0)
+
+BH make_bh(const tde_bh_state *s) {
+  BH b{};
+  if (!s) return b;
+  b.on = s->on;
+  b.excise = s->excise;
+  b.GM = s->GM;
+  b.rs2 = s->r_soft * s->r_soft;
+  b.rexc = s->r_exc;
+  b.t0 = s->t0;
+  for (int a = 0; a < 3; ++a) {
+    b.x0[a] = s->x0[a];
+    b.v0[a] = s->v0[a];
+    b.a0[a] = s->a0[a];
+  }
+  return b;
+}
+
+bool fill_phys(tde_mesh *m, const tde_params *pr, tde_eos *eos) {
+  Phys &p = m->phys;
+  p.eos = pr->eos;
+  p.recon = pr->recon;
+  p.dual = pr->dual ? 1 : 0;
+  p.nvar = 5 + p.dual;
+  p.nwv = (p.eos == EOS_TABLE ? 7 : 5) + p.dual;
+  p.gamma = pr->gamma;
+  p.gm1 = pr->gamma - 1.0;
+  p.inv_gm1 = 1.0 / (pr->gamma - 1.0);
+  p.eta1 = pr->eta1;
+  p.eta2 = pr->eta2;
+  p.rho_floor = pr->rho_floor;
+  p.p_floor = pr->p_floor;
+  p.u_floor = pr->u_floor;
+  p.unit_rho = pr->unit_rho;
+  p.unit_e = pr->unit_e;
+  p.inv_unit_p = 1.0 / (pr->unit_rho * pr->unit_e);
+  p.inv_unit_e = 1.0 / pr->unit_e;
+  if (p.eos == EOS_TABLE) {
+    if (!eos) return false;
+    p.tab = eos->tab;
+  }
+  return true;
+}
+
+}  // namespace
+
+// ======================================================== context ====
+
+extern "C" int tde_init(tde_ctx **out, int device, void *cuda_stream) {
+  if (!out) return TDE_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TDE_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return TDE_ECUDA;
+  tde_ctx *c = new (std::nothrow) tde_ctx;
+  if (!c) return TDE_ENOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  *out = c;
+  return TDE_OK;
+}
+
+extern "C" int tde_set_stream(tde_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return TDE_EINVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return TDE_OK;
+}
+
+extern "C" const char *tde_last_error(const tde_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" int tde_finalize(tde_ctx *ctx) {
+  if (!ctx) return TDE_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &r : ctx->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  delete ctx;
+  return TDE_OK;
+}
+
+// ============================================================= EOS ====
+
+extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_min, double lr_max,
+                                  double lT_min, double lT_max, const double *log10_e,
+                                  const double *log10_P, const double *log10_cs2, tde_eos **out) {
+  if (!ctx || !out) return TDE_EINVAL;
+  *out = nullptr;
+  if (n_rho < 2 || n_T < 2 || !log10_e || !log10_P || !log10_cs2)
+    return fail(ctx, TDE_EINVAL, "tde_eos_load_table: table size or pointer");
+  if (!(lr_max > lr_min) || !(lT_max > lT_min))
+    return fail(ctx, TDE_EINVAL, "tde_eos_load_table: empty range");
+  const size_t nn = (size_t)n_rho * n_T;
+  for (size_t k = 0; k < nn; ++k)
+    if (!isfinite(log10_e[k]) || !isfinite(log10_P[k]) || !isfinite(log10_cs2[k]))
+      return fail(ctx, TDE_EINVAL, "tde_eos_load_table: non-finite entry");
+  for (int i = 0; i < n_rho; ++i)
+    for (int j = 0; j + 1 < n_T; ++j)
+      if (!(log10_e[(size_t)i * n_T + j + 1] > log10_e[(size_t)i * n_T + j]))
+        return fail(ctx, TDE_EINVAL, "tde_eos_load_table: log10 e column not increasing in T");
+  tde_eos *e = new (std::nothrow) tde_eos;
+  if (!e) return TDE_ENOMEM;
+  e->ctx = ctx;
+  cudaError_t err = cudaMalloc(&e->d_data, 3 * nn * sizeof(double));
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_cnt, sizeof(Counters));
+  if (err != cudaSuccess) {
+    cudaFree(e->d_data);
+    delete e;
+    return cuda_fail(ctx, err, "tde_eos_load_table: cudaMalloc");
+  }
+  cudaMemcpy(e->d_data, log10_e, nn * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(e->d_data + nn, log10_P, nn * sizeof(double), cudaMemcpyHostToDevice);
+  err = cudaMemcpy(e->d_data + 2 * nn, log10_cs2, nn * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemset(e->d_cnt, 0, sizeof(Counters));
+  if (err != cudaSuccess) {
+    cudaFree(e->d_data);
+    cudaFree(e->d_cnt);
+    delete e;
+    return cuda_fail(ctx, err, "tde_eos_load_table: cudaMemcpy");
+  }
+  DTable &t = e->tab;
+  t.nr = n_rho;
+  t.nt = n_T;
+  t.lr0 = lr_min;
+  t.inv_dlr = (n_rho - 1) / (lr_max - lr_min);
+  t.lt0 = lT_min;
+  t.dlt = (lT_max - lT_min) / (n_T - 1);
+  t.le = e->d_data;
+  t.lp = e->d_data + nn;
+  t.lc = e->d_data + 2 * nn;
+  *out = e;
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_destroy(tde_eos *e) {
+  if (!e) return TDE_EINVAL;
+  cudaFree(e->d_data);
+  cudaFree(e->d_cnt);
+  delete e;
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_invert(tde_eos *e, int mode, int64_t n, const double *rho, const double *en,
+                              double *T, double *P, double *cs2, tde_counts *counts) {
+  if (!e) return TDE_EINVAL;
+  tde_ctx *c = e->ctx;
+  if (n < 0 || (n > 0 && (!rho || !en))) return fail(c, TDE_EINVAL, "tde_eos_invert: arguments");
+  if (mode != TDE_INVERT_BISECT) return fail(c, TDE_EINVAL, "tde_eos_invert: unknown mode");
+  CK(c, launch_eos_invert(e, n, rho, en, T, P, cs2, c->stream));
+  if (counts) {
+    Counters h;
+    CK(c, cudaMemcpyAsync(&h, e->d_cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    memcpy(counts, &h, sizeof h);
+  }
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_eval_rhoT(tde_eos *e, int64_t n, const double *rho, const double *T,
+                                 double *P, double *en, double *cs2) {
+  if (!e) return TDE_EINVAL;
+  tde_ctx *c = e->ctx;
+  if (n < 0 || (n > 0 && (!rho || !T))) return fail(c, TDE_EINVAL, "tde_eos_eval_rhoT: arguments");
+  CK(c, launch_eos_eval(e, n, rho, T, P, en, cs2, c->stream));
+  return TDE_OK;
+}
+
+// ============================================================ mesh ====
+
+static int gcd_int(int a, int b) {
+  while (b) { int t = a % b; a = b; b = t; }
+  return a < 0 ? -a : a;
+}
+
+extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *blocks,
+                               const tde_grid_desc *grid, const tde_params *params, tde_eos *eos,
+                               tde_mesh **out) {
+  if (!ctx || !out) return TDE_EINVAL;
+  *out = nullptr;
+  if (nblocks <= 0 || !blocks || !grid || !params)
+    return fail(ctx, TDE_EINVAL, "tde_mesh_create: null argument or no blocks");
+  const int ng = grid->ng;
+  int act[3];
+  for (int a = 0; a < 3; ++a) {
+    if (grid->N[a] < 1 || !(grid->dx[a] > 0.0)) return fail(ctx, TDE_EINVAL, "tde_mesh_create: grid");
+    if (grid->bc[a] != TDE_BC_OUTFLOW && grid->bc[a] != TDE_BC_PERIODIC)
+      return fail(ctx, TDE_EINVAL, "tde_mesh_create: boundary condition");
+    act[a] = grid->N[a] > 1;
+  }
+  if (!act[0] && !act[1] && !act[2]) return fail(ctx, TDE_EINVAL, "tde_mesh_create: no active direction");
+  if (params->recon != TDE_RECON_PLM && params->recon != TDE_RECON_PPM)
+    return fail(ctx, TDE_EINVAL, "tde_mesh_create: reconstruction");
+  if (ng < (params->recon == TDE_RECON_PPM ? 3 : 2) || ng > 4)
+    return fail(ctx, TDE_EINVAL, "tde_mesh_create: ghost width below the reconstruction stencil");
+  if (params->eos != TDE_EOS_IDEAL && params->eos != TDE_EOS_TABLE)
+    return fail(ctx, TDE_EINVAL, "tde_mesh_create: eos kind");
+  if (params->eos == TDE_EOS_TABLE && !eos) return fail(ctx, TDE_EINVAL, "tde_mesh_create: table EOS without a table");
+  if (params->eos == TDE_EOS_IDEAL && !(params->gamma > 1.0)) return fail(ctx, TDE_EINVAL, "tde_mesh_create: gamma");
+  if (!(params->unit_rho > 0.0) || !(params->unit_e > 0.0)) return fail(ctx, TDE_EINVAL, "tde_mesh_create: units");
+
+  tde_mesh *m = new (std::nothrow) tde_mesh;
+  if (!m) return TDE_ENOMEM;
+  m->ctx = ctx;
+  m->eos = eos;
+  m->params = *params;
+  m->grid = *grid;
+  m->nb = nblocks;
+  if (!fill_phys(m, params, eos)) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: eos"); }
+  Phys &p = m->phys;
+  p.ng = ng;
+  p.dxmin = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    p.N[a] = grid->N[a];
+    p.bc[a] = grid->bc[a];
+    p.active[a] = act[a];
+    p.g[a] = act[a] ? ng : 0;
+    p.xmin[a] = grid->xmin[a];
+    p.dx[a] = grid->dx[a];
+    p.idx[a] = 1.0 / grid->dx[a];
+    if (act[a] && grid->dx[a] < p.dxmin) p.dxmin = grid->dx[a];
+  }
+
+  // block geometry, offsets, coverage
+  m->hblocks.resize(nblocks);
+  m->hoff.resize(nblocks + 1);
+  int unit[3] = {0, 0, 0};
+  int64_t off = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    const tde_block_desc &d = blocks[b];
+    const int o[3] = {d.i0, d.j0, d.k0}, n[3] = {d.nx, d.ny, d.nz};
+    DevBlock &B = m->hblocks[b];
+    B.i0 = d.i0; B.j0 = d.j0; B.k0 = d.k0;
+    int64_t cells = 1, inter = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (n[a] < 1 || o[a] < 0 || o[a] + n[a] > grid->N[a] || n[a] > 32 || (!act[a] && n[a] != 1)) {
+        delete m;
+        return fail(ctx, TDE_EINVAL, "tde_mesh_create: block outside the grid or edge above 32 cells");
+      }
+      B.n[a] = n[a];
+      B.p[a] = n[a] + 2 * p.g[a];
+      cells *= B.p[a];
+      inter *= n[a];
+      unit[a] = gcd_int(gcd_int(unit[a], o[a]), n[a]);
+      m->nmax[a] = std::max(m->nmax[a], n[a]);
+    }
+    B.off = off;
+    m->hoff[b] = off;
+    off += cells;
+    m->max_interior = std::max(m->max_interior, inter);
+  }
+  m->hoff[nblocks] = off;
+  m->ntot = off;
+  if (off >= (int64_t)INT32_MAX) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: more than 2^31 padded cells"); }
+  if (sweep_smem_max(m) > 227 * 1024) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: block too large for one sweep tile"); }
+
+  // owner map on the coarsest unit lattice that every block edge lies on
+  int cn[3];
+  for (int a = 0; a < 3; ++a) {
+    unit[a] = gcd_int(unit[a], grid->N[a]);
+    if (unit[a] <= 0) unit[a] = 1;
+    cn[a] = grid->N[a] / unit[a];
+  }
+  const int64_t ncoarse = (int64_t)cn[0] * cn[1] * cn[2];
+  std::vector<int32_t> owner(ncoarse, -1);
+  int64_t covered = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    const tde_block_desc &d = blocks[b];
+    for (int k = d.k0 / unit[2]; k < (d.k0 + d.nz) / unit[2]; ++k)
+      for (int j = d.j0 / unit[1]; j < (d.j0 + d.ny) / unit[1]; ++j)
+        for (int i = d.i0 / unit[0]; i < (d.i0 + d.nx) / unit[0]; ++i) {
+          int32_t &w = owner[((int64_t)k * cn[1] + j) * cn[0] + i];
+          if (w != -1) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: overlapping blocks"); }
+          w = b;
+          ++covered;
+        }
+  }
+  if (covered != ncoarse) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: blocks do not cover the grid"); }
+
+  // ghost map: every non-interior padded cell <- interior cell of the owner of
+  // its periodic image (periodic) or of the nearest boundary cell (outflow)
+  std::vector<int32_t> gmap;
+  std::vector<int32_t> gstart(nblocks + 1, 0);
+  for (int b = 0; b < nblocks; ++b) {
+    const DevBlock &B = m->hblocks[b];
+    const int o[3] = {B.i0, B.j0, B.k0};
+    int cnt = 0;
+    for (int k = 0; k < B.p[2]; ++k)
+      for (int j = 0; j < B.p[1]; ++j)
+        for (int i = 0; i < B.p[0]; ++i) {
+          const int c[3] = {i, j, k};
+          bool inside = true;
+          for (int a = 0; a < 3; ++a)
+            if (c[a] < p.g[a] || c[a] >= p.g[a] + B.n[a]) inside = false;
+          if (inside) continue;
+          int gg[3];
+          for (int a = 0; a < 3; ++a) {
+            int v = o[a] + c[a] - p.g[a];
+            const int N = grid->N[a];
+            if (v < 0 || v >= N) {
+              if (grid->bc[a] == TDE_BC_PERIODIC) v = ((v % N) + N) % N;
+              else v = v < 0 ? 0 : N - 1;
+            }
+            gg[a] = v;
+          }
+          const int ob = owner[((int64_t)(gg[2] / unit[2]) * cn[1] + gg[1] / unit[1]) * cn[0] + gg[0] / unit[0]];
+          const DevBlock &O = m->hblocks[ob];
+          const int oo[3] = {O.i0, O.j0, O.k0};
+          int64_t src = O.off + ((int64_t)(gg[2] - oo[2] + p.g[2]) * O.p[1] + (gg[1] - oo[1] + p.g[1])) * O.p[0] +
+                        (gg[0] - oo[0] + p.g[0]);
+          int64_t dst = B.off + ((int64_t)k * B.p[1] + j) * B.p[0] + i;
+          gmap.push_back((int32_t)dst);
+          gmap.push_back((int32_t)src);
+          ++cnt;
+        }
+    gstart[b + 1] = gstart[b] + cnt;
+    m->max_ghosts = std::max(m->max_ghosts, cnt);
+  }
+
+  // device allocations
+  std::vector<int32_t> allids(nblocks);
+  std::iota(allids.begin(), allids.end(), 0);
+  const size_t nt = (size_t)m->ntot;
+  cudaError_t err = cudaSuccess;
+  auto A = [&](void **ptr, size_t bytes) {
+    if (err == cudaSuccess) err = cudaMalloc(ptr, bytes > 0 ? bytes : 8);
+  };
+  A((void **)&m->d_blocks, sizeof(DevBlock) * nblocks);
+  A((void **)&m->d_ghost, sizeof(int32_t) * gmap.size());
+  A((void **)&m->d_gstart, sizeof(int32_t) * (nblocks + 1));
+  A((void **)&m->d_allids, sizeof(int32_t) * nblocks);
+  A((void **)&m->d_W, sizeof(double) * nt * p.nwv);
+  A((void **)&m->d_dU, sizeof(double) * nt * (p.nvar + 1));
+  A((void **)&m->d_scal, sizeof(double) * 4);
+  A((void **)&m->d_dtb, sizeof(double) * nblocks);
+  A((void **)&m->d_dtbits, sizeof(unsigned long long) * nblocks);
+  A((void **)&m->d_cnt, sizeof(Counters));
+  if (err != cudaSuccess) {
+    tde_mesh_destroy(m);
+    return cuda_fail(ctx, err, "tde_mesh_create: cudaMalloc");
+  }
+  std::vector<unsigned long long> inf_bits(nblocks);
+  const double inf = INFINITY;
+  unsigned long long ib;
+  memcpy(&ib, &inf, 8);
+  std::fill(inf_bits.begin(), inf_bits.end(), ib);
+  const double zeros[4] = {0, 0, 0, 0};
+  cudaMemcpy(m->d_blocks, m->hblocks.data(), sizeof(DevBlock) * nblocks, cudaMemcpyHostToDevice);
+  if (!gmap.empty()) cudaMemcpy(m->d_ghost, gmap.data(), sizeof(int32_t) * gmap.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(m->d_gstart, gstart.data(), sizeof(int32_t) * (nblocks + 1), cudaMemcpyHostToDevice);
+  cudaMemcpy(m->d_allids, allids.data(), sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
+  cudaMemcpy(m->d_scal, zeros, sizeof zeros, cudaMemcpyHostToDevice);
+  cudaMemcpy(m->d_dtbits, inf_bits.data(), sizeof(unsigned long long) * nblocks, cudaMemcpyHostToDevice);
+  cudaMemset(m->d_dU, 0, sizeof(double) * nt * (p.nvar + 1));
+  cudaMemset(m->d_W, 0, sizeof(double) * nt * p.nwv);
+  err = cudaMemset(m->d_cnt, 0, sizeof(Counters));
+  if (err == cudaSuccess) err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) {
+    tde_mesh_destroy(m);
+    return cuda_fail(ctx, err, "tde_mesh_create: upload");
+  }
+  *out = m;
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_destroy(tde_mesh *m) {
+  if (!m) return TDE_EINVAL;
+  cudaFree(m->d_blocks);
+  cudaFree(m->d_ghost);
+  cudaFree(m->d_gstart);
+  cudaFree(m->d_allids);
+  cudaFree(m->d_W);
+  cudaFree(m->d_dU);
+  cudaFree(m->d_scal);
+  cudaFree(m->d_dtb);
+  cudaFree(m->d_dtbits);
+  cudaFree(m->d_cnt);
+  delete m;
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_info(const tde_mesh *m, int64_t *ntot, int *nvar, int64_t *offsets) {
+  if (!m) return TDE_EINVAL;
+  if (ntot) *ntot = m->ntot;
+  if (nvar) *nvar = m->phys.nvar;
+  if (offsets) memcpy(offsets, m->hoff.data(), sizeof(int64_t) * (m->nb + 1));
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_set_params(tde_mesh *m, const tde_params *pr) {
+  if (!m || !pr) return TDE_EINVAL;
+  if (pr->eos != m->params.eos || (pr->dual ? 1 : 0) != m->phys.dual)
+    return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_params: eos kind or dual flag changed");
+  if (pr->recon == TDE_RECON_PPM && m->phys.ng < 3) return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_params: PPM needs ng >= 3");
+  Phys keep = m->phys;
+  if (!fill_phys(m, pr, m->eos)) { m->phys = keep; return TDE_EINVAL; }
+  Phys &p = m->phys;
+  for (int a = 0; a < 3; ++a) {
+    p.N[a] = keep.N[a]; p.bc[a] = keep.bc[a]; p.active[a] = keep.active[a]; p.g[a] = keep.g[a];
+    p.xmin[a] = keep.xmin[a]; p.dx[a] = keep.dx[a]; p.idx[a] = keep.idx[a];
+  }
+  p.ng = keep.ng;
+  p.dxmin = keep.dxmin;
+  m->params = *pr;
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_bind_state(tde_mesh *m, double *U, double *U1) {
+  if (!m || !U || !U1 || U == U1) return m ? fail(m->ctx, TDE_EINVAL, "tde_mesh_bind_state: states") : TDE_EINVAL;
+  m->U = U;
+  m->U1 = U1;
+  return TDE_OK;
+}
+
+extern "C" int tde_prim_to_cons(tde_mesh *m, const double *W, double *U) {
+  if (!m || !W || !U) return TDE_EINVAL;
+  CK(m->ctx, launch_prim2cons(m, W, U));
+  return TDE_OK;
+}
+
+extern "C" int tde_ghost_fill(tde_mesh *m, double *state, int nvar) {
+  if (!m || !state || nvar < 1 || nvar > 8) return TDE_EINVAL;
+  CK(m->ctx, launch_ghost(m, state, nvar, m->nb, m->d_allids));
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_set_time(tde_mesh *m, double t) {
+  if (!m) return TDE_EINVAL;
+  CK(m->ctx, cudaMemcpyAsync(m->d_scal, &t, sizeof t, cudaMemcpyHostToDevice, m->ctx->stream));
+  CK(m->ctx, cudaStreamSynchronize(m->ctx->stream));
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_get_time(tde_mesh *m, double *t) {
+  if (!m || !t) return TDE_EINVAL;
+  CK(m->ctx, cudaMemcpyAsync(t, m->d_scal, sizeof *t, cudaMemcpyDeviceToHost, m->ctx->stream));
+  CK(m->ctx, cudaStreamSynchronize(m->ctx->stream));
+  return TDE_OK;
+}
+
+// ============================================================ stage ====
+
+static int run_stage(tde_mesh *m, int stage, int nblk, const int32_t *ids, const BH &bh,
+                     TimeArgs ta, bool prims_ready) {
+  tde_ctx *c = m->ctx;
+  const double *Uin = stage == 0 ? m->U : m->U1;
+  double *Uout = stage == 0 ? m->U1 : m->U;
+  const bool all = ids == m->d_allids;
+  if (all) {
+    // every block advances: primitives of the interiors, then a copy of the
+    // neighbours' primitives into the ghost layer
+    if (!prims_ready) CK(c, launch_c2p(m, Uin, nblk, ids, false, bh, ta));
+    CK(c, launch_ghost(m, m->d_W, m->phys.nwv, nblk, ids));
+  } else {
+    // a subset advances: refresh the conserved ghosts of the listed blocks from
+    // the stage input and convert every padded cell of those blocks
+    CK(c, launch_ghost(m, const_cast<double *>(Uin), m->phys.nvar, nblk, ids));
+    CK(c, launch_c2p_padded(m, Uin, nblk, ids));
+  }
+  CK(c, launch_sweeps(m, stage, m->U, Uin, Uout, nblk, ids, bh, ta));
+  return TDE_OK;
+}
+
+extern "C" int tde_hydro_stage(tde_mesh *m, int stage, int nblk, const int32_t *ids,
+                               const double *dt_block, const double *t_block,
+                               const tde_bh_state *bh) {
+  if (!m) return TDE_EINVAL;
+  if (!m->U || !m->U1) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: no bound state");
+  if ((stage != 0 && stage != 1) || !dt_block) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: arguments");
+  if (!ids) { ids = m->d_allids; nblk = m->nb; }
+  if (nblk <= 0 || nblk > m->nb) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: block count");
+  TimeArgs ta{dt_block, 1, t_block, 1};
+  return run_stage(m, stage, nblk, ids, make_bh(bh), ta, false);
+}
+
+extern "C" int tde_compute_dt(tde_mesh *m, double cfl, const double *t_block,
+                              const tde_bh_state *bh, double *dt_block, double *dt_min) {
+  if (!m || !m->U || !(cfl > 0.0)) return m ? fail(m->ctx, TDE_EINVAL, "tde_compute_dt: arguments") : TDE_EINVAL;
+  TimeArgs ta{nullptr, 0, t_block, 1};
+  CK(m->ctx, launch_c2p(m, m->U, m->nb, m->d_allids, true, make_bh(bh), ta));
+  CK(m->ctx, launch_dt_finalize(m, cfl, dt_block ? dt_block : m->d_dtb, dt_min));
+  return TDE_OK;
+}
+
+extern "C" int tde_excise(tde_mesh *m, int nblk, const int32_t *ids, const double *t_end_block,
+                          const tde_bh_state *bh) {
+  if (!m || !m->U || !t_end_block) return TDE_EINVAL;
+  if (!bh || !bh->excise) return TDE_OK;
+  if (!ids) { ids = m->d_allids; nblk = m->nb; }
+  TimeArgs ta{nullptr, 0, t_end_block, 1};
+  CK(m->ctx, launch_excise(m, m->U, nblk, ids, make_bh(bh), ta));
+  return TDE_OK;
+}
+
+extern "C" int tde_dual_energy_sync(tde_mesh *m, int nblk, const int32_t *ids, double eta2) {
+  if (!m || !m->U) return TDE_EINVAL;
+  if (!m->phys.dual) return TDE_OK;
+  if (!ids) { ids = m->d_allids; nblk = m->nb; }
+  CK(m->ctx, launch_sync(m, m->U, nblk, ids, eta2 < 0.0 ? m->phys.eta2 : eta2));
+  return TDE_OK;
+}
+
+extern "C" int tde_step(tde_mesh *m, double cfl, double dt_fixed, const tde_bh_state *bhs,
+                        double *dt_out) {
+  if (!m) return TDE_EINVAL;
+  if (!m->U || !m->U1) return fail(m->ctx, TDE_EINVAL, "tde_step: no bound state");
+  if (!(cfl > 0.0) && !(dt_fixed > 0.0)) return fail(m->ctx, TDE_EINVAL, "tde_step: need cfl or dt");
+  tde_ctx *c = m->ctx;
+  const BH bh = make_bh(bhs);
+  TimeArgs ta{m->d_scal + 1, 0, m->d_scal, 0};
+  if (cfl > 0.0) {
+    CK(c, launch_c2p(m, m->U, m->nb, m->d_allids, true, bh, ta));
+    CK(c, launch_dt_finalize(m, cfl, m->d_dtb, nullptr));
+  } else {
+    CK(c, launch_set_dt(m, dt_fixed));
+    CK(c, launch_c2p(m, m->U, m->nb, m->d_allids, false, bh, ta));
+  }
+  int r = run_stage(m, 0, m->nb, m->d_allids, bh, ta, true);
+  if (r) return r;
+  r = run_stage(m, 1, m->nb, m->d_allids, bh, ta, false);
+  if (r) return r;
+  if (bh.excise) CK(c, launch_excise(m, m->U, m->nb, m->d_allids, bh, ta));
+  if (m->phys.dual) CK(c, launch_sync(m, m->U, m->nb, m->d_allids, m->phys.eta2));
+  if (dt_out) CK(c, cudaMemcpyAsync(dt_out, m->d_scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, launch_advance_time(m));
+  return TDE_OK;
+}
+
+extern "C" int tde_counts_read(tde_mesh *m, tde_counts *out, int reset) {
+  if (!m || !out) return TDE_EINVAL;
+  Counters h;
+  CK(m->ctx, cudaMemcpyAsync(&h, m->d_cnt, sizeof h, cudaMemcpyDeviceToHost, m->ctx->stream));
+  if (reset) CK(m->ctx, cudaMemsetAsync(m->d_cnt, 0, sizeof(Counters), m->ctx->stream));
+  CK(m->ctx, cudaStreamSynchronize(m->ctx->stream));
+  static_assert(sizeof(Counters) == sizeof(tde_counts), "counter layout");
+  memcpy(out, &h, sizeof h);
+  return TDE_OK;
+}
+
+// ====================================================== measurement ====
+
+extern "C" int tde_profile(tde_ctx *ctx, int enable) {
+  if (!ctx) return TDE_EINVAL;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto &r : ctx->pending) {
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+  for (int k = 0; k < TDE_K_NKIND; ++k) {
+    ctx->launches[k] = 0;
+    ctx->ms[k] = 0.0;
+  }
+  ctx->prof = enable != 0;
+  return TDE_OK;
+}
+
+extern "C" int tde_profile_read(tde_ctx *ctx, uint64_t *launches, double *ms) {
+  if (!ctx) return TDE_EINVAL;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto &r : ctx->pending) {
+    float t = 0.f;
+    CK(ctx, cudaEventElapsedTime(&t, r.a, r.b));
+    ctx->ms[r.kind] += t;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+  for (int k = 0; k < TDE_K_NKIND; ++k) {
+    if (launches) launches[k] = ctx->launches[k];
+    if (ms) ms[k] = ctx->ms[k];
+  }
+  return TDE_OK;
+}
+
+namespace tde {
+// 8 independent FMA chains per thread; the result is stored so nothing is elided
+__global__ void __launch_bounds__(256) k_probe_fp64(double *out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+}  // namespace tde
+
+extern "C" int tde_probe_fp64(tde_ctx *ctx, double *flops) {
+  if (!ctx || !flops) return TDE_EINVAL;
+  int sms = 0;
+  CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int grid = sms * 8, iters = 4096;
+  double *buf = nullptr;
+  CK(ctx, cudaMalloc(&buf, sizeof(double) * grid * 256));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    ProfScope ps(ctx, TDE_K_PROBE);
+    cudaEventRecord(e0, ctx->stream);
+    k_probe_fp64<<<grid, 256, 0, ctx->stream>>>(buf, iters, 0.999999, 1e-7);
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t err = cudaEventSynchronize(e1);
+    if (err != cudaSuccess) {
+      cudaFree(buf);
+      return cuda_fail(ctx, err, "tde_probe_fp64");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  *flops = 2.0 * 8.0 * iters * (double)grid * 256 / (best * 1e-3);
+  return TDE_OK;
+}

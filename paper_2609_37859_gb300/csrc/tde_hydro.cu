@@ -1,0 +1,802 @@
+// tde_hydro.cu -- the kernels of the per-MeshBlock hydro stage on sm_103a.
+//
+// One Runge-Kutta stage is four kinds of launches on the context's stream:
+//   k_c2p     conserved -> primitive (+ EOS, + optional per-block CFL minimum)
+//             on the interior cells only;
+//   k_ghost   the ghost layer of the primitives, gathered from the neighbours'
+//             interiors through a precomputed (dst, src) map (a1) -- the
+//             primitive recovery is pointwise, so copying primitives equals
+//             converting copied conserved variables and saves the EOS work of
+//             every ghost cell;
+//   k_sweep   one launch per active direction: a CTA stages a tile of pencils
+//             (with ghosts) in shared memory, reconstructs every cell's two face
+//             states once, solves every face once (HLLC), and accumulates the
+//             flux divergence, the gravity sources and div v; the last active
+//             direction also finishes the update (RK combination, dual-energy
+//             compression, floors) and writes the output state.
+// The FP64 pipe bounds this path on GB300, so no FP64 result is ever computed
+// twice: a slope per cell and direction, a flux per face, an EOS inversion per
+// interior cell.
+#include <math.h>
+
+#include <algorithm>
+
+#include "tde_internal.h"
+
+namespace tde {
+
+constexpr int NT = 256;   // threads per CTA
+
+__device__ __forceinline__ double ta_t(const TimeArgs &ta, int b) {
+  return ta.t ? ta.t[ta.t_pb ? b : 0] : 0.0;
+}
+__device__ __forceinline__ double ta_dt(const TimeArgs &ta, int b) {
+  return ta.dt ? ta.dt[ta.dt_pb ? b : 0] : 0.0;
+}
+
+__device__ __forceinline__ void bh_pos(const BH &bh, double t, double r[3]) {
+  double s = t - bh.t0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r[a] = bh.x0[a] + bh.v0[a] * s + 0.5 * bh.a0[a] * s * s;
+}
+
+// centre of padded cell c[] of block B; periodic directions wrap to the image
+__device__ __forceinline__ void cell_centre(const Phys &p, const DevBlock &B, const int c[3],
+                                            double x[3]) {
+  const int o[3] = {B.i0, B.j0, B.k0};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int g = o[a] + c[a] - p.g[a];
+    if (p.bc[a] == 1) {
+      g %= p.N[a];
+      if (g < 0) g += p.N[a];
+    }
+    x[a] = p.xmin[a] + (g + 0.5) * p.dx[a];
+  }
+}
+
+__device__ __forceinline__ double block_min(double v) {
+  __shared__ double red[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < NT / 32 ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// ------------------------------------------------------------ k_c2p ----
+
+template <int EOSK, int DUAL>
+__global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
+                                            const DevBlock *__restrict__ blocks,
+                                            const int32_t *__restrict__ ids,
+                                            const double *__restrict__ U, double *__restrict__ W,
+                                            long long ntot, Counters *cnt, int want_dt,
+                                            unsigned long long *dtbits) {
+  const int b = ids[blockIdx.y];
+  const DevBlock B = blocks[b];
+  const int nint = B.n[0] * B.n[1] * B.n[2];
+  const int e = blockIdx.x * NT + threadIdx.x;
+  if (blockIdx.x * NT >= nint) return;   // whole CTA past this block (uniform)
+  double best = INFINITY;
+  if (e < nint) {
+    const int i = e % B.n[0], r = e / B.n[0];
+    const int j = r % B.n[1], k = r / B.n[1];
+    const int c[3] = {i + p.g[0], j + p.g[1], k + p.g[2]};
+    const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
+    double u[6], w[8];
+#pragma unroll
+    for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
+    cons_to_prim<EOSK, DUAL>(p, u, w, cnt);
+    constexpr int NWV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
+#pragma unroll
+    for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
+    if (want_dt) {
+      bool skip = false;
+      double x[3], rb[3], d[3];
+      const double tb = ta_t(ta, b);
+      if (bh.on || bh.excise) {
+        cell_centre(p, B, c, x);
+        bh_pos(bh, tb, rb);
+        d[0] = x[0] - rb[0]; d[1] = x[1] - rb[1]; d[2] = x[2] - rb[2];
+      }
+      double r2 = 0.0;
+      if (bh.on || bh.excise) r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (bh.excise && sqrt(r2) < bh.rexc) skip = true;
+      if (!skip) {
+        const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
+        const double cs = sqrt(g1 * w[4] / w[0]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (p.active[a]) best = fmin(best, p.dx[a] / (fabs(w[1 + a]) + cs));
+        if (bh.on) {
+          double s2 = r2 + bh.rs2;
+          double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
+          if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin / gmag));
+        }
+      }
+    }
+  }
+  if (want_dt) {
+    best = block_min(best);
+    if (threadIdx.x == 0)
+      atomicMin(dtbits + b, (unsigned long long)__double_as_longlong(best));
+  }
+}
+
+
+// every padded cell of the listed blocks (used when only a subset of blocks
+// advances, so the ghost layer cannot be copied from freshly converted
+// neighbours); events are counted on interior cells only
+template <int EOSK, int DUAL>
+__global__ void __launch_bounds__(NT) k_c2p_padded(Phys p, const DevBlock *__restrict__ blocks,
+                                                   const int32_t *__restrict__ ids,
+                                                   const double *__restrict__ U,
+                                                   double *__restrict__ W, long long ntot,
+                                                   Counters *cnt) {
+  const int b = ids[blockIdx.y];
+  const DevBlock B = blocks[b];
+  const int npad = B.p[0] * B.p[1] * B.p[2];
+  for (int e = blockIdx.x * NT + threadIdx.x; e < npad; e += gridDim.x * NT) {
+    const int i = e % B.p[0], r = e / B.p[0];
+    const int j = r % B.p[1], k = r / B.p[1];
+    const bool interior = i >= p.g[0] && i < p.g[0] + B.n[0] && j >= p.g[1] &&
+                          j < p.g[1] + B.n[1] && k >= p.g[2] && k < p.g[2] + B.n[2];
+    const long long flat = B.off + e;
+    double u[6], w[8];
+#pragma unroll
+    for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
+    cons_to_prim<EOSK, DUAL>(p, u, w, interior ? cnt : nullptr);
+    constexpr int NWV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
+#pragma unroll
+    for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
+  }
+}
+
+// per-block dt = cfl * minimum; global minimum; re-arm the per-block minima
+__global__ void __launch_bounds__(1024) k_dt_finalize(int nb, double cfl,
+                                                      unsigned long long *dtbits,
+                                                      double *dt_block, double *dt_min,
+                                                      double *scal) {
+  __shared__ double red[32];
+  double m = INFINITY;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double v = cfl * __longlong_as_double((long long)dtbits[b]);
+    if (dt_block) dt_block[b] = v;
+    m = fmin(m, v);
+    dtbits[b] = (unsigned long long)__double_as_longlong(INFINITY);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      if (dt_min) *dt_min = m;
+      if (scal) { scal[1] = m; scal[2] = m; }
+    }
+  }
+}
+
+// ---------------------------------------------------------- k_ghost ----
+
+__global__ void __launch_bounds__(NT) k_ghost(const int32_t *__restrict__ map,
+                                              const int32_t *__restrict__ gstart,
+                                              const int32_t *__restrict__ ids, double *f, int nf,
+                                              long long ntot) {
+  const int b = ids[blockIdx.y];
+  const int s0 = gstart[b], s1 = gstart[b + 1];
+  for (int e = s0 + blockIdx.x * NT + threadIdx.x; e < s1; e += gridDim.x * NT) {
+    const int2 m = reinterpret_cast<const int2 *>(map)[e];
+    for (int v = 0; v < nf; ++v) f[v * ntot + m.x] = f[v * ntot + m.y];
+  }
+}
+
+// ---------------------------------------------------------- k_sweep ----
+
+struct SweepArgs {
+  Phys p;
+  BH bh;
+  TimeArgs ta;
+  const DevBlock *blocks;
+  const int32_t *ids;
+  const double *W;
+  double *dU;
+  const double *U0;
+  const double *Uin;
+  double *Uout;
+  long long ntot;
+  Counters *cnt;
+  int stage, first, PD, NF;
+};
+
+template <int D>
+struct SweepGeo {
+  static constexpr int LA = D == 0 ? 1 : 0;   // lane axis (transverse, one thread column per lane)
+  static constexpr int OA = D == 2 ? 1 : 2;   // other transverse axis (one CTA per index)
+  static constexpr int M = D == 0 ? 8 : 16;   // lanes per tile
+};
+
+template <int D, int RECON, int EOSK, int DUAL, int LAST>
+__global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a) {
+  constexpr int LA = SweepGeo<D>::LA, OA = SweepGeo<D>::OA, M = SweepGeo<D>::M;
+  constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;   // reconstructed primitives
+  constexpr int NVAR = 5 + DUAL;                            // conserved variables
+  extern __shared__ double sm[];
+  const Phys &p = a.p;
+  const int b = a.ids[blockIdx.y];
+  const DevBlock B = a.blocks[b];
+  const int nd = B.n[D], nl = B.n[LA], no = B.n[OA];
+  const int nlc = (nl + M - 1) / M;
+  if ((int)blockIdx.x >= nlc * no) return;
+  const int l0 = (blockIdx.x % nlc) * M, o = blockIdx.x / nlc;
+  const int nlane = min(M, nl - l0);
+  const int g = p.g[D], pd = B.p[D];
+  const long long st[3] = {1, B.p[0], (long long)B.p[0] * B.p[1]};
+  const long long sD = st[D], sL = st[LA];
+  const long long base = B.off + (long long)(p.g[LA] + l0) * sL + (long long)(p.g[OA] + o) * st[OA];
+  const int PD = a.PD, NF = a.NF, NFF = a.NF - 1;
+  const long long ntot = a.ntot;
+
+  double *Wt = sm;                       // [NV][PD][M]  primitives of the tile
+  double *FMs = Wt + NV * PD * M;        // [NV][NF][M]  value at the low face of cells g-1 .. g+nd
+  double *FPs = FMs + NV * NF * M;       // [NV][NF][M]  value at the high face
+  double *Fl = FPs + NV * NF * M;        // [7][NFF][M]  fluxes and face velocity
+  double *Ph = Fl + 7 * NFF * M;         // [NF][M]      potential of cells g-1 .. g+nd
+  unsigned char *Ex = reinterpret_cast<unsigned char *>(Ph + NF * M);   // [NF][M] excised
+
+  // shared-memory indices: D = 0 keeps the pencil axis contiguous (it is
+  // contiguous in global memory too), D = 1, 2 keep the lane axis contiguous
+  auto sw = [&](int v, int pos, int lane) {
+    return D == 0 ? (v * M + lane) * PD + pos : (v * PD + pos) * M + lane;
+  };
+  auto sf = [&](int v, int c, int lane) {
+    return D == 0 ? (v * M + lane) * NF + c : (v * NF + c) * M + lane;
+  };
+  auto sfl = [&](int q, int f, int lane) {
+    return D == 0 ? (q * M + lane) * NFF + f : (q * NFF + f) * M + lane;
+  };
+  auto split = [&](int e, int len, int &c, int &lane) {
+    if (D == 0) { lane = e / len; c = e - lane * len; }
+    else { c = e / M; lane = e - c * M; }
+  };
+
+  // ---- A: stage the tile's primitives (all pencil cells incl. ghosts)
+  {
+    const int per = pd * M;
+    for (int e = threadIdx.x; e < NV * per; e += NT) {
+      const int v = e / per;
+      int pos, lane;
+      split(e - v * per, pd, pos, lane);
+      if (lane < nlane) Wt[sw(v, pos, lane)] = a.W[v * ntot + base + pos * sD + lane * sL];
+    }
+  }
+  const bool grav = a.bh.on, exc = a.bh.excise;
+  if (grav || exc) {
+    const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
+    double rb[3];
+    bh_pos(a.bh, ts, rb);
+    for (int e = threadIdx.x; e < (nd + 2) * M; e += NT) {
+      int c, lane;
+      split(e, nd + 2, c, lane);
+      if (lane >= nlane) continue;
+      int cc[3];
+      cc[D] = g - 1 + c;
+      cc[LA] = p.g[LA] + l0 + lane;
+      cc[OA] = p.g[OA] + o;
+      double x[3];
+      cell_centre(p, B, cc, x);
+      const double dx0 = x[0] - rb[0], dx1 = x[1] - rb[1], dx2 = x[2] - rb[2];
+      const double r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
+      const int idx = D == 0 ? lane * NF + c : c * M + lane;
+      if (grav) Ph[idx] = -a.bh.GM / sqrt(r2 + a.bh.rs2);
+      if (exc) Ex[idx] = sqrt(r2) < a.bh.rexc ? 1 : 0;
+    }
+  }
+  __syncthreads();
+
+  // ---- B: face values of every cell adjacent to a face of the tile
+  for (int e = threadIdx.x; e < (nd + 2) * M; e += NT) {
+    int c, lane;
+    split(e, nd + 2, c, lane);
+    if (lane >= nlane) continue;
+    const int pos = g - 1 + c;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double lo, hi;
+      if (RECON == PLM) {
+        plm(Wt[sw(v, pos - 1, lane)], Wt[sw(v, pos, lane)], Wt[sw(v, pos + 1, lane)], lo, hi);
+      } else {
+        const double qm2 = Wt[sw(v, pos - 2, lane)], qm1 = Wt[sw(v, pos - 1, lane)];
+        const double q0 = Wt[sw(v, pos, lane)], qp1 = Wt[sw(v, pos + 1, lane)];
+        const double qp2 = Wt[sw(v, pos + 2, lane)];
+        lo = ppm_iface(qm2, qm1, q0, qp1);
+        hi = ppm_iface(qm1, q0, qp1, qp2);
+        ppm_limit(q0, lo, hi);
+      }
+      FMs[sf(v, c, lane)] = lo;
+      FPs[sf(v, c, lane)] = hi;
+    }
+  }
+  __syncthreads();
+
+  // ---- C: one HLLC solve per face
+  for (int e = threadIdx.x; e < (nd + 1) * M; e += NT) {
+    int f, lane;
+    split(e, nd + 1, f, lane);
+    if (lane >= nlane) continue;
+    FState L, R;
+    L.r = FPs[sf(0, f, lane)];
+    R.r = FMs[sf(0, f + 1, lane)];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      L.v[q] = FPs[sf(1 + q, f, lane)];
+      R.v[q] = FMs[sf(1 + q, f + 1, lane)];
+    }
+    L.P = FPs[sf(4, f, lane)];
+    R.P = FMs[sf(4, f + 1, lane)];
+    if (EOSK == EOS_TABLE) {
+      L.ge = FPs[sf(5, f, lane)]; R.ge = FMs[sf(5, f + 1, lane)];
+      L.g1 = FPs[sf(6, f, lane)]; R.g1 = FMs[sf(6, f + 1, lane)];
+    } else {
+      L.ge = L.g1 = R.ge = R.g1 = p.gamma;
+    }
+    if (DUAL) {
+      L.A = FPs[sf(NV - 1, f, lane)];
+      R.A = FMs[sf(NV - 1, f + 1, lane)];
+    } else {
+      L.A = R.A = 0.0;
+    }
+    double F[6], vf;
+    hllc<D, EOSK, DUAL>(p, L, R, F, vf);
+    if (exc) {
+      const int il = D == 0 ? lane * NF + f : f * M + lane;
+      const int ir = D == 0 ? lane * NF + f + 1 : (f + 1) * M + lane;
+      if (Ex[il] != Ex[ir]) {
+        const bool into = Ex[ir] ? (F[0] > 0.0) : (F[0] < 0.0);
+        if (!into) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) F[q] = 0.0;
+          vf = 0.0;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NVAR; ++q) Fl[sfl(q, f, lane)] = F[q];
+    if (DUAL) Fl[sfl(6, f, lane)] = vf;
+  }
+  __syncthreads();
+
+  // ---- D: divergence, sources; the last direction completes the update
+  const double idx = p.idx[D];
+  const double hidx = 0.5 * p.idx[D];
+  for (int e = threadIdx.x; e < nd * M; e += NT) {
+    int c, lane;
+    split(e, nd, c, lane);
+    if (lane >= nlane) continue;
+    const long long flat = base + (long long)(g + c) * sD + lane * sL;
+    double acc[NVAR], dv = 0.0;
+#pragma unroll
+    for (int q = 0; q < NVAR; ++q) acc[q] = a.first ? 0.0 : a.dU[q * ntot + flat];
+    if (DUAL) dv = a.first ? 0.0 : a.dU[NVAR * ntot + flat];
+#pragma unroll
+    for (int q = 0; q < NVAR; ++q) acc[q] -= (Fl[sfl(q, c + 1, lane)] - Fl[sfl(q, c, lane)]) * idx;
+    if (DUAL) dv += (Fl[sfl(6, c + 1, lane)] - Fl[sfl(6, c, lane)]) * idx;
+    if (grav) {
+      const int i0 = D == 0 ? lane * NF + c : c * M + lane;
+      const int i1 = D == 0 ? i0 + 1 : i0 + M;
+      const int i2 = D == 0 ? i0 + 2 : i0 + 2 * M;
+      const double phm = Ph[i0], ph0 = Ph[i1], php = Ph[i2];
+      const double rho = Wt[sw(0, g + c, lane)];
+      acc[1 + D] -= rho * (php - phm) * hidx;
+      acc[4] -= (Fl[sfl(0, c + 1, lane)] * (php - ph0) + Fl[sfl(0, c, lane)] * (ph0 - phm)) * hidx;
+    }
+    if (!LAST) {
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) a.dU[q * ntot + flat] = acc[q];
+      if (DUAL) a.dU[NVAR * ntot + flat] = dv;
+    } else {
+      const double dt = ta_dt(a.ta, b);
+      double un[NVAR];
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) {
+        const double u0 = a.U0[q * ntot + flat];
+        un[q] = a.stage == 0 ? u0 + dt * acc[q] : 0.5 * (u0 + (a.Uin[q * ntot + flat] + dt * acc[q]));
+      }
+      if (un[0] < p.rho_floor) { un[0] = p.rho_floor; count(&a.cnt->rho_floor); }
+      if (DUAL) {
+        const double dtl = a.stage == 0 ? dt : 0.5 * dt;
+        if (EOSK == EOS_IDEAL) {
+          un[5] = un[5] * exp(-p.gm1 * dv * dtl);
+        } else {
+          double Pa, c2a, Uu;
+          eos_closure<EOS_TABLE>(p, un[0], un[5], Pa, c2a, Uu, a.cnt);
+          un[5] = un[5] - Pa * dv * dtl;
+        }
+        if (un[5] < p.u_floor) { un[5] = p.u_floor; count(&a.cnt->u_floor); }
+      }
+      bool bad = !(un[0] > 0.0);
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) {
+        bad |= !isfinite(un[q]);
+        a.Uout[q * ntot + flat] = un[q];
+      }
+      if (bad) count(&a.cnt->nonfinite);
+    }
+  }
+}
+
+// ---------------------------------------------------- excision, resync ----
+
+__global__ void __launch_bounds__(NT) k_excise(Phys p, BH bh, TimeArgs ta,
+                                               const DevBlock *__restrict__ blocks,
+                                               const int32_t *__restrict__ ids, double *U,
+                                               long long ntot, Counters *cnt) {
+  const int b = ids[blockIdx.y];
+  const DevBlock B = blocks[b];
+  const int nint = B.n[0] * B.n[1] * B.n[2];
+  const int e = blockIdx.x * NT + threadIdx.x;
+  if (e >= nint) return;
+  const int i = e % B.n[0], r = e / B.n[0];
+  const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
+  double x[3], rb[3];
+  cell_centre(p, B, c, x);
+  bh_pos(bh, ta_t(ta, b) + ta_dt(ta, b), rb);
+  const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
+  if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) < bh.rexc)) return;
+  const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
+  U[flat] = p.rho_floor;
+  U[ntot + flat] = 0.0;
+  U[2 * ntot + flat] = 0.0;
+  U[3 * ntot + flat] = 0.0;
+  U[4 * ntot + flat] = p.u_floor;
+  if (p.dual) U[5 * ntot + flat] = p.u_floor;
+  count(&cnt->excised);
+}
+
+__global__ void __launch_bounds__(NT) k_sync(Phys p, const DevBlock *__restrict__ blocks,
+                                             const int32_t *__restrict__ ids, double *U,
+                                             long long ntot, double eta2, Counters *cnt) {
+  const int b = ids[blockIdx.y];
+  const DevBlock B = blocks[b];
+  const int nint = B.n[0] * B.n[1] * B.n[2];
+  const int e = blockIdx.x * NT + threadIdx.x;
+  if (e >= nint) return;
+  const int i = e % B.n[0], r = e / B.n[0];
+  const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
+  const long long sy = B.p[0], sz = (long long)B.p[0] * B.p[1];
+  const long long flat = B.off + c[2] * sz + c[1] * sy + c[0];
+  const double *E = U + 4 * ntot;
+  const int ax = p.active[0], ay = p.active[1], az = p.active[2];
+  double emax = -INFINITY;
+  for (int dk = -az; dk <= az; ++dk)
+    for (int dj = -ay; dj <= ay; ++dj)
+      for (int di = -ax; di <= ax; ++di) emax = fmax(emax, E[flat + dk * sz + dj * sy + di]);
+  const double u0 = U[flat], u1 = U[ntot + flat], u2 = U[2 * ntot + flat], u3 = U[3 * ntot + flat];
+  const double rho = u0 < p.rho_floor ? p.rho_floor : u0;
+  const double ir = 1.0 / rho;
+  const double Uc = E[flat] - 0.5 * (u1 * (u1 * ir) + u2 * (u2 * ir) + u3 * (u3 * ir));
+  if (Uc > 0.0 && Uc > eta2 * emax) {
+    U[5 * ntot + flat] = Uc;
+    count(&cnt->synced);
+  }
+}
+
+// ------------------------------------------------------ prim -> cons ----
+
+// log10 T at which the interpolated log10 P at density cell (i, w) equals lp
+__device__ double table_lT_from_lP(const DTable &t, int i, double w, double lp) {
+  double lo = 0.0, hi = (double)(t.nt - 1);   // in units of table cells
+  for (int it = 0; it < 100; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    int j = (int)floor(mid);
+    if (j > t.nt - 2) j = t.nt - 2;
+    if (bilin(t.lp, t.nt, i, w, j, mid - j) < lp) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__global__ void __launch_bounds__(NT) k_prim2cons(Phys p, const DevBlock *__restrict__ blocks,
+                                                  const double *__restrict__ W, double *U,
+                                                  long long ntot, int nb) {
+  const int b = blockIdx.y;
+  const DevBlock B = blocks[b];
+  const int nint = B.n[0] * B.n[1] * B.n[2];
+  for (int e = blockIdx.x * NT + threadIdx.x; e < nint; e += gridDim.x * NT) {
+    const int i = e % B.n[0], r = e / B.n[0];
+    const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
+    const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
+    const double rho = W[flat], vx = W[ntot + flat], vy = W[2 * ntot + flat];
+    const double vz = W[3 * ntot + flat], P = W[4 * ntot + flat];
+    double Uint;
+    if (p.eos == EOS_IDEAL) {
+      Uint = P * p.inv_gm1;
+    } else {
+      int ti;
+      double tw;
+      rho_cell(p.tab, rho * p.unit_rho, ti, tw);
+      const double y = table_lT_from_lP(p.tab, ti, tw, log10(P * p.unit_rho * p.unit_e));
+      int j = (int)floor(y);
+      if (j > p.tab.nt - 2) j = p.tab.nt - 2;
+      const double ec = exp10(bilin(p.tab.le, p.tab.nt, ti, tw, j, y - j));
+      Uint = rho * (ec * p.inv_unit_e);
+    }
+    U[flat] = rho;
+    U[ntot + flat] = rho * vx;
+    U[2 * ntot + flat] = rho * vy;
+    U[3 * ntot + flat] = rho * vz;
+    U[4 * ntot + flat] = Uint + 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    if (p.dual) U[5 * ntot + flat] = Uint;
+  }
+}
+
+// ------------------------------------------------------------- scalars ----
+
+__global__ void k_advance_time(double *scal) { scal[0] += scal[1]; }
+__global__ void k_set_dt(double *scal, double dt) { scal[1] = dt; scal[2] = dt; }
+
+// ---------------------------------------------------------- EOS batch ----
+
+__global__ void __launch_bounds__(NT) k_eos_invert(DTable t, long long n, const double *__restrict__ rho,
+                                                   const double *__restrict__ en, double *T,
+                                                   double *P, double *cs2, Counters *cnt) {
+  for (long long e = blockIdx.x * (long long)NT + threadIdx.x; e < n; e += (long long)gridDim.x * NT) {
+    double Pv, cv, eu, Tv;
+    bool cl = eos_invert(t, rho[e], en[e], Pv, cv, eu, &Tv);
+    if (cl) count(&cnt->table_clamp);
+    if (T) T[e] = Tv;
+    if (P) P[e] = Pv;
+    if (cs2) cs2[e] = cv;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_eos_eval(DTable t, long long n, const double *__restrict__ rho,
+                                                 const double *__restrict__ T, double *P,
+                                                 double *en, double *cs2) {
+  for (long long e = blockIdx.x * (long long)NT + threadIdx.x; e < n; e += (long long)gridDim.x * NT) {
+    int i;
+    double w;
+    rho_cell(t, rho[e], i, w);
+    double y = (log10(T[e]) - t.lt0) / t.dlt;
+    if (!(y >= 0.0)) y = 0.0;
+    if (y > (double)(t.nt - 1)) y = (double)(t.nt - 1);
+    int j = (int)floor(y);
+    if (j > t.nt - 2) j = t.nt - 2;
+    const double s = y - j;
+    if (P) P[e] = exp10(bilin(t.lp, t.nt, i, w, j, s));
+    if (en) en[e] = exp10(bilin(t.le, t.nt, i, w, j, s));
+    if (cs2) cs2[e] = exp10(bilin(t.lc, t.nt, i, w, j, s));
+  }
+}
+
+// ============================================================ launchers ====
+
+static int n_sm() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+cudaError_t launch_c2p(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids, bool want_dt,
+                       const BH &bh, TimeArgs ta) {
+  ProfScope _ps(m->ctx, TDE_K_C2P);
+  dim3 grid((unsigned)((m->max_interior + NT - 1) / NT), (unsigned)nblk);
+  const Phys &p = m->phys;
+#define C2P_ARGS p, bh, ta, m->d_blocks, ids, Uin, m->d_W, (long long)m->ntot, m->d_cnt, \
+                 (int)want_dt, m->d_dtbits
+  if (p.eos == EOS_IDEAL) {
+    if (p.dual) k_c2p<EOS_IDEAL, 1><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
+    else k_c2p<EOS_IDEAL, 0><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
+  } else {
+    if (p.dual) k_c2p<EOS_TABLE, 1><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
+    else k_c2p<EOS_TABLE, 0><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
+  }
+#undef C2P_ARGS
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids) {
+  ProfScope _ps(m->ctx, TDE_K_C2P);
+  int64_t npad = 0;
+  for (const DevBlock &B : m->hblocks) npad = std::max<int64_t>(npad, (int64_t)B.p[0] * B.p[1] * B.p[2]);
+  dim3 grid((unsigned)std::min<int64_t>((npad + NT - 1) / NT, 256), (unsigned)nblk);
+  const Phys &p = m->phys;
+#define C2PP_ARGS p, m->d_blocks, ids, Uin, m->d_W, (long long)m->ntot, m->d_cnt
+  if (p.eos == EOS_IDEAL) {
+    if (p.dual) k_c2p_padded<EOS_IDEAL, 1><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
+    else k_c2p_padded<EOS_IDEAL, 0><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
+  } else {
+    if (p.dual) k_c2p_padded<EOS_TABLE, 1><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
+    else k_c2p_padded<EOS_TABLE, 0><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
+  }
+#undef C2PP_ARGS
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double *dt_min) {
+  ProfScope _ps(m->ctx, TDE_K_DT);
+  k_dt_finalize<<<1, 1024, 0, m->ctx->stream>>>(m->nb, cfl, m->d_dtbits, dt_block, dt_min,
+                                                m->d_scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids) {
+  if (m->max_ghosts == 0) return cudaSuccess;
+  ProfScope _ps(m->ctx, TDE_K_GHOST);
+  unsigned gx = (unsigned)min((m->max_ghosts + NT - 1) / NT, 64);
+  k_ghost<<<dim3(gx, (unsigned)nblk), NT, 0, m->ctx->stream>>>(m->d_ghost, m->d_gstart, ids, field,
+                                                                 nf, (long long)m->ntot);
+  return cudaGetLastError();
+}
+
+template <int D, int RECON, int EOSK, int DUAL>
+static cudaError_t sweep_one(const SweepArgs &a, bool last, dim3 grid, size_t smem, cudaStream_t s) {
+  static bool attr[2] = {false, false};
+  if (last) {
+    auto k = k_sweep<D, RECON, EOSK, DUAL, 1>;
+    if (!attr[1]) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr[1] = true;
+    }
+    k<<<grid, NT, smem, s>>>(a);
+  } else {
+    auto k = k_sweep<D, RECON, EOSK, DUAL, 0>;
+    if (!attr[0]) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr[0] = true;
+    }
+    k<<<grid, NT, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t sweep_dispatch(const SweepArgs &a, bool last, dim3 grid, size_t smem,
+                                  cudaStream_t s) {
+  const Phys &p = a.p;
+  if (p.recon == PLM) {
+    if (p.eos == EOS_IDEAL) {
+      return p.dual ? sweep_one<D, PLM, EOS_IDEAL, 1>(a, last, grid, smem, s)
+                    : sweep_one<D, PLM, EOS_IDEAL, 0>(a, last, grid, smem, s);
+    }
+    return p.dual ? sweep_one<D, PLM, EOS_TABLE, 1>(a, last, grid, smem, s)
+                  : sweep_one<D, PLM, EOS_TABLE, 0>(a, last, grid, smem, s);
+  }
+  if (p.eos == EOS_IDEAL) {
+    return p.dual ? sweep_one<D, PPM, EOS_IDEAL, 1>(a, last, grid, smem, s)
+                  : sweep_one<D, PPM, EOS_IDEAL, 0>(a, last, grid, smem, s);
+  }
+  return p.dual ? sweep_one<D, PPM, EOS_TABLE, 1>(a, last, grid, smem, s)
+                : sweep_one<D, PPM, EOS_TABLE, 0>(a, last, grid, smem, s);
+}
+
+// shared memory of one sweep CTA (doubles, then the excision bytes)
+static size_t sweep_smem(const Phys &p, int PD, int NF, int M) {
+  const int NV = p.nwv;
+  size_t nd = (size_t)NV * PD * M + 2 * (size_t)NV * NF * M + 7 * (size_t)(NF - 1) * M +
+              (size_t)NF * M;
+  return nd * sizeof(double) + (size_t)NF * M;
+}
+
+size_t sweep_smem_max(const tde_mesh *m) {
+  size_t best = 0;
+  for (int D = 0; D < 3; ++D) {
+    const int PD = m->nmax[D] + 2 * m->phys.g[D], NF = m->nmax[D] + 2;
+    const size_t s = sweep_smem(m->phys, PD, NF, D == 0 ? 8 : 16);
+    if (s > best) best = s;
+  }
+  return best;
+}
+
+cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double *Uin,
+                          double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta) {
+  const Phys &p = m->phys;
+  int lastD = -1, firstD = -1;
+  for (int D = 0; D < 3; ++D)
+    if (p.active[D]) { lastD = D; if (firstD < 0) firstD = D; }
+  if (lastD < 0) return cudaErrorInvalidValue;
+  SweepArgs a;
+  a.p = p;
+  a.bh = bh;
+  a.ta = ta;
+  a.blocks = m->d_blocks;
+  a.ids = ids;
+  a.W = m->d_W;
+  a.dU = m->d_dU;
+  a.U0 = U0;
+  a.Uin = Uin;
+  a.Uout = Uout;
+  a.ntot = (long long)m->ntot;
+  a.cnt = m->d_cnt;
+  a.stage = stage;
+  for (int D = 0; D < 3; ++D) {
+    if (!p.active[D]) continue;
+    const int M = D == 0 ? 8 : 16;
+    const int LA = D == 0 ? 1 : 0, OA = D == 2 ? 1 : 2;
+    a.first = D == firstD;
+    a.PD = m->nmax[D] + 2 * p.g[D];
+    a.NF = m->nmax[D] + 2;
+    const size_t smem = sweep_smem(p, a.PD, a.NF, M);
+    dim3 grid((unsigned)(((m->nmax[LA] + M - 1) / M) * m->nmax[OA]), (unsigned)nblk);
+    cudaError_t err;
+    ProfScope _ps(m->ctx, TDE_K_SWEEP_X + D);
+    if (D == 0) err = sweep_dispatch<0>(a, D == lastD, grid, smem, m->ctx->stream);
+    else if (D == 1) err = sweep_dispatch<1>(a, D == lastD, grid, smem, m->ctx->stream);
+    else err = sweep_dispatch<2>(a, D == lastD, grid, smem, m->ctx->stream);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
+                          TimeArgs ta) {
+  ProfScope _ps(m->ctx, TDE_K_EXCISE);
+  dim3 grid((unsigned)((m->max_interior + NT - 1) / NT), (unsigned)nblk);
+  k_excise<<<grid, NT, 0, m->ctx->stream>>>(m->phys, bh, ta, m->d_blocks, ids, U,
+                                             (long long)m->ntot, m->d_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2) {
+  cudaError_t err = launch_ghost(m, U + 4 * m->ntot, 1, nblk, ids);
+  if (err != cudaSuccess) return err;
+  dim3 grid((unsigned)((m->max_interior + NT - 1) / NT), (unsigned)nblk);
+  ProfScope _ps(m->ctx, TDE_K_SYNC);
+  k_sync<<<grid, NT, 0, m->ctx->stream>>>(m->phys, m->d_blocks, ids, U, (long long)m->ntot, eta2,
+                                           m->d_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim2cons(tde_mesh *m, const double *W, double *U) {
+  ProfScope _ps(m->ctx, TDE_K_P2C);
+  dim3 grid((unsigned)min((m->max_interior + NT - 1) / NT, (int64_t)1024), (unsigned)m->nb);
+  k_prim2cons<<<grid, NT, 0, m->ctx->stream>>>(m->phys, m->d_blocks, W, U, (long long)m->ntot, m->nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_time(tde_mesh *m) {
+  ProfScope _ps(m->ctx, TDE_K_SCALAR);
+  k_advance_time<<<1, 1, 0, m->ctx->stream>>>(m->d_scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt(tde_mesh *m, double dt) {
+  ProfScope _ps(m->ctx, TDE_K_SCALAR);
+  k_set_dt<<<1, 1, 0, m->ctx->stream>>>(m->d_scal, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eos_invert(tde_eos *e, int64_t n, const double *rho, const double *en,
+                              double *T, double *P, double *cs2, cudaStream_t s) {
+  ProfScope _ps(e->ctx, TDE_K_EOS);
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + NT - 1) / NT;
+  unsigned g = (unsigned)(blocks < 8LL * n_sm() ? blocks : 8LL * n_sm());
+  k_eos_invert<<<g, NT, 0, s>>>(e->tab, (long long)n, rho, en, T, P, cs2, e->d_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eos_eval(tde_eos *e, int64_t n, const double *rho, const double *T, double *P,
+                            double *en, double *cs2, cudaStream_t s) {
+  ProfScope _ps(e->ctx, TDE_K_EOS);
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + NT - 1) / NT;
+  unsigned g = (unsigned)(blocks < 8LL * n_sm() ? blocks : 8LL * n_sm());
+  k_eos_eval<<<g, NT, 0, s>>>(e->tab, (long long)n, rho, T, P, en, cs2);
+  return cudaGetLastError();
+}
+
+}  // namespace tde

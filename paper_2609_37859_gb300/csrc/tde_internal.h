@@ -1,0 +1,119 @@
+// tde_internal.h -- host-side objects of libtde.so and the kernel launchers
+// shared between the C-ABI layer (tde_api.cu) and the kernels (tde_hydro.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tde_device.cuh"
+#include "../../include/tde.h"
+
+struct tde_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // launch accounting (always) and event timing (when prof is set)
+  bool prof = false;
+  uint64_t launches[TDE_K_NKIND] = {};
+  double ms[TDE_K_NKIND] = {};
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace tde {
+// brackets one kernel launch: counts it and, when profiling, records events
+struct ProfScope {
+  tde_ctx *c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfScope(tde_ctx *ctx, int k) : c(ctx), kind(k) {
+    c->launches[k]++;
+    if (c->prof) {
+      a = take();
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = take();
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({kind, a, b});
+    }
+  }
+  cudaEvent_t take() {
+    if (!c->pool.empty()) {
+      cudaEvent_t e = c->pool.back();
+      c->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+}  // namespace tde
+
+struct tde_eos {
+  tde_ctx *ctx = nullptr;
+  tde::DTable tab{};
+  double *d_data = nullptr;          // 3 * n_rho * n_T doubles
+  tde::Counters *d_cnt = nullptr;
+};
+
+struct tde_mesh {
+  tde_ctx *ctx = nullptr;
+  tde_eos *eos = nullptr;
+  tde::Phys phys{};
+  tde_params params{};
+  tde_grid_desc grid{};
+  int nb = 0;
+  int nmax[3] = {0, 0, 0};           // largest interior block edge per direction
+  int64_t ntot = 0;
+  int64_t max_interior = 0;          // largest interior cell count of a block
+  int max_ghosts = 0;                // largest ghost count of a block
+  std::vector<tde::DevBlock> hblocks;
+  std::vector<int64_t> hoff;
+  tde::DevBlock *d_blocks = nullptr;
+  int32_t *d_ghost = nullptr;        // [n_ghost][2] (dst, src) flat padded indices
+  int32_t *d_gstart = nullptr;       // [nb + 1]
+  int32_t *d_allids = nullptr;       // 0..nb-1
+  double *d_W = nullptr;             // primitives, nwv * ntot
+  double *d_dU = nullptr;            // accumulated L(U) and div v, (nvar + 1) * ntot
+  double *d_scal = nullptr;          // device scalars: [0] t, [1] dt, [2] dt_min
+  double *d_dtb = nullptr;           // per-block dt [nb]
+  unsigned long long *d_dtbits = nullptr;  // per-block CFL minima (bit patterns) [nb]
+  tde::Counters *d_cnt = nullptr;
+  double *U = nullptr, *U1 = nullptr;  // caller-owned states
+};
+
+namespace tde {
+
+// time / step-size source of a launch: per-block device array or one device scalar
+struct TimeArgs {
+  const double *dt;   // dt[b] if dt_pb else dt[0]
+  int dt_pb;
+  const double *t;    // t[b] if t_pb else t[0]; NULL = 0
+  int t_pb;
+};
+
+cudaError_t launch_c2p(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids, bool want_dt,
+                       const BH &bh, TimeArgs ta);
+cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double *dt_min);
+cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids);
+cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double *Uin,
+                          double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta);
+cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
+                          TimeArgs ta);
+cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2);
+cudaError_t launch_prim2cons(tde_mesh *m, const double *W, double *U);
+cudaError_t launch_advance_time(tde_mesh *m);
+cudaError_t launch_set_dt(tde_mesh *m, double dt);
+cudaError_t launch_eos_invert(tde_eos *e, int64_t n, const double *rho, const double *en,
+                              double *T, double *P, double *cs2, cudaStream_t s);
+cudaError_t launch_eos_eval(tde_eos *e, int64_t n, const double *rho, const double *T, double *P,
+                            double *en, double *cs2, cudaStream_t s);
+
+}  // namespace tde

@@ -1,0 +1,314 @@
+"""Python binding of libtde.so (include/tde.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch provides device memory and
+the stream.  The binding raises if the library is missing or a call fails --
+there is no CPU path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+TDE_OK, TDE_EINVAL, TDE_ENOMEM, TDE_ECUDA, TDE_ERANGE, TDE_ENUMERIC, TDE_ETIMEOUT = range(7)
+EOS_IDEAL, EOS_TABLE = 0, 1
+RECON_PLM, RECON_PPM = 0, 1
+BC_OUTFLOW, BC_PERIODIC = 0, 1
+INVERT_BISECT, INVERT_SURROGATE = 0, 1
+STATUS = {0: "TDE_OK", 1: "TDE_EINVAL", 2: "TDE_ENOMEM", 3: "TDE_ECUDA", 4: "TDE_ERANGE",
+          5: "TDE_ENUMERIC", 6: "TDE_ETIMEOUT"}
+
+
+class TDEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("eos", C.c_int), ("recon", C.c_int), ("dual", C.c_int), ("gamma", C.c_double),
+                ("eta1", C.c_double), ("eta2", C.c_double), ("rho_floor", C.c_double),
+                ("p_floor", C.c_double), ("u_floor", C.c_double), ("unit_rho", C.c_double),
+                ("unit_e", C.c_double)]
+
+
+class BHState(C.Structure):
+    _fields_ = [("on", C.c_int), ("excise", C.c_int), ("GM", C.c_double), ("r_soft", C.c_double),
+                ("r_exc", C.c_double), ("t0", C.c_double), ("x0", C.c_double * 3),
+                ("v0", C.c_double * 3), ("a0", C.c_double * 3)]
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("i0", "j0", "k0", "nx", "ny", "nz")]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("N", C.c_int * 3), ("xmin", C.c_double * 3), ("dx", C.c_double * 3),
+                ("bc", C.c_int * 3), ("ng", C.c_int)]
+
+
+class Counts(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("rho_floor", "p_floor", "u_floor", "table_clamp",
+                                          "excised", "dual_aux_used", "synced", "nonfinite")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+vp = C.c_void_p
+dp = C.c_void_p   # device pointers travel as integers
+_SIGS = {
+    "tde_init": [C.POINTER(vp), C.c_int, vp],
+    "tde_set_stream": [vp, vp],
+    "tde_finalize": [vp],
+    "tde_eos_load_table": [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                           C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                           C.POINTER(vp)],
+    "tde_eos_destroy": [vp],
+    "tde_eos_invert": [vp, C.c_int, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(Counts)],
+    "tde_eos_eval_rhoT": [vp, C.c_int64, dp, dp, dp, dp, dp],
+    "tde_mesh_create": [vp, C.c_int, C.POINTER(BlockDesc), C.POINTER(GridDesc), C.POINTER(Params),
+                        vp, C.POINTER(vp)],
+    "tde_mesh_destroy": [vp],
+    "tde_mesh_info": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int64)],
+    "tde_mesh_set_params": [vp, C.POINTER(Params)],
+    "tde_mesh_bind_state": [vp, dp, dp],
+    "tde_prim_to_cons": [vp, dp, dp],
+    "tde_ghost_fill": [vp, dp, C.c_int],
+    "tde_hydro_stage": [vp, C.c_int, C.c_int, dp, dp, dp, C.POINTER(BHState)],
+    "tde_compute_dt": [vp, C.c_double, dp, C.POINTER(BHState), dp, dp],
+    "tde_excise": [vp, C.c_int, dp, dp, C.POINTER(BHState)],
+    "tde_dual_energy_sync": [vp, C.c_int, dp, C.c_double],
+    "tde_mesh_set_time": [vp, C.c_double],
+    "tde_mesh_get_time": [vp, C.POINTER(C.c_double)],
+    "tde_step": [vp, C.c_double, C.c_double, C.POINTER(BHState), dp],
+    "tde_counts_read": [vp, C.POINTER(Counts), C.c_int],
+    "tde_profile": [vp, C.c_int],
+    "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
+    "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
+}
+KERNEL_KINDS = ("c2p", "dt", "ghost", "sweep_x", "sweep_y", "sweep_z", "sync", "excise", "scalar",
+                "p2c", "eos", "probe")
+NKIND = 16
+
+_lib = None
+
+
+def lib():
+    """Load libtde.so (building it first if it is absent and nvcc is available)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtde.so is missing: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.tde_last_error.argtypes = [vp]
+        L.tde_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(list(_SIGS) + ["tde_last_error"])
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+class Context:
+    """tde_ctx bound to a torch CUDA device and stream."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        self.stream = s
+        h = vp()
+        self._check(lib().tde_init(C.byref(h), device, s.cuda_stream), None)
+        self.h = h
+
+    def _check(self, code, h="self"):
+        if code != TDE_OK:
+            msg = lib().tde_last_error(self.h if h == "self" else None)
+            raise TDEError(code, msg.decode() if msg else "")
+
+    def check(self, code):
+        self._check(code)
+
+    def profile(self, enable=True):
+        self.check(lib().tde_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (launches, device ms)} since the last tde_profile() call."""
+        n = (C.c_uint64 * NKIND)()
+        ms = (C.c_double * NKIND)()
+        self.check(lib().tde_profile_read(self.h, n, ms))
+        return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+    def probe_fp64(self):
+        f = C.c_double()
+        self.check(lib().tde_probe_fp64(self.h, C.byref(f)))
+        return f.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tde_finalize(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class EOS:
+    """tde_eos: a (log10 rho, log10 T) table copied to the device."""
+
+    def __init__(self, ctx, n_rho, n_T, lrho, lT, log10_e, log10_P, log10_cs2):
+        self.ctx = ctx
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (log10_e, log10_P, log10_cs2)]
+        h = vp()
+        ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs]
+        ctx.check(lib().tde_eos_load_table(ctx.h, n_rho, n_T, lrho[0], lrho[1], lT[0], lT[1],
+                                           *ptrs, C.byref(h)))
+        self.h = h
+        self.n_rho, self.n_T, self.lrho, self.lT = n_rho, n_T, tuple(lrho), tuple(lT)
+
+    @classmethod
+    def from_file(cls, ctx, path):
+        d = np.load(path)
+        return cls(ctx, int(d["n_rho"]), int(d["n_T"]), tuple(d["lrho"]), tuple(d["lT"]),
+                   d["log10_e"], d["log10_P"], d["log10_cs2"])
+
+    def invert(self, rho, e, T=None, P=None, cs2=None, mode=INVERT_BISECT, counts=False):
+        c = Counts() if counts else None
+        self.ctx.check(lib().tde_eos_invert(self.h, mode, rho.numel(), _ptr(rho), _ptr(e), _ptr(T),
+                                            _ptr(P), _ptr(cs2), C.byref(c) if c else None))
+        return c
+
+    def eval_rhoT(self, rho, T, P=None, e=None, cs2=None):
+        self.ctx.check(lib().tde_eos_eval_rhoT(self.h, rho.numel(), _ptr(rho), _ptr(T), _ptr(P),
+                                               _ptr(e), _ptr(cs2)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tde_eos_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(**kw):
+    p = Params(EOS_IDEAL, RECON_PLM, 0, 5.0 / 3.0, 1e-3, 1e-4, 1e-300, 1e-300, 1e-300, 1.0, 1.0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_bh(on=1, excise=0, GM=0.0, r_soft=0.0, r_exc=0.0, t0=0.0, x0=(0, 0, 0), v0=(0, 0, 0),
+            a0=(0, 0, 0)):
+    return BHState(on, excise, GM, r_soft, r_exc, t0, (C.c_double * 3)(*x0),
+                   (C.c_double * 3)(*v0), (C.c_double * 3)(*a0))
+
+
+class Mesh:
+    """tde_mesh over a workloads.MeshLayout, with torch-owned states U and U1."""
+
+    def __init__(self, ctx, layout, params, eos=None):
+        torch = ctx.torch
+        self.ctx, self.layout, self.params, self.eos = ctx, layout, params, eos
+        nb = layout.nb
+        blocks = (BlockDesc * nb)(*[BlockDesc(*map(int, b)) for b in layout.blocks])
+        g = GridDesc((C.c_int * 3)(*layout.N), (C.c_double * 3)(*layout.xmin),
+                     (C.c_double * 3)(*layout.dx), (C.c_int * 3)(*layout.bc), layout.ng)
+        h = vp()
+        ctx.check(lib().tde_mesh_create(ctx.h, nb, blocks, C.byref(g), C.byref(params),
+                                        eos.h if eos is not None else None, C.byref(h)))
+        self.h = h
+        ntot, nvar = C.c_int64(), C.c_int()
+        offs = (C.c_int64 * (nb + 1))()
+        ctx.check(lib().tde_mesh_info(h, C.byref(ntot), C.byref(nvar), offs))
+        self.ntot, self.nvar = ntot.value, nvar.value
+        self.offsets = np.array(offs[:], dtype=np.int64)
+        dev = torch.device("cuda", ctx.device)
+        self.U = torch.zeros((self.nvar, self.ntot), dtype=torch.float64, device=dev)
+        self.U1 = torch.zeros_like(self.U)
+        ctx.check(lib().tde_mesh_bind_state(h, _ptr(self.U), _ptr(self.U1)))
+
+    def set_params(self, params):
+        self.ctx.check(lib().tde_mesh_set_params(self.h, C.byref(params)))
+        self.params = params
+
+    def prim_to_cons(self, W):
+        self.ctx.check(lib().tde_prim_to_cons(self.h, _ptr(W), _ptr(self.U)))
+
+    def ghost_fill(self, state, nvar=None):
+        self.ctx.check(lib().tde_ghost_fill(self.h, _ptr(state), nvar or self.nvar))
+
+    def hydro_stage(self, stage, dt_block, t_block=None, ids=None, bh=None):
+        n = 0 if ids is None else ids.numel()
+        self.ctx.check(lib().tde_hydro_stage(self.h, stage, n, _ptr(ids), _ptr(dt_block),
+                                             _ptr(t_block), C.byref(bh) if bh is not None else None))
+
+    def compute_dt(self, cfl, dt_block, dt_min=None, t_block=None, bh=None):
+        self.ctx.check(lib().tde_compute_dt(self.h, cfl, _ptr(t_block),
+                                            C.byref(bh) if bh is not None else None,
+                                            _ptr(dt_block), _ptr(dt_min)))
+
+    def excise(self, t_end_block, bh, ids=None):
+        n = 0 if ids is None else ids.numel()
+        self.ctx.check(lib().tde_excise(self.h, n, _ptr(ids), _ptr(t_end_block), C.byref(bh)))
+
+    def dual_energy_sync(self, ids=None, eta2=-1.0):
+        n = 0 if ids is None else ids.numel()
+        self.ctx.check(lib().tde_dual_energy_sync(self.h, n, _ptr(ids), eta2))
+
+    def set_time(self, t):
+        self.ctx.check(lib().tde_mesh_set_time(self.h, t))
+
+    def get_time(self):
+        t = C.c_double()
+        self.ctx.check(lib().tde_mesh_get_time(self.h, C.byref(t)))
+        return t.value
+
+    def step(self, cfl=0.0, dt=0.0, bh=None, dt_out=None):
+        self.ctx.check(lib().tde_step(self.h, cfl, dt, C.byref(bh) if bh is not None else None,
+                                      _ptr(dt_out)))
+
+    def counts(self, reset=False):
+        c = Counts()
+        self.ctx.check(lib().tde_counts_read(self.h, C.byref(c), 1 if reset else 0))
+        return c.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tde_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,380 @@
+"""GPU parity of the CUDA hydro stage against the oracle, through the C ABI.
+
+Every input comes from the seeded workload generators and the oracle (which
+converts the primitives); the GPU never supplies an expected value.  Sizes span
+several MeshBlocks, ragged block tails, both boundary kinds, PLM and PPM, the
+ideal gas and the Saha table, dual energy, the moving point mass and excision.
+"""
+import numpy as np
+import pytest
+
+from parity import assert_parity, cell_errors
+from paper_2609_37859_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+STAGE_TOL = 1e-12
+STEPS_TOL = 1e-10
+TABLE_FILE = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.dirname(
+    __import__("os").path.abspath(__file__))), "paper_2609_37859_gb300", "data", "eos_saha_hhe_256.npz")
+SCHEME_KEYS = ("eos", "recon", "dual", "gamma", "eta1", "eta2", "rho_floor", "p_floor", "u_floor",
+               "unit_rho", "unit_e")
+
+
+@pytest.fixture(scope="module")
+def tde():
+    from paper_2609_37859_gb300 import build, tde as T
+    build.build()
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(tde):
+    return tde.Context(0)
+
+
+@pytest.fixture(scope="module")
+def tables(oracle, tde, ctx):
+    d = np.load(TABLE_FILE)
+    ot = oracle.EOSTable(int(d["n_rho"]), int(d["n_T"]), tuple(d["lrho"]), tuple(d["lT"]),
+                         d["log10_e"], d["log10_P"], d["log10_cs2"])
+    gt = tde.EOS.from_file(ctx, TABLE_FILE)
+    return ot, gt
+
+
+class Pair:
+    """The same mesh on the oracle and on the GPU, started from the same state."""
+
+    def __init__(self, oracle, tde, ctx, layout, W, tables=None, bh=None, **scheme):
+        self.oracle, self.tde, self.ctx, self.layout = oracle, tde, ctx, layout
+        bhkw = {}
+        if bh is not None:
+            bhkw = dict(bh_on=bh.get("on", 1), excision_on=bh.get("excise", 0), GM=bh.get("GM", 0.0),
+                        r_soft=bh.get("r_soft", 0.0), r_exc=bh.get("r_exc", 0.0),
+                        bh_t0=bh.get("t0", 0.0), bh_x0=bh.get("x0", (0, 0, 0)),
+                        bh_v0=bh.get("v0", (0, 0, 0)), bh_a0=bh.get("a0", (0, 0, 0)))
+        self.op = oracle.make_params(**scheme, **bhkw)
+        self.om = oracle.Mesh(layout, self.op, tables[0] if tables else None)
+        gp = tde.make_params(**{k: v for k, v in scheme.items() if k in SCHEME_KEYS})
+        self.gm = tde.Mesh(ctx, layout, gp, tables[1] if tables else None)
+        self.bh = None
+        if bh is not None:
+            self.bh = tde.make_bh(on=bh.get("on", 1), excise=bh.get("excise", 0), GM=bh.get("GM", 0.0),
+                                  r_soft=bh.get("r_soft", 0.0), r_exc=bh.get("r_exc", 0.0),
+                                  t0=bh.get("t0", 0.0), x0=bh.get("x0", (0, 0, 0)),
+                                  v0=bh.get("v0", (0, 0, 0)), a0=bh.get("a0", (0, 0, 0)))
+        self.U = self.om.prim_to_cons(W)
+        self.gm.U.copy_(torch.from_numpy(self.U))
+        self.dev = self.gm.U.device
+        self.nb = layout.nb
+
+    def gpu(self, which="U"):
+        torch.cuda.synchronize()
+        return getattr(self.gm, which).cpu().numpy()
+
+    def dvec(self, x):
+        return torch.tensor(np.broadcast_to(np.asarray(x, dtype=np.float64), (self.nb,)).copy(),
+                            device=self.dev)
+
+
+# ------------------------------------------------------------ C1: Sod ----
+
+def test_c1_sod_one_block(oracle, tde, ctx):
+    """One 32^3 block, ideal gas, PLM + HLLC + RK2, outflow, Sod along x."""
+    lay = wl.uniform_layout((32, 32, 32), (32, 32, 32), bc=(0, 0, 0), ng=2)
+    P = Pair(oracle, tde, ctx, lay, wl.sod(lay))
+    om, gm = P.om, P.gm
+    dt = om.cfl_dt(P.U, 0.3).min()
+    # stage 0
+    U0 = P.U.copy()
+    om.ghost_fill(U0)
+    O1 = om.new_state()
+    om.stage(0, U0, U0, O1, np.full(1, dt), np.zeros(1))
+    gm.hydro_stage(0, P.dvec(dt), P.dvec(0.0))
+    assert_parity(lay.to_global(P.gpu("U1")), lay.to_global(O1), STAGE_TOL, "stage 0")
+    # stage 1 from the same stage-0 state
+    gm.U1.copy_(torch.from_numpy(O1))
+    om.ghost_fill(O1)
+    O2 = U0.copy()
+    om.stage(1, U0, O1, O2, np.full(1, dt), np.zeros(1))
+    gm.hydro_stage(1, P.dvec(dt), P.dvec(0.0))
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(O2), STAGE_TOL, "stage 1")
+    # 10 CFL steps, each side choosing its own dt
+    gm.U.copy_(torch.from_numpy(P.U))
+    gm.set_time(0.0)
+    U = P.U.copy()
+    t = 0.0
+    for _ in range(10):
+        d = om.cfl_dt(U, 0.3).min()
+        om.step(U, d, t)
+        t += d
+        gm.step(cfl=0.3)
+    assert gm.get_time() == pytest.approx(t, rel=1e-13)
+    G = lay.to_global(P.gpu("U"))
+    assert_parity(G, lay.to_global(U), STEPS_TOL, "10 steps")
+    assert (G[2] == 0).all() and (G[3] == 0).all()
+
+
+def test_prim_to_cons_parity(oracle, tde, ctx, tables):
+    lay = wl.uniform_layout((16, 16, 16), (8, 16, 16), bc=(1, 1, 1), ng=2)
+    W = wl.random_smooth(lay, seed=9)
+    P = Pair(oracle, tde, ctx, lay, W, dual=1)
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).to(P.dev)
+    P.gm.prim_to_cons(Wd)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(P.U), 1e-15, "ideal")
+    # table, cgs
+    rho0, T0 = 1e-8, 1e3
+    P0 = tables[0].eval_rhoT(rho0, T0)[0]
+    Wt, _ = wl.entropy_wave(lay, rho0, P0, 3e5, amp=1e-2, seed=1)
+    Q = Pair(oracle, tde, ctx, lay, Wt, tables, eos=1, dual=1)
+    Q.gm.U.zero_()
+    Q.gm.prim_to_cons(torch.from_numpy(np.ascontiguousarray(Wt)).to(Q.dev))
+    assert_parity(lay.to_global(Q.gpu("U")), lay.to_global(Q.U), 1e-12, "table")
+
+
+# ------------------------------------------------------ C2: entropy wave ----
+
+def c2_pair(oracle, tde, ctx, tables, N, block, seed=7):
+    rho0, T0 = 1e-8, 1e3
+    Pw, _, cs2 = tables[0].eval_rhoT(rho0, T0)
+    lay = wl.uniform_layout((N, N, N), (block, block, block), bc=(1, 1, 1), ng=2)
+    W, _ = wl.entropy_wave(lay, rho0, Pw, 1e7 * np.sqrt(cs2), amp=1e-3, seed=seed)
+    P = Pair(oracle, tde, ctx, lay, W, tables, eos=1, dual=1, eta1=1e-3, eta2=1e-4,
+             rho_floor=1e-20, p_floor=1e-20, u_floor=1e-20)
+    return P, Pw
+
+
+def test_c2_entropy_wave_parity(oracle, tde, ctx, tables):
+    """Saha table, dual energy, periodic, Mach 1e7 (the bench physics), 2^3 blocks."""
+    P, Pw = c2_pair(oracle, tde, ctx, tables, 32, 16)
+    om, gm, lay = P.om, P.gm, P.layout
+    dt = om.cfl_dt(P.U, 0.3).min()
+    U0 = P.U.copy()
+    om.ghost_fill(U0)
+    O1 = om.new_state()
+    om.stage(0, U0, U0, O1, np.full(P.nb, dt), np.zeros(P.nb))
+    gm.hydro_stage(0, P.dvec(dt), P.dvec(0.0))
+    assert_parity(lay.to_global(P.gpu("U1")), lay.to_global(O1), STAGE_TOL, "stage 0")
+    U = P.U.copy()
+    gm.set_time(0.0)
+    for _ in range(20):
+        d = om.cfl_dt(U, 0.3).min()
+        om.step(U, d, 0.0)
+        gm.step(cfl=0.3)
+    G = lay.to_global(P.gpu("U"))
+    assert_parity(G, lay.to_global(U), STEPS_TOL, "20 steps")
+    c = gm.counts()
+    assert c["table_clamp"] == 0 and c["dual_aux_used"] > 0 and c["nonfinite"] == 0
+
+
+def test_c2_full_size_sampled_stage_and_100_step_invariants(oracle, tde, ctx, tables):
+    """128^3 as 64 blocks of 32^3 (the benchmark workload).  One stage: the oracle
+    recomputes 4 sampled blocks from the same ghost-filled input.  100 steps:
+    conservation and the uniform pressure of the entropy wave hold at any size."""
+    P, Pw = c2_pair(oracle, tde, ctx, tables, 128, 32, seed=3)
+    om, gm, lay = P.om, P.gm, P.layout
+    dt = om.cfl_dt(P.U, 0.3).min()
+    U0 = P.U.copy()
+    om.ghost_fill(U0)
+    O1 = om.new_state()
+    sample = [0, 21, 42, 63]
+    om.stage(0, U0, U0, O1, np.full(P.nb, dt), np.zeros(P.nb), ids=sample)
+    gm.hydro_stage(0, P.dvec(dt), P.dvec(0.0))
+    G1 = P.gpu("U1")
+    for b in sample:
+        flat, _ = lay.interior_index(b)
+        assert_parity(G1[:, flat], O1[:, flat], STAGE_TOL, "block %d" % b)
+    gm.U.copy_(torch.from_numpy(P.U))
+    gm.set_time(0.0)
+    G0 = lay.to_global(P.U)
+    for _ in range(100):
+        gm.step(cfl=0.3)
+    G = lay.to_global(P.gpu("U"))
+    for v in (0, 1, 4):
+        assert abs(G[v].sum() - G0[v].sum()) <= 1e-13 * np.abs(G0[v]).sum()
+    assert np.abs(G[2]).max() == 0 and np.abs(G[3]).max() == 0
+    # pressure from the auxiliary energy through the GPU's own table inversion
+    rho = torch.from_numpy(G[0].ravel().copy()).cuda()
+    e = torch.from_numpy((G[5] / G[0]).ravel().copy()).cuda()
+    Pg = torch.empty_like(rho)
+    P.gm.eos.invert(rho, e, P=Pg)
+    assert float((Pg / Pw - 1).abs().max()) < 1e-10
+    assert gm.counts()["nonfinite"] == 0
+
+
+# ------------------------------------------ ragged blocks, PPM, 2D, subsets ----
+
+@pytest.mark.parametrize("recon,bc", [(0, (1, 0, 1)), (1, (1, 1, 1)), (1, (0, 0, 0))])
+def test_ragged_blocks_ideal_dual(oracle, tde, ctx, recon, bc):
+    lay = wl.uniform_layout((20, 13, 9), (8, 8, 4), bc=bc, ng=2 + recon)
+    W = wl.random_smooth(lay, seed=5)
+    P = Pair(oracle, tde, ctx, lay, W, recon=recon, dual=1, eta1=1e-3)
+    om, gm = P.om, P.gm
+    U = P.U.copy()
+    gm.set_time(0.0)
+    for n in range(8):
+        d = om.cfl_dt(U, 0.3).min()
+        om.step(U, d, 0.0)
+        gm.step(cfl=0.3)
+        if n == 0:
+            assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STAGE_TOL * 10, "first step")
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "8 steps")
+
+
+def test_two_dimensional_mesh(oracle, tde, ctx):
+    lay = wl.uniform_layout((24, 16, 1), (8, 8, 1), bc=(1, 0, 0), ng=2)
+    P = Pair(oracle, tde, ctx, lay, wl.random_smooth(lay, seed=2))
+    U = P.U.copy()
+    for _ in range(6):
+        d = P.om.cfl_dt(U, 0.4).min()
+        P.om.step(U, d, 0.0)
+        P.gm.step(cfl=0.4)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "2D")
+
+
+def test_subset_of_blocks_with_per_block_dt_and_time(oracle, tde, ctx):
+    """A stage on a listed subset with per-block dt and t (the LAT calling
+    pattern): the padded-conversion path, gravity at each block's own time."""
+    lay = wl.uniform_layout((16, 16, 16), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    bh = dict(on=1, GM=0.05, r_soft=0.1, x0=(0.3, 0.5, 0.6), v0=(2.0, 0.0, -1.0), a0=(0.5, 0.1, 0.0))
+    P = Pair(oracle, tde, ctx, lay, wl.random_smooth(lay, seed=4, P0=3.0), bh=bh)
+    ids = [1, 2, 5, 6]
+    rng = np.random.default_rng(0)
+    dtb = rng.uniform(1e-3, 2e-3, P.nb)
+    tb = rng.uniform(0.0, 0.1, P.nb)
+    U0 = P.U.copy()
+    om = P.om
+    om.ghost_fill(U0)
+    O1 = U0.copy()
+    om.stage(0, U0, U0, O1, dtb, tb, ids=ids)
+    P.gm.U1.copy_(torch.from_numpy(U0))
+    P.gm.hydro_stage(0, P.dvec(dtb), P.dvec(tb), ids=torch.tensor(ids, dtype=torch.int32, device=P.dev),
+                     bh=P.bh)
+    G1 = P.gpu("U1")
+    for b in ids:
+        flat, _ = lay.interior_index(b)
+        assert_parity(G1[:, flat], O1[:, flat], STAGE_TOL, "block %d" % b)
+
+
+# ------------------------------------------- BH, excision, table in code units ----
+
+def test_bh_excision_ppm_table_code_units(oracle, tde, ctx, tables):
+    """Code units of Table 1 (table lookups scaled by rho0 and v0^2), PPM, dual
+    energy, moving point mass with excision, mixed 8^3 / 4^3 blocks."""
+    rho0, v0 = 0.7382, 1.0948e8
+    lay = wl.mixed_layout((16, 16, 8), 8, {(0, 0, 0), (1, 1, 0)},
+                          ((-2.0, 2.0), (-2.0, 2.0), (-1.0, 1.0)), (0, 0, 0), 3)
+    x, y, z = lay.cell_centres()
+    r = np.sqrt(x ** 2 + y ** 2 + z ** 2)
+    rho = 1e-6 + 1e-3 * np.exp(-((r - 1.0) / 0.3) ** 2)
+    # temperature ~1e4 K gas: P in code units from the ideal-gas estimate
+    Pc = rho * rho0 * 1.380649e-16 * 1e4 / (0.6 * 1.6605e-24) / (rho0 * v0 * v0)
+    vx, vy = -y * 0.3, x * 0.3
+    W = wl.prim_state(lay, rho, vx, vy, 0 * rho, Pc)
+    bh = dict(on=1, excise=1, GM=1000 / (4 * np.pi), r_soft=0.005, r_exc=0.35, x0=(0.05, -0.02, 0.0),
+              v0=(0.1, 0.0, 0.0))
+    P = Pair(oracle, tde, ctx, lay, W, tables, bh=bh, eos=1, recon=1, dual=1, eta1=1e-3, eta2=1e-4,
+             rho_floor=1e-10, p_floor=1e-16, u_floor=1.5e-16, unit_rho=rho0, unit_e=v0 * v0)
+    U = P.U.copy()
+    P.gm.set_time(0.0)
+    t = 0.0
+    dtb = P.dvec(0.0)
+    for _ in range(5):
+        d = P.om.cfl_dt(U, 0.3, np.full(P.nb, t)).min()
+        P.om.step(U, d, t)
+        t += d
+        P.gm.step(cfl=0.3, bh=P.bh)
+    assert P.gm.get_time() == pytest.approx(t, rel=1e-12)
+    G = lay.to_global(P.gpu("U"))
+    assert_parity(G, lay.to_global(U), STEPS_TOL, "bh")
+    c = P.gm.counts()
+    assert c["excised"] > 0 and c["nonfinite"] == 0
+
+
+def test_compute_dt_parity(oracle, tde, ctx):
+    lay = wl.uniform_layout((16, 16, 16), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    bh = dict(on=1, excise=1, GM=0.3, r_soft=0.05, r_exc=0.12, x0=(0.5, 0.5, 0.5))
+    P = Pair(oracle, tde, ctx, lay, wl.random_smooth(lay, seed=8), bh=bh)
+    want = P.om.cfl_dt(P.U, 0.35)
+    dtb = torch.zeros(P.nb, dtype=torch.float64, device=P.dev)
+    dmin = torch.zeros(1, dtype=torch.float64, device=P.dev)
+    P.gm.compute_dt(0.35, dtb, dmin, t_block=P.dvec(0.0), bh=P.bh)
+    assert np.allclose(dtb.cpu().numpy(), want, rtol=1e-14, atol=0)
+    assert float(dmin) == pytest.approx(want.min(), rel=1e-14)
+
+
+def test_dual_sync_and_excise_parity(oracle, tde, ctx):
+    lay = wl.uniform_layout((12, 10, 8), (6, 5, 8), bc=(1, 0, 1), ng=2)
+    rng = np.random.default_rng(4)
+    G = np.zeros((6, 8, 10, 12))
+    G[0] = rng.uniform(0.5, 2.0, G[0].shape)
+    G[1:4] = rng.normal(0, 1.0, G[1:4].shape)
+    ke = 0.5 * (G[1] ** 2 + G[2] ** 2 + G[3] ** 2) / G[0]
+    G[4] = ke + rng.uniform(-0.05, 0.3, ke.shape) * rng.uniform(0.1, 10, ke.shape)
+    G[5] = rng.uniform(0.01, 0.02, ke.shape)
+    U = lay.from_global(G)
+    bh = dict(on=1, excise=1, GM=0.0, r_exc=0.3, x0=(0.5, 0.5, 0.5))
+    P = Pair(oracle, tde, ctx, lay, np.zeros((5, lay.ntot)), bh=bh, dual=1, eta2=0.05,
+             rho_floor=1e-3, u_floor=2e-3)
+    P.gm.U.copy_(torch.from_numpy(U))
+    O = U.copy()
+    P.om.ghost_fill(O)
+    P.om.dual_sync(O)
+    P.gm.dual_energy_sync()
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(O), 1e-13, "sync")
+    P.om.excise(O, np.full(P.nb, 0.25))
+    P.gm.excise(P.dvec(0.25), P.bh)
+    Gg = lay.to_global(P.gpu("U"))
+    assert np.array_equal(Gg[0], lay.to_global(O)[0])
+    assert P.gm.counts()["excised"] > 0
+
+
+# ------------------------------------------------------ EOS inversion ----
+
+def test_eos_invert_parity(oracle, tde, ctx, tables):
+    """(rho, e) -> (T, P, cs2) on 2^14 seeded points across the table, plus
+    out-of-range points that must be clamped and counted."""
+    ot, _ = tables
+    gt = tde.EOS.from_file(ctx, TABLE_FILE)   # fresh counters
+    rng = np.random.default_rng(12)
+    n = 1 << 14
+    lr = rng.uniform(-14, 2, n)
+    lT = rng.uniform(2.0, 8.0, n)
+    e = np.array([ot.eval_rhoT(10 ** a, 10 ** b)[1] for a, b in zip(lr, lT)])
+    e *= np.exp(rng.normal(0, 1e-3, n))
+    rho = 10 ** lr
+    e[:8] = [1e-30, -1.0, 1e40, 1e40, 1e-30, 1e10, 1e10, 1e10]
+    rho[5:8] = [1e-20, 1e5, 1.0]
+    want = np.array([ot.invert(r, x) for r, x in zip(rho, e)])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    T, Pr, c2 = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+    gt.invert(d(rho), d(e), T=T, P=Pr, cs2=c2)
+    cnt = gt.invert(d(rho), d(e), counts=True)
+    for got, col in ((T, 0), (Pr, 1), (c2, 2)):
+        g = got.cpu().numpy()
+        assert np.max(np.abs(g / want[:, col] - 1)) < 1e-12
+    assert cnt.table_clamp == 2 * int(want[:, 3].sum())
+
+
+def test_invalid_arguments(tde, ctx):
+    lay = wl.uniform_layout((8, 8, 8), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    with pytest.raises(tde.TDEError) as ei:
+        tde.Mesh(ctx, lay, tde.make_params(recon=tde.RECON_PPM))
+    assert ei.value.code == tde.TDE_EINVAL
+    bad = wl.MeshLayout(np.array([[0, 0, 0, 8, 8, 8], [4, 0, 0, 4, 8, 8]]), (8, 8, 8), (0, 0, 0),
+                        (0.1,) * 3, (1, 1, 1), 2)
+    with pytest.raises(tde.TDEError):
+        tde.Mesh(ctx, bad, tde.make_params())
+    big = wl.uniform_layout((64, 8, 8), (64, 8, 8), bc=(1, 1, 1), ng=2)
+    with pytest.raises(tde.TDEError):
+        tde.Mesh(ctx, big, tde.make_params())
+    le = np.tile(np.linspace(1, 2, 4), (3, 1))
+    le[1, 2] = le[1, 1]
+    with pytest.raises(tde.TDEError):
+        tde.EOS(ctx, 3, 4, (0, 1), (0, 1), le, le, le)
+    with pytest.raises(tde.TDEError):
+        tde.make_params(eos=tde.EOS_TABLE) and tde.Mesh(ctx, lay, tde.make_params(eos=tde.EOS_TABLE))
