@@ -1,0 +1,347 @@
+"""Benchmark of the GB300 hydro stage: FP64 cell-updates/s on the tabulated-EOS,
+dual-energy entropy-wave workload (128^3 cells as 64 MeshBlocks of 32^3, PLM +
+HLLC + SSP-RK2, Saha H/He table, periodic, Mach 1e7 on rho = 1e-8 g/cm^3,
+T = 1e3 K).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = one synchronised RK2 step of every MeshBlock through the C ABI
+(tde_step: CFL dt, two stages, resync), i.e. 128^3 cell-updates.  Prints one
+JSON line (rank 0).  --impl reference times the CPU oracle on the host cores
+instead (a bounded sample of blocks per step).  Under torchrun each rank runs an
+independent replica on its own GPU (weak scaling, no collective on the data
+path); the timed region is bracketed by a barrier and the maximum over ranks
+is reported.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 cell-updates/s and % of HBM roofline; surrogate+batched vs plain form at 1e-10"
+UNIT = "cell-updates/s"
+TABLE = os.path.join(ROOT, "paper_2609_37859_gb300", "data", "eos_saha_hhe_256.npz")
+N, BLOCK, CFL = 128, 32, 0.3
+RHO0, T0, MACH, AMP, SEED = 1e-8, 1e3, 1e7, 1e-3, 2609
+SCHEME = dict(eos=1, dual=1, eta1=1e-3, eta2=1e-4, rho_floor=1e-20, p_floor=1e-20, u_floor=1e-20)
+# algorithmic HBM bytes per cell-update (FP64, 6 conserved fields): stage 1 reads
+# and writes 6 fields, stage 2 reads U0 and U1 and writes U2 -> 5 * 6 * 8
+BYTES_PER_CELL_UPDATE = 240.0
+WORKLOAD = ("entropy wave, 128^3 cells as 64 MeshBlocks of 32^3, ghost width 2, Saha H/He "
+            "256x256 table, dual energy, PLM+HLLC+SSP-RK2, periodic, Mach 1e7, CFL 0.3")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), \
+        int(os.environ.get("WORLD_SIZE", 1))
+
+
+def layout():
+    from paper_2609_37859_gb300 import workloads as wl
+    return wl.uniform_layout((N, N, N), (BLOCK, BLOCK, BLOCK), bc=(1, 1, 1), ng=2)
+
+
+def eos_point(table_arrays):
+    """P and c_s^2 of the background (rho0, T0) by bilinear table evaluation."""
+    d = table_arrays
+    lr = (np.log10(RHO0) - d["lrho"][0]) / ((d["lrho"][1] - d["lrho"][0]) / (d["n_rho"] - 1))
+    lt = (np.log10(T0) - d["lT"][0]) / ((d["lT"][1] - d["lT"][0]) / (d["n_T"] - 1))
+    i, j = int(lr), int(lt)
+    w, s = lr - i, lt - j
+
+    def bil(f):
+        return (1 - w) * ((1 - s) * f[i, j] + s * f[i, j + 1]) + w * ((1 - s) * f[i + 1, j] + s * f[i + 1, j + 1])
+    return 10 ** bil(d["log10_P"]), 10 ** bil(d["log10_cs2"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def run_gpu(args):
+    import torch
+    from paper_2609_37859_gb300 import tde, workloads as wl
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tde.Context(local, stream)
+    tab = np.load(TABLE)
+    eos = tde.EOS.from_file(ctx, TABLE)
+    Pw, cs2 = eos_point(tab)
+    lay = layout()
+    W, _ = wl.entropy_wave(lay, RHO0, Pw, MACH * np.sqrt(cs2), amp=AMP, seed=SEED + rank)
+    mesh = tde.Mesh(ctx, lay, tde.make_params(**SCHEME), eos)
+    W_d = torch.from_numpy(np.ascontiguousarray(W)).to(dev)
+    mesh.prim_to_cons(W_d)
+    U_init = mesh.U.clone()
+    del W_d
+    ncell = lay.ncells
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident timed region (value)
+    for _ in range(args.warmup):
+        mesh.step(cfl=CFL)
+    barrier()
+    ctx.profile(True)
+    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                    if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        mesh.step(cfl=CFL)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    clk = clocks.stop()
+    ctx.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    counts = mesh.counts()
+
+    # ---- end-to-end through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory and the result back out
+    host_in = U_init.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    nbytes = host_in.numel() * 8
+    mesh.U.copy_(U_init)
+    mesh.set_time(0.0)
+    for _ in range(max(1, args.warmup)):
+        mesh.U.copy_(host_in, non_blocking=True)
+        mesh.step(cfl=CFL)
+        host_out.copy_(mesh.U, non_blocking=True)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        mesh.U.copy_(host_in, non_blocking=True)
+        mesh.step(cfl=CFL)
+        host_out.copy_(mesh.U, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    ms_e2e = f0.elapsed_time(f1)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t)
+
+    fp64_peak = ctx.probe_fp64()
+    if rank == 0:
+        steps = args.steps
+        value = world * ncell * steps / (ms * 1e-3)
+        e2e = world * ncell * steps / (ms_e2e * 1e-3)
+        sweeps = {k: prof[k] for k in ("sweep_x", "sweep_y", "sweep_z")}
+        dom = max(sweeps, key=lambda k: sweeps[k][1])
+        n_dom, ms_dom = sweeps[dom]
+        avg_ms = ms_dom / max(n_dom, 1)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        fp64_per_cell = FP64_FLOP_PER_CELL_SWEEP.get(dom)
+        roof = {"bound": "alu", "kernel": "k_sweep (%s)" % dom.replace("sweep_", ""),
+                "unit": "TFLOP/s", "peak": fp64_peak * 1e-12,
+                "peak_source": "FP64 FMA probe measured in this run (tde_probe_fp64)",
+                "traffic": DRAM_BYTES_SWEEP.get(dom) if KERNELS_AS_CAPTURED else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
+                "avg_launch_ms": avg_ms}
+        if fp64_per_cell:
+            ach = fp64_per_cell * ncell / (avg_ms * 1e-3)
+            roof.update({"achieved": ach * 1e-12, "frac": ach / fp64_peak,
+                         "fp64_flop_per_cell": fp64_per_cell})
+        else:
+            roof.update({"achieved": None, "frac": None})
+        total_launches = sum(v[0] for v in prof.values())
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": ncell, "meshblocks": lay.nb,
+                       "global_batch": world * ncell, "parallelism": "replica per GPU" if world > 1 else "1 GPU",
+                       "l2": "working set %.2f GB per step > 129 MB L2 (no flush needed)" %
+                             ((mesh.U.numel() * 2 + mesh.ntot * (7 + 8)) * 8 / 1e9)},
+            "hbm_roofline": {"bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
+                             "achieved_gbs": value / world * BYTES_PER_CELL_UPDATE * 1e-9,
+                             "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                             "frac": value / world * BYTES_PER_CELL_UPDATE * 1e-9 / hbm_peak},
+            "roofline": roof,
+            "kernels_ms": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
+            "kernels_launches": {k: v[0] for k, v in prof.items() if v[0]},
+            "gpu_launches": total_launches,
+            "clocks": clk,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "counters": counts,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# FP64 operations (DADD + DMUL + 2 x DFMA thread-instructions, ncu SASS counters)
+# per interior cell in one launch of each sweep kernel on this workload, and the
+# DRAM bytes of one launch; profiles/k_sweep_c2_entropy_wave_ncu.md holds the
+# capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
+# False (traffic reported as null) whenever a sweep kernel changes.
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 332.3, "sweep_y": 279.6, "sweep_z": 506.1}
+DRAM_BYTES_SWEEP = {"sweep_x": 267.2e6, "sweep_y": 397.4e6, "sweep_z": 540.4e6}
+KERNELS_AS_CAPTURED = True
+
+
+# ------------------------------------------------------------------ oracle ---
+
+def oracle_setup(sample_blocks):
+    from oracle import tref
+    d = np.load(TABLE)
+    ot = tref.EOSTable(int(d["n_rho"]), int(d["n_T"]), tuple(d["lrho"]), tuple(d["lT"]),
+                       d["log10_e"], d["log10_P"], d["log10_cs2"])
+    Pw, cs2 = eos_point(d)
+    from paper_2609_37859_gb300 import workloads as wl
+    lay = layout()
+    W, _ = wl.entropy_wave(lay, RHO0, Pw, MACH * np.sqrt(cs2), amp=AMP, seed=SEED)
+    m = tref.Mesh(lay, tref.make_params(**SCHEME), ot)
+    U = m.prim_to_cons(W)
+    ids = np.linspace(0, lay.nb - 1, sample_blocks).astype(np.int32)
+    m.dt = float(m.cfl_dt(U, CFL).min())
+    return tref, m, U, ids, lay
+
+
+def oracle_step(tref, m, U, S, ids, lay):
+    """One RK2 step of the sampled blocks (ghost fill, two stages, resync)."""
+    nb = lay.nb
+    dtb, tb = np.full(nb, m.dt), np.zeros(nb)
+    m.ghost_fill(U)
+    m.stage(0, U, U, S, dtb, tb, ids=ids)
+    m.ghost_fill(S)
+    m.stage(1, U, S, U, dtb, tb, ids=ids)
+    m.ghost_fill(U)
+    m.dual_sync(U, ids=ids)
+
+
+def cpu_baseline(seconds):
+    """The oracle as it stands, on the host cores, on a bounded sample (whole
+    RK2 steps of 8 of the 64 MeshBlocks, repeated for about `seconds`)."""
+    tref, m, U, ids, lay = oracle_setup(8)
+    S = m.new_state()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle_step(tref, m, U, S, ids, lay)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cells = n * len(ids) * BLOCK ** 3
+    return {"value": cells / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d RK2 steps of %d of the 64 MeshBlocks (32^3) of the workload, %.1f s" %
+                      (n, len(ids), el)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    tref, m, U, ids, lay = oracle_setup(4)
+    S = m.new_state()
+    for _ in range(args.warmup):
+        oracle_step(tref, m, U, S, ids, lay)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(tref, m, U, S, ids, lay)
+    el = time.perf_counter() - t0
+    cells = args.steps * len(ids) * BLOCK ** 3
+    v = cells / el
+    sample = "each step: one RK2 step of %d of the 64 MeshBlocks (32^3) of the workload" % len(ids)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "cells_per_step": len(ids) * BLOCK ** 3},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -638,9 +638,12 @@ void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *
   double dxmin = HUGE_VAL;
   for (int a = 0; a < 3; ++a)
     if (m->active[a] && m->d.dx[a] < dxmin) dxmin = m->d.dx[a];
+#pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < m->d.nb; ++b) {
     const int *B = m->blocks + 6 * b;
     double best = HUGE_VAL;
+    tref_counts lc;
+    memset(&lc, 0, sizeof lc);
     for (int k = 0; k < B[5]; ++k)
       for (int j = 0; j < B[4]; ++j)
         for (int i = 0; i < B[3]; ++i) {
@@ -652,7 +655,7 @@ void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *
           int64_t l = cidx(m, b, ii, jj, kk);
           double u[6], w[8];
           for (int v = 0; v < m->nvar; ++v) u[v] = U[v * m->ntot + l];
-          c2p(m, u, w, c);
+          c2p(m, u, w, &lc);
           double cs = sqrt(w[6] * w[4] / w[0]);
           for (int a = 0; a < 3; ++a) {
             if (!m->active[a]) continue;
@@ -673,6 +676,10 @@ void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *
           }
         }
     dt_b[b] = cfl * best;
+    if (c) {
+#pragma omp critical
+      add_counts(c, &lc);
+    }
   }
 }
 
@@ -698,6 +705,7 @@ void tref_prim_to_cons(const tref_mesh *m, const double *W, double *U) {
   /* W holds 5 fields (rho, vx, vy, vz, P) in the same padded layout as U */
   const tref_params *p = &m->p;
   const int64_t nt = m->ntot;
+#pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < m->d.nb; ++b) {
     const int *B = m->blocks + 6 * b;
     for (int k = 0; k < B[5]; ++k)
