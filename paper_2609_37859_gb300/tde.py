@@ -312,3 +312,4 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
