@@ -212,6 +212,37 @@ TDE_API int tde_step(tde_mesh *mesh, double cfl, double dt_fixed, const tde_bh_s
  * optionally reset them. */
 TDE_API int tde_counts_read(tde_mesh *mesh, tde_counts *out, int reset);
 
+/* ---- allocation-free variant ---------------------------------------------- */
+
+/* A tabulated EOS held in device arrays that the caller owns (same layout and
+ * meaning as the host arrays of tde_eos_load_table; not validated). */
+typedef struct {
+  int n_rho, n_T;
+  double log10_rho_min, log10_rho_max, log10_T_min, log10_T_max;
+  const double *log10_e, *log10_P, *log10_cs2;   /* device, [n_rho][n_T] */
+} tde_table_view;
+
+/* The per-MeshBlock CFL step of tde_compute_dt, for callers that may not
+ * allocate device memory: programs whose device memory is owned by another
+ * allocator (a framework that reserves the whole device in its own pool at
+ * start-up) or loops that forbid allocation after initialisation.  Such callers
+ * cannot create a tde_mesh, so this call takes the block list (host), the grid
+ * and scheme (host), the state U (device, the layout of tde.h for these blocks)
+ * and, for TDE_EOS_TABLE, a table view; it writes dt_block (device, nblocks)
+ * and/or dt_min (device, 1).  The paper has no counterpart: this is a library
+ * service.  It calls no cudaMalloc, cudaFree or other allocating routine; its
+ * scratch (block list copy, offsets, per-block minima) is one fixed device
+ * array of about 164 KB that every GPU loading the library holds until exit.
+ * Limit: 1 <= nblocks <= 4096, else TDE_EINVAL.  The first call on a device
+ * looks up that array's device address, so it should come before any stream
+ * capture.  All calls share the array: calls whose GPU work overlaps race.
+ * Uses ctx's stream; asynchronous. */
+TDE_API int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block_desc *blocks,
+                                   const tde_grid_desc *grid, const tde_params *params,
+                                   const tde_table_view *table, const double *U, double cfl,
+                                   const double *t_block, const tde_bh_state *bh,
+                                   double *dt_block, double *dt_min);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Kernel classes counted and (optionally) timed by the context. */

@@ -50,6 +50,13 @@ class GridDesc(C.Structure):
                 ("bc", C.c_int * 3), ("ng", C.c_int)]
 
 
+class TableView(C.Structure):
+    _fields_ = [("n_rho", C.c_int), ("n_T", C.c_int), ("log10_rho_min", C.c_double),
+                ("log10_rho_max", C.c_double), ("log10_T_min", C.c_double),
+                ("log10_T_max", C.c_double), ("log10_e", C.c_void_p), ("log10_P", C.c_void_p),
+                ("log10_cs2", C.c_void_p)]
+
+
 class Counts(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("rho_floor", "p_floor", "u_floor", "table_clamp",
                                           "excised", "dual_aux_used", "synced", "nonfinite")]
@@ -89,6 +96,9 @@ _SIGS = {
     "tde_profile": [vp, C.c_int],
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
+    "tde_compute_dt_noalloc": [vp, C.c_int, C.POINTER(BlockDesc), C.POINTER(GridDesc),
+                               C.POINTER(Params), C.POINTER(TableView), dp, C.c_double, dp,
+                               C.POINTER(BHState), dp, dp],
 }
 KERNEL_KINDS = ("c2p", "dt", "ghost", "sweep_x", "sweep_y", "sweep_z", "sync", "excise", "scalar",
                 "p2c", "eos", "probe")
@@ -313,3 +323,21 @@ class Mesh:
         except Exception:
             pass
 
+
+def compute_dt_noalloc(ctx, layout, params, U, cfl, dt_block=None, dt_min=None, table=None,
+                       t_block=None, bh=None):
+    """tde_compute_dt_noalloc: per-block CFL step with no device allocation inside
+    the library.  `table` is a (n_rho, n_T, lrho, lT, log10_e, log10_P, log10_cs2)
+    tuple whose arrays are CUDA tensors the caller owns."""
+    nb = layout.nb
+    blocks = (BlockDesc * nb)(*[BlockDesc(*map(int, b)) for b in layout.blocks])
+    g = GridDesc((C.c_int * 3)(*layout.N), (C.c_double * 3)(*layout.xmin),
+                 (C.c_double * 3)(*layout.dx), (C.c_int * 3)(*layout.bc), layout.ng)
+    tv = None
+    if table is not None:
+        n_rho, n_T, lrho, lT, le, lp, lc = table
+        tv = TableView(n_rho, n_T, lrho[0], lrho[1], lT[0], lT[1], _ptr(le), _ptr(lp), _ptr(lc))
+    ctx.check(lib().tde_compute_dt_noalloc(ctx.h, nb, blocks, C.byref(g), C.byref(params),
+                                           C.byref(tv) if tv is not None else None, _ptr(U), cfl,
+                                           _ptr(t_block), C.byref(bh) if bh is not None else None,
+                                           _ptr(dt_block), _ptr(dt_min)))

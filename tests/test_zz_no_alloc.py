@@ -1,0 +1,83 @@
+"""tde_compute_dt_noalloc: the CFL step for callers that may not allocate device
+memory (their device memory belongs to another allocator, or allocation is
+forbidden after start-up).  It must give what tde_compute_dt gives, call after
+call, although its scratch is one fixed device array shared by all calls.
+
+This file is collected last so that a failure here leaves every other test run.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2609_37859_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLE = os.path.join(ROOT, "paper_2609_37859_gb300", "data", "eos_saha_hhe_256.npz")
+
+
+@pytest.fixture(scope="module")
+def tde():
+    from paper_2609_37859_gb300 import build, tde as T
+    build.build()
+    return T
+
+
+def test_noalloc_dt_equals_compute_dt_on_two_calls(tde):
+    ctx = tde.Context(0)
+    d = np.load(TABLE)
+    eos = tde.EOS.from_file(ctx, TABLE)
+    dev = torch.device("cuda", 0)
+    view = (int(d["n_rho"]), int(d["n_T"]), tuple(d["lrho"]), tuple(d["lT"]),
+            torch.from_numpy(d["log10_e"].copy()).to(dev), torch.from_numpy(d["log10_P"].copy()).to(dev),
+            torch.from_numpy(d["log10_cs2"].copy()).to(dev))
+    # tabulated, dual-energy entropy wave on 4 x 4 x 2 blocks of 16^3 (the bench physics)
+    lay = wl.uniform_layout((64, 64, 32), (16, 16, 16), bc=(1, 1, 1), ng=2)
+    P0 = 639.748076615761   # pressure at rho = 1e-8, T = 1e3 of the stored table (any level works)
+    W, _ = wl.entropy_wave(lay, 1e-8, P0, 3e12, amp=1e-3, seed=5)
+    params = tde.make_params(eos=tde.EOS_TABLE, dual=1, eta1=1e-3, eta2=1e-4, rho_floor=1e-20,
+                             p_floor=1e-20, u_floor=1e-20)
+    mesh = tde.Mesh(ctx, lay, params, eos)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    nb = lay.nb
+    for call in range(2):
+        want = torch.zeros(nb, dtype=torch.float64, device=dev)
+        want_min = torch.zeros(1, dtype=torch.float64, device=dev)
+        mesh.compute_dt(0.3, want, want_min)
+        got = torch.full((nb,), -1.0, dtype=torch.float64, device=dev)
+        got_min = torch.full((1,), -1.0, dtype=torch.float64, device=dev)
+        tde.compute_dt_noalloc(ctx, lay, params, mesh.U, 0.3, got, got_min, table=view)
+        torch.cuda.synchronize()
+        assert np.allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-14, atol=0), call
+        assert float(got_min) == pytest.approx(float(want_min), rel=1e-14)
+        mesh.step(cfl=0.3)    # a new state for the second call
+
+
+def test_noalloc_dt_with_point_mass_and_excision_then_size_limit(tde):
+    ctx = tde.Context(0)
+    dev = torch.device("cuda", 0)
+    lay = wl.uniform_layout((24, 16, 16), (8, 8, 8), bc=(1, 0, 1), ng=2)
+    params = tde.make_params(dual=1)
+    mesh = tde.Mesh(ctx, lay, params)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(wl.random_smooth(lay, seed=6))).to(dev))
+    bh = tde.make_bh(on=1, excise=1, GM=0.2, r_soft=0.05, r_exc=0.15, x0=(0.5, 0.5, 0.5),
+                     v0=(0.3, 0.0, 0.0))
+    tb = torch.linspace(0.0, 0.2, lay.nb, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        want = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
+        mesh.compute_dt(0.4, want, t_block=tb, bh=bh)
+        got = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
+        tde.compute_dt_noalloc(ctx, lay, params, mesh.U, 0.4, got, t_block=tb, bh=bh)
+        torch.cuda.synchronize()
+        assert np.allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-14, atol=0)
+        tb += 0.05
+    big = wl.uniform_layout((8, 8, 4097), (8, 8, 1), bc=(1, 1, 1), ng=2)
+    with pytest.raises(tde.TDEError) as ei:
+        tde.compute_dt_noalloc(ctx, big, params, mesh.U, 0.4, got)
+    assert ei.value.code == tde.TDE_EINVAL and "4096" in str(ei.value)
