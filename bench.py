@@ -249,8 +249,8 @@ def run_gpu(args):
 # DRAM bytes of one launch; profiles/k_sweep_c2_entropy_wave_ncu.md holds the
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
 # False (traffic reported as null) whenever a sweep kernel changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 332.3, "sweep_y": 279.6, "sweep_z": 506.1}
-DRAM_BYTES_SWEEP = {"sweep_x": 267.2e6, "sweep_y": 397.4e6, "sweep_z": 540.4e6}
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 295.5, "sweep_y": 252.2, "sweep_z": 478.2}
+DRAM_BYTES_SWEEP = {"sweep_x": 267.4e6, "sweep_y": 400.1e6, "sweep_z": 542.9e6}
 KERNELS_AS_CAPTURED = True
 
 

@@ -5,7 +5,7 @@
 // Every routine is a per-cell or per-face function in registers; the kernels in
 // tde_hydro.cu stage the data through shared memory and call them.  The FP64
 // pipe is the limiting resource of this path on sm_103a (FP64 FMA issues at
-// 1/64 of the FP32 rate), so the routines avoid divisions where an algebraically
+// about 1/55 of the FP32 rate), so the routines avoid divisions where an algebraically
 // equal form with fewer of them exists, and never branch on the Riemann wave
 // pattern (a warp that diverged would pay for every branch).
 #pragma once
@@ -57,6 +57,20 @@ __device__ __forceinline__ void count(unsigned long long *c) {
   if (c) atomicAdd(c, 1ull);
 }
 
+// 1/d by Newton-Raphson (x <- x (2 - d x), written as two FMAs per step) from
+// the hardware's approximate double reciprocal; two steps take the seed's
+// ~2^-23 relative error below the FP64 rounding, so the result is within about
+// one ulp of 1/d.  For normal d whose reciprocal is normal (every use below:
+// sums of same-signed slopes, wave-speed differences, densities).
+__device__ __forceinline__ double rcp_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // ---------------------------------------------------------------- EOS ----
 
 // Density cell i and weight w of log10 rho (clamped to the table).
@@ -84,7 +98,9 @@ __device__ __forceinline__ double bilin(const double *__restrict__ f, int nt, in
 // (rho, e) -> P, cs2 (cgs) by binary search of the interpolated log10 e column
 // at fixed density weight, then an exact linear solve inside the cell
 // (Sec. 4.2, runtime map).  Returns true if the input was clamped to the table
-// edge; then *e_used is the table's e at the clamped point.
+// edge; then *e_used is the table's e at the clamped point.  WANT_CS2 = false
+// computes P only (cs2, T and e_used are left untouched).
+template <bool WANT_CS2 = true>
 __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e, double &P,
                                            double &cs2, double &e_used, double *T = nullptr) {
   int i;
@@ -116,9 +132,11 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
     s = (y - g0) / (g1 - g0);
   }
   P = exp10(bilin(t.lp, nt, i, w, j, s));
-  cs2 = exp10(bilin(t.lc, nt, i, w, j, s));
-  if (T) *T = exp10(t.lt0 + (j + s) * t.dlt);
-  e_used = cl ? exp10(bilin(t.le, nt, i, w, j, s)) : e;
+  if (WANT_CS2) {
+    cs2 = exp10(bilin(t.lc, nt, i, w, j, s));
+    if (T) *T = exp10(t.lt0 + (j + s) * t.dlt);
+    e_used = cl ? exp10(bilin(t.le, nt, i, w, j, s)) : e;
+  }
   return cl;
 }
 
@@ -139,6 +157,16 @@ __device__ __forceinline__ void eos_closure(const Phys &p, double rho, double U,
     cs2 = c2c * p.inv_unit_e;
     Uu = cl ? rho * (eu * p.inv_unit_e) : U;
   }
+}
+
+// Pressure of internal energy density U at density rho (code units), table EOS
+// (the compression source of Eq. dual-tabulated-compression needs P only).
+__device__ __forceinline__ double table_pressure(const Phys &p, double rho, double U,
+                                                 Counters *cnt) {
+  double Pc, c2c, eu;
+  bool cl = eos_invert<false>(p.tab, rho * p.unit_rho, (U / rho) * p.unit_e, Pc, c2c, eu);
+  if (cl && cnt) count(&cnt->table_clamp);
+  return Pc * p.inv_unit_p;
 }
 
 // Conserved (rho, m, E[, U_aux]) -> primitives w = (rho, vx, vy, vz, P
@@ -174,7 +202,8 @@ __device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, dou
 // PLM, van Leer limiter: half-slope h = dl dr / (dl + dr) if dl dr > 0; faces q -+ h
 __device__ __forceinline__ void plm(double qm, double q0, double qp, double &left, double &right) {
   double dl = q0 - qm, dr = qp - q0;
-  double h = (dl * dr > 0.0) ? dl * dr / (dl + dr) : 0.0;
+  double pr = dl * dr;
+  double h = (pr > 0.0) ? pr * rcp_nr(dl + dr) : 0.0;
   left = q0 - h;
   right = q0 + h;
 }
@@ -223,7 +252,7 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   double SL = fmin(ul - cl, ur - cr);
   double SR = fmax(ul + cl, ur + cr);
   double al = L.r * (SL - ul), ar = R.r * (SR - ur);
-  double SM = (R.P - L.P + al * ul - ar * ur) / (al - ar);
+  double SM = (R.P - L.P + al * ul - ar * ur) * rcp_nr(al - ar);
   bool supL = SL >= 0.0, supR = SR <= 0.0;
   bool useL = supL || (!supR && SM >= 0.0);
   // chosen side K
@@ -234,7 +263,7 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   double den = S - SM;
   if (den == 0.0) den = 1.0;   // only reachable when Seff == 0
   double rS = r * (S - un);
-  double inv = 1.0 / den;
+  double inv = rcp_nr(den);
   double fac = rS * inv;
   double mflux = r * un;
   // U*_K - U_K and F_K in the (normal, t1, t2) frame
@@ -256,7 +285,7 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
     double f = F[0];
     bool up = f > 0.0;
     double ru = up ? L.r : R.r, Au = up ? L.A : R.A;
-    double iru = 1.0 / ru;
+    double iru = rcp_nr(ru);
     F[5] = f != 0.0 ? f * (Au * iru) : 0.0;
     vf = f != 0.0 ? f * iru : 0.0;
   } else {

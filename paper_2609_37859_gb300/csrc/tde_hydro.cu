@@ -222,7 +222,7 @@ template <int D>
 struct SweepGeo {
   static constexpr int LA = D == 0 ? 1 : 0;   // lane axis (transverse, one thread column per lane)
   static constexpr int OA = D == 2 ? 1 : 2;   // other transverse axis (one CTA per index)
-  static constexpr int M = D == 0 ? 8 : 16;   // lanes per tile
+  static constexpr int M = 8;                 // lanes per tile (3 CTAs fit per SM)
 };
 
 template <int D, int RECON, int EOSK, int DUAL, int LAST>
@@ -417,8 +417,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a) {
         if (EOSK == EOS_IDEAL) {
           un[5] = un[5] * exp(-p.gm1 * dv * dtl);
         } else {
-          double Pa, c2a, Uu;
-          eos_closure<EOS_TABLE>(p, un[0], un[5], Pa, c2a, Uu, a.cnt);
+          const double Pa = table_pressure(p, un[0], un[5], a.cnt);
           un[5] = un[5] - Pa * dv * dtl;
         }
         if (un[5] < p.u_floor) { un[5] = p.u_floor; count(&a.cnt->u_floor); }
@@ -695,7 +694,7 @@ size_t sweep_smem_max(const tde_mesh *m) {
   size_t best = 0;
   for (int D = 0; D < 3; ++D) {
     const int PD = m->nmax[D] + 2 * m->phys.g[D], NF = m->nmax[D] + 2;
-    const size_t s = sweep_smem(m->phys, PD, NF, D == 0 ? 8 : 16);
+    const size_t s = sweep_smem(m->phys, PD, NF, 8);
     if (s > best) best = s;
   }
   return best;
@@ -724,7 +723,7 @@ cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double
   a.stage = stage;
   for (int D = 0; D < 3; ++D) {
     if (!p.active[D]) continue;
-    const int M = D == 0 ? 8 : 16;
+    const int M = 8;
     const int LA = D == 0 ? 1 : 0, OA = D == 2 ? 1 : 2;
     a.first = D == firstD;
     a.PD = m->nmax[D] + 2 * p.g[D];
