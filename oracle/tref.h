@@ -147,6 +147,17 @@ void tref_prim_to_cons(const tref_mesh *m, const double *W, double *U);
 /* Softened point-mass potential at position x (Eq. bh-softened-gravity). */
 double tref_phi_bh(const tref_params *p, const double *x, double t);
 
+/* ---- localized adaptive time stepping (oracle/tref_lat.c) ------------------ */
+
+/* Eq. lat-base-dt, Eq. lat-factor, sparse-bin merging and neighbour limiting.
+ * Returns f_max; *dt0 = min_b dt_b. */
+int tref_lat_factors(const tref_mesh *m, const double *dt_b, int n_lat, double merge_frac,
+                     int32_t *f_b, double *dt0);
+/* One LAT window of f_max * dt0 from the synchronised state U at time t (Sec. 7.1).
+ * Returns f_max; *block_updates = MeshBlock RK2 steps taken. */
+int tref_lat_window(const tref_mesh *m, double *U, const int32_t *f_b, double dt0, double t,
+                    tref_counts *c, int64_t *block_updates);
+
 /* ---- learned EOS guess: MLP 2 -> 64 -> 64 -> 2 with SiLU (oracle/tref_mlp.c) */
 
 enum { TREF_MLP_H = 64, TREF_MLP_NPARAM = 2 * 64 + 64 + 64 * 64 + 64 + 64 * 2 + 2 };

@@ -287,6 +287,21 @@ class Mesh:
         lib().tref_step(self.h, P(U), P(S), dt, t, C.byref(c))
         return c
 
+    def lat_factors(self, dt_b, n_lat, merge_frac=0.01):
+        f = np.zeros(self.layout.nb, dtype=np.int32)
+        dt0 = C.c_double()
+        fmax = lib().tref_lat_factors(self.h, P(np.ascontiguousarray(dt_b, dtype=np.float64)), n_lat,
+                                      merge_frac, f.ctypes.data_as(i32p), C.byref(dt0))
+        return f, dt0.value, fmax
+
+    def lat_window(self, U, f_b, dt0, t=0.0, counts=None):
+        c = counts if counts is not None else Counts()
+        upd = C.c_int64()
+        fb = np.ascontiguousarray(f_b, dtype=np.int32)
+        fmax = lib().tref_lat_window(self.h, P(U), fb.ctypes.data_as(i32p), dt0, t, C.byref(c),
+                                     C.byref(upd))
+        return fmax, upd.value
+
     def interior(self, U, var=None):
         """Global-grid array [nvar][Nz][Ny][Nx] of the interior cells."""
         return self.layout.to_global(U if var is None else U[var:var + 1])

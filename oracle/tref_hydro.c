@@ -731,3 +731,35 @@ void tref_prim_to_cons(const tref_mesh *m, const double *W, double *U) {
         }
   }
 }
+
+/* read-only view of the mesh internals for the LAT oracle (tref_lat.c) */
+typedef struct {
+  int nb, N[3], bc[3], ng, active[3], nvar;
+  const int *blocks;
+  const int *pd;
+  const int64_t *off;
+  const int *owner;
+  double dx[3];
+  const tref_params *p;
+  int64_t ntot;
+} tref_mesh_view;
+
+void tref_mesh_get_view(const tref_mesh *m, tref_mesh_view *v) {
+  v->nb = m->d.nb;
+  for (int a = 0; a < 3; ++a) {
+    v->N[a] = m->d.N[a];
+    v->bc[a] = m->d.bc[a];
+    v->active[a] = m->active[a];
+    v->dx[a] = m->d.dx[a];
+  }
+  v->ng = m->d.ng;
+  v->nvar = m->nvar;
+  v->blocks = m->blocks;
+  v->pd = m->pd;
+  v->off = m->off;
+  v->owner = m->owner;
+  v->p = &m->p;
+  v->ntot = m->ntot;
+}
+
+void tref_cell_pos(const tref_mesh *m, int b, int i, int j, int k, double *x) { cell_pos(m, b, i, j, k, x); }
