@@ -208,6 +208,35 @@ TDE_API int tde_mesh_get_time(tde_mesh *mesh, double *t);   /* synchronises the 
  * written to dt_out (device double, may be NULL). */
 TDE_API int tde_step(tde_mesh *mesh, double cfl, double dt_fixed, const tde_bh_state *bh, double *dt_out);
 
+/* ---- localized adaptive time stepping (Sec. 7 of the paper) -------------- */
+
+/* Per-block factors for the next window (Eq. lat-base-dt, Eq. lat-factor): the
+ * CFL step of every block from U at the mesh time (as tde_compute_dt), dt0 =
+ * min, f_b = 2^min(n_lat, floor(log2(dt_b / dt0))), top bins holding fewer than
+ * merge_frac * nblocks blocks merged into the next smaller bin, then factors
+ * lowered until blocks sharing a face, edge or corner differ by at most 2x.
+ * Outputs (host, each may be NULL): factors[nblocks], f_max, dt0.  Synchronises
+ * the stream (the schedule is built on the host).  TDE_ETIMEOUT if the bounded
+ * limiting passes did not converge. */
+TDE_API int tde_lat_assign(tde_mesh *mesh, int n_lat, double merge_frac, double cfl,
+                           const tde_bh_state *bh, int32_t *factors, int *f_max, double *dt0);
+/* Impose factors (host, powers of two) and dt0 instead of tde_lat_assign. */
+TDE_API int tde_lat_set_factors(tde_mesh *mesh, const int32_t *factors, double dt0);
+/* One LAT window of f_max * dt0 from the mesh time (Sec. 7.1): at each fine
+ * sub-step tau the blocks of every factor f dividing tau advance one RK2 step of
+ * f dt0 in one batched launch sequence per level, slow levels first; ghost
+ * cells from a neighbour on another schedule are its frozen state (faster
+ * neighbour) or a linear interpolation in time between its stored endpoint
+ * states (slower neighbour); when a block completes, its faces shared with
+ * faster neighbours take the neighbours' time-integrated fluxes
+ * (Eq. lat-flux-impulse) with the gravitational work correction of
+ * Eq. lat-grav-reflux, then excision and resync run for it.  All factors 1 is
+ * the synchronised step.  use_graph = 1 captures the window's launches in a CUDA
+ * graph on first use and replays it while factors, bh, states and parameters are
+ * unchanged.  *block_updates (host, may be NULL) = MeshBlock steps taken. */
+TDE_API int tde_lat_window(tde_mesh *mesh, const tde_bh_state *bh, int use_graph,
+                           int64_t *block_updates);
+
 /* Copy the cumulative device counters to *out (synchronises the stream) and
  * optionally reset them. */
 TDE_API int tde_counts_read(tde_mesh *mesh, tde_counts *out, int reset);
@@ -259,6 +288,7 @@ enum {
   TDE_K_P2C = 9,      /* primitive -> conserved */
   TDE_K_EOS = 10,     /* batch EOS inversion / evaluation */
   TDE_K_PROBE = 11,   /* peak-rate probe */
+  TDE_K_LATGRAPH = 12, /* replayed LAT window graphs (launches counted per kernel inside) */
   TDE_K_NKIND = 16
 };
 

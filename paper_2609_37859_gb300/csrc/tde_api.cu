@@ -12,11 +12,6 @@
 
 #include "tde_internal.h"
 
-namespace tde {
-size_t sweep_smem_max(const tde_mesh *m);
-cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids);
-}
-
 using namespace tde;
 
 namespace {
@@ -321,12 +316,15 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
 
   // ghost map: every non-interior padded cell <- interior cell of the owner of
   // its periodic image (periodic) or of the nearest boundary cell (outflow)
-  std::vector<int32_t> gmap;
+  std::vector<int32_t> gmap, gsrcb;
   std::vector<int32_t> gstart(nblocks + 1, 0);
+  m->h_nbr_start.assign(nblocks + 1, 0);
+  m->h_nbr.clear();
   for (int b = 0; b < nblocks; ++b) {
     const DevBlock &B = m->hblocks[b];
     const int o[3] = {B.i0, B.j0, B.k0};
     int cnt = 0;
+    std::vector<int32_t> nbrs;
     for (int k = 0; k < B.p[2]; ++k)
       for (int j = 0; j < B.p[1]; ++j)
         for (int i = 0; i < B.p[0]; ++i) {
@@ -353,9 +351,16 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
           int64_t dst = B.off + ((int64_t)k * B.p[1] + j) * B.p[0] + i;
           gmap.push_back((int32_t)dst);
           gmap.push_back((int32_t)src);
+          gsrcb.push_back(ob);
+          bool shell = true;   // neighbours = owners of the first ghost layer (face, edge, corner)
+          for (int a = 0; a < 3; ++a)
+            if (c[a] < p.g[a] - 1 || c[a] > p.g[a] + B.n[a]) shell = false;
+          if (shell && ob != b && std::find(nbrs.begin(), nbrs.end(), ob) == nbrs.end()) nbrs.push_back(ob);
           ++cnt;
         }
     gstart[b + 1] = gstart[b] + cnt;
+    m->h_nbr.insert(m->h_nbr.end(), nbrs.begin(), nbrs.end());
+    m->h_nbr_start[b + 1] = (int32_t)m->h_nbr.size();
     m->max_ghosts = std::max(m->max_ghosts, cnt);
   }
 
@@ -377,6 +382,11 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   A((void **)&m->d_dtb, sizeof(double) * nblocks);
   A((void **)&m->d_dtbits, sizeof(unsigned long long) * nblocks);
   A((void **)&m->d_cnt, sizeof(Counters));
+  A((void **)&m->d_gsrcb, sizeof(int32_t) * gsrcb.size());
+  A((void **)&m->d_nbr_start, sizeof(int32_t) * (nblocks + 1));
+  A((void **)&m->d_nbr, sizeof(int32_t) * m->h_nbr.size());
+  A((void **)&m->d_owner, sizeof(int32_t) * owner.size());
+  A((void **)&m->d_tstart, sizeof(double) * nblocks);
   if (err != cudaSuccess) {
     tde_mesh_destroy(m);
     return cuda_fail(ctx, err, "tde_mesh_create: cudaMalloc");
@@ -393,6 +403,15 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   cudaMemcpy(m->d_allids, allids.data(), sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_scal, zeros, sizeof zeros, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_dtbits, inf_bits.data(), sizeof(unsigned long long) * nblocks, cudaMemcpyHostToDevice);
+  if (!gsrcb.empty()) cudaMemcpy(m->d_gsrcb, gsrcb.data(), sizeof(int32_t) * gsrcb.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(m->d_nbr_start, m->h_nbr_start.data(), sizeof(int32_t) * (nblocks + 1), cudaMemcpyHostToDevice);
+  if (!m->h_nbr.empty()) cudaMemcpy(m->d_nbr, m->h_nbr.data(), sizeof(int32_t) * m->h_nbr.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(m->d_owner, owner.data(), sizeof(int32_t) * owner.size(), cudaMemcpyHostToDevice);
+  cudaMemset(m->d_tstart, 0, sizeof(double) * nblocks);
+  for (int a = 0; a < 3; ++a) {
+    m->unit[a] = unit[a];
+    m->cn[a] = cn[a];
+  }
   cudaMemset(m->d_dU, 0, sizeof(double) * nt * (p.nvar + 1));
   cudaMemset(m->d_W, 0, sizeof(double) * nt * p.nwv);
   err = cudaMemset(m->d_cnt, 0, sizeof(Counters));
@@ -417,6 +436,20 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_dtb);
   cudaFree(m->d_dtbits);
   cudaFree(m->d_cnt);
+  cudaFree(m->d_gsrcb);
+  cudaFree(m->d_nbr_start);
+  cudaFree(m->d_nbr);
+  cudaFree(m->d_owner);
+  cudaFree(m->d_tstart);
+  cudaFree(m->d_f);
+  cudaFree(m->d_f2);
+  cudaFree(m->d_sorted);
+  cudaFree(m->d_Uold);
+  cudaFree(m->d_freg);
+  cudaFree(m->d_fo);
+  cudaFree(m->d_flag);
+  if (m->lat_graph) cudaGraphExecDestroy(m->lat_graph);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
   return TDE_OK;
 }
@@ -444,6 +477,10 @@ extern "C" int tde_mesh_set_params(tde_mesh *m, const tde_params *pr) {
   p.ng = keep.ng;
   p.dxmin = keep.dxmin;
   m->params = *pr;
+  if (m->lat_graph) {   // captured launches hold the old parameters
+    cudaGraphExecDestroy(m->lat_graph);
+    m->lat_graph = nullptr;
+  }
   return TDE_OK;
 }
 

@@ -216,6 +216,9 @@ struct SweepArgs {
   long long ntot;
   Counters *cnt;
   int stage, first, PD, NF;
+  double *freg;              // flux impulse registers (LAT) or null
+  const long long *fo;       // register offset per block
+  int nvar;
 };
 
 template <int D>
@@ -372,6 +375,22 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a) {
 #pragma unroll
     for (int q = 0; q < NVAR; ++q) Fl[sfl(q, f, lane)] = F[q];
     if (DUAL) Fl[sfl(6, f, lane)] = vf;
+    if (a.freg && (f == 0 || f == nd)) {
+      // time integral dt (F^1 + F^2) / 2 of a boundary face (Eq. lat-flux-impulse);
+      // register sides x-, x+, y-, y+, z-, z+, each [nvar][n_OA][n_LA]
+      long long so = a.fo[b];
+      const int side = 2 * D + (f == nd ? 1 : 0);
+      for (int s = 0; s < side; ++s) {
+        const int aa = s >> 1;
+        const int u1 = aa == 0 ? 1 : 0, u2 = aa == 2 ? 1 : 2;
+        so += (long long)B.n[u1] * B.n[u2] * a.nvar;
+      }
+      const long long ncell = (long long)nl * no;
+      const long long cidx = (long long)o * nl + l0 + lane;
+      const double w = 0.5 * ta_dt(a.ta, b);
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) a.freg[so + q * ncell + cidx] += w * F[q];
+    }
   }
   __syncthreads();
 
@@ -701,7 +720,8 @@ size_t sweep_smem_max(const tde_mesh *m) {
 }
 
 cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double *Uin,
-                          double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta) {
+                          double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta,
+                          double *freg) {
   const Phys &p = m->phys;
   int lastD = -1, firstD = -1;
   for (int D = 0; D < 3; ++D)
@@ -721,6 +741,9 @@ cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double
   a.ntot = (long long)m->ntot;
   a.cnt = m->d_cnt;
   a.stage = stage;
+  a.freg = freg;
+  a.fo = m->d_fo;
+  a.nvar = p.nvar;
   for (int D = 0; D < 3; ++D) {
     if (!p.active[D]) continue;
     const int M = 8;

@@ -87,6 +87,32 @@ struct tde_mesh {
   unsigned long long *d_dtbits = nullptr;  // per-block CFL minima (bit patterns) [nb]
   tde::Counters *d_cnt = nullptr;
   double *U = nullptr, *U1 = nullptr;  // caller-owned states
+  // neighbour lists (blocks supplying ghost cells) and the owner lattice
+  std::vector<int32_t> h_nbr_start, h_nbr;
+  int32_t *d_nbr_start = nullptr, *d_nbr = nullptr;
+  int32_t *d_gsrcb = nullptr;          // source block of each ghost entry
+  int unit[3] = {1, 1, 1}, cn[3] = {1, 1, 1};
+  int32_t *d_owner = nullptr;          // owner block per unit-lattice cell
+  // localized adaptive time stepping
+  bool lat_ready = false;
+  int lat_fmax = 1;
+  double lat_dt0 = 0.0;
+  std::vector<int32_t> h_f;            // factor per block
+  std::vector<int32_t> h_sorted;       // block ids by ascending factor
+  std::vector<int> h_levels;           // distinct factors, ascending
+  std::vector<int> h_level_start;      // segment of each level in h_sorted
+  int32_t *d_f = nullptr, *d_f2 = nullptr, *d_sorted = nullptr;
+  double *d_Uold = nullptr;            // start-of-step states (LAT)
+  double *d_freg = nullptr;            // flux impulse registers
+  long long *d_fo = nullptr;           // register offset per block
+  long long freg_size = 0;
+  double *d_tstart = nullptr;          // per-block step start time
+  int *d_flag = nullptr;               // device status word of the factor kernel
+  cudaGraphExec_t lat_graph = nullptr;
+  tde::BH lat_graph_bh{};
+  const double *lat_graph_U = nullptr, *lat_graph_U1 = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  uint64_t lat_graph_launches = 0;
 };
 
 namespace tde {
@@ -104,7 +130,10 @@ cudaError_t launch_c2p(tde_mesh *m, const double *Uin, int nblk, const int32_t *
 cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double *dt_min);
 cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids);
 cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double *Uin,
-                          double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta);
+                          double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta,
+                          double *freg = nullptr);
+cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids);
+size_t sweep_smem_max(const tde_mesh *m);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);
 cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2);

@@ -96,12 +96,16 @@ _SIGS = {
     "tde_profile": [vp, C.c_int],
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
+    "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
+                       C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "tde_lat_set_factors": [vp, C.POINTER(C.c_int32), C.c_double],
+    "tde_lat_window": [vp, C.POINTER(BHState), C.c_int, C.POINTER(C.c_int64)],
     "tde_compute_dt_noalloc": [vp, C.c_int, C.POINTER(BlockDesc), C.POINTER(GridDesc),
                                C.POINTER(Params), C.POINTER(TableView), dp, C.c_double, dp,
                                C.POINTER(BHState), dp, dp],
 }
 KERNEL_KINDS = ("c2p", "dt", "ghost", "sweep_x", "sweep_y", "sweep_z", "sync", "excise", "scalar",
-                "p2c", "eos", "probe")
+                "p2c", "eos", "probe", "lat_graph")
 NKIND = 16
 
 _lib = None
@@ -306,6 +310,24 @@ class Mesh:
     def step(self, cfl=0.0, dt=0.0, bh=None, dt_out=None):
         self.ctx.check(lib().tde_step(self.h, cfl, dt, C.byref(bh) if bh is not None else None,
                                       _ptr(dt_out)))
+
+    def lat_assign(self, n_lat, cfl, merge_frac=0.01, bh=None):
+        f = (C.c_int32 * self.layout.nb)()
+        fmax, dt0 = C.c_int(), C.c_double()
+        self.ctx.check(lib().tde_lat_assign(self.h, n_lat, merge_frac, cfl,
+                                            C.byref(bh) if bh is not None else None, f,
+                                            C.byref(fmax), C.byref(dt0)))
+        return np.array(f[:], dtype=np.int32), dt0.value, fmax.value
+
+    def lat_set_factors(self, factors, dt0):
+        f = np.ascontiguousarray(factors, dtype=np.int32)
+        self.ctx.check(lib().tde_lat_set_factors(self.h, f.ctypes.data_as(C.POINTER(C.c_int32)), dt0))
+
+    def lat_window(self, bh=None, use_graph=False):
+        upd = C.c_int64()
+        self.ctx.check(lib().tde_lat_window(self.h, C.byref(bh) if bh is not None else None,
+                                            1 if use_graph else 0, C.byref(upd)))
+        return upd.value
 
     def counts(self, reset=False):
         c = Counts()
