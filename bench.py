@@ -236,6 +236,8 @@ def run_gpu(args):
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "counters": counts,
         }
+        if not args.no_eos:
+            line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -252,6 +254,56 @@ def run_gpu(args):
 FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 295.5, "sweep_y": 252.2, "sweep_z": 478.2}
 DRAM_BYTES_SWEEP = {"sweep_x": 267.4e6, "sweep_y": 400.1e6, "sweep_z": 542.9e6}
 KERNELS_AS_CAPTURED = True
+
+
+# ------------------------------------------------------- EOS inversion (C3) ---
+
+EOS_CELLS = 1 << 24
+EOS_BAND = (3.4, 5.4)   # log10 T band of H and He recombination across the density range
+
+
+def eos_bench(ctx, eos, tde, torch, dev, args):
+    """2^24 (rho, e) cells -> (T, P, cs2): table bisection against the learned guess
+    plus one Newton step (identical results, checked), after training the network
+    on the device (2^20 table samples)."""
+    rep = eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED)
+    lr = torch.rand(EOS_CELLS, generator=g, device=dev, dtype=torch.float64) * 16.0 - 14.0
+    lT = torch.rand(EOS_CELLS, generator=g, device=dev, dtype=torch.float64) * (EOS_BAND[1] - EOS_BAND[0]) + EOS_BAND[0]
+    rho = torch.pow(10.0, lr)
+    T0 = torch.pow(10.0, lT)
+    del lr, lT
+    e = torch.empty_like(rho)
+    eos.eval_rhoT(rho, T0, e=e)
+    del T0
+    res = {}
+    outs = {}
+    for name, mode in (("bisect", tde.INVERT_BISECT), ("surrogate", tde.INVERT_SURROGATE)):
+        T, P, c2 = (torch.empty_like(rho) for _ in range(3))
+        for _ in range(2):
+            eos.invert(rho, e, T=T, P=P, cs2=c2, mode=mode)
+        before = eos.counts()["surrogate_accepted"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(reps):
+            eos.invert(rho, e, T=T, P=P, cs2=c2, mode=mode)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        acc = (eos.counts()["surrogate_accepted"] - before) / (reps * EOS_CELLS)
+        res[name] = {"cells_per_s": EOS_CELLS / (ms * 1e-3), "ms": ms, "accepted": acc,
+                     "hbm_gbs": EOS_CELLS * 40 / (ms * 1e-3) * 1e-9}
+        outs[name] = (T, P, c2)
+    same = all(torch.equal(a, b) for a, b in zip(outs["bisect"], outs["surrogate"]))
+    return {"workload": "2^24 cells, log10 rho U[-14, 2], log10 T U[%.1f, %.1f] mapped to e by the "
+                        "table; outputs T, P, cs2 (40 B/cell)" % EOS_BAND,
+            "bisect": res["bisect"], "surrogate_newton": res["surrogate"],
+            "speedup": res["bisect"]["ms"] / res["surrogate"]["ms"], "identical_results": bool(same),
+            "training": {"samples": rep["samples"], "epochs": rep["epochs"], "ms": rep["ms"],
+                         "loss_first": rep["loss_first"], "loss_last": rep["loss_last"]}}
 
 
 # ------------------------------------------------------------------ oracle ---
@@ -336,6 +388,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-eos", action="store_true", help="skip the EOS-inversion comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -98,6 +98,7 @@ typedef struct {
 /* Device-side event counters (cumulative until reset). */
 typedef struct {
   uint64_t rho_floor, p_floor, u_floor, table_clamp, excised, dual_aux_used, synced, nonfinite;
+  uint64_t surrogate_accepted;   /* table inversions settled by the learned guess's Newton step */
 } tde_counts;
 
 /* ---- context ----------------------------------------------------------- */
@@ -132,6 +133,51 @@ TDE_API int tde_eos_destroy(tde_eos *eos);
  * counted (counts may be NULL; reading it synchronises the stream). */
 TDE_API int tde_eos_invert(tde_eos *eos, int mode, int64_t n, const double *rho, const double *e,
                    double *T, double *P, double *cs2, tde_counts *counts);
+/* ---- learned EOS guess (a project addition; the paper has none) -------------
+ * A 2 -> 64 -> 64 -> 2 SiLU network maps normalised (log10 rho, z) to
+ * normalised (log10 T, log10 P), where z = (log10 e - g_lo) / (g_hi - g_lo) is
+ * the position of log10 e inside the table's interpolated log10 e column at
+ * that density (0 at T_min, 1 at T_max); normalisation x_n = (x - c) / s with
+ * c, s the centre and half-width of the log10 rho, z (0.5, 0.5), log10 T and
+ * log10 P ranges (tde_eos_surrogate_norm).  Parameters, 4482 floats:
+ *   W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+ * TDE_INVERT_SURROGATE uses the network (BF16 weights; the 64 x 64 layer on the
+ * tensor cores, FP32 accumulation) to pick the temperature cell, takes one FP64
+ * Newton step on the interpolated log10 e column there and accepts it iff the
+ * root lies in that cell -- then the result equals bisection's exactly -- and
+ * falls back to bisection otherwise.  The results of both modes are identical;
+ * only the work differs. */
+typedef struct {
+  double loss_first, loss_last;   /* mean-squared error of the first and last batch */
+  int epochs, samples, batches;
+  double ms;                      /* device time of the training */
+} tde_train_report;
+
+/* Draw n_samples points (log10 rho, log10 T) uniformly over the table with a
+ * counter-based generator seeded by seed, map them through the table to inputs
+ * (log10 rho, log10 e) and targets (log10 T, log10 P), and train with Adam
+ * (learning rate lr with cosine decay, batch size batch) for the given epochs,
+ * from a seeded initialisation if the network has no weights yet.  rep may be
+ * NULL.  Synchronises the stream. */
+TDE_API int tde_eos_surrogate_train(tde_eos *eos, uint64_t seed, int n_samples, int epochs, int batch,
+                                    double lr, tde_train_report *rep);
+/* Forget the weights: the next tde_eos_surrogate_train starts from its seeded
+ * initialisation. */
+TDE_API int tde_eos_surrogate_reset(tde_eos *eos);
+/* FP32 master weights in / out (host, n = 4482). */
+TDE_API int tde_eos_surrogate_set_weights(tde_eos *eos, const float *w, size_t n);
+TDE_API int tde_eos_surrogate_get_weights(tde_eos *eos, float *w, size_t n);
+/* Loss L = (1/n) sum (y - target)^2 and its gradient (device: x, target [n][2],
+ * grad [4482], loss [1]) with the BF16-rounded weights, FP32 arithmetic: the
+ * training kernels' own forward and backward pass. */
+TDE_API int tde_eos_surrogate_grad(tde_eos *eos, int64_t n, const float *x, const float *target,
+                                   float *grad, float *loss);
+/* Network outputs y [n][2] for inputs x [n][2] (device, normalised) through the
+ * tensor-core inference kernel. */
+TDE_API int tde_eos_surrogate_forward(tde_eos *eos, int64_t n, const float *x, float *y);
+/* The eight normalisation constants (c, s for log10 rho, e, T, P), host. */
+TDE_API int tde_eos_surrogate_norm(const tde_eos *eos, double *out8);
+
 /* Forward evaluation at (rho, T), cgs, device arrays; outputs may be NULL. */
 TDE_API int tde_eos_eval_rhoT(tde_eos *eos, int64_t n, const double *rho, const double *T, double *P,
                       double *e, double *cs2);

@@ -97,6 +97,12 @@ void tref_eos_eval_rhoT(const tref_table *t, double rho, double T, double *P, do
 /* Inversion (rho, e) -> (T, P, cs2), cgs.  Returns 1 if clamped to the table edge. */
 int tref_eos_invert(const tref_table *t, double rho, double e, double *T, double *P, double *cs2,
                     double *e_used);
+/* Inversion from a guessed log10 T: one Newton step in the guessed cell of the
+ * interpolated log10 e column, accepted iff the root lies in that cell (then the
+ * result equals tref_eos_invert's exactly), else tref_eos_invert.  Returns 1 if
+ * accepted. */
+int tref_eos_invert_guess(const tref_table *t, double rho, double e, double log10_T_guess,
+                          double *T, double *P, double *cs2);
 /* Inversion (rho, P) -> T on the pressure column (initial data only). */
 double tref_eos_T_from_P(const tref_table *t, double rho, double P);
 

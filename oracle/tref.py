@@ -92,6 +92,8 @@ def lib():
             "tref_eos_eval_rhoT": (None, [C.POINTER(Table), C.c_double, C.c_double, dp, dp, dp]),
             "tref_eos_invert": (C.c_int, [C.POINTER(Table), C.c_double, C.c_double, dp, dp, dp, dp]),
             "tref_eos_T_from_P": (C.c_double, [C.POINTER(Table), C.c_double, C.c_double]),
+            "tref_eos_invert_guess": (C.c_int, [C.POINTER(Table), C.c_double, C.c_double, C.c_double,
+                                                dp, dp, dp]),
             "tref_mesh_new": (C.c_void_p, [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(Table)]),
             "tref_mesh_free": (None, [C.c_void_p]),
             "tref_mesh_ntot": (C.c_int64, [C.c_void_p]),
@@ -173,6 +175,12 @@ class EOSTable:
         Pr, e, c2 = C.c_double(), C.c_double(), C.c_double()
         lib().tref_eos_eval_rhoT(C.byref(self.c), rho, T, C.byref(Pr), C.byref(e), C.byref(c2))
         return Pr.value, e.value, c2.value
+
+    def invert_guess(self, rho, e, log10_T_guess):
+        T, Pr, c2 = C.c_double(), C.c_double(), C.c_double()
+        acc = lib().tref_eos_invert_guess(C.byref(self.c), rho, e, log10_T_guess, C.byref(T),
+                                          C.byref(Pr), C.byref(c2))
+        return T.value, Pr.value, c2.value, bool(acc)
 
     def T_from_P(self, rho, Pr):
         return lib().tref_eos_T_from_P(C.byref(self.c), rho, Pr)

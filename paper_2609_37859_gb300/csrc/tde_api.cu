@@ -156,6 +156,22 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
     delete e;
     return cuda_fail(ctx, err, "tde_eos_load_table: cudaMemcpy");
   }
+  {   // normalisation of the learned guess: centre and half-width of each range
+    double emin = log10_e[0], emax = log10_e[0], pmin = log10_P[0], pmax = log10_P[0];
+    for (size_t k = 0; k < nn; ++k) {
+      emin = std::min(emin, log10_e[k]);
+      emax = std::max(emax, log10_e[k]);
+      pmin = std::min(pmin, log10_P[k]);
+      pmax = std::max(pmax, log10_P[k]);
+    }
+    // second network input: z = position of log10 e in its interpolated column, in [0, 1]
+    const double nv[8] = {0.5 * (lr_min + lr_max), 0.5 * (lr_max - lr_min), 0.5, 0.5,
+                          0.5 * (lT_min + lT_max), 0.5 * (lT_max - lT_min),
+                          0.5 * (pmin + pmax),     0.5 * (pmax - pmin)};
+    (void)emin;
+    (void)emax;
+    memcpy(e->norm, nv, sizeof nv);
+  }
   DTable &t = e->tab;
   t.nr = n_rho;
   t.nt = n_T;
@@ -174,6 +190,9 @@ extern "C" int tde_eos_destroy(tde_eos *e) {
   if (!e) return TDE_EINVAL;
   cudaFree(e->d_data);
   cudaFree(e->d_cnt);
+  cudaFree(e->d_w);
+  cudaFree(e->d_wb);
+  cudaFree(e->d_status);
   delete e;
   return TDE_OK;
 }
@@ -183,8 +202,14 @@ extern "C" int tde_eos_invert(tde_eos *e, int mode, int64_t n, const double *rho
   if (!e) return TDE_EINVAL;
   tde_ctx *c = e->ctx;
   if (n < 0 || (n > 0 && (!rho || !en))) return fail(c, TDE_EINVAL, "tde_eos_invert: arguments");
-  if (mode != TDE_INVERT_BISECT) return fail(c, TDE_EINVAL, "tde_eos_invert: unknown mode");
-  CK(c, launch_eos_invert(e, n, rho, en, T, P, cs2, c->stream));
+  if (mode == TDE_INVERT_BISECT) {
+    CK(c, launch_eos_invert(e, n, rho, en, T, P, cs2, c->stream));
+  } else if (mode == TDE_INVERT_SURROGATE) {
+    if (!e->has_net) return fail(c, TDE_EINVAL, "tde_eos_invert: no trained surrogate");
+    CK(c, launch_eos_surrogate(e, n, rho, en, T, P, cs2, c->stream));
+  } else {
+    return fail(c, TDE_EINVAL, "tde_eos_invert: unknown mode");
+  }
   if (counts) {
     Counters h;
     CK(c, cudaMemcpyAsync(&h, e->d_cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream));

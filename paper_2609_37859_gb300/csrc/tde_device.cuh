@@ -28,7 +28,7 @@ struct DTable {
 
 struct Counters {
   unsigned long long rho_floor, p_floor, u_floor, table_clamp, excised, dual_aux_used, synced,
-      nonfinite;
+      nonfinite, surrogate_accepted;
 };
 
 // Scheme, physics and geometry constants, passed by value to every kernel.

@@ -61,6 +61,13 @@ struct tde_eos {
   tde::DTable tab{};
   double *d_data = nullptr;          // 3 * n_rho * n_T doubles
   tde::Counters *d_cnt = nullptr;
+  // learned guess (tde_mlp.cu): normalisation of inputs and outputs
+  // (c_rho, s_rho, c_e, s_e, c_T, s_T, c_P, s_P; x_norm = (x - c) / s)
+  double norm[8] = {0, 1, 0, 1, 0, 1, 0, 1};
+  bool has_net = false;
+  float *d_w = nullptr;              // FP32 master weights, then Adam m, v and the gradient
+  void *d_wb = nullptr;              // BF16 weights used by training forward and inference
+  int *d_status = nullptr;
 };
 
 struct tde_mesh {
@@ -142,6 +149,8 @@ cudaError_t launch_advance_time(tde_mesh *m);
 cudaError_t launch_set_dt(tde_mesh *m, double dt);
 cudaError_t launch_eos_invert(tde_eos *e, int64_t n, const double *rho, const double *en,
                               double *T, double *P, double *cs2, cudaStream_t s);
+cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const double *en,
+                                 double *T, double *P, double *cs2, cudaStream_t s);
 cudaError_t launch_eos_eval(tde_eos *e, int64_t n, const double *rho, const double *T, double *P,
                             double *en, double *cs2, cudaStream_t s);
 

@@ -1,0 +1,676 @@
+// tde_mlp.cu -- the learned EOS guess: a 2 -> 64 -> 64 -> 2 SiLU network that maps
+// normalised (log10 rho, log10 e) to normalised (log10 T, log10 P).  The paper
+// has no learned component; the network only chooses the temperature cell in
+// which one FP64 Newton step on the interpolated log10 e column is taken, and
+// table bisection stays both the fallback and the judge (Sec. 4.2 runtime map).
+//
+//  * Training: FP32 forward/backward kernels on BF16-rounded weights (the
+//    weights inference uses), gradients reduced per CTA in shared memory, then
+//    Adam on FP32 master weights.  Samples are drawn on the device from the
+//    table itself with a counter-based generator (SplitMix64).
+//  * Inference: per CTA tile of 128 cells, layer 1 and the SiLU in FP32 CUDA
+//    cores, the 64 x 64 layer on the 5th-generation tensor cores
+//    (tcgen05.mma kind::f16, BF16 operands from shared memory, FP32 accumulator
+//    in tensor memory, read back with tcgen05.ld), layer 3 in FP32, then the
+//    FP64 Newton step with the bisection fallback.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "tde_internal.h"
+
+namespace tde {
+
+constexpr int H = 64;
+constexpr int NPARAM = 2 * H + H + H * H + H + 2 * H + 2;   // 4482
+// parameter offsets (same layout as the oracle's)
+constexpr int OW1 = 0, OB1 = 2 * H, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H, OB3 = OW3 + 2 * H;
+
+struct MLPNorm {
+  float cr, sr, ce, se, cT, sT, cP, sP;   // x_norm = (x - c) / s
+};
+
+__device__ __forceinline__ float silu_f(float a) { return a / (1.0f + __expf(-a)); }
+__device__ __forceinline__ float dsilu_f(float a) {
+  const float s = 1.0f / (1.0f + __expf(-a));
+  return s * (1.0f + a * (1.0f - s));
+}
+
+// ---------------------------------------------------------------- SplitMix64
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double u01(unsigned long long seed, unsigned long long ctr) {
+  return (double)(splitmix64(seed ^ splitmix64(ctr)) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// training samples: (log rho, log T) uniform over the table -> inputs
+// (log rho, log e) and targets (log T, log P), normalised
+__global__ void k_mlp_samples(DTable t, MLPNorm nm, long long n, unsigned long long seed, float *x,
+                              float *y) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+       s += (long long)gridDim.x * blockDim.x) {
+    const double a = u01(seed, 2 * s), c = u01(seed, 2 * s + 1);
+    const double xr = a * (t.nr - 1), yt = c * (t.nt - 1);
+    int i = (int)floor(xr), j = (int)floor(yt);
+    if (i > t.nr - 2) i = t.nr - 2;
+    if (j > t.nt - 2) j = t.nt - 2;
+    const double w = xr - i, u = yt - j;
+    const double lr = t.lr0 + xr / t.inv_dlr;
+    const double lT = t.lt0 + yt * t.dlt;
+    const double le = bilin(t.le, t.nt, i, w, j, u);
+    const double lp = bilin(t.lp, t.nt, i, w, j, u);
+    // second input: position of log10 e inside the interpolated column at this density
+    const double glo = (1.0 - w) * t.le[(size_t)i * t.nt] + w * t.le[(size_t)(i + 1) * t.nt];
+    const double ghi = (1.0 - w) * t.le[(size_t)i * t.nt + t.nt - 1] + w * t.le[(size_t)(i + 1) * t.nt + t.nt - 1];
+    x[2 * s] = (float)((lr - nm.cr) / nm.sr);
+    x[2 * s + 1] = (float)(((le - glo) / (ghi - glo) - nm.ce) / nm.se);
+    y[2 * s] = (float)((lT - nm.cT) / nm.sT);
+    y[2 * s + 1] = (float)((lp - nm.cP) / nm.sP);
+  }
+}
+
+// ------------------------------------------------------------------ training
+
+constexpr int GT = 128;   // samples (threads) per CTA in the gradient kernel
+
+// loss and gradient of L = (1/n) sum_s sum_o (y - target)^2 over samples
+// [s0, s0 + count) with the BF16-rounded weights wb; gradient and loss are
+// accumulated into g (NPARAM floats) and *loss.
+__global__ void __launch_bounds__(GT) k_mlp_grad(const __nv_bfloat16 *__restrict__ wb,
+                                                 const float *__restrict__ x,
+                                                 const float *__restrict__ tg, long long s0,
+                                                 long long count, float inv_n, float *g,
+                                                 float *loss) {
+  extern __shared__ float sh[];
+  float *sw = sh;                       // NPARAM weights (as float)
+  float *sh1 = sw + NPARAM;             // [GT][H + 1]
+  float *sga2 = sh1 + GT * (H + 1);     // [GT][H + 1]
+  float *sh2 = sga2 + GT * (H + 1);     // [GT][H + 1]
+  float *sga1 = sh2 + GT * (H + 1);     // [GT][H + 1]
+  float *sx = sga1 + GT * (H + 1);      // [GT][2]
+  float *sgy = sx + 2 * GT;             // [GT][2]
+  const int tid = threadIdx.x;
+  for (int q = tid; q < NPARAM; q += GT) sw[q] = __bfloat162float(wb[q]);
+  __syncthreads();
+  const long long s = s0 + blockIdx.x * (long long)GT + tid;
+  const bool live = s < s0 + count;
+  float *ra1 = sga1 + tid * (H + 1), *ra2 = sga2 + tid * (H + 1);   // pre-activations, then grads
+  float *rh1 = sh1 + tid * (H + 1), *rh2 = sh2 + tid * (H + 1);
+  float xi0 = 0.f, xi1 = 0.f, t0 = 0.f, t1 = 0.f;
+  if (live) {
+    xi0 = x[2 * s]; xi1 = x[2 * s + 1];
+    t0 = tg[2 * s]; t1 = tg[2 * s + 1];
+  }
+  for (int o = 0; o < H; ++o) {
+    const float a1 = sw[OW1 + 2 * o] * xi0 + sw[OW1 + 2 * o + 1] * xi1 + sw[OB1 + o];
+    ra1[o] = a1;
+    rh1[o] = silu_f(a1);
+  }
+  for (int o = 0; o < H; ++o) {
+    float acc = sw[OB2 + o];
+#pragma unroll 16
+    for (int i = 0; i < H; ++i) acc += sw[OW2 + o * H + i] * rh1[i];
+    ra2[o] = acc;
+    rh2[o] = silu_f(acc);
+  }
+  float y0 = sw[OB3], y1 = sw[OB3 + 1];
+  for (int i = 0; i < H; ++i) {
+    const float h = rh2[i];
+    y0 += sw[OW3 + i] * h;
+    y1 += sw[OW3 + H + i] * h;
+  }
+  const float r0 = live ? y0 - t0 : 0.f, r1 = live ? y1 - t1 : 0.f;
+  const float gy0 = 2.f * r0 * inv_n, gy1 = 2.f * r1 * inv_n;
+  sx[2 * tid] = xi0;
+  sx[2 * tid + 1] = xi1;
+  sgy[2 * tid] = gy0;
+  sgy[2 * tid + 1] = gy1;
+  float gh1[H];
+#pragma unroll
+  for (int i = 0; i < H; ++i) gh1[i] = 0.f;
+  for (int o = 0; o < H; ++o) {
+    const float gh2 = sw[OW3 + o] * gy0 + sw[OW3 + H + o] * gy1;
+    const float ga2 = gh2 * dsilu_f(ra2[o]);
+    ra2[o] = ga2;
+#pragma unroll
+    for (int i = 0; i < H; ++i) gh1[i] += sw[OW2 + o * H + i] * ga2;
+  }
+#pragma unroll
+  for (int o = 0; o < H; ++o) ra1[o] = gh1[o] * dsilu_f(ra1[o]);
+  // per-CTA loss
+  float l = r0 * r0 + r1 * r1;
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((tid & 31) == 0) atomicAdd(loss, l * inv_n);
+  __syncthreads();
+  // reductions over the CTA's samples
+  for (int q = tid; q < H * H; q += GT) {   // dW2[o][i] = sum_s ga2[s][o] h1[s][i]
+    const int o = q / H, i = q % H;
+    float acc = 0.f;
+    for (int k = 0; k < GT; ++k) acc += sga2[k * (H + 1) + o] * sh1[k * (H + 1) + i];
+    atomicAdd(g + OW2 + q, acc);
+  }
+  if (tid < H) {
+    const int o = tid;
+    float d1 = 0.f, w0 = 0.f, w1 = 0.f, d2 = 0.f, v0 = 0.f, v1 = 0.f;
+    for (int k = 0; k < GT; ++k) {
+      const float ga1 = sga1[k * (H + 1) + o];
+      d1 += ga1;
+      w0 += ga1 * sx[2 * k];
+      w1 += ga1 * sx[2 * k + 1];
+      d2 += sga2[k * (H + 1) + o];
+      const float h2 = sh2[k * (H + 1) + o];
+      v0 += sgy[2 * k] * h2;
+      v1 += sgy[2 * k + 1] * h2;
+    }
+    atomicAdd(g + OB1 + o, d1);
+    atomicAdd(g + OW1 + 2 * o, w0);
+    atomicAdd(g + OW1 + 2 * o + 1, w1);
+    atomicAdd(g + OB2 + o, d2);
+    atomicAdd(g + OW3 + o, v0);
+    atomicAdd(g + OW3 + H + o, v1);
+  }
+  if (tid == H) {
+    float b0 = 0.f, b1 = 0.f;
+    for (int k = 0; k < GT; ++k) { b0 += sgy[2 * k]; b1 += sgy[2 * k + 1]; }
+    atomicAdd(g + OB3, b0);
+    atomicAdd(g + OB3 + 1, b1);
+  }
+}
+
+__global__ void k_adam(float *w, float *m, float *v, float *g, __nv_bfloat16 *wb, int n, float lr,
+                       float b1, float b2, float eps, float bc1, float bc2) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const float gq = g[q];
+    const float mq = b1 * m[q] + (1.f - b1) * gq;
+    const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    const float wq = w[q] - lr * (mq / bc1) / (sqrtf(vq / bc2) + eps);
+    w[q] = wq;
+    wb[q] = __float2bfloat16_rn(wq);
+    g[q] = 0.f;
+  }
+}
+
+__global__ void k_round_bf16(const float *w, __nv_bfloat16 *wb, int n) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+    wb[q] = __float2bfloat16_rn(w[q]);
+}
+
+// ---------------------------------------------------------------- inference
+
+// tcgen05 shared-memory matrix descriptor: K-major, no swizzle ("interleaved"
+// core matrices of 8 rows x 16 bytes), leading-dimension byte offset = distance
+// between core matrices along K, stride byte offset = distance between 8-row
+// groups, descriptor version 1 (bits 46-47).
+__device__ __forceinline__ unsigned long long smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | ((unsigned long long)(lbo >> 4) << 16) |
+         ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28
+constexpr uint32_t IDESC_BF16_M128_N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+                                         ((128u >> 4) << 24);
+
+// byte offset of element (row r, k) of a [rows][64] BF16 tile in the core-matrix layout
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+constexpr int IT = 128;   // cells per tile = threads per CTA
+
+struct SurrogateArgs {
+  DTable t;
+  MLPNorm nm;
+  const __nv_bfloat16 *wb;
+  long long n;
+  const double *rho, *e;
+  double *T, *P, *cs2;
+  float *yout;        // optional: raw network outputs [n][2] (normalised)
+  const float *xin;   // optional: network inputs instead of (rho, e) [n][2]
+  Counters *cnt;
+  int *status;        // set to 1 if a bounded wait expired
+};
+
+__global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
+  __shared__ __align__(1024) unsigned char sA[IT * H * 2];   // h1, BF16, core-matrix layout
+  __shared__ __align__(1024) unsigned char sB[H * H * 2];    // W2, BF16, core-matrix layout
+  __shared__ float sW1[2 * H], sb1[H], sb2[H], sW3[2 * H], sb3[2];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sA_addr = (uint32_t)__cvta_generic_to_shared(sA);
+  const uint32_t sB_addr = (uint32_t)__cvta_generic_to_shared(sB);
+  const uint32_t mbar_addr = (uint32_t)__cvta_generic_to_shared(&mbar);
+  if (warp == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int q = tid; q < H * H; q += IT) {
+    const int o = q / H, i = q % H;
+    *reinterpret_cast<__nv_bfloat16 *>(sB + core_off(o, i)) = a.wb[OW2 + q];
+  }
+  for (int q = tid; q < 2 * H; q += IT) {
+    sW1[q] = __bfloat162float(a.wb[OW1 + q]);
+    sW3[q] = __bfloat162float(a.wb[OW3 + q]);
+  }
+  if (tid < H) {
+    sb1[tid] = __bfloat162float(a.wb[OB1 + tid]);
+    sb2[tid] = __bfloat162float(a.wb[OB2 + tid]);
+  }
+  if (tid < 2) sb3[tid] = __bfloat162float(a.wb[OB3 + tid]);
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_addr), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tbase = tmem_base;
+  uint32_t phase = 0;
+  const long long ntiles = (a.n + IT - 1) / IT;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long c = tile * IT + tid;
+    const bool live = c < a.n;
+    // ---- inputs and layer 1 (FP32)
+    double ly = 0.0, rho = 1.0, en = 1.0, w = 0.0, glo = 0.0, ghi = 1.0;
+    int ti = 0;
+    bool cl = true;
+    float x0 = 0.f, x1 = 0.f;
+    if (live) {
+      if (a.xin) {
+        x0 = a.xin[2 * c];
+        x1 = a.xin[2 * c + 1];
+      } else {
+        const DTable &t = a.t;
+        rho = a.rho[c];
+        en = a.e[c];
+        cl = rho_cell(t, rho, ti, w);
+        const double *__restrict__ ra = t.le + (size_t)ti * t.nt;
+        const double *__restrict__ rb = ra + t.nt;
+        glo = (1.0 - w) * __ldg(ra) + w * __ldg(rb);
+        ghi = (1.0 - w) * __ldg(ra + t.nt - 1) + w * __ldg(rb + t.nt - 1);
+        ly = en > 0.0 ? log10(en) : -INFINITY;
+        const double lr = t.lr0 + (ti + w) / t.inv_dlr;
+        x0 = (float)((lr - a.nm.cr) / a.nm.sr);
+        const double z = en > 0.0 ? (ly - glo) / (ghi - glo) : 0.0;
+        x1 = (float)((fmin(fmax(z, -1.0), 2.0) - a.nm.ce) / a.nm.se);
+      }
+    }
+#pragma unroll
+    for (int k8 = 0; k8 < H / 8; ++k8) {
+      __align__(16) __nv_bfloat16 hv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int o = 8 * k8 + u;
+        hv[u] = __float2bfloat16_rn(silu_f(sW1[2 * o] * x0 + sW1[2 * o + 1] * x1 + sb1[o]));
+      }
+      *reinterpret_cast<uint4 *>(sA + core_off(tid, 8 * k8)) = *reinterpret_cast<uint4 *>(hv);
+    }
+    // make the generic-proxy shared stores visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    // ---- layer 2 on the tensor core: D[128 x 64] = h1[128 x 64] * W2^T
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int ks = 0; ks < H / 16; ++ks) {
+        const unsigned long long ad = smem_desc(sA_addr + ks * 256, 128, 1024);
+        const unsigned long long bd = smem_desc(sB_addr + ks * 256, 128, 1024);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tbase),
+            "l"(ad), "l"(bd), "r"(IDESC_BF16_M128_N64), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          mbar_addr));
+    }
+    // bounded wait for the MMAs (about 1 s of polling at most)
+    {
+      uint32_t done = 0;
+      for (long long it = 0; it < (1ll << 22) && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar_addr), "r"(phase));
+      }
+      if (!done) s_abort = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    if (s_abort) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // ---- read the accumulator row of this thread (warp w owns TMEM lanes 32w..32w+31)
+    uint32_t r[64];
+    const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+        "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63},"
+        " [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+          "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    // ---- layer 3 (FP32)
+    float y0 = sb3[0], y1 = sb3[1];
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+      const float h2 = silu_f(__uint_as_float(r[o]) + sb2[o]);
+      y0 += sW3[o] * h2;
+      y1 += sW3[H + o] * h2;
+    }
+    if (live && a.yout) {
+      a.yout[2 * c] = y0;
+      a.yout[2 * c + 1] = y1;
+    }
+    // ---- FP64 Newton step in the guessed cell, bisection fallback
+    if (live && !a.xin) {
+      const DTable &t = a.t;
+      const int i = ti;
+      const double *__restrict__ ra = t.le + (size_t)i * t.nt;
+      const double *__restrict__ rb = ra + t.nt;
+      const double w1 = 1.0 - w;
+      const double lTg = a.nm.cT + a.nm.sT * (double)y0;
+      const double xj = (lTg - t.lt0) / t.dlt;
+      bool ok = false;
+      double Pv, cv, Tv;
+      if (!cl && ly > glo && ly < ghi && xj >= 0.0 && xj < (double)(t.nt - 1)) {
+        const int j = (int)floor(xj);
+        const double g0 = w1 * __ldg(ra + j) + w * __ldg(rb + j);
+        const double g1 = w1 * __ldg(ra + j + 1) + w * __ldg(rb + j + 1);
+        if (g0 <= ly && ly < g1) {
+          const double s = (ly - g0) / (g1 - g0);
+          Pv = exp10(bilin(t.lp, t.nt, i, w, j, s));
+          cv = exp10(bilin(t.lc, t.nt, i, w, j, s));
+          Tv = exp10(t.lt0 + (j + s) * t.dlt);
+          ok = true;
+        }
+      }
+      if (ok) {
+        count(&a.cnt->surrogate_accepted);
+      } else {
+        double eu;
+        if (eos_invert(t, rho, en, Pv, cv, eu, &Tv)) count(&a.cnt->table_clamp);
+      }
+      if (a.T) a.T[c] = Tv;
+      if (a.P) a.P[c] = Pv;
+      if (a.cs2) a.cs2[c] = cv;
+    }
+    // every thread has its row in registers: the next tile may reuse sA and TMEM
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (s_abort && tid == 0) atomicExch(a.status, 1);
+  // wait (bounded) for any MMA still in flight before freeing tensor memory
+  if (s_abort) {
+    for (long long it = 0; it < (1ll << 22); ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          "selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(mbar_addr), "r"(phase ^ 1u));
+      if (done) break;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(64));
+}
+
+}  // namespace tde
+
+// ================================================================ host side
+
+#include <random>
+
+using namespace tde;
+
+namespace {
+
+int mlp_fail(tde_ctx *c, int code, const char *msg) {
+  c->err = msg;
+  return code;
+}
+
+#define MCK(ctx, call)                                                   \
+  do {                                                                   \
+    cudaError_t _e = (call);                                             \
+    if (_e != cudaSuccess) {                                             \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(_e);   \
+      return TDE_ECUDA;                                                  \
+    }                                                                    \
+  } while (0)
+
+MLPNorm norm_of(const tde_eos *e) {
+  MLPNorm n;
+  n.cr = (float)e->norm[0]; n.sr = (float)e->norm[1];
+  n.ce = (float)e->norm[2]; n.se = (float)e->norm[3];
+  n.cT = (float)e->norm[4]; n.sT = (float)e->norm[5];
+  n.cP = (float)e->norm[6]; n.sP = (float)e->norm[7];
+  return n;
+}
+
+int ensure_net_buffers(tde_eos *e) {
+  tde_ctx *c = e->ctx;
+  if (!e->d_w) {
+    MCK(c, cudaMalloc(&e->d_w, sizeof(float) * 4 * NPARAM));
+    MCK(c, cudaMemset(e->d_w, 0, sizeof(float) * 4 * NPARAM));
+  }
+  if (!e->d_wb) MCK(c, cudaMalloc(&e->d_wb, sizeof(__nv_bfloat16) * NPARAM));
+  if (!e->d_status) {
+    MCK(c, cudaMalloc(&e->d_status, sizeof(int)));
+    MCK(c, cudaMemset(e->d_status, 0, sizeof(int)));
+  }
+  return TDE_OK;
+}
+
+int upload_weights(tde_eos *e, const float *w) {
+  tde_ctx *c = e->ctx;
+  MCK(c, cudaMemcpyAsync(e->d_w, w, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, c->stream));
+  MCK(c, cudaMemsetAsync(e->d_w + NPARAM, 0, sizeof(float) * 3 * NPARAM, c->stream));   // m, v, g
+  k_round_bf16<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(e->d_w, (__nv_bfloat16 *)e->d_wb, NPARAM);
+  MCK(c, cudaGetLastError());
+  MCK(c, cudaStreamSynchronize(c->stream));
+  e->has_net = true;
+  return TDE_OK;
+}
+
+size_t grad_smem() { return sizeof(float) * (NPARAM + 4 * GT * (H + 1) + 4 * GT); }
+
+cudaError_t launch_grad(tde_eos *e, const float *x, const float *tg, long long s0, long long count,
+                        float inv_n, float *g, float *loss, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+    attr = true;
+  }
+  const unsigned grid = (unsigned)((count + GT - 1) / GT);
+  k_mlp_grad<<<grid, GT, grad_smem(), s>>>((const __nv_bfloat16 *)e->d_wb, x, tg, s0, count, inv_n, g,
+                                           loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, const double *en,
+                                    double *T, double *P, double *cs2, const float *xin, float *yout,
+                                    cudaStream_t s) {
+  SurrogateArgs a;
+  a.t = e->tab;
+  a.nm = norm_of(e);
+  a.wb = (const __nv_bfloat16 *)e->d_wb;
+  a.n = n;
+  a.rho = rho;
+  a.e = en;
+  a.T = T;
+  a.P = P;
+  a.cs2 = cs2;
+  a.yout = yout;
+  a.xin = xin;
+  a.cnt = e->d_cnt;
+  a.status = e->d_status;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
+  const long long tiles = (n + IT - 1) / IT;
+  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * 8);
+  k_eos_surrogate<<<grid, IT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace tde {
+cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const double *en,
+                                 double *T, double *P, double *cs2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope ps(e->ctx, TDE_K_EOS);
+  return launch_surrogate_kernel(e, n, rho, en, T, P, cs2, nullptr, nullptr, s);
+}
+}  // namespace tde
+
+extern "C" int tde_eos_surrogate_set_weights(tde_eos *e, const float *w, size_t n) {
+  if (!e) return TDE_EINVAL;
+  if (!w || n != (size_t)NPARAM) return mlp_fail(e->ctx, TDE_EINVAL, "tde_eos_surrogate_set_weights: need 4482 floats");
+  int r = ensure_net_buffers(e);
+  if (r) return r;
+  return upload_weights(e, w);
+}
+
+extern "C" int tde_eos_surrogate_get_weights(tde_eos *e, float *w, size_t n) {
+  if (!e) return TDE_EINVAL;
+  if (!w || n != (size_t)NPARAM || !e->has_net) return mlp_fail(e->ctx, TDE_EINVAL, "tde_eos_surrogate_get_weights: no weights or size");
+  MCK(e->ctx, cudaMemcpyAsync(w, e->d_w, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, e->ctx->stream));
+  MCK(e->ctx, cudaStreamSynchronize(e->ctx->stream));
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_surrogate_reset(tde_eos *e) {
+  if (!e) return TDE_EINVAL;
+  e->has_net = false;
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_surrogate_norm(const tde_eos *e, double *out8) {
+  if (!e || !out8) return TDE_EINVAL;
+  memcpy(out8, e->norm, sizeof(e->norm));
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_surrogate_grad(tde_eos *e, int64_t n, const float *x, const float *target,
+                                      float *grad, float *loss) {
+  if (!e) return TDE_EINVAL;
+  tde_ctx *c = e->ctx;
+  if (n <= 0 || !x || !target || !grad || !loss || !e->has_net)
+    return mlp_fail(c, TDE_EINVAL, "tde_eos_surrogate_grad: arguments or no weights");
+  MCK(c, cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, c->stream));
+  MCK(c, cudaMemsetAsync(loss, 0, sizeof(float), c->stream));
+  ProfScope ps(c, TDE_K_EOS);
+  MCK(c, launch_grad(e, x, target, 0, n, 1.0f / (float)n, grad, loss, c->stream));
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_surrogate_forward(tde_eos *e, int64_t n, const float *x, float *y) {
+  if (!e) return TDE_EINVAL;
+  tde_ctx *c = e->ctx;
+  if (n <= 0 || !x || !y || !e->has_net) return mlp_fail(c, TDE_EINVAL, "tde_eos_surrogate_forward: arguments or no weights");
+  ProfScope ps(c, TDE_K_EOS);
+  MCK(c, launch_surrogate_kernel(e, n, nullptr, nullptr, nullptr, nullptr, nullptr, x, y, c->stream));
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_surrogate_train(tde_eos *e, uint64_t seed, int n_samples, int epochs, int batch,
+                                       double lr, tde_train_report *rep) {
+  if (!e) return TDE_EINVAL;
+  tde_ctx *c = e->ctx;
+  if (n_samples < GT || epochs < 1 || batch < GT || batch % GT || !(lr > 0.0))
+    return mlp_fail(c, TDE_EINVAL, "tde_eos_surrogate_train: sizes (batch a multiple of 128)");
+  int r = ensure_net_buffers(e);
+  if (r) return r;
+  if (!e->has_net) {   // seeded Glorot-normal initialisation, zero biases
+    std::vector<float> w(NPARAM, 0.f);
+    std::mt19937_64 rng(seed ^ 0x5eedull);
+    auto fill = [&](int off, int fan_out, int fan_in) {
+      std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (fan_in + fan_out)));
+      for (int q = 0; q < fan_out * fan_in; ++q) w[off + q] = nd(rng);
+    };
+    fill(OW1, H, 2);
+    fill(OW2, H, H);
+    fill(OW3, 2, H);
+    r = upload_weights(e, w.data());
+    if (r) return r;
+  }
+  float *d_x = nullptr, *d_y = nullptr, *d_loss = nullptr;
+  const int nb_per_epoch = n_samples / batch;
+  const int nbt = nb_per_epoch * epochs;
+  MCK(c, cudaMalloc(&d_x, sizeof(float) * 2 * n_samples));
+  MCK(c, cudaMalloc(&d_y, sizeof(float) * 2 * n_samples));
+  MCK(c, cudaMalloc(&d_loss, sizeof(float) * nbt));
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaMemsetAsync(d_loss, 0, sizeof(float) * nbt, s);
+  k_mlp_samples<<<1024, 256, 0, s>>>(e->tab, norm_of(e), n_samples, seed, d_x, d_y);
+  float *w = e->d_w, *m = w + NPARAM, *v = m + NPARAM, *g = v + NPARAM;
+  const float b1 = 0.9f, b2 = 0.999f;
+  int step = 0;
+  cudaError_t err = cudaGetLastError();
+  for (int ep = 0; ep < epochs && err == cudaSuccess; ++ep) {
+    for (int bi = 0; bi < nb_per_epoch && err == cudaSuccess; ++bi, ++step) {
+      err = launch_grad(e, d_x, d_y, (long long)bi * batch, batch, 1.0f / batch, g, d_loss + step, s);
+      const double prog = (double)step / (double)nbt;
+      const float lrs = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + cos(3.141592653589793 * prog))));
+      const float bc1 = 1.f - powf(b1, (float)(step + 1)), bc2 = 1.f - powf(b2, (float)(step + 1));
+      k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(w, m, v, g, (__nv_bfloat16 *)e->d_wb, NPARAM, lrs, b1, b2,
+                                                   1e-8f, bc1, bc2);
+      if (err == cudaSuccess) err = cudaGetLastError();
+    }
+  }
+  cudaEventRecord(e1, s);
+  std::vector<float> losses(nbt);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(losses.data(), d_loss, sizeof(float) * nbt, cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_x);
+  cudaFree(d_y);
+  cudaFree(d_loss);
+  if (err != cudaSuccess) {
+    c->err = std::string("tde_eos_surrogate_train: ") + cudaGetErrorString(err);
+    return TDE_ECUDA;
+  }
+  c->launches[TDE_K_EOS] += 2 * (uint64_t)nbt + 1;
+  if (rep) {
+    rep->loss_first = losses.front();
+    rep->loss_last = losses.back();
+    rep->epochs = epochs;
+    rep->samples = n_samples;
+    rep->batches = nbt;
+    rep->ms = ms;
+  }
+  return TDE_OK;
+}

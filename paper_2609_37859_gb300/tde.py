@@ -59,10 +59,16 @@ class TableView(C.Structure):
 
 class Counts(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("rho_floor", "p_floor", "u_floor", "table_clamp",
-                                          "excised", "dual_aux_used", "synced", "nonfinite")]
+                                          "excised", "dual_aux_used", "synced", "nonfinite",
+                                          "surrogate_accepted")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class TrainReport(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("epochs", C.c_int),
+                ("samples", C.c_int), ("batches", C.c_int), ("ms", C.c_double)]
 
 
 vp = C.c_void_p
@@ -77,6 +83,14 @@ _SIGS = {
     "tde_eos_destroy": [vp],
     "tde_eos_invert": [vp, C.c_int, C.c_int64, dp, dp, dp, dp, dp, C.POINTER(Counts)],
     "tde_eos_eval_rhoT": [vp, C.c_int64, dp, dp, dp, dp, dp],
+    "tde_eos_surrogate_train": [vp, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_double,
+                                C.POINTER(TrainReport)],
+    "tde_eos_surrogate_reset": [vp],
+    "tde_eos_surrogate_set_weights": [vp, C.POINTER(C.c_float), C.c_size_t],
+    "tde_eos_surrogate_get_weights": [vp, C.POINTER(C.c_float), C.c_size_t],
+    "tde_eos_surrogate_grad": [vp, C.c_int64, dp, dp, dp, dp],
+    "tde_eos_surrogate_forward": [vp, C.c_int64, dp, dp],
+    "tde_eos_surrogate_norm": [vp, C.POINTER(C.c_double)],
     "tde_mesh_create": [vp, C.c_int, C.POINTER(BlockDesc), C.POINTER(GridDesc), C.POINTER(Params),
                         vp, C.POINTER(vp)],
     "tde_mesh_destroy": [vp],
@@ -217,6 +231,44 @@ class EOS:
         self.ctx.check(lib().tde_eos_invert(self.h, mode, rho.numel(), _ptr(rho), _ptr(e), _ptr(T),
                                             _ptr(P), _ptr(cs2), C.byref(c) if c else None))
         return c
+
+    def counts(self):
+        c = Counts()
+        self.ctx.check(lib().tde_eos_invert(self.h, INVERT_BISECT, 0, None, None, None, None, None,
+                                            C.byref(c)))
+        return c.as_dict()
+
+    def set_weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        self.ctx.check(lib().tde_eos_surrogate_set_weights(self.h, a.ctypes.data_as(C.POINTER(C.c_float)),
+                                                           a.size))
+
+    def get_weights(self):
+        a = np.zeros(4482, dtype=np.float32)
+        self.ctx.check(lib().tde_eos_surrogate_get_weights(self.h, a.ctypes.data_as(C.POINTER(C.c_float)),
+                                                           a.size))
+        return a
+
+    def reset_weights_for_training(self):
+        self.ctx.check(lib().tde_eos_surrogate_reset(self.h))
+
+    def train(self, seed=0, n_samples=1 << 20, epochs=20, batch=8192, lr=3e-3):
+        r = TrainReport()
+        self.ctx.check(lib().tde_eos_surrogate_train(self.h, seed, n_samples, epochs, batch, lr,
+                                                     C.byref(r)))
+        return {n: getattr(r, n) for n, _ in r._fields_}
+
+    def grad(self, x, target, grad, loss):
+        self.ctx.check(lib().tde_eos_surrogate_grad(self.h, x.shape[0], _ptr(x), _ptr(target),
+                                                    _ptr(grad), _ptr(loss)))
+
+    def forward(self, x, y):
+        self.ctx.check(lib().tde_eos_surrogate_forward(self.h, x.shape[0], _ptr(x), _ptr(y)))
+
+    def norm(self):
+        out = (C.c_double * 8)()
+        self.ctx.check(lib().tde_eos_surrogate_norm(self.h, out))
+        return list(out)
 
     def eval_rhoT(self, rho, T, P=None, e=None, cs2=None):
         self.ctx.check(lib().tde_eos_eval_rhoT(self.h, rho.numel(), _ptr(rho), _ptr(T), _ptr(P),

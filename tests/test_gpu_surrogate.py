@@ -1,0 +1,144 @@
+"""The learned EOS guess on the GPU, through the C ABI: the training kernels'
+gradient against the FP64 oracle on the same BF16-rounded weights, the
+tensor-core forward pass against the oracle network, training, and the
+surrogate inversion against table bisection (identical results by
+construction; the acceptance rate is what the network buys)."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLE = os.path.join(ROOT, "paper_2609_37859_gb300", "data", "eos_saha_hhe_256.npz")
+NP = 4482
+
+
+@pytest.fixture(scope="module")
+def tde():
+    from paper_2609_37859_gb300 import build, tde as T
+    build.build()
+    return T
+
+
+@pytest.fixture(scope="module")
+def env(tde, oracle):
+    ctx = tde.Context(0)
+    eos = tde.EOS.from_file(ctx, TABLE)
+    d = np.load(TABLE)
+    ot = oracle.EOSTable(int(d["n_rho"]), int(d["n_T"]), tuple(d["lrho"]), tuple(d["lT"]),
+                         d["log10_e"], d["log10_P"], d["log10_cs2"])
+    return ctx, eos, ot
+
+
+def bf16_round(w):
+    """float32 -> nearest-even BF16, returned as float64."""
+    b = np.asarray(w, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def random_weights(seed):
+    rng = np.random.default_rng(seed)
+    w = np.zeros(NP, dtype=np.float32)
+    w[:128] = rng.normal(0, 0.7, 128)
+    w[128:192] = rng.normal(0, 0.1, 64)
+    w[192:4288] = rng.normal(0, 0.125, 4096)
+    w[4288:4352] = rng.normal(0, 0.1, 64)
+    w[4352:4480] = rng.normal(0, 0.125, 128)
+    w[4480:] = rng.normal(0, 0.1, 2)
+    return w
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def test_training_gradient_matches_oracle(tde, oracle, env):
+    ctx, eos, _ = env
+    w = random_weights(1)
+    eos.set_weights(w)
+    rng = np.random.default_rng(2)
+    n = 1000
+    x = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    t = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    g = torch.zeros(NP, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    eos.grad(dev(x), dev(t), g, loss)
+    torch.cuda.synchronize()
+    lo, go = oracle.mlp_loss_grad(bf16_round(w), x.astype(np.float64), t.astype(np.float64))
+    gg = g.cpu().numpy().astype(np.float64)
+    assert float(loss) == pytest.approx(lo, rel=1e-4)
+    assert np.linalg.norm(gg - go) <= 1e-3 * np.linalg.norm(go)
+    for sl in (slice(0, 128), slice(128, 192), slice(192, 4288), slice(4288, 4352), slice(4352, 4482)):
+        assert np.linalg.norm(gg[sl] - go[sl]) <= 2e-3 * np.linalg.norm(go[sl]) + 1e-7
+
+
+def test_tensor_core_forward_matches_oracle_network(tde, oracle, env):
+    ctx, eos, _ = env
+    w = random_weights(3)
+    eos.set_weights(w)
+    rng = np.random.default_rng(4)
+    n = 1000   # 8 tiles of 128, ragged tail
+    x = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    y = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    eos.forward(dev(x), y)
+    torch.cuda.synchronize()
+    yo = oracle.mlp_forward(bf16_round(w), x.astype(np.float64))
+    yg = y.cpu().numpy()
+    # the hidden layer enters the tensor core as BF16 (relative rounding 2^-9)
+    err = np.abs(yg - yo)
+    assert err.max() < 0.05 * np.abs(yo).max() + 1e-3, err.max()
+    assert np.corrcoef(yg.ravel(), yo.ravel())[0, 1] > 0.9995
+
+
+@pytest.fixture(scope="module")
+def trained(tde, env):
+    ctx, eos, _ = env
+    eos.reset_weights_for_training()
+    rep = eos.train(seed=2609, n_samples=1 << 20, epochs=30, batch=4096, lr=3e-3)
+    print("training report", rep)
+    return rep
+
+
+def test_training_reduces_loss(trained):
+    assert trained["loss_last"] < 0.01 * trained["loss_first"]
+
+
+def test_surrogate_inversion_equals_bisection(tde, oracle, env, trained):
+    ctx, eos, ot = env
+    rng = np.random.default_rng(9)
+    n = 1 << 16
+    lr = rng.uniform(-14, 2, n)
+    lT = rng.uniform(2.0, 8.0, n)
+    rho = torch.tensor(10 ** lr, dtype=torch.float64, device="cuda")
+    T0 = torch.tensor(10 ** lT, dtype=torch.float64, device="cuda")
+    e = torch.empty_like(rho)
+    eos.eval_rhoT(rho, T0, e=e)
+    e[:4] = torch.tensor([-1.0, 1e-40, 1e40, 1e12], dtype=torch.float64)   # clamped inputs
+    outs = {}
+    for mode in (tde.INVERT_BISECT, tde.INVERT_SURROGATE):
+        T, P, c2 = (torch.empty_like(rho) for _ in range(3))
+        before = eos.counts()
+        eos.invert(rho, e, T=T, P=P, cs2=c2, mode=mode)
+        after = eos.counts()
+        outs[mode] = (T.cpu().numpy(), P.cpu().numpy(), c2.cpu().numpy(),
+                      after["surrogate_accepted"] - before["surrogate_accepted"])
+    for k in range(3):
+        assert np.array_equal(outs[tde.INVERT_BISECT][k], outs[tde.INVERT_SURROGATE][k])
+    acc = outs[tde.INVERT_SURROGATE][3] / n
+    print("surrogate acceptance", acc)
+    assert acc > 0.2, acc
+    # and both equal the oracle's inversion
+    idx = rng.integers(0, n, 300)
+    ec = e.cpu().numpy()
+    rc = rho.cpu().numpy()
+    for q in idx:
+        want = ot.invert(rc[q], ec[q])
+        assert outs[tde.INVERT_SURROGATE][0][q] == pytest.approx(want[0], rel=1e-12)
+        assert outs[tde.INVERT_SURROGATE][1][q] == pytest.approx(want[1], rel=1e-12)

@@ -170,3 +170,30 @@ def test_T_from_P(saha_table):
     rho = 1e-8
     Pr, e, c2 = saha_table.eval_rhoT(rho, 1e3)
     assert saha_table.T_from_P(rho, Pr) == pytest.approx(1e3, rel=1e-12)
+
+
+def test_invert_from_guess_equals_bisection(saha_table):
+    """Any guess gives the bisection result bit for bit; a guess in the right
+    temperature cell is accepted (the one Newton step is exact there)."""
+    t = saha_table
+    rng = np.random.default_rng(3)
+    d = 6.0 / 255
+    n_acc = 0
+    for k in range(3000):
+        lr = rng.uniform(-14, 2)
+        lT = rng.uniform(2.0, 8.0)
+        Pr, e, c2 = t.eval_rhoT(10 ** lr, 10 ** lT)
+        want = t.invert(10 ** lr, e)
+        guess = {0: lT, 1: lT + rng.normal(0, 0.5), 2: rng.uniform(-1, 11)}[k % 3]
+        T, P2, c22, acc = t.invert_guess(10 ** lr, e, guess)
+        assert (T, P2, c22) == want[:3]
+        if k % 3 == 0:
+            # exact guess: accepted unless it sits on the upper edge of a cell
+            xj = (lT - 2.0) / d
+            if 1e-9 < xj - np.floor(xj) < 1 - 1e-9:
+                assert acc
+        n_acc += acc
+    assert n_acc > 1000
+    # out of range input: never accepted, clamped like the plain inversion
+    T, P2, c22, acc = t.invert_guess(1e-20, 1e10, 3.0)
+    assert not acc and (T, P2, c22) == t.invert(1e-20, 1e10)[:3]
