@@ -238,6 +238,10 @@ def run_gpu(args):
         }
         if not args.no_eos:
             line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
+        if not args.no_lat:
+            del mesh
+            torch.cuda.empty_cache()
+            line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -304,6 +308,97 @@ def eos_bench(ctx, eos, tde, torch, dev, args):
             "speedup": res["bisect"]["ms"] / res["surrogate"]["ms"], "identical_results": bool(same),
             "training": {"samples": rep["samples"], "epochs": rep["epochs"], "ms": rep["ms"],
                          "loss_first": rep["loss_first"], "loss_last": rep["loss_last"]}}
+
+
+# ------------------------------------------------------------- LAT stream (C4) ---
+
+def lat_bench(ctx, eos, tde, torch, dev, args):
+    """The LAT workload: 384 x 32^3 + 128 x 16^3 MeshBlocks (13.1 M cells), PPM,
+    Saha table in code units, dual energy, point mass with excision, N_LAT = 5.
+    Compares, over the same physical time f_max dt0: LAT windows (per-level
+    batched launches, replayed as a CUDA graph), synchronised steps of dt0 (every
+    block every fine step), and the plain form of one launch sequence per block
+    and stage (measured on one step)."""
+    from paper_2609_37859_gb300 import workloads as wl
+    lay, f, bhp = wl.stream_c4()
+    rho_cgs = torch.from_numpy(np.ascontiguousarray(f["rho"] * wl.RHO0_CGS).ravel()).to(dev)
+    Tt = torch.from_numpy(np.ascontiguousarray(f["T"]).ravel()).to(dev)
+    Pc = torch.empty_like(rho_cgs)
+    eos.eval_rhoT(rho_cgs, Tt, P=Pc)
+    P_code = (Pc / (wl.RHO0_CGS * wl.V0_CGS ** 2)).cpu().numpy().reshape(f["rho"].shape)
+    del rho_cgs, Tt, Pc
+    W = wl.prim_state(lay, f["rho"], f["vx"], f["vy"], f["vz"], P_code)
+    params = tde.make_params(eos=tde.EOS_TABLE, recon=tde.RECON_PPM, dual=1, eta1=1e-3, eta2=1e-4,
+                             rho_floor=1e-17, p_floor=1e-30, u_floor=1.5e-30,
+                             unit_rho=wl.RHO0_CGS, unit_e=wl.V0_CGS ** 2)
+    mesh = tde.Mesh(ctx, lay, params, eos)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    del W
+    bh = tde.make_bh(on=1, excise=1, GM=bhp["GM"], r_soft=bhp["r_soft"], r_exc=bhp["r_exc"],
+                     x0=bhp["x0"])
+    U0 = mesh.U.clone()
+    n_lat = 5
+    fac, dt0, fmax = mesh.lat_assign(n_lat, CFL, merge_frac=0.01, bh=bh)
+    cells = np.array([b[3] * b[4] * b[5] for b in lay.blocks], dtype=np.float64)
+    work = float((cells * (fmax // fac)).sum() / (cells.sum() * fmax))
+    levels = {int(k): int((fac == k).sum()) for k in np.unique(fac)}
+
+    def timed(fn, reps):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    # LAT: eager first window (warm-up), then graph replay
+    mesh.lat_set_factors(fac, dt0)
+    mesh.lat_window(bh=bh, use_graph=False)
+    mesh.lat_window(bh=bh, use_graph=True)
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+    ms_lat = timed(lambda: mesh.lat_window(bh=bh, use_graph=True), 2)
+    lat_counts = mesh.counts(reset=True)
+    # synchronised steps of dt0 over the same physical time
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+    mesh.step(dt=dt0, bh=bh)
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+
+    def sync_window():
+        for _ in range(fmax):
+            mesh.step(dt=dt0, bh=bh)
+    ms_sync = timed(sync_window, 1)
+    # plain form: one launch sequence per block and stage, one step of dt0
+    ids = torch.arange(lay.nb, dtype=torch.int32, device=dev)
+    dtb = torch.full((lay.nb,), dt0, dtype=torch.float64, device=dev)
+    tb = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
+    mesh.U.copy_(U0)
+
+    def plain_step():
+        for st in (0, 1):
+            for b in range(lay.nb):
+                mesh.hydro_stage(st, dtb, tb, ids=ids[b:b + 1], bh=bh)
+    plain_step()
+    ms_plain_step = timed(plain_step, 1)
+    ncell = lay.ncells
+    upd = ncell * fmax
+    del mesh, U0
+    torch.cuda.empty_cache()
+    return {"workload": "cold stream on an ellipse (r_p 10, r_a 28 Rsun) around 1e3 Msun with excision, "
+                        "384 x 32^3 + 128 x 16^3 MeshBlocks, PPM+HLLC, Saha table, dual energy, N_LAT 5",
+            "cells": ncell, "meshblocks": lay.nb, "f_max": int(fmax), "blocks_per_factor": levels,
+            "work_fraction": work, "work_reduction": 1.0 - work,
+            "lat_window_ms": ms_lat, "sync_window_ms": ms_sync,
+            "plain_per_block_step_ms": ms_plain_step, "plain_window_ms_est": ms_plain_step * fmax,
+            "lat_speedup_vs_sync": ms_sync / ms_lat,
+            "lat_speedup_vs_plain": ms_plain_step * fmax / ms_lat,
+            "effective_cell_updates_per_s": {"lat": upd / (ms_lat * 1e-3), "sync": upd / (ms_sync * 1e-3),
+                                             "plain": ncell / (ms_plain_step * 1e-3)},
+            "lat_counters": lat_counts}
 
 
 # ------------------------------------------------------------------ oracle ---
@@ -389,6 +484,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eos", action="store_true", help="skip the EOS-inversion comparison")
+    ap.add_argument("--no-lat", action="store_true", help="skip the LAT stream comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -187,3 +187,91 @@ def random_smooth(layout, seed=0, rho0=1.0, P0=1.0, drho=0.2, dv=0.3, dP=0.2, mo
 
     r = rho0 * (1 + field_(drho))
     return prim_state(layout, r, field_(dv), field_(dv), field_(dv), P0 * (1 + field_(dP)))
+
+
+# ------------------------------------------------------------ stream (C4) ---
+
+# code units of Table 1: M0 = 1 Msun, L0 = 2 Rsun, t0 = 1270.9 s, G = 1 / (4 pi)
+RHO0_CGS, V0_CGS = 0.7382, 1.0948e8
+G_CODE = 1.0 / (4.0 * np.pi)
+RSUN_CODE = 0.5
+
+
+def stream_c4(split_nearest=16, n_root=(10, 10, 4), block=32, ng=3, rp_rsun=10.0, ra_rsun=28.0,
+              sigma_rsun=1.0, rho_peri=1e-2, rho_apo=1e-10, rho_amb=1e-14, mach_max=1e3,
+              m_bh=1000.0, mu=1.3, gamma=5.0 / 3.0):
+    """Cold thin stream on an ellipse around a point mass (the LAT workload).
+
+    Domain x, y in [-32, 32] Rsun, z in [-12.8, 12.8] Rsun (code units of
+    Table 1), cells of 0.2 Rsun; root blocks of `block`^3, the `split_nearest`
+    root blocks closest to pericentre split into eight half-size blocks.  A
+    Gaussian tube (sigma) follows the ellipse with the BH at its focus
+    (pericentre rp, apocentre ra); its centre density falls log-linearly in the
+    orbital phase from rho_peri to rho_apo (g/cm^3); the gas moves on the
+    Keplerian ellipse; one temperature makes the fastest cell Mach mach_max for
+    an ideal-gas sound speed with mean molecular weight mu (the caller turns
+    (rho, T) into pressure with its EOS).  Returns (layout, fields) with fields a
+    dict of global arrays rho (code units), vx, vy, vz (code units), T (K), and
+    the BH parameters."""
+    N = (n_root[0] * block, n_root[1] * block, n_root[2] * block)
+    half = (32.0 * RSUN_CODE, 32.0 * RSUN_CODE, 12.8 * RSUN_CODE)
+    domain = tuple((-h, h) for h in half)
+    rp, ra = rp_rsun * RSUN_CODE, ra_rsun * RSUN_CODE
+    a_orb = 0.5 * (rp + ra)
+    ecc = (ra - rp) / (ra + rp)
+    # root blocks nearest to pericentre (at +x)
+    centres = []
+    dx = tuple((domain[a][1] - domain[a][0]) / N[a] for a in range(3))
+    for bk in range(n_root[2]):
+        for bj in range(n_root[1]):
+            for bi in range(n_root[0]):
+                c = [domain[0][0] + (bi + 0.5) * block * dx[0], domain[1][0] + (bj + 0.5) * block * dx[1],
+                     domain[2][0] + (bk + 0.5) * block * dx[2]]
+                centres.append(((c[0] - rp) ** 2 + c[1] ** 2 + c[2] ** 2, (bi, bj, bk)))
+    centres.sort()
+    split = {c[1] for c in centres[:split_nearest]}
+    lay = mixed_layout(N, block, split, domain, (0, 0, 0), ng)
+    x, y, z = lay.cell_centres()
+    # distance to the ellipse r(phi) = a (1 - e^2) / (1 + e cos phi), sampled
+    # densely, on the (x, y) plane (it does not depend on z)
+    phi = np.linspace(-np.pi, np.pi, 4097)
+    rr = a_orb * (1 - ecc ** 2) / (1 + ecc * np.cos(phi))
+    pts = np.stack([rr * np.cos(phi), rr * np.sin(phi)], axis=1)
+    flat = np.stack([x[0].ravel(), y[0].ravel()], axis=1)
+    best_d2 = np.full(flat.shape[0], np.inf)
+    best_k = np.zeros(flat.shape[0], dtype=np.int64)
+    for k0 in range(0, len(pts), 32):
+        chunk = pts[k0:k0 + 32]
+        d2 = ((flat[:, None, :] - chunk[None, :, :]) ** 2).sum(axis=2)
+        kk = np.argmin(d2, axis=1)
+        dd = d2[np.arange(len(kk)), kk]
+        upd = dd < best_d2
+        best_d2[upd] = dd[upd]
+        best_k[upd] = kk[upd] + k0
+    best_d2 = np.broadcast_to(best_d2.reshape(x.shape[1:]), x.shape)
+    best_k = np.broadcast_to(best_k.reshape(x.shape[1:]), x.shape)
+    best_d2 = best_d2 + z ** 2
+    ph = phi[best_k]
+    frac = np.abs(ph) / np.pi                      # 0 at pericentre, 1 at apocentre
+    lrho_c = np.log10(rho_peri) + frac * (np.log10(rho_apo) - np.log10(rho_peri))
+    sig = sigma_rsun * RSUN_CODE
+    tube = np.exp(-0.5 * best_d2 / sig ** 2)
+    rho_cgs = rho_amb + (10.0 ** lrho_c) * tube
+    # Keplerian speed on the ellipse, direction tangent (counter-clockwise)
+    GM = G_CODE * m_bh
+    rloc = a_orb * (1 - ecc ** 2) / (1 + ecc * np.cos(ph))
+    vmag = np.sqrt(GM * (2.0 / rloc - 1.0 / a_orb))
+    # tangent of the ellipse at phi: d/dphi (r cos phi, r sin phi)
+    drdphi = a_orb * (1 - ecc ** 2) * ecc * np.sin(ph) / (1 + ecc * np.cos(ph)) ** 2
+    tx = drdphi * np.cos(ph) - rloc * np.sin(ph)
+    ty = drdphi * np.sin(ph) + rloc * np.cos(ph)
+    tn = np.sqrt(tx ** 2 + ty ** 2)
+    w = np.clip(tube * 4.0, 0.0, 1.0)               # gas in the tube moves, ambient at rest
+    vx, vy = w * vmag * tx / tn, w * vmag * ty / tn
+    vmax = float(np.max(np.sqrt(vx ** 2 + vy ** 2)))
+    cs = vmax * V0_CGS / mach_max
+    kB, mu_m = 1.380649e-16, mu * 1.66053906660e-24
+    T = np.full(x.shape, cs * cs * mu_m / (gamma * kB))
+    fields = {"rho": rho_cgs / RHO0_CGS, "vx": vx, "vy": vy, "vz": np.zeros_like(vx), "T": T}
+    bh = {"GM": GM, "r_soft": 0.01 * RSUN_CODE, "r_exc": 0.4 * RSUN_CODE, "x0": (0.0, 0.0, 0.0)}
+    return lay, fields, bh
