@@ -255,8 +255,8 @@ def run_gpu(args):
 # DRAM bytes of one launch; profiles/k_sweep_c2_entropy_wave_ncu.md holds the
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
 # False (traffic reported as null) whenever a sweep kernel changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 295.5, "sweep_y": 252.2, "sweep_z": 478.2}
-DRAM_BYTES_SWEEP = {"sweep_x": 267.4e6, "sweep_y": 400.1e6, "sweep_z": 542.9e6}
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 296.0, "sweep_y": 252.2, "sweep_z": 383.2}
+DRAM_BYTES_SWEEP = {"sweep_x": 268.0e6, "sweep_y": 402.4e6, "sweep_z": 542.4e6}
 KERNELS_AS_CAPTURED = True
 
 

@@ -347,6 +347,12 @@ TDE_API int tde_profile(tde_ctx *ctx, int enable);
  * (arrays of TDE_K_NKIND entries, either may be NULL).  Synchronises the stream. */
 TDE_API int tde_profile_read(tde_ctx *ctx, uint64_t *launches, double *ms);
 
+/* The table-driven log10 and exp10 that the EOS kernels use (device arrays of
+ * n doubles; either output may be NULL), for checking them against the CUDA
+ * math library.  Uses eos's tables; asynchronous. */
+TDE_API int tde_math_selftest(tde_eos *eos, int64_t n, const double *x, double *log10_out,
+                              double *exp10_out);
+
 /* Measured FP64 fused multiply-add throughput of the device (FLOP/s, an FMA
  * counted as 2), from a kernel of independent FMA chains on every SM.  The
  * hydro stage is bound by this rate on sm_103a.  Synchronises the stream. */

@@ -139,7 +139,7 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
   tde_eos *e = new (std::nothrow) tde_eos;
   if (!e) return TDE_ENOMEM;
   e->ctx = ctx;
-  cudaError_t err = cudaMalloc(&e->d_data, 3 * nn * sizeof(double));
+  cudaError_t err = cudaMalloc(&e->d_data, 3 * nn * sizeof(double) + nn * sizeof(float));
   if (err == cudaSuccess) err = cudaMalloc(&e->d_cnt, sizeof(Counters));
   if (err != cudaSuccess) {
     cudaFree(e->d_data);
@@ -149,6 +149,12 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
   cudaMemcpy(e->d_data, log10_e, nn * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(e->d_data + nn, log10_P, nn * sizeof(double), cudaMemcpyHostToDevice);
   err = cudaMemcpy(e->d_data + 2 * nn, log10_cs2, nn * sizeof(double), cudaMemcpyHostToDevice);
+  {
+    std::vector<float> le32(nn);
+    for (size_t k = 0; k < nn; ++k) le32[k] = (float)log10_e[k];
+    if (err == cudaSuccess)
+      err = cudaMemcpy(e->d_data + 3 * nn, le32.data(), nn * sizeof(float), cudaMemcpyHostToDevice);
+  }
   cudaMemset(e->d_cnt, 0, sizeof(Counters));
   if (err != cudaSuccess) {
     cudaFree(e->d_data);
@@ -182,12 +188,33 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
   t.le = e->d_data;
   t.lp = e->d_data + nn;
   t.lc = e->d_data + 2 * nn;
+  t.le32 = reinterpret_cast<const float *>(e->d_data + 3 * nn);
+  {   // tables of the table-driven log10 / exp10, computed in extended precision
+    MathTables h;
+    for (int j = 0; j < 182; ++j) {
+      const long double F = j / 128.0L;
+      h.logF[j] = j > 0 ? (double)logl(F) : 0.0;
+      h.invF[j] = j > 0 ? (double)(1.0L / F) : 0.0;
+    }
+    for (int j = 0; j < 128; ++j) h.exp2j[j] = (double)exp2l(j / 128.0L);
+    err = cudaMalloc(&e->d_mt, sizeof(MathTables));
+    if (err == cudaSuccess) err = cudaMemcpy(e->d_mt, &h, sizeof h, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+      cudaFree(e->d_data);
+      cudaFree(e->d_cnt);
+      cudaFree(e->d_mt);
+      delete e;
+      return cuda_fail(ctx, err, "tde_eos_load_table: math tables");
+    }
+    t.mt = e->d_mt;
+  }
   *out = e;
   return TDE_OK;
 }
 
 extern "C" int tde_eos_destroy(tde_eos *e) {
   if (!e) return TDE_EINVAL;
+  cudaFree(e->d_mt);
   cudaFree(e->d_data);
   cudaFree(e->d_cnt);
   cudaFree(e->d_w);
@@ -719,5 +746,27 @@ extern "C" int tde_probe_fp64(tde_ctx *ctx, double *flops) {
   cudaEventDestroy(e1);
   cudaFree(buf);
   *flops = 2.0 * 8.0 * iters * (double)grid * 256 / (best * 1e-3);
+  return TDE_OK;
+}
+
+namespace tde {
+__global__ void k_math_selftest(const MathTables *mt, long long n, const double *x, double *lg,
+                                double *ex) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (lg) lg[i] = fast_log10(mt, x[i]);
+    if (ex) ex[i] = fast_exp10(mt, x[i]);
+  }
+}
+}  // namespace tde
+
+extern "C" int tde_math_selftest(tde_eos *e, int64_t n, const double *x, double *log10_out,
+                                 double *exp10_out) {
+  if (!e || n < 0 || (n > 0 && !x)) return TDE_EINVAL;
+  if (n == 0) return TDE_OK;
+  ProfScope ps(e->ctx, TDE_K_PROBE);
+  k_math_selftest<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, e->ctx->stream>>>(
+      e->d_mt, (long long)n, x, log10_out, exp10_out);
+  CK(e->ctx, cudaGetLastError());
   return TDE_OK;
 }

@@ -17,6 +17,74 @@ namespace tde {
 enum { EOS_IDEAL = 0, EOS_TABLE = 1 };
 enum { PLM = 0, PPM = 1 };
 
+// ------------------------------------------------ log10 / exp10 (FP64) ----
+//
+// Table-driven logarithm and exponential after P. T. P. Tang (ACM TOMS 15, 1989:
+// exp; ACM TOMS 16, 1990: log), written for this library: an exact argument
+// reduction onto one of 128 table points, a short polynomial of the small
+// remainder, and a split (Cody-Waite) constant so that the reduction adds no
+// rounding.  Fewer FP64 instructions than the general-purpose routines; within
+// a few units in the last place (checked against CUDA's log10 / exp10 by
+// tde_math_selftest).  Arguments outside the normal range go to the library.
+
+struct MathTables {
+  double logF[182];    // ln(j/128), j = 90 .. 181 (the reduced argument's table points)
+  double invF[182];    // 128 / j
+  double exp2j[128];   // 2^(j/128)
+};
+
+__device__ __forceinline__ double fast_log10(const MathTables *__restrict__ mt, double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff || bits < 0) return log10(x);
+  // x = 2^k m with m in [sqrt(1/2), sqrt(2)) (no cancellation near x = 1), and
+  // m = F (1 + r) with F = j/128 the nearest table point, m - F exact
+  const long long mant = bits & 0x000fffffffffffffLL;
+  const bool upper = mant >= 0x6a09e667f3bcdLL;            // m0 = 1 + mant 2^-52 >= sqrt(2)
+  const int k = upper ? ex - 1022 : ex - 1023;
+  const double m = __longlong_as_double(mant | (upper ? 0x3fe0000000000000LL : 0x3ff0000000000000LL));
+  const int j = upper ? 64 + (int)((mant + (1LL << 45)) >> 46) : 128 + (int)((mant + (1LL << 44)) >> 45);
+  const double F = j * (1.0 / 128.0);
+  const double r = __dmul_rn(__dsub_rn(m, F), __ldg(&mt->invF[j]));    // |r| <= 2^-7.5
+  // ln(1 + r) = r - r^2/2 + ... - r^8/8
+  double q = -1.0 / 8.0;
+  q = __fma_rn(q, r, 1.0 / 7.0);
+  q = __fma_rn(q, r, -1.0 / 6.0);
+  q = __fma_rn(q, r, 1.0 / 5.0);
+  q = __fma_rn(q, r, -1.0 / 4.0);
+  q = __fma_rn(q, r, 1.0 / 3.0);
+  q = __fma_rn(q, r, -0.5);
+  const double lp = __fma_rn(__dmul_rn(q, r), r, r);
+  const double kd = (double)k;
+  const double ln2_hi = 0.6931471803691238;   // 32 significant bits: k * ln2_hi is exact
+  const double ln2_lo = 1.9082149292705877e-10;
+  const double hi = __fma_rn(kd, ln2_hi, __ldg(&mt->logF[j]));
+  const double lo = __fma_rn(kd, ln2_lo, lp);
+  return __dmul_rn(__dadd_rn(hi, lo), 0.4342944819032518);   // log10(e)
+}
+
+__device__ __forceinline__ double fast_exp10(const MathTables *__restrict__ mt, double x) {
+  if (!(fabs(x) < 300.0)) return exp10(x);
+  // 10^x = 2^(n/128) 10^r with n = round(128 x log2 10), r = x - n log10(2)/128
+  const double n = rint(__dmul_rn(x, 425.20679614558236));   // 128 log2(10)
+  const double c_hi = 0.002351796840230236;   // log10(2)/128, 32 significant bits
+  const double c_lo = 8.946172576579561e-13;
+  const double r = __fma_rn(-n, c_lo, __fma_rn(-n, c_hi, x));   // |r| <= log10(2)/256
+  const double u = __dmul_rn(r, 2.302585092994046);             // ln 10
+  // e^u - 1 = u + u^2/2 + ... + u^6/720, |u| <= 2.7e-3
+  double q = 1.0 / 720.0;
+  q = __fma_rn(q, u, 1.0 / 120.0);
+  q = __fma_rn(q, u, 1.0 / 24.0);
+  q = __fma_rn(q, u, 1.0 / 6.0);
+  q = __fma_rn(q, u, 0.5);
+  const double eu = __fma_rn(__dmul_rn(q, u), u, u);
+  const int ni = (int)n;
+  const int jj = ni & 127, kk = ni >> 7;
+  const double tj = __ldg(&mt->exp2j[jj]);
+  const double v = __fma_rn(tj, eu, tj);   // 2^(jj/128) e^u
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)kk << 52));
+}
+
 // Tabulated EOS on a uniform (log10 rho, log10 T) grid, [n_rho][n_T], cgs.
 struct DTable {
   int nr, nt;
@@ -24,7 +92,16 @@ struct DTable {
   const double *__restrict__ le;   // log10 e
   const double *__restrict__ lp;   // log10 P
   const double *__restrict__ lc;   // log10 cs^2
+  const float *__restrict__ le32;  // log10 e rounded to FP32 (guides the search)
+  const MathTables *__restrict__ mt;   // tables of fast_log10 / fast_exp10 (or null)
 };
+
+__device__ __forceinline__ double tlog10(const DTable &t, double x) {
+  return t.mt ? fast_log10(t.mt, x) : log10(x);
+}
+__device__ __forceinline__ double texp10(const DTable &t, double x) {
+  return t.mt ? fast_exp10(t.mt, x) : exp10(x);
+}
 
 struct Counters {
   unsigned long long rho_floor, p_floor, u_floor, table_clamp, excised, dual_aux_used, synced,
@@ -75,7 +152,7 @@ __device__ __forceinline__ double rcp_nr(double d) {
 
 // Density cell i and weight w of log10 rho (clamped to the table).
 __device__ __forceinline__ bool rho_cell(const DTable &t, double rho, int &i, double &w) {
-  double x = (log10(rho) - t.lr0) * t.inv_dlr;
+  double x = (tlog10(t, rho) - t.lr0) * t.inv_dlr;
   bool cl = false;
   if (!(x >= 0.0)) { x = 0.0; cl = true; }
   if (x > (double)(t.nr - 1)) { x = (double)(t.nr - 1); cl = true; }
@@ -86,13 +163,20 @@ __device__ __forceinline__ bool rho_cell(const DTable &t, double rho, int &i, do
   return cl;
 }
 
+// Interpolation formulas are written with explicit rounding so that every kernel
+// computes the same bits for the same cell (the surrogate's accepted path must
+// equal the bisection path exactly, whatever the compiler fuses around it).
+__device__ __forceinline__ double lerp_rn(double w, double a, double b) {
+  return __fma_rn(w, b, __dmul_rn(__dsub_rn(1.0, w), a));
+}
+
 __device__ __forceinline__ double bilin(const double *__restrict__ f, int nt, int i, double w, int j,
                                         double s) {
   const double *a = f + (size_t)i * nt + j;
   const double *b = a + nt;
-  double lo = (1.0 - s) * __ldg(a) + s * __ldg(a + 1);
-  double hi = (1.0 - s) * __ldg(b) + s * __ldg(b + 1);
-  return (1.0 - w) * lo + w * hi;
+  const double lo = lerp_rn(s, __ldg(a), __ldg(a + 1));
+  const double hi = lerp_rn(s, __ldg(b), __ldg(b + 1));
+  return lerp_rn(w, lo, hi);
 }
 
 // (rho, e) -> P, cs2 (cgs) by binary search of the interpolated log10 e column
@@ -109,10 +193,9 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
   const int nt = t.nt;
   const double *__restrict__ a = t.le + (size_t)i * nt;
   const double *__restrict__ b = a + nt;
-  const double w1 = 1.0 - w;
-  double glo = w1 * __ldg(a) + w * __ldg(b);
-  double ghi = w1 * __ldg(a + nt - 1) + w * __ldg(b + nt - 1);
-  double y = e > 0.0 ? log10(e) : -INFINITY;
+  double glo = lerp_rn(w, __ldg(a), __ldg(b));
+  double ghi = lerp_rn(w, __ldg(a + nt - 1), __ldg(b + nt - 1));
+  double y = e > 0.0 ? tlog10(t, e) : -INFINITY;
   int j;
   double s;
   if (!(y > glo)) {
@@ -120,22 +203,45 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
   } else if (y >= ghi) {
     j = nt - 2; s = 1.0; cl = true;
   } else {
+    // search in FP32 (FP64 issues 55x slower on this part), then confirm the cell
+    // with the FP64 bracket the linear solve needs anyway; the cell with
+    // g_j <= y < g_{j+1} is unique, so a confirmed FP32 answer equals the FP64
+    // bisection's, and an unconfirmed one (y within FP32 rounding of a node)
+    // falls back to it
     int lo = 0, hi = nt - 1;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      double g = w1 * __ldg(a + mid) + w * __ldg(b + mid);
-      if (g <= y) lo = mid; else hi = mid;
+    if (t.le32) {   // tables without the FP32 copy (caller-owned views) skip this
+      const float *__restrict__ a32 = t.le32 + (size_t)i * nt;
+      const float *__restrict__ b32 = a32 + nt;
+      const float w32 = (float)w, y32 = (float)y;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        const float a0 = __ldg(a32 + mid);
+        const float g = fmaf(w32, __ldg(b32 + mid) - a0, a0);
+        if (g <= y32) lo = mid; else hi = mid;
+      }
     }
     j = lo;
-    double g0 = w1 * __ldg(a + j) + w * __ldg(b + j);
-    double g1 = w1 * __ldg(a + j + 1) + w * __ldg(b + j + 1);
-    s = (y - g0) / (g1 - g0);
+    double g0 = lerp_rn(w, __ldg(a + j), __ldg(b + j));
+    double g1 = lerp_rn(w, __ldg(a + j + 1), __ldg(b + j + 1));
+    if (!(g0 <= y && y < g1)) {
+      lo = 0;
+      hi = nt - 1;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        const double g = lerp_rn(w, __ldg(a + mid), __ldg(b + mid));
+        if (g <= y) lo = mid; else hi = mid;
+      }
+      j = lo;
+      g0 = lerp_rn(w, __ldg(a + j), __ldg(b + j));
+      g1 = lerp_rn(w, __ldg(a + j + 1), __ldg(b + j + 1));
+    }
+    s = __dmul_rn(__dsub_rn(y, g0), rcp_nr(__dsub_rn(g1, g0)));
   }
-  P = exp10(bilin(t.lp, nt, i, w, j, s));
+  P = texp10(t, bilin(t.lp, nt, i, w, j, s));
   if (WANT_CS2) {
-    cs2 = exp10(bilin(t.lc, nt, i, w, j, s));
-    if (T) *T = exp10(t.lt0 + (j + s) * t.dlt);
-    e_used = cl ? exp10(bilin(t.le, nt, i, w, j, s)) : e;
+    cs2 = texp10(t, bilin(t.lc, nt, i, w, j, s));
+    if (T) *T = texp10(t, t.lt0 + (j + s) * t.dlt);
+    e_used = cl ? texp10(t, bilin(t.le, nt, i, w, j, s)) : e;
   }
   return cl;
 }
@@ -151,7 +257,7 @@ __device__ __forceinline__ void eos_closure(const Phys &p, double rho, double U,
     Uu = U;
   } else {
     double Pc, c2c, eu;
-    bool cl = eos_invert(p.tab, rho * p.unit_rho, (U / rho) * p.unit_e, Pc, c2c, eu);
+    bool cl = eos_invert(p.tab, rho * p.unit_rho, (U * rcp_nr(rho)) * p.unit_e, Pc, c2c, eu);
     if (cl && cnt) count(&cnt->table_clamp);
     P = Pc * p.inv_unit_p;
     cs2 = c2c * p.inv_unit_e;
@@ -164,7 +270,7 @@ __device__ __forceinline__ void eos_closure(const Phys &p, double rho, double U,
 __device__ __forceinline__ double table_pressure(const Phys &p, double rho, double U,
                                                  Counters *cnt) {
   double Pc, c2c, eu;
-  bool cl = eos_invert<false>(p.tab, rho * p.unit_rho, (U / rho) * p.unit_e, Pc, c2c, eu);
+  bool cl = eos_invert<false>(p.tab, rho * p.unit_rho, (U * rcp_nr(rho)) * p.unit_e, Pc, c2c, eu);
   if (cl && cnt) count(&cnt->table_clamp);
   return Pc * p.inv_unit_p;
 }
@@ -177,7 +283,7 @@ __device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, dou
                                              Counters *cnt) {
   double rho = u[0];
   if (rho < p.rho_floor) { rho = p.rho_floor; if (cnt) count(&cnt->rho_floor); }
-  double ir = 1.0 / rho;
+  double ir = rcp_nr(rho);
   double vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
   double Uc = u[4] - 0.5 * (u[1] * vx + u[2] * vy + u[3] * vz);   // Eq. dual-econs
   double Ue = Uc;
@@ -189,8 +295,8 @@ __device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, dou
   if (P < p.p_floor) { P = p.p_floor; if (cnt) count(&cnt->p_floor); }
   w[0] = rho; w[1] = vx; w[2] = vy; w[3] = vz; w[4] = P;
   if (EOSK == EOS_TABLE) {
-    w[5] = 1.0 + P / Uu;          // Gamma_e
-    w[6] = rho * cs2 / P;         // Gamma_1
+    w[5] = 1.0 + P * rcp_nr(Uu);         // Gamma_e
+    w[6] = rho * cs2 * rcp_nr(P);        // Gamma_1
     if (DUAL) w[7] = u[5];
   } else {
     if (DUAL) w[5] = u[5];

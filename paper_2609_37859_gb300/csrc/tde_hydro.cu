@@ -110,10 +110,13 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
       if (bh.excise && sqrt(r2) < bh.rexc) skip = true;
       if (!skip) {
         const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
-        const double cs = sqrt(g1 * w[4] / w[0]);
+        const double cs = sqrt(g1 * w[4] * rcp_nr(w[0]));
+        // min_d dx_d / (|v_d| + cs) as the reciprocal of the largest signal rate
+        double rate = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          if (p.active[a]) best = fmin(best, p.dx[a] / (fabs(w[1 + a]) + cs));
+          if (p.active[a]) rate = fmax(rate, (fabs(w[1 + a]) + cs) * p.idx[a]);
+        best = fmin(best, rcp_nr(rate));
         if (bh.on) {
           double s2 = r2 + bh.rs2;
           double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
@@ -229,7 +232,7 @@ struct SweepGeo {
 };
 
 template <int D, int RECON, int EOSK, int DUAL, int LAST>
-__global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
   constexpr int LA = SweepGeo<D>::LA, OA = SweepGeo<D>::OA, M = SweepGeo<D>::M;
   constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;   // reconstructed primitives
   constexpr int NVAR = 5 + DUAL;                            // conserved variables

@@ -59,6 +59,7 @@ struct ProfScope {
 struct tde_eos {
   tde_ctx *ctx = nullptr;
   tde::DTable tab{};
+  tde::MathTables *d_mt = nullptr;   // tables of the fast log10 / exp10
   double *d_data = nullptr;          // 3 * n_rho * n_T doubles
   tde::Counters *d_cnt = nullptr;
   // learned guess (tde_mlp.cu): normalisation of inputs and outputs

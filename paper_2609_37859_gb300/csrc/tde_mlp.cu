@@ -298,9 +298,9 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
         cl = rho_cell(t, rho, ti, w);
         const double *__restrict__ ra = t.le + (size_t)ti * t.nt;
         const double *__restrict__ rb = ra + t.nt;
-        glo = (1.0 - w) * __ldg(ra) + w * __ldg(rb);
-        ghi = (1.0 - w) * __ldg(ra + t.nt - 1) + w * __ldg(rb + t.nt - 1);
-        ly = en > 0.0 ? log10(en) : -INFINITY;
+        glo = lerp_rn(w, __ldg(ra), __ldg(rb));
+        ghi = lerp_rn(w, __ldg(ra + t.nt - 1), __ldg(rb + t.nt - 1));
+        ly = en > 0.0 ? tlog10(t, en) : -INFINITY;
         const double lr = t.lr0 + (ti + w) / t.inv_dlr;
         x0 = (float)((lr - a.nm.cr) / a.nm.sr);
         const double z = en > 0.0 ? (ly - glo) / (ghi - glo) : 0.0;
@@ -390,20 +390,19 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
       const int i = ti;
       const double *__restrict__ ra = t.le + (size_t)i * t.nt;
       const double *__restrict__ rb = ra + t.nt;
-      const double w1 = 1.0 - w;
       const double lTg = a.nm.cT + a.nm.sT * (double)y0;
       const double xj = (lTg - t.lt0) / t.dlt;
       bool ok = false;
       double Pv, cv, Tv;
       if (!cl && ly > glo && ly < ghi && xj >= 0.0 && xj < (double)(t.nt - 1)) {
         const int j = (int)floor(xj);
-        const double g0 = w1 * __ldg(ra + j) + w * __ldg(rb + j);
-        const double g1 = w1 * __ldg(ra + j + 1) + w * __ldg(rb + j + 1);
+        const double g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
+        const double g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
         if (g0 <= ly && ly < g1) {
-          const double s = (ly - g0) / (g1 - g0);
-          Pv = exp10(bilin(t.lp, t.nt, i, w, j, s));
-          cv = exp10(bilin(t.lc, t.nt, i, w, j, s));
-          Tv = exp10(t.lt0 + (j + s) * t.dlt);
+          const double s = __dmul_rn(__dsub_rn(ly, g0), rcp_nr(__dsub_rn(g1, g0)));
+          Pv = texp10(t, bilin(t.lp, t.nt, i, w, j, s));
+          cv = texp10(t, bilin(t.lc, t.nt, i, w, j, s));
+          Tv = texp10(t, t.lt0 + (j + s) * t.dlt);
           ok = true;
         }
       }

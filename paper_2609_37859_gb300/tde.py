@@ -110,6 +110,7 @@ _SIGS = {
     "tde_profile": [vp, C.c_int],
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
+    "tde_math_selftest": [vp, C.c_int64, dp, dp, dp],
     "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
                        C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "tde_lat_set_factors": [vp, C.POINTER(C.c_int32), C.c_double],
@@ -264,6 +265,10 @@ class EOS:
 
     def forward(self, x, y):
         self.ctx.check(lib().tde_eos_surrogate_forward(self.h, x.shape[0], _ptr(x), _ptr(y)))
+
+    def math_selftest(self, x, log10_out=None, exp10_out=None):
+        self.ctx.check(lib().tde_math_selftest(self.h, x.numel(), _ptr(x), _ptr(log10_out),
+                                               _ptr(exp10_out)))
 
     def norm(self):
         out = (C.c_double * 8)()
