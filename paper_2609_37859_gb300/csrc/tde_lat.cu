@@ -478,6 +478,9 @@ extern "C" int tde_lat_assign(tde_mesh *m, int n_lat, double merge_frac, double 
 
 extern "C" int tde_lat_set_factors(tde_mesh *m, const int32_t *factors, double dt0) {
   if (!m || !factors || !(dt0 > 0.0)) return m ? lat_fail(m->ctx, TDE_EINVAL, "tde_lat_set_factors: arguments") : TDE_EINVAL;
+  for (int b = 0; b < m->nb; ++b)   // reject before touching the current assignment
+    if (factors[b] < 1 || (factors[b] & (factors[b] - 1)))
+      return lat_fail(m->ctx, TDE_EINVAL, "tde_lat_set_factors: factors must be powers of two >= 1");
   int r = ensure_factor_buffers(m);
   if (r) return r;
   m->h_f.assign(factors, factors + m->nb);

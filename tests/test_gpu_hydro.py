@@ -399,3 +399,90 @@ def test_fast_log10_exp10_against_cuda_libm(tde, ctx, tables):
     ref = torch.pow(10.0, y)
     rel = torch.abs(ex - ref) / ref
     assert float(rel.max()) <= 8 * 2.2e-16, float(rel.max())
+
+
+# ------------------------------------------------ determinism, failure reporting ----
+
+def test_step_is_bitwise_deterministic(oracle, tde, ctx, tables):
+    """Two runs of the same steps give identical bits (no race in the ghost
+    gather, the sweeps' shared-memory phases or the CFL atomics)."""
+    P, _ = c2_pair(oracle, tde, ctx, tables, 32, 16, seed=13)
+    outs = []
+    for _ in range(2):
+        P.gm.U.copy_(torch.from_numpy(P.U))
+        P.gm.set_time(0.0)
+        for _ in range(5):
+            P.gm.step(cfl=0.3)
+        outs.append(P.gpu("U").copy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_bad_state_is_reported_not_trapped(oracle, tde, ctx):
+    """Invalid input (NaN, negative density, negative pressure) is counted by the
+    device counters and floors; the kernels neither trap nor hang."""
+    lay = wl.uniform_layout((16, 16, 16), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    P = Pair(oracle, tde, ctx, lay, wl.random_smooth(lay, seed=1), dual=1, rho_floor=1e-6,
+             p_floor=1e-8, u_floor=1.5e-8)
+    U = P.U.copy()
+    flat = lay.interior_index(3)[0].ravel()
+    U[0, flat[0]] = np.nan           # a NaN density
+    U[0, flat[5]] = -1.0             # a negative density
+    U[4, flat[9]] = -50.0            # negative total energy -> negative pressure
+    P.gm.U.copy_(torch.from_numpy(U))
+    P.gm.counts(reset=True)
+    P.gm.step(dt=1e-4)
+    c = P.gm.counts()
+    assert c["rho_floor"] > 0 and c["p_floor"] + c["dual_aux_used"] > 0
+    assert c["nonfinite"] > 0        # the NaN propagates into its neighbourhood and is counted
+    torch.cuda.synchronize()         # the context is still usable
+    P.gm.U.copy_(torch.from_numpy(P.U))
+    P.gm.step(dt=1e-4)
+    assert np.isfinite(P.gpu("U")).all()
+
+
+def test_table_eos_without_dual_energy(oracle, tde, ctx, tables):
+    """Saha table, dual energy off, PLM, outflow, a hot sound pulse (cgs)."""
+    lay = wl.uniform_layout((24, 16, 16), (8, 8, 8), bc=(0, 1, 0), ng=2)
+    x, y, z = lay.cell_centres()
+    rho = 1e-6 * (1 + 0.3 * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.02))
+    Pr = np.array([tables[0].eval_rhoT(r, 2e4)[0] for r in rho.ravel()]).reshape(rho.shape)
+    W = wl.prim_state(lay, rho, 0 * rho, 0 * rho, 0 * rho, Pr)
+    P = Pair(oracle, tde, ctx, lay, W, tables, eos=1, dual=0, rho_floor=1e-20, p_floor=1e-20)
+    U = P.U.copy()
+    for _ in range(6):
+        d = P.om.cfl_dt(U, 0.3).min()
+        P.om.step(U, d, 0.0)
+        P.gm.step(cfl=0.3)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "table, no dual")
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_one_dimensional_meshes(oracle, tde, ctx, axis):
+    """A single active direction (the other two inactive, no ghosts): Sod along it."""
+    N = [1, 1, 1]
+    N[axis] = 64
+    B = [1, 1, 1]
+    B[axis] = 32
+    lay = wl.uniform_layout(tuple(N), tuple(B), bc=(0, 0, 0), ng=2)
+    P = Pair(oracle, tde, ctx, lay, wl.sod(lay, axis=axis))
+    U = P.U.copy()
+    for _ in range(10):
+        d = P.om.cfl_dt(U, 0.3).min()
+        P.om.step(U, d, 0.0)
+        P.gm.step(cfl=0.3)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "1D")
+
+
+def test_calls_in_the_wrong_order_fail_cleanly(tde, ctx):
+    lay = wl.uniform_layout((8, 8, 8), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    m = tde.Mesh(ctx, lay, tde.make_params())
+    with pytest.raises(tde.TDEError) as ei:
+        m.lat_window()
+    assert ei.value.code == tde.TDE_EINVAL
+    with pytest.raises(tde.TDEError):
+        m.lat_set_factors(np.array([3], dtype=np.int32), 1e-3)   # not a power of two
+    e = tde.EOS.from_file(ctx, TABLE_FILE)
+    r = torch.ones(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(tde.TDEError):   # no trained surrogate yet
+        e.invert(r, r, mode=tde.INVERT_SURROGATE)
+    e.invert(r[:0], r[:0])               # empty input is fine
