@@ -353,6 +353,17 @@ TDE_API int tde_profile_read(tde_ctx *ctx, uint64_t *launches, double *ms);
 TDE_API int tde_math_selftest(tde_eos *eos, int64_t n, const double *x, double *log10_out,
                               double *exp10_out);
 
+/* The reciprocal and square-root building blocks of the hydro kernels, on n
+ * device doubles: TDE_MATH_RCP out = 1/x (refined hardware seed, within one
+ * ulp), TDE_MATH_SQRT_RATIO out = sqrt(x / y) (within about two ulps; x y and
+ * x / y normal), TDE_MATH_RCP_SEED and TDE_MATH_RSQRT_SEED the raw hardware
+ * approximations of 1/x and 1/sqrt(x) that the two refine.  y is read only by
+ * TDE_MATH_SQRT_RATIO.  TDE_EINVAL for an unknown op or null arrays with n > 0;
+ * asynchronous on the context's stream. */
+enum { TDE_MATH_RCP = 0, TDE_MATH_SQRT_RATIO = 1, TDE_MATH_RCP_SEED = 2, TDE_MATH_RSQRT_SEED = 3 };
+TDE_API int tde_math_probe(tde_ctx *ctx, int op, int64_t n, const double *x, const double *y,
+                           double *out);
+
 /* Measured FP64 fused multiply-add throughput of the device (FLOP/s, an FMA
  * counted as 2), from a kernel of independent FMA chains on every SM.  The
  * hydro stage is bound by this rate on sm_103a.  Synchronises the stream. */

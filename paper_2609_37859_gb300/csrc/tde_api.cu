@@ -758,7 +758,36 @@ __global__ void k_math_selftest(const MathTables *mt, long long n, const double 
     if (ex) ex[i] = fast_exp10(mt, x[i]);
   }
 }
+
+__global__ void k_math_probe(int op, long long n, const double *x, const double *y, double *out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = x[i];
+    double r;
+    switch (op) {
+      case TDE_MATH_RCP: r = rcp_nr(a); break;
+      case TDE_MATH_SQRT_RATIO: r = sqrt_ratio(a, y[i]); break;
+      case TDE_MATH_RCP_SEED: r = rcp_seed(a); break;
+      default: r = rsqrt_seed(a); break;
+    }
+    out[i] = r;
+  }
+}
 }  // namespace tde
+
+extern "C" int tde_math_probe(tde_ctx *c, int op, int64_t n, const double *x, const double *y,
+                              double *out) {
+  if (!c) return TDE_EINVAL;
+  if (op < TDE_MATH_RCP || op > TDE_MATH_RSQRT_SEED || n < 0 || (n > 0 && (!x || !out)) ||
+      (n > 0 && op == TDE_MATH_SQRT_RATIO && !y))
+    return fail(c, TDE_EINVAL, "tde_math_probe: arguments");
+  if (n == 0) return TDE_OK;
+  ProfScope ps(c, TDE_K_PROBE);
+  k_math_probe<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(
+      op, (long long)n, x, y, out);
+  CK(c, cudaGetLastError());
+  return TDE_OK;
+}
 
 extern "C" int tde_math_selftest(tde_eos *e, int64_t n, const double *x, double *log10_out,
                                  double *exp10_out) {

@@ -134,18 +134,45 @@ __device__ __forceinline__ void count(unsigned long long *c) {
   if (c) atomicAdd(c, 1ull);
 }
 
-// 1/d by Newton-Raphson (x <- x (2 - d x), written as two FMAs per step) from
-// the hardware's approximate double reciprocal; two steps take the seed's
-// ~2^-23 relative error below the FP64 rounding, so the result is within about
-// one ulp of 1/d.  For normal d whose reciprocal is normal (every use below:
-// sums of same-signed slopes, wave-speed differences, densities).
-__device__ __forceinline__ double rcp_nr(double d) {
+// Hardware seeds: approximate double reciprocal and reciprocal square root
+// (relative error about 2^-20, under 2^-19, over the normal range, measured by
+// tde_math_probe; flush-to-zero).
+__device__ __forceinline__ double rcp_seed(double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  return r;
+}
+__device__ __forceinline__ double rsqrt_seed(double d) {
+  double r;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  return r;
+}
+
+// 1/d from the seed r: with e = 1 - d r, 1/d = r / (1 - e) = r (1 + e + e^2 +
+// e^3 + ...); keeping the terms through e^2 (two FMAs after the residual)
+// leaves a truncation error ~e^3 < 2^-59, far below the FP64 rounding, so the
+// result is within one ulp of 1/d.  For normal d whose reciprocal is normal
+// (every use below: sums of same-signed slopes, wave-speed differences,
+// densities, Gamma_e - 1).
+__device__ __forceinline__ double rcp_nr(double d) {
+  const double r = rcp_seed(d);
+  const double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// sqrt(a / b) for a, b > 0 as a / sqrt(a b): y = seed of 1/sqrt(t), t = a b,
+// e = 1 - t y^2, 1/sqrt(t) = y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2/8 + ...);
+// the truncation error ~(5/16) e^3 is below 2^-61, and the roundings of t, y^2
+// and the final product keep the result within about two ulps of the correctly
+// rounded sqrt(a / b).  For a b and a / b normal (sound speeds: a = Gamma_1 P,
+// b = rho).  Replaces a division and a square root (the wave-speed estimates
+// of the Riemann solver and of the time-step condition).
+__device__ __forceinline__ double sqrt_ratio(double a, double b) {
+  const double t = a * b;
+  const double y = rsqrt_seed(t);
+  const double e = fma(-t, y * y, 1.0);
+  const double y1 = fma(y, e * fma(e, 0.375, 0.5), y);
+  return a * y1;
 }
 
 // ---------------------------------------------------------------- EOS ----
@@ -350,9 +377,9 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
                                      double &vf) {
   const int t1 = D == 0 ? 1 : 0, t2 = D == 2 ? 1 : 2;
   double ul = L.v[D], ur = R.v[D];
-  double cl = sqrt(L.g1 * L.P / L.r), cr = sqrt(R.g1 * R.P / R.r);
-  double Ul = EOSK == EOS_IDEAL ? L.P * p.inv_gm1 : L.P / (L.ge - 1.0);
-  double Ur = EOSK == EOS_IDEAL ? R.P * p.inv_gm1 : R.P / (R.ge - 1.0);
+  double cl = sqrt_ratio(L.g1 * L.P, L.r), cr = sqrt_ratio(R.g1 * R.P, R.r);
+  double Ul = EOSK == EOS_IDEAL ? L.P * p.inv_gm1 : L.P * rcp_nr(L.ge - 1.0);
+  double Ur = EOSK == EOS_IDEAL ? R.P * p.inv_gm1 : R.P * rcp_nr(R.ge - 1.0);
   double El = Ul + 0.5 * L.r * (L.v[0] * L.v[0] + L.v[1] * L.v[1] + L.v[2] * L.v[2]);
   double Er = Ur + 0.5 * R.r * (R.v[0] * R.v[0] + R.v[1] * R.v[1] + R.v[2] * R.v[2]);
   double SL = fmin(ul - cl, ur - cr);

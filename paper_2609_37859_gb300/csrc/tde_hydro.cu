@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
       if (bh.excise && sqrt(r2) < bh.rexc) skip = true;
       if (!skip) {
         const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
-        const double cs = sqrt(g1 * w[4] * rcp_nr(w[0]));
+        const double cs = sqrt_ratio(g1 * w[4], w[0]);
         // min_d dx_d / (|v_d| + cs) as the reciprocal of the largest signal rate
         double rate = 0.0;
 #pragma unroll

@@ -13,6 +13,7 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
+MATH_RCP, MATH_SQRT_RATIO, MATH_RCP_SEED, MATH_RSQRT_SEED = range(4)
 TDE_OK, TDE_EINVAL, TDE_ENOMEM, TDE_ECUDA, TDE_ERANGE, TDE_ENUMERIC, TDE_ETIMEOUT = range(7)
 EOS_IDEAL, EOS_TABLE = 0, 1
 RECON_PLM, RECON_PPM = 0, 1
@@ -111,6 +112,7 @@ _SIGS = {
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
     "tde_math_selftest": [vp, C.c_int64, dp, dp, dp],
+    "tde_math_probe": [vp, C.c_int, C.c_int64, dp, dp, dp],
     "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
                        C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "tde_lat_set_factors": [vp, C.POINTER(C.c_int32), C.c_double],
@@ -195,6 +197,9 @@ class Context:
         f = C.c_double()
         self.check(lib().tde_probe_fp64(self.h, C.byref(f)))
         return f.value
+
+    def math_probe(self, op, x, out, y=None):
+        self.check(lib().tde_math_probe(self.h, op, x.numel(), _ptr(x), _ptr(y), _ptr(out)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -401,6 +401,38 @@ def test_fast_log10_exp10_against_cuda_libm(tde, ctx, tables):
     assert float(rel.max()) <= 8 * 2.2e-16, float(rel.max())
 
 
+def _ulps(got, want):
+    return np.abs(got - want) / np.abs(np.spacing(want))
+
+
+def test_reciprocal_and_sqrt_ratio_against_correct_rounding(tde, ctx):
+    """The refined reciprocal (within one ulp) and sqrt(a / b) (within two ulps)
+    against numpy's correctly rounded IEEE division and square root, and the
+    hardware seeds' error bound that the third-order refinement relies on."""
+    rng = np.random.default_rng(23)
+    n = 400000
+    x = np.concatenate([10 ** rng.uniform(-150, 150, n), rng.uniform(0.5, 2.0, n),
+                        [1.0, 2.0, 3.0, np.nextafter(1.0, 2), np.nextafter(2.0, 0), 1e-300, 1e300]])
+    y = np.concatenate([10 ** rng.uniform(-150, 150, n), rng.uniform(0.5, 2.0, n),
+                        [1.0, 3.0, 7.0, 1.0, 5.0, 1e-5, 1e5]])
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = torch.empty_like(xd)
+
+    def run(op, yy=None):
+        ctx.math_probe(op, xd, out, yy)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    seed_r = run(tde.MATH_RCP_SEED)
+    assert np.abs(seed_r * x - 1).max() < 2.0 ** -19
+    seed_s = run(tde.MATH_RSQRT_SEED)
+    assert np.abs(seed_s * np.sqrt(x) - 1).max() < 2.0 ** -19
+    u = _ulps(run(tde.MATH_RCP), 1.0 / x)
+    assert u.max() <= 1.0, u.max()
+    u = _ulps(run(tde.MATH_SQRT_RATIO, yd), np.sqrt(x / y))
+    assert u.max() <= 2.0, u.max()
+
+
 # ------------------------------------------------ determinism, failure reporting ----
 
 def test_step_is_bitwise_deterministic(oracle, tde, ctx, tables):
