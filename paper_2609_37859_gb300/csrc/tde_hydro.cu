@@ -224,6 +224,12 @@ struct SweepArgs {
   int nvar;
 };
 
+// Sweep CTA width: one thread per cell of a tile's phase-B range, (32 + 2) x 8
+// for 32-cell pencils, so that phases B (34 cells), C (33 faces) and D (32
+// cells) each take a single pass and no warp waits at a barrier for a second
+// pass of another (nine warps, the last half full).
+constexpr int NTS = 272;
+
 template <int D>
 struct SweepGeo {
   static constexpr int LA = D == 0 ? 1 : 0;   // lane axis (transverse, one thread column per lane)
@@ -232,7 +238,7 @@ struct SweepGeo {
 };
 
 template <int D, int RECON, int EOSK, int DUAL, int LAST>
-__global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(NTS, 3) k_sweep(const SweepArgs a) {
   constexpr int LA = SweepGeo<D>::LA, OA = SweepGeo<D>::OA, M = SweepGeo<D>::M;
   constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;   // reconstructed primitives
   constexpr int NVAR = 5 + DUAL;                            // conserved variables
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
   // ---- A: stage the tile's primitives (all pencil cells incl. ghosts)
   {
     const int per = pd * M;
-    for (int e = threadIdx.x; e < NV * per; e += NT) {
+    for (int e = threadIdx.x; e < NV * per; e += NTS) {
       const int v = e / per;
       int pos, lane;
       split(e - v * per, pd, pos, lane);
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
     const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
     double rb[3];
     bh_pos(a.bh, ts, rb);
-    for (int e = threadIdx.x; e < (nd + 2) * M; e += NT) {
+    for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
       int c, lane;
       split(e, nd + 2, c, lane);
       if (lane >= nlane) continue;
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
   __syncthreads();
 
   // ---- B: face values of every cell adjacent to a face of the tile
-  for (int e = threadIdx.x; e < (nd + 2) * M; e += NT) {
+  for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
     int c, lane;
     split(e, nd + 2, c, lane);
     if (lane >= nlane) continue;
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
   __syncthreads();
 
   // ---- C: one HLLC solve per face
-  for (int e = threadIdx.x; e < (nd + 1) * M; e += NT) {
+  for (int e = threadIdx.x; e < (nd + 1) * M; e += NTS) {
     int f, lane;
     split(e, nd + 1, f, lane);
     if (lane >= nlane) continue;
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(NT, 3) k_sweep(const SweepArgs a) {
   // ---- D: divergence, sources; the last direction completes the update
   const double idx = p.idx[D];
   const double hidx = 0.5 * p.idx[D];
-  for (int e = threadIdx.x; e < nd * M; e += NT) {
+  for (int e = threadIdx.x; e < nd * M; e += NTS) {
     int c, lane;
     split(e, nd, c, lane);
     if (lane >= nlane) continue;
@@ -672,14 +678,14 @@ static cudaError_t sweep_one(const SweepArgs &a, bool last, dim3 grid, size_t sm
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       attr[1] = true;
     }
-    k<<<grid, NT, smem, s>>>(a);
+    k<<<grid, NTS, smem, s>>>(a);
   } else {
     auto k = k_sweep<D, RECON, EOSK, DUAL, 0>;
     if (!attr[0]) {
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       attr[0] = true;
     }
-    k<<<grid, NT, smem, s>>>(a);
+    k<<<grid, NTS, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
