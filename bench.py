@@ -283,7 +283,8 @@ def eos_bench(ctx, eos, tde, torch, dev, args):
     del T0
     res = {}
     outs = {}
-    for name, mode in (("bisect", tde.INVERT_BISECT), ("surrogate", tde.INVERT_SURROGATE)):
+    for name, mode in (("bisect_plain", tde.INVERT_BISECT_PLAIN), ("bisect", tde.INVERT_BISECT),
+                       ("surrogate", tde.INVERT_SURROGATE)):
         T, P, c2 = (torch.empty_like(rho) for _ in range(3))
         for _ in range(2):
             eos.invert(rho, e, T=T, P=P, cs2=c2, mode=mode)
@@ -301,11 +302,15 @@ def eos_bench(ctx, eos, tde, torch, dev, args):
         res[name] = {"cells_per_s": EOS_CELLS / (ms * 1e-3), "ms": ms, "accepted": acc,
                      "hbm_gbs": EOS_CELLS * 40 / (ms * 1e-3) * 1e-9}
         outs[name] = (T, P, c2)
-    same = all(torch.equal(a, b) for a, b in zip(outs["bisect"], outs["surrogate"]))
+    same = all(torch.equal(a, b) and torch.equal(a, c)
+               for a, b, c in zip(outs["bisect"], outs["surrogate"], outs["bisect_plain"]))
     return {"workload": "2^24 cells, log10 rho U[-14, 2], log10 T U[%.1f, %.1f] mapped to e by the "
                         "table; outputs T, P, cs2 (40 B/cell)" % EOS_BAND,
-            "bisect": res["bisect"], "surrogate_newton": res["surrogate"],
-            "speedup": res["bisect"]["ms"] / res["surrogate"]["ms"], "identical_results": bool(same),
+            "bisect_plain": res["bisect_plain"], "bisect_fp32_guided": res["bisect"],
+            "surrogate_newton": res["surrogate"],
+            "speedup_vs_plain": res["bisect_plain"]["ms"] / res["surrogate"]["ms"],
+            "speedup_vs_fp32_guided": res["bisect"]["ms"] / res["surrogate"]["ms"],
+            "identical_results": bool(same),
             "training": {"samples": rep["samples"], "epochs": rep["epochs"], "ms": rep["ms"],
                          "loss_first": rep["loss_first"], "loss_last": rep["loss_last"]}}
 

@@ -54,7 +54,7 @@ typedef enum {
 enum { TDE_EOS_IDEAL = 0, TDE_EOS_TABLE = 1 };
 enum { TDE_RECON_PLM = 0, TDE_RECON_PPM = 1 };
 enum { TDE_BC_OUTFLOW = 0, TDE_BC_PERIODIC = 1 };
-enum { TDE_INVERT_BISECT = 0, TDE_INVERT_SURROGATE = 1 };
+enum { TDE_INVERT_BISECT = 0, TDE_INVERT_SURROGATE = 1, TDE_INVERT_BISECT_PLAIN = 2 };
 
 typedef struct tde_ctx tde_ctx;
 typedef struct tde_eos tde_eos;
@@ -128,8 +128,11 @@ TDE_API int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double log10_rh
 TDE_API int tde_eos_destroy(tde_eos *eos);
 
 /* Invert n cells (rho, e) -> (T, P, cs2), all cgs, device arrays of n doubles.
- * mode TDE_INVERT_BISECT: binary search of the interpolated log10 e column.
- * T, P or cs2 may be NULL.  Inputs outside the table are clamped to its edge and
+ * mode TDE_INVERT_BISECT: binary search of the interpolated log10 e column,
+ * carried out in FP32 on a rounded copy of the table and confirmed by the FP64
+ * bracket of the cell (FP64 bisection where FP32 cannot decide);
+ * TDE_INVERT_BISECT_PLAIN: the same search entirely in FP64 (the plain form of
+ * Sec. 4.2's runtime map).  Both give identical results.  T, P or cs2 may be NULL.  Inputs outside the table are clamped to its edge and
  * counted (counts may be NULL; reading it synchronises the stream). */
 TDE_API int tde_eos_invert(tde_eos *eos, int mode, int64_t n, const double *rho, const double *e,
                    double *T, double *P, double *cs2, tde_counts *counts);
@@ -142,11 +145,13 @@ TDE_API int tde_eos_invert(tde_eos *eos, int mode, int64_t n, const double *rho,
  * log10 P ranges (tde_eos_surrogate_norm).  Parameters, 4482 floats:
  *   W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
  * TDE_INVERT_SURROGATE uses the network (BF16 weights; the 64 x 64 layer on the
- * tensor cores, FP32 accumulation) to pick the temperature cell, takes one FP64
- * Newton step on the interpolated log10 e column there and accepts it iff the
- * root lies in that cell -- then the result equals bisection's exactly -- and
- * falls back to bisection otherwise.  The results of both modes are identical;
- * only the work differs. */
+ * tensor cores, FP32 accumulation) to guess log10 T, takes one FP64 Newton step
+ * on the interpolated log10 e column (linear inside a cell) from the guess's
+ * cell, and accepts the cell the step lands in iff the table brackets the root
+ * there -- then the result equals bisection's exactly.  The cells it does not
+ * settle are gathered (warp-aggregated queue) and inverted by bisection in a
+ * second launch.  The results of all modes are identical; only the work
+ * differs. */
 typedef struct {
   double loss_first, loss_last;   /* mean-squared error of the first and last batch */
   int epochs, samples, batches;

@@ -215,30 +215,47 @@ double tref_eos_T_from_P(const tref_table *t, double rho, double P) {
 }
 
 /* Learned-guess inversion (the project's addition to the runtime map of
- * Sec. 4.2): a guessed log10 T selects a temperature cell j of the interpolated
- * log10 e column g at the density weight of rho; one Newton step on g, which is
- * linear inside the cell, gives t = (y - g_j) / (g_{j+1} - g_j).  If 0 <= t < 1
- * the root lies in that cell and the step is exact: the state is evaluated there
- * with the same formulas as tref_eos_invert, so the result is the bisection
- * result itself.  Otherwise (or at a table edge) the plain inversion is used.
- * Returns 1 if the guess was accepted. */
+ * Sec. 4.2): the guessed log10 T is placed in its temperature cell j (clamped
+ * to the table) of the interpolated log10 e column g at the density weight of
+ * rho.  g is linear inside a cell, so one Newton step from the guess lands on
+ * x = j + t, t = (y - g_j) / (g_{j+1} - g_j).  If g_j <= y < g_{j+1} that is the
+ * root; otherwise x lies in cell j' = floor(x), and if the column brackets y
+ * there the root is taken in j'.  Either way the cell is the unique one that
+ * bisection finds and the state is evaluated with the same formulas as
+ * tref_eos_invert, so the result is the bisection result itself.  Otherwise (a
+ * step that misses, a clamped input) the plain inversion is used.  Returns 1 if
+ * the guess was accepted. */
+static double column(const tref_table *t, int i, double w, int j) {
+  const int nT = t->n_T;
+  return (1.0 - w) * t->log10_e[i * nT + j] + w * t->log10_e[(i + 1) * nT + j];
+}
+
 int tref_eos_invert_guess(const tref_table *t, double rho, double e, double log10_T_guess,
                           double *T, double *P, double *cs2) {
   int i; double w;
   int clamped = rho_cell(t, rho, &i, &w);
   const int nT = t->n_T;
-  const double *le = t->log10_e;
-  double glo = (1.0 - w) * le[i * nT] + w * le[(i + 1) * nT];
-  double ghi = (1.0 - w) * le[i * nT + nT - 1] + w * le[(i + 1) * nT + nT - 1];
+  double glo = column(t, i, w, 0), ghi = column(t, i, w, nT - 1);
   double y = (e > 0.0) ? log10(e) : -HUGE_VAL;
   double d = (t->lT_max - t->lT_min) / (nT - 1);
-  double xj = (log10_T_guess - t->lT_min) / d;
   int accepted = 0;
-  if (!clamped && y > glo && y < ghi && xj >= 0.0 && xj < (double)(nT - 1)) {
+  if (!clamped && y > glo && y < ghi) {
+    double xj = (log10_T_guess - t->lT_min) / d;
+    if (!(xj >= 0.0)) xj = 0.0;
+    if (xj > (double)(nT - 2)) xj = (double)(nT - 2);
     int j = (int)floor(xj);
-    double g0 = (1.0 - w) * le[i * nT + j] + w * le[(i + 1) * nT + j];
-    double g1 = (1.0 - w) * le[i * nT + j + 1] + w * le[(i + 1) * nT + j + 1];
-    if (g0 <= y && y < g1) {
+    double g0 = column(t, i, w, j), g1 = column(t, i, w, j + 1);
+    int in = g0 <= y && y < g1;
+    if (!in) {
+      double x = j + (y - g0) / (g1 - g0);   /* the Newton result */
+      if (x >= 0.0 && x < (double)(nT - 1) && (int)floor(x) != j) {
+        j = (int)floor(x);
+        g0 = column(t, i, w, j);
+        g1 = column(t, i, w, j + 1);
+        in = g0 <= y && y < g1;
+      }
+    }
+    if (in) {
       double s = (y - g0) / (g1 - g0);
       *T = pow(10.0, t->lT_min + (j + s) * d);
       *P = pow(10.0, bilin(t->log10_P, nT, i, w, j, s));

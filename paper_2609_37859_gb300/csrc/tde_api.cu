@@ -220,6 +220,9 @@ extern "C" int tde_eos_destroy(tde_eos *e) {
   cudaFree(e->d_w);
   cudaFree(e->d_wb);
   cudaFree(e->d_status);
+  cudaFree(e->d_queue);
+  cudaFree(e->d_guess);
+  cudaFree(e->d_qcount);
   delete e;
   return TDE_OK;
 }
@@ -229,8 +232,8 @@ extern "C" int tde_eos_invert(tde_eos *e, int mode, int64_t n, const double *rho
   if (!e) return TDE_EINVAL;
   tde_ctx *c = e->ctx;
   if (n < 0 || (n > 0 && (!rho || !en))) return fail(c, TDE_EINVAL, "tde_eos_invert: arguments");
-  if (mode == TDE_INVERT_BISECT) {
-    CK(c, launch_eos_invert(e, n, rho, en, T, P, cs2, c->stream));
+  if (mode == TDE_INVERT_BISECT || mode == TDE_INVERT_BISECT_PLAIN) {
+    CK(c, launch_eos_invert(e, n, rho, en, T, P, cs2, c->stream, mode == TDE_INVERT_BISECT_PLAIN));
   } else if (mode == TDE_INVERT_SURROGATE) {
     if (!e->has_net) return fail(c, TDE_EINVAL, "tde_eos_invert: no trained surrogate");
     CK(c, launch_eos_surrogate(e, n, rho, en, T, P, cs2, c->stream));

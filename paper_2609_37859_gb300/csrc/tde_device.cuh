@@ -46,9 +46,9 @@ __device__ __forceinline__ double fast_log10(const MathTables *__restrict__ mt, 
   const int j = upper ? 64 + (int)((mant + (1LL << 45)) >> 46) : 128 + (int)((mant + (1LL << 44)) >> 45);
   const double F = j * (1.0 / 128.0);
   const double r = __dmul_rn(__dsub_rn(m, F), __ldg(&mt->invF[j]));    // |r| <= 2^-7.5
-  // ln(1 + r) = r - r^2/2 + ... - r^8/8
-  double q = -1.0 / 8.0;
-  q = __fma_rn(q, r, 1.0 / 7.0);
+  // ln(1 + r) = r - r^2/2 + ... + r^7/7 (the next term, r^8/8, is below 2^-55.5
+  // relative to the result for |r| <= 2^-7.5)
+  double q = 1.0 / 7.0;
   q = __fma_rn(q, r, -1.0 / 6.0);
   q = __fma_rn(q, r, 1.0 / 5.0);
   q = __fma_rn(q, r, -1.0 / 4.0);
@@ -71,9 +71,9 @@ __device__ __forceinline__ double fast_exp10(const MathTables *__restrict__ mt, 
   const double c_lo = 8.946172576579561e-13;
   const double r = __fma_rn(-n, c_lo, __fma_rn(-n, c_hi, x));   // |r| <= log10(2)/256
   const double u = __dmul_rn(r, 2.302585092994046);             // ln 10
-  // e^u - 1 = u + u^2/2 + ... + u^6/720, |u| <= 2.7e-3
-  double q = 1.0 / 720.0;
-  q = __fma_rn(q, u, 1.0 / 120.0);
+  // e^u - 1 = u + u^2/2 + ... + u^5/120, |u| <= 2.7e-3 (the next term, u^6/720,
+  // is below 2^-60 relative to the result)
+  double q = 1.0 / 120.0;
   q = __fma_rn(q, u, 1.0 / 24.0);
   q = __fma_rn(q, u, 1.0 / 6.0);
   q = __fma_rn(q, u, 0.5);
@@ -206,6 +206,16 @@ __device__ __forceinline__ double bilin(const double *__restrict__ f, int nt, in
   return lerp_rn(w, lo, hi);
 }
 
+// Exact linear solve inside temperature cell j of the interpolated column: the
+// fraction s of the cell at which it reaches y (g0 <= y < g1), and log10 T
+// there.  Shared by every inversion so that all of them compute the same bits.
+__device__ __forceinline__ double cell_solve(double y, double g0, double g1) {
+  return __dmul_rn(__dsub_rn(y, g0), rcp_nr(__dsub_rn(g1, g0)));
+}
+__device__ __forceinline__ double cell_log10T(const DTable &t, int j, double s) {
+  return __fma_rn(__dadd_rn((double)j, s), t.dlt, t.lt0);
+}
+
 // (rho, e) -> P, cs2 (cgs) by binary search of the interpolated log10 e column
 // at fixed density weight, then an exact linear solve inside the cell
 // (Sec. 4.2, runtime map).  Returns true if the input was clamped to the table
@@ -262,12 +272,12 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
       g0 = lerp_rn(w, __ldg(a + j), __ldg(b + j));
       g1 = lerp_rn(w, __ldg(a + j + 1), __ldg(b + j + 1));
     }
-    s = __dmul_rn(__dsub_rn(y, g0), rcp_nr(__dsub_rn(g1, g0)));
+    s = cell_solve(y, g0, g1);
   }
   P = texp10(t, bilin(t.lp, nt, i, w, j, s));
   if (WANT_CS2) {
     cs2 = texp10(t, bilin(t.lc, nt, i, w, j, s));
-    if (T) *T = texp10(t, t.lt0 + (j + s) * t.dlt);
+    if (T) *T = texp10(t, cell_log10T(t, j, s));
     e_used = cl ? texp10(t, bilin(t.le, nt, i, w, j, s)) : e;
   }
   return cl;

@@ -811,12 +811,14 @@ cudaError_t launch_set_dt(tde_mesh *m, double dt) {
 }
 
 cudaError_t launch_eos_invert(tde_eos *e, int64_t n, const double *rho, const double *en,
-                              double *T, double *P, double *cs2, cudaStream_t s) {
+                              double *T, double *P, double *cs2, cudaStream_t s, bool plain) {
   ProfScope _ps(e->ctx, TDE_K_EOS);
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + NT - 1) / NT;
   unsigned g = (unsigned)(blocks < 8LL * n_sm() ? blocks : 8LL * n_sm());
-  k_eos_invert<<<g, NT, 0, s>>>(e->tab, (long long)n, rho, en, T, P, cs2, e->d_cnt);
+  DTable t = e->tab;
+  if (plain) t.le32 = nullptr;   // no FP32 guide: every bisection step in FP64
+  k_eos_invert<<<g, NT, 0, s>>>(t, (long long)n, rho, en, T, P, cs2, e->d_cnt);
   return cudaGetLastError();
 }
 

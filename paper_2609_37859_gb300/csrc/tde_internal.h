@@ -68,6 +68,10 @@ struct tde_eos {
   bool has_net = false;
   float *d_w = nullptr;              // FP32 master weights, then Adam m, v and the gradient
   void *d_wb = nullptr;              // BF16 weights used by training forward and inference
+  long long *d_queue = nullptr;      // cells the surrogate's Newton step left for bisection
+  float *d_guess = nullptr;          // the network's log10 T guess per cell
+  int64_t queue_cap = 0;
+  unsigned long long *d_qcount = nullptr;
   int *d_status = nullptr;
 };
 
@@ -149,7 +153,7 @@ cudaError_t launch_prim2cons(tde_mesh *m, const double *W, double *U);
 cudaError_t launch_advance_time(tde_mesh *m);
 cudaError_t launch_set_dt(tde_mesh *m, double dt);
 cudaError_t launch_eos_invert(tde_eos *e, int64_t n, const double *rho, const double *en,
-                              double *T, double *P, double *cs2, cudaStream_t s);
+                              double *T, double *P, double *cs2, cudaStream_t s, bool plain = false);
 cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const double *en,
                                  double *T, double *P, double *cs2, cudaStream_t s);
 cudaError_t launch_eos_eval(tde_eos *e, int64_t n, const double *rho, const double *T, double *P,

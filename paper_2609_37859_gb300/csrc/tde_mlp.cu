@@ -30,9 +30,17 @@ constexpr int OW1 = 0, OB1 = 2 * H, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 
 
 struct MLPNorm {
   float cr, sr, ce, se, cT, sT, cP, sP;   // x_norm = (x - c) / s
+  float isr, ise;                         // 1 / sr, 1 / se
+  float idlt;                             // 1 / (log10 T cell width)
 };
 
 __device__ __forceinline__ float silu_f(float a) { return a / (1.0f + __expf(-a)); }
+// SiLU for inference with one MUFU operation: sigmoid(a) = (1 + tanh(a / 2)) / 2
+__device__ __forceinline__ float silu_tanh(float a) {
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(0.5f * a));
+  return a * fmaf(0.5f, th, 0.5f);
+}
 __device__ __forceinline__ float dsilu_f(float a) {
   const float s = 1.0f / (1.0f + __expf(-a));
   return s * (1.0f + a * (1.0f - s));
@@ -237,9 +245,10 @@ struct SurrogateArgs {
   const float *xin;   // optional: network inputs instead of (rho, e) [n][2]
   Counters *cnt;
   int *status;        // set to 1 if a bounded wait expired
+  float *lTg;         // optional: the guessed log10 T of each cell
 };
 
-__global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
+__global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   __shared__ __align__(1024) unsigned char sA[IT * H * 2];   // h1, BF16, core-matrix layout
   __shared__ __align__(1024) unsigned char sB[H * H * 2];    // W2, BF16, core-matrix layout
   __shared__ float sW1[2 * H], sb1[H], sb2[H], sW3[2 * H], sb3[2];
@@ -282,10 +291,9 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long c = tile * IT + tid;
     const bool live = c < a.n;
-    // ---- inputs and layer 1 (FP32)
-    double ly = 0.0, rho = 1.0, en = 1.0, w = 0.0, glo = 0.0, ghi = 1.0;
-    int ti = 0;
-    bool cl = true;
+    // ---- inputs and layer 1, FP32 only: the network needs log10 rho and the
+    // position z of log10 e in its column to FP32 accuracy (the FP64 work of
+    // the inversion is k_eos_newton's)
     float x0 = 0.f, x1 = 0.f;
     if (live) {
       if (a.xin) {
@@ -293,18 +301,18 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
         x1 = a.xin[2 * c + 1];
       } else {
         const DTable &t = a.t;
-        rho = a.rho[c];
-        en = a.e[c];
-        cl = rho_cell(t, rho, ti, w);
-        const double *__restrict__ ra = t.le + (size_t)ti * t.nt;
-        const double *__restrict__ rb = ra + t.nt;
-        glo = lerp_rn(w, __ldg(ra), __ldg(rb));
-        ghi = lerp_rn(w, __ldg(ra + t.nt - 1), __ldg(rb + t.nt - 1));
-        ly = en > 0.0 ? tlog10(t, en) : -INFINITY;
-        const double lr = t.lr0 + (ti + w) / t.inv_dlr;
-        x0 = (float)((lr - a.nm.cr) / a.nm.sr);
-        const double z = en > 0.0 ? (ly - glo) / (ghi - glo) : 0.0;
-        x1 = (float)((fmin(fmax(z, -1.0), 2.0) - a.nm.ce) / a.nm.se);
+        const float lr = __log2f((float)a.rho[c]) * 0.30102999566f;
+        const float ly = __log2f((float)a.e[c]) * 0.30102999566f;
+        const float xr = fminf(fmaxf((lr - (float)t.lr0) * (float)t.inv_dlr, 0.f), (float)(t.nr - 1));
+        const int ti = min((int)xr, t.nr - 2);
+        const float w32 = xr - (float)ti;
+        const float *__restrict__ ra = t.le32 + (size_t)ti * t.nt;
+        const float *__restrict__ rb = ra + t.nt;
+        const float glo = fmaf(w32, __ldg(rb) - __ldg(ra), __ldg(ra));
+        const float ghi = fmaf(w32, __ldg(rb + t.nt - 1) - __ldg(ra + t.nt - 1), __ldg(ra + t.nt - 1));
+        x0 = fminf(fmaxf((lr - a.nm.cr) * a.nm.isr, -2.f), 2.f);
+        const float z = __fdividef(ly - glo, ghi - glo);
+        x1 = (fminf(fmaxf(z, -1.f), 2.f) - a.nm.ce) * a.nm.ise;
       }
     }
 #pragma unroll
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int o = 8 * k8 + u;
-        hv[u] = __float2bfloat16_rn(silu_f(sW1[2 * o] * x0 + sW1[2 * o + 1] * x1 + sb1[o]));
+        hv[u] = __float2bfloat16_rn(silu_tanh(sW1[2 * o] * x0 + sW1[2 * o + 1] * x1 + sb1[o]));
       }
       *reinterpret_cast<uint4 *>(sA + core_off(tid, 8 * k8)) = *reinterpret_cast<uint4 *>(hv);
     }
@@ -353,69 +361,36 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
     __syncthreads();
     if (s_abort) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // ---- read the accumulator row of this thread (warp w owns TMEM lanes 32w..32w+31)
-    uint32_t r[64];
-    const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
-        "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63},"
-        " [%64];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
-          "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
-          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    // ---- layer 3 (FP32)
+    // ---- read the accumulator row of this thread (warp w owns TMEM lanes
+    // 32w..32w+31) in two halves of 32 columns, and apply layer 3 (FP32)
     float y0 = sb3[0], y1 = sb3[1];
 #pragma unroll
-    for (int o = 0; o < H; ++o) {
-      const float h2 = silu_f(__uint_as_float(r[o]) + sb2[o]);
-      y0 += sW3[o] * h2;
-      y1 += sW3[H + o] * h2;
+    for (int hf = 0; hf < 2; ++hf) {
+      uint32_t r[32];
+      const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * hf);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+          "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+            "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+            "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+            "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int o = 32 * hf + q;
+        const float h2 = silu_tanh(__uint_as_float(r[q]) + sb2[o]);
+        y0 += sW3[o] * h2;
+        y1 += sW3[H + o] * h2;
+      }
     }
     if (live && a.yout) {
       a.yout[2 * c] = y0;
       a.yout[2 * c + 1] = y1;
     }
-    // ---- FP64 Newton step in the guessed cell, bisection fallback
-    if (live && !a.xin) {
-      const DTable &t = a.t;
-      const int i = ti;
-      const double *__restrict__ ra = t.le + (size_t)i * t.nt;
-      const double *__restrict__ rb = ra + t.nt;
-      const double lTg = a.nm.cT + a.nm.sT * (double)y0;
-      const double xj = (lTg - t.lt0) / t.dlt;
-      bool ok = false;
-      double Pv, cv, Tv;
-      if (!cl && ly > glo && ly < ghi && xj >= 0.0 && xj < (double)(t.nt - 1)) {
-        const int j = (int)floor(xj);
-        const double g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
-        const double g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
-        if (g0 <= ly && ly < g1) {
-          const double s = __dmul_rn(__dsub_rn(ly, g0), rcp_nr(__dsub_rn(g1, g0)));
-          Pv = texp10(t, bilin(t.lp, t.nt, i, w, j, s));
-          cv = texp10(t, bilin(t.lc, t.nt, i, w, j, s));
-          Tv = texp10(t, t.lt0 + (j + s) * t.dlt);
-          ok = true;
-        }
-      }
-      if (ok) {
-        count(&a.cnt->surrogate_accepted);
-      } else {
-        double eu;
-        if (eos_invert(t, rho, en, Pv, cv, eu, &Tv)) count(&a.cnt->table_clamp);
-      }
-      if (a.T) a.T[c] = Tv;
-      if (a.P) a.P[c] = Pv;
-      if (a.cs2) a.cs2[c] = cv;
-    }
+    if (live && a.lTg) a.lTg[c] = a.nm.cT + a.nm.sT * y0;
     // every thread has its row in registers: the next tile may reuse sA and TMEM
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -437,6 +412,116 @@ __global__ void __launch_bounds__(IT) k_eos_surrogate(SurrogateArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(64));
+}
+
+// One FP64 Newton step from the guessed log10 T, judged by the table bracket.
+// The column g is linear inside a temperature cell, so the step from the
+// guess's cell j lands on x = j + s with s the cell solve; if the root is in
+// cell j that is the root itself, otherwise x lies in the cell j' the linear
+// extension points to, and the root is taken there when j' brackets it.  An
+// accepted cell is the one bisection finds (g_j <= y < g_{j+1} is unique) and the
+// state is evaluated with the same formulas, so the result is the bisection
+// result bit for bit.  Cells not settled this way (clamped inputs, a step that
+// misses) are queued for k_eos_fallback; the queue slots of a CTA's 256 cells
+// are reserved with one atomic, and the accepted count is added once per CTA.
+__global__ void __launch_bounds__(256) k_eos_newton(DTable t, const float *__restrict__ lTg,
+                                                    float idlt, long long n,
+                                                    const double *__restrict__ rho,
+                                                    const double *__restrict__ en, double *T, double *P,
+                                                    double *cs2, Counters *cnt, long long *queue,
+                                                    unsigned long long *qcount) {
+  __shared__ unsigned s_wc[8];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned s_acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = t.nt;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned n_acc = 0;
+  // every lane runs the same number of iterations (the warp votes below)
+  for (long long c0 = blockIdx.x * (long long)blockDim.x; c0 < n; c0 += stride) {
+    const long long c = c0 + threadIdx.x;
+    bool ok = true, acc = false;
+    if (c < n) {
+      int i;
+      double w;
+      const bool cl = rho_cell(t, rho[c], i, w);
+      const double e = en[c];
+      const double ly = e > 0.0 ? tlog10(t, e) : -INFINITY;
+      const double *__restrict__ ra = t.le + (size_t)i * nt;
+      const double *__restrict__ rb = ra + nt;
+      ok = false;
+      if (!cl && ly > -INFINITY) {
+        const float xg = (lTg[c] - (float)t.lt0) * idlt;
+        int j = (int)floorf(fminf(fmaxf(xg, 0.f), (float)(nt - 2)));
+        j = min(max(j, 0), nt - 2);
+        double g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
+        double g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
+        double sc = cell_solve(ly, g0, g1);
+        bool in = g0 <= ly && ly < g1;
+        if (!in) {
+          const double xn = (double)j + sc;   // the Newton result, in cell units
+          if (xn >= 0.0 && xn < (double)(nt - 1)) {
+            const int j2 = (int)floor(xn);
+            if (j2 != j) {
+              j = j2;
+              g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
+              g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
+              in = g0 <= ly && ly < g1;
+              if (in) sc = cell_solve(ly, g0, g1);
+            }
+          }
+        }
+        // at the coldest node bisection clamps (y <= g_0): leave that to it
+        ok = in && (j > 0 || ly > g0);
+        if (ok) {
+          if (P) P[c] = texp10(t, bilin(t.lp, nt, i, w, j, sc));
+          if (cs2) cs2[c] = texp10(t, bilin(t.lc, nt, i, w, j, sc));
+          if (T) T[c] = texp10(t, cell_log10T(t, j, sc));
+          acc = true;
+        }
+      }
+    }
+    n_acc += acc ? 1u : 0u;
+    const unsigned rm = __ballot_sync(0xffffffffu, !ok);
+    if (lane == 0) s_wc[warp] = __popc(rm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned tot = 0;
+      for (int q = 0; q < 8; ++q) {
+        const unsigned v = s_wc[q];
+        s_wc[q] = tot;   // exclusive prefix over the warps
+        tot += v;
+      }
+      s_base = tot ? atomicAdd(qcount, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (!ok) queue[s_base + s_wc[warp] + __popc(rm & ((1u << lane) - 1u))] = c;
+    __syncthreads();   // s_wc and s_base are rewritten by the next iteration
+  }
+  // accepted cells: one atomic per CTA
+  for (int o = 16; o > 0; o >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
+  if (threadIdx.x == 0) s_acc = 0;
+  __syncthreads();
+  if (lane == 0) atomicAdd(&s_acc, n_acc);
+  __syncthreads();
+  if (threadIdx.x == 0 && cnt && s_acc) atomicAdd(&cnt->surrogate_accepted, (unsigned long long)s_acc);
+}
+
+// Table bisection for the cells the Newton step left (their indices in queue).
+__global__ void __launch_bounds__(256) k_eos_fallback(DTable t, const long long *__restrict__ queue,
+                                                      const unsigned long long *__restrict__ qcount,
+                                                      const double *__restrict__ rho,
+                                                      const double *__restrict__ e, double *T, double *P,
+                                                      double *cs2, Counters *cnt) {
+  const long long nq = (long long)*qcount;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long c = queue[q];
+    double Pv, cv, eu, Tv;
+    if (eos_invert(t, rho[c], e[c], Pv, cv, eu, &Tv)) count(&cnt->table_clamp);
+    if (T) T[c] = Tv;
+    if (P) P[c] = Pv;
+    if (cs2) cs2[c] = cv;
+  }
 }
 
 }  // namespace tde
@@ -469,6 +554,9 @@ MLPNorm norm_of(const tde_eos *e) {
   n.ce = (float)e->norm[2]; n.se = (float)e->norm[3];
   n.cT = (float)e->norm[4]; n.sT = (float)e->norm[5];
   n.cP = (float)e->norm[6]; n.sP = (float)e->norm[7];
+  n.isr = (float)(1.0 / e->norm[1]);
+  n.ise = (float)(1.0 / e->norm[3]);
+  n.idlt = (float)(1.0 / e->tab.dlt);
   return n;
 }
 
@@ -514,7 +602,7 @@ cudaError_t launch_grad(tde_eos *e, const float *x, const float *tg, long long s
 
 cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, const double *en,
                                     double *T, double *P, double *cs2, const float *xin, float *yout,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, float *lTg = nullptr) {
   SurrogateArgs a;
   a.t = e->tab;
   a.nm = norm_of(e);
@@ -529,10 +617,17 @@ cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, 
   a.xin = xin;
   a.cnt = e->d_cnt;
   a.status = e->d_status;
+  a.lTg = lTg;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
+  // one wave of resident CTAs: registers (64 x 128 threads) and shared memory
+  // (26 KB, largest carveout) admit 8 per SM, and 8 x 64 TMEM columns fill the
+  // SM's 512 exactly
+  cudaFuncSetAttribute(k_eos_surrogate, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+  const int per_sm = 8;
   const long long tiles = (n + IT - 1) / IT;
-  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * 8);
+  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
   k_eos_surrogate<<<grid, IT, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -543,8 +638,35 @@ namespace tde {
 cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const double *en,
                                  double *T, double *P, double *cs2, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if (e->queue_cap < n) {
+    cudaFree(e->d_queue);
+    cudaFree(e->d_guess);
+    e->d_queue = nullptr;
+    e->d_guess = nullptr;
+    e->queue_cap = 0;
+    cudaError_t r = cudaMalloc(&e->d_queue, sizeof(long long) * (size_t)n);
+    if (r == cudaSuccess) r = cudaMalloc(&e->d_guess, sizeof(float) * (size_t)n);
+    if (r != cudaSuccess) return r;
+    e->queue_cap = n;
+  }
+  if (!e->d_qcount) {
+    cudaError_t r = cudaMalloc(&e->d_qcount, sizeof(unsigned long long));
+    if (r != cudaSuccess) return r;
+  }
   ProfScope ps(e->ctx, TDE_K_EOS);
-  return launch_surrogate_kernel(e, n, rho, en, T, P, cs2, nullptr, nullptr, s);
+  cudaError_t r = cudaMemsetAsync(e->d_qcount, 0, sizeof(unsigned long long), s);
+  if (r != cudaSuccess) return r;
+  r = launch_surrogate_kernel(e, n, rho, en, nullptr, nullptr, nullptr, nullptr, nullptr, s, e->d_guess);
+  if (r != cudaSuccess) return r;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
+  const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sms * 8);
+  k_eos_newton<<<grid, 256, 0, s>>>(e->tab, e->d_guess, (float)(1.0 / e->tab.dlt), n, rho, en, T, P,
+                                    cs2, e->d_cnt, e->d_queue, e->d_qcount);
+  r = cudaGetLastError();
+  if (r != cudaSuccess) return r;
+  k_eos_fallback<<<grid, 256, 0, s>>>(e->tab, e->d_queue, e->d_qcount, rho, en, T, P, cs2, e->d_cnt);
+  return cudaGetLastError();
 }
 }  // namespace tde
 

@@ -18,7 +18,7 @@ TDE_OK, TDE_EINVAL, TDE_ENOMEM, TDE_ECUDA, TDE_ERANGE, TDE_ENUMERIC, TDE_ETIMEOU
 EOS_IDEAL, EOS_TABLE = 0, 1
 RECON_PLM, RECON_PPM = 0, 1
 BC_OUTFLOW, BC_PERIODIC = 0, 1
-INVERT_BISECT, INVERT_SURROGATE = 0, 1
+INVERT_BISECT, INVERT_SURROGATE, INVERT_BISECT_PLAIN = 0, 1, 2
 STATUS = {0: "TDE_OK", 1: "TDE_EINVAL", 2: "TDE_ENOMEM", 3: "TDE_ECUDA", 4: "TDE_ERANGE",
           5: "TDE_ENUMERIC", 6: "TDE_ETIMEOUT"}
 

@@ -197,3 +197,35 @@ def test_invert_from_guess_equals_bisection(saha_table):
     # out of range input: never accepted, clamped like the plain inversion
     T, P2, c22, acc = t.invert_guess(1e-20, 1e10, 3.0)
     assert not acc and (T, P2, c22) == t.invert(1e-20, 1e10)[:3]
+
+
+def test_guess_acceptance_rule_brute_force(saha_table):
+    """Acceptance is decided by where the one Newton step lands: a guess k cells
+    off is accepted exactly when the cell of j + (y - g_j) / (g_{j+1} - g_j),
+    recomputed here from the table arrays, brackets y (or j itself does)."""
+    t = saha_table
+    rng = np.random.default_rng(31)
+    nT = t.n_T
+    d = 6.0 / (nT - 1)
+    le = t.log10_e
+    seen = {True: 0, False: 0}
+    for k in range(2000):
+        lr = rng.uniform(-13.9, 1.9)
+        lT = rng.uniform(2.05, 7.95)
+        e = t.eval_rhoT(10 ** lr, 10 ** lT)[1]
+        x = (np.log10(10 ** lr) + 14.0) * (nT - 1) / 16.0
+        i = min(int(np.floor(x)), t.n_rho - 2)
+        w = x - i
+        g = (1 - w) * le[i] + w * le[i + 1]       # the column at this density
+        y = np.log10(e)
+        jt = int(np.searchsorted(g, y, side="right") - 1)   # the bracketing cell
+        off = int(rng.integers(-4, 5))
+        jg = min(max(jt + off, 0), nT - 2)
+        guess = 2.0 + (jg + 0.5) * d
+        xn = jg + (y - g[jg]) / (g[jg + 1] - g[jg])
+        predict = jg == jt or (0 <= xn < nT - 1 and int(np.floor(xn)) == jt)
+        _, _, _, acc = t.invert_guess(10 ** lr, e, guess)
+        if abs(xn - round(xn)) > 1e-9:       # skip landings within rounding of a node
+            assert acc == predict, (k, off, jg, jt, xn)
+            seen[acc] += 1
+    assert seen[True] > 500 and seen[False] > 100
