@@ -358,6 +358,26 @@ TDE_API int tde_profile_read(tde_ctx *ctx, uint64_t *launches, double *ms);
 TDE_API int tde_math_selftest(tde_eos *eos, int64_t n, const double *x, double *log10_out,
                               double *exp10_out);
 
+/* ---- sweep tile shapes and their autotuner (a9) -----------------------------
+ * A sweep CTA works on a tile of pencils of one block along the sweep direction.
+ * Shapes (index: lanes per tile, threads per CTA): 0: 8 x 272 (default), 1: 16 x
+ * 288, 2: 4 x 160; a shape whose tile needs more than 227 KB of shared memory for
+ * the mesh's block size is not available.  Results do not depend on the shape
+ * (every face and cell is computed by the same operations); only the time does.
+ *
+ * tde_mesh_autotune times every available shape per active direction over all
+ * blocks of the bound state (reps timed launches after one warm-up, CUDA events)
+ * and keeps the fastest; bh (may be NULL) is the point mass the timing includes.
+ * It reads the state and writes only scratch memory: state, counters and time are
+ * unchanged.  tiles (may be NULL) receives the chosen shape per direction x, y, z;
+ * ms (may be NULL) receives [3][3] mean launch times (-1 where a shape was not
+ * run).  Synchronises the stream.  tde_mesh_set_tiles forces shapes (TDE_EINVAL
+ * for an unknown or too large shape); tde_mesh_get_tiles reads them. */
+TDE_API int tde_mesh_autotune(tde_mesh *mesh, const tde_bh_state *bh, int reps, int32_t *tiles,
+                              float *ms);
+TDE_API int tde_mesh_set_tiles(tde_mesh *mesh, const int32_t *tiles);
+TDE_API int tde_mesh_get_tiles(const tde_mesh *mesh, int32_t *tiles);
+
 /* The reciprocal and square-root building blocks of the hydro kernels, on n
  * device doubles: TDE_MATH_RCP out = 1/x (refined hardware seed, within one
  * ulp), TDE_MATH_SQRT_RATIO out = sqrt(x / y) (within about two ulps; x y and

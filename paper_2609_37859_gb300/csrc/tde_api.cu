@@ -660,6 +660,39 @@ extern "C" int tde_step(tde_mesh *m, double cfl, double dt_fixed, const tde_bh_s
   return TDE_OK;
 }
 
+extern "C" int tde_mesh_set_tiles(tde_mesh *m, const int32_t *tiles) {
+  if (!m) return TDE_EINVAL;
+  if (!tiles) return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_tiles: null");
+  for (int D = 0; D < 3; ++D)
+    if (tiles[D] < 0 || tiles[D] >= N_SWEEP_SHAPES || sweep_smem_for(m, D, tiles[D]) > 227 * 1024)
+      return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_tiles: unknown shape or tile too large");
+  for (int D = 0; D < 3; ++D) m->tile[D] = tiles[D];
+  invalidate_graph(m);
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_get_tiles(const tde_mesh *m, int32_t *tiles) {
+  if (!m || !tiles) return TDE_EINVAL;
+  for (int D = 0; D < 3; ++D) tiles[D] = m->tile[D];
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_autotune(tde_mesh *m, const tde_bh_state *bhs, int reps, int32_t *tiles,
+                                 float *ms) {
+  if (!m) return TDE_EINVAL;
+  if (!m->U || !m->U1) return fail(m->ctx, TDE_EINVAL, "tde_mesh_autotune: no bound state");
+  if (reps < 1) return fail(m->ctx, TDE_EINVAL, "tde_mesh_autotune: reps < 1");
+  float t[3][N_SWEEP_SHAPES];
+  CK(m->ctx, autotune_sweeps(m, make_bh(bhs), reps, t));
+  invalidate_graph(m);
+  if (tiles)
+    for (int D = 0; D < 3; ++D) tiles[D] = m->tile[D];
+  if (ms)
+    for (int D = 0; D < 3; ++D)
+      for (int k = 0; k < N_SWEEP_SHAPES; ++k) ms[D * N_SWEEP_SHAPES + k] = t[D][k];
+  return TDE_OK;
+}
+
 extern "C" int tde_counts_read(tde_mesh *m, tde_counts *out, int reset) {
   if (!m || !out) return TDE_EINVAL;
   Counters h;

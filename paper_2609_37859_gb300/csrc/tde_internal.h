@@ -83,6 +83,7 @@ struct tde_mesh {
   tde_grid_desc grid{};
   int nb = 0;
   int nmax[3] = {0, 0, 0};           // largest interior block edge per direction
+  int tile[3] = {0, 0, 0};           // sweep tile shape per direction (kTileShapes index)
   int64_t ntot = 0;
   int64_t max_interior = 0;          // largest interior cell count of a block
   int max_ghosts = 0;                // largest ghost count of a block
@@ -146,6 +147,10 @@ cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double
                           double *freg = nullptr);
 cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids);
 size_t sweep_smem_max(const tde_mesh *m);
+size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
+constexpr int N_SWEEP_SHAPES = 3;
+cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3][N_SWEEP_SHAPES]);
+void invalidate_graph(tde_mesh *m);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);
 cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2);

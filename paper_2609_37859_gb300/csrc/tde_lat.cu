@@ -283,6 +283,14 @@ __global__ void __launch_bounds__(LNT) k_reflux(Phys p, BH bh, OwnerLattice ol,
   }
 }
 
+// A captured LAT window is stale once the mesh's launch configuration changes.
+void invalidate_graph(tde_mesh *m) {
+  if (m->lat_graph) {
+    cudaGraphExecDestroy(m->lat_graph);
+    m->lat_graph = nullptr;
+  }
+}
+
 }  // namespace tde
 
 using namespace tde;
@@ -303,12 +311,6 @@ int lat_fail(tde_ctx *c, int code, const char *msg) {
     }                                                                        \
   } while (0)
 
-void invalidate_graph(tde_mesh *m) {
-  if (m->lat_graph) {
-    cudaGraphExecDestroy(m->lat_graph);
-    m->lat_graph = nullptr;
-  }
-}
 
 // host-side level lists from the factors; allocates the LAT buffers once
 int lat_build(tde_mesh *m) {

@@ -1,0 +1,356 @@
+// tde_sweep.cuh -- the per-direction sweep kernel of the hydro stage
+// (reconstruction, HLLC, flux divergence, sources, and on the last direction
+// the stage update), templated on the tile shape, and the device helpers it
+// shares with the other hydro kernels.
+#pragma once
+#include <math.h>
+
+#include "tde_internal.h"
+
+namespace tde {
+
+__device__ __forceinline__ double ta_t(const TimeArgs &ta, int b) {
+  return ta.t ? ta.t[ta.t_pb ? b : 0] : 0.0;
+}
+__device__ __forceinline__ double ta_dt(const TimeArgs &ta, int b) {
+  return ta.dt ? ta.dt[ta.dt_pb ? b : 0] : 0.0;
+}
+
+__device__ __forceinline__ void bh_pos(const BH &bh, double t, double r[3]) {
+  double s = t - bh.t0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r[a] = bh.x0[a] + bh.v0[a] * s + 0.5 * bh.a0[a] * s * s;
+}
+
+// centre of padded cell c[] of block B; periodic directions wrap to the image
+__device__ __forceinline__ void cell_centre(const Phys &p, const DevBlock &B, const int c[3],
+                                            double x[3]) {
+  const int o[3] = {B.i0, B.j0, B.k0};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int g = o[a] + c[a] - p.g[a];
+    if (p.bc[a] == 1) {
+      g %= p.N[a];
+      if (g < 0) g += p.N[a];
+    }
+    x[a] = p.xmin[a] + (g + 0.5) * p.dx[a];
+  }
+}
+
+// ---------------------------------------------------------- k_sweep ----
+
+struct SweepArgs {
+  Phys p;
+  BH bh;
+  TimeArgs ta;
+  const DevBlock *blocks;
+  const int32_t *ids;
+  const double *W;
+  double *dU;
+  const double *U0;
+  const double *Uin;
+  double *Uout;
+  long long ntot;
+  Counters *cnt;
+  int stage, first, PD, NF;
+  double *freg;              // flux impulse registers (LAT) or null
+  const long long *fo;       // register offset per block
+  int nvar;
+};
+
+// A sweep tile is M pencils (lanes) of one block along D; its CTA has NTS
+// threads.  NTS = (n + 2) M for pencils of n cells makes phases B (n + 2 cells),
+// C (n + 1 faces) and D (n cells) each a single pass, so no warp waits at a
+// barrier for another warp's second pass.  The shapes offered (tile_shapes)
+// are chosen per direction by tde_mesh_autotune; every shape computes the same
+// operations on the same data, so results do not depend on the choice.
+template <int D>
+struct SweepGeo {
+  static constexpr int LA = D == 0 ? 1 : 0;   // lane axis (transverse, one thread column per lane)
+  static constexpr int OA = D == 2 ? 1 : 2;   // other transverse axis (one CTA per index)
+};
+
+template <int D, int RECON, int EOSK, int DUAL, int LAST, int M, int NTS, int MINB>
+__global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
+  constexpr int LA = SweepGeo<D>::LA, OA = SweepGeo<D>::OA;
+  constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;   // reconstructed primitives
+  constexpr int NVAR = 5 + DUAL;                            // conserved variables
+  extern __shared__ double sm[];
+  const Phys &p = a.p;
+  const int b = a.ids[blockIdx.y];
+  const DevBlock B = a.blocks[b];
+  const int nd = B.n[D], nl = B.n[LA], no = B.n[OA];
+  const int nlc = (nl + M - 1) / M;
+  if ((int)blockIdx.x >= nlc * no) return;
+  const int l0 = (blockIdx.x % nlc) * M, o = blockIdx.x / nlc;
+  const int nlane = min(M, nl - l0);
+  const int g = p.g[D], pd = B.p[D];
+  const long long st[3] = {1, B.p[0], (long long)B.p[0] * B.p[1]};
+  const long long sD = st[D], sL = st[LA];
+  const long long base = B.off + (long long)(p.g[LA] + l0) * sL + (long long)(p.g[OA] + o) * st[OA];
+  const int PD = a.PD, NF = a.NF, NFF = a.NF - 1;
+  const long long ntot = a.ntot;
+
+  double *Wt = sm;                       // [NV][PD][M]  primitives of the tile
+  double *FMs = Wt + NV * PD * M;        // [NV][NF][M]  value at the low face of cells g-1 .. g+nd
+  double *FPs = FMs + NV * NF * M;       // [NV][NF][M]  value at the high face
+  double *Fl = FPs + NV * NF * M;        // [7][NFF][M]  fluxes and face velocity
+  double *Ph = Fl + 7 * NFF * M;         // [NF][M]      potential of cells g-1 .. g+nd
+  unsigned char *Ex = reinterpret_cast<unsigned char *>(Ph + NF * M);   // [NF][M] excised
+
+  // shared-memory indices: D = 0 keeps the pencil axis contiguous (it is
+  // contiguous in global memory too), D = 1, 2 keep the lane axis contiguous
+  auto sw = [&](int v, int pos, int lane) {
+    return D == 0 ? (v * M + lane) * PD + pos : (v * PD + pos) * M + lane;
+  };
+  auto sf = [&](int v, int c, int lane) {
+    return D == 0 ? (v * M + lane) * NF + c : (v * NF + c) * M + lane;
+  };
+  auto sfl = [&](int q, int f, int lane) {
+    return D == 0 ? (q * M + lane) * NFF + f : (q * NFF + f) * M + lane;
+  };
+  auto split = [&](int e, int len, int &c, int &lane) {
+    if (D == 0) { lane = e / len; c = e - lane * len; }
+    else { c = e / M; lane = e - c * M; }
+  };
+
+  // ---- A: stage the tile's primitives (all pencil cells incl. ghosts)
+  {
+    const int per = pd * M;
+    for (int e = threadIdx.x; e < NV * per; e += NTS) {
+      const int v = e / per;
+      int pos, lane;
+      split(e - v * per, pd, pos, lane);
+      if (lane < nlane) Wt[sw(v, pos, lane)] = a.W[v * ntot + base + pos * sD + lane * sL];
+    }
+  }
+  const bool grav = a.bh.on, exc = a.bh.excise;
+  if (grav || exc) {
+    const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
+    double rb[3];
+    bh_pos(a.bh, ts, rb);
+    for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
+      int c, lane;
+      split(e, nd + 2, c, lane);
+      if (lane >= nlane) continue;
+      int cc[3];
+      cc[D] = g - 1 + c;
+      cc[LA] = p.g[LA] + l0 + lane;
+      cc[OA] = p.g[OA] + o;
+      double x[3];
+      cell_centre(p, B, cc, x);
+      const double dx0 = x[0] - rb[0], dx1 = x[1] - rb[1], dx2 = x[2] - rb[2];
+      const double r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
+      const int idx = D == 0 ? lane * NF + c : c * M + lane;
+      if (grav) Ph[idx] = -a.bh.GM / sqrt(r2 + a.bh.rs2);
+      if (exc) Ex[idx] = sqrt(r2) < a.bh.rexc ? 1 : 0;
+    }
+  }
+  __syncthreads();
+
+  // ---- B: face values of every cell adjacent to a face of the tile
+  for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
+    int c, lane;
+    split(e, nd + 2, c, lane);
+    if (lane >= nlane) continue;
+    const int pos = g - 1 + c;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double lo, hi;
+      if (RECON == PLM) {
+        plm(Wt[sw(v, pos - 1, lane)], Wt[sw(v, pos, lane)], Wt[sw(v, pos + 1, lane)], lo, hi);
+      } else {
+        const double qm2 = Wt[sw(v, pos - 2, lane)], qm1 = Wt[sw(v, pos - 1, lane)];
+        const double q0 = Wt[sw(v, pos, lane)], qp1 = Wt[sw(v, pos + 1, lane)];
+        const double qp2 = Wt[sw(v, pos + 2, lane)];
+        lo = ppm_iface(qm2, qm1, q0, qp1);
+        hi = ppm_iface(qm1, q0, qp1, qp2);
+        ppm_limit(q0, lo, hi);
+      }
+      FMs[sf(v, c, lane)] = lo;
+      FPs[sf(v, c, lane)] = hi;
+    }
+  }
+  __syncthreads();
+
+  // ---- C: one HLLC solve per face
+  for (int e = threadIdx.x; e < (nd + 1) * M; e += NTS) {
+    int f, lane;
+    split(e, nd + 1, f, lane);
+    if (lane >= nlane) continue;
+    FState L, R;
+    L.r = FPs[sf(0, f, lane)];
+    R.r = FMs[sf(0, f + 1, lane)];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      L.v[q] = FPs[sf(1 + q, f, lane)];
+      R.v[q] = FMs[sf(1 + q, f + 1, lane)];
+    }
+    L.P = FPs[sf(4, f, lane)];
+    R.P = FMs[sf(4, f + 1, lane)];
+    if (EOSK == EOS_TABLE) {
+      L.ge = FPs[sf(5, f, lane)]; R.ge = FMs[sf(5, f + 1, lane)];
+      L.g1 = FPs[sf(6, f, lane)]; R.g1 = FMs[sf(6, f + 1, lane)];
+    } else {
+      L.ge = L.g1 = R.ge = R.g1 = p.gamma;
+    }
+    if (DUAL) {
+      L.A = FPs[sf(NV - 1, f, lane)];
+      R.A = FMs[sf(NV - 1, f + 1, lane)];
+    } else {
+      L.A = R.A = 0.0;
+    }
+    double F[6], vf;
+    hllc<D, EOSK, DUAL>(p, L, R, F, vf);
+    if (exc) {
+      const int il = D == 0 ? lane * NF + f : f * M + lane;
+      const int ir = D == 0 ? lane * NF + f + 1 : (f + 1) * M + lane;
+      if (Ex[il] != Ex[ir]) {
+        const bool into = Ex[ir] ? (F[0] > 0.0) : (F[0] < 0.0);
+        if (!into) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) F[q] = 0.0;
+          vf = 0.0;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NVAR; ++q) Fl[sfl(q, f, lane)] = F[q];
+    if (DUAL) Fl[sfl(6, f, lane)] = vf;
+    if (a.freg && (f == 0 || f == nd)) {
+      // time integral dt (F^1 + F^2) / 2 of a boundary face (Eq. lat-flux-impulse);
+      // register sides x-, x+, y-, y+, z-, z+, each [nvar][n_OA][n_LA]
+      long long so = a.fo[b];
+      const int side = 2 * D + (f == nd ? 1 : 0);
+      for (int s = 0; s < side; ++s) {
+        const int aa = s >> 1;
+        const int u1 = aa == 0 ? 1 : 0, u2 = aa == 2 ? 1 : 2;
+        so += (long long)B.n[u1] * B.n[u2] * a.nvar;
+      }
+      const long long ncell = (long long)nl * no;
+      const long long cidx = (long long)o * nl + l0 + lane;
+      const double w = 0.5 * ta_dt(a.ta, b);
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) a.freg[so + q * ncell + cidx] += w * F[q];
+    }
+  }
+  __syncthreads();
+
+  // ---- D: divergence, sources; the last direction completes the update
+  const double idx = p.idx[D];
+  const double hidx = 0.5 * p.idx[D];
+  for (int e = threadIdx.x; e < nd * M; e += NTS) {
+    int c, lane;
+    split(e, nd, c, lane);
+    if (lane >= nlane) continue;
+    const long long flat = base + (long long)(g + c) * sD + lane * sL;
+    double acc[NVAR], dv = 0.0;
+#pragma unroll
+    for (int q = 0; q < NVAR; ++q) acc[q] = a.first ? 0.0 : a.dU[q * ntot + flat];
+    if (DUAL) dv = a.first ? 0.0 : a.dU[NVAR * ntot + flat];
+#pragma unroll
+    for (int q = 0; q < NVAR; ++q) acc[q] -= (Fl[sfl(q, c + 1, lane)] - Fl[sfl(q, c, lane)]) * idx;
+    if (DUAL) dv += (Fl[sfl(6, c + 1, lane)] - Fl[sfl(6, c, lane)]) * idx;
+    if (grav) {
+      const int i0 = D == 0 ? lane * NF + c : c * M + lane;
+      const int i1 = D == 0 ? i0 + 1 : i0 + M;
+      const int i2 = D == 0 ? i0 + 2 : i0 + 2 * M;
+      const double phm = Ph[i0], ph0 = Ph[i1], php = Ph[i2];
+      const double rho = Wt[sw(0, g + c, lane)];
+      acc[1 + D] -= rho * (php - phm) * hidx;
+      acc[4] -= (Fl[sfl(0, c + 1, lane)] * (php - ph0) + Fl[sfl(0, c, lane)] * (ph0 - phm)) * hidx;
+    }
+    if (!LAST) {
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) a.dU[q * ntot + flat] = acc[q];
+      if (DUAL) a.dU[NVAR * ntot + flat] = dv;
+    } else {
+      const double dt = ta_dt(a.ta, b);
+      double un[NVAR];
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) {
+        const double u0 = a.U0[q * ntot + flat];
+        un[q] = a.stage == 0 ? u0 + dt * acc[q] : 0.5 * (u0 + (a.Uin[q * ntot + flat] + dt * acc[q]));
+      }
+      if (un[0] < p.rho_floor) { un[0] = p.rho_floor; count(&a.cnt->rho_floor); }
+      if (DUAL) {
+        const double dtl = a.stage == 0 ? dt : 0.5 * dt;
+        if (EOSK == EOS_IDEAL) {
+          un[5] = un[5] * exp(-p.gm1 * dv * dtl);
+        } else {
+          const double Pa = table_pressure(p, un[0], un[5], a.cnt);
+          un[5] = un[5] - Pa * dv * dtl;
+        }
+        if (un[5] < p.u_floor) { un[5] = p.u_floor; count(&a.cnt->u_floor); }
+      }
+      bool bad = !(un[0] > 0.0);
+#pragma unroll
+      for (int q = 0; q < NVAR; ++q) {
+        bad |= !isfinite(un[q]);
+        a.Uout[q * ntot + flat] = un[q];
+      }
+      if (bad) count(&a.cnt->nonfinite);
+    }
+  }
+}
+
+// ============================================================ launchers ====
+
+template <int D, int RECON, int EOSK, int DUAL, int M, int NTS, int MINB>
+cudaError_t sweep_one(const SweepArgs &a, bool last, dim3 grid, size_t smem, cudaStream_t s) {
+  // the dynamic shared-memory limit is a per-function attribute (set on every
+  // launch: cheap, and correct on whichever device is current)
+  if (last) {
+    auto k = k_sweep<D, RECON, EOSK, DUAL, 1, M, NTS, MINB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k<<<grid, NTS, smem, s>>>(a);
+  } else {
+    auto k = k_sweep<D, RECON, EOSK, DUAL, 0, M, NTS, MINB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k<<<grid, NTS, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int D, int M, int NTS, int MINB>
+cudaError_t sweep_dispatch(const SweepArgs &a, bool last, dim3 grid, size_t smem, cudaStream_t s) {
+  const Phys &p = a.p;
+  if (p.recon == PLM) {
+    if (p.eos == EOS_IDEAL) {
+      return p.dual ? sweep_one<D, PLM, EOS_IDEAL, 1, M, NTS, MINB>(a, last, grid, smem, s)
+                    : sweep_one<D, PLM, EOS_IDEAL, 0, M, NTS, MINB>(a, last, grid, smem, s);
+    }
+    return p.dual ? sweep_one<D, PLM, EOS_TABLE, 1, M, NTS, MINB>(a, last, grid, smem, s)
+                  : sweep_one<D, PLM, EOS_TABLE, 0, M, NTS, MINB>(a, last, grid, smem, s);
+  }
+  if (p.eos == EOS_IDEAL) {
+    return p.dual ? sweep_one<D, PPM, EOS_IDEAL, 1, M, NTS, MINB>(a, last, grid, smem, s)
+                  : sweep_one<D, PPM, EOS_IDEAL, 0, M, NTS, MINB>(a, last, grid, smem, s);
+  }
+  return p.dual ? sweep_one<D, PPM, EOS_TABLE, 1, M, NTS, MINB>(a, last, grid, smem, s)
+                : sweep_one<D, PPM, EOS_TABLE, 0, M, NTS, MINB>(a, last, grid, smem, s);
+}
+
+// All directions and scheme variants of one tile shape (instantiated in its own
+// translation unit, tde_sweep_m<M>.cu, so that the shapes compile in parallel).
+template <int M, int NTS, int MINB>
+cudaError_t sweep_launch_shape(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem,
+                               cudaStream_t s) {
+  if (D == 0) return sweep_dispatch<0, M, NTS, MINB>(a, last, grid, smem, s);
+  if (D == 1) return sweep_dispatch<1, M, NTS, MINB>(a, last, grid, smem, s);
+  return sweep_dispatch<2, M, NTS, MINB>(a, last, grid, smem, s);
+}
+
+// The tile shapes offered to the autotuner: lanes per tile, CTA width, and the
+// CTAs per SM the register budget is sized for.  Index 0 is the default.
+struct TileShape {
+  int M, NTS, MINB;
+};
+constexpr int N_TILE_SHAPES = N_SWEEP_SHAPES;
+constexpr TileShape kTileShapes[N_TILE_SHAPES] = {{8, 272, 3}, {16, 288, 3}, {4, 160, 5}};
+
+cudaError_t sweep_launch_m8(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
+cudaError_t sweep_launch_m16(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
+cudaError_t sweep_launch_m4(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
+
+}  // namespace tde

@@ -113,6 +113,9 @@ _SIGS = {
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
     "tde_math_selftest": [vp, C.c_int64, dp, dp, dp],
     "tde_math_probe": [vp, C.c_int, C.c_int64, dp, dp, dp],
+    "tde_mesh_autotune": [vp, C.POINTER(BHState), C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
+    "tde_mesh_set_tiles": [vp, C.POINTER(C.c_int32)],
+    "tde_mesh_get_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
                        C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "tde_lat_set_factors": [vp, C.POINTER(C.c_int32), C.c_double],
@@ -390,6 +393,23 @@ class Mesh:
         self.ctx.check(lib().tde_lat_window(self.h, C.byref(bh) if bh is not None else None,
                                             1 if use_graph else 0, C.byref(upd)))
         return upd.value
+
+    def autotune(self, bh=None, reps=3):
+        """Pick the fastest sweep tile shape per direction; returns (shapes, ms[3][3])."""
+        t = (C.c_int32 * 3)()
+        ms = (C.c_float * 9)()
+        self.ctx.check(lib().tde_mesh_autotune(self.h, C.byref(bh) if bh is not None else None, reps,
+                                               t, ms))
+        return list(t), [list(ms[3 * d:3 * d + 3]) for d in range(3)]
+
+    def set_tiles(self, tiles):
+        t = (C.c_int32 * 3)(*tiles)
+        self.ctx.check(lib().tde_mesh_set_tiles(self.h, t))
+
+    def get_tiles(self):
+        t = (C.c_int32 * 3)()
+        self.ctx.check(lib().tde_mesh_get_tiles(self.h, t))
+        return list(t)
 
     def counts(self, reset=False):
         c = Counts()
