@@ -70,6 +70,11 @@ typedef struct {
   double eta1, eta2;    /* Eq. dual-primitive-switch and Eq. dual-sync thresholds */
   double rho_floor, p_floor, u_floor;  /* floors; u_floor = internal energy density of the floor state */
   double unit_rho, unit_e;             /* code -> cgs factors applied before table lookups */
+  int eos_mode;         /* TDE_EOS_TABLE: how the cons -> prim closure inverts the table,
+                           TDE_INVERT_BISECT (default), TDE_INVERT_BISECT_PLAIN or
+                           TDE_INVERT_SURROGATE (needs a trained network on the tde_eos when a
+                           stage runs; the learned guess runs as separate launches over the
+                           stage's cells).  All three give identical results. */
 } tde_params;
 
 /* Softened point-mass potential on the trajectory

@@ -70,11 +70,42 @@ bool fill_phys(tde_mesh *m, const tde_params *pr, tde_eos *eos) {
   p.unit_e = pr->unit_e;
   p.inv_unit_p = 1.0 / (pr->unit_rho * pr->unit_e);
   p.inv_unit_e = 1.0 / pr->unit_e;
+  p.eos_mode = pr->eos_mode;
+  if (p.eos_mode < TDE_INVERT_BISECT || p.eos_mode > TDE_INVERT_BISECT_PLAIN) return false;
   if (p.eos == EOS_TABLE) {
     if (!eos) return false;
     p.tab = eos->tab;
+    if (p.eos_mode == TDE_INVERT_BISECT_PLAIN) p.tab.le32 = nullptr;   // every step in FP64
   }
   return true;
+}
+
+}  // namespace
+
+namespace tde {
+// A mesh whose closure uses the learned guess needs a trained network.
+bool closure_ready(const tde_mesh *m) {
+  return !(m->phys.eos == EOS_TABLE && m->phys.eos_mode == TDE_INVERT_SURROGATE) ||
+         (m->eos && m->eos->has_net && m->sb.rho);
+}
+}  // namespace tde
+
+namespace {
+
+// Buffers of the learned-guess closure (allocated when a mesh first selects it).
+int ensure_surrogate_buffers(tde_mesh *m) {
+  if (m->sb.rho || !(m->phys.eos == EOS_TABLE && m->phys.eos_mode == TDE_INVERT_SURROGATE)) return TDE_OK;
+  const size_t nt = (size_t)m->ntot;
+  cudaError_t err = cudaMalloc(&m->sb.rho, sizeof(double) * nt * 5);
+  if (err == cudaSuccess) err = cudaMalloc(&m->sb.lTg, sizeof(float) * nt);
+  if (err == cudaSuccess) err = cudaMalloc(&m->sb.queue, sizeof(long long) * nt);
+  if (err == cudaSuccess) err = cudaMalloc(&m->sb.qcount, sizeof(unsigned long long));
+  if (err != cudaSuccess) return cuda_fail(m->ctx, err, "learned-guess closure buffers");
+  m->sb.e = m->sb.rho + nt;
+  m->sb.P = m->sb.rho + 2 * nt;
+  m->sb.cs2 = m->sb.rho + 3 * nt;
+  m->sb.eu = m->sb.rho + 4 * nt;
+  return TDE_OK;
 }
 
 }  // namespace
@@ -475,6 +506,10 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
     tde_mesh_destroy(m);
     return cuda_fail(ctx, err, "tde_mesh_create: upload");
   }
+  if (ensure_surrogate_buffers(m) != TDE_OK) {
+    tde_mesh_destroy(m);
+    return TDE_ENOMEM;
+  }
   *out = m;
   return TDE_OK;
 }
@@ -496,6 +531,10 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_nbr);
   cudaFree(m->d_owner);
   cudaFree(m->d_tstart);
+  cudaFree(m->sb.rho);
+  cudaFree(m->sb.lTg);
+  cudaFree(m->sb.queue);
+  cudaFree(m->sb.qcount);
   cudaFree(m->d_f);
   cudaFree(m->d_f2);
   cudaFree(m->d_sorted);
@@ -532,6 +571,8 @@ extern "C" int tde_mesh_set_params(tde_mesh *m, const tde_params *pr) {
   p.ng = keep.ng;
   p.dxmin = keep.dxmin;
   m->params = *pr;
+  int rb = ensure_surrogate_buffers(m);
+  if (rb) return rb;
   if (m->lat_graph) {   // captured launches hold the old parameters
     cudaGraphExecDestroy(m->lat_graph);
     m->lat_graph = nullptr;
@@ -600,6 +641,7 @@ extern "C" int tde_hydro_stage(tde_mesh *m, int stage, int nblk, const int32_t *
                                const tde_bh_state *bh) {
   if (!m) return TDE_EINVAL;
   if (!m->U || !m->U1) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: no bound state");
+  if (!closure_ready(m)) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: surrogate closure without a trained network");
   if ((stage != 0 && stage != 1) || !dt_block) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: arguments");
   if (!ids) { ids = m->d_allids; nblk = m->nb; }
   if (nblk <= 0 || nblk > m->nb) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: block count");
@@ -638,6 +680,7 @@ extern "C" int tde_step(tde_mesh *m, double cfl, double dt_fixed, const tde_bh_s
                         double *dt_out) {
   if (!m) return TDE_EINVAL;
   if (!m->U || !m->U1) return fail(m->ctx, TDE_EINVAL, "tde_step: no bound state");
+  if (!closure_ready(m)) return fail(m->ctx, TDE_EINVAL, "tde_step: surrogate closure without a trained network");
   if (!(cfl > 0.0) && !(dt_fixed > 0.0)) return fail(m->ctx, TDE_EINVAL, "tde_step: need cfl or dt");
   tde_ctx *c = m->ctx;
   const BH bh = make_bh(bhs);

@@ -111,6 +111,7 @@ struct Counters {
 // Scheme, physics and geometry constants, passed by value to every kernel.
 struct Phys {
   int eos, recon, dual, nvar, nwv;
+  int eos_mode;   // TDE_INVERT_*: how the table is inverted (the results are identical)
   double gamma, gm1, inv_gm1, eta1, eta2;
   double rho_floor, p_floor, u_floor;
   double unit_rho, unit_e, inv_unit_p, inv_unit_e;
@@ -283,18 +284,45 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
   return cl;
 }
 
+// The table's inputs (cgs density and specific internal energy) of a cell with
+// density rho and internal energy density U in code units.
+__device__ __forceinline__ void eos_inputs(const Phys &p, double rho, double U, double &rho_c,
+                                           double &e_c) {
+  rho_c = rho * p.unit_rho;
+  e_c = (U * rcp_nr(rho)) * p.unit_e;
+}
+
+// Table results of a cell computed by a separate pass (the learned-guess
+// inversion runs as its own launches): P, cs2 in cgs and eu = the clamped
+// table energy, or 0 where the input was inside the table.
+struct EOSBuf {
+  const double *P, *cs2, *eu;
+};
+
 // EOS closure in code units: internal energy density U at density rho ->
-// P, cs^2 and the internal energy the table actually represents.
-template <int EOSK>
+// P, cs^2 and the internal energy the table actually represents.  EOSB: take
+// the table results of the cell at index flat from eb instead of inverting.
+template <int EOSK, int EOSB = 0>
 __device__ __forceinline__ void eos_closure(const Phys &p, double rho, double U, double &P,
-                                            double &cs2, double &Uu, Counters *cnt) {
+                                            double &cs2, double &Uu, Counters *cnt,
+                                            const EOSBuf *eb = nullptr, long long flat = 0) {
   if (EOSK == EOS_IDEAL) {
     P = p.gm1 * U;
     cs2 = p.gamma * P / rho;
     Uu = U;
   } else {
     double Pc, c2c, eu;
-    bool cl = eos_invert(p.tab, rho * p.unit_rho, (U * rcp_nr(rho)) * p.unit_e, Pc, c2c, eu);
+    bool cl;
+    if (EOSB) {
+      Pc = eb->P[flat];
+      c2c = eb->cs2[flat];
+      eu = eb->eu[flat];
+      cl = eu > 0.0;
+    } else {
+      double rc, ec;
+      eos_inputs(p, rho, U, rc, ec);
+      cl = eos_invert(p.tab, rc, ec, Pc, c2c, eu);
+    }
     if (cl && cnt) count(&cnt->table_clamp);
     P = Pc * p.inv_unit_p;
     cs2 = c2c * p.inv_unit_e;
@@ -312,23 +340,33 @@ __device__ __forceinline__ double table_pressure(const Phys &p, double rho, doub
   return Pc * p.inv_unit_p;
 }
 
-// Conserved (rho, m, E[, U_aux]) -> primitives w = (rho, vx, vy, vz, P
-// [, Gamma_e, Gamma_1][, U_aux]) with the dual-energy switch of
-// Eq. dual-primitive-switch and the density / pressure floors.
-template <int EOSK, int DUAL>
-__device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, double *w,
-                                             Counters *cnt) {
-  double rho = u[0];
+// Density (floored), velocities and the internal energy density the EOS gets
+// (Eq. dual-econs with the dual-energy switch of Eq. dual-primitive-switch).
+template <int DUAL>
+__device__ __forceinline__ void c2p_energy(const Phys &p, const double *u, double &rho, double &vx,
+                                           double &vy, double &vz, double &Ue, Counters *cnt) {
+  rho = u[0];
   if (rho < p.rho_floor) { rho = p.rho_floor; if (cnt) count(&cnt->rho_floor); }
   double ir = rcp_nr(rho);
-  double vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
+  vx = u[1] * ir; vy = u[2] * ir; vz = u[3] * ir;
   double Uc = u[4] - 0.5 * (u[1] * vx + u[2] * vy + u[3] * vz);   // Eq. dual-econs
-  double Ue = Uc;
+  Ue = Uc;
   if (DUAL) {
     if (!(Uc > 0.0 && Uc > p.eta1 * u[4])) { Ue = u[5]; if (cnt) count(&cnt->dual_aux_used); }
   }
+}
+
+// Conserved (rho, m, E[, U_aux]) -> primitives w = (rho, vx, vy, vz, P
+// [, Gamma_e, Gamma_1][, U_aux]) with the dual-energy switch of
+// Eq. dual-primitive-switch and the density / pressure floors.
+template <int EOSK, int DUAL, int EOSB = 0>
+__device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, double *w,
+                                             Counters *cnt, const EOSBuf *eb = nullptr,
+                                             long long flat = 0) {
+  double rho, vx, vy, vz, Ue;
+  c2p_energy<DUAL>(p, u, rho, vx, vy, vz, Ue, cnt);
   double P, cs2, Uu;
-  eos_closure<EOSK>(p, rho, Ue, P, cs2, Uu, cnt);
+  eos_closure<EOSK, EOSB>(p, rho, Ue, P, cs2, Uu, cnt, eb, flat);
   if (P < p.p_floor) { P = p.p_floor; if (cnt) count(&cnt->p_floor); }
   w[0] = rho; w[1] = vx; w[2] = vy; w[3] = vz; w[4] = P;
   if (EOSK == EOS_TABLE) {

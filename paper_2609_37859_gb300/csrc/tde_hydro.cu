@@ -44,13 +44,13 @@ __device__ __forceinline__ double block_min(double v) {
 
 // ------------------------------------------------------------ k_c2p ----
 
-template <int EOSK, int DUAL>
+template <int EOSK, int DUAL, int EOSB = 0>
 __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
                                             const DevBlock *__restrict__ blocks,
                                             const int32_t *__restrict__ ids,
                                             const double *__restrict__ U, double *__restrict__ W,
                                             long long ntot, Counters *cnt, int want_dt,
-                                            unsigned long long *dtbits) {
+                                            unsigned long long *dtbits, EOSBuf eb) {
   const int b = ids[blockIdx.y];
   const DevBlock B = blocks[b];
   const int nint = B.n[0] * B.n[1] * B.n[2];
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
     double u[6], w[8];
 #pragma unroll
     for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
-    cons_to_prim<EOSK, DUAL>(p, u, w, cnt);
+    cons_to_prim<EOSK, DUAL, EOSB>(p, u, w, cnt, &eb, flat);
     constexpr int NWV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
 #pragma unroll
     for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
@@ -109,12 +109,12 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
 // every padded cell of the listed blocks (used when only a subset of blocks
 // advances, so the ghost layer cannot be copied from freshly converted
 // neighbours); events are counted on interior cells only
-template <int EOSK, int DUAL>
+template <int EOSK, int DUAL, int EOSB = 0>
 __global__ void __launch_bounds__(NT) k_c2p_padded(Phys p, const DevBlock *__restrict__ blocks,
                                                    const int32_t *__restrict__ ids,
                                                    const double *__restrict__ U,
                                                    double *__restrict__ W, long long ntot,
-                                                   Counters *cnt) {
+                                                   Counters *cnt, EOSBuf eb) {
   const int b = ids[blockIdx.y];
   const DevBlock B = blocks[b];
   const int npad = B.p[0] * B.p[1] * B.p[2];
@@ -127,10 +127,43 @@ __global__ void __launch_bounds__(NT) k_c2p_padded(Phys p, const DevBlock *__res
     double u[6], w[8];
 #pragma unroll
     for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
-    cons_to_prim<EOSK, DUAL>(p, u, w, interior ? cnt : nullptr);
+    cons_to_prim<EOSK, DUAL, EOSB>(p, u, w, interior ? cnt : nullptr, &eb, flat);
     constexpr int NWV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
 #pragma unroll
     for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
+  }
+}
+
+// The table inputs (cgs rho, e) of the interior (PADDED = 0) or all padded
+// (PADDED = 1) cells of the listed blocks, by the same expressions as the
+// closure inside k_c2p, for the learned-guess inversion's launches; nothing is
+// counted here (k_c2p counts when it takes the results).
+template <int DUAL, int PADDED>
+__global__ void __launch_bounds__(NT) k_c2p_eosin(Phys p, const DevBlock *__restrict__ blocks,
+                                                  const int32_t *__restrict__ ids,
+                                                  const double *__restrict__ U, double *rho_in,
+                                                  double *e_in, long long ntot) {
+  const int b = ids[blockIdx.y];
+  const DevBlock B = blocks[b];
+  const int n = PADDED ? B.p[0] * B.p[1] * B.p[2] : B.n[0] * B.n[1] * B.n[2];
+  for (int e = blockIdx.x * NT + threadIdx.x; e < n; e += gridDim.x * NT) {
+    long long flat;
+    if (PADDED) {
+      flat = B.off + e;
+    } else {
+      const int i = e % B.n[0], r = e / B.n[0];
+      const int j = r % B.n[1], k = r / B.n[1];
+      flat = B.off + ((long long)(k + p.g[2]) * B.p[1] + (j + p.g[1])) * B.p[0] + (i + p.g[0]);
+    }
+    double u[6];
+#pragma unroll
+    for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
+    double rho, vx, vy, vz, Ue;
+    c2p_energy<DUAL>(p, u, rho, vx, vy, vz, Ue, nullptr);
+    double rc, ec;
+    eos_inputs(p, rho, Ue, rc, ec);
+    rho_in[flat] = rc;
+    e_in[flat] = ec;
   }
 }
 
@@ -332,16 +365,53 @@ static int n_sm() {
   return n;
 }
 
+static bool surrogate_closure(const tde_mesh *m) {
+  return m->phys.eos == EOS_TABLE && m->phys.eos_mode == TDE_INVERT_SURROGATE;
+}
+
+// The learned-guess inversion of the listed blocks' cells (interior or all
+// padded): table inputs -> guess, Newton, queued bisection -> m->sb (P, cs2, eu).
+static cudaError_t surrogate_table_pass(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids,
+                                        bool padded, dim3 grid) {
+  const Phys &p = m->phys;
+  cudaStream_t s = m->ctx->stream;
+  if (!m->sb.rho || !m->eos || !m->eos->has_net) return cudaErrorInvalidValue;
+  const long long nt = (long long)m->ntot;
+  if (padded) {
+    if (p.dual) k_c2p_eosin<1, 1><<<grid, NT, 0, s>>>(p, m->d_blocks, ids, Uin, m->sb.rho, m->sb.e, nt);
+    else k_c2p_eosin<0, 1><<<grid, NT, 0, s>>>(p, m->d_blocks, ids, Uin, m->sb.rho, m->sb.e, nt);
+  } else {
+    if (p.dual) k_c2p_eosin<1, 0><<<grid, NT, 0, s>>>(p, m->d_blocks, ids, Uin, m->sb.rho, m->sb.e, nt);
+    else k_c2p_eosin<0, 0><<<grid, NT, 0, s>>>(p, m->d_blocks, ids, Uin, m->sb.rho, m->sb.e, nt);
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  CellMap cm{m->d_blocks, ids, nblk, padded ? 1 : 0, {p.g[0], p.g[1], p.g[2]}};
+  int64_t nmax = 0;
+  for (const DevBlock &B : m->hblocks)
+    nmax = std::max<int64_t>(nmax, padded ? (int64_t)B.p[0] * B.p[1] * B.p[2]
+                                          : (int64_t)B.n[0] * B.n[1] * B.n[2]);
+  return launch_eos_surrogate_cells(m->eos, cm, nmax, m->sb, m->d_cnt, s);
+}
+
 cudaError_t launch_c2p(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids, bool want_dt,
                        const BH &bh, TimeArgs ta) {
   ProfScope _ps(m->ctx, TDE_K_C2P);
   dim3 grid((unsigned)((m->max_interior + NT - 1) / NT), (unsigned)nblk);
   const Phys &p = m->phys;
+  EOSBuf eb{m->sb.P, m->sb.cs2, m->sb.eu};
+  if (surrogate_closure(m)) {
+    cudaError_t err = surrogate_table_pass(m, Uin, nblk, ids, false, grid);
+    if (err != cudaSuccess) return err;
+  }
 #define C2P_ARGS p, bh, ta, m->d_blocks, ids, Uin, m->d_W, (long long)m->ntot, m->d_cnt, \
-                 (int)want_dt, m->d_dtbits
+                 (int)want_dt, m->d_dtbits, eb
   if (p.eos == EOS_IDEAL) {
     if (p.dual) k_c2p<EOS_IDEAL, 1><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
     else k_c2p<EOS_IDEAL, 0><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
+  } else if (surrogate_closure(m)) {
+    if (p.dual) k_c2p<EOS_TABLE, 1, 1><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
+    else k_c2p<EOS_TABLE, 0, 1><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
   } else {
     if (p.dual) k_c2p<EOS_TABLE, 1><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
     else k_c2p<EOS_TABLE, 0><<<grid, NT, 0, m->ctx->stream>>>(C2P_ARGS);
@@ -356,10 +426,18 @@ cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const in
   for (const DevBlock &B : m->hblocks) npad = std::max<int64_t>(npad, (int64_t)B.p[0] * B.p[1] * B.p[2]);
   dim3 grid((unsigned)std::min<int64_t>((npad + NT - 1) / NT, 256), (unsigned)nblk);
   const Phys &p = m->phys;
-#define C2PP_ARGS p, m->d_blocks, ids, Uin, m->d_W, (long long)m->ntot, m->d_cnt
+  EOSBuf eb{m->sb.P, m->sb.cs2, m->sb.eu};
+  if (surrogate_closure(m)) {
+    cudaError_t err = surrogate_table_pass(m, Uin, nblk, ids, true, grid);
+    if (err != cudaSuccess) return err;
+  }
+#define C2PP_ARGS p, m->d_blocks, ids, Uin, m->d_W, (long long)m->ntot, m->d_cnt, eb
   if (p.eos == EOS_IDEAL) {
     if (p.dual) k_c2p_padded<EOS_IDEAL, 1><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
     else k_c2p_padded<EOS_IDEAL, 0><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
+  } else if (surrogate_closure(m)) {
+    if (p.dual) k_c2p_padded<EOS_TABLE, 1, 1><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
+    else k_c2p_padded<EOS_TABLE, 0, 1><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
   } else {
     if (p.dual) k_c2p_padded<EOS_TABLE, 1><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
     else k_c2p_padded<EOS_TABLE, 0><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);

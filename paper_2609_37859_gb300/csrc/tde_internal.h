@@ -75,6 +75,25 @@ struct tde_eos {
   int *d_status = nullptr;
 };
 
+namespace tde {
+// The cells a pass covers: the interior (padded = 0) or all padded cells
+// (padded = 1) of the blocks ids[0 .. nblk); blocks == null means plain arrays.
+struct CellMap {
+  const DevBlock *blocks;
+  const int32_t *ids;
+  int nblk, padded;
+  int g[3];
+};
+// Buffers of the learned-guess closure, each indexed like the state (ntot):
+// table inputs, results (eu = clamped table energy or 0), guess and queue.
+struct SurrogateBuf {
+  double *rho = nullptr, *e = nullptr, *P = nullptr, *cs2 = nullptr, *eu = nullptr;
+  float *lTg = nullptr;
+  long long *queue = nullptr;
+  unsigned long long *qcount = nullptr;
+};
+}  // namespace tde
+
 struct tde_mesh {
   tde_ctx *ctx = nullptr;
   tde_eos *eos = nullptr;
@@ -84,6 +103,7 @@ struct tde_mesh {
   int nb = 0;
   int nmax[3] = {0, 0, 0};           // largest interior block edge per direction
   int tile[3] = {0, 0, 0};           // sweep tile shape per direction (kTileShapes index)
+  tde::SurrogateBuf sb;              // learned-guess closure buffers (eos_mode SURROGATE)
   int64_t ntot = 0;
   int64_t max_interior = 0;          // largest interior cell count of a block
   int max_ghosts = 0;                // largest ghost count of a block
@@ -151,6 +171,7 @@ size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
 constexpr int N_SWEEP_SHAPES = 3;
 cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3][N_SWEEP_SHAPES]);
 void invalidate_graph(tde_mesh *m);
+bool closure_ready(const tde_mesh *m);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);
 cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2);
@@ -161,6 +182,8 @@ cudaError_t launch_eos_invert(tde_eos *e, int64_t n, const double *rho, const do
                               double *T, double *P, double *cs2, cudaStream_t s, bool plain = false);
 cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const double *en,
                                  double *T, double *P, double *cs2, cudaStream_t s);
+cudaError_t launch_eos_surrogate_cells(tde_eos *e, const CellMap &cm, int64_t nmax,
+                                       const SurrogateBuf &sb, Counters *cnt, cudaStream_t s);
 cudaError_t launch_eos_eval(tde_eos *e, int64_t n, const double *rho, const double *T, double *P,
                             double *en, double *cs2, cudaStream_t s);
 

@@ -496,6 +496,7 @@ extern "C" int tde_lat_window(tde_mesh *m, const tde_bh_state *bhs, int use_grap
   if (!m) return TDE_EINVAL;
   tde_ctx *c = m->ctx;
   if (!m->U || !m->U1) return lat_fail(c, TDE_EINVAL, "tde_lat_window: no bound state");
+  if (!closure_ready(m)) return lat_fail(c, TDE_EINVAL, "tde_lat_window: surrogate closure without a trained network");
   if (!m->lat_ready) return lat_fail(c, TDE_EINVAL, "tde_lat_window: no factors (tde_lat_assign)");
   BH bh{};
   if (bhs) {

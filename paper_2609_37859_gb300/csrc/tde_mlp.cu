@@ -246,7 +246,25 @@ struct SurrogateArgs {
   Counters *cnt;
   int *status;        // set to 1 if a bounded wait expired
   float *lTg;         // optional: the guessed log10 T of each cell
+  CellMap cm;         // which cells: plain arrays (cm.blocks null) or cells of blocks
 };
+
+// Cells of a cell map: block position bp's cell count, and the array index of
+// its cell `local` (plain arrays: one "block" of n cells, index = local).
+__device__ __forceinline__ long long cm_cells(const CellMap &cm, long long n, int bp) {
+  if (!cm.blocks) return n;
+  const DevBlock &B = cm.blocks[cm.ids[bp]];
+  return cm.padded ? (long long)B.p[0] * B.p[1] * B.p[2] : (long long)B.n[0] * B.n[1] * B.n[2];
+}
+__device__ __forceinline__ long long cm_flat(const CellMap &cm, int bp, long long local) {
+  if (!cm.blocks) return local;
+  const DevBlock &B = cm.blocks[cm.ids[bp]];
+  if (cm.padded) return B.off + local;
+  const int i = (int)(local % B.n[0]);
+  const long long r = local / B.n[0];
+  const int j = (int)(r % B.n[1]), k = (int)(r / B.n[1]);
+  return B.off + ((long long)(k + cm.g[2]) * B.p[1] + (j + cm.g[1])) * B.p[0] + (i + cm.g[0]);
+}
 
 __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   __shared__ __align__(1024) unsigned char sA[IT * H * 2];   // h1, BF16, core-matrix layout
@@ -287,10 +305,16 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tmem_base;
   uint32_t phase = 0;
-  const long long ntiles = (a.n + IT - 1) / IT;
+  // tiles of IT cells, tpb per block (a.n = the largest block's cell count)
+  const long long tpb = (a.n + IT - 1) / IT;
+  const long long ntiles = tpb * (a.cm.blocks ? a.cm.nblk : 1);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long c = tile * IT + tid;
-    const bool live = c < a.n;
+    const int bp = (int)(tile / tpb);
+    const long long local = (tile - (long long)bp * tpb) * IT + tid;
+    const long long ncell = cm_cells(a.cm, a.n, bp);
+    if ((tile - (long long)bp * tpb) * IT >= ncell) continue;   // the whole tile (uniform)
+    const bool live = local < ncell;
+    const long long c = live ? cm_flat(a.cm, bp, local) : 0;
     // ---- inputs and layer 1, FP32 only: the network needs log10 rho and the
     // position z of log10 e in its column to FP32 accuracy (the FP64 work of
     // the inversion is k_eos_newton's)
@@ -424,23 +448,29 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
 // result bit for bit.  Cells not settled this way (clamped inputs, a step that
 // misses) are queued for k_eos_fallback; the queue slots of a CTA's 256 cells
 // are reserved with one atomic, and the accepted count is added once per CTA.
-__global__ void __launch_bounds__(256) k_eos_newton(DTable t, const float *__restrict__ lTg,
+__global__ void __launch_bounds__(256) k_eos_newton(DTable t, CellMap cm, const float *__restrict__ lTg,
                                                     float idlt, long long n,
                                                     const double *__restrict__ rho,
                                                     const double *__restrict__ en, double *T, double *P,
-                                                    double *cs2, Counters *cnt, long long *queue,
-                                                    unsigned long long *qcount) {
+                                                    double *cs2, double *eu, Counters *cnt,
+                                                    long long *queue, unsigned long long *qcount) {
   __shared__ unsigned s_wc[8];
   __shared__ unsigned long long s_base;
   __shared__ unsigned s_acc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = t.nt;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long cpb = (n + 255) / 256;   // chunks of 256 cells per block
+  const long long nchunks = cpb * (cm.blocks ? cm.nblk : 1);
   unsigned n_acc = 0;
-  // every lane runs the same number of iterations (the warp votes below)
-  for (long long c0 = blockIdx.x * (long long)blockDim.x; c0 < n; c0 += stride) {
-    const long long c = c0 + threadIdx.x;
+  // every thread of the CTA runs the same chunks (the CTA votes below)
+  for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int bp = (int)(ch / cpb);
+    const long long local0 = (ch - (long long)bp * cpb) * 256;
+    const long long ncell = cm_cells(cm, n, bp);
+    if (local0 >= ncell) continue;   // uniform over the CTA
+    const long long local = local0 + threadIdx.x;
+    const long long c = local < ncell ? cm_flat(cm, bp, local) : -1;
     bool ok = true, acc = false;
-    if (c < n) {
+    if (c >= 0) {
       int i;
       double w;
       const bool cl = rho_cell(t, rho[c], i, w);
@@ -476,6 +506,7 @@ __global__ void __launch_bounds__(256) k_eos_newton(DTable t, const float *__res
           if (P) P[c] = texp10(t, bilin(t.lp, nt, i, w, j, sc));
           if (cs2) cs2[c] = texp10(t, bilin(t.lc, nt, i, w, j, sc));
           if (T) T[c] = texp10(t, cell_log10T(t, j, sc));
+          if (eu) eu[c] = 0.0;   // inside the table
           acc = true;
         }
       }
@@ -495,7 +526,7 @@ __global__ void __launch_bounds__(256) k_eos_newton(DTable t, const float *__res
     }
     __syncthreads();
     if (!ok) queue[s_base + s_wc[warp] + __popc(rm & ((1u << lane) - 1u))] = c;
-    __syncthreads();   // s_wc and s_base are rewritten by the next iteration
+    __syncthreads();   // s_wc and s_base are rewritten by the next chunk
   }
   // accepted cells: one atomic per CTA
   for (int o = 16; o > 0; o >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
@@ -507,20 +538,24 @@ __global__ void __launch_bounds__(256) k_eos_newton(DTable t, const float *__res
 }
 
 // Table bisection for the cells the Newton step left (their indices in queue).
+// With eu (the hydro closure's buffers) the clamped table energy is returned
+// (0 inside the table) and the closure counts clamps; without, they are counted here.
 __global__ void __launch_bounds__(256) k_eos_fallback(DTable t, const long long *__restrict__ queue,
                                                       const unsigned long long *__restrict__ qcount,
                                                       const double *__restrict__ rho,
                                                       const double *__restrict__ e, double *T, double *P,
-                                                      double *cs2, Counters *cnt) {
+                                                      double *cs2, double *eu, Counters *cnt) {
   const long long nq = (long long)*qcount;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
        q += (long long)gridDim.x * blockDim.x) {
     const long long c = queue[q];
-    double Pv, cv, eu, Tv;
-    if (eos_invert(t, rho[c], e[c], Pv, cv, eu, &Tv)) count(&cnt->table_clamp);
+    double Pv, cv, euv, Tv;
+    const bool cl = eos_invert(t, rho[c], e[c], Pv, cv, euv, &Tv);
+    if (cl && !eu) count(&cnt->table_clamp);
     if (T) T[c] = Tv;
     if (P) P[c] = Pv;
     if (cs2) cs2[c] = cv;
+    if (eu) eu[c] = cl ? euv : 0.0;
   }
 }
 
@@ -602,7 +637,7 @@ cudaError_t launch_grad(tde_eos *e, const float *x, const float *tg, long long s
 
 cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, const double *en,
                                     double *T, double *P, double *cs2, const float *xin, float *yout,
-                                    cudaStream_t s, float *lTg = nullptr) {
+                                    cudaStream_t s, float *lTg = nullptr, const CellMap *cm = nullptr) {
   SurrogateArgs a;
   a.t = e->tab;
   a.nm = norm_of(e);
@@ -618,6 +653,7 @@ cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, 
   a.cnt = e->d_cnt;
   a.status = e->d_status;
   a.lTg = lTg;
+  a.cm = cm ? *cm : CellMap{};
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
   // one wave of resident CTAs: registers (64 x 128 threads) and shared memory
@@ -626,9 +662,34 @@ cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, 
   cudaFuncSetAttribute(k_eos_surrogate, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
   const int per_sm = 8;
-  const long long tiles = (n + IT - 1) / IT;
+  const long long tiles = (n + IT - 1) / IT * (a.cm.blocks ? a.cm.nblk : 1);
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
   k_eos_surrogate<<<grid, IT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The learned-guess inversion of the cells of cm (n = largest block's cell
+// count, or the array length): guess, FP64 Newton with queueing, bisection of
+// the queue.  The same inputs give the bisection results bit for bit.
+cudaError_t surrogate_run(tde_eos *e, const CellMap &cm, long long n, const double *rho,
+                          const double *en, double *T, double *P, double *cs2, double *eu,
+                          float *lTg, long long *queue, unsigned long long *qcount, Counters *cnt,
+                          cudaStream_t s) {
+  cudaError_t r = cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), s);
+  if (r != cudaSuccess) return r;
+  r = launch_surrogate_kernel(e, n, rho, en, nullptr, nullptr, nullptr, nullptr, nullptr, s, lTg, &cm);
+  if (r != cudaSuccess) return r;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
+  const long long chunks = (n + 255) / 256 * (cm.blocks ? cm.nblk : 1);
+  const unsigned grid = (unsigned)std::min<long long>(chunks, (long long)sms * 8);
+  k_eos_newton<<<grid, 256, 0, s>>>(e->tab, cm, lTg, (float)(1.0 / e->tab.dlt), n, rho, en, T, P,
+                                    cs2, eu, cnt, queue, qcount);
+  r = cudaGetLastError();
+  if (r != cudaSuccess) return r;
+  const long long ncell = n * (cm.blocks ? cm.nblk : 1);
+  const unsigned gf = (unsigned)std::min<long long>((ncell + 255) / 256, (long long)sms * 8);
+  k_eos_fallback<<<gf, 256, 0, s>>>(e->tab, queue, qcount, rho, en, T, P, cs2, eu, cnt);
   return cudaGetLastError();
 }
 
@@ -654,19 +715,15 @@ cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const
     if (r != cudaSuccess) return r;
   }
   ProfScope ps(e->ctx, TDE_K_EOS);
-  cudaError_t r = cudaMemsetAsync(e->d_qcount, 0, sizeof(unsigned long long), s);
-  if (r != cudaSuccess) return r;
-  r = launch_surrogate_kernel(e, n, rho, en, nullptr, nullptr, nullptr, nullptr, nullptr, s, e->d_guess);
-  if (r != cudaSuccess) return r;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
-  const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sms * 8);
-  k_eos_newton<<<grid, 256, 0, s>>>(e->tab, e->d_guess, (float)(1.0 / e->tab.dlt), n, rho, en, T, P,
-                                    cs2, e->d_cnt, e->d_queue, e->d_qcount);
-  r = cudaGetLastError();
-  if (r != cudaSuccess) return r;
-  k_eos_fallback<<<grid, 256, 0, s>>>(e->tab, e->d_queue, e->d_qcount, rho, en, T, P, cs2, e->d_cnt);
-  return cudaGetLastError();
+  return surrogate_run(e, CellMap{}, n, rho, en, T, P, cs2, nullptr, e->d_guess, e->d_queue,
+                       e->d_qcount, e->d_cnt, s);
+}
+
+cudaError_t launch_eos_surrogate_cells(tde_eos *e, const CellMap &cm, int64_t nmax,
+                                       const SurrogateBuf &sb, Counters *cnt, cudaStream_t s) {
+  if (nmax <= 0 || cm.nblk <= 0) return cudaSuccess;
+  return surrogate_run(e, cm, nmax, sb.rho, sb.e, nullptr, sb.P, sb.cs2, sb.eu, sb.lTg, sb.queue,
+                       sb.qcount, cnt, s);
 }
 }  // namespace tde
 

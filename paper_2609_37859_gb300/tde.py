@@ -33,7 +33,7 @@ class Params(C.Structure):
     _fields_ = [("eos", C.c_int), ("recon", C.c_int), ("dual", C.c_int), ("gamma", C.c_double),
                 ("eta1", C.c_double), ("eta2", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("u_floor", C.c_double), ("unit_rho", C.c_double),
-                ("unit_e", C.c_double)]
+                ("unit_e", C.c_double), ("eos_mode", C.c_int)]
 
 
 class BHState(C.Structure):
@@ -300,7 +300,7 @@ class EOS:
 
 
 def make_params(**kw):
-    p = Params(EOS_IDEAL, RECON_PLM, 0, 5.0 / 3.0, 1e-3, 1e-4, 1e-300, 1e-300, 1e-300, 1.0, 1.0)
+    p = Params(EOS_IDEAL, RECON_PLM, 0, 5.0 / 3.0, 1e-3, 1e-4, 1e-300, 1e-300, 1e-300, 1.0, 1.0, 0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
