@@ -129,6 +129,8 @@ def run_gpu(args):
     U_init = mesh.U.clone()
     del W_d
     ncell = lay.ncells
+    # sweep tile shapes: timed per direction on this workload, fastest kept
+    tiles, tile_ms = mesh.autotune(reps=3)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -229,6 +231,7 @@ def run_gpu(args):
                              "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                              "frac": value / world * BYTES_PER_CELL_UPDATE * 1e-9 / hbm_peak},
             "roofline": roof,
+            "autotune": autotune_report(tiles, tile_ms),
             "kernels_ms": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
             "kernels_launches": {k: v[0] for k, v in prof.items() if v[0]},
             "gpu_launches": total_launches,
@@ -238,7 +241,10 @@ def run_gpu(args):
         }
         if not args.no_eos:
             line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
+            line["closure_modes"] = closure_bench(mesh, U_init, tde, torch, dev, args)
         if not args.no_lat:
+            if args.no_eos:   # the learned arm needs the network
+                eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
             del mesh
             torch.cuda.empty_cache()
             line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
@@ -258,6 +264,50 @@ def run_gpu(args):
 FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 296.0, "sweep_y": 252.2, "sweep_z": 383.2}
 DRAM_BYTES_SWEEP = {"sweep_x": 268.0e6, "sweep_y": 402.4e6, "sweep_z": 542.4e6}
 KERNELS_AS_CAPTURED = True
+
+
+SHAPE_NAMES = ("8 lanes x 272 threads", "16 lanes x 288 threads", "4 lanes x 160 threads")
+
+
+def autotune_report(tiles, ms):
+    return {"chosen": {d: SHAPE_NAMES[t] for d, t in zip("xyz", tiles)},
+            "launch_ms": {d: {SHAPE_NAMES[k]: (round(v, 4) if v >= 0 else None) for k, v in enumerate(row)}
+                          for d, row in zip("xyz", ms)}}
+
+
+def closure_bench(mesh, U_init, tde, torch, dev, args):
+    """The bench step with each way of inverting the table in cons -> prim
+    (same results, checked bitwise): FP32-guided bisection (the headline), plain
+    FP64 bisection, and the learned guess + one FP64 Newton step."""
+    out, ref = {}, None
+    nsteps = 10
+    for name, mode in (("bisect_fp32_guided", tde.INVERT_BISECT), ("bisect_plain", tde.INVERT_BISECT_PLAIN),
+                       ("surrogate_newton", tde.INVERT_SURROGATE)):
+        mesh.set_params(tde.make_params(eos_mode=mode, **SCHEME))
+        mesh.U.copy_(U_init)
+        mesh.set_time(0.0)
+        for _ in range(max(1, args.warmup)):
+            mesh.step(cfl=CFL)
+        mesh.U.copy_(U_init)
+        mesh.set_time(0.0)
+        mesh.counts(reset=True)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(nsteps):
+            mesh.step(cfl=CFL)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / nsteps
+        c = mesh.counts()
+        U = mesh.U.clone()
+        if ref is None:
+            ref = U
+        out[name] = {"ms_per_step": ms, "cell_updates_per_s": mesh.layout.ncells / (ms * 1e-3),
+                     "identical_to_fp32_guided": bool(torch.equal(U, ref)),
+                     "accepted_fraction": c["surrogate_accepted"] / (mesh.layout.ncells * 2 * nsteps)}
+    mesh.set_params(tde.make_params(**SCHEME))
+    return {"workload": "the bench step (C2), %d steps per mode" % nsteps, **out}
 
 
 # ------------------------------------------------------- EOS inversion (C3) ---
@@ -358,14 +408,37 @@ def lat_bench(ctx, eos, tde, torch, dev, args):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / reps
 
-    # LAT: eager first window (warm-up), then graph replay
-    mesh.lat_set_factors(fac, dt0)
-    mesh.lat_window(bh=bh, use_graph=False)
-    mesh.lat_window(bh=bh, use_graph=True)
-    mesh.U.copy_(U0)
-    mesh.set_time(0.0)
-    ms_lat = timed(lambda: mesh.lat_window(bh=bh, use_graph=True), 2)
-    lat_counts = mesh.counts(reset=True)
+    def set_mode(mode):
+        mesh.set_params(tde.make_params(eos_mode=mode, **{f: getattr(params, f) for f, _ in params._fields_
+                                                          if f != "eos_mode"}))
+
+    def lat_arm(mode):
+        set_mode(mode)
+        mesh.U.copy_(U0)
+        mesh.set_time(0.0)
+        mesh.lat_set_factors(fac, dt0)
+        mesh.lat_window(bh=bh, use_graph=False)   # warm-up: eager, then capture
+        mesh.lat_window(bh=bh, use_graph=True)
+        mesh.U.copy_(U0)
+        mesh.set_time(0.0)
+        mesh.lat_window(bh=bh, use_graph=True)
+        U1w = mesh.U.clone()
+        mesh.U.copy_(U0)
+        mesh.set_time(0.0)
+        mesh.counts(reset=True)
+        ms = timed(lambda: mesh.lat_window(bh=bh, use_graph=True), 2)
+        c = mesh.counts(reset=True)
+        c["surrogate_accepted"] //= 2   # per window
+        return ms, U1w, c
+
+    # LAT with tiles autotuned on this mesh: FP32-guided bisection (the GB300
+    # form) and the learned guess (the learned + batched form)
+    tiles, tile_ms = mesh.autotune(bh=bh, reps=2)
+    ms_lat, U_lat, lat_counts = lat_arm(tde.INVERT_BISECT)
+    ms_lat_sur, U_sur, sur_counts = lat_arm(tde.INVERT_SURROGATE)
+    same_lat = bool(torch.equal(U_lat, U_sur))
+    del U_lat, U_sur
+    set_mode(tde.INVERT_BISECT)
     # synchronised steps of dt0 over the same physical time
     mesh.U.copy_(U0)
     mesh.set_time(0.0)
@@ -377,7 +450,10 @@ def lat_bench(ctx, eos, tde, torch, dev, args):
         for _ in range(fmax):
             mesh.step(dt=dt0, bh=bh)
     ms_sync = timed(sync_window, 1)
-    # plain form: one launch sequence per block and stage, one step of dt0
+    # plain form: plain FP64 table bisection, the default tile shape, one launch
+    # sequence per block and stage; one step of dt0
+    set_mode(tde.INVERT_BISECT_PLAIN)
+    mesh.set_tiles((0, 0, 0))
     ids = torch.arange(lay.nb, dtype=torch.int32, device=dev)
     dtb = torch.full((lay.nb,), dt0, dtype=torch.float64, device=dev)
     tb = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
@@ -389,6 +465,7 @@ def lat_bench(ctx, eos, tde, torch, dev, args):
                 mesh.hydro_stage(st, dtb, tb, ids=ids[b:b + 1], bh=bh)
     plain_step()
     ms_plain_step = timed(plain_step, 1)
+    set_mode(tde.INVERT_BISECT)
     ncell = lay.ncells
     upd = ncell * fmax
     del mesh, U0
@@ -397,13 +474,30 @@ def lat_bench(ctx, eos, tde, torch, dev, args):
                         "384 x 32^3 + 128 x 16^3 MeshBlocks, PPM+HLLC, Saha table, dual energy, N_LAT 5",
             "cells": ncell, "meshblocks": lay.nb, "f_max": int(fmax), "blocks_per_factor": levels,
             "work_fraction": work, "work_reduction": 1.0 - work,
+            "autotune": autotune_report(tiles, tile_ms),
             "lat_window_ms": ms_lat, "sync_window_ms": ms_sync,
+            "learned_batched_window_ms": ms_lat_sur,
+            "learned_batched_identical_to_lat": same_lat,
+            "learned_accepted_per_window": sur_counts["surrogate_accepted"],
+            "closure_interior_cell_stages_per_window": lat_counts_cells(lay, fac, fmax),
             "plain_per_block_step_ms": ms_plain_step, "plain_window_ms_est": ms_plain_step * fmax,
             "lat_speedup_vs_sync": ms_sync / ms_lat,
             "lat_speedup_vs_plain": ms_plain_step * fmax / ms_lat,
+            "learned_batched_speedup_vs_plain": ms_plain_step * fmax / ms_lat_sur,
             "effective_cell_updates_per_s": {"lat": upd / (ms_lat * 1e-3), "sync": upd / (ms_sync * 1e-3),
+                                             "learned_batched": upd / (ms_lat_sur * 1e-3),
                                              "plain": ncell / (ms_plain_step * 1e-3)},
+            "plain_form": "plain FP64 table bisection, default tiles, one launch sequence per block and stage",
+            "learned_batched_form": "learned guess + one FP64 Newton step, autotuned tiles, per-level batched "
+                                    "launches replayed as a CUDA graph",
             "lat_counters": lat_counts}
+
+
+def lat_counts_cells(lay, fac, fmax):
+    """Interior cell-stages of one LAT window (2 stages per update; slow blocks
+    also convert their ghost cells, which this count leaves out)."""
+    cells = np.array([b[3] * b[4] * b[5] for b in lay.blocks], dtype=np.int64)
+    return int((cells * (fmax // fac)).sum() * 2)
 
 
 # ------------------------------------------------------------------ oracle ---
