@@ -215,6 +215,12 @@ def run_gpu(args):
             ach = fp64_per_cell * ncell / (avg_ms * 1e-3)
             roof.update({"achieved": ach * 1e-12, "frac": ach / fp64_peak,
                          "fp64_flop_per_cell": fp64_per_cell})
+            slots = FP64_SLOTS_PER_CELL_SWEEP.get(dom)
+            if slots and KERNELS_AS_CAPTURED:
+                # the same kernel counted in FP64-pipe issue slots (peak = FMA rate / 2)
+                rate = slots * ncell / (avg_ms * 1e-3)
+                roof["fp64_issue"] = {"slots_per_cell": slots, "achieved_slots_per_s": rate,
+                                      "peak_slots_per_s": fp64_peak / 2, "frac": rate / (fp64_peak / 2)}
         else:
             roof.update({"achieved": None, "frac": None})
         total_launches = sum(v[0] for v in prof.values())
@@ -261,8 +267,11 @@ def run_gpu(args):
 # DRAM bytes of one launch; profiles/k_sweep_c2_entropy_wave_ncu.md holds the
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
 # False (traffic reported as null) whenever a sweep kernel changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 296.0, "sweep_y": 252.2, "sweep_z": 383.2}
-DRAM_BYTES_SWEEP = {"sweep_x": 268.0e6, "sweep_y": 402.4e6, "sweep_z": 542.4e6}
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 228.5, "sweep_y": 193.4, "sweep_z": 315.4}
+DRAM_BYTES_SWEEP = {"sweep_x": 266.7e6, "sweep_y": 398.6e6, "sweep_z": 543.3e6}
+# FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
+# holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
+FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 217.6, "sweep_y": 217.6, "sweep_z": 323.6}
 KERNELS_AS_CAPTURED = True
 
 
