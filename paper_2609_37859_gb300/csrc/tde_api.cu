@@ -652,6 +652,7 @@ extern "C" int tde_hydro_stage(tde_mesh *m, int stage, int nblk, const int32_t *
 extern "C" int tde_compute_dt(tde_mesh *m, double cfl, const double *t_block,
                               const tde_bh_state *bh, double *dt_block, double *dt_min) {
   if (!m || !m->U || !(cfl > 0.0)) return m ? fail(m->ctx, TDE_EINVAL, "tde_compute_dt: arguments") : TDE_EINVAL;
+  if (!closure_ready(m)) return fail(m->ctx, TDE_EINVAL, "tde_compute_dt: surrogate closure without a trained network");
   TimeArgs ta{nullptr, 0, t_block, 1};
   CK(m->ctx, launch_c2p(m, m->U, m->nb, m->d_allids, true, make_bh(bh), ta));
   CK(m->ctx, launch_dt_finalize(m, cfl, dt_block ? dt_block : m->d_dtb, dt_min));

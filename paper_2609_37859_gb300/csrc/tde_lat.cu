@@ -446,6 +446,7 @@ extern "C" int tde_lat_assign(tde_mesh *m, int n_lat, double merge_frac, double 
   tde_ctx *c = m->ctx;
   if (!m->U || n_lat < 0 || n_lat > 20 || !(cfl > 0.0) || merge_frac < 0.0)
     return lat_fail(c, TDE_EINVAL, "tde_lat_assign: arguments");
+  if (!closure_ready(m)) return lat_fail(c, TDE_EINVAL, "tde_lat_assign: surrogate closure without a trained network");
   int r = ensure_factor_buffers(m);
   if (r) return r;
   BH bh{};

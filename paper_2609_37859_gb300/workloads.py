@@ -275,3 +275,79 @@ def stream_c4(split_nearest=16, n_root=(10, 10, 4), block=32, ng=3, rp_rsun=10.0
     fields = {"rho": rho_cgs / RHO0_CGS, "vx": vx, "vy": vy, "vz": np.zeros_like(vx), "T": T}
     bh = {"GM": GM, "r_soft": 0.01 * RSUN_CODE, "r_exc": 0.4 * RSUN_CODE, "x0": (0.0, 0.0, 0.0)}
     return lay, fields, bh
+
+
+def lane_emden(n=1.5, h=1e-3):
+    """Lane-Emden function theta(xi) of index n by fourth-order Runge-Kutta from
+    the series start at small xi; returns (xi, theta, xi_1, -xi_1^2 theta'(xi_1))."""
+    xi0 = 1e-4
+    y = np.array([1.0 - xi0 ** 2 / 6.0, -xi0 / 3.0])
+
+    def f(x, v):
+        th = max(v[0], 0.0)
+        return np.array([v[1], -th ** n - 2.0 * v[1] / x])
+    xs, ths = [xi0], [y[0]]
+    x = xi0
+    while y[0] > 0.0:
+        k1 = f(x, y)
+        k2 = f(x + h / 2, y + h / 2 * k1)
+        k3 = f(x + h / 2, y + h / 2 * k2)
+        k4 = f(x + h, y + h * k3)
+        y_new = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        if y_new[0] <= 0.0:   # linear interpolation to the surface
+            t = y[0] / (y[0] - y_new[0])
+            x1 = x + t * h
+            dth = y[1] + t * (y_new[1] - y[1])
+            xs.append(x1)
+            ths.append(0.0)
+            return np.array(xs), np.array(ths), x1, -x1 * x1 * dth
+        x += h
+        y = y_new
+        xs.append(x)
+        ths.append(y[0])
+    raise RuntimeError("Lane-Emden integration did not reach the surface")
+
+
+def star_c5(n_blocks=(16, 16, 8), block=32, ng=3, half_rsun=(32.0, 32.0, 16.0), stretch=4.0,
+            star_at_rsun=(-10.0, 8.0), m_star=1.0, r_star_rsun=1.0, m_bh=1000.0,
+            bh_at_rsun=(0.0, 0.0, 0.0), bh_v_frac=0.05, rho_floor=1e-10, p_floor=1e-12, seed=0):
+    """Production-shaped workload: an n = 1.5 polytrope (m_star, r_star) stretched
+    along its direction of motion into an ellipsoid (long semi-axis stretch * R,
+    the other two R / sqrt(stretch): volume and mass kept), moving at the
+    parabolic speed about a point mass m_bh, with a seeded linear velocity
+    gradient along the long axis; the point mass moves slowly across the domain.
+    The ambient is the floor state of Table 1 (rho_floor, p_floor in code units).
+    Code units of Table 1 (length 2 Rsun, mass 1 Msun, G = 1/(4 pi)).  Uniform
+    grid of n_blocks blocks of `block`^3 cells on x, y in [-half, half] and z in
+    [-half_z, half_z] Rsun.  Returns (layout, fields, bh) with fields the global
+    arrays rho, vx, vy, vz, P (code units) and bh the point mass (position,
+    velocity, softening, excision radius)."""
+    rng = np.random.default_rng(seed)
+    N = tuple(n_blocks[a] * block for a in range(3))
+    domain = tuple((-h * RSUN_CODE, h * RSUN_CODE) for h in half_rsun)
+    lay = uniform_layout(N, (block, block, block), domain, (0, 0, 0), ng)
+    x, y, z = lay.cell_centres()
+    xi, th, xi1, mass_c = lane_emden(1.5)
+    R = r_star_rsun * RSUN_CODE
+    alpha = R / xi1
+    rho_c = m_star / (4.0 * np.pi * alpha ** 3 * mass_c)          # code units
+    P_c = 4.0 * np.pi * G_CODE * alpha ** 2 * rho_c ** 2 / 2.5     # (n + 1) = 2.5
+    a_l, a_t = stretch * R, R / np.sqrt(stretch)
+    xs, ys = (c * RSUN_CODE for c in star_at_rsun)
+    xp, yp = x - xs, y - ys
+    re = np.sqrt((xp / a_l) ** 2 + (yp / a_t) ** 2 + (z / a_t) ** 2)   # 1 at the surface
+    inside = re < 1.0
+    thv = np.where(inside, np.interp(np.minimum(re, 1.0) * xi1, xi, th), 0.0)
+    rho = rho_floor + rho_c * thv ** 1.5
+    P = p_floor + P_c * thv ** 2.5
+    GM = G_CODE * m_bh
+    bx = tuple(c * RSUN_CODE for c in bh_at_rsun)
+    r0 = np.hypot(xs - bx[0], ys - bx[1])
+    v_c = np.sqrt(2.0 * GM / r0)                                   # parabolic speed
+    kappa = rng.uniform(0.5, 1.0) * v_c / a_l                      # seeded shear rate
+    w = np.clip(thv * 20.0, 0.0, 1.0)                              # star moves, ambient at rest
+    vx = w * (v_c + kappa * xp)
+    fields = {"rho": rho, "vx": vx, "vy": np.zeros_like(vx), "vz": np.zeros_like(vx), "P": P}
+    bh = {"GM": GM, "r_soft": 0.01 * RSUN_CODE, "r_exc": 0.4 * RSUN_CODE, "x0": bx,
+          "v0": (0.0, bh_v_frac * v_c, 0.0), "v_star": v_c, "rho_c": rho_c, "P_c": P_c}
+    return lay, fields, bh

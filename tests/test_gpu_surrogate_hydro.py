@@ -6,6 +6,7 @@ convert their padded cells)."""
 import numpy as np
 import pytest
 
+from parity import assert_parity
 from paper_2609_37859_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -88,10 +89,49 @@ def test_closure_modes_identical_lat_window(oracle, tde, ctx, trained_tables):
         assert np.array_equal(outs[mode], outs["INVERT_BISECT"]), mode
 
 
-def test_surrogate_closure_needs_a_network(tde, ctx, tables):
+def test_surrogate_closure_needs_a_network(tde, ctx):
+    from test_gpu_hydro import TABLE_FILE
     lay = wl.uniform_layout((8, 8, 8), (8, 8, 8), bc=(1, 1, 1), ng=2)
-    tables[1].reset_weights_for_training()   # no network
+    fresh = tde.EOS.from_file(ctx, TABLE_FILE)   # no network
     m = tde.Mesh(ctx, lay, tde.make_params(eos=1, eos_mode=tde.INVERT_SURROGATE, rho_floor=1e-20,
-                                           p_floor=1e-20), tables[1])
-    with pytest.raises(tde.TDEError):
-        m.step(dt=1e-3)
+                                           p_floor=1e-20), fresh)
+    for call in (lambda: m.step(dt=1e-3), lambda: m.lat_assign(3, 0.3)):
+        with pytest.raises(tde.TDEError) as ei:
+            call()
+        assert ei.value.code == tde.TDE_EINVAL
+
+
+def test_c5_like_star_lat_surrogate_parity(oracle, tde, ctx, trained_tables):
+    """Reduced production-shaped run: a stretched n = 1.5 polytrope passing a
+    moving point mass with excision, PPM, Saha table in code units, dual energy,
+    the learned-guess closure, factors on 6 levels from the CFL assignment;
+    two LAT windows against the oracle (which inverts the table by its own
+    bisection)."""
+    # a resolved star (transverse radius ~3.4 cells) and floors 10^-4 / 10^-6: at
+    # this size the paper's floors leave a 10^11 density jump across a cell or two
+    lay, f, bhp = wl.star_c5(n_blocks=(4, 4, 2), block=8, half_rsun=(4.0, 4.0, 2.0),
+                             star_at_rsun=(-1.5, 1.0), bh_at_rsun=(1.5, -0.5, 0.0), stretch=2.0,
+                             r_star_rsun=1.2, rho_floor=1e-4, p_floor=1e-6, seed=5)
+    W = wl.prim_state(lay, f["rho"], f["vx"], f["vy"], f["vz"], f["P"])
+    bh = dict(on=1, excise=1, GM=bhp["GM"], r_soft=bhp["r_soft"], r_exc=bhp["r_exc"], x0=bhp["x0"],
+              v0=bhp["v0"])
+    scheme = dict(eos=1, recon=1, dual=1, eta1=1e-3, eta2=1e-4, rho_floor=1e-4, p_floor=1e-6,
+                  u_floor=1.5e-6, unit_rho=wl.RHO0_CGS, unit_e=wl.V0_CGS ** 2)
+    P = Pair(oracle, tde, ctx, lay, W, trained_tables, bh=bh, **scheme)
+    with_mode(tde, P, scheme, "INVERT_SURROGATE")
+    U = P.U.copy()
+    t = 0.0
+    P.gm.set_time(0.0)
+    P.gm.counts(reset=True)
+    for w in range(2):
+        dt = P.om.cfl_dt(U, 0.3, np.full(P.nb, t))
+        fo, dt0, fmax = P.om.lat_factors(dt, 6, 0.0)
+        fg, dt0g, fmaxg = P.gm.lat_assign(6, 0.3, 0.0, bh=P.bh)
+        assert np.array_equal(fg, fo) and fmaxg == fmax
+        P.om.lat_window(U, fo, dt0, t)
+        P.gm.lat_window(bh=P.bh, use_graph=(w == 1))
+        t += fmax * dt0
+    assert len(np.unique(fo)) >= 2
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), 1e-10, "C5-like LAT, learned closure")
+    c = P.gm.counts()
+    assert c["nonfinite"] == 0 and c["surrogate_accepted"] > 0
