@@ -248,12 +248,14 @@ def run_gpu(args):
         if not args.no_eos:
             line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
             line["closure_modes"] = closure_bench(mesh, U_init, tde, torch, dev, args)
+        elif not (args.no_lat and args.no_c5):   # their learned arms need the network
+            eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
+        del mesh, U_init, host_in, host_out
+        torch.cuda.empty_cache()
         if not args.no_lat:
-            if args.no_eos:   # the learned arm needs the network
-                eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
-            del mesh
-            torch.cuda.empty_cache()
             line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
+        if not args.no_c5:
+            line["c5_production"] = c5_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -509,6 +511,94 @@ def lat_counts_cells(lay, fac, fmax):
     return int((cells * (fmax // fac)).sum() * 2)
 
 
+# ------------------------------------------------------ production shape (C5) ---
+
+# rho_floor (rho0), p_floor (rho0 v0^2): 100x Table 1's.  With Table 1's floors
+# this unrelaxed star (no self-gravity, floor gas falling onto the point mass)
+# leaves ~7e4 non-finite cell-stages per window; with these, none.
+C5_FLOORS = (1e-8, 1e-10)
+
+
+def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
+    """The production-shaped run: 2048 x 32^3 MeshBlocks (67 M cells), PPM + HLLC,
+    Saha table in code units with the learned-guess closure, dual energy, the
+    floors of Table 1, a stretched n = 1.5 polytrope (1 Msun, 1 Rsun) passing a
+    moving 1e3 Msun point mass with excision; factors on N_LAT = 6 levels,
+    re-assigned at every window; LAT windows covering 200 fine steps (at most 4
+    windows), replayed as a CUDA graph, against synchronised steps of dt0."""
+    from paper_2609_37859_gb300 import workloads as wl
+    t_setup = time.time()
+    lay, f, bhp = wl.star_c5(seed=SEED, rho_floor=floors[0], p_floor=floors[1])
+    W = wl.prim_state(lay, f["rho"], f["vx"], f["vy"], f["vz"], f["P"])
+    del f
+    params = tde.make_params(eos=tde.EOS_TABLE, recon=tde.RECON_PPM, dual=1, eta1=1e-3, eta2=1e-4,
+                             rho_floor=floors[0], p_floor=floors[1], u_floor=1.5 * floors[1],
+                             unit_rho=wl.RHO0_CGS, unit_e=wl.V0_CGS ** 2, eos_mode=tde.INVERT_SURROGATE)
+    mesh = tde.Mesh(ctx, lay, params, eos)
+    mesh.prim_to_cons(torch.from_numpy(W).to(dev))
+    del W
+    bh = tde.make_bh(on=1, excise=1, GM=bhp["GM"], r_soft=bhp["r_soft"], r_exc=bhp["r_exc"],
+                     x0=bhp["x0"], v0=bhp["v0"])
+    setup_s = time.time() - t_setup
+    tiles, tile_ms = mesh.autotune(bh=bh, reps=1)
+    fac, dt0, fmax = mesh.lat_assign(6, CFL, merge_frac=0.01, bh=bh)
+    cells = np.array([b[3] * b[4] * b[5] for b in lay.blocks], dtype=np.float64)
+    work = float((cells * (fmax // fac)).sum() / (cells.sum() * fmax))
+    levels = {int(k): int((fac == k).sum()) for k in np.unique(fac)}
+    nwin = int(max(1, min(4, -(-200 // fmax))))
+    U0 = mesh.U.clone()
+
+    def timed(fn, reps):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    mesh.lat_set_factors(fac, dt0)
+    mesh.lat_window(bh=bh, use_graph=False)   # warm-up: eager, then capture
+    mesh.lat_window(bh=bh, use_graph=True)
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+    mesh.counts(reset=True)
+    fmaxes, structures = [], set()
+
+    def window():
+        # as in production: factors from the CFL condition at each window start
+        # (the captured window is kept while the levels keep their sizes)
+        fw, _, fm = mesh.lat_assign(6, CFL, merge_frac=0.01, bh=bh)
+        fmaxes.append(int(fm))
+        structures.add(tuple(int((fw == k).sum()) for k in (1, 2, 4, 8, 16, 32, 64)))
+        mesh.lat_window(bh=bh, use_graph=True)
+    ms_win = timed(window, nwin)
+    c = mesh.counts(reset=True)
+    # synchronised steps of dt0 (two timed) for the same physical time
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+    mesh.step(dt=dt0, bh=bh)
+    ms_step = timed(lambda: mesh.step(dt=dt0, bh=bh), 2)
+    ncell = lay.ncells
+    del mesh, U0
+    torch.cuda.empty_cache()
+    return {"workload": "stretched n=1.5 polytrope (1 Msun, 1 Rsun, 4:1) passing a moving 1e3 Msun point "
+                        "mass with excision, 2048 x 32^3 MeshBlocks, PPM+HLLC, Saha table, learned-guess "
+                        "closure, dual energy, Table 1 floors, N_LAT 6",
+            "cells": ncell, "meshblocks": lay.nb, "f_max": int(fmax), "blocks_per_factor": levels,
+            "work_fraction": work, "windows": nwin, "fine_steps": nwin * int(fmax),
+            "autotune": autotune_report(tiles, tile_ms),
+            "window_f_max": fmaxes, "distinct_level_structures": len(structures),
+            "lat_window_ms": ms_win, "sync_step_ms": ms_step, "sync_window_ms_est": ms_step * fmax,
+            "lat_speedup_vs_sync": ms_step * np.mean(fmaxes) / ms_win,
+            "effective_cell_updates_per_s": ncell * np.mean(fmaxes) / (ms_win * 1e-3),
+            "sync_cell_updates_per_s": ncell / (ms_step * 1e-3),
+            "floors": {"rho_floor": floors[0], "p_floor": floors[1], "unit": "rho0, rho0 v0^2"},
+            "counters_per_window": {k: v // nwin for k, v in c.items()},
+            "host_setup_s": setup_s}
+
+
 # ------------------------------------------------------------------ oracle ---
 
 def oracle_setup(sample_blocks):
@@ -588,6 +678,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--no-c5", action="store_true", help="skip the production-shaped LAT run")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -324,6 +324,7 @@ int lat_build(tde_mesh *m) {
   std::iota(m->h_sorted.begin(), m->h_sorted.end(), 0);
   std::stable_sort(m->h_sorted.begin(), m->h_sorted.end(),
                    [&](int a, int b) { return m->h_f[a] < m->h_f[b]; });
+  const std::vector<int> old_levels = m->h_levels, old_start = m->h_level_start;
   m->h_levels.clear();
   m->h_level_start.clear();
   for (int q = 0; q < nb; ++q) {
@@ -360,7 +361,9 @@ int lat_build(tde_mesh *m) {
   LCK(c, cudaMemcpyAsync(m->d_f, m->h_f.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, c->stream));
   LCK(c, cudaStreamSynchronize(c->stream));
   m->lat_ready = true;
-  invalidate_graph(m);
+  // a captured window reads the block lists, factors and dt0 from device memory
+  // when it is replayed; it stays valid while the levels and their sizes do
+  if (m->h_levels != old_levels || m->h_level_start != old_start) invalidate_graph(m);
   return TDE_OK;
 }
 

@@ -308,20 +308,23 @@ def lane_emden(n=1.5, h=1e-3):
     raise RuntimeError("Lane-Emden integration did not reach the surface")
 
 
-def star_c5(n_blocks=(16, 16, 8), block=32, ng=3, half_rsun=(32.0, 32.0, 16.0), stretch=4.0,
-            star_at_rsun=(-10.0, 8.0), m_star=1.0, r_star_rsun=1.0, m_bh=1000.0,
-            bh_at_rsun=(0.0, 0.0, 0.0), bh_v_frac=0.05, rho_floor=1e-10, p_floor=1e-12, seed=0):
+def star_c5(n_blocks=(16, 16, 8), block=32, ng=3, half_rsun=(16.0, 16.0, 8.0), stretch=4.0,
+            star_at_rsun=(0.0, 0.0), m_star=1.0, r_star_rsun=1.0, m_bh=1000.0,
+            bh_at_rsun=(12.0, 10.0, 0.0), shear=0.1, rho_floor=1e-10, p_floor=1e-12,
+            inflow_rsun=4.0, seed=0):
     """Production-shaped workload: an n = 1.5 polytrope (m_star, r_star) stretched
-    along its direction of motion into an ellipsoid (long semi-axis stretch * R,
-    the other two R / sqrt(stretch): volume and mass kept), moving at the
-    parabolic speed about a point mass m_bh, with a seeded linear velocity
-    gradient along the long axis; the point mass moves slowly across the domain.
-    The ambient is the floor state of Table 1 (rho_floor, p_floor in code units).
-    Code units of Table 1 (length 2 Rsun, mass 1 Msun, G = 1/(4 pi)).  Uniform
-    grid of n_blocks blocks of `block`^3 cells on x, y in [-half, half] and z in
-    [-half_z, half_z] Rsun.  Returns (layout, fields, bh) with fields the global
-    arrays rho, vx, vy, vz, P (code units) and bh the point mass (position,
-    velocity, softening, excision radius)."""
+    along x into an ellipsoid (long semi-axis stretch * R, the other two
+    R / sqrt(stretch): volume and mass kept), in the frame that moves with the
+    star (the paper's runs start in such a translating frame): the gas carries
+    only a seeded linear velocity gradient along the long axis, and the point
+    mass m_bh passes at the parabolic speed for its initial distance, moving
+    along -x.  The ambient is the floor state of Table 1 (rho_floor, p_floor in
+    code units); within inflow_rsun of the point mass it moves with it and falls
+    in at the free-fall speed.  Code units of Table 1 (length 2 Rsun, mass 1 Msun,
+    G = 1/(4 pi)).  Uniform grid of n_blocks blocks of `block`^3 cells on x, y in
+    [-half, half] and z in [-half_z, half_z] Rsun.  Returns (layout, fields, bh)
+    with fields the global arrays rho, vx, vy, vz, P (code units) and bh the point
+    mass (position, velocity, softening, excision radius)."""
     rng = np.random.default_rng(seed)
     N = tuple(n_blocks[a] * block for a in range(3))
     domain = tuple((-h * RSUN_CODE, h * RSUN_CODE) for h in half_rsun)
@@ -344,10 +347,26 @@ def star_c5(n_blocks=(16, 16, 8), block=32, ng=3, half_rsun=(32.0, 32.0, 16.0), 
     bx = tuple(c * RSUN_CODE for c in bh_at_rsun)
     r0 = np.hypot(xs - bx[0], ys - bx[1])
     v_c = np.sqrt(2.0 * GM / r0)                                   # parabolic speed
-    kappa = rng.uniform(0.5, 1.0) * v_c / a_l                      # seeded shear rate
-    w = np.clip(thv * 20.0, 0.0, 1.0)                              # star moves, ambient at rest
-    vx = w * (v_c + kappa * xp)
-    fields = {"rho": rho, "vx": vx, "vy": np.zeros_like(vx), "vz": np.zeros_like(vx), "P": P}
+    kappa = rng.uniform(0.5, 1.0) * shear * v_c / a_l              # seeded shear rate
+    w = np.clip(thv * 20.0, 0.0, 1.0)                              # the star's gas only
+    vx = w * kappa * xp
+    vy = np.zeros_like(vx)
+    vz = np.zeros_like(vx)
+    # floor gas near the point mass already falls in (radially in its frame,
+    # free-fall speed of the softened potential, blended to rest at r_in), so the
+    # run starts from the quasi-steady inflow instead of its transient
+    rx, ry, rz = x - bx[0], y - bx[1], z - bx[2]
+    r = np.sqrt(rx ** 2 + ry ** 2 + rz ** 2)
+    r_in = inflow_rsun * RSUN_CODE
+    r_s = 0.01 * RSUN_CODE
+    u_ff = np.sqrt(2.0 * GM * np.maximum(1.0 / np.sqrt(r ** 2 + r_s ** 2) - 1.0 / np.sqrt(r_in ** 2 + r_s ** 2), 0.0))
+    blend = np.where(r < r_in, 1.0 - w, 0.0)
+    u = np.where(r < r_in, u_ff, 0.0) * blend
+    rr = np.maximum(r, 1e-30)
+    vx += blend * (-v_c) - u * rx / rr
+    vy += -u * ry / rr
+    vz += -u * rz / rr
+    fields = {"rho": rho, "vx": vx, "vy": vy, "vz": vz, "P": P}
     bh = {"GM": GM, "r_soft": 0.01 * RSUN_CODE, "r_exc": 0.4 * RSUN_CODE, "x0": bx,
-          "v0": (0.0, bh_v_frac * v_c, 0.0), "v_star": v_c, "rho_c": rho_c, "P_c": P_c}
+          "v0": (-v_c, 0.0, 0.0), "v_star": v_c, "rho_c": rho_c, "P_c": P_c}
     return lay, fields, bh

@@ -130,3 +130,23 @@ def test_lat_mixed_block_sizes_table_eos_bh_excision(oracle, tde, ctx, tables):
     assert fmax > 1
     assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), 1e-10, "C4-like LAT")
     assert P.gm.counts()["nonfinite"] == 0
+
+
+def test_lat_graph_survives_reassignment_with_same_levels(oracle, tde, ctx):
+    """A re-assignment that keeps the levels and their sizes (here: the factors
+    moved between blocks) keeps the captured window, which then reads the new
+    block lists; the result equals eager windows with the same factors."""
+    P = smooth_pair(oracle, tde, ctx, bh=dict(on=1, GM=0.02, r_soft=0.1, x0=(0.5, 0.25, 0.25)))
+    f1 = band_factors(P.layout, (1, 2, 4, 2))
+    f2 = np.roll(f1, 3)
+    assert sorted(f1) == sorted(f2) and not np.array_equal(f1, f2)
+    dt0 = 0.4 * P.om.cfl_dt(P.U, 0.3).min() / f1.max()
+    outs = []
+    for use_graph in (False, True):
+        P.gm.U.copy_(torch.from_numpy(P.U))
+        P.gm.set_time(0.0)
+        for f in (f1, f2, f1):
+            P.gm.lat_set_factors(f, dt0)
+            P.gm.lat_window(bh=P.bh, use_graph=use_graph)
+        outs.append(P.gpu("U").copy())
+    assert np.array_equal(outs[0], outs[1])
