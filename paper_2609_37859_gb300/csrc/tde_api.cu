@@ -214,6 +214,7 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
   t.nt = n_T;
   t.lr0 = lr_min;
   t.inv_dlr = (n_rho - 1) / (lr_max - lr_min);
+  t.xr_max = (double)(n_rho - 1);
   t.lt0 = lT_min;
   t.dlt = (lT_max - lT_min) / (n_T - 1);
   t.le = e->d_data;
@@ -226,6 +227,7 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
       const long double F = j / 128.0L;
       h.logF[j] = j > 0 ? (double)logl(F) : 0.0;
       h.invF[j] = j > 0 ? (double)(1.0L / F) : 0.0;
+      h.F[j] = j / 128.0;
     }
     for (int j = 0; j < 128; ++j) h.exp2j[j] = (double)exp2l(j / 128.0L);
     err = cudaMalloc(&e->d_mt, sizeof(MathTables));

@@ -17,6 +17,46 @@ namespace tde {
 enum { EOS_IDEAL = 0, EOS_TABLE = 1 };
 enum { PLM = 0, PPM = 1 };
 
+// ------------------------------------- comparisons on the integer pipe ----
+//
+// A double's bit pattern, read as a signed 64-bit integer, orders positive
+// values like the values themselves; flipping the magnitude bits of negative
+// patterns extends that to a total order (-0 just below +0).  Comparisons,
+// minima and maxima written this way run on the integer ALUs, which sit idle
+// while the FP64 pipe (where DSETP and DMNMX would issue) bounds the path.
+// For NaN operands they are not the IEEE predicates; the kernels count
+// non-finite states rather than rely on comparisons with NaN.
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// order key: key(a) < key(b) iff a < b for non-NaN a, b (except -0 < +0)
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool dgt0(double x) { return dbits(x) > 0; }          // x > 0
+__device__ __forceinline__ bool dge0(double x) { return dkey(x) >= -1; }         // x >= 0 (incl. -0)
+__device__ __forceinline__ bool dle0(double x) { return dkey(x) <= 0; }          // x <= 0 (incl. +0)
+__device__ __forceinline__ bool dzero(double x) { return (dbits(x) << 1) == 0; }  // x == +-0
+__device__ __forceinline__ bool dlt(double a, double b) { return dkey(a) < dkey(b); }
+__device__ __forceinline__ bool dle(double a, double b) { return dkey(a) <= dkey(b); }
+__device__ __forceinline__ double dmin(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }
+__device__ __forceinline__ double dmax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+__device__ __forceinline__ bool dfinite(double x) { return ((dbits(x) >> 52) & 0x7ff) != 0x7ff; }
+// the double value of a small integer |k| < 2^51, by one FP64 add
+__device__ __forceinline__ double dint(long long k) {
+  return __longlong_as_double(0x4338000000000000LL + k) - 6755399441055744.0;
+}
+// x truncated to FP32 on the integer pipe (a guide value: normal x with
+// 2^-126 <= |x| < 2^128, or zero)
+__device__ __forceinline__ float d2f_guide(double x) {
+  const long long b = dbits(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  const unsigned u = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)e << 23) |
+                     (unsigned)((b >> 29) & 0x7fffff);
+  return __uint_as_float(u);
+}
+
 // ------------------------------------------------ log10 / exp10 (FP64) ----
 //
 // Table-driven logarithm and exponential after P. T. P. Tang (ACM TOMS 15, 1989:
@@ -30,6 +70,7 @@ enum { PLM = 0, PPM = 1 };
 struct MathTables {
   double logF[182];    // ln(j/128), j = 90 .. 181 (the reduced argument's table points)
   double invF[182];    // 128 / j
+  double F[182];       // j / 128
   double exp2j[128];   // 2^(j/128)
 };
 
@@ -44,7 +85,7 @@ __device__ __forceinline__ double fast_log10(const MathTables *__restrict__ mt, 
   const int k = upper ? ex - 1022 : ex - 1023;
   const double m = __longlong_as_double(mant | (upper ? 0x3fe0000000000000LL : 0x3ff0000000000000LL));
   const int j = upper ? 64 + (int)((mant + (1LL << 45)) >> 46) : 128 + (int)((mant + (1LL << 44)) >> 45);
-  const double F = j * (1.0 / 128.0);
+  const double F = __ldg(&mt->F[j]);
   const double r = __dmul_rn(__dsub_rn(m, F), __ldg(&mt->invF[j]));    // |r| <= 2^-7.5
   // ln(1 + r) = r - r^2/2 + ... + r^7/7 (the next term, r^8/8, is below 2^-55.5
   // relative to the result for |r| <= 2^-7.5)
@@ -55,7 +96,7 @@ __device__ __forceinline__ double fast_log10(const MathTables *__restrict__ mt, 
   q = __fma_rn(q, r, 1.0 / 3.0);
   q = __fma_rn(q, r, -0.5);
   const double lp = __fma_rn(__dmul_rn(q, r), r, r);
-  const double kd = (double)k;
+  const double kd = dint(k);
   const double ln2_hi = 0.6931471803691238;   // 32 significant bits: k * ln2_hi is exact
   const double ln2_lo = 1.9082149292705877e-10;
   const double hi = __fma_rn(kd, ln2_hi, __ldg(&mt->logF[j]));
@@ -64,9 +105,11 @@ __device__ __forceinline__ double fast_log10(const MathTables *__restrict__ mt, 
 }
 
 __device__ __forceinline__ double fast_exp10(const MathTables *__restrict__ mt, double x) {
-  if (!(fabs(x) < 300.0)) return exp10(x);
-  // 10^x = 2^(n/128) 10^r with n = round(128 x log2 10), r = x - n log10(2)/128
-  const double n = rint(__dmul_rn(x, 425.20679614558236));   // 128 log2(10)
+  if (!((dbits(x) & 0x7fffffffffffffffLL) < dbits(300.0))) return exp10(x);   // |x| < 300
+  // 10^x = 2^(n/128) 10^r with n = round(128 x log2 10), r = x - n log10(2)/128;
+  // adding 1.5 2^52 rounds to an integer in the low mantissa bits
+  const double big = __fma_rn(x, 425.20679614558236, 6755399441055744.0);   // 128 log2(10)
+  const double n = __dsub_rn(big, 6755399441055744.0);
   const double c_hi = 0.002351796840230236;   // log10(2)/128, 32 significant bits
   const double c_lo = 8.946172576579561e-13;
   const double r = __fma_rn(-n, c_lo, __fma_rn(-n, c_hi, x));   // |r| <= log10(2)/256
@@ -78,7 +121,7 @@ __device__ __forceinline__ double fast_exp10(const MathTables *__restrict__ mt, 
   q = __fma_rn(q, u, 1.0 / 6.0);
   q = __fma_rn(q, u, 0.5);
   const double eu = __fma_rn(__dmul_rn(q, u), u, u);
-  const int ni = (int)n;
+  const int ni = (int)dbits(big);   // n, from the low bits
   const int jj = ni & 127, kk = ni >> 7;
   const double tj = __ldg(&mt->exp2j[jj]);
   const double v = __fma_rn(tj, eu, tj);   // 2^(jj/128) e^u
@@ -89,6 +132,7 @@ __device__ __forceinline__ double fast_exp10(const MathTables *__restrict__ mt, 
 struct DTable {
   int nr, nt;
   double lr0, inv_dlr, lt0, dlt;
+  double xr_max;                   // nr - 1 (the largest density coordinate)
   const double *__restrict__ le;   // log10 e
   const double *__restrict__ lp;   // log10 P
   const double *__restrict__ lc;   // log10 cs^2
@@ -182,12 +226,23 @@ __device__ __forceinline__ double sqrt_ratio(double a, double b) {
 __device__ __forceinline__ bool rho_cell(const DTable &t, double rho, int &i, double &w) {
   double x = (tlog10(t, rho) - t.lr0) * t.inv_dlr;
   bool cl = false;
-  if (!(x >= 0.0)) { x = 0.0; cl = true; }
-  if (x > (double)(t.nr - 1)) { x = (double)(t.nr - 1); cl = true; }
-  int ii = (int)floor(x);
-  if (ii > t.nr - 2) ii = t.nr - 2;
+  if (!dge0(x) || (dbits(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) { x = 0.0; cl = true; }  // < 0, NaN
+  if (dlt(t.xr_max, x)) { x = t.xr_max; cl = true; }
+  // i = floor(x) and w = x - i from the bit fields (0 <= x <= nr - 1 < 2^31); the
+  // same values as the FP64 floor and subtraction, without the FP64 pipe
+  const long long b = dbits(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  int ii;
+  if (e < 0) {
+    ii = 0;
+    w = x;
+  } else {
+    const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;
+    ii = (int)(m >> (52 - e));
+    w = __longlong_as_double(0x3ff0000000000000LL | ((m << e) & 0xfffffffffffffLL)) - 1.0;
+  }
+  if (ii > t.nr - 2) { ii = t.nr - 2; w = 1.0; }   // x = nr - 1 exactly
   i = ii;
-  w = x - ii;
   return cl;
 }
 
@@ -214,7 +269,7 @@ __device__ __forceinline__ double cell_solve(double y, double g0, double g1) {
   return __dmul_rn(__dsub_rn(y, g0), rcp_nr(__dsub_rn(g1, g0)));
 }
 __device__ __forceinline__ double cell_log10T(const DTable &t, int j, double s) {
-  return __fma_rn(__dadd_rn((double)j, s), t.dlt, t.lt0);
+  return __fma_rn(__dadd_rn(dint(j), s), t.dlt, t.lt0);
 }
 
 // (rho, e) -> P, cs2 (cgs) by binary search of the interpolated log10 e column
@@ -233,12 +288,12 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
   const double *__restrict__ b = a + nt;
   double glo = lerp_rn(w, __ldg(a), __ldg(b));
   double ghi = lerp_rn(w, __ldg(a + nt - 1), __ldg(b + nt - 1));
-  double y = e > 0.0 ? tlog10(t, e) : -INFINITY;
+  double y = dgt0(e) ? tlog10(t, e) : -INFINITY;
   int j;
   double s;
-  if (!(y > glo)) {
+  if (!dlt(glo, y)) {
     j = 0; s = 0.0; cl = true;
-  } else if (y >= ghi) {
+  } else if (dle(ghi, y)) {
     j = nt - 2; s = 1.0; cl = true;
   } else {
     // search in FP32 (FP64 issues 55x slower on this part), then confirm the cell
@@ -250,7 +305,7 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
     if (t.le32) {   // tables without the FP32 copy (caller-owned views) skip this
       const float *__restrict__ a32 = t.le32 + (size_t)i * nt;
       const float *__restrict__ b32 = a32 + nt;
-      const float w32 = (float)w, y32 = (float)y;
+      const float w32 = d2f_guide(w), y32 = d2f_guide(y);
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         const float a0 = __ldg(a32 + mid);
@@ -261,13 +316,13 @@ __device__ __forceinline__ bool eos_invert(const DTable &t, double rho, double e
     j = lo;
     double g0 = lerp_rn(w, __ldg(a + j), __ldg(b + j));
     double g1 = lerp_rn(w, __ldg(a + j + 1), __ldg(b + j + 1));
-    if (!(g0 <= y && y < g1)) {
+    if (!(dle(g0, y) && dlt(y, g1))) {
       lo = 0;
       hi = nt - 1;
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         const double g = lerp_rn(w, __ldg(a + mid), __ldg(b + mid));
-        if (g <= y) lo = mid; else hi = mid;
+        if (dle(g, y)) lo = mid; else hi = mid;
       }
       j = lo;
       g0 = lerp_rn(w, __ldg(a + j), __ldg(b + j));
@@ -346,13 +401,13 @@ template <int DUAL>
 __device__ __forceinline__ void c2p_energy(const Phys &p, const double *u, double &rho, double &vx,
                                            double &vy, double &vz, double &Ue, Counters *cnt) {
   rho = u[0];
-  if (rho < p.rho_floor) { rho = p.rho_floor; if (cnt) count(&cnt->rho_floor); }
+  if (dlt(rho, p.rho_floor)) { rho = p.rho_floor; if (cnt) count(&cnt->rho_floor); }
   double ir = rcp_nr(rho);
   vx = u[1] * ir; vy = u[2] * ir; vz = u[3] * ir;
   double Uc = u[4] - 0.5 * (u[1] * vx + u[2] * vy + u[3] * vz);   // Eq. dual-econs
   Ue = Uc;
   if (DUAL) {
-    if (!(Uc > 0.0 && Uc > p.eta1 * u[4])) { Ue = u[5]; if (cnt) count(&cnt->dual_aux_used); }
+    if (!(dgt0(Uc) && dlt(p.eta1 * u[4], Uc))) { Ue = u[5]; if (cnt) count(&cnt->dual_aux_used); }
   }
 }
 
@@ -367,7 +422,7 @@ __device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, dou
   c2p_energy<DUAL>(p, u, rho, vx, vy, vz, Ue, cnt);
   double P, cs2, Uu;
   eos_closure<EOSK, EOSB>(p, rho, Ue, P, cs2, Uu, cnt, eb, flat);
-  if (P < p.p_floor) { P = p.p_floor; if (cnt) count(&cnt->p_floor); }
+  if (dlt(P, p.p_floor)) { P = p.p_floor; if (cnt) count(&cnt->p_floor); }
   w[0] = rho; w[1] = vx; w[2] = vy; w[3] = vz; w[4] = P;
   if (EOSK == EOS_TABLE) {
     w[5] = 1.0 + P * rcp_nr(Uu);         // Gamma_e
@@ -384,7 +439,7 @@ __device__ __forceinline__ void cons_to_prim(const Phys &p, const double *u, dou
 __device__ __forceinline__ void plm(double qm, double q0, double qp, double &left, double &right) {
   double dl = q0 - qm, dr = qp - q0;
   double pr = dl * dr;
-  double h = (pr > 0.0) ? pr * rcp_nr(dl + dr) : 0.0;
+  double h = dgt0(pr) ? pr * rcp_nr(dl + dr) : 0.0;
   left = q0 - h;
   right = q0 + h;
 }
@@ -392,20 +447,20 @@ __device__ __forceinline__ void plm(double qm, double q0, double qp, double &lef
 // PPM: 4th-order interface value between q0 and q1, clipped to [q0, q1]
 __device__ __forceinline__ double ppm_iface(double qm1, double q0, double q1, double q2) {
   double a = (7.0 / 12.0) * (q0 + q1) - (1.0 / 12.0) * (qm1 + q2);
-  double lo = fmin(q0, q1), hi = fmax(q0, q1);
-  return fmin(fmax(a, lo), hi);
+  double lo = dmin(q0, q1), hi = dmax(q0, q1);
+  return dmin(dmax(a, lo), hi);
 }
 
 // Colella-Woodward (1984) monotonicity constraints on the parabola (aL, q0, aR)
 __device__ __forceinline__ void ppm_limit(double q0, double &aL, double &aR) {
-  if ((aR - q0) * (q0 - aL) <= 0.0) {
+  if (dle0((aR - q0) * (q0 - aL))) {
     aL = q0;
     aR = q0;
   } else {
     double da = aR - aL;
     double q6 = 6.0 * (q0 - 0.5 * (aL + aR));
-    if (da * q6 > da * da) aL = 3.0 * q0 - 2.0 * aR;
-    else if (-(da * da) > da * q6) aR = 3.0 * q0 - 2.0 * aL;
+    if (dlt(da * da, da * q6)) aL = 3.0 * q0 - 2.0 * aR;
+    else if (dlt(da * q6, -(da * da))) aR = 3.0 * q0 - 2.0 * aL;
   }
 }
 
@@ -430,19 +485,19 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   double Ur = EOSK == EOS_IDEAL ? R.P * p.inv_gm1 : R.P * rcp_nr(R.ge - 1.0);
   double El = Ul + 0.5 * L.r * (L.v[0] * L.v[0] + L.v[1] * L.v[1] + L.v[2] * L.v[2]);
   double Er = Ur + 0.5 * R.r * (R.v[0] * R.v[0] + R.v[1] * R.v[1] + R.v[2] * R.v[2]);
-  double SL = fmin(ul - cl, ur - cr);
-  double SR = fmax(ul + cl, ur + cr);
+  double SL = dmin(ul - cl, ur - cr);
+  double SR = dmax(ul + cl, ur + cr);
   double al = L.r * (SL - ul), ar = R.r * (SR - ur);
   double SM = (R.P - L.P + al * ul - ar * ur) * rcp_nr(al - ar);
-  bool supL = SL >= 0.0, supR = SR <= 0.0;
-  bool useL = supL || (!supR && SM >= 0.0);
+  bool supL = dge0(SL), supR = dle0(SR);
+  bool useL = supL || (!supR && dge0(SM));
   // chosen side K
   double r = useL ? L.r : R.r, un = useL ? ul : ur, P = useL ? L.P : R.P, E = useL ? El : Er;
   double vt1 = useL ? L.v[t1] : R.v[t1], vt2 = useL ? L.v[t2] : R.v[t2];
   double S = useL ? SL : SR;
   double Seff = (supL || supR) ? 0.0 : S;
   double den = S - SM;
-  if (den == 0.0) den = 1.0;   // only reachable when Seff == 0
+  if (dzero(den)) den = 1.0;   // only reachable when Seff == 0
   double rS = r * (S - un);
   double inv = rcp_nr(den);
   double fac = rS * inv;
@@ -464,11 +519,11 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   F[4] = (E + P) * un + Seff * dE;
   if (DUAL) {
     double f = F[0];
-    bool up = f > 0.0;
+    bool up = dgt0(f);
     double ru = up ? L.r : R.r, Au = up ? L.A : R.A;
     double iru = rcp_nr(ru);
-    F[5] = f != 0.0 ? f * (Au * iru) : 0.0;
-    vf = f != 0.0 ? f * iru : 0.0;
+    F[5] = !dzero(f) ? f * (Au * iru) : 0.0;
+    vf = !dzero(f) ? f * iru : 0.0;
   } else {
     F[5] = 0.0;
     vf = 0.0;

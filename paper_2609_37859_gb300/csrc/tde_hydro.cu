@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         double rate = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          if (p.active[a]) rate = fmax(rate, (fabs(w[1 + a]) + cs) * p.idx[a]);
-        best = fmin(best, rcp_nr(rate));
+          if (p.active[a]) rate = dmax(rate, (fabs(w[1 + a]) + cs) * p.idx[a]);
+        best = dmin(best, rcp_nr(rate));
         if (bh.on) {
           double s2 = r2 + bh.rs2;
           double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));

@@ -260,10 +260,27 @@ __device__ __forceinline__ long long cm_flat(const CellMap &cm, int bp, long lon
   if (!cm.blocks) return local;
   const DevBlock &B = cm.blocks[cm.ids[bp]];
   if (cm.padded) return B.off + local;
-  const int i = (int)(local % B.n[0]);
-  const long long r = local / B.n[0];
-  const int j = (int)(r % B.n[1]), k = (int)(r / B.n[1]);
+  // 32-bit division only (a block has < 2^31 cells; 64-bit division would
+  // take the FP64 pipe)
+  const unsigned l = (unsigned)local, nx = (unsigned)B.n[0], ny = (unsigned)B.n[1];
+  const unsigned r = l / nx;
+  const int i = (int)(l - r * nx), k = (int)(r / ny), j = (int)(r - (unsigned)k * ny);
   return B.off + ((long long)(k + cm.g[2]) * B.p[1] + (j + cm.g[1])) * B.p[0] + (i + cm.g[0]);
+}
+
+// Split a tile or chunk index of a cell map into (block position, first cell),
+// per = tiles or chunks per block, size = cells per tile or chunk; 32-bit
+// division (counts < 2^31), none for plain arrays.
+__device__ __forceinline__ void cm_split(const CellMap &cm, long long t, long long per, int size, int &bp,
+                                         long long &first) {
+  if (!cm.blocks) {
+    bp = 0;
+    first = t * size;
+    return;
+  }
+  const unsigned q = (unsigned)t / (unsigned)per;
+  bp = (int)q;
+  first = (long long)((unsigned)t - q * (unsigned)per) * size;
 }
 
 __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
@@ -309,10 +326,12 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   const long long tpb = (a.n + IT - 1) / IT;
   const long long ntiles = tpb * (a.cm.blocks ? a.cm.nblk : 1);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int bp = (int)(tile / tpb);
-    const long long local = (tile - (long long)bp * tpb) * IT + tid;
+    int bp;
+    long long first;
+    cm_split(a.cm, tile, tpb, IT, bp, first);
     const long long ncell = cm_cells(a.cm, a.n, bp);
-    if ((tile - (long long)bp * tpb) * IT >= ncell) continue;   // the whole tile (uniform)
+    if (first >= ncell) continue;   // the whole tile (uniform)
+    const long long local = first + tid;
     const bool live = local < ncell;
     const long long c = live ? cm_flat(a.cm, bp, local) : 0;
     // ---- inputs and layer 1, FP32 only: the network needs log10 rho and the
@@ -463,8 +482,9 @@ __global__ void __launch_bounds__(256) k_eos_newton(DTable t, CellMap cm, const 
   unsigned n_acc = 0;
   // every thread of the CTA runs the same chunks (the CTA votes below)
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int bp = (int)(ch / cpb);
-    const long long local0 = (ch - (long long)bp * cpb) * 256;
+    int bp;
+    long long local0;
+    cm_split(cm, ch, cpb, 256, bp, local0);
     const long long ncell = cm_cells(cm, n, bp);
     if (local0 >= ncell) continue;   // uniform over the CTA
     const long long local = local0 + threadIdx.x;

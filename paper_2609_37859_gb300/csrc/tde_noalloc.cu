@@ -201,6 +201,7 @@ extern "C" int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block
     p.tab.nt = table->n_T;
     p.tab.lr0 = table->log10_rho_min;
     p.tab.inv_dlr = (table->n_rho - 1) / (table->log10_rho_max - table->log10_rho_min);
+    p.tab.xr_max = (double)(table->n_rho - 1);
     p.tab.lt0 = table->log10_T_min;
     p.tab.dlt = (table->log10_T_max - table->log10_T_min) / (table->n_T - 1);
     p.tab.le = table->log10_e;

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       const int il = D == 0 ? lane * NF + f : f * M + lane;
       const int ir = D == 0 ? lane * NF + f + 1 : (f + 1) * M + lane;
       if (Ex[il] != Ex[ir]) {
-        const bool into = Ex[ir] ? (F[0] > 0.0) : (F[0] < 0.0);
+        const bool into = Ex[ir] ? dgt0(F[0]) : !dge0(F[0]);
         if (!into) {
 #pragma unroll
           for (int q = 0; q < 6; ++q) F[q] = 0.0;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
         const double u0 = a.U0[q * ntot + flat];
         un[q] = a.stage == 0 ? u0 + dt * acc[q] : 0.5 * (u0 + (a.Uin[q * ntot + flat] + dt * acc[q]));
       }
-      if (un[0] < p.rho_floor) { un[0] = p.rho_floor; count(&a.cnt->rho_floor); }
+      if (dlt(un[0], p.rho_floor)) { un[0] = p.rho_floor; count(&a.cnt->rho_floor); }
       if (DUAL) {
         const double dtl = a.stage == 0 ? dt : 0.5 * dt;
         if (EOSK == EOS_IDEAL) {
@@ -281,12 +281,12 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
           const double Pa = table_pressure(p, un[0], un[5], a.cnt);
           un[5] = un[5] - Pa * dv * dtl;
         }
-        if (un[5] < p.u_floor) { un[5] = p.u_floor; count(&a.cnt->u_floor); }
+        if (dlt(un[5], p.u_floor)) { un[5] = p.u_floor; count(&a.cnt->u_floor); }
       }
-      bool bad = !(un[0] > 0.0);
+      bool bad = !dgt0(un[0]);
 #pragma unroll
       for (int q = 0; q < NVAR; ++q) {
-        bad |= !isfinite(un[q]);
+        bad |= !dfinite(un[q]);
         a.Uout[q * ntot + flat] = un[q];
       }
       if (bad) count(&a.cnt->nonfinite);
