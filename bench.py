@@ -44,6 +44,21 @@ def dist_env():
         int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (the job time is the slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(units_per_rank, world, steps, ms):
+    """Units processed by all ranks per second over the timed region."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 def layout():
     from paper_2609_37859_gb300 import workloads as wl
     return wl.uniform_layout((N, N, N), (BLOCK, BLOCK, BLOCK), bc=(1, 1, 1), ng=2)
@@ -157,10 +172,7 @@ def run_gpu(args):
     prof = ctx.profile_read()
     clk = clocks.stop()
     ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
+    ms = max_over_ranks(ms, dist, dev)
     counts = mesh.counts()
 
     # ---- end-to-end through the C ABI with host buffers: every step copies the
@@ -183,17 +195,13 @@ def run_gpu(args):
         host_out.copy_(mesh.U, non_blocking=True)
     f1.record(stream)
     barrier()
-    ms_e2e = f0.elapsed_time(f1)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t)
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, dev)
 
     fp64_peak = ctx.probe_fp64()
     if rank == 0:
         steps = args.steps
-        value = world * ncell * steps / (ms * 1e-3)
-        e2e = world * ncell * steps / (ms_e2e * 1e-3)
+        value = whole_job_rate(ncell, world, steps, ms)
+        e2e = whole_job_rate(ncell, world, steps, ms_e2e)
         sweeps = {k: prof[k] for k in ("sweep_x", "sweep_y", "sweep_z")}
         dom = max(sweeps, key=lambda k: sweeps[k][1])
         n_dom, ms_dom = sweeps[dom]
@@ -642,7 +650,7 @@ def cpu_baseline(seconds):
         if el >= seconds:
             break
     cells = n * len(ids) * BLOCK ** 3
-    return {"value": cells / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": cells / el, "unit": UNIT, "cores": tref.num_threads(), "kind": "oracle",
             "sample": "%d RK2 steps of %d of the 64 MeshBlocks (32^3) of the workload, %.1f s" %
                       (n, len(ids), el)}
 
@@ -667,7 +675,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "cells_per_step": len(ids) * BLOCK ** 3},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": tref.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

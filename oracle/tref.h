@@ -113,6 +113,7 @@ void tref_mesh_free(tref_mesh *m);
 int64_t tref_mesh_ntot(const tref_mesh *m);            /* padded cells of all blocks */
 int64_t tref_mesh_block_offset(const tref_mesh *m, int b);
 int tref_nvar(const tref_mesh *m);
+int tref_num_threads(void);   /* OpenMP threads of the block loops */
 void tref_set_params(tref_mesh *m, const tref_params *p);
 
 /* a1: copy neighbour interior cells (periodic wrap or zero-gradient outflow)

@@ -85,6 +85,7 @@ def lib():
         build()
         L = C.CDLL(SO)
         sig = {
+            "tref_num_threads": (C.c_int, []),
             "tref_saha_state": (None, [C.c_double, C.c_double, C.c_double, C.c_double, dp]),
             "tref_saha_pure_h_xe": (C.c_double, [C.c_double, C.c_double]),
             "tref_eos_build": (None, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -329,3 +330,8 @@ def mlp_loss_grad(params, x, target):
     loss = lib().tref_mlp_loss_grad(P(np.ascontiguousarray(params, dtype=np.float64)), len(x),
                                     P(x), P(t), P(g))
     return loss, g
+
+
+def num_threads():
+    """Threads the oracle's OpenMP loops use."""
+    return int(lib().tref_num_threads())

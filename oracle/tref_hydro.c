@@ -44,6 +44,9 @@
  *  - CFL (Sec. 7.1): dt_b = C min over interior non-excised cells of
  *    min_d dx_d / (|v_d| + c_s) and sqrt(dx_min / |g_bh|).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "tref.h"
 #include <math.h>
 #include <stdlib.h>
@@ -119,6 +122,15 @@ void tref_mesh_free(tref_mesh *m) {
 int64_t tref_mesh_ntot(const tref_mesh *m) { return m->ntot; }
 int64_t tref_mesh_block_offset(const tref_mesh *m, int b) { return m->off[b]; }
 int tref_nvar(const tref_mesh *m) { return m->nvar; }
+
+/* Threads the OpenMP loops over blocks use (1 without OpenMP). */
+int tref_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 void tref_set_params(tref_mesh *m, const tref_params *p) { m->p = *p; }
 
 static int gofs(const tref_mesh *m, int a) { return m->active[a] ? m->d.ng : 0; }
