@@ -75,7 +75,11 @@ typedef struct {
                            TDE_INVERT_SURROGATE (needs a trained network on the tde_eos when a
                            stage runs; the learned guess runs as separate launches over the
                            stage's cells).  All three give identical results. */
+  int riemann;          /* TDE_RIEMANN_HLLC (default) or TDE_RIEMANN_HLLE (the solver of the
+                           paper's production runs, Table 1) */
 } tde_params;
+
+enum { TDE_RIEMANN_HLLC = 0, TDE_RIEMANN_HLLE = 1 };
 
 /* Softened point-mass potential on the trajectory
  * r_bh(t) = x0 + v0 (t - t0) + a0 (t - t0)^2 / 2 (Eq. bh-softened-gravity, Sec. 3.1). */

@@ -60,7 +60,10 @@ typedef struct {
   int bh_on, excision_on;               /* softened moving point mass, one-way sink (Sec. 3.1) */
   double GM, r_soft, r_exc;
   double bh_t0, bh_x0[3], bh_v0[3], bh_a0[3];   /* r_bh(t) = x0 + v0 (t-t0) + a0 (t-t0)^2 / 2 */
+  int riemann;                          /* TREF_HLLC (0) or TREF_HLLE (1, the solver of Table 1) */
 } tref_params;
+
+enum { TREF_HLLC = 0, TREF_HLLE = 1 };
 
 /* Mesh: a uniform-cell global grid covered by MeshBlocks (no AMR). */
 typedef struct {

@@ -22,6 +22,7 @@ SOURCES = ["tref_eos.c", "tref_hydro.c", "tref_mlp.c", "tref_lat.c"]
 EOS_IDEAL, EOS_TABLE = 0, 1
 PLM, PPM = 0, 1
 OUTFLOW, PERIODIC = 0, 1
+HLLC, HLLE = 0, 1
 MLP_NPARAM = 4482
 
 
@@ -54,7 +55,7 @@ class Params(C.Structure):
                 ("unit_e", C.c_double), ("bh_on", C.c_int), ("excision_on", C.c_int),
                 ("GM", C.c_double), ("r_soft", C.c_double), ("r_exc", C.c_double),
                 ("bh_t0", C.c_double), ("bh_x0", C.c_double * 3), ("bh_v0", C.c_double * 3),
-                ("bh_a0", C.c_double * 3)]
+                ("bh_a0", C.c_double * 3), ("riemann", C.c_int)]
 
 
 class MeshDesc(C.Structure):
@@ -204,6 +205,7 @@ def make_params(**kw):
     p.unit_rho, p.unit_e = 1.0, 1.0
     p.bh_on = p.excision_on = 0
     p.GM = p.r_soft = p.r_exc = p.bh_t0 = 0.0
+    p.riemann = HLLC
     for k, v in kw.items():
         if k in ("bh_x0", "bh_v0", "bh_a0"):
             setattr(p, k, (C.c_double * 3)(*v))

@@ -388,6 +388,35 @@ static void hllc(const double *wl, const double *wr, int d, int dual, double *F,
   }
 }
 
+/* HLLE flux (Harten, Lax and van Leer with Einfeldt's two-wave form; the
+ * production solver of Table 1): with b- = min(S_L, 0) and b+ = max(S_R, 0) from
+ * the same Davis wave-speed bounds as hllc,
+ *   F = (b+ F_L - b- F_R + b+ b- (U_R - U_L)) / (b+ - b-);
+ * the auxiliary-energy flux and face velocity follow the sign of the mass flux
+ * as for hllc.  b+ = b- only when both states have zero speed and sound speed,
+ * where both physical fluxes vanish. */
+static void hlle(const double *wl, const double *wr, int d, int dual, double *F, double *vf) {
+  double rl = wl[0], ul = wl[1 + d], pl = wl[4];
+  double rr = wr[0], ur = wr[1 + d], pr = wr[4];
+  double cl = sqrt(wl[6] * pl / rl), cr = sqrt(wr[6] * pr / rr);
+  double El = total_energy(wl), Er = total_energy(wr);
+  double bm = fmin(fmin(ul - cl, ur - cr), 0.0);
+  double bp = fmax(fmax(ul + cl, ur + cr), 0.0);
+  double FL[5], FR[5];
+  phys_flux(wl, d, El, FL);
+  phys_flux(wr, d, Er, FR);
+  double UL[5] = {rl, rl * wl[1], rl * wl[2], rl * wl[3], El};
+  double UR[5] = {rr, rr * wr[1], rr * wr[2], rr * wr[3], Er};
+  for (int q = 0; q < 5; ++q)
+    F[q] = bp > bm ? (bp * FL[q] - bm * FR[q] + bp * bm * (UR[q] - UL[q])) / (bp - bm) : FL[q];
+  F[5] = 0.0;
+  *vf = 0.0;
+  if (dual) {   /* Eqs. dual-flux, dual-face-velocity */
+    if (F[0] > 0.0) { F[5] = F[0] * (wl[7] / wl[0]); *vf = F[0] / wl[0]; }
+    else if (F[0] < 0.0) { F[5] = F[0] * (wr[7] / wr[0]); *vf = F[0] / wr[0]; }
+  }
+}
+
 /* -------------------------------------------------------------- stage ----- */
 
 /* flux-register layout of one block: sides x-, x+, y-, y+, z-, z+; each
@@ -466,7 +495,8 @@ static void stage_block(const tref_mesh *m, int stage, int b, const double *U0, 
             }
           }
           double Fl[6], vf;
-          hllc(wl, wr, a, p->dual, Fl, &vf);
+          if (p->riemann == TREF_HLLE) hlle(wl, wr, a, p->dual, Fl, &vf);
+          else hllc(wl, wr, a, p->dual, Fl, &vf);
           if (p->excision_on && exc[ll] != exc[lr]) {
             /* one-way sink: keep only mass flowing into the excised cell */
             int into = exc[lr] ? (Fl[0] > 0.0) : (Fl[0] < 0.0);

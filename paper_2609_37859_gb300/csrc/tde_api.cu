@@ -71,6 +71,8 @@ bool fill_phys(tde_mesh *m, const tde_params *pr, tde_eos *eos) {
   p.inv_unit_p = 1.0 / (pr->unit_rho * pr->unit_e);
   p.inv_unit_e = 1.0 / pr->unit_e;
   p.eos_mode = pr->eos_mode;
+  p.riemann = pr->riemann;
+  if (p.riemann != TDE_RIEMANN_HLLC && p.riemann != TDE_RIEMANN_HLLE) return false;
   if (p.eos_mode < TDE_INVERT_BISECT || p.eos_mode > TDE_INVERT_BISECT_PLAIN) return false;
   if (p.eos == EOS_TABLE) {
     if (!eos) return false;

@@ -16,6 +16,7 @@ namespace tde {
 
 enum { EOS_IDEAL = 0, EOS_TABLE = 1 };
 enum { PLM = 0, PPM = 1 };
+enum { RIEMANN_HLLC = 0, RIEMANN_HLLE = 1 };
 
 // ------------------------------------- comparisons on the integer pipe ----
 //
@@ -156,6 +157,7 @@ struct Counters {
 struct Phys {
   int eos, recon, dual, nvar, nwv;
   int eos_mode;   // TDE_INVERT_*: how the table is inverted (the results are identical)
+  int riemann;    // RIEMANN_HLLC or RIEMANN_HLLE
   double gamma, gm1, inv_gm1, eta1, eta2;
   double rho_floor, p_floor, u_floor;
   double unit_rho, unit_e, inv_unit_p, inv_unit_e;
@@ -517,6 +519,48 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   F[1 + t1] = F1;
   F[1 + t2] = F2;
   F[4] = (E + P) * un + Seff * dE;
+  if (DUAL) {
+    double f = F[0];
+    bool up = dgt0(f);
+    double ru = up ? L.r : R.r, Au = up ? L.A : R.A;
+    double iru = rcp_nr(ru);
+    F[5] = !dzero(f) ? f * (Au * iru) : 0.0;
+    vf = !dzero(f) ? f * iru : 0.0;
+  } else {
+    F[5] = 0.0;
+    vf = 0.0;
+  }
+}
+
+// HLLE flux across a face normal to direction D (Harten, Lax and van Leer with
+// Einfeldt's two-wave form; the production solver of Table 1) with the same
+// Davis wave-speed bounds as hllc: b- = min(S_L, 0), b+ = max(S_R, 0),
+// F = (b+ F_L - b- F_R + b+ b- (U_R - U_L)) / (b+ - b-); F[5] and vf follow the
+// sign of the mass flux as for hllc.
+template <int D, int EOSK, int DUAL>
+__device__ __forceinline__ void hlle(const Phys &p, const FState &L, const FState &R, double *F,
+                                     double &vf) {
+  double ul = L.v[D], ur = R.v[D];
+  double cl = sqrt_ratio(L.g1 * L.P, L.r), cr = sqrt_ratio(R.g1 * R.P, R.r);
+  double Ul = EOSK == EOS_IDEAL ? L.P * p.inv_gm1 : L.P * rcp_nr(L.ge - 1.0);
+  double Ur = EOSK == EOS_IDEAL ? R.P * p.inv_gm1 : R.P * rcp_nr(R.ge - 1.0);
+  double El = Ul + 0.5 * L.r * (L.v[0] * L.v[0] + L.v[1] * L.v[1] + L.v[2] * L.v[2]);
+  double Er = Ur + 0.5 * R.r * (R.v[0] * R.v[0] + R.v[1] * R.v[1] + R.v[2] * R.v[2]);
+  const double bm = dmin(dmin(ul - cl, ur - cr), 0.0);
+  const double bp = dmax(dmax(ul + cl, ur + cr), 0.0);
+  double den = bp - bm;
+  if (dzero(den)) den = 1.0;   // both fluxes vanish there
+  const double inv = rcp_nr(den), bpm = bp * bm;
+  const double ml = L.r * ul, mr = R.r * ur;
+  // mass, momentum (x, y, z), energy: physical fluxes and conserved states
+  F[0] = (bp * ml - bm * mr + bpm * (R.r - L.r)) * inv;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double fl = ml * L.v[q] + (q == D ? L.P : 0.0);
+    const double fr = mr * R.v[q] + (q == D ? R.P : 0.0);
+    F[1 + q] = (bp * fl - bm * fr + bpm * (R.r * R.v[q] - L.r * L.v[q])) * inv;
+  }
+  F[4] = (bp * ((El + L.P) * ul) - bm * ((Er + R.P) * ur) + bpm * (Er - El)) * inv;
   if (DUAL) {
     double f = F[0];
     bool up = dgt0(f);

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       L.A = R.A = 0.0;
     }
     double F[6], vf;
-    hllc<D, EOSK, DUAL>(p, L, R, F, vf);
+    if (p.riemann == RIEMANN_HLLE) hlle<D, EOSK, DUAL>(p, L, R, F, vf);   // uniform branch
+    else hllc<D, EOSK, DUAL>(p, L, R, F, vf);
     if (exc) {
       const int il = D == 0 ? lane * NF + f : f * M + lane;
       const int ir = D == 0 ? lane * NF + f + 1 : (f + 1) * M + lane;

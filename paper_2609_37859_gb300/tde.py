@@ -18,6 +18,7 @@ TDE_OK, TDE_EINVAL, TDE_ENOMEM, TDE_ECUDA, TDE_ERANGE, TDE_ENUMERIC, TDE_ETIMEOU
 EOS_IDEAL, EOS_TABLE = 0, 1
 RECON_PLM, RECON_PPM = 0, 1
 BC_OUTFLOW, BC_PERIODIC = 0, 1
+RIEMANN_HLLC, RIEMANN_HLLE = 0, 1
 INVERT_BISECT, INVERT_SURROGATE, INVERT_BISECT_PLAIN = 0, 1, 2
 STATUS = {0: "TDE_OK", 1: "TDE_EINVAL", 2: "TDE_ENOMEM", 3: "TDE_ECUDA", 4: "TDE_ERANGE",
           5: "TDE_ENUMERIC", 6: "TDE_ETIMEOUT"}
@@ -33,7 +34,7 @@ class Params(C.Structure):
     _fields_ = [("eos", C.c_int), ("recon", C.c_int), ("dual", C.c_int), ("gamma", C.c_double),
                 ("eta1", C.c_double), ("eta2", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("u_floor", C.c_double), ("unit_rho", C.c_double),
-                ("unit_e", C.c_double), ("eos_mode", C.c_int)]
+                ("unit_e", C.c_double), ("eos_mode", C.c_int), ("riemann", C.c_int)]
 
 
 class BHState(C.Structure):
@@ -300,7 +301,7 @@ class EOS:
 
 
 def make_params(**kw):
-    p = Params(EOS_IDEAL, RECON_PLM, 0, 5.0 / 3.0, 1e-3, 1e-4, 1e-300, 1e-300, 1e-300, 1.0, 1.0, 0)
+    p = Params(EOS_IDEAL, RECON_PLM, 0, 5.0 / 3.0, 1e-3, 1e-4, 1e-300, 1e-300, 1e-300, 1.0, 1.0, 0, 0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

@@ -22,7 +22,7 @@ STEPS_TOL = 1e-10
 TABLE_FILE = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.dirname(
     __import__("os").path.abspath(__file__))), "paper_2609_37859_gb300", "data", "eos_saha_hhe_256.npz")
 SCHEME_KEYS = ("eos", "recon", "dual", "gamma", "eta1", "eta2", "rho_floor", "p_floor", "u_floor",
-               "unit_rho", "unit_e")
+               "unit_rho", "unit_e", "riemann")
 
 
 @pytest.fixture(scope="module")
@@ -518,3 +518,71 @@ def test_calls_in_the_wrong_order_fail_cleanly(tde, ctx):
     with pytest.raises(tde.TDEError):   # no trained surrogate yet
         e.invert(r, r, mode=tde.INVERT_SURROGATE)
     e.invert(r[:0], r[:0])               # empty input is fine
+
+
+# ---------------------------------------------------------------- HLLE ----
+
+def test_hlle_sod_one_block(oracle, tde, ctx):
+    """The production solver (HLLE): one 32^3 block, Sod along x, 10 steps."""
+    lay = wl.uniform_layout((32, 32, 32), (32, 32, 32), bc=(0, 0, 0), ng=2)
+    P = Pair(oracle, tde, ctx, lay, wl.sod(lay), riemann=1)
+    U = P.U.copy()
+    for _ in range(10):
+        d = P.om.cfl_dt(U, 0.3).min()
+        P.om.step(U, d, 0.0)
+        P.gm.step(cfl=0.3)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "HLLE Sod")
+
+
+def test_hlle_table_dual_stage_and_steps(oracle, tde, ctx, tables):
+    """HLLE with the Saha table and dual energy: one stage to 1e-12, five steps."""
+    rho0, T0 = 1e-8, 1e3
+    Pw, _, cs2 = tables[0].eval_rhoT(rho0, T0)
+    lay = wl.uniform_layout((32, 32, 32), (16, 16, 16), bc=(1, 1, 1), ng=2)
+    W, _ = wl.entropy_wave(lay, rho0, Pw, 3.0 * np.sqrt(cs2), amp=1e-2, seed=21)
+    P = Pair(oracle, tde, ctx, lay, W, tables, eos=1, dual=1, eta1=1e-3, eta2=1e-4,
+             rho_floor=1e-20, p_floor=1e-20, u_floor=1e-20, riemann=1)
+    om, gm = P.om, P.gm
+    dt = om.cfl_dt(P.U, 0.3).min()
+    U0 = P.U.copy()
+    om.ghost_fill(U0)
+    O1 = om.new_state()
+    om.stage(0, U0, U0, O1, np.full(P.nb, dt), np.zeros(P.nb))
+    gm.hydro_stage(0, P.dvec(dt), P.dvec(0.0))
+    assert_parity(lay.to_global(P.gpu("U1")), lay.to_global(O1), STAGE_TOL, "HLLE stage 0")
+    U = P.U.copy()
+    for _ in range(5):
+        d = om.cfl_dt(U, 0.3).min()
+        om.step(U, d, 0.0)
+        gm.step(cfl=0.3)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "HLLE steps")
+
+
+def test_hlle_lat_ppm_bh_excision(oracle, tde, ctx, tables):
+    """HLLE inside LAT windows: mixed 8^3 / 4^3 blocks, PPM, point mass with excision."""
+    rho0, v0 = 0.7382, 1.0948e8
+    lay = wl.mixed_layout((16, 16, 8), 8, {(0, 0, 0), (1, 1, 0)},
+                          ((-2.0, 2.0), (-2.0, 2.0), (-1.0, 1.0)), (0, 0, 0), 3)
+    x, y, z = lay.cell_centres()
+    r = np.sqrt(x ** 2 + y ** 2 + z ** 2)
+    rho = 1e-6 + 1e-3 * np.exp(-((r - 1.0) / 0.3) ** 2)
+    Pc = rho * rho0 * 1.380649e-16 * 1e4 / (0.6 * 1.6605e-24) / (rho0 * v0 * v0)
+    W = wl.prim_state(lay, rho, -y * 0.3, x * 0.3, 0 * rho, Pc)
+    bh = dict(on=1, excise=1, GM=1000 / (4 * np.pi), r_soft=0.005, r_exc=0.35, x0=(0.05, -0.02, 0.0),
+              v0=(0.1, 0.0, 0.0))
+    P = Pair(oracle, tde, ctx, lay, W, tables, bh=bh, eos=1, recon=1, dual=1, eta1=1e-3, eta2=1e-4,
+             rho_floor=1e-10, p_floor=1e-16, u_floor=1.5e-16, unit_rho=rho0, unit_e=v0 * v0, riemann=1)
+    U = P.U.copy()
+    t = 0.0
+    P.gm.set_time(0.0)
+    for w in range(2):
+        dt = P.om.cfl_dt(U, 0.3, np.full(P.nb, t))
+        fo, dt0, fmax = P.om.lat_factors(dt, 4, 0.0)
+        fg, _, _ = P.gm.lat_assign(4, 0.3, 0.0, bh=P.bh)
+        assert np.array_equal(fg, fo)
+        P.om.lat_window(U, fo, dt0, t)
+        P.gm.lat_window(bh=P.bh)
+        t += fmax * dt0
+    assert fmax > 1
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), 1e-10, "HLLE LAT")
+

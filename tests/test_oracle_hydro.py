@@ -28,9 +28,9 @@ def run_to(m, U, t_end, cfl, t0=0.0, max_steps=100000, counts=None):
 
 # ------------------------------------------------------------------ Sod ----
 
-def sod_l1(oracle, N, recon=0, t_end=0.2):
+def sod_l1(oracle, N, recon=0, t_end=0.2, riemann=0):
     lay = wl.uniform_layout((N, 1, 1), (32, 1, 1), bc=(0, 0, 0), ng=2 if recon == 0 else 3)
-    m = oracle.Mesh(lay, oracle.make_params(recon=recon))
+    m = oracle.Mesh(lay, oracle.make_params(recon=recon, riemann=riemann))
     U = m.prim_to_cons(wl.sod(lay))
     run_to(m, U, t_end, 0.3)
     G = m.interior(U)[:, 0, 0, :]
@@ -122,14 +122,43 @@ def test_sound_wave_second_order(oracle, recon):
     assert orders.min() >= 1.8, (errs, orders)
 
 
+def test_hlle_sod_against_exact_riemann(oracle):
+    """PLM + HLLE + RK2 (the solver of Table 1) converges to the exact Sod
+    solution, more diffusively than HLLC at the same resolution."""
+    errs = [sod_l1(oracle, N, riemann=oracle.HLLE)[0] for N in (64, 128, 256)]
+    assert errs[2] < 8e-3
+    assert errs[0] > 1.3 * errs[1] > 1.3 * 1.3 * errs[2] * 0.99
+    assert errs[2] > sod_l1(oracle, 256)[0]
+
+
+def test_stationary_contact_hllc_exact_hlle_diffusive(oracle):
+    """A contact at rest (density jump, uniform pressure, no flow): HLLC's
+    middle wave has speed exactly zero and the mass flux vanishes, so the
+    density stays as it was to the bit; HLLE has no contact wave and smears it
+    (b+ b- (rho_R - rho_L) / (b+ - b-) mass flux)."""
+    lay = wl.uniform_layout((64, 1, 1), (32, 1, 1), bc=(0, 0, 0), ng=2)
+    x = lay.cell_centres()[0]
+    rho = np.where(x < 0.5, 1.0, 0.1)
+    W = wl.prim_state(lay, rho, 0 * rho, 0 * rho, 0 * rho, 1.0 + 0 * rho)
+    out = {}
+    for riemann in (oracle.HLLC, oracle.HLLE):
+        m = oracle.Mesh(lay, oracle.make_params(riemann=riemann))
+        U = m.prim_to_cons(W)
+        run_to(m, U, 0.05, 0.3)
+        out[riemann] = m.interior(U)[0, 0, 0, :]
+    r0 = rho[0, 0]
+    assert np.array_equal(out[oracle.HLLC], r0)
+    assert np.abs(out[oracle.HLLE] - r0).max() > 0.05
+
+
 # --------------------------------------------------------- conservation ----
 
-@pytest.mark.parametrize("recon,dual", [(0, 0), (0, 1), (1, 1)])
-def test_conservation_periodic_ragged_blocks(oracle, recon, dual):
+@pytest.mark.parametrize("recon,dual,riemann", [(0, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, 1)])
+def test_conservation_periodic_ragged_blocks(oracle, recon, dual, riemann):
     """Periodic box, ragged block tails: total mass, momentum and energy change by
     roundoff only (U_aux has the non-conservative compression source)."""
     lay = wl.uniform_layout((12, 10, 9), (5, 4, 4), bc=(1, 1, 1), ng=2 + recon)
-    m = oracle.Mesh(lay, oracle.make_params(recon=recon, dual=dual, eta1=1e-3))
+    m = oracle.Mesh(lay, oracle.make_params(recon=recon, dual=dual, eta1=1e-3, riemann=riemann))
     U = m.prim_to_cons(wl.random_smooth(lay, seed=3))
     G0 = m.interior(U).reshape(m.nvar, -1).sum(axis=1)
     S = m.new_state()
