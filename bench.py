@@ -325,6 +325,21 @@ def closure_bench(mesh, U_init, tde, torch, dev, args):
         out[name] = {"ms_per_step": ms, "cell_updates_per_s": mesh.layout.ncells / (ms * 1e-3),
                      "identical_to_fp32_guided": bool(torch.equal(U, ref)),
                      "accepted_fraction": c["surrogate_accepted"] / (mesh.layout.ncells * 2 * nsteps)}
+    # the Riemann solver of the paper's production runs (HLLE) against HLLC
+    for name, rs in (("hllc", tde.RIEMANN_HLLC), ("hlle", tde.RIEMANN_HLLE)):
+        mesh.set_params(tde.make_params(riemann=rs, **SCHEME))
+        mesh.U.copy_(U_init)
+        mesh.set_time(0.0)
+        mesh.step(cfl=CFL)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(nsteps):
+            mesh.step(cfl=CFL)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / nsteps
+        out["riemann_" + name] = {"ms_per_step": ms, "cell_updates_per_s": mesh.layout.ncells / (ms * 1e-3)}
     mesh.set_params(tde.make_params(**SCHEME))
     return {"workload": "the bench step (C2), %d steps per mode" % nsteps, **out}
 

@@ -82,12 +82,18 @@ typedef struct {
 enum { TDE_RIEMANN_HLLC = 0, TDE_RIEMANN_HLLE = 1 };
 
 /* Softened point-mass potential on the trajectory
- * r_bh(t) = x0 + v0 (t - t0) + a0 (t - t0)^2 / 2 (Eq. bh-softened-gravity, Sec. 3.1). */
+ * r_bh(t) = x0 + v0 (t - t0) + a0 (t - t0)^2 / 2 (Eq. bh-softened-gravity, Sec. 3.1),
+ * and the moving frame: with frame_on, the uniform inertial acceleration -afr
+ * acts on the gas (Eq. frame-momentum: -rho afr on the momentum, -(rho v).afr on
+ * the energy, from each stage's input state); in the frame that follows the
+ * star the point mass then moves with acceleration a0 = -afr (Sec. 3.1). */
 typedef struct {
   int on;               /* gravity source terms on */
   int excise;           /* one-way sink of radius r_exc */
   double GM, r_soft, r_exc;
   double t0, x0[3], v0[3], a0[3];
+  int frame_on;         /* inertial source of the accelerating frame on */
+  double afr[3];        /* frame acceleration A_fr, held over the step */
 } tde_bh_state;
 
 /* One MeshBlock: global index of its first interior cell and its size. */
@@ -386,6 +392,19 @@ TDE_API int tde_mesh_autotune(tde_mesh *mesh, const tde_bh_state *bh, int reps, 
                               float *ms);
 TDE_API int tde_mesh_set_tiles(tde_mesh *mesh, const int32_t *tiles);
 TDE_API int tde_mesh_get_tiles(const tde_mesh *mesh, int32_t *tiles);
+
+/* ---- moving frame (Sec. 3.1) ---------------------------------------------
+ * tde_frame_acceleration: Eq. frame-acceleration at the mesh time, the
+ * mass-weighted acceleration -grad Phi_bh of the point mass bh over the interior
+ * gas with rho > rho_min outside the excision sphere (bh->excise); A[3] and the
+ * gas mass it averaged over (mass = 0: A = 0).  Deterministic (fixed-order
+ * reduction).  Synchronises the stream.
+ * tde_mesh_boost: Galilean boost of Eq. galilean-boost by V[3] of the interior
+ * cells with rho > rho_min: (rho v)' = rho (v + V), E' = E + rho v.V + rho |V|^2/2;
+ * floor-density cells and U_aux are left as they are.  Asynchronous. */
+TDE_API int tde_frame_acceleration(tde_mesh *mesh, const tde_bh_state *bh, double rho_min,
+                                   double *A, double *mass);
+TDE_API int tde_mesh_boost(tde_mesh *mesh, const double *V, double rho_min);
 
 /* The reciprocal and square-root building blocks of the hydro kernels, on n
  * device doubles: TDE_MATH_RCP out = 1/x (refined hardware seed, within one

@@ -61,6 +61,8 @@ typedef struct {
   double GM, r_soft, r_exc;
   double bh_t0, bh_x0[3], bh_v0[3], bh_a0[3];   /* r_bh(t) = x0 + v0 (t-t0) + a0 (t-t0)^2 / 2 */
   int riemann;                          /* TREF_HLLC (0) or TREF_HLLE (1, the solver of Table 1) */
+  int frame_on;                         /* moving frame: inertial source -rho A_fr (Eq. frame-momentum) */
+  double afr[3];                        /* the frame acceleration A_fr held over the step */
 } tref_params;
 
 enum { TREF_HLLC = 0, TREF_HLLE = 1 };
@@ -176,6 +178,15 @@ void tref_mlp_forward(const double *params, int64_t n, const double *x, double *
 /* Mean-squared-error loss over n samples and its gradient w.r.t. params. */
 double tref_mlp_loss_grad(const double *params, int64_t n, const double *x, const double *target,
                           double *grad);
+
+/* Frame acceleration of Eq. frame-acceleration at time t: the mass-weighted
+ * point-mass acceleration g = -grad Phi_bh of the interior gas with rho > rho_min
+ * outside the excision sphere; A[3], and the mass it averaged over (0: A = 0). */
+void tref_frame_acceleration(const tref_mesh *m, const double *U, double t, double rho_min,
+                             double *A, double *mass);
+/* Galilean boost of Eq. galilean-boost by V[3] of the interior cells with
+ * rho > rho_min (floor-density gas is left as it is). */
+void tref_boost(const tref_mesh *m, double *U, const double *V, double rho_min);
 
 #ifdef __cplusplus
 }

@@ -55,7 +55,8 @@ class Params(C.Structure):
                 ("unit_e", C.c_double), ("bh_on", C.c_int), ("excision_on", C.c_int),
                 ("GM", C.c_double), ("r_soft", C.c_double), ("r_exc", C.c_double),
                 ("bh_t0", C.c_double), ("bh_x0", C.c_double * 3), ("bh_v0", C.c_double * 3),
-                ("bh_a0", C.c_double * 3), ("riemann", C.c_int)]
+                ("bh_a0", C.c_double * 3), ("riemann", C.c_int), ("frame_on", C.c_int),
+                ("afr", C.c_double * 3)]
 
 
 class MeshDesc(C.Structure):
@@ -87,6 +88,8 @@ def lib():
         L = C.CDLL(SO)
         sig = {
             "tref_num_threads": (C.c_int, []),
+            "tref_frame_acceleration": (None, [C.c_void_p, dp, C.c_double, C.c_double, dp, dp]),
+            "tref_boost": (None, [C.c_void_p, dp, dp, C.c_double]),
             "tref_saha_state": (None, [C.c_double, C.c_double, C.c_double, C.c_double, dp]),
             "tref_saha_pure_h_xe": (C.c_double, [C.c_double, C.c_double]),
             "tref_eos_build": (None, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -207,7 +210,7 @@ def make_params(**kw):
     p.GM = p.r_soft = p.r_exc = p.bh_t0 = 0.0
     p.riemann = HLLC
     for k, v in kw.items():
-        if k in ("bh_x0", "bh_v0", "bh_a0"):
+        if k in ("bh_x0", "bh_v0", "bh_a0", "afr"):
             setattr(p, k, (C.c_double * 3)(*v))
         else:
             setattr(p, k, v)
@@ -285,6 +288,17 @@ class Mesh:
         lib().tref_dual_sync(self.h, P(U), 0 if ids_a is None else len(ids_a),
                              None if ids_a is None else IP(ids_a), C.byref(c))
         return c
+
+    def frame_acceleration(self, U, t, rho_min):
+        """(A_fr[3], mass) of Eq. frame-acceleration at time t."""
+        A = np.zeros(3)
+        mass = np.zeros(1)
+        lib().tref_frame_acceleration(self.h, P(U), t, rho_min, P(A), P(mass))
+        return A, float(mass[0])
+
+    def boost(self, U, V, rho_min):
+        """Galilean boost of Eq. galilean-boost, in place."""
+        lib().tref_boost(self.h, P(U), P(np.ascontiguousarray(V, dtype=np.float64)), rho_min)
 
     def cfl_dt(self, U, cfl, t_b=None):
         dt = np.zeros(self.layout.nb)

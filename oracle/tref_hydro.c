@@ -532,6 +532,13 @@ static void stage_block(const tref_mesh *m, int stage, int b, const double *U0, 
             L[4] -= (F[a][fhi] * (ph - p0) + F[a][flo] * (p0 - pl)) / (2.0 * m->d.dx[a]);
           }
         }
+        if (p->frame_on) {
+          /* inertial force of the accelerating frame (Eq. frame-momentum) and its
+           * work, from the stage's input state at the cell centre */
+          const double rho_in = Uin[gl];
+          for (int a = 0; a < 3; ++a) L[1 + a] -= rho_in * p->afr[a];
+          L[4] -= Uin[1 * nt + gl] * p->afr[0] + Uin[2 * nt + gl] * p->afr[1] + Uin[3 * nt + gl] * p->afr[2];
+        }
         double un[6];
         for (int q = 0; q < nvar; ++q) {
           if (stage == 0) un[q] = U0[q * nt + gl] + dt * L[q];
@@ -805,3 +812,57 @@ void tref_mesh_get_view(const tref_mesh *m, tref_mesh_view *v) {
 }
 
 void tref_cell_pos(const tref_mesh *m, int b, int i, int j, int k, double *x) { cell_pos(m, b, i, j, k, x); }
+
+/* ---------------------------------------------------------- moving frame --- */
+
+void tref_frame_acceleration(const tref_mesh *m, const double *U, double t, double rho_min,
+                             double *A, double *mass) {
+  const tref_params *p = &m->p;
+  const int64_t nt = m->ntot;
+  double rb[3];
+  bh_pos(p, t, rb);
+  double s0 = 0.0, s[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < m->d.nb; ++b) {
+    const int *B = m->blocks + 6 * b;
+    const int *P = m->pd + 3 * b;
+    for (int k = 0; k < B[5]; ++k)
+      for (int j = 0; j < B[4]; ++j)
+        for (int i = 0; i < B[3]; ++i) {
+          const int ci = i + gofs(m, 0), cj = j + gofs(m, 1), ck = k + gofs(m, 2);
+          const double rho = U[m->off[b] + ((int64_t)ck * P[1] + cj) * P[0] + ci];
+          if (!(rho > rho_min)) continue;
+          double x[3];
+          cell_pos(m, b, ci, cj, ck, x);
+          if (p->excision_on && excised_at(p, x, t)) continue;
+          const double d[3] = {x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]};
+          const double q2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + p->r_soft * p->r_soft;
+          const double gfac = -p->GM / (q2 * sqrt(q2));   /* g = -grad Phi_bh = -GM d / q^3 */
+          for (int a = 0; a < 3; ++a) s[a] += rho * gfac * d[a];
+          s0 += rho;
+        }
+  }
+  (void)nt;
+  for (int a = 0; a < 3; ++a) A[a] = s0 > 0.0 ? s[a] / s0 : 0.0;
+  *mass = s0 * m->d.dx[0] * m->d.dx[1] * m->d.dx[2];
+}
+
+void tref_boost(const tref_mesh *m, double *U, const double *V, double rho_min) {
+  const int64_t nt = m->ntot;
+  for (int b = 0; b < m->d.nb; ++b) {
+    const int *B = m->blocks + 6 * b;
+    const int *P = m->pd + 3 * b;
+    for (int k = 0; k < B[5]; ++k)
+      for (int j = 0; j < B[4]; ++j)
+        for (int i = 0; i < B[3]; ++i) {
+          const int64_t l = m->off[b] + ((int64_t)(k + gofs(m, 2)) * P[1] + (j + gofs(m, 1))) * P[0] +
+                            (i + gofs(m, 0));
+          const double rho = U[l];
+          if (!(rho > rho_min)) continue;
+          const double mv = U[nt + l] * V[0] + U[2 * nt + l] * V[1] + U[3 * nt + l] * V[2];
+          const double v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+          U[4 * nt + l] += mv + 0.5 * rho * v2;          /* E' = E + rho v.V + rho |V|^2 / 2 */
+          for (int a = 0; a < 3; ++a) U[(1 + a) * nt + l] += rho * V[a];   /* (rho v)' = rho (v + V) */
+        }
+  }
+}
+

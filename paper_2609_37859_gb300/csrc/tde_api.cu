@@ -43,10 +43,12 @@ BH make_bh(const tde_bh_state *s) {
   b.rs2 = s->r_soft * s->r_soft;
   b.rexc = s->r_exc;
   b.t0 = s->t0;
+  b.frame = s->frame_on;
   for (int a = 0; a < 3; ++a) {
     b.x0[a] = s->x0[a];
     b.v0[a] = s->v0[a];
     b.a0[a] = s->a0[a];
+    b.afr[a] = s->afr[a];
   }
   return b;
 }
@@ -539,6 +541,8 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->sb.lTg);
   cudaFree(m->sb.queue);
   cudaFree(m->sb.qcount);
+  cudaFree(m->d_frame_part);
+  cudaFree(m->d_frame_out);
   cudaFree(m->d_f);
   cudaFree(m->d_f2);
   cudaFree(m->d_sorted);
@@ -738,6 +742,27 @@ extern "C" int tde_mesh_autotune(tde_mesh *m, const tde_bh_state *bhs, int reps,
   if (ms)
     for (int D = 0; D < 3; ++D)
       for (int k = 0; k < N_SWEEP_SHAPES; ++k) ms[D * N_SWEEP_SHAPES + k] = t[D][k];
+  return TDE_OK;
+}
+
+extern "C" int tde_frame_acceleration(tde_mesh *m, const tde_bh_state *bh, double rho_min, double *A,
+                                      double *mass) {
+  if (!m) return TDE_EINVAL;
+  if (!m->U || !bh || !A) return fail(m->ctx, TDE_EINVAL, "tde_frame_acceleration: arguments");
+  if (!m->d_frame_out) CK(m->ctx, cudaMalloc(&m->d_frame_out, sizeof(double) * 4));
+  CK(m->ctx, launch_frame_acceleration(m, make_bh(bh), rho_min, m->d_frame_out));
+  double h[4];
+  CK(m->ctx, cudaMemcpyAsync(h, m->d_frame_out, sizeof h, cudaMemcpyDeviceToHost, m->ctx->stream));
+  CK(m->ctx, cudaStreamSynchronize(m->ctx->stream));
+  for (int k = 0; k < 3; ++k) A[k] = h[k];
+  if (mass) *mass = h[3];
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_boost(tde_mesh *m, const double *V, double rho_min) {
+  if (!m) return TDE_EINVAL;
+  if (!m->U || !V) return fail(m->ctx, TDE_EINVAL, "tde_mesh_boost: arguments");
+  CK(m->ctx, launch_boost(m, V, rho_min));
   return TDE_OK;
 }
 

@@ -169,6 +169,8 @@ struct Phys {
 struct BH {
   int on, excise;
   double GM, rs2, rexc, t0, x0[3], v0[3], a0[3];
+  int frame;          // inertial source of the accelerating frame
+  double afr[3];
 };
 
 // padded geometry of one MeshBlock
@@ -211,11 +213,13 @@ __device__ __forceinline__ double rcp_nr(double d) {
 // e = 1 - t y^2, 1/sqrt(t) = y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2/8 + ...);
 // the truncation error ~(5/16) e^3 is below 2^-61, and the roundings of t, y^2
 // and the final product keep the result within about two ulps of the correctly
-// rounded sqrt(a / b).  For a b and a / b normal (sound speeds: a = Gamma_1 P,
-// b = rho).  Replaces a division and a square root (the wave-speed estimates
-// of the Riemann solver and of the time-step condition).
+// rounded sqrt(a / b).  Replaces a division and a square root (the wave-speed
+// estimates of the Riemann solver and of the time-step condition).  Where a b
+// leaves the range in which the seed and y^2 are normal (floor states of
+// 1e-300 give a b ~ 1e-600) the IEEE form is used instead.
 __device__ __forceinline__ double sqrt_ratio(double a, double b) {
   const double t = a * b;
+  if ((unsigned long long)(((dbits(t) >> 52) & 0x7ff) - 2) >= 0x7fcull) return sqrt(a / b);
   const double y = rsqrt_seed(t);
   const double e = fma(-t, y * y, 1.0);
   const double y1 = fma(y, e * fma(e, 0.375, 0.5), y);

@@ -352,6 +352,98 @@ __global__ void __launch_bounds__(NT) k_eos_eval(DTable t, long long n, const do
   }
 }
 
+// ------------------------------------------------------- moving frame ----
+
+// Partial sums of Eq. frame-acceleration: rho g (3) and rho over the interior
+// cells with rho > rho_min outside the excision sphere, one slot per CTA.
+__global__ void __launch_bounds__(NT) k_frame_partial(Phys p, BH bh, const double *__restrict__ tnow,
+                                                      const DevBlock *__restrict__ blocks,
+                                                      const double *__restrict__ U, double rho_min,
+                                                      double *part) {
+  __shared__ double red[4][NT / 32];
+  const int b = blockIdx.y;
+  const DevBlock B = blocks[b];
+  const int nint = B.n[0] * B.n[1] * B.n[2];
+  double rb[3];
+  bh_pos(bh, *tnow, rb);
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = blockIdx.x * NT + threadIdx.x; e < nint; e += gridDim.x * NT) {
+    const int i = e % B.n[0], r = e / B.n[0];
+    const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
+    const double rho = U[B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0]];
+    if (!(rho > rho_min)) continue;
+    double x[3];
+    cell_centre(p, B, c, x);
+    const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
+    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    if (bh.excise && sqrt(r2) < bh.rexc) continue;
+    const double q2 = r2 + bh.rs2;
+    const double gfac = -bh.GM / (q2 * sqrt(q2));   // g = -grad Phi_bh = -GM d / q^3
+    s[0] += rho * gfac * d0;
+    s[1] += rho * gfac * d1;
+    s[2] += rho * gfac * d2;
+    s[3] += rho;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double v = s[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int w = 0; w < NT / 32; ++w) v += red[threadIdx.x][w];
+    part[((long long)b * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = v;
+  }
+}
+
+// The partial sums in a fixed order (deterministic): out = (A_fr[3], mass).
+__global__ void __launch_bounds__(NT) k_frame_final(const double *__restrict__ part, int nparts,
+                                                    double dV, double *out) {
+  __shared__ double red[4][NT];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < nparts; q += NT)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] += part[(long long)q * 4 + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int h = NT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = red[3][0];
+    for (int k = 0; k < 3; ++k) out[k] = m > 0.0 ? red[k][0] / m : 0.0;
+    out[3] = m * dV;
+  }
+}
+
+// Galilean boost of Eq. galilean-boost of the interior cells with rho > rho_min.
+__global__ void __launch_bounds__(NT) k_boost(Phys p, const DevBlock *__restrict__ blocks, double *U,
+                                              long long ntot, double V0, double V1, double V2,
+                                              double rho_min) {
+  const int b = blockIdx.y;
+  const DevBlock B = blocks[b];
+  const int nint = B.n[0] * B.n[1] * B.n[2];
+  for (int e = blockIdx.x * NT + threadIdx.x; e < nint; e += gridDim.x * NT) {
+    const int i = e % B.n[0], r = e / B.n[0];
+    const long long l = B.off + ((long long)(r / B.n[1] + p.g[2]) * B.p[1] + (r % B.n[1] + p.g[1])) * B.p[0] +
+                        (i + p.g[0]);
+    const double rho = U[l];
+    if (!(rho > rho_min)) continue;
+    const double mv = U[ntot + l] * V0 + U[2 * ntot + l] * V1 + U[3 * ntot + l] * V2;
+    const double v2 = V0 * V0 + V1 * V1 + V2 * V2;
+    U[4 * ntot + l] += mv + 0.5 * rho * v2;
+    U[ntot + l] += rho * V0;
+    U[2 * ntot + l] += rho * V1;
+    U[3 * ntot + l] += rho * V2;
+  }
+}
+
 // ============================================================ launchers ====
 
 static int n_sm() {
@@ -669,6 +761,35 @@ cudaError_t launch_eos_eval(tde_eos *e, int64_t n, const double *rho, const doub
   long long blocks = (n + NT - 1) / NT;
   unsigned g = (unsigned)(blocks < 8LL * n_sm() ? blocks : 8LL * n_sm());
   k_eos_eval<<<g, NT, 0, s>>>(e->tab, (long long)n, rho, T, P, en, cs2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_acceleration(tde_mesh *m, const BH &bh, double rho_min, double *out4) {
+  ProfScope _ps(m->ctx, TDE_K_SCALAR);
+  const int gx = (int)std::min<int64_t>((m->max_interior + NT - 1) / NT, 64);
+  const size_t need = (size_t)m->nb * gx * 4;
+  if (m->frame_part_cap < need) {
+    cudaFree(m->d_frame_part);
+    m->d_frame_part = nullptr;
+    m->frame_part_cap = 0;
+    cudaError_t err = cudaMalloc(&m->d_frame_part, sizeof(double) * need);
+    if (err != cudaSuccess) return err;
+    m->frame_part_cap = need;
+  }
+  k_frame_partial<<<dim3((unsigned)gx, (unsigned)m->nb), NT, 0, m->ctx->stream>>>(
+      m->phys, bh, m->d_scal, m->d_blocks, m->U, rho_min, m->d_frame_part);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const double dV = m->phys.dx[0] * m->phys.dx[1] * m->phys.dx[2];
+  k_frame_final<<<1, NT, 0, m->ctx->stream>>>(m->d_frame_part, m->nb * gx, dV, out4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boost(tde_mesh *m, const double *V, double rho_min) {
+  ProfScope _ps(m->ctx, TDE_K_SCALAR);
+  dim3 grid((unsigned)std::min<int64_t>((m->max_interior + NT - 1) / NT, 64), (unsigned)m->nb);
+  k_boost<<<grid, NT, 0, m->ctx->stream>>>(m->phys, m->d_blocks, m->U, (long long)m->ntot, V[0], V[1],
+                                           V[2], rho_min);
   return cudaGetLastError();
 }
 

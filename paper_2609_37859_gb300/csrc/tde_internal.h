@@ -104,6 +104,9 @@ struct tde_mesh {
   int nmax[3] = {0, 0, 0};           // largest interior block edge per direction
   int tile[3] = {0, 0, 0};           // sweep tile shape per direction (kTileShapes index)
   tde::SurrogateBuf sb;              // learned-guess closure buffers (eos_mode SURROGATE)
+  double *d_frame_part = nullptr;    // partial sums of the frame acceleration
+  size_t frame_part_cap = 0;
+  double *d_frame_out = nullptr;     // (A_fr[3], mass)
   int64_t ntot = 0;
   int64_t max_interior = 0;          // largest interior cell count of a block
   int max_ghosts = 0;                // largest ghost count of a block
@@ -171,6 +174,8 @@ size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
 constexpr int N_SWEEP_SHAPES = 3;
 cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3][N_SWEEP_SHAPES]);
 void invalidate_graph(tde_mesh *m);
+cudaError_t launch_frame_acceleration(tde_mesh *m, const BH &bh, double rho_min, double *out4);
+cudaError_t launch_boost(tde_mesh *m, const double *V, double rho_min);
 bool closure_ready(const tde_mesh *m);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);

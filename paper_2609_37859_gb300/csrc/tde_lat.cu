@@ -456,7 +456,8 @@ extern "C" int tde_lat_assign(tde_mesh *m, int n_lat, double merge_frac, double 
   if (bhs) {
     bh.on = bhs->on; bh.excise = bhs->excise; bh.GM = bhs->GM; bh.rs2 = bhs->r_soft * bhs->r_soft;
     bh.rexc = bhs->r_exc; bh.t0 = bhs->t0;
-    for (int a = 0; a < 3; ++a) { bh.x0[a] = bhs->x0[a]; bh.v0[a] = bhs->v0[a]; bh.a0[a] = bhs->a0[a]; }
+    bh.frame = bhs->frame_on;
+    for (int a = 0; a < 3; ++a) { bh.x0[a] = bhs->x0[a]; bh.v0[a] = bhs->v0[a]; bh.a0[a] = bhs->a0[a]; bh.afr[a] = bhs->afr[a]; }
   }
   TimeArgs ta{nullptr, 0, m->d_scal, 0};
   LCK(c, launch_c2p(m, m->U, m->nb, m->d_allids, true, bh, ta));
@@ -506,7 +507,8 @@ extern "C" int tde_lat_window(tde_mesh *m, const tde_bh_state *bhs, int use_grap
   if (bhs) {
     bh.on = bhs->on; bh.excise = bhs->excise; bh.GM = bhs->GM; bh.rs2 = bhs->r_soft * bhs->r_soft;
     bh.rexc = bhs->r_exc; bh.t0 = bhs->t0;
-    for (int a = 0; a < 3; ++a) { bh.x0[a] = bhs->x0[a]; bh.v0[a] = bhs->v0[a]; bh.a0[a] = bhs->a0[a]; }
+    bh.frame = bhs->frame_on;
+    for (int a = 0; a < 3; ++a) { bh.x0[a] = bhs->x0[a]; bh.v0[a] = bhs->v0[a]; bh.a0[a] = bhs->a0[a]; bh.afr[a] = bhs->afr[a]; }
   }
   int64_t upd = 0;
   for (size_t L = 0; L < m->h_levels.size(); ++L)

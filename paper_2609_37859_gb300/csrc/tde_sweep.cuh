@@ -267,6 +267,16 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       if (DUAL) a.dU[NVAR * ntot + flat] = dv;
     } else {
       const double dt = ta_dt(a.ta, b);
+      if (a.bh.frame) {
+        // inertial force of the accelerating frame (Eq. frame-momentum) and its
+        // work, from the stage's input state at the cell centre
+        const double rin = a.Uin[flat];
+        acc[1] -= rin * a.bh.afr[0];
+        acc[2] -= rin * a.bh.afr[1];
+        acc[3] -= rin * a.bh.afr[2];
+        acc[4] -= a.Uin[ntot + flat] * a.bh.afr[0] + a.Uin[2 * ntot + flat] * a.bh.afr[1] +
+                  a.Uin[3 * ntot + flat] * a.bh.afr[2];
+      }
       double un[NVAR];
 #pragma unroll
       for (int q = 0; q < NVAR; ++q) {

@@ -40,7 +40,8 @@ class Params(C.Structure):
 class BHState(C.Structure):
     _fields_ = [("on", C.c_int), ("excise", C.c_int), ("GM", C.c_double), ("r_soft", C.c_double),
                 ("r_exc", C.c_double), ("t0", C.c_double), ("x0", C.c_double * 3),
-                ("v0", C.c_double * 3), ("a0", C.c_double * 3)]
+                ("v0", C.c_double * 3), ("a0", C.c_double * 3), ("frame_on", C.c_int),
+                ("afr", C.c_double * 3)]
 
 
 class BlockDesc(C.Structure):
@@ -115,6 +116,9 @@ _SIGS = {
     "tde_math_selftest": [vp, C.c_int64, dp, dp, dp],
     "tde_math_probe": [vp, C.c_int, C.c_int64, dp, dp, dp],
     "tde_mesh_autotune": [vp, C.POINTER(BHState), C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
+    "tde_frame_acceleration": [vp, C.POINTER(BHState), C.c_double, C.POINTER(C.c_double),
+                               C.POINTER(C.c_double)],
+    "tde_mesh_boost": [vp, C.POINTER(C.c_double), C.c_double],
     "tde_mesh_set_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_mesh_get_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
@@ -308,9 +312,9 @@ def make_params(**kw):
 
 
 def make_bh(on=1, excise=0, GM=0.0, r_soft=0.0, r_exc=0.0, t0=0.0, x0=(0, 0, 0), v0=(0, 0, 0),
-            a0=(0, 0, 0)):
+            a0=(0, 0, 0), frame_on=0, afr=(0, 0, 0)):
     return BHState(on, excise, GM, r_soft, r_exc, t0, (C.c_double * 3)(*x0),
-                   (C.c_double * 3)(*v0), (C.c_double * 3)(*a0))
+                   (C.c_double * 3)(*v0), (C.c_double * 3)(*a0), frame_on, (C.c_double * 3)(*afr))
 
 
 class Mesh:
@@ -394,6 +398,17 @@ class Mesh:
         self.ctx.check(lib().tde_lat_window(self.h, C.byref(bh) if bh is not None else None,
                                             1 if use_graph else 0, C.byref(upd)))
         return upd.value
+
+    def frame_acceleration(self, bh, rho_min):
+        """(A_fr[3], mass) of Eq. frame-acceleration at the mesh time."""
+        A = (C.c_double * 3)()
+        mass = C.c_double()
+        self.ctx.check(lib().tde_frame_acceleration(self.h, C.byref(bh), rho_min, A, C.byref(mass)))
+        return list(A), mass.value
+
+    def boost(self, V, rho_min):
+        v = (C.c_double * 3)(*V)
+        self.ctx.check(lib().tde_mesh_boost(self.h, v, rho_min))
 
     def autotune(self, bh=None, reps=3):
         """Pick the fastest sweep tile shape per direction; returns (shapes, ms[3][3])."""

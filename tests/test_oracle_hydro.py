@@ -434,3 +434,80 @@ def test_entropy_wave_tabulated_eos_dual_energy(oracle, saha_table):
     assert c.table_clamp == 0 and c.dual_aux_used > 0
     Ucons = G[4] - 0.5 * G[1] ** 2 / G[0]
     assert np.max(np.abs(Ucons / G[5] - 1)) > 1e-3    # the conservative subtraction is useless here
+
+
+# ---------------------------------------------------------- moving frame ----
+
+def test_frame_acceleration_closed_forms(oracle):
+    """Eq. frame-acceleration: zero for gas placed symmetrically about the point
+    mass; the point mass's acceleration at a lone dense cell's centre; nothing
+    from floor gas or from gas inside the excision sphere."""
+    lay = wl.uniform_layout((16, 16, 16), (8, 8, 8), domain=((-1, 1),) * 3, bc=(0, 0, 0), ng=2)
+    GM, rs = 2.0, 0.05
+    m = oracle.Mesh(lay, oracle.make_params(bh_on=1, excision_on=1, GM=GM, r_soft=rs, r_exc=0.15,
+                                            bh_x0=(0.0, 0.0, 0.0)))
+    x, y, z = lay.cell_centres()
+    rho = 1.0 + 0.5 * np.cos(np.pi * x) * np.cos(np.pi * y) * np.cos(np.pi * z)   # even in x, y, z
+    U = m.prim_to_cons(wl.prim_state(lay, rho, 0 * rho, 0 * rho, 0 * rho, 1.0 + 0 * rho))
+    A, mass = m.frame_acceleration(U, 0.0, 1e-6)
+    assert np.abs(A).max() < 1e-12
+    outside = np.sqrt(x ** 2 + y ** 2 + z ** 2) >= 0.15     # the excised cells do not count
+    assert mass == pytest.approx(rho[outside].sum() * (2 / 16) ** 3, rel=1e-13)
+    # one dense cell at (ic, jc, kc), everything else at the threshold
+    ic, jc, kc = 11, 4, 9
+    rho2 = np.full_like(rho, 1e-6)
+    rho2[kc, jc, ic] = 3.0
+    U = m.prim_to_cons(wl.prim_state(lay, rho2, 0 * rho, 0 * rho, 0 * rho, 1.0 + 0 * rho))
+    A, mass = m.frame_acceleration(U, 0.0, 1e-6)
+    d = np.array([x[kc, jc, ic], y[kc, jc, ic], z[kc, jc, ic]])
+    g = -GM * d / (d @ d + rs * rs) ** 1.5
+    assert np.allclose(A, g, rtol=1e-14, atol=0)
+    # the same cell inside the excision sphere (point mass moved onto it): nothing
+    m.set_params(oracle.make_params(bh_on=1, excision_on=1, GM=GM, r_soft=rs, r_exc=0.15, bh_x0=tuple(d)))
+    A, mass = m.frame_acceleration(U, 0.0, 1e-6)
+    assert mass == 0.0 and not A.any()
+
+
+def test_frame_source_uniform_gas_closed_form(oracle):
+    """Gas at rest in a frame accelerating at a: after one RK2 step of dt the
+    momentum is -rho a dt and the energy gain is rho |a|^2 dt^2 / 2 (exact: the
+    source is linear in time, which RK2 integrates without error)."""
+    lay = wl.uniform_layout((8, 8, 8), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    a = np.array([0.3, -0.2, 0.1])
+    m = oracle.Mesh(lay, oracle.make_params(frame_on=1, afr=tuple(a)))
+    U = m.prim_to_cons(wl.prim_state(lay, 2.0, 0.0, 0.0, 0.0, 1.0))
+    E0 = m.interior(U)[4].copy()
+    dt = 0.01
+    m.step(U, dt, 0.0)
+    G = m.interior(U)
+    for k in range(3):
+        assert np.allclose(G[1 + k], -2.0 * a[k] * dt, rtol=1e-13, atol=0)
+    assert np.allclose(G[4] - E0, 0.5 * 2.0 * (a @ a) * dt * dt, rtol=1e-10, atol=0)
+    assert np.allclose(G[0], 2.0, rtol=0, atol=1e-15)
+
+
+def test_boost_closed_form_and_inverse(oracle):
+    """Eq. galilean-boost: (rho v)' = rho (v + V), E' = E + rho v.V + rho V^2 / 2;
+    floor-density cells untouched; the internal energy E - |m|^2 / (2 rho) and
+    U_aux unchanged; boosting back by -V restores the state to rounding."""
+    lay = wl.uniform_layout((12, 8, 8), (4, 8, 8), bc=(1, 1, 1), ng=2)
+    m = oracle.Mesh(lay, oracle.make_params(dual=1))
+    W = wl.random_smooth(lay, seed=4)
+    U = m.prim_to_cons(W)
+    G = m.interior(U).copy()
+    floor_cells = G[0] < np.quantile(G[0], 0.2)
+    V = np.array([1.5, -0.7, 0.25])
+    rho_min = float(np.quantile(G[0], 0.2))
+    m.boost(U, V, rho_min)
+    H = m.interior(U)
+    sel = G[0] > rho_min
+    for k in range(3):
+        assert np.allclose(H[1 + k][sel], G[1 + k][sel] + G[0][sel] * V[k], rtol=1e-15, atol=1e-15)
+        assert np.array_equal(H[1 + k][~sel], G[1 + k][~sel])
+    ein0 = G[4] - 0.5 * (G[1] ** 2 + G[2] ** 2 + G[3] ** 2) / G[0]
+    ein1 = H[4] - 0.5 * (H[1] ** 2 + H[2] ** 2 + H[3] ** 2) / H[0]
+    assert np.allclose(ein1, ein0, rtol=1e-10, atol=1e-12)
+    assert np.array_equal(H[5], G[5]) and np.array_equal(H[0], G[0])
+    assert floor_cells.any()
+    m.boost(U, -V, rho_min)
+    assert np.allclose(m.interior(U), G, rtol=1e-13, atol=1e-14)
