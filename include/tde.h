@@ -355,6 +355,7 @@ enum {
   TDE_K_EOS = 10,     /* batch EOS inversion / evaluation */
   TDE_K_PROBE = 11,   /* peak-rate probe */
   TDE_K_LATGRAPH = 12, /* replayed LAT window graphs (launches counted per kernel inside) */
+  TDE_K_GRAV = 13,    /* self-gravity multigrid */
   TDE_K_NKIND = 16
 };
 
@@ -405,6 +406,39 @@ TDE_API int tde_mesh_get_tiles(const tde_mesh *mesh, int32_t *tiles);
 TDE_API int tde_frame_acceleration(tde_mesh *mesh, const tde_bh_state *bh, double rho_min,
                                    double *A, double *mass);
 TDE_API int tde_mesh_boost(tde_mesh *mesh, const double *V, double rho_min);
+
+/* ---- self-gravity (Sec. 3.2) -----------------------------------------------
+ * Geometric multigrid for A_h phi = S_h, A_h = -lap_h (seven-point, weights
+ * (dx/dy)^2 and (dx/dz)^2, Eq. selfgrav-poisson), S_h = -4 pi G rho_sg with
+ * rho_sg = rho where rho > rho_min (floor gas excluded), on the mesh's uniform
+ * grid with periodic boundaries in every direction (each N a power of two; the
+ * mean of S is removed in two passes).  V-cycles of npre / npost red-black
+ * Gauss-Seidel sweeps with over-relaxation omega (the paper: 2, 2, 1.15), a
+ * full-approximation coarse correction, trilinear prolongation, post-smoothing
+ * on every level and one extra fine sweep, until the rms defect (Eq.
+ * selfgrav-defect) is below tol or max_cycles are done; warm = 1 starts from the
+ * previous potential. */
+typedef struct {
+  double G;            /* gravitational constant in code units (1 / (4 pi) for Table 1's) */
+  double rho_min;      /* density above which gas is a source */
+  double tol;          /* rms defect to reach */
+  int max_cycles, npre, npost;
+  double omega;        /* over-relaxation of the Gauss-Seidel sweeps */
+  int warm;            /* start from the previous potential */
+} tde_grav_params;
+/* Solve for phi_sg from the bound state's density; the potential is kept by the
+ * mesh (also in the MeshBlock layout, ghosts included).  cycles and defect (may
+ * be NULL) receive the V-cycles run and the final rms defect.  TDE_EINVAL unless
+ * every active direction is periodic with a power-of-two size.  Synchronises. */
+TDE_API int tde_gravity_solve(tde_mesh *mesh, const tde_grav_params *params, int *cycles,
+                              double *defect);
+/* on = 1: the hydro stage adds the kept phi_sg (frozen between solves) to the
+ * point mass's potential in its gravity sources (Eqs. lat-grav-momentum,
+ * lat-grav-energy, and the refluxing of Eq. lat-grav-reflux). */
+TDE_API int tde_gravity_enable(tde_mesh *mesh, int on);
+/* The potential on the global grid, [Nz][Ny][Nx] doubles into device memory
+ * phi (TDE_EINVAL before the first solve).  Asynchronous. */
+TDE_API int tde_gravity_phi(tde_mesh *mesh, double *phi);
 
 /* The reciprocal and square-root building blocks of the hydro kernels, on n
  * device doubles: TDE_MATH_RCP out = 1/x (refined hardware seed, within one

@@ -188,6 +188,21 @@ void tref_frame_acceleration(const tref_mesh *m, const double *U, double t, doub
  * rho > rho_min (floor-density gas is left as it is). */
 void tref_boost(const tref_mesh *m, double *U, const double *V, double rho_min);
 
+/* Self-gravity multigrid (tref_grav.c): solve A_h phi = S_h, A_h = -lap_h with
+ * anisotropic weights, on a periodic nx x ny x nz grid (each a power of two) of
+ * cell widths dx[3]; src, phi [nz][ny][nx]; phi is the start and the result.
+ * V-cycles (npre, npost red-black sweeps, over-relaxation omega) until the rms
+ * defect is below tol or max_cycles; returns the cycles, *defect the final rms. */
+int tref_mg_solve(int nx, int ny, int nz, const double *dx, const double *src, double *phi,
+                  int max_cycles, double tol, int npre, int npost, double omega, double *defect);
+double tref_mg_defect_rms(int nx, int ny, int nz, const double *dx, const double *src, const double *phi);
+
+/* Self-gravity potential of the hydro sources, in the mesh's padded layout
+ * (ghosts included; the caller keeps the array), NULL to switch it off.  It is
+ * added to the point mass's potential in the stage and in the refluxing. */
+void tref_set_phi_sg(tref_mesh *m, const double *phi_padded);
+const double *tref_phi_sg(const tref_mesh *m);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libtref.so")
-SOURCES = ["tref_eos.c", "tref_hydro.c", "tref_mlp.c", "tref_lat.c"]
+SOURCES = ["tref_eos.c", "tref_hydro.c", "tref_mlp.c", "tref_lat.c", "tref_grav.c"]
 
 EOS_IDEAL, EOS_TABLE = 0, 1
 PLM, PPM = 0, 1
@@ -88,6 +88,10 @@ def lib():
         L = C.CDLL(SO)
         sig = {
             "tref_num_threads": (C.c_int, []),
+            "tref_set_phi_sg": (None, [C.c_void_p, dp]),
+            "tref_mg_solve": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_double,
+                                        C.c_int, C.c_int, C.c_double, dp]),
+            "tref_mg_defect_rms": (C.c_double, [C.c_int, C.c_int, C.c_int, dp, dp, dp]),
             "tref_frame_acceleration": (None, [C.c_void_p, dp, C.c_double, C.c_double, dp, dp]),
             "tref_boost": (None, [C.c_void_p, dp, dp, C.c_double]),
             "tref_saha_state": (None, [C.c_double, C.c_double, C.c_double, C.c_double, dp]),
@@ -289,6 +293,12 @@ class Mesh:
                              None if ids_a is None else IP(ids_a), C.byref(c))
         return c
 
+    def set_phi_sg(self, phi_padded):
+        """Self-gravity potential (padded layout, ghosts filled) for the hydro
+        sources; None switches it off.  The mesh keeps a reference."""
+        self._phi_sg = None if phi_padded is None else np.ascontiguousarray(phi_padded, dtype=np.float64)
+        lib().tref_set_phi_sg(self.h, None if self._phi_sg is None else P(self._phi_sg))
+
     def frame_acceleration(self, U, t, rho_min):
         """(A_fr[3], mass) of Eq. frame-acceleration at time t."""
         A = np.zeros(3)
@@ -351,3 +361,23 @@ def mlp_loss_grad(params, x, target):
 def num_threads():
     """Threads the oracle's OpenMP loops use."""
     return int(lib().tref_num_threads())
+
+
+def mg_solve(src, dx, phi=None, max_cycles=20, tol=0.0, npre=2, npost=2, omega=1.15):
+    """Multigrid solve of A_h phi = src on a periodic grid; src [nz][ny][nx].
+    Returns (phi, cycles, rms defect)."""
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    nz, ny, nx = src.shape
+    phi = np.zeros_like(src) if phi is None else np.ascontiguousarray(phi, dtype=np.float64).copy()
+    d = np.zeros(1)
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    n = lib().tref_mg_solve(nx, ny, nz, P(dxa), P(src), P(phi), max_cycles, tol, npre, npost, omega, P(d))
+    return phi, n, float(d[0])
+
+
+def mg_defect(src, phi, dx):
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    nz, ny, nx = src.shape
+    return lib().tref_mg_defect_rms(nx, ny, nz, P(np.ascontiguousarray(dx, dtype=np.float64)), P(src),
+                                    P(np.ascontiguousarray(phi, dtype=np.float64)))
+

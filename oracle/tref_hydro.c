@@ -64,6 +64,7 @@ struct tref_mesh {
   int64_t *off;
   int *pd;      /* nb * 3 padded sizes */
   int *owner;   /* global cell -> block */
+  const double *phi_sg;   /* self-gravity potential, padded layout (caller's), or NULL */
 };
 
 /* ---------------------------------------------------------------- mesh --- */
@@ -122,6 +123,9 @@ void tref_mesh_free(tref_mesh *m) {
 int64_t tref_mesh_ntot(const tref_mesh *m) { return m->ntot; }
 int64_t tref_mesh_block_offset(const tref_mesh *m, int b) { return m->off[b]; }
 int tref_nvar(const tref_mesh *m) { return m->nvar; }
+
+void tref_set_phi_sg(tref_mesh *m, const double *phi_padded) { m->phi_sg = phi_padded; }
+const double *tref_phi_sg(const tref_mesh *m) { return m->phi_sg; }
 
 /* Threads the OpenMP loops over blocks use (1 without OpenMP). */
 int tref_num_threads(void) {
@@ -466,6 +470,7 @@ static void stage_block(const tref_mesh *m, int stage, int b, const double *U0, 
           if (p->bh_on) phi[l] = tref_phi_bh(p, x, tst);
           if (p->excision_on) exc[l] = (char)excised_at(p, x, tst);
         }
+        if (m->phi_sg) phi[l] += m->phi_sg[m->off[b] + l];   /* Eq. potential-decomposition */
       }
 
   /* a4 + a5: fluxes on every face of every active direction */
@@ -526,7 +531,7 @@ static void stage_block(const tref_mesh *m, int stage, int b, const double *U0, 
           int64_t fhi = ((int64_t)ci[2] * nf[a][1] + ci[1]) * nf[a][0] + ci[0];
           for (int q = 0; q < nvar; ++q) L[q] -= (F[a][q * nfa + fhi] - F[a][q * nfa + flo]) / m->d.dx[a];
           divv += (F[a][6 * nfa + fhi] - F[a][6 * nfa + flo]) / m->d.dx[a];
-          if (p->bh_on) {
+          if (p->bh_on || m->phi_sg) {
             double ph = phi[l + st[a]], p0 = phi[l], pl = phi[l - st[a]];
             L[1 + a] -= W[l] * (ph - pl) / (2.0 * m->d.dx[a]);
             L[4] -= (F[a][fhi] * (ph - p0) + F[a][flo] * (p0 - pl)) / (2.0 * m->d.dx[a]);

@@ -190,14 +190,20 @@ static void reflux(const tref_mesh *m, const tref_mesh_view *v, double *U, doubl
                 double Is = R[fo[b] + side_index(v, b, s, c1, c2, q)];
                 dI[q] = Io - Is;   /* accepted minus local impulse */
               }
-              if (p->bh_on) {
+              const double *psg = tref_phi_sg(m);
+              if (p->bh_on || psg) {
                 double xi[3], xn[3];
                 int pos[3] = {ci[0] + gofs(v, 0), ci[1] + gofs(v, 1), ci[2] + gofs(v, 2)};
                 tref_cell_pos(m, b, pos[0], pos[1], pos[2], xi);
                 int pn[3] = {pos[0], pos[1], pos[2]};
                 pn[a] += side ? 1 : -1;
                 tref_cell_pos(m, b, pn[0], pn[1], pn[2], xn);
-                double phi_i = tref_phi_bh(p, xi, t), phi_n = tref_phi_bh(p, xn, t);
+                double phi_i = p->bh_on ? tref_phi_bh(p, xi, t) : 0.0;
+                double phi_n = p->bh_on ? tref_phi_bh(p, xn, t) : 0.0;
+                if (psg) {   /* the frozen self-gravity potential */
+                  phi_i += psg[l];
+                  phi_n += psg[v->off[b] + ((int64_t)pn[2] * P[1] + pn[1]) * P[0] + pn[0]];
+                }
                 /* Eq. lat-grav-reflux with dI_rho = local - accepted = -dI[0] */
                 U[4 * v->ntot + l] += sigma / (2.0 * v->dx[a]) * (-dI[0]) * (phi_n - phi_i);
               }

@@ -543,6 +543,7 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->sb.qcount);
   cudaFree(m->d_frame_part);
   cudaFree(m->d_frame_out);
+  gravity_release(m);
   cudaFree(m->d_f);
   cudaFree(m->d_f2);
   cudaFree(m->d_sorted);
@@ -763,6 +764,35 @@ extern "C" int tde_mesh_boost(tde_mesh *m, const double *V, double rho_min) {
   if (!m) return TDE_EINVAL;
   if (!m->U || !V) return fail(m->ctx, TDE_EINVAL, "tde_mesh_boost: arguments");
   CK(m->ctx, launch_boost(m, V, rho_min));
+  return TDE_OK;
+}
+
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+extern "C" int tde_gravity_solve(tde_mesh *m, const tde_grav_params *gp, int *cycles, double *defect) {
+  if (!m) return TDE_EINVAL;
+  if (!m->U || !gp || gp->max_cycles < 0 || gp->npre < 0 || gp->npost < 0)
+    return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: arguments");
+  for (int a = 0; a < 3; ++a)
+    if (m->phys.N[a] > 1 && (m->phys.bc[a] != TDE_BC_PERIODIC || !pow2(m->phys.N[a])))
+      return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: needs periodic power-of-two directions");
+  CK(m->ctx, gravity_solve(m, *gp, cycles, defect));
+  invalidate_graph(m);
+  return TDE_OK;
+}
+
+extern "C" int tde_gravity_enable(tde_mesh *m, int on) {
+  if (!m) return TDE_EINVAL;
+  if (on && !m->d_phi_sg) return fail(m->ctx, TDE_EINVAL, "tde_gravity_enable: no potential solved yet");
+  m->grav_on = on ? 1 : 0;
+  invalidate_graph(m);
+  return TDE_OK;
+}
+
+extern "C" int tde_gravity_phi(tde_mesh *m, double *phi) {
+  if (!m) return TDE_EINVAL;
+  if (!phi || !m->grav) return fail(m->ctx, TDE_EINVAL, "tde_gravity_phi: no potential");
+  CK(m->ctx, gravity_copy_phi(m, phi));
   return TDE_OK;
 }
 

@@ -602,6 +602,7 @@ static SweepArgs sweep_args(tde_mesh *m, int stage, const double *U0, const doub
   a.freg = freg;
   a.fo = m->d_fo;
   a.nvar = m->phys.nvar;
+  a.phi_sg = m->grav_on ? m->d_phi_sg : nullptr;
   return a;
 }
 

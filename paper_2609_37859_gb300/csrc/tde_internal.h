@@ -29,8 +29,9 @@ struct ProfScope {
   tde_ctx *c;
   int kind;
   cudaEvent_t a = nullptr;
-  ProfScope(tde_ctx *ctx, int k) : c(ctx), kind(k) {
-    c->launches[k]++;
+  // count = false: the caller counts the scope's launches itself
+  ProfScope(tde_ctx *ctx, int k, bool count = true) : c(ctx), kind(k) {
+    if (count) c->launches[k]++;
     if (c->prof) {
       a = take();
       cudaEventRecord(a, c->stream);
@@ -107,6 +108,9 @@ struct tde_mesh {
   double *d_frame_part = nullptr;    // partial sums of the frame acceleration
   size_t frame_part_cap = 0;
   double *d_frame_out = nullptr;     // (A_fr[3], mass)
+  void *grav = nullptr;              // multigrid levels (tde_grav.cu)
+  double *d_phi_sg = nullptr;        // self-gravity potential, MeshBlock layout
+  int grav_on = 0;                   // the hydro sources add d_phi_sg
   int64_t ntot = 0;
   int64_t max_interior = 0;          // largest interior cell count of a block
   int max_ghosts = 0;                // largest ghost count of a block
@@ -176,6 +180,9 @@ cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3]
 void invalidate_graph(tde_mesh *m);
 cudaError_t launch_frame_acceleration(tde_mesh *m, const BH &bh, double rho_min, double *out4);
 cudaError_t launch_boost(tde_mesh *m, const double *V, double rho_min);
+cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, double *defect);
+cudaError_t gravity_copy_phi(tde_mesh *m, double *dst);
+void gravity_release(tde_mesh *m);
 bool closure_ready(const tde_mesh *m);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(LNT) k_reflux(Phys p, BH bh, OwnerLattice ol,
                                                 const int32_t *__restrict__ f, double *U,
                                                 long long ntot, double *R,
                                                 const long long *__restrict__ fo, int nvar,
-                                                const double *__restrict__ scal, int tau) {
+                                                const double *__restrict__ scal, int tau, const double *__restrict__ phi_sg) {
   const int b = ids[blockIdx.x];
   const DevBlock B = blocks[b];
   const int fb = f[b];
@@ -260,16 +260,23 @@ __global__ void __launch_bounds__(LNT) k_reflux(Phys p, BH bh, OwnerLattice ol,
           const long long l = B.off + ((long long)pos[2] * B.p[1] + pos[1]) * B.p[0] + pos[0];
           double dI[6];
           for (int q = 0; q < nvar; ++q) dI[q] = R[soo + q * ncell_o + co] - R[sos + q * ncell + cs];
-          if (bh.on) {
+          if (bh.on || phi_sg) {
             int pn[3] = {pos[0], pos[1], pos[2]};
             pn[a] += side ? 1 : -1;
-            double xi[3], xn[3];
-            lat_cell_centre(p, B, pos, xi);
-            lat_cell_centre(p, B, pn, xn);
-            const double di0 = xi[0] - rb[0], di1 = xi[1] - rb[1], di2 = xi[2] - rb[2];
-            const double dn0 = xn[0] - rb[0], dn1 = xn[1] - rb[1], dn2 = xn[2] - rb[2];
-            const double phi_i = -bh.GM / sqrt(di0 * di0 + di1 * di1 + di2 * di2 + bh.rs2);
-            const double phi_n = -bh.GM / sqrt(dn0 * dn0 + dn1 * dn1 + dn2 * dn2 + bh.rs2);
+            double phi_i = 0.0, phi_n = 0.0;
+            if (bh.on) {
+              double xi[3], xn[3];
+              lat_cell_centre(p, B, pos, xi);
+              lat_cell_centre(p, B, pn, xn);
+              const double di0 = xi[0] - rb[0], di1 = xi[1] - rb[1], di2 = xi[2] - rb[2];
+              const double dn0 = xn[0] - rb[0], dn1 = xn[1] - rb[1], dn2 = xn[2] - rb[2];
+              phi_i = -bh.GM / sqrt(di0 * di0 + di1 * di1 + di2 * di2 + bh.rs2);
+              phi_n = -bh.GM / sqrt(dn0 * dn0 + dn1 * dn1 + dn2 * dn2 + bh.rs2);
+            }
+            if (phi_sg) {   // the frozen self-gravity potential, ghosts included
+              phi_i += phi_sg[l];
+              phi_n += phi_sg[B.off + ((long long)pn[2] * B.p[1] + pn[1]) * B.p[0] + pn[0]];
+            }
             U[4 * ntot + l] += sigma / (2.0 * p.dx[a]) * (-dI[0]) * (phi_n - phi_i);
           }
           for (int q = 0; q < nvar; ++q) U[q * ntot + l] += -sigma * dI[q] / p.dx[a];
@@ -401,7 +408,8 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
         {
           ProfScope ps(c, TDE_K_SCALAR);
           k_reflux<<<ncomp, LNT, 0, s>>>(p, bh, ol, m->d_blocks, m->d_sorted, m->d_f, m->U, (long long)m->ntot,
-                                         m->d_freg, m->d_fo, nvar, m->d_scal, tau);
+                                         m->d_freg, m->d_fo, nvar, m->d_scal, tau,
+                                         m->grav_on ? m->d_phi_sg : nullptr);
         }
         LCK(c, cudaGetLastError());
         if (bh.excise) LCK(c, launch_excise(m, m->U, ncomp, m->d_sorted, bh, ta));

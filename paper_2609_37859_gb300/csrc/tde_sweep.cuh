@@ -54,6 +54,7 @@ struct SweepArgs {
   Counters *cnt;
   int stage, first, PD, NF;
   double *freg;              // flux impulse registers (LAT) or null
+  const double *phi_sg;      // self-gravity potential (MeshBlock layout) or null
   const long long *fo;       // register offset per block
   int nvar;
 };
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       if (lane < nlane) Wt[sw(v, pos, lane)] = a.W[v * ntot + base + pos * sD + lane * sL];
     }
   }
-  const bool grav = a.bh.on, exc = a.bh.excise;
+  const bool grav = a.bh.on || a.phi_sg, exc = a.bh.excise;
   if (grav || exc) {
     const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
     double rb[3];
@@ -142,7 +143,11 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       const double dx0 = x[0] - rb[0], dx1 = x[1] - rb[1], dx2 = x[2] - rb[2];
       const double r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
       const int idx = D == 0 ? lane * NF + c : c * M + lane;
-      if (grav) Ph[idx] = -a.bh.GM / sqrt(r2 + a.bh.rs2);
+      if (grav) {
+        double ph = a.bh.on ? -a.bh.GM / sqrt(r2 + a.bh.rs2) : 0.0;
+        if (a.phi_sg) ph += a.phi_sg[base + (long long)(g - 1 + c) * sD + lane * sL];   // Phi_bh + Phi_sg
+        Ph[idx] = ph;
+      }
       if (exc) Ex[idx] = sqrt(r2) < a.bh.rexc ? 1 : 0;
     }
   }

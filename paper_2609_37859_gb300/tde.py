@@ -44,6 +44,11 @@ class BHState(C.Structure):
                 ("afr", C.c_double * 3)]
 
 
+class GravParams(C.Structure):
+    _fields_ = [("G", C.c_double), ("rho_min", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
+                ("npre", C.c_int), ("npost", C.c_int), ("omega", C.c_double), ("warm", C.c_int)]
+
+
 class BlockDesc(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("i0", "j0", "k0", "nx", "ny", "nz")]
 
@@ -119,6 +124,9 @@ _SIGS = {
     "tde_frame_acceleration": [vp, C.POINTER(BHState), C.c_double, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
     "tde_mesh_boost": [vp, C.POINTER(C.c_double), C.c_double],
+    "tde_gravity_solve": [vp, C.POINTER(GravParams), C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "tde_gravity_enable": [vp, C.c_int],
+    "tde_gravity_phi": [vp, dp],
     "tde_mesh_set_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_mesh_get_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
@@ -405,6 +413,24 @@ class Mesh:
         mass = C.c_double()
         self.ctx.check(lib().tde_frame_acceleration(self.h, C.byref(bh), rho_min, A, C.byref(mass)))
         return list(A), mass.value
+
+    def gravity_solve(self, G, rho_min, tol=1e-10, max_cycles=20, npre=2, npost=2, omega=1.15, warm=True):
+        """Self-gravity potential from the bound state's density; returns (cycles, rms defect)."""
+        gp = GravParams(G, rho_min, tol, max_cycles, npre, npost, omega, 1 if warm else 0)
+        n, d = C.c_int(), C.c_double()
+        self.ctx.check(lib().tde_gravity_solve(self.h, C.byref(gp), C.byref(n), C.byref(d)))
+        return n.value, d.value
+
+    def gravity_enable(self, on=True):
+        self.ctx.check(lib().tde_gravity_enable(self.h, 1 if on else 0))
+
+    def gravity_phi(self):
+        """The potential on the global grid, [Nz, Ny, Nx] (a CUDA tensor)."""
+        import torch
+        N = self.layout.N
+        out = torch.empty((N[2], N[1], N[0]), dtype=torch.float64, device=self.U.device)
+        self.ctx.check(lib().tde_gravity_phi(self.h, _ptr(out)))
+        return out
 
     def boost(self, V, rho_min):
         v = (C.c_double * 3)(*V)
