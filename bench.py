@@ -260,6 +260,8 @@ def run_gpu(args):
             eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
         del mesh, U_init, host_in, host_out
         torch.cuda.empty_cache()
+        if not args.no_grav:
+            line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
         if not args.no_lat:
             line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_c5:
@@ -534,6 +536,59 @@ def lat_counts_cells(lay, fac, fmax):
     return int((cells * (fmax // fac)).sum() * 2)
 
 
+# ------------------------------------------------------------ self-gravity ---
+
+def gravity_bench(ctx, tde, torch, dev, args, n=256):
+    """Self-gravity multigrid on an n^3 periodic grid (n^3 / 32^3 MeshBlocks):
+    time per V-cycle as the paper measures it (runs of 6 and 2 fixed V-cycles,
+    difference / 4), V-cycles and time to a 1e-9 rms defect from zero and from the
+    previous potential, and the fine-level traffic of a V-cycle against HBM."""
+    from paper_2609_37859_gb300 import workloads as wl
+    lay = wl.uniform_layout((n, n, n), (32, 32, 32), bc=(1, 1, 1), ng=2)
+    W = wl.random_smooth(lay, seed=SEED, drho=0.5, P0=1.0, modes=4)
+    mesh = tde.Mesh(ctx, lay, tde.make_params())
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    del W
+    G = 1.0 / (4.0 * np.pi)
+    mesh.gravity_solve(G, 0.0, tol=0.0, max_cycles=2, warm=False)   # allocation, warm-up
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3, r
+    ms6, _ = timed(lambda: mesh.gravity_solve(G, 0.0, tol=0.0, max_cycles=6, warm=False))
+    ms2, _ = timed(lambda: mesh.gravity_solve(G, 0.0, tol=0.0, max_cycles=2, warm=False))
+    per_cycle = (ms6 - ms2) / 4.0
+    ms_cold, (ncold, dcold) = timed(lambda: mesh.gravity_solve(G, 0.0, tol=1e-9, max_cycles=30, warm=False))
+    # a warm start after a small change of the density (one hydro step)
+    mesh.step(cfl=CFL)
+    ms_warm, (nwarm, dwarm) = timed(lambda: mesh.gravity_solve(G, 0.0, tol=1e-9, max_cycles=30, warm=True))
+    ncell = lay.ncells
+    # fine-level algorithmic traffic per V-cycle: 5 red-black sweeps (2 pre, 2 post,
+    # 1 extra) of 24 B/cell (phi and source read, phi written), restriction 19,
+    # prolongation 18, the defect norm 16 B/cell; coarser levels add 1/7
+    bytes_cycle = ncell * (5 * 24 + 19 + 18 + 16) * 8.0 / 7.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    del mesh
+    torch.cuda.empty_cache()
+    return {"workload": "%d^3 periodic, %d MeshBlocks of 32^3, random smooth density, G = 1/(4 pi)" %
+                        (n, lay.nb),
+            "ms_per_vcycle": per_cycle, "cold": {"vcycles": ncold, "defect": dcold, "ms": ms_cold},
+            "warm_after_one_step": {"vcycles": nwarm, "defect": dwarm, "ms": ms_warm},
+            "hbm": {"algorithmic_bytes_per_vcycle": bytes_cycle,
+                    "achieved_gbs": bytes_cycle / (per_cycle * 1e-3) * 1e-9, "peak_gbs": hbm,
+                    "frac": bytes_cycle / (per_cycle * 1e-3) * 1e-9 / hbm},
+            "paper_context": "Table mg-cost: 6.2 / 11.3 ms per V-cycle (16^3 / 32^3 MeshBlocks, 5 AMR "
+                             "levels, two V100s; AthenaK public solver 22.4 / 49.6 ms)"}
+
+
 # ------------------------------------------------------ production shape (C5) ---
 
 # rho_floor (rho0), p_floor (rho0 v0^2): 100x Table 1's.  With Table 1's floors
@@ -702,6 +757,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--no-c5", action="store_true", help="skip the production-shaped LAT run")
+    ap.add_argument("--no-grav", action="store_true", help="skip the self-gravity multigrid")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -12,6 +12,7 @@
 // cell.  The levels are global arrays (x fastest); the MeshBlock layout is
 // gathered into level 0 and the potential scattered back (ghosts included).
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -27,29 +28,34 @@ struct Lev {
   int n[3];
   double dx[3];
   double *phi, *src, *tmp;
+  // seven-point operator, per level: (A phi)_c = aw . (2 phi_c - phi_{c+a} - phi_{c-a});
+  // Gauss-Seidel value = cs src + cw . (phi_{c+a} + phi_{c-a}) (cw = w_a / diag,
+  // cs = dx^2 / diag); zero weights in directions with one cell
+  double aw[3], cw[3], cs;
 };
 
-__device__ __forceinline__ long long wrap_idx(const Lev &L, int i, int j, int k) {
+// 32-bit index arithmetic throughout (levels have < 2^31 cells; 64-bit integer
+// division would issue on the FP64 pipe)
+__device__ __forceinline__ unsigned wrap_idx(const Lev &L, int i, int j, int k) {
   i = i < 0 ? i + L.n[0] : (i >= L.n[0] ? i - L.n[0] : i);
   j = j < 0 ? j + L.n[1] : (j >= L.n[1] ? j - L.n[1] : j);
   k = k < 0 ? k + L.n[2] : (k >= L.n[2] ? k - L.n[2] : k);
-  return ((long long)k * L.n[1] + j) * L.n[0] + i;
+  return ((unsigned)k * L.n[1] + j) * L.n[0] + i;
 }
 
-__device__ __forceinline__ void lev_weights(const Lev &L, double w[3]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) w[a] = L.n[a] > 1 ? (L.dx[0] / L.dx[a]) * (L.dx[0] / L.dx[a]) : 0.0;
+__device__ __forceinline__ void decompose(const Lev &L, unsigned c, int &i, int &j, int &k) {
+  const unsigned r = c / (unsigned)L.n[0];
+  i = (int)(c - r * L.n[0]);
+  k = (int)(r / (unsigned)L.n[1]);
+  j = (int)(r - (unsigned)k * L.n[1]);
 }
 
-// (A phi)_c = -(1/dx^2) sum_a w_a (phi_{c+a} + phi_{c-a} - 2 phi_c)
 __device__ __forceinline__ double apply_A(const Lev &L, const double *phi, int i, int j, int k) {
-  double w[3];
-  lev_weights(L, w);
-  const double c = phi[wrap_idx(L, i, j, k)];
-  double s = w[0] * (phi[wrap_idx(L, i + 1, j, k)] + phi[wrap_idx(L, i - 1, j, k)] - 2.0 * c);
-  s += w[1] * (phi[wrap_idx(L, i, j + 1, k)] + phi[wrap_idx(L, i, j - 1, k)] - 2.0 * c);
-  s += w[2] * (phi[wrap_idx(L, i, j, k + 1)] + phi[wrap_idx(L, i, j, k - 1)] - 2.0 * c);
-  return -s / (L.dx[0] * L.dx[0]);
+  const double c2 = 2.0 * phi[wrap_idx(L, i, j, k)];
+  double s = L.aw[0] * (c2 - phi[wrap_idx(L, i + 1, j, k)] - phi[wrap_idx(L, i - 1, j, k)]);
+  s = fma(L.aw[1], c2 - phi[wrap_idx(L, i, j + 1, k)] - phi[wrap_idx(L, i, j - 1, k)], s);
+  s = fma(L.aw[2], c2 - phi[wrap_idx(L, i, j, k + 1)] - phi[wrap_idx(L, i, j, k - 1)], s);
+  return s;
 }
 
 // level-0 source from the MeshBlock density: S = -4 pi G rho where rho > rho_min
@@ -71,13 +77,12 @@ __global__ void __launch_bounds__(GT) k_mg_gather(Phys p, const DevBlock *__rest
 // partial sums (one per CTA) of f, or of the squared defect if sq
 __global__ void __launch_bounds__(GT) k_mg_partial(Lev L, int sq, double *part) {
   __shared__ double red[GT / 32];
-  const long long n = (long long)L.n[0] * L.n[1] * L.n[2];
+  const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
   double s = 0.0;
-  for (long long c = blockIdx.x * (long long)GT + threadIdx.x; c < n; c += (long long)gridDim.x * GT) {
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
     if (sq) {
-      const int i = (int)(c % L.n[0]);
-      const long long r = c / L.n[0];
-      const int j = (int)(r % L.n[1]), k = (int)(r / L.n[1]);
+      int i, j, k;
+      decompose(L, c, i, j, k);
       const double d = L.src[c] - apply_A(L, L.phi, i, j, k);
       s += d * d;
     } else {
@@ -110,50 +115,50 @@ __global__ void __launch_bounds__(GT) k_mg_final(const double *__restrict__ part
 }
 
 __global__ void __launch_bounds__(GT) k_mg_sub_mean(Lev L, const double *__restrict__ mean) {
-  const long long n = (long long)L.n[0] * L.n[1] * L.n[2];
+  const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
   const double m = *mean;
-  for (long long c = blockIdx.x * (long long)GT + threadIdx.x; c < n; c += (long long)gridDim.x * GT)
-    L.src[c] -= m;
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) L.src[c] -= m;
 }
 
-// one colour of a red-black Gauss-Seidel sweep (colour = parity of i + j + k)
+// one colour of a red-black Gauss-Seidel sweep (colour = parity of i + j + k):
+// phi <- phi + omega (GS value - phi)
 __global__ void __launch_bounds__(GT) k_mg_smooth(Lev L, int colour, double omega) {
-  double w[3];
-  lev_weights(L, w);
-  const double diag = 2.0 * (w[0] + w[1] + w[2]);
-  const double h2 = L.dx[0] * L.dx[0];
-  const int hx = (L.n[0] + 1) / 2;   // cells of one colour per row (n[0] even, or 1)
-  const long long nrow = (long long)L.n[1] * L.n[2];
-  for (long long e = blockIdx.x * (long long)GT + threadIdx.x; e < nrow * hx; e += (long long)gridDim.x * GT) {
-    const long long row = e / hx;
-    const int j = (int)(row % L.n[1]), k = (int)(row / L.n[1]);
-    const int i = L.n[0] > 1 ? 2 * (int)(e - row * hx) + ((j + k + colour) & 1) : 0;
-    if (L.n[0] == 1 && ((j + k) & 1) != colour) continue;
-    const long long c = (row * L.n[0]) + i;
-    const double nb = w[0] * (L.phi[wrap_idx(L, i + 1, j, k)] + L.phi[wrap_idx(L, i - 1, j, k)]) +
-                      w[1] * (L.phi[wrap_idx(L, i, j + 1, k)] + L.phi[wrap_idx(L, i, j - 1, k)]) +
-                      w[2] * (L.phi[wrap_idx(L, i, j, k + 1)] + L.phi[wrap_idx(L, i, j, k - 1)]);
-    const double gs = (h2 * L.src[c] + nb) / diag;
-    L.phi[c] = (1.0 - omega) * L.phi[c] + omega * gs;
+  const unsigned hx = (unsigned)(L.n[0] + 1) / 2;   // cells of one colour per row (n[0] even, or 1)
+  const unsigned nrow = (unsigned)L.n[1] * L.n[2];
+  for (unsigned e = blockIdx.x * GT + threadIdx.x; e < nrow * hx; e += gridDim.x * GT) {
+    const unsigned row = e / hx;
+    const int k = (int)(row / (unsigned)L.n[1]), j = (int)(row - (unsigned)k * L.n[1]);
+    int i;
+    if (L.n[0] > 1) {
+      i = 2 * (int)(e - row * hx) + ((j + k + colour) & 1);
+    } else {
+      if (((j + k) & 1) != colour) continue;
+      i = 0;
+    }
+    const unsigned c = row * L.n[0] + i;
+    double nb = L.cw[0] * (L.phi[wrap_idx(L, i + 1, j, k)] + L.phi[wrap_idx(L, i - 1, j, k)]);
+    nb = fma(L.cw[1], L.phi[wrap_idx(L, i, j + 1, k)] + L.phi[wrap_idx(L, i, j - 1, k)], nb);
+    nb = fma(L.cw[2], L.phi[wrap_idx(L, i, j, k + 1)] + L.phi[wrap_idx(L, i, j, k - 1)], nb);
+    const double gs = fma(L.cs, L.src[c], nb);
+    const double p0 = L.phi[c];
+    L.phi[c] = fma(omega, gs - p0, p0);
   }
 }
 
 // coarse cell: phi_C = R phi_f (also kept in C.tmp), R d_f (defect of the fine
 // level averaged over the children) into C.src
-__global__ void __launch_bounds__(GT) k_mg_restrict(Lev F, Lev C) {
+__global__ void __launch_bounds__(GT) k_mg_restrict(Lev F, Lev C, double inv) {
   const int r0 = F.n[0] / C.n[0], r1 = F.n[1] / C.n[1], r2 = F.n[2] / C.n[2];
-  const double inv = 1.0 / (r0 * r1 * r2);
-  const long long n = (long long)C.n[0] * C.n[1] * C.n[2];
-  for (long long c = blockIdx.x * (long long)GT + threadIdx.x; c < n; c += (long long)gridDim.x * GT) {
-    const int I = (int)(c % C.n[0]);
-    const long long r = c / C.n[0];
-    const int J = (int)(r % C.n[1]), K = (int)(r / C.n[1]);
+  const unsigned n = (unsigned)C.n[0] * C.n[1] * C.n[2];
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    int I, J, K;
+    decompose(C, c, I, J, K);
     double sp = 0.0, sd = 0.0;
     for (int cz = 0; cz < r2; ++cz)
       for (int by = 0; by < r1; ++by)
         for (int ax = 0; ax < r0; ++ax) {
           const int i = r0 * I + ax, j = r1 * J + by, k = r2 * K + cz;
-          const long long f = ((long long)k * F.n[1] + j) * F.n[0] + i;
+          const unsigned f = ((unsigned)k * F.n[1] + j) * F.n[0] + i;
           sp += F.phi[f];
           sd += F.src[f] - apply_A(F, F.phi, i, j, k);
         }
@@ -165,30 +170,39 @@ __global__ void __launch_bounds__(GT) k_mg_restrict(Lev F, Lev C) {
 
 // coarse source of the full-approximation equation: S_C = R d_f + A_C (R phi_f)
 __global__ void __launch_bounds__(GT) k_mg_fas(Lev C) {
-  const long long n = (long long)C.n[0] * C.n[1] * C.n[2];
-  for (long long c = blockIdx.x * (long long)GT + threadIdx.x; c < n; c += (long long)gridDim.x * GT) {
-    const int I = (int)(c % C.n[0]);
-    const long long r = c / C.n[0];
-    const int J = (int)(r % C.n[1]), K = (int)(r / C.n[1]);
+  const unsigned n = (unsigned)C.n[0] * C.n[1] * C.n[2];
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    int I, J, K;
+    decompose(C, c, I, J, K);
     C.src[c] += apply_A(C, C.tmp, I, J, K);
   }
 }
 
-// fine phi += P (phi_C - R phi_f), trilinear (cell centred): per halved
-// direction 3/4 on the parent, 1/4 on its neighbour towards the fine cell
+// the coarse correction phi_C - R phi_f, formed once per coarse cell (into tmp)
+__global__ void __launch_bounds__(GT) k_mg_corr(Lev C) {
+  const unsigned n = (unsigned)C.n[0] * C.n[1] * C.n[2];
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) C.tmp[c] = C.phi[c] - C.tmp[c];
+}
+
+// fine phi += P e, e = phi_C - R phi_f (in C.tmp), trilinear (cell centred):
+// per halved direction 3/4 on the parent, 1/4 on its neighbour towards the fine cell
 __global__ void __launch_bounds__(GT) k_mg_prolong(Lev F, Lev C) {
-  const long long n = (long long)F.n[0] * F.n[1] * F.n[2];
-  for (long long c = blockIdx.x * (long long)GT + threadIdx.x; c < n; c += (long long)gridDim.x * GT) {
-    const int f[3] = {(int)(c % F.n[0]), (int)((c / F.n[0]) % F.n[1]), (int)(c / ((long long)F.n[0] * F.n[1]))};
+  const unsigned n = (unsigned)F.n[0] * F.n[1] * F.n[2];
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    int f[3];
+    decompose(F, c, f[0], f[1], f[2]);
     int p[3], q[3];
-    double wp[3];
+    bool h[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      if (F.n[a] == C.n[a]) { p[a] = q[a] = f[a]; wp[a] = 1.0; continue; }
-      p[a] = f[a] >> 1;
-      q[a] = (f[a] & 1) ? p[a] + 1 : p[a] - 1;
-      wp[a] = 0.75;
+      h[a] = F.n[a] != C.n[a];
+      p[a] = h[a] ? f[a] >> 1 : f[a];
+      q[a] = h[a] ? ((f[a] & 1) ? p[a] + 1 : p[a] - 1) : p[a];
     }
+    // the weight of coarse cell (ax, by, cz) is the product over halved directions
+    // of 3/4 (parent) or 1/4 (neighbour): w = 3^(number of parents) / 4^(halved)
+    const int nh = (int)h[0] + (int)h[1] + (int)h[2];
+    const double scale = nh == 3 ? 1.0 / 64.0 : (nh == 2 ? 1.0 / 16.0 : (nh == 1 ? 0.25 : 1.0));
     double s = 0.0;
 #pragma unroll
     for (int cz = 0; cz < 2; ++cz)
@@ -196,14 +210,12 @@ __global__ void __launch_bounds__(GT) k_mg_prolong(Lev F, Lev C) {
       for (int by = 0; by < 2; ++by)
 #pragma unroll
         for (int ax = 0; ax < 2; ++ax) {
-          const double wa = ax ? 1.0 - wp[0] : wp[0];
-          const double wb = by ? 1.0 - wp[1] : wp[1];
-          const double wc = cz ? 1.0 - wp[2] : wp[2];
-          if (wa == 0.0 || wb == 0.0 || wc == 0.0) continue;
-          const long long e = wrap_idx(C, ax ? q[0] : p[0], by ? q[1] : p[1], cz ? q[2] : p[2]);
-          s += wa * wb * wc * (C.phi[e] - C.tmp[e]);
+          if ((ax && !h[0]) || (by && !h[1]) || (cz && !h[2])) continue;
+          const int np = (h[0] && !ax) + (h[1] && !by) + (h[2] && !cz);
+          const double w = np == 3 ? 27.0 : (np == 2 ? 9.0 : (np == 1 ? 3.0 : 1.0));
+          s = fma(w, C.tmp[wrap_idx(C, ax ? q[0] : p[0], by ? q[1] : p[1], cz ? q[2] : p[2])], s);
         }
-    F.phi[c] += s;
+    F.phi[c] = fma(scale, s, F.phi[c]);
   }
 }
 
@@ -231,6 +243,9 @@ unsigned grid_for(long long n) {
 
 struct GravState {
   long long launches = 0;   // kernels launched since the last count (for the profile)
+  cudaGraphExec_t cycle = nullptr;   // one V-cycle + the extra sweep + the defect norm
+  int cycle_launches = 0;
+  double cycle_key[4] = {0, 0, 0, 0};  // npre, npost, omega the graph was captured with
   int nl = 0;
   Lev lev[40];
   double *part = nullptr, *scal = nullptr;   // partial sums; [0] mean, [1] defect
@@ -239,6 +254,7 @@ struct GravState {
 
 static void grav_free(GravState *g) {
   if (!g) return;
+  if (g->cycle) cudaGraphExecDestroy(g->cycle);
   for (int l = 0; l < g->nl; ++l) {
     cudaFree(g->lev[l].phi);
     cudaFree(g->lev[l].src);
@@ -265,6 +281,17 @@ static cudaError_t grav_init(tde_mesh *m) {
   for (;;) {
     Lev &L = g->lev[g->nl++];
     for (int a = 0; a < 3; ++a) { L.n[a] = n[a]; L.dx[a] = h[a]; }
+    double w[3], wsum = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      w[a] = n[a] > 1 ? (h[0] / h[a]) * (h[0] / h[a]) : 0.0;
+      wsum += w[a];
+    }
+    const double diag = 2.0 * wsum;
+    for (int a = 0; a < 3; ++a) {
+      L.aw[a] = w[a] / (h[0] * h[0]);
+      L.cw[a] = diag > 0.0 ? w[a] / diag : 0.0;
+    }
+    L.cs = diag > 0.0 ? h[0] * h[0] / diag : 0.0;
     const size_t nc = (size_t)n[0] * n[1] * n[2];
     L.phi = L.src = L.tmp = nullptr;
     if (err == cudaSuccess) err = cudaMalloc(&L.phi, sizeof(double) * nc);
@@ -309,11 +336,13 @@ static void vcycle(GravState *g, int l, const tde_grav_params &gp, cudaStream_t 
   const Lev &F = g->lev[l], &C = g->lev[l + 1];
   for (int q = 0; q < gp.npre; ++q) smooth(g, F, gp.omega, s);
   const long long nc = (long long)C.n[0] * C.n[1] * C.n[2];
-  k_mg_restrict<<<grid_for(nc), GT, 0, s>>>(F, C);
+  const double inv = (double)nc / ((double)F.n[0] * F.n[1] * F.n[2]);   // 1 / children per cell
+  k_mg_restrict<<<grid_for(nc), GT, 0, s>>>(F, C, inv);
   k_mg_fas<<<grid_for(nc), GT, 0, s>>>(C);
   vcycle(g, l + 1, gp, s);
+  k_mg_corr<<<grid_for(nc), GT, 0, s>>>(C);
   k_mg_prolong<<<grid_for((long long)F.n[0] * F.n[1] * F.n[2]), GT, 0, s>>>(F, C);
-  g->launches += 3;
+  g->launches += 4;
   for (int q = 0; q < gp.npost; ++q) smooth(g, F, gp.omega, s);
 }
 
@@ -337,20 +366,55 @@ cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, d
   }
   int ncyc = 0;
   double d = 0.0;
-  for (;;) {
-    {
-      ProfScope ps(c, TDE_K_GRAV, false);
-      reduce(g, L0, 1, g->scal + 1, s);
+  {
+    ProfScope ps(c, TDE_K_GRAV, false);
+    reduce(g, L0, 1, g->scal + 1, s);
+  }
+  // one cycle (V-cycle, the extra fine sweep, the defect norm) as a CUDA graph:
+  // about a hundred small launches on the coarse levels replayed as one
+  const double key[4] = {(double)gp.npre, (double)gp.npost, gp.omega, 1.0};
+  if (g->cycle && memcmp(key, g->cycle_key, sizeof key) != 0) {
+    cudaGraphExecDestroy(g->cycle);
+    g->cycle = nullptr;
+  }
+  if (!g->cycle && gp.max_cycles > 0) {
+    // captured on the mesh's private stream (the context's stream may be the
+    // legacy default stream, which cannot be captured), after the work queued so far
+    if (!m->cap_stream) {
+      err = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+      if (err != cudaSuccess) return err;
     }
+    err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return err;
+    const long long before = g->launches;
+    cudaStream_t cs = m->cap_stream;
+    cudaGraph_t graph = nullptr;
+    err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+      vcycle(g, 0, gp, cs);
+      smooth(g, L0, gp.omega, cs);   // the extra sweep on the finest level
+      reduce(g, L0, 1, g->scal + 1, cs);
+      err = cudaStreamEndCapture(cs, &graph);
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&g->cycle, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+      g->cycle = nullptr;
+      return err;
+    }
+    g->cycle_launches = (int)(g->launches - before);
+    g->launches = before;
+    memcpy(g->cycle_key, key, sizeof key);
+  }
+  for (;;) {
     err = cudaMemcpyAsync(&d, g->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return err;
     if (d < gp.tol || ncyc >= gp.max_cycles) break;
     ProfScope ps(c, TDE_K_GRAV, false);
-    vcycle(g, 0, gp, s);
-    smooth(g, L0, gp.omega, s);   // the extra sweep on the finest level
-    err = cudaGetLastError();
+    err = cudaGraphLaunch(g->cycle, s);
     if (err != cudaSuccess) return err;
+    g->launches += g->cycle_launches;
     ++ncyc;
   }
   {
