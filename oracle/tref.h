@@ -203,6 +203,19 @@ double tref_mg_defect_rms(int nx, int ny, int nz, const double *dx, const double
 void tref_set_phi_sg(tref_mesh *m, const double *phi_padded);
 const double *tref_phi_sg(const tref_mesh *m);
 
+const tref_mesh_desc *tref_mesh_get_desc(const tref_mesh *m);
+/* padded index of the interior cell at global cell (i, j, k) */
+int64_t tref_cell_index(const tref_mesh *m, int i, int j, int k);
+
+/* Conserved-variable remap (Sec. 5.2) of src's state Usrc onto dst's state Udst
+ * (interior cells): midpoint-quadrature averages of trilinear interpolants,
+ * energy carried as thermal energy (mode TREF_REMAP_THERMAL) or as total energy
+ * (TREF_REMAP_TOTAL); coincident cells copied; samples outside the source
+ * domain take the floor state (rho_floor, at rest, internal energy u_floor). */
+enum { TREF_REMAP_THERMAL = 0, TREF_REMAP_TOTAL = 1 };
+void tref_remap(const tref_mesh *dst, double *Udst, const tref_mesh *src, const double *Usrc, int mode,
+                double rho_floor, double u_floor);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,12 +17,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libtref.so")
-SOURCES = ["tref_eos.c", "tref_hydro.c", "tref_mlp.c", "tref_lat.c", "tref_grav.c"]
+SOURCES = ["tref_eos.c", "tref_hydro.c", "tref_mlp.c", "tref_lat.c", "tref_grav.c", "tref_remap.c"]
 
 EOS_IDEAL, EOS_TABLE = 0, 1
 PLM, PPM = 0, 1
 OUTFLOW, PERIODIC = 0, 1
 HLLC, HLLE = 0, 1
+REMAP_THERMAL, REMAP_TOTAL = 0, 1
 MLP_NPARAM = 4482
 
 
@@ -88,6 +89,7 @@ def lib():
         L = C.CDLL(SO)
         sig = {
             "tref_num_threads": (C.c_int, []),
+            "tref_remap": (None, [C.c_void_p, dp, C.c_void_p, dp, C.c_int, C.c_double, C.c_double]),
             "tref_set_phi_sg": (None, [C.c_void_p, dp]),
             "tref_mg_solve": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_double,
                                         C.c_int, C.c_int, C.c_double, dp]),
@@ -380,4 +382,12 @@ def mg_defect(src, phi, dx):
     nz, ny, nx = src.shape
     return lib().tref_mg_defect_rms(nx, ny, nz, P(np.ascontiguousarray(dx, dtype=np.float64)), P(src),
                                     P(np.ascontiguousarray(phi, dtype=np.float64)))
+
+
+def remap(dst, src, Usrc, mode=REMAP_THERMAL, rho_floor=1e-300, u_floor=1e-300):
+    """Remap the state Usrc of mesh src onto a new state of mesh dst (Sec. 5.2)."""
+    Ud = dst.new_state()
+    lib().tref_remap(dst.h, P(Ud), src.h, P(np.ascontiguousarray(Usrc, dtype=np.float64)), mode,
+                     rho_floor, u_floor)
+    return Ud
 

@@ -144,6 +144,16 @@ static int64_t cidx(const tref_mesh *m, int b, int i, int j, int k) {
   return m->off[b] + ((int64_t)k * P[1] + j) * P[0] + i;
 }
 
+const tref_mesh_desc *tref_mesh_get_desc(const tref_mesh *m) { return &m->d; }
+/* padded index (within all blocks) of the interior cell at global cell (i, j, k) */
+int64_t tref_cell_index(const tref_mesh *m, int i, int j, int k) {
+  const int b = m->owner[((int64_t)k * m->d.N[1] + j) * m->d.N[0] + i];
+  const int *B = m->blocks + 6 * b;
+  const int *P = m->pd + 3 * b;
+  return m->off[b] + ((int64_t)(k - B[2] + gofs(m, 2)) * P[1] + (j - B[1] + gofs(m, 1))) * P[0] +
+         (i - B[0] + gofs(m, 0));
+}
+
 /* global cell index of padded cell (i,j,k) of block b after the boundary map:
  * periodic wrap, outflow clamp.  Returns the owning block and its local padded
  * index through *src. */
