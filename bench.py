@@ -262,6 +262,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         if not args.no_grav:
             line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
+        if not args.no_remap:
+            line["remap"] = remap_bench(ctx, tde, torch, dev, args)
         if not args.no_lat:
             line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_c5:
@@ -589,6 +591,56 @@ def gravity_bench(ctx, tde, torch, dev, args, n=256):
                              "levels, two V100s; AthenaK public solver 22.4 / 49.6 ms)"}
 
 
+def remap_bench(ctx, tde, torch, dev, args, n=256, reps=5):
+    """Domain remap (Sec. 5.2) of an n^3 dual-energy state in 32^3 MeshBlocks:
+    (a) onto an n^3 grid over a domain twice as wide (the debris outgrowing its
+    box: an eighth of the target samples the whole source 2x coarser, the rest
+    is floor), (b) onto a grid twice as fine, on the half of the source's
+    domain with |z| < 1/2 (2n x 2n x n target cells).  Device
+    time per remap from CUDA events on the context's stream; algorithmic HBM
+    bytes = the source's interior state read once + the target's written."""
+    from paper_2609_37859_gb300 import workloads as wl
+    src_lay = wl.uniform_layout((n, n, n), (32, 32, 32), ((-1, 1),) * 3, bc=(0, 0, 0), ng=2)
+    W = wl.random_smooth(src_lay, seed=SEED, drho=0.5, P0=1.0, modes=4)
+    src = tde.Mesh(ctx, src_lay, tde.make_params(dual=1))
+    src.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    del W
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    cases = (("enlarge2_coarsen2", (n, n, n), ((-2, 2),) * 3, src_lay.ncells),
+             ("refine2_slab", (2 * n, 2 * n, n), ((-1, 1), (-1, 1), (-0.5, 0.5)), src_lay.ncells // 2))
+    for name, N, dom, src_cells_read in cases:
+        lay = wl.uniform_layout(N, (32, 32, 32), dom, bc=(0, 0, 0), ng=2)
+        dst = tde.Mesh(ctx, lay, tde.make_params(dual=1, rho_floor=1e-8, u_floor=1e-10))
+        dst.remap_from(src, src.U)   # warm-up
+        torch.cuda.synchronize(dev)
+        ctx.profile(True)
+        for _ in range(reps):
+            dst.remap_from(src, src.U)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms_stage = prof["scalar"][1] / reps   # staging and weight tables
+        ms_map = prof["remap"][1] / reps
+        ms = ms_stage + ms_map
+        nbytes = 6 * 8.0 * (src_cells_read + lay.ncells)
+        out[name] = {"target_cells": lay.ncells, "ms": ms, "ms_stage": ms_stage, "ms_remap_kernel": ms_map,
+                     "target_cells_per_s": lay.ncells / (ms * 1e-3),
+                     "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (ms * 1e-3) * 1e-9,
+                     "peak_gbs": hbm, "frac": nbytes / (ms * 1e-3) * 1e-9 / hbm,
+                     "finite": bool(torch.isfinite(dst.U).all().item())}
+        del dst
+        torch.cuda.empty_cache()
+    del src
+    torch.cuda.empty_cache()
+    return {"workload": "%d^3 dual-energy source, 32^3 MeshBlocks, random smooth; thermal-energy form, "
+                        "N_qd = 8" % n, "cases": out}
+
+
 # ------------------------------------------------------ production shape (C5) ---
 
 # rho_floor (rho0), p_floor (rho0 v0^2): 100x Table 1's.  With Table 1's floors
@@ -758,6 +810,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--no-c5", action="store_true", help="skip the production-shaped LAT run")
     ap.add_argument("--no-grav", action="store_true", help="skip the self-gravity multigrid")
+    ap.add_argument("--no-remap", action="store_true", help="skip the domain remap")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -356,6 +356,7 @@ enum {
   TDE_K_PROBE = 11,   /* peak-rate probe */
   TDE_K_LATGRAPH = 12, /* replayed LAT window graphs (launches counted per kernel inside) */
   TDE_K_GRAV = 13,    /* self-gravity multigrid */
+  TDE_K_REMAP = 14,   /* domain remap (the staging pass counts as scalar) */
   TDE_K_NKIND = 16
 };
 
@@ -439,6 +440,30 @@ TDE_API int tde_gravity_enable(tde_mesh *mesh, int on);
 /* The potential on the global grid, [Nz][Ny][Nx] doubles into device memory
  * phi (TDE_EINVAL before the first solve).  Asynchronous. */
 TDE_API int tde_gravity_phi(tde_mesh *mesh, double *phi);
+
+/* ---- domain remap (Sec. 5.2) ---------------------------------------------
+ * Eqs. remap-state-vector and remap-cell-average: every interior cell of dst
+ * becomes the mean of 2^(active directions of dst) midpoint samples (two per
+ * active direction, at the centres of the cell's halves), each a trilinear
+ * interpolation of src's cell-centred rho, m and thermal energy density U (src's
+ * U_aux if it evolves one, else E - |m|^2 / (2 rho)); dst's E is rebuilt as
+ * U + |m|^2 / (2 rho) (TDE_REMAP_THERMAL, the paper's form) or E itself is
+ * interpolated (TDE_REMAP_TOTAL, the form it compares against); a dual dst gets
+ * U_aux = U.  A dst cell coincident with a src cell (same width, centre within
+ * 1e-9 cells) is copied, so a remap onto the same grid is the identity.
+ * Samples outside src's domain in a non-periodic direction count as the floor
+ * state at rest (rho_floor, zero momentum, thermal energy density u_floor);
+ * lookups past src's last cells follow its boundary map (periodic wrap, outflow
+ * copy of the edge cell).
+ * Usrc: device, src's nvar * ntot layout (ghost cells not read); Udst: device,
+ * dst's layout, interior cells written (fill its ghosts with tde_ghost_fill);
+ * distinct buffers.  Both meshes on one context.  The excision reset of the new
+ * domain is the caller's (tde_excise).  TDE_EINVAL on a bad mode, NULL or shared
+ * buffers, or meshes of different contexts.  Asynchronous on the context's
+ * stream. */
+enum { TDE_REMAP_THERMAL = 0, TDE_REMAP_TOTAL = 1 };
+TDE_API int tde_mesh_remap(tde_mesh *dst, double *Udst, const tde_mesh *src, const double *Usrc, int mode,
+                           double rho_floor, double u_floor);
 
 /* The reciprocal and square-root building blocks of the hydro kernels, on n
  * device doubles: TDE_MATH_RCP out = 1/x (refined hardware seed, within one

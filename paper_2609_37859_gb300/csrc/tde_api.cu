@@ -796,6 +796,17 @@ extern "C" int tde_gravity_phi(tde_mesh *m, double *phi) {
   return TDE_OK;
 }
 
+extern "C" int tde_mesh_remap(tde_mesh *dst, double *Udst, const tde_mesh *src, const double *Usrc, int mode,
+                              double rho_floor, double u_floor) {
+  if (!dst) return TDE_EINVAL;
+  if (!src || !Udst || !Usrc || (const double *)Udst == Usrc ||
+      (mode != TDE_REMAP_THERMAL && mode != TDE_REMAP_TOTAL))
+    return fail(dst->ctx, TDE_EINVAL, "tde_mesh_remap: arguments");
+  if (src->ctx != dst->ctx) return fail(dst->ctx, TDE_EINVAL, "tde_mesh_remap: meshes of different contexts");
+  CK(dst->ctx, launch_remap(dst, Udst, src, Usrc, mode, rho_floor, u_floor));
+  return TDE_OK;
+}
+
 extern "C" int tde_counts_read(tde_mesh *m, tde_counts *out, int reset) {
   if (!m || !out) return TDE_EINVAL;
   Counters h;

@@ -183,6 +183,8 @@ cudaError_t launch_boost(tde_mesh *m, const double *V, double rho_min);
 cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, double *defect);
 cudaError_t gravity_copy_phi(tde_mesh *m, double *dst);
 void gravity_release(tde_mesh *m);
+cudaError_t launch_remap(tde_mesh *dst, double *Udst, const tde_mesh *src, const double *Usrc, int mode,
+                         double rho_floor, double u_floor);
 bool closure_ready(const tde_mesh *m);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);

@@ -20,6 +20,7 @@ RECON_PLM, RECON_PPM = 0, 1
 BC_OUTFLOW, BC_PERIODIC = 0, 1
 RIEMANN_HLLC, RIEMANN_HLLE = 0, 1
 INVERT_BISECT, INVERT_SURROGATE, INVERT_BISECT_PLAIN = 0, 1, 2
+REMAP_THERMAL, REMAP_TOTAL = 0, 1
 STATUS = {0: "TDE_OK", 1: "TDE_EINVAL", 2: "TDE_ENOMEM", 3: "TDE_ECUDA", 4: "TDE_ERANGE",
           5: "TDE_ENUMERIC", 6: "TDE_ETIMEOUT"}
 
@@ -127,6 +128,7 @@ _SIGS = {
     "tde_gravity_solve": [vp, C.POINTER(GravParams), C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "tde_gravity_enable": [vp, C.c_int],
     "tde_gravity_phi": [vp, dp],
+    "tde_mesh_remap": [vp, dp, vp, dp, C.c_int, C.c_double, C.c_double],
     "tde_mesh_set_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_mesh_get_tiles": [vp, C.POINTER(C.c_int32)],
     "tde_lat_assign": [vp, C.c_int, C.c_double, C.c_double, C.POINTER(BHState), C.POINTER(C.c_int32),
@@ -138,7 +140,7 @@ _SIGS = {
                                C.POINTER(BHState), dp, dp],
 }
 KERNEL_KINDS = ("c2p", "dt", "ghost", "sweep_x", "sweep_y", "sweep_z", "sync", "excise", "scalar",
-                "p2c", "eos", "probe", "lat_graph")
+                "p2c", "eos", "probe", "lat_graph", "grav", "remap")
 NKIND = 16
 
 _lib = None
@@ -430,6 +432,15 @@ class Mesh:
         N = self.layout.N
         out = torch.empty((N[2], N[1], N[0]), dtype=torch.float64, device=self.U.device)
         self.ctx.check(lib().tde_gravity_phi(self.h, _ptr(out)))
+        return out
+
+    def remap_from(self, src, Usrc, mode=REMAP_THERMAL, rho_floor=None, u_floor=None, out=None):
+        """Sec. 5.2 remap of src's state Usrc onto this mesh's interior cells (into
+        out, default this mesh's U); the floors default to this mesh's."""
+        out = self.U if out is None else out
+        rf = self.params.rho_floor if rho_floor is None else rho_floor
+        uf = self.params.u_floor if u_floor is None else u_floor
+        self.ctx.check(lib().tde_mesh_remap(self.h, _ptr(out), src.h, _ptr(Usrc), mode, rf, uf))
         return out
 
     def boost(self, V, rho_min):
