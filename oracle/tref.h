@@ -67,15 +67,22 @@ typedef struct {
 
 enum { TREF_HLLC = 0, TREF_HLLE = 1 };
 
-/* Mesh: a uniform-cell global grid covered by MeshBlocks (no AMR). */
+/* Mesh: a global grid covered by MeshBlocks, optionally with static refinement.
+ * A block of level L has cells of width dx / 2^L in every active direction and
+ * its indices count level-L cells (the level-L grid has N[a] 2^L cells in an
+ * active direction).  Refined meshes (some level > 0) must be 2:1 balanced
+ * across faces, edges and corners, and every block of level >= 1 must have its
+ * first index and its size multiples of 4 in the active directions (so that
+ * the children of a coarser cell, and their children, lie in one block). */
 typedef struct {
   int nb;               /* number of MeshBlocks */
-  const int *blocks;    /* nb * 6 ints: i0, j0, k0, nx, ny, nz (global cell index of the first interior cell, size) */
-  int N[3];             /* global cells per direction */
+  const int *blocks;    /* nb * 6 ints: i0, j0, k0, nx, ny, nz (first interior cell on the block's level grid, size) */
+  int N[3];             /* level-0 cells per direction */
   double xmin[3];       /* lower domain corner */
-  double dx[3];         /* cell widths */
+  double dx[3];         /* level-0 cell widths */
   int bc[3];            /* TREF_OUTFLOW or TREF_PERIODIC per direction */
   int ng;               /* ghost width (2 for PLM, 3 for PPM) */
+  const int *levels;    /* nb refinement levels, or NULL (all 0) */
 } tref_mesh_desc;
 
 /* Event counters (floors applied, table clamps, excised cells). */
@@ -121,8 +128,12 @@ int tref_nvar(const tref_mesh *m);
 int tref_num_threads(void);   /* OpenMP threads of the block loops */
 void tref_set_params(tref_mesh *m, const tref_params *p);
 
-/* a1: copy neighbour interior cells (periodic wrap or zero-gradient outflow)
- * into the ghost cells of the listed blocks (all blocks if ids == NULL). */
+/* a1: fill the ghost cells of the listed blocks (all blocks if ids == NULL) from
+ * the neighbours' interior cells after the boundary map (periodic wrap or
+ * zero-gradient outflow): a cell of the same level is copied, a region covered
+ * by finer cells is their volume average (restriction), a cell inside a coarser
+ * block is prolonged from the coarser level (the parent plus minmod-limited
+ * slopes toward its neighbours, each itself a level value). */
 void tref_ghost_fill(const tref_mesh *m, double *U, int nvar, int nact, const int *ids);
 /* a1 under LAT: mode[o] of the source block o selects the ghost value:
  * 0 copy from Udst, 1 copy from Ucur, 2 Uold + s_block[o] (Ucur - Uold). */

@@ -63,7 +63,7 @@ class Params(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("nb", C.c_int), ("blocks", C.POINTER(C.c_int)), ("N", C.c_int * 3),
                 ("xmin", C.c_double * 3), ("dx", C.c_double * 3), ("bc", C.c_int * 3),
-                ("ng", C.c_int)]
+                ("ng", C.c_int), ("levels", C.POINTER(C.c_int))]
 
 
 class Counts(C.Structure):
@@ -240,6 +240,9 @@ class Mesh:
         d.dx = (C.c_double * 3)(*layout.dx)
         d.bc = (C.c_int * 3)(*layout.bc)
         d.ng = layout.ng
+        lev = getattr(layout, "levels", None)
+        self._levels = None if lev is None else np.ascontiguousarray(lev, dtype=np.int32)
+        d.levels = self._levels.ctypes.data_as(ip) if self._levels is not None else None
         self.desc = d
         self.h = lib().tref_mesh_new(C.byref(d), C.byref(params),
                                      C.byref(table.c) if table is not None else None)

@@ -63,9 +63,41 @@ struct tref_mesh {
   int64_t ntot;
   int64_t *off;
   int *pd;      /* nb * 3 padded sizes */
-  int *owner;   /* global cell -> block */
+  int *lev;     /* refinement level per block */
+  int lmax;     /* finest level */
+  int NF[3];    /* cells per direction of the finest level's grid */
+  int *owner;   /* finest-level cell -> block */
   const double *phi_sg;   /* self-gravity potential, padded layout (caller's), or NULL */
 };
+
+/* cells per direction of the level-L grid */
+static int n_at(const tref_mesh *m, int a, int L) { return m->active[a] ? m->d.N[a] << L : 1; }
+
+/* cell width of block b along a */
+static double bdx(const tref_mesh *m, int b, int a) {
+  return m->active[a] ? ldexp(m->d.dx[a], -m->lev[b]) : m->d.dx[a];
+}
+
+/* the block owning the level-L cell g (inside the level-L grid) */
+static int owner_at(const tref_mesh *m, int L, const int *g) {
+  int f[3];
+  for (int a = 0; a < 3; ++a) f[a] = m->active[a] ? g[a] << (m->lmax - L) : 0;
+  return m->owner[((int64_t)f[2] * m->NF[1] + f[1]) * m->NF[0] + f[0]];
+}
+
+/* boundary map of a level-L index: periodic wrap, outflow clamp to the edge cell.
+ * Returns 0 if some direction was clamped. */
+static int bmap(const tref_mesh *m, int L, int *g) {
+  int in = 1;
+  for (int a = 0; a < 3; ++a) {
+    const int N = n_at(m, a, L);
+    if (g[a] < 0 || g[a] >= N) {
+      if (m->d.bc[a] == TREF_PERIODIC) g[a] = ((g[a] % N) + N) % N;
+      else { g[a] = g[a] < 0 ? 0 : N - 1; in = 0; }
+    }
+  }
+  return in;
+}
 
 /* ---------------------------------------------------------------- mesh --- */
 
@@ -93,32 +125,71 @@ tref_mesh *tref_mesh_new(const tref_mesh_desc *d, const tref_params *p, const tr
   }
   m->off[d->nb] = o;
   m->ntot = o;
-  int64_t ng = (int64_t)d->N[0] * d->N[1] * d->N[2];
+  m->lev = (int *)calloc(d->nb, sizeof(int));
+  m->lmax = 0;
+  for (int b = 0; b < d->nb; ++b) {
+    m->lev[b] = d->levels ? d->levels[b] : 0;
+    if (m->lev[b] < 0 || m->lev[b] > 8) { tref_mesh_free(m); return NULL; }
+    if (m->lev[b] > m->lmax) m->lmax = m->lev[b];
+  }
+  m->d.levels = m->lev;
+  for (int a = 0; a < 3; ++a) m->NF[a] = n_at(m, a, m->lmax);
+  int64_t ng = (int64_t)m->NF[0] * m->NF[1] * m->NF[2];
   m->owner = (int *)malloc(sizeof(int) * ng);
   for (int64_t c = 0; c < ng; ++c) m->owner[c] = -1;
   for (int b = 0; b < d->nb; ++b) {
     const int *B = m->blocks + 6 * b;
-    for (int k = 0; k < B[5]; ++k)
-      for (int j = 0; j < B[4]; ++j)
-        for (int i = 0; i < B[3]; ++i) {
-          int gi = B[0] + i, gj = B[1] + j, gk = B[2] + k;
-          if (gi < 0 || gj < 0 || gk < 0 || gi >= d->N[0] || gj >= d->N[1] || gk >= d->N[2]) {
-            tref_mesh_free(m);
-            return NULL;
-          }
-          int64_t c = ((int64_t)gk * d->N[1] + gj) * d->N[0] + gi;
+    const int L = m->lev[b];
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      if (B[a] < 0 || B[3 + a] < 1 || B[a] + B[3 + a] > n_at(m, a, L)) { tref_mesh_free(m); return NULL; }
+      if (L > 0 && m->active[a] && ((B[a] & 3) || (B[3 + a] & 3))) { tref_mesh_free(m); return NULL; }
+      const int s = m->active[a] ? m->lmax - L : 0;
+      lo[a] = B[a] << s;
+      hi[a] = (B[a] + B[3 + a]) << s;
+    }
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i) {
+          int64_t c = ((int64_t)k * m->NF[1] + j) * m->NF[0] + i;
           if (m->owner[c] != -1) { tref_mesh_free(m); return NULL; }
           m->owner[c] = b;
         }
   }
   for (int64_t c = 0; c < ng; ++c)
     if (m->owner[c] < 0) { tref_mesh_free(m); return NULL; }
+  /* 2:1 balance across faces, edges and corners */
+  if (m->lmax > 0)
+    for (int b = 0; b < d->nb; ++b) {
+      const int *B = m->blocks + 6 * b;
+      const int L = m->lev[b];
+      int lo[3], hi[3];
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = m->active[a] ? B[a] - 1 : 0;
+        hi[a] = m->active[a] ? B[a] + B[3 + a] : 0;
+      }
+      for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+          for (int i = lo[0]; i <= hi[0]; ++i) {
+            int g[3] = {i, j, k};
+            if (!bmap(m, L, g)) continue;
+            const int s = m->lmax - L;
+            for (int fk = 0; fk < (m->active[2] ? 1 << s : 1); ++fk)
+              for (int fj = 0; fj < (m->active[1] ? 1 << s : 1); ++fj)
+                for (int fi = 0; fi < (m->active[0] ? 1 << s : 1); ++fi) {
+                  int f[3] = {m->active[0] ? (g[0] << s) + fi : 0, m->active[1] ? (g[1] << s) + fj : 0,
+                              m->active[2] ? (g[2] << s) + fk : 0};
+                  int o = m->owner[((int64_t)f[2] * m->NF[1] + f[1]) * m->NF[0] + f[0]];
+                  if (abs(m->lev[o] - L) > 1) { tref_mesh_free(m); return NULL; }
+                }
+          }
+    }
   return m;
 }
 
 void tref_mesh_free(tref_mesh *m) {
   if (!m) return;
-  free(m->blocks); free(m->off); free(m->pd); free(m->owner); free(m);
+  free(m->blocks); free(m->off); free(m->pd); free(m->lev); free(m->owner); free(m);
 }
 int64_t tref_mesh_ntot(const tref_mesh *m) { return m->ntot; }
 int64_t tref_mesh_block_offset(const tref_mesh *m, int b) { return m->off[b]; }
@@ -147,30 +218,12 @@ static int64_t cidx(const tref_mesh *m, int b, int i, int j, int k) {
 const tref_mesh_desc *tref_mesh_get_desc(const tref_mesh *m) { return &m->d; }
 /* padded index (within all blocks) of the interior cell at global cell (i, j, k) */
 int64_t tref_cell_index(const tref_mesh *m, int i, int j, int k) {
-  const int b = m->owner[((int64_t)k * m->d.N[1] + j) * m->d.N[0] + i];
+  const int g0[3] = {i, j, k};
+  const int b = owner_at(m, 0, g0);
   const int *B = m->blocks + 6 * b;
   const int *P = m->pd + 3 * b;
   return m->off[b] + ((int64_t)(k - B[2] + gofs(m, 2)) * P[1] + (j - B[1] + gofs(m, 1))) * P[0] +
          (i - B[0] + gofs(m, 0));
-}
-
-/* global cell index of padded cell (i,j,k) of block b after the boundary map:
- * periodic wrap, outflow clamp.  Returns the owning block and its local padded
- * index through *src. */
-static void ghost_source(const tref_mesh *m, int b, int i, int j, int k, int *sb, int64_t *src) {
-  const int *B = m->blocks + 6 * b;
-  int g[3] = {B[0] + i - gofs(m, 0), B[1] + j - gofs(m, 1), B[2] + k - gofs(m, 2)};
-  for (int a = 0; a < 3; ++a) {
-    int N = m->d.N[a];
-    if (g[a] < 0 || g[a] >= N) {
-      if (m->d.bc[a] == TREF_PERIODIC) g[a] = ((g[a] % N) + N) % N;
-      else g[a] = g[a] < 0 ? 0 : N - 1;
-    }
-  }
-  int o = m->owner[((int64_t)g[2] * m->d.N[1] + g[1]) * m->d.N[0] + g[0]];
-  const int *O = m->blocks + 6 * o;
-  *sb = o;
-  *src = cidx(m, o, g[0] - O[0] + gofs(m, 0), g[1] - O[1] + gofs(m, 1), g[2] - O[2] + gofs(m, 2));
 }
 
 static int is_interior(const tref_mesh *m, int b, int i, int j, int k) {
@@ -179,47 +232,108 @@ static int is_interior(const tref_mesh *m, int b, int i, int j, int k) {
   return i >= gx && i < gx + B[3] && j >= gy && j < gy + B[4] && k >= gz && k < gz + B[5];
 }
 
+/* Where a ghost fill reads a source block's cells: mode == NULL, or mode[o] == 0:
+ * from Udst; 1: from Ucur; 2: Uold + s[o] (Ucur - Uold). */
+typedef struct {
+  const double *Udst, *Ucur, *Uold;
+  const int *mode;
+  const double *s;
+} src_ctx;
+
+static double fetch(const tref_mesh *m, const src_ctx *sc, int o, int64_t l, int v) {
+  const int64_t i = v * m->ntot + l;
+  if (!sc->mode || sc->mode[o] == 0) return sc->Udst[i];
+  if (sc->mode[o] == 1) return sc->Ucur[i];
+  return sc->Uold[i] + sc->s[o] * (sc->Ucur[i] - sc->Uold[i]);
+}
+
+static double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+/* The value (first nvar variables) of the level-L cell g after the boundary map:
+ * a cell of a level-L block is read; a region covered by finer blocks is the
+ * mean of its 2^d children's level values (restriction); a cell inside a
+ * coarser block is prolonged: the parent's level value plus, per active
+ * direction, a quarter of the minmod of the parent's one-sided differences to
+ * its two neighbours (level values too), toward the child's side. */
+static void level_value(const tref_mesh *m, const src_ctx *sc, int nvar, int L, const int *gin, double *out) {
+  int g[3] = {gin[0], gin[1], gin[2]};
+  bmap(m, L, g);
+  const int o = owner_at(m, L, g);
+  const int Lo = m->lev[o];
+  if (Lo == L) {
+    const int *O = m->blocks + 6 * o;
+    const int64_t l = cidx(m, o, g[0] - O[0] + gofs(m, 0), g[1] - O[1] + gofs(m, 1), g[2] - O[2] + gofs(m, 2));
+    for (int v = 0; v < nvar; ++v) out[v] = fetch(m, sc, o, l, v);
+    return;
+  }
+  if (Lo > L) {
+    double acc[6] = {0, 0, 0, 0, 0, 0}, ch[6];
+    int nch = 0;
+    for (int dk = 0; dk < (m->active[2] ? 2 : 1); ++dk)
+      for (int dj = 0; dj < (m->active[1] ? 2 : 1); ++dj)
+        for (int di = 0; di < (m->active[0] ? 2 : 1); ++di) {
+          const int c[3] = {m->active[0] ? 2 * g[0] + di : 0, m->active[1] ? 2 * g[1] + dj : 0,
+                            m->active[2] ? 2 * g[2] + dk : 0};
+          level_value(m, sc, nvar, L + 1, c, ch);
+          for (int v = 0; v < nvar; ++v) acc[v] += ch[v];
+          ++nch;
+        }
+    for (int v = 0; v < nvar; ++v) out[v] = acc[v] / nch;
+    return;
+  }
+  int p[3];
+  for (int a = 0; a < 3; ++a) p[a] = m->active[a] ? g[a] >> 1 : 0;
+  double c0[6], cp[6], cm[6];
+  level_value(m, sc, nvar, L - 1, p, c0);
+  for (int v = 0; v < nvar; ++v) out[v] = c0[v];
+  for (int a = 0; a < 3; ++a) {
+    if (!m->active[a]) continue;
+    int q[3] = {p[0], p[1], p[2]};
+    q[a] = p[a] + 1;
+    level_value(m, sc, nvar, L - 1, q, cp);
+    q[a] = p[a] - 1;
+    level_value(m, sc, nvar, L - 1, q, cm);
+    const double side = (g[a] & 1) ? 0.25 : -0.25;
+    for (int v = 0; v < nvar; ++v) out[v] += side * minmod(cp[v] - c0[v], c0[v] - cm[v]);
+  }
+}
+
+static void fill_ghosts(const tref_mesh *m, double *Udst, const src_ctx *sc, int nvar, int b) {
+  const int *B = m->blocks + 6 * b;
+  const int *P = m->pd + 3 * b;
+  double val[6];
+  for (int k = 0; k < P[2]; ++k)
+    for (int j = 0; j < P[1]; ++j)
+      for (int i = 0; i < P[0]; ++i) {
+        if (is_interior(m, b, i, j, k)) continue;
+        const int g[3] = {B[0] + i - gofs(m, 0), B[1] + j - gofs(m, 1), B[2] + k - gofs(m, 2)};
+        level_value(m, sc, nvar, m->lev[b], g, val);
+        const int64_t dst = cidx(m, b, i, j, k);
+        for (int v = 0; v < nvar; ++v) Udst[v * m->ntot + dst] = val[v];
+      }
+}
+
 void tref_ghost_fill(const tref_mesh *m, double *U, int nvar, int nact, const int *ids) {
   int n = ids ? nact : m->d.nb;
-  for (int q = 0; q < n; ++q) {
-    int b = ids ? ids[q] : q;
-    const int *P = m->pd + 3 * b;
-    for (int k = 0; k < P[2]; ++k)
-      for (int j = 0; j < P[1]; ++j)
-        for (int i = 0; i < P[0]; ++i) {
-          if (is_interior(m, b, i, j, k)) continue;
-          int sb; int64_t s;
-          ghost_source(m, b, i, j, k, &sb, &s);
-          int64_t dst = cidx(m, b, i, j, k);
-          for (int v = 0; v < nvar; ++v) U[v * m->ntot + dst] = U[v * m->ntot + s];
-        }
-  }
+  const src_ctx sc = {U, NULL, NULL, NULL, NULL};
+  for (int q = 0; q < n; ++q) fill_ghosts(m, U, &sc, nvar, ids ? ids[q] : q);
 }
 
 /* LAT ghost fill (Sec. 7.1, ghost states of neighbours on another schedule):
  * mode[o] = 0 copy from Udst (neighbour on the same schedule), 1 copy from
  * Ucur (faster neighbour, frozen at the current fine time), 2 linear
- * interpolation Uold + s (Ucur - Uold) with s = s_block[o] (slower neighbour). */
+ * interpolation Uold + s (Ucur - Uold) with s = s_block[o] (slower neighbour).
+ * At coarse-fine interfaces every cell entering a restriction or a prolongation
+ * is first taken at the stage time this way (Sec. 7.1: the histories are
+ * restricted, interpolated in time, then prolonged; restriction and the linear
+ * time interpolation commute). */
 void tref_ghost_fill_modes(const tref_mesh *m, double *Udst, const double *Ucur, const double *Uold,
                            const int *mode, const double *s_block, int nact, const int *ids) {
-  for (int q = 0; q < nact; ++q) {
-    int b = ids[q];
-    const int *P = m->pd + 3 * b;
-    for (int k = 0; k < P[2]; ++k)
-      for (int j = 0; j < P[1]; ++j)
-        for (int i = 0; i < P[0]; ++i) {
-          if (is_interior(m, b, i, j, k)) continue;
-          int sb; int64_t s;
-          ghost_source(m, b, i, j, k, &sb, &s);
-          int64_t dst = cidx(m, b, i, j, k);
-          for (int v = 0; v < m->nvar; ++v) {
-            int64_t ds = v * m->ntot + dst, ss = v * m->ntot + s;
-            if (mode[sb] == 0) Udst[ds] = Udst[ss];
-            else if (mode[sb] == 1) Udst[ds] = Ucur[ss];
-            else Udst[ds] = Uold[ss] + s_block[sb] * (Ucur[ss] - Uold[ss]);
-          }
-        }
-  }
+  const src_ctx sc = {Udst, Ucur, Uold, mode, s_block};
+  for (int q = 0; q < nact; ++q) fill_ghosts(m, Udst, &sc, m->nvar, ids[q]);
 }
 
 /* -------------------------------------------------------------- physics --- */
@@ -241,9 +355,9 @@ static void cell_pos(const tref_mesh *m, int b, int i, int j, int k, double *x) 
   const int *B = m->blocks + 6 * b;
   int g[3] = {B[0] + i - gofs(m, 0), B[1] + j - gofs(m, 1), B[2] + k - gofs(m, 2)};
   for (int a = 0; a < 3; ++a) {
-    int N = m->d.N[a];
+    int N = n_at(m, a, m->lev[b]);
     if (m->d.bc[a] == TREF_PERIODIC) g[a] = ((g[a] % N) + N) % N;
-    x[a] = m->d.xmin[a] + (g[a] + 0.5) * m->d.dx[a];
+    x[a] = m->d.xmin[a] + (g[a] + 0.5) * bdx(m, b, a);
   }
 }
 
@@ -461,6 +575,7 @@ static void stage_block(const tref_mesh *m, int stage, int b, const double *U0, 
   const double tst = stage == 0 ? t0 : t0 + dt;
   const int g[3] = {gofs(m, 0), gofs(m, 1), gofs(m, 2)};
   const int64_t st[3] = {1, P[0], (int64_t)P[0] * P[1]};
+  const double dxb[3] = {bdx(m, b, 0), bdx(m, b, 1), bdx(m, b, 2)};   /* the block level's widths */
 
   /* a2 + a3 on every padded cell */
   double *W = (double *)malloc(sizeof(double) * 8 * npc);
@@ -539,12 +654,12 @@ static void stage_block(const tref_mesh *m, int stage, int b, const double *U0, 
           int64_t flo = ((int64_t)ci[2] * nf[a][1] + ci[1]) * nf[a][0] + ci[0];
           ci[a] += 1;
           int64_t fhi = ((int64_t)ci[2] * nf[a][1] + ci[1]) * nf[a][0] + ci[0];
-          for (int q = 0; q < nvar; ++q) L[q] -= (F[a][q * nfa + fhi] - F[a][q * nfa + flo]) / m->d.dx[a];
-          divv += (F[a][6 * nfa + fhi] - F[a][6 * nfa + flo]) / m->d.dx[a];
+          for (int q = 0; q < nvar; ++q) L[q] -= (F[a][q * nfa + fhi] - F[a][q * nfa + flo]) / dxb[a];
+          divv += (F[a][6 * nfa + fhi] - F[a][6 * nfa + flo]) / dxb[a];
           if (p->bh_on || m->phi_sg) {
             double ph = phi[l + st[a]], p0 = phi[l], pl = phi[l - st[a]];
-            L[1 + a] -= W[l] * (ph - pl) / (2.0 * m->d.dx[a]);
-            L[4] -= (F[a][fhi] * (ph - p0) + F[a][flo] * (p0 - pl)) / (2.0 * m->d.dx[a]);
+            L[1 + a] -= W[l] * (ph - pl) / (2.0 * dxb[a]);
+            L[4] -= (F[a][fhi] * (ph - p0) + F[a][flo] * (p0 - pl)) / (2.0 * dxb[a]);
           }
         }
         if (p->frame_on) {
@@ -699,12 +814,12 @@ void tref_dual_sync(const tref_mesh *m, double *U, int nact, const int *ids, tre
 void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *t_b, double *dt_b,
                  tref_counts *c) {
   const tref_params *p = &m->p;
-  double dxmin = HUGE_VAL;
-  for (int a = 0; a < 3; ++a)
-    if (m->active[a] && m->d.dx[a] < dxmin) dxmin = m->d.dx[a];
 #pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < m->d.nb; ++b) {
     const int *B = m->blocks + 6 * b;
+    double dxmin = HUGE_VAL;
+    for (int a = 0; a < 3; ++a)
+      if (m->active[a] && bdx(m, b, a) < dxmin) dxmin = bdx(m, b, a);
     double best = HUGE_VAL;
     tref_counts lc;
     memset(&lc, 0, sizeof lc);
@@ -723,7 +838,7 @@ void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *
           double cs = sqrt(w[6] * w[4] / w[0]);
           for (int a = 0; a < 3; ++a) {
             if (!m->active[a]) continue;
-            double s = m->d.dx[a] / (fabs(w[1 + a]) + cs);
+            double s = bdx(m, b, a) / (fabs(w[1 + a]) + cs);
             if (s < best) best = s;
           }
           if (p->bh_on) {
@@ -749,6 +864,15 @@ void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *
 
 void tref_step(const tref_mesh *m, double *U, double *Uscr, double dt, double t, tref_counts *c) {
   int nb = m->d.nb;
+  if (m->lmax > 0) {
+    /* refined mesh: the coarse-fine flux correction needs the flux registers;
+     * one LAT window with every factor 1 is exactly the synchronised step */
+    int32_t *ones = (int32_t *)malloc(sizeof(int32_t) * nb);
+    for (int b = 0; b < nb; ++b) ones[b] = 1;
+    tref_lat_window(m, U, ones, dt, t, c, NULL);
+    free(ones);
+    return;
+  }
   double *dtb = (double *)malloc(sizeof(double) * nb);
   double *tb = (double *)malloc(sizeof(double) * nb);
   double *te = (double *)malloc(sizeof(double) * nb);
@@ -806,10 +930,15 @@ typedef struct {
   double dx[3];
   const tref_params *p;
   int64_t ntot;
+  const int *lev;
+  int lmax, NF[3];
 } tref_mesh_view;
 
 void tref_mesh_get_view(const tref_mesh *m, tref_mesh_view *v) {
   v->nb = m->d.nb;
+  v->lev = m->lev;
+  v->lmax = m->lmax;
+  for (int a = 0; a < 3; ++a) v->NF[a] = m->NF[a];
   for (int a = 0; a < 3; ++a) {
     v->N[a] = m->d.N[a];
     v->bc[a] = m->d.bc[a];
@@ -840,6 +969,8 @@ void tref_frame_acceleration(const tref_mesh *m, const double *U, double t, doub
   for (int b = 0; b < m->d.nb; ++b) {
     const int *B = m->blocks + 6 * b;
     const int *P = m->pd + 3 * b;
+    /* a level-L cell holds 2^-(L d) level-0 cell volumes (d active directions) */
+    const double vw = ldexp(1.0, -m->lev[b] * (m->active[0] + m->active[1] + m->active[2]));
     for (int k = 0; k < B[5]; ++k)
       for (int j = 0; j < B[4]; ++j)
         for (int i = 0; i < B[3]; ++i) {
@@ -852,8 +983,9 @@ void tref_frame_acceleration(const tref_mesh *m, const double *U, double t, doub
           const double d[3] = {x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]};
           const double q2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + p->r_soft * p->r_soft;
           const double gfac = -p->GM / (q2 * sqrt(q2));   /* g = -grad Phi_bh = -GM d / q^3 */
-          for (int a = 0; a < 3; ++a) s[a] += rho * gfac * d[a];
-          s0 += rho;
+          const double rw = rho * vw;   /* mass in level-0 cell volumes */
+          for (int a = 0; a < 3; ++a) s[a] += rw * gfac * d[a];
+          s0 += rw;
         }
   }
   (void)nt;

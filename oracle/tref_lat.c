@@ -41,15 +41,44 @@ typedef struct {
   double dx[3];
   const tref_params *p;
   int64_t ntot;
+  const int *lev;
+  int lmax, NF[3];
 } tref_mesh_view;
 void tref_mesh_get_view(const tref_mesh *m, tref_mesh_view *v);
 void tref_cell_pos(const tref_mesh *m, int b, int i, int j, int k, double *x);
 
 static int gofs(const tref_mesh_view *v, int a) { return v->active[a] ? v->ng : 0; }
 
-/* block adjacency: every block whose interior supplies a ghost cell of b */
+static int n_at(const tref_mesh_view *v, int a, int L) { return v->active[a] ? v->N[a] << L : 1; }
+
+static double bdx(const tref_mesh_view *v, int b, int a) {
+  return v->active[a] ? ldexp(v->dx[a], -v->lev[b]) : v->dx[a];
+}
+
+/* owner of the finest-level cell f */
+static int owner_f(const tref_mesh_view *v, const int *f) {
+  return v->owner[((int64_t)f[2] * v->NF[1] + f[1]) * v->NF[0] + f[0]];
+}
+
+/* boundary map of a level-L index (periodic wrap, outflow clamp); 0 if clamped */
+static int bmap(const tref_mesh_view *v, int L, int *g) {
+  int in = 1;
+  for (int a = 0; a < 3; ++a) {
+    const int N = n_at(v, a, L);
+    if (g[a] < 0 || g[a] >= N) {
+      if (v->bc[a] == TREF_PERIODIC) g[a] = ((g[a] % N) + N) % N;
+      else { g[a] = g[a] < 0 ? 0 : N - 1; in = 0; }
+    }
+  }
+  return in;
+}
+
+/* block adjacency: every block sharing a face, edge or corner with b (the
+ * blocks covering its one-cell shell, on every level; across an outflow
+ * boundary the shell maps onto the edge cells) */
 static void neighbours(const tref_mesh_view *v, int b, int *nbr, int *nn) {
   const int *B = v->blocks + 6 * b;
+  const int L = v->lev[b], sft = v->lmax - L;
   *nn = 0;
   int lo[3], hi[3];
   for (int a = 0; a < 3; ++a) {
@@ -60,21 +89,19 @@ static void neighbours(const tref_mesh_view *v, int b, int *nbr, int *nn) {
     for (int j = lo[1]; j <= hi[1]; ++j)
       for (int i = lo[0]; i <= hi[0]; ++i) {
         int g[3] = {B[0] + i, B[1] + j, B[2] + k};
-        int inside = 1;
-        for (int a = 0; a < 3; ++a) {
-          if (g[a] < 0 || g[a] >= v->N[a]) {
-            inside = 0;
-            if (v->bc[a] == TREF_PERIODIC) g[a] = ((g[a] % v->N[a]) + v->N[a]) % v->N[a];
-            else g[a] = g[a] < 0 ? 0 : v->N[a] - 1;
-          }
-        }
-        (void)inside;
-        int o = v->owner[((int64_t)g[2] * v->N[1] + g[1]) * v->N[0] + g[0]];
-        if (o == b) continue;
-        int seen = 0;
-        for (int q = 0; q < *nn; ++q)
-          if (nbr[q] == o) seen = 1;
-        if (!seen) nbr[(*nn)++] = o;
+        bmap(v, L, g);
+        for (int fk = 0; fk < (v->active[2] ? 1 << sft : 1); ++fk)
+          for (int fj = 0; fj < (v->active[1] ? 1 << sft : 1); ++fj)
+            for (int fi = 0; fi < (v->active[0] ? 1 << sft : 1); ++fi) {
+              const int f[3] = {v->active[0] ? (g[0] << sft) + fi : 0, v->active[1] ? (g[1] << sft) + fj : 0,
+                                v->active[2] ? (g[2] << sft) + fk : 0};
+              const int o = owner_f(v, f);
+              if (o == b) continue;
+              int seen = 0;
+              for (int q = 0; q < *nn; ++q)
+                if (nbr[q] == o) seen = 1;
+              if (!seen) nbr[(*nn)++] = o;
+            }
       }
 }
 
@@ -107,16 +134,21 @@ int tref_lat_factors(const tref_mesh *m, const double *dt_b, int n_lat, double m
     for (int b = 0; b < nb; ++b)
       if (f_b[b] == fmax) f_b[b] = fmax / 2;
   }
-  /* neighbour limiting: f_b <= 2 min over face/edge/corner neighbours */
-  int *nbr = (int *)malloc(sizeof(int) * 27 * 64);
+  /* neighbour limiting, by lowering factors until it holds: f_b <= 2 f_o over
+   * face/edge/corner neighbours o, and f_fine <= f_coarse across coarse-fine
+   * interfaces (with the first rule, f_fine <= f_coarse <= 2 f_fine) */
+  int *nbr = (int *)malloc(sizeof(int) * nb);
   int changed = 1;
   while (changed) {
     changed = 0;
     for (int b = 0; b < nb; ++b) {
       int nn;
       neighbours(&v, b, nbr, &nn);
-      for (int q = 0; q < nn; ++q)
-        if (f_b[b] > 2 * f_b[nbr[q]]) { f_b[b] = 2 * f_b[nbr[q]]; changed = 1; }
+      for (int q = 0; q < nn; ++q) {
+        const int o = nbr[q];
+        if (f_b[b] > 2 * f_b[o]) { f_b[b] = 2 * f_b[o]; changed = 1; }
+        if (v.lev[b] > v.lev[o] && f_b[b] > f_b[o]) { f_b[b] = f_b[o]; changed = 1; }
+      }
     }
   }
   free(nbr);
@@ -150,69 +182,117 @@ static int64_t side_index(const tref_mesh_view *v, int b, int side, int c1, int 
   return o + q * ncell + (int64_t)c2 * B[3 + t1] + c1;
 }
 
-/* refluxing of the listed completing blocks at time t (see the file comment) */
+/* Eq. lat-grav-reflux: the gravitational work of a mass-impulse mismatch dIrho
+ * (local minus accepted) through the face between padded cell pos of block b and
+ * its neighbour across side (a, sigma), with Phi at time t */
+static double grav_reflux(const tref_mesh *m, const tref_mesh_view *v, int b, const int *pos, int a, int side,
+                          double dIrho, double t) {
+  const tref_params *p = v->p;
+  const double *psg = tref_phi_sg(m);
+  if (!p->bh_on && !psg) return 0.0;
+  const int *P = v->pd + 3 * b;
+  double xi[3], xn[3];
+  tref_cell_pos(m, b, pos[0], pos[1], pos[2], xi);
+  int pn[3] = {pos[0], pos[1], pos[2]};
+  pn[a] += side ? 1 : -1;
+  tref_cell_pos(m, b, pn[0], pn[1], pn[2], xn);
+  double phi_i = p->bh_on ? tref_phi_bh(p, xi, t) : 0.0;
+  double phi_n = p->bh_on ? tref_phi_bh(p, xn, t) : 0.0;
+  if (psg) {   /* the frozen self-gravity potential */
+    phi_i += psg[v->off[b] + ((int64_t)pos[2] * P[1] + pos[1]) * P[0] + pos[0]];
+    phi_n += psg[v->off[b] + ((int64_t)pn[2] * P[1] + pn[1]) * P[0] + pn[0]];
+  }
+  const double sigma = side ? 1.0 : -1.0;
+  return sigma / (2.0 * bdx(v, b, a)) * dIrho * (phi_n - phi_i);
+}
+
+/* Refluxing of the listed completing blocks at time t (see the file comment).
+ * Across a coarse-fine face the fine side's impulses are the accepted ones: a
+ * completing coarse block replaces its own impulse on each face cell by the mean
+ * of the 2^(d-1) fine impulses behind it (their area-weighted flux), and a fine
+ * block keeps its impulses for the coarse side (f_fine <= f_coarse, so the
+ * coarse block completes at a phase where every fine neighbour completes too). */
 static void reflux(const tref_mesh *m, const tref_mesh_view *v, double *U, double *R,
                    const int64_t *fo, const int32_t *f_b, int ncomp, const int *comp, double t) {
-  const tref_params *p = v->p;
   for (int qb = 0; qb < ncomp; ++qb) {
     int b = comp[qb];
     const int *B = v->blocks + 6 * b;
     const int *P = v->pd + 3 * b;
+    const int L = v->lev[b];
     for (int a = 0; a < 3; ++a) {
       if (!v->active[a]) continue;
       int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+      const double dxa = bdx(v, b, a);
       for (int side = 0; side < 2; ++side) {
         int s = 2 * a + side;
         double sigma = side ? 1.0 : -1.0;   /* outward orientation of the face */
+        int os = 2 * a + (1 - side);
         for (int c2 = 0; c2 < B[3 + t2]; ++c2)
           for (int c1 = 0; c1 < B[3 + t1]; ++c1) {
             int ci[3];
             ci[a] = side ? B[3 + a] - 1 : 0;
             ci[t1] = c1;
             ci[t2] = c2;
-            /* neighbour cell across the face */
+            /* level-L cell across the face */
             int g[3] = {B[0] + ci[0], B[1] + ci[1], B[2] + ci[2]};
             g[a] += side ? 1 : -1;
-            if (g[a] < 0 || g[a] >= v->N[a]) {
+            const int N = n_at(v, a, L);
+            if (g[a] < 0 || g[a] >= N) {
               if (v->bc[a] != TREF_PERIODIC) continue;
-              g[a] = ((g[a] % v->N[a]) + v->N[a]) % v->N[a];
+              g[a] = ((g[a] % N) + N) % N;
             }
-            int o = v->owner[((int64_t)g[2] * v->N[1] + g[1]) * v->N[0] + g[0]];
-            const int *O = v->blocks + 6 * o;
-            int oc[3] = {g[0] - O[0], g[1] - O[1], g[2] - O[2]};
-            int os = 2 * a + (1 - side);
-            if (f_b[o] < f_b[b]) {
-              int64_t l = v->off[b] + ((int64_t)(ci[2] + gofs(v, 2)) * P[1] + (ci[1] + gofs(v, 1))) * P[0] +
-                          (ci[0] + gofs(v, 0));
-              double dI[6];
-              for (int q = 0; q < v->nvar; ++q) {
-                double Io = R[fo[o] + side_index(v, o, os, oc[t1], oc[t2], q)];
-                double Is = R[fo[b] + side_index(v, b, s, c1, c2, q)];
-                dI[q] = Io - Is;   /* accepted minus local impulse */
-              }
-              const double *psg = tref_phi_sg(m);
-              if (p->bh_on || psg) {
-                double xi[3], xn[3];
-                int pos[3] = {ci[0] + gofs(v, 0), ci[1] + gofs(v, 1), ci[2] + gofs(v, 2)};
-                tref_cell_pos(m, b, pos[0], pos[1], pos[2], xi);
-                int pn[3] = {pos[0], pos[1], pos[2]};
-                pn[a] += side ? 1 : -1;
-                tref_cell_pos(m, b, pn[0], pn[1], pn[2], xn);
-                double phi_i = p->bh_on ? tref_phi_bh(p, xi, t) : 0.0;
-                double phi_n = p->bh_on ? tref_phi_bh(p, xn, t) : 0.0;
-                if (psg) {   /* the frozen self-gravity potential */
-                  phi_i += psg[l];
-                  phi_n += psg[v->off[b] + ((int64_t)pn[2] * P[1] + pn[1]) * P[0] + pn[0]];
+            const int sft = v->lmax - L;
+            const int f[3] = {v->active[0] ? g[0] << sft : 0, v->active[1] ? g[1] << sft : 0,
+                              v->active[2] ? g[2] << sft : 0};
+            const int o = owner_f(v, f);
+            const int pos[3] = {ci[0] + gofs(v, 0), ci[1] + gofs(v, 1), ci[2] + gofs(v, 2)};
+            const int64_t l = v->off[b] + ((int64_t)pos[2] * P[1] + pos[1]) * P[0] + pos[0];
+            double dI[6];
+            if (v->lev[o] == L) {
+              const int *O = v->blocks + 6 * o;
+              int oc[3] = {g[0] - O[0], g[1] - O[1], g[2] - O[2]};
+              if (f_b[o] < f_b[b]) {
+                for (int q = 0; q < v->nvar; ++q) {
+                  double Io = R[fo[o] + side_index(v, o, os, oc[t1], oc[t2], q)];
+                  double Is = R[fo[b] + side_index(v, b, s, c1, c2, q)];
+                  dI[q] = Io - Is;   /* accepted minus local impulse */
                 }
-                /* Eq. lat-grav-reflux with dI_rho = local - accepted = -dI[0] */
-                U[4 * v->ntot + l] += sigma / (2.0 * v->dx[a]) * (-dI[0]) * (phi_n - phi_i);
+                U[4 * v->ntot + l] += grav_reflux(m, v, b, pos, a, side, -dI[0], t);
+                for (int q = 0; q < v->nvar; ++q) U[q * v->ntot + l] += -sigma * dI[q] / dxa;
+                for (int q = 0; q < v->nvar; ++q)
+                  R[fo[o] + side_index(v, o, os, oc[t1], oc[t2], q)] = 0.0;
               }
-              for (int q = 0; q < v->nvar; ++q) U[q * v->ntot + l] += -sigma * dI[q] / v->dx[a];
-              for (int q = 0; q < v->nvar; ++q)
-                R[fo[o] + side_index(v, o, os, oc[t1], oc[t2], q)] = 0.0;
-            }
-            if (f_b[o] <= f_b[b])
+              if (f_b[o] <= f_b[b])
+                for (int q = 0; q < v->nvar; ++q) R[fo[b] + side_index(v, b, s, c1, c2, q)] = 0.0;
+            } else if (v->lev[o] == L + 1) {
+              /* the fine face cells behind this coarse face cell, on level L + 1 */
+              double acc[6] = {0, 0, 0, 0, 0, 0};
+              int nf = 0;
+              for (int e2 = 0; e2 < (v->active[t2] ? 2 : 1); ++e2)
+                for (int e1 = 0; e1 < (v->active[t1] ? 2 : 1); ++e1) {
+                  int h[3];
+                  h[a] = side ? 2 * g[a] : 2 * g[a] + 1;
+                  h[t1] = v->active[t1] ? 2 * g[t1] + e1 : 0;
+                  h[t2] = v->active[t2] ? 2 * g[t2] + e2 : 0;
+                  const int sf = v->lmax - L - 1;
+                  const int ff[3] = {v->active[0] ? h[0] << sf : 0, v->active[1] ? h[1] << sf : 0,
+                                     v->active[2] ? h[2] << sf : 0};
+                  const int o2 = owner_f(v, ff);
+                  const int *O = v->blocks + 6 * o2;
+                  const int lc1 = h[t1] - O[t1], lc2 = h[t2] - O[t2];
+                  for (int q = 0; q < v->nvar; ++q) {
+                    int64_t r = fo[o2] + side_index(v, o2, os, lc1, lc2, q);
+                    acc[q] += R[r];
+                    R[r] = 0.0;
+                  }
+                  ++nf;
+                }
+              for (int q = 0; q < v->nvar; ++q) dI[q] = acc[q] / nf - R[fo[b] + side_index(v, b, s, c1, c2, q)];
+              U[4 * v->ntot + l] += grav_reflux(m, v, b, pos, a, side, -dI[0], t);
+              for (int q = 0; q < v->nvar; ++q) U[q * v->ntot + l] += -sigma * dI[q] / dxa;
               for (int q = 0; q < v->nvar; ++q) R[fo[b] + side_index(v, b, s, c1, c2, q)] = 0.0;
+            }
+            /* a coarser neighbour (level L - 1) reads this block's impulses */
           }
       }
     }

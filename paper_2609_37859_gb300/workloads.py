@@ -28,11 +28,16 @@ class MeshLayout:
     dx: tuple
     bc: tuple                   # OUTFLOW / PERIODIC per direction
     ng: int
+    levels: np.ndarray = None   # [nb] refinement level per block (None: all 0)
     off: np.ndarray = field(init=False)
     pd: np.ndarray = field(init=False)
 
     def __post_init__(self):
         self.blocks = np.ascontiguousarray(self.blocks, dtype=np.int32).reshape(-1, 6)
+        if self.levels is not None:
+            self.levels = np.ascontiguousarray(self.levels, dtype=np.int32).reshape(-1)
+            if not self.levels.any():
+                self.levels = None
         act = np.array([n > 1 for n in self.N])
         self.active = act
         self.pd = self.blocks[:, 3:6] + 2 * self.ng * act[None, :]
@@ -81,6 +86,36 @@ class MeshLayout:
             U[:, flat] = G[:, gk, gj, gi]
         return U
 
+    def level(self, b):
+        return 0 if self.levels is None else int(self.levels[b])
+
+    def block_dx(self, b):
+        L = self.level(b)
+        return tuple(self.dx[a] / (1 << L) if self.active[a] else self.dx[a] for a in range(3))
+
+    def interior_flat(self):
+        """Flat padded indices of every interior cell, block by block."""
+        return np.concatenate([self.interior_index(b)[0].ravel() for b in range(self.nb)])
+
+    def interior_centres(self):
+        """x, y, z and cell volume of every interior cell, in interior_flat() order."""
+        xs, ys, zs, vs = [], [], [], []
+        for b in range(self.nb):
+            _, (gk, gj, gi) = self.interior_index(b)
+            d = self.block_dx(b)
+            xs.append((self.xmin[0] + (gi.ravel() + 0.5) * d[0]))
+            ys.append((self.xmin[1] + (gj.ravel() + 0.5) * d[1]))
+            zs.append((self.xmin[2] + (gk.ravel() + 0.5) * d[2]))
+            vs.append(np.full(gi.size, d[0] * d[1] * d[2]))
+        return np.concatenate(xs), np.concatenate(ys), np.concatenate(zs), np.concatenate(vs)
+
+    def state_from_cells(self, F):
+        """[nvar, n_interior] values in interior_flat() order -> [nvar, ntot] state."""
+        F = np.asarray(F)
+        U = np.zeros((F.shape[0], self.ntot), dtype=F.dtype)
+        U[:, self.interior_flat()] = F
+        return U
+
     def cell_centres(self):
         """x, y, z of the global interior grid, each [Nz, Ny, Nx]."""
         ax = [self.xmin[a] + (np.arange(self.N[a]) + 0.5) * self.dx[a] for a in range(3)]
@@ -123,6 +158,98 @@ def mixed_layout(root_N, root_block, split, domain, bc, ng):
                     blocks.append((i0, j0, k0, root_block, root_block, root_block))
     dx = tuple((domain[a][1] - domain[a][0]) / root_N[a] for a in range(3))
     return MeshLayout(np.array(blocks), tuple(root_N), tuple(d[0] for d in domain), dx, tuple(bc), ng)
+
+
+def smr_layout(root_N, block, domain, bc, ng, refine, max_level):
+    """Statically refined mesh: root blocks of `block` cells (a multiple of 4 per
+    active direction) on the level-0 grid of root_N cells; a block of level L < max_level
+    whose region meets refine(lo, hi, L) (lo, hi: its corners) is split into 2^d
+    children of the same cell count on level L + 1; then blocks are split until the
+    mesh is 2:1 balanced across faces, edges and corners (periodic images included)."""
+    act = [n > 1 for n in root_N]
+    dx0 = tuple((domain[a][1] - domain[a][0]) / root_N[a] for a in range(3))
+    bs = [block[a] if act[a] else 1 for a in range(3)]
+    blocks = []
+    for k0 in range(0, root_N[2], bs[2]):
+        for j0 in range(0, root_N[1], bs[1]):
+            for i0 in range(0, root_N[0], bs[0]):
+                blocks.append((0, i0, j0, k0))
+
+    def corners(blk):
+        L, i0, j0, k0 = blk
+        lo, hi = [], []
+        for a, o in enumerate((i0, j0, k0)):
+            d = dx0[a] / (1 << L) if act[a] else dx0[a]
+            lo.append(domain[a][0] + o * d)
+            hi.append(domain[a][0] + (o + bs[a]) * d)
+        return lo, hi
+
+    def children(blk):
+        L, i0, j0, k0 = blk
+        out = []
+        for dk in (range(2) if act[2] else (0,)):
+            for dj in (range(2) if act[1] else (0,)):
+                for di in (range(2) if act[0] else (0,)):
+                    o = [2 * i0 + di * bs[0], 2 * j0 + dj * bs[1], 2 * k0 + dk * bs[2]]
+                    out.append((L + 1, *[o[a] if act[a] else 0 for a in range(3)]))
+        return out
+
+    for L in range(max_level):
+        nxt = []
+        for blk in blocks:
+            if blk[0] == L and refine(*corners(blk), L):
+                nxt.extend(children(blk))
+            else:
+                nxt.append(blk)
+        blocks = nxt
+    # 2:1 balance on the finest lattice
+    while True:
+        lmax = max(b[0] for b in blocks)
+        NF = [root_N[a] << lmax if act[a] else 1 for a in range(3)]
+        own = np.full(NF[::-1], -1, dtype=np.int64)
+        for q, (L, i0, j0, k0) in enumerate(blocks):
+            s = lmax - L
+            sl = []
+            for a, o in zip((2, 1, 0), (k0, j0, i0)):
+                if act[a]:
+                    sl.append(slice(o << s, (o + bs[a]) << s))
+                else:
+                    sl.append(slice(0, 1))
+            own[tuple(sl)] = q
+        lev = np.array([b[0] for b in blocks])
+        split = set()
+        for q, (L, i0, j0, k0) in enumerate(blocks):
+            s = lmax - L
+            idx = []
+            for a, o in zip((2, 1, 0), (k0, j0, i0)):
+                if not act[a]:
+                    idx.append(np.array([0]))
+                    continue
+                r = np.arange((o - 1) << s, (o + bs[a] + 1) << s)
+                if bc[a] == PERIODIC:
+                    r = r % NF[a]
+                else:
+                    r = np.clip(r, 0, NF[a] - 1)
+                idx.append(r)
+            nb_lev = lev[own[np.ix_(*idx)]]
+            if nb_lev.max() > L + 1:
+                split.add(q)
+        if not split:
+            break
+        nxt = []
+        for q, blk in enumerate(blocks):
+            nxt.extend(children(blk) if q in split else [blk])
+        blocks = nxt
+    arr = np.array([(i0, j0, k0, bs[0], bs[1], bs[2]) for (L, i0, j0, k0) in blocks], dtype=np.int32)
+    lev = np.array([b[0] for b in blocks], dtype=np.int32)
+    return MeshLayout(arr, tuple(root_N), tuple(d[0] for d in domain), dx0, tuple(bc), ng, lev)
+
+
+def prim_cells(layout, rho, vx, vy, vz, P):
+    """Pack per-cell primitive values (interior_flat() order) into the padded layout."""
+    F = np.stack([np.broadcast_to(np.asarray(f, dtype=np.float64), (layout.interior_flat().size,))
+                  for f in (rho, vx, vy, vz, P)])
+    return layout.state_from_cells(F)
 
 
 def prim_state(layout, rho, vx, vy, vz, P):
