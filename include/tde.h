@@ -96,16 +96,20 @@ typedef struct {
   double afr[3];        /* frame acceleration A_fr, held over the step */
 } tde_bh_state;
 
-/* One MeshBlock: global index of its first interior cell and its size. */
+/* One MeshBlock: index of its first interior cell on its level's grid, its
+ * size, and its refinement level (static refinement, Sec. 7.1: a level-L block
+ * has cells of width dx / 2^L in every active direction and counts cells on the
+ * level-L grid of N[a] 2^L cells). */
 typedef struct {
   int i0, j0, k0, nx, ny, nz;
+  int level;            /* 0 = the grid's own cells */
 } tde_block_desc;
 
-/* Uniform-cell global grid covered by the MeshBlocks (no refinement). */
+/* The level-0 global grid covered by the MeshBlocks. */
 typedef struct {
-  int N[3];             /* global cells per direction (1 = inactive direction) */
+  int N[3];             /* level-0 cells per direction (1 = inactive direction) */
   double xmin[3];       /* lower domain corner */
-  double dx[3];         /* cell widths */
+  double dx[3];         /* level-0 cell widths */
   int bc[3];            /* TDE_BC_OUTFLOW / TDE_BC_PERIODIC per direction */
   int ng;               /* ghost width */
 } tde_grid_desc;
@@ -205,10 +209,14 @@ TDE_API int tde_eos_eval_rhoT(tde_eos *eos, int64_t n, const double *rho, const 
 /* ---- mesh (MeshBlocks with ghost zones: Sec. 2, Sec. 3.2) ---------------- */
 
 /* Build a mesh of nblocks MeshBlocks (host array) covering `grid` exactly once,
- * with the ghost map (periodic wrap / zero-gradient outflow copy).  eos may be
- * NULL for TDE_EOS_IDEAL.  TDE_EINVAL for overlaps, gaps, ng below the
- * reconstruction's stencil (PLM 2, PPM 3), more than 2^31 padded cells or a
- * block edge above 64 cells. */
+ * with the ghost map (periodic wrap / zero-gradient outflow; see tde_ghost_fill
+ * for refined meshes).  eos may be NULL for TDE_EOS_IDEAL.  TDE_EINVAL for
+ * overlaps, gaps, ng below the reconstruction's stencil (PLM 2, PPM 3), more
+ * than 2^31 padded cells, a block edge above 32 cells, and on refined meshes
+ * (some level > 0): levels above 8, blocks of level >= 1 whose first index or
+ * size is not a multiple of 4 in an active direction, neighbours (face, edge or
+ * corner, periodic images included) more than one level apart, or a ghost
+ * stencil reaching a cell two levels coarser. */
 TDE_API int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *blocks,
                     const tde_grid_desc *grid, const tde_params *params, tde_eos *eos,
                     tde_mesh **out);
@@ -228,7 +236,13 @@ TDE_API int tde_mesh_bind_state(tde_mesh *mesh, double *U, double *U1);
  * EOS finds T from (rho, P) by bisection of the interpolated pressure. */
 TDE_API int tde_prim_to_cons(tde_mesh *mesh, const double *W, double *U);
 
-/* Fill the ghost cells of the first nvar fields of a state (a1). */
+/* Fill the ghost cells of the first nvar fields of a state (a1) from the
+ * neighbours' interior cells after the boundary map: a cell of the same level
+ * is copied; a region covered by finer cells is their volume average
+ * (restriction, conserved variables); a cell inside a coarser block is
+ * prolonged: the parent plus, per active direction, a quarter of the minmod of
+ * the parent's one-sided differences to its neighbours (each a copied or
+ * restricted coarse value), signed toward the child's half. */
 TDE_API int tde_ghost_fill(tde_mesh *mesh, double *state, int nvar);
 
 /* One stage of the SSP-RK2 update (a1-a6 of the hydro stage) on nblk blocks:
@@ -244,6 +258,8 @@ TDE_API int tde_ghost_fill(tde_mesh *mesh, double *state, int nvar);
  * and step start time, as LAT needs).  bh: host struct, may be NULL (no gravity). */
 TDE_API int tde_hydro_stage(tde_mesh *mesh, int stage, int nblk, const int32_t *block_ids,
                     const double *dt_block, const double *t_block, const tde_bh_state *bh);
+/* (On a refined mesh a single stage cannot apply the coarse-fine flux
+ * correction, which spans both stages: TDE_EINVAL; use tde_step or LAT windows.) */
 
 /* Per-block CFL step (a7, Sec. 7.1 "local CFL limit from hydrodynamic and source
  * terms"): dt_b = cfl * min over interior cells outside the excision sphere of
@@ -271,7 +287,9 @@ TDE_API int tde_mesh_get_time(tde_mesh *mesh, double *t);   /* synchronises the 
 /* One synchronised SSP-RK2 step of every block from the mesh time t: dt from the
  * CFL condition if cfl > 0 (else dt_fixed), stage 0, stage 1, excision (at
  * t + dt), resync if dual energy is on; then t += dt.  The step's dt is also
- * written to dt_out (device double, may be NULL). */
+ * written to dt_out (device double, may be NULL).  On a refined mesh the step
+ * is a LAT window with every factor 1 (the coarse-fine flux correction of
+ * Eq. lat-flux-impulse at its end), and it leaves those factors assigned. */
 TDE_API int tde_step(tde_mesh *mesh, double cfl, double dt_fixed, const tde_bh_state *bh, double *dt_out);
 
 /* ---- localized adaptive time stepping (Sec. 7 of the paper) -------------- */
@@ -327,7 +345,7 @@ typedef struct {
  * and/or dt_min (device, 1).  The paper has no counterpart: this is a library
  * service.  It calls no cudaMalloc, cudaFree or other allocating routine; its
  * scratch (block list copy, offsets, per-block minima) is one fixed device
- * array of about 164 KB that every GPU loading the library holds until exit.
+ * array of about 176 KB that every GPU loading the library holds until exit.
  * Limit: 1 <= nblocks <= 4096, else TDE_EINVAL.  The first call on a device
  * looks up that array's device address, so it should come before any stream
  * capture.  All calls share the array: calls whose GPU work overlaps race.

@@ -350,9 +350,19 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
     if (act[a] && grid->dx[a] < p.dxmin) p.dxmin = grid->dx[a];
   }
 
-  // block geometry, offsets, coverage
+  // block geometry, offsets, levels
   m->hblocks.resize(nblocks);
   m->hoff.resize(nblocks + 1);
+  int lmax = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    if (blocks[b].level < 0 || blocks[b].level > 8) {
+      delete m;
+      return fail(ctx, TDE_EINVAL, "tde_mesh_create: refinement level outside 0..8");
+    }
+    lmax = std::max(lmax, blocks[b].level);
+  }
+  m->lmax = lmax;
+  auto n_at = [&](int a, int L) { return act[a] ? grid->N[a] << L : 1; };
   int unit[3] = {0, 0, 0};
   int64_t off = 0;
   for (int b = 0; b < nblocks; ++b) {
@@ -360,17 +370,23 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
     const int o[3] = {d.i0, d.j0, d.k0}, n[3] = {d.nx, d.ny, d.nz};
     DevBlock &B = m->hblocks[b];
     B.i0 = d.i0; B.j0 = d.j0; B.k0 = d.k0;
+    B.level = d.level;
     int64_t cells = 1, inter = 1;
     for (int a = 0; a < 3; ++a) {
-      if (n[a] < 1 || o[a] < 0 || o[a] + n[a] > grid->N[a] || n[a] > 32 || (!act[a] && n[a] != 1)) {
+      if (n[a] < 1 || o[a] < 0 || o[a] + n[a] > n_at(a, d.level) || n[a] > 32 || (!act[a] && n[a] != 1)) {
         delete m;
         return fail(ctx, TDE_EINVAL, "tde_mesh_create: block outside the grid or edge above 32 cells");
+      }
+      if (d.level > 0 && act[a] && ((o[a] & 3) || (n[a] & 3))) {
+        delete m;
+        return fail(ctx, TDE_EINVAL, "tde_mesh_create: refined block not aligned to 4 cells");
       }
       B.n[a] = n[a];
       B.p[a] = n[a] + 2 * p.g[a];
       cells *= B.p[a];
       inter *= n[a];
-      unit[a] = gcd_int(gcd_int(unit[a], o[a]), n[a]);
+      const int sh = act[a] ? lmax - d.level : 0;   // on the finest level's grid
+      unit[a] = gcd_int(gcd_int(unit[a], o[a] << sh), n[a] << sh);
       m->nmax[a] = std::max(m->nmax[a], n[a]);
     }
     B.off = off;
@@ -383,21 +399,30 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   if (off >= (int64_t)INT32_MAX) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: more than 2^31 padded cells"); }
   if (sweep_smem_max(m) > 227 * 1024) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: block too large for one sweep tile"); }
 
-  // owner map on the coarsest unit lattice that every block edge lies on
-  int cn[3];
+  // owner map of the finest level's grid, one entry per cube of unit cells that
+  // every block edge lies on
+  int cn[3], NF[3];
   for (int a = 0; a < 3; ++a) {
-    unit[a] = gcd_int(unit[a], grid->N[a]);
+    NF[a] = n_at(a, lmax);
+    unit[a] = gcd_int(unit[a], NF[a]);
     if (unit[a] <= 0) unit[a] = 1;
-    cn[a] = grid->N[a] / unit[a];
+    cn[a] = NF[a] / unit[a];
   }
   const int64_t ncoarse = (int64_t)cn[0] * cn[1] * cn[2];
   std::vector<int32_t> owner(ncoarse, -1);
   int64_t covered = 0;
   for (int b = 0; b < nblocks; ++b) {
     const tde_block_desc &d = blocks[b];
-    for (int k = d.k0 / unit[2]; k < (d.k0 + d.nz) / unit[2]; ++k)
-      for (int j = d.j0 / unit[1]; j < (d.j0 + d.ny) / unit[1]; ++j)
-        for (int i = d.i0 / unit[0]; i < (d.i0 + d.nx) / unit[0]; ++i) {
+    int lo[3], hi[3];
+    const int o[3] = {d.i0, d.j0, d.k0}, n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+      const int sh = act[a] ? lmax - d.level : 0;
+      lo[a] = (o[a] << sh) / unit[a];
+      hi[a] = ((o[a] + n[a]) << sh) / unit[a];
+    }
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i) {
           int32_t &w = owner[((int64_t)k * cn[1] + j) * cn[0] + i];
           if (w != -1) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: overlapping blocks"); }
           w = b;
@@ -406,17 +431,104 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   }
   if (covered != ncoarse) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: blocks do not cover the grid"); }
 
-  // ghost map: every non-interior padded cell <- interior cell of the owner of
-  // its periodic image (periodic) or of the nearest boundary cell (outflow)
-  std::vector<int32_t> gmap, gsrcb;
-  std::vector<int32_t> gstart(nblocks + 1, 0);
+  // level-L index helpers: boundary map (periodic wrap, outflow clamp), owner
+  auto bmap = [&](int L, int *g) {
+    for (int a = 0; a < 3; ++a) {
+      const int N = n_at(a, L);
+      if (g[a] < 0 || g[a] >= N) {
+        if (grid->bc[a] == TDE_BC_PERIODIC) g[a] = ((g[a] % N) + N) % N;
+        else g[a] = g[a] < 0 ? 0 : N - 1;
+      }
+    }
+  };
+  auto owner_f = [&](const int *f) {
+    return owner[((int64_t)(f[2] / unit[2]) * cn[1] + f[1] / unit[1]) * cn[0] + f[0] / unit[0]];
+  };
+  auto owner_at = [&](int L, const int *g) {
+    int f[3];
+    for (int a = 0; a < 3; ++a) f[a] = act[a] ? g[a] << (lmax - L) : 0;
+    return owner_f(f);
+  };
+  auto padded = [&](int o, const int *c) {   // padded index of level cell c in block o
+    const DevBlock &O = m->hblocks[o];
+    return O.off + ((int64_t)(c[2] - O.k0 + p.g[2]) * O.p[1] + (c[1] - O.j0 + p.g[1])) * O.p[0] +
+           (c[0] - O.i0 + p.g[0]);
+  };
+  // a coarse value of the level-L cell g: one cell of a level-L block, or the
+  // mean of its children (one or two levels finer, inside one block)
+  auto coarse_value = [&](int L, const int *gin, AmrCV &cv) {
+    int g[3] = {gin[0], gin[1], gin[2]};
+    bmap(L, g);
+    const int o = owner_at(L, g);
+    const int d = m->hblocks[o].level - L;
+    if (d < 0 || d > 2) return false;
+    int c[3], last[3];
+    for (int a = 0; a < 3; ++a) {
+      c[a] = act[a] ? g[a] << d : 0;
+      last[a] = act[a] ? c[a] + (1 << d) - 1 : 0;
+    }
+    if (owner_at(L + d, last) != o) return false;
+    cv.base = (int32_t)padded(o, c);
+    cv.blk = o;
+    cv.depth = d;
+    return true;
+  };
+
+  // 2:1 balance (faces, edges, corners, periodic images) and the neighbour
+  // lists of the factor limiting: every block covering a cell of the one-cell
+  // shell, on the finest grid
   m->h_nbr_start.assign(nblocks + 1, 0);
   m->h_nbr.clear();
   for (int b = 0; b < nblocks; ++b) {
     const DevBlock &B = m->hblocks[b];
     const int o[3] = {B.i0, B.j0, B.k0};
-    int cnt = 0;
+    const int L = B.level;
     std::vector<int32_t> nbrs;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = act[a] ? -1 : 0;
+      hi[a] = act[a] ? B.n[a] : 0;
+    }
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const int c[3] = {i, j, k};
+          bool shell = false;
+          for (int a = 0; a < 3; ++a)
+            if (act[a] && (c[a] < 0 || c[a] >= B.n[a])) shell = true;
+          if (!shell) continue;
+          int g[3] = {o[0] + i, o[1] + j, o[2] + k};
+          bmap(L, g);
+          const int sh = lmax - L;
+          for (int fk = 0; fk < (act[2] ? 1 << sh : 1); ++fk)
+            for (int fj = 0; fj < (act[1] ? 1 << sh : 1); ++fj)
+              for (int fi = 0; fi < (act[0] ? 1 << sh : 1); ++fi) {
+                const int f[3] = {act[0] ? (g[0] << sh) + fi : 0, act[1] ? (g[1] << sh) + fj : 0,
+                                  act[2] ? (g[2] << sh) + fk : 0};
+                const int ob = owner_f(f);
+                if (std::abs(m->hblocks[ob].level - L) > 1) {
+                  delete m;
+                  return fail(ctx, TDE_EINVAL, "tde_mesh_create: neighbours more than one level apart");
+                }
+                if (ob != b && std::find(nbrs.begin(), nbrs.end(), ob) == nbrs.end()) nbrs.push_back(ob);
+              }
+        }
+    m->h_nbr.insert(m->h_nbr.end(), nbrs.begin(), nbrs.end());
+    m->h_nbr_start[b + 1] = (int32_t)m->h_nbr.size();
+  }
+
+  // ghost map: a ghost cell whose mapped cell lies in a block of its own level
+  // is a copy (gmap, source block gsrcb); on a refined mesh the others are
+  // restriction or prolongation ops
+  std::vector<int32_t> gmap, gsrcb;
+  std::vector<int32_t> gstart(nblocks + 1, 0);
+  std::vector<AmrOp> amr;
+  std::vector<int32_t> amr_start(nblocks + 1, 0);
+  for (int b = 0; b < nblocks; ++b) {
+    const DevBlock &B = m->hblocks[b];
+    const int o[3] = {B.i0, B.j0, B.k0};
+    const int L = B.level;
+    int cnt = 0, namr = 0;
     for (int k = 0; k < B.p[2]; ++k)
       for (int j = 0; j < B.p[1]; ++j)
         for (int i = 0; i < B.p[0]; ++i) {
@@ -426,34 +538,52 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
             if (c[a] < p.g[a] || c[a] >= p.g[a] + B.n[a]) inside = false;
           if (inside) continue;
           int gg[3];
-          for (int a = 0; a < 3; ++a) {
-            int v = o[a] + c[a] - p.g[a];
-            const int N = grid->N[a];
-            if (v < 0 || v >= N) {
-              if (grid->bc[a] == TDE_BC_PERIODIC) v = ((v % N) + N) % N;
-              else v = v < 0 ? 0 : N - 1;
-            }
-            gg[a] = v;
+          for (int a = 0; a < 3; ++a) gg[a] = o[a] + c[a] - p.g[a];
+          bmap(L, gg);
+          const int ob = owner_at(L, gg);
+          const int64_t dst = B.off + ((int64_t)k * B.p[1] + j) * B.p[0] + i;
+          const int Lo = m->hblocks[ob].level;
+          if (Lo == L) {
+            gmap.push_back((int32_t)dst);
+            gmap.push_back((int32_t)padded(ob, gg));
+            gsrcb.push_back(ob);
+            ++cnt;
+            continue;
           }
-          const int ob = owner[((int64_t)(gg[2] / unit[2]) * cn[1] + gg[1] / unit[1]) * cn[0] + gg[0] / unit[0]];
-          const DevBlock &O = m->hblocks[ob];
-          const int oo[3] = {O.i0, O.j0, O.k0};
-          int64_t src = O.off + ((int64_t)(gg[2] - oo[2] + p.g[2]) * O.p[1] + (gg[1] - oo[1] + p.g[1])) * O.p[0] +
-                        (gg[0] - oo[0] + p.g[0]);
-          int64_t dst = B.off + ((int64_t)k * B.p[1] + j) * B.p[0] + i;
-          gmap.push_back((int32_t)dst);
-          gmap.push_back((int32_t)src);
-          gsrcb.push_back(ob);
-          bool shell = true;   // neighbours = owners of the first ghost layer (face, edge, corner)
-          for (int a = 0; a < 3; ++a)
-            if (c[a] < p.g[a] - 1 || c[a] > p.g[a] + B.n[a]) shell = false;
-          if (shell && ob != b && std::find(nbrs.begin(), nbrs.end(), ob) == nbrs.end()) nbrs.push_back(ob);
-          ++cnt;
+          AmrOp op{};
+          op.dst = (int32_t)dst;
+          bool ok = true;
+          if (Lo > L) {
+            op.kind = -1;
+            ok = coarse_value(L, gg, op.cv[0]);
+          } else {
+            int par[3];
+            op.kind = 0;
+            for (int a = 0; a < 3; ++a) {
+              par[a] = act[a] ? gg[a] >> 1 : 0;
+              if (act[a] && (gg[a] & 1)) op.kind |= 1 << a;
+            }
+            ok = Lo == L - 1 && coarse_value(L - 1, par, op.cv[0]);
+            for (int a = 0; ok && a < 3; ++a) {
+              if (!act[a]) continue;
+              int q[3] = {par[0], par[1], par[2]};
+              q[a] = par[a] + 1;
+              ok = coarse_value(L - 1, q, op.cv[1 + 2 * a]);
+              q[a] = par[a] - 1;
+              if (ok) ok = coarse_value(L - 1, q, op.cv[2 + 2 * a]);
+            }
+          }
+          if (!ok) {
+            delete m;
+            return fail(ctx, TDE_EINVAL, "tde_mesh_create: a ghost stencil reaches two levels coarser or finer");
+          }
+          amr.push_back(op);
+          ++namr;
         }
     gstart[b + 1] = gstart[b] + cnt;
-    m->h_nbr.insert(m->h_nbr.end(), nbrs.begin(), nbrs.end());
-    m->h_nbr_start[b + 1] = (int32_t)m->h_nbr.size();
+    amr_start[b + 1] = amr_start[b] + namr;
     m->max_ghosts = std::max(m->max_ghosts, cnt);
+    m->max_amr = std::max(m->max_amr, namr);
   }
 
   // device allocations
@@ -479,6 +609,10 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   A((void **)&m->d_nbr, sizeof(int32_t) * m->h_nbr.size());
   A((void **)&m->d_owner, sizeof(int32_t) * owner.size());
   A((void **)&m->d_tstart, sizeof(double) * nblocks);
+  if (!amr.empty()) {
+    A((void **)&m->d_amr, sizeof(AmrOp) * amr.size());
+    A((void **)&m->d_amr_start, sizeof(int32_t) * (nblocks + 1));
+  }
   if (err != cudaSuccess) {
     tde_mesh_destroy(m);
     return cuda_fail(ctx, err, "tde_mesh_create: cudaMalloc");
@@ -500,6 +634,10 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   if (!m->h_nbr.empty()) cudaMemcpy(m->d_nbr, m->h_nbr.data(), sizeof(int32_t) * m->h_nbr.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_owner, owner.data(), sizeof(int32_t) * owner.size(), cudaMemcpyHostToDevice);
   cudaMemset(m->d_tstart, 0, sizeof(double) * nblocks);
+  if (!amr.empty()) {
+    cudaMemcpy(m->d_amr, amr.data(), sizeof(AmrOp) * amr.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(m->d_amr_start, amr_start.data(), sizeof(int32_t) * (nblocks + 1), cudaMemcpyHostToDevice);
+  }
   for (int a = 0; a < 3; ++a) {
     m->unit[a] = unit[a];
     m->cn[a] = cn[a];
@@ -537,6 +675,8 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_nbr);
   cudaFree(m->d_owner);
   cudaFree(m->d_tstart);
+  cudaFree(m->d_amr);
+  cudaFree(m->d_amr_start);
   cudaFree(m->sb.rho);
   cudaFree(m->sb.lTg);
   cudaFree(m->sb.queue);
@@ -605,6 +745,7 @@ extern "C" int tde_prim_to_cons(tde_mesh *m, const double *W, double *U) {
 extern "C" int tde_ghost_fill(tde_mesh *m, double *state, int nvar) {
   if (!m || !state || nvar < 1 || nvar > 8) return TDE_EINVAL;
   CK(m->ctx, launch_ghost(m, state, nvar, m->nb, m->d_allids));
+  CK(m->ctx, launch_ghost_amr(m, state, nullptr, nullptr, nvar, m->nb, m->d_allids, nullptr, 0, 0, 0));
   return TDE_OK;
 }
 
@@ -652,6 +793,7 @@ extern "C" int tde_hydro_stage(tde_mesh *m, int stage, int nblk, const int32_t *
   if (!m->U || !m->U1) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: no bound state");
   if (!closure_ready(m)) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: surrogate closure without a trained network");
   if ((stage != 0 && stage != 1) || !dt_block) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: arguments");
+  if (m->lmax > 0) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: refined mesh (use tde_step or LAT windows)");
   if (!ids) { ids = m->d_allids; nblk = m->nb; }
   if (nblk <= 0 || nblk > m->nb) return fail(m->ctx, TDE_EINVAL, "tde_hydro_stage: block count");
   TimeArgs ta{dt_block, 1, t_block, 1};
@@ -700,7 +842,14 @@ extern "C" int tde_step(tde_mesh *m, double cfl, double dt_fixed, const tde_bh_s
     CK(c, launch_dt_finalize(m, cfl, m->d_dtb, nullptr));
   } else {
     CK(c, launch_set_dt(m, dt_fixed));
-    CK(c, launch_c2p(m, m->U, m->nb, m->d_allids, false, bh, ta));
+    if (m->lmax == 0) CK(c, launch_c2p(m, m->U, m->nb, m->d_allids, false, bh, ta));
+  }
+  if (m->lmax > 0) {
+    // refined mesh: one LAT window with every factor 1 (dt0 = this step's dt)
+    int r = lat_step_all_ones(m, bh);
+    if (r) return r;
+    if (dt_out) CK(c, cudaMemcpyAsync(dt_out, m->d_scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return TDE_OK;
   }
   int r = run_stage(m, 0, m->nb, m->d_allids, bh, ta, true);
   if (r) return r;
@@ -776,6 +925,7 @@ extern "C" int tde_gravity_solve(tde_mesh *m, const tde_grav_params *gp, int *cy
   for (int a = 0; a < 3; ++a)
     if (m->phys.N[a] > 1 && (m->phys.bc[a] != TDE_BC_PERIODIC || !pow2(m->phys.N[a])))
       return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: needs periodic power-of-two directions");
+  if (m->lmax > 0) return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: refined mesh");
   CK(m->ctx, gravity_solve(m, *gp, cycles, defect));
   invalidate_graph(m);
   return TDE_OK;
@@ -803,6 +953,7 @@ extern "C" int tde_mesh_remap(tde_mesh *dst, double *Udst, const tde_mesh *src, 
       (mode != TDE_REMAP_THERMAL && mode != TDE_REMAP_TOTAL))
     return fail(dst->ctx, TDE_EINVAL, "tde_mesh_remap: arguments");
   if (src->ctx != dst->ctx) return fail(dst->ctx, TDE_EINVAL, "tde_mesh_remap: meshes of different contexts");
+  if (src->lmax > 0 || dst->lmax > 0) return fail(dst->ctx, TDE_EINVAL, "tde_mesh_remap: refined mesh");
   CK(dst->ctx, launch_remap(dst, Udst, src, Usrc, mode, rho_floor, u_floor));
   return TDE_OK;
 }

@@ -173,11 +173,31 @@ struct BH {
   double afr[3];
 };
 
-// padded geometry of one MeshBlock
+// padded geometry of one MeshBlock; origin (i0, j0, k0) on its level's grid
 struct DevBlock {
-  int i0, j0, k0, n[3], p[3], pad;
+  int i0, j0, k0, n[3], p[3], level;
   long long off;
 };
+
+// 2^e for |e| < 1000, exact (built from the exponent field)
+__host__ __device__ __forceinline__ double exp2i(int e) {
+  unsigned long long b = (unsigned long long)(1023 + e) << 52;
+  double r;
+  memcpy(&r, &b, 8);
+  return r;
+}
+
+// cell width, its reciprocal and the grid size along a on block B's level
+// (refinement halves the cells of the active directions only)
+__device__ __forceinline__ double block_dx(const Phys &p, const DevBlock &B, int a) {
+  return p.active[a] ? p.dx[a] * exp2i(-B.level) : p.dx[a];
+}
+__device__ __forceinline__ double block_idx(const Phys &p, const DevBlock &B, int a) {
+  return p.active[a] ? p.idx[a] * exp2i(B.level) : p.idx[a];
+}
+__device__ __forceinline__ int level_n(const Phys &p, int a, int L) {
+  return p.active[a] ? p.N[a] << L : 1;
+}
 
 __device__ __forceinline__ void count(unsigned long long *c) {
   if (c) atomicAdd(c, 1ull);

@@ -88,12 +88,12 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         double rate = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          if (p.active[a]) rate = dmax(rate, (fabs(w[1 + a]) + cs) * p.idx[a]);
+          if (p.active[a]) rate = dmax(rate, (fabs(w[1 + a]) + cs) * block_idx(p, B, a));
         best = dmin(best, rcp_nr(rate));
         if (bh.on) {
           double s2 = r2 + bh.rs2;
           double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-          if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin / gmag));
+          if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin * exp2i(-B.level) / gmag));
         }
       }
     }
@@ -366,6 +366,8 @@ __global__ void __launch_bounds__(NT) k_frame_partial(Phys p, BH bh, const doubl
   const int nint = B.n[0] * B.n[1] * B.n[2];
   double rb[3];
   bh_pos(bh, *tnow, rb);
+  // a level-L cell holds 2^-(L d) level-0 cell volumes (d active directions)
+  const double vw = exp2i(-B.level * (p.active[0] + p.active[1] + p.active[2]));
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int e = blockIdx.x * NT + threadIdx.x; e < nint; e += gridDim.x * NT) {
     const int i = e % B.n[0], r = e / B.n[0];
@@ -379,10 +381,11 @@ __global__ void __launch_bounds__(NT) k_frame_partial(Phys p, BH bh, const doubl
     if (bh.excise && sqrt(r2) < bh.rexc) continue;
     const double q2 = r2 + bh.rs2;
     const double gfac = -bh.GM / (q2 * sqrt(q2));   // g = -grad Phi_bh = -GM d / q^3
-    s[0] += rho * gfac * d0;
-    s[1] += rho * gfac * d1;
-    s[2] += rho * gfac * d2;
-    s[3] += rho;
+    const double rw = rho * vw;   // mass in level-0 cell volumes
+    s[0] += rw * gfac * d0;
+    s[1] += rw * gfac * d1;
+    s[2] += rw * gfac * d2;
+    s[3] += rw;
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -716,6 +719,8 @@ cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, 
 
 cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2) {
   cudaError_t err = launch_ghost(m, U + 4 * m->ntot, 1, nblk, ids);
+  if (err != cudaSuccess) return err;
+  err = launch_ghost_amr(m, U + 4 * m->ntot, nullptr, nullptr, 1, nblk, ids, nullptr, 0, 0, 0);
   if (err != cudaSuccess) return err;
   dim3 grid((unsigned)((m->max_interior + NT - 1) / NT), (unsigned)nblk);
   ProfScope _ps(m->ctx, TDE_K_SYNC);

@@ -79,6 +79,20 @@ struct tde_eos {
 namespace tde {
 // The cells a pass covers: the interior (padded = 0) or all padded cells
 // (padded = 1) of the blocks ids[0 .. nblk); blocks == null means plain arrays.
+// Refined-mesh ghost cells (tde_ghost_fill): a coarse value is the mean of
+// (2^depth)^d cells of block blk starting at padded index base (depth 0: one
+// cell); a ghost op writes, at padded index dst, either one coarse value
+// (kind < 0: restriction) or a prolongation: cv[0] the parent, cv[1 + 2a] and
+// cv[2 + 2a] its neighbours at +a and -a (active directions), bit a of kind set
+// when the ghost cell is the parent's upper half along a.
+struct AmrCV {
+  int32_t base, blk, depth;
+};
+struct AmrOp {
+  int32_t dst, kind;
+  AmrCV cv[7];
+};
+
 struct CellMap {
   const DevBlock *blocks;
   const int32_t *ids;
@@ -132,7 +146,11 @@ struct tde_mesh {
   int32_t *d_nbr_start = nullptr, *d_nbr = nullptr;
   int32_t *d_gsrcb = nullptr;          // source block of each ghost entry
   int unit[3] = {1, 1, 1}, cn[3] = {1, 1, 1};
-  int32_t *d_owner = nullptr;          // owner block per unit-lattice cell
+  int32_t *d_owner = nullptr;          // owner block per unit cube of the finest level's grid
+  int lmax = 0;                        // finest refinement level
+  tde::AmrOp *d_amr = nullptr;         // refined-mesh ghost ops, grouped by block
+  int32_t *d_amr_start = nullptr;      // [nb + 1]
+  int max_amr = 0;                     // most ops of one block
   // localized adaptive time stepping
   bool lat_ready = false;
   int lat_fmax = 1;
@@ -183,6 +201,14 @@ cudaError_t launch_boost(tde_mesh *m, const double *V, double rho_min);
 cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, double *defect);
 cudaError_t gravity_copy_phi(tde_mesh *m, double *dst);
 void gravity_release(tde_mesh *m);
+// one window of every block with factor 1 and dt0 = the device scalar dt
+// (the synchronised step of a refined mesh); advances the mesh time
+int lat_step_all_ones(tde_mesh *m, const BH &bh);
+// refined-mesh ghost ops of the listed blocks into Udst (nvar fields); f == NULL:
+// every source from Udst, else the LAT modes of k_ghost_lat (level flevel, fine
+// sub-step tau, stage)
+cudaError_t launch_ghost_amr(tde_mesh *m, double *Udst, const double *Ucur, const double *Uold, int nvar,
+                             int nblk, const int32_t *ids, const int32_t *f, int flevel, int tau, int stage);
 cudaError_t launch_remap(tde_mesh *dst, double *Udst, const tde_mesh *src, const double *Usrc, int mode,
                          double rho_floor, double u_floor);
 bool closure_ready(const tde_mesh *m);

@@ -3,7 +3,8 @@
 //  * k_lat_factors: one CTA computes dt0 = min_b dt_b (Eq. lat-base-dt), the
 //    power-of-two factors of Eq. lat-factor (exact floor(log2) via ilogb),
 //    merges sparse top bins and limits neighbouring factors to a ratio of two
-//    by Jacobi passes (the greatest fixed point, the same as any pass order);
+//    and, across coarse-fine interfaces, f_fine <= f_coarse by Jacobi passes
+//    (the greatest fixed point, the same as any pass order);
 //    the pass count is bounded and an overrun is reported in a status word.
 //  * A window of f_max * dt0 advances, at each fine sub-step tau, every level
 //    f with tau mod f = 0 as ONE batched launch sequence over that level's block
@@ -42,7 +43,8 @@ constexpr int LNT = 256;
 __global__ void __launch_bounds__(1024) k_lat_factors(int nb, const double *__restrict__ dt, int n_lat,
                                                       double merge_frac,
                                                       const int32_t *__restrict__ nbr_start,
-                                                      const int32_t *__restrict__ nbr, int32_t *f,
+                                                      const int32_t *__restrict__ nbr,
+                                                      const DevBlock *__restrict__ blocks, int32_t *f,
                                                       int32_t *f2, double *scal, int *flag) {
   __shared__ double sd[32];
   __shared__ int si[32], sc[32];
@@ -106,7 +108,12 @@ __global__ void __launch_bounds__(1024) k_lat_factors(int nb, const double *__re
     __syncthreads();
     for (int b = tid; b < nb; b += blockDim.x) {
       int v = f[b], lim = v;
-      for (int q = nbr_start[b]; q < nbr_start[b + 1]; ++q) lim = min(lim, 2 * f[nbr[q]]);
+      const int Lb = blocks[b].level;
+      // f_b <= 2 f_o; across a coarse-fine interface also f_fine <= f_coarse
+      for (int q = nbr_start[b]; q < nbr_start[b + 1]; ++q) {
+        const int o = nbr[q];
+        lim = min(lim, (Lb > blocks[o].level ? 1 : 2) * f[o]);
+      }
       f2[b] = lim;
       if (lim < v) s_changed = 1;
     }
@@ -181,16 +188,94 @@ __global__ void __launch_bounds__(LNT) k_ghost_lat(const int32_t *__restrict__ m
   }
 }
 
+// ---- refined-mesh ghost ops (restriction, prolongation; Sec. 7.1) ----------
+
+struct AmrSrc {
+  const double *Udst, *Ucur, *Uold;
+  const int32_t *f;   // NULL: every source cell from Udst
+  int flevel, tau, stage;
+  long long ntot;
+};
+
+// the value of padded cell l (variable offset included) of block o at the stage
+// time: same level -> Udst, faster -> Ucur, slower -> interpolation in time
+__device__ __forceinline__ double amr_fetch(const AmrSrc &S, int o, long long l) {
+  if (!S.f) return S.Udst[l];
+  const int fn = S.f[o];
+  if (fn == S.flevel) return S.Udst[l];
+  if (fn < S.flevel) return S.Ucur[l];
+  const double sv = (double)(S.tau % fn + S.stage * S.flevel) / (double)fn;
+  const double a = S.Uold[l];
+  return a + sv * (S.Ucur[l] - a);
+}
+
+// mean of the (2^depth)^d cells of a coarse value (depth <= 2), the children
+// summed in (z, y, x) order and each level averaged in turn
+__device__ double amr_cv(const AmrSrc &S, const Phys &p, const DevBlock *__restrict__ blocks, const AmrCV &cv,
+                         long long voff) {
+  if (cv.depth == 0) return amr_fetch(S, cv.blk, voff + cv.base);
+  const DevBlock O = blocks[cv.blk];
+  const long long sx = p.active[0] ? 1 : 0, sy = p.active[1] ? O.p[0] : 0,
+                  sz = p.active[2] ? (long long)O.p[0] * O.p[1] : 0;
+  const int nx = p.active[0] ? 2 : 1, ny = p.active[1] ? 2 : 1, nz = p.active[2] ? 2 : 1;
+  const int nch = nx * ny * nz;
+  double acc = 0.0;
+  for (int dk = 0; dk < nz; ++dk)
+    for (int dj = 0; dj < ny; ++dj)
+      for (int di = 0; di < nx; ++di) {
+        if (cv.depth == 1) {
+          acc += amr_fetch(S, cv.blk, voff + cv.base + dk * sz + dj * sy + di * sx);
+        } else {
+          const long long c0 = cv.base + 2 * (dk * sz + dj * sy + di * sx);
+          double in = 0.0;
+          for (int ek = 0; ek < nz; ++ek)
+            for (int ej = 0; ej < ny; ++ej)
+              for (int ei = 0; ei < nx; ++ei) in += amr_fetch(S, cv.blk, voff + c0 + ek * sz + ej * sy + ei * sx);
+          acc += in / nch;
+        }
+      }
+  return acc / nch;
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+__global__ void __launch_bounds__(LNT) k_ghost_amr(const AmrOp *__restrict__ ops, const int32_t *__restrict__ start,
+                                                   const int32_t *__restrict__ ids, const DevBlock *__restrict__ blocks,
+                                                   Phys p, AmrSrc S, double *Udst, int nvar) {
+  const int b = ids[blockIdx.y];
+  const int s0 = start[b], s1 = start[b + 1];
+  for (int e = s0 + blockIdx.x * LNT + threadIdx.x; e < s1; e += gridDim.x * LNT) {
+    const AmrOp op = ops[e];
+    for (int v = 0; v < nvar; ++v) {
+      const long long voff = v * S.ntot;
+      const double c0 = amr_cv(S, p, blocks, op.cv[0], voff);
+      double out = c0;
+      if (op.kind >= 0)
+        for (int a = 0; a < 3; ++a) {
+          if (!p.active[a]) continue;
+          const double cp = amr_cv(S, p, blocks, op.cv[1 + 2 * a], voff);
+          const double cm = amr_cv(S, p, blocks, op.cv[2 + 2 * a], voff);
+          out += ((op.kind >> a) & 1 ? 0.25 : -0.25) * minmod(cp - c0, c0 - cm);
+        }
+      Udst[voff + op.dst] = out;
+    }
+  }
+}
+
 __device__ __forceinline__ void lat_cell_centre(const Phys &p, const DevBlock &B, const int c[3],
                                                 double x[3]) {
   const int o[3] = {B.i0, B.j0, B.k0};
   for (int a = 0; a < 3; ++a) {
     int g = o[a] + c[a] - p.g[a];
     if (p.bc[a] == 1) {
-      g %= p.N[a];
-      if (g < 0) g += p.N[a];
+      const int N = level_n(p, a, B.level);
+      g %= N;
+      if (g < 0) g += N;
     }
-    x[a] = p.xmin[a] + (g + 0.5) * p.dx[a];
+    x[a] = p.xmin[a] + (g + 0.5) * block_dx(p, B, a);
   }
 }
 
@@ -204,10 +289,20 @@ __device__ __forceinline__ long long side_offset(const DevBlock &B, int side, in
   return so;
 }
 
+// owner block of every cell of the finest level's grid, stored per unit cube
 struct OwnerLattice {
   const int32_t *owner;
   int unit[3], cn[3];
+  int lmax;
 };
+
+// the block owning the level-L cell g (inside the level-L grid)
+__device__ __forceinline__ int owner_at(const OwnerLattice &ol, const Phys &p, int L, const int g[3]) {
+  int f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) f[a] = p.active[a] ? (g[a] << (ol.lmax - L)) / ol.unit[a] : 0;
+  return ol.owner[((long long)f[2] * ol.cn[1] + f[1]) * ol.cn[0] + f[0]];
+}
 
 __global__ void __launch_bounds__(LNT) k_reflux(Phys p, BH bh, OwnerLattice ol,
                                                 const DevBlock *__restrict__ blocks,
@@ -242,24 +337,60 @@ __global__ void __launch_bounds__(LNT) k_reflux(Phys p, BH bh, OwnerLattice ol,
         ci[t2] = c2;
         int g[3] = {org[0] + ci[0], org[1] + ci[1], org[2] + ci[2]};
         g[a] += side ? 1 : -1;
-        if (g[a] < 0 || g[a] >= p.N[a]) {
+        const int NL = level_n(p, a, B.level);
+        if (g[a] < 0 || g[a] >= NL) {
           if (p.bc[a] != 1) continue;
-          g[a] = ((g[a] % p.N[a]) + p.N[a]) % p.N[a];
+          g[a] = ((g[a] % NL) + NL) % NL;
         }
-        const int o = ol.owner[((long long)(g[2] / ol.unit[2]) * ol.cn[1] + g[1] / ol.unit[1]) * ol.cn[0] +
-                               g[0] / ol.unit[0]];
+        const int o = owner_at(ol, p, B.level, g);
         const DevBlock O = blocks[o];
-        const int oc[3] = {g[0] - O.i0, g[1] - O.j0, g[2] - O.k0};
         const int os = 2 * a + (1 - side);
-        const long long soo = fo[o] + side_offset(O, os, nvar);
-        const long long ncell_o = (long long)O.n[t1] * O.n[t2];
-        const long long co = (long long)oc[t2] * O.n[t1] + oc[t1];
         const long long cs = (long long)c2 * B.n[t1] + c1;
-        if (f[o] < fb) {
-          const int pos[3] = {ci[0] + p.g[0], ci[1] + p.g[1], ci[2] + p.g[2]};
-          const long long l = B.off + ((long long)pos[2] * B.p[1] + pos[1]) * B.p[0] + pos[0];
-          double dI[6];
-          for (int q = 0; q < nvar; ++q) dI[q] = R[soo + q * ncell_o + co] - R[sos + q * ncell + cs];
+        const int pos[3] = {ci[0] + p.g[0], ci[1] + p.g[1], ci[2] + p.g[2]};
+        const long long l = B.off + ((long long)pos[2] * B.p[1] + pos[1]) * B.p[0] + pos[0];
+        double dI[6];
+        bool correct = false;
+        if (O.level == B.level) {
+          const int oc[3] = {g[0] - O.i0, g[1] - O.j0, g[2] - O.k0};
+          const long long soo = fo[o] + side_offset(O, os, nvar);
+          const long long ncell_o = (long long)O.n[t1] * O.n[t2];
+          const long long co = (long long)oc[t2] * O.n[t1] + oc[t1];
+          if (f[o] < fb) {
+            for (int q = 0; q < nvar; ++q) dI[q] = R[soo + q * ncell_o + co] - R[sos + q * ncell + cs];
+            for (int q = 0; q < nvar; ++q) R[soo + q * ncell_o + co] = 0.0;
+            correct = true;
+          }
+          if (f[o] <= fb && !correct)
+            for (int q = 0; q < nvar; ++q) R[sos + q * ncell + cs] = 0.0;
+        } else if (O.level == B.level + 1) {
+          // the fine face cells behind this coarse face cell: their impulses are
+          // the accepted ones, averaged over the coarse face
+          double acc[6] = {0, 0, 0, 0, 0, 0};
+          int nf = 0;
+          for (int e2 = 0; e2 < (p.active[t2] ? 2 : 1); ++e2)
+            for (int e1 = 0; e1 < (p.active[t1] ? 2 : 1); ++e1) {
+              int h[3];
+              h[a] = side ? 2 * g[a] : 2 * g[a] + 1;
+              h[t1] = p.active[t1] ? 2 * g[t1] + e1 : 0;
+              h[t2] = p.active[t2] ? 2 * g[t2] + e2 : 0;
+              const int o2 = owner_at(ol, p, B.level + 1, h);
+              const DevBlock F = blocks[o2];
+              const int hc[3] = {h[0] - F.i0, h[1] - F.j0, h[2] - F.k0};
+              const long long sof = fo[o2] + side_offset(F, os, nvar);
+              const long long ncell_f = (long long)F.n[t1] * F.n[t2];
+              const long long cf = (long long)hc[t2] * F.n[t1] + hc[t1];
+              for (int q = 0; q < nvar; ++q) {
+                acc[q] += R[sof + q * ncell_f + cf];
+                R[sof + q * ncell_f + cf] = 0.0;
+              }
+              ++nf;
+            }
+          for (int q = 0; q < nvar; ++q) dI[q] = acc[q] / nf - R[sos + q * ncell + cs];
+          correct = true;
+        }
+        // a coarser neighbour (level - 1) reads this block's impulses: kept
+        if (correct) {
+          const double dxa = block_dx(p, B, a);
           if (bh.on || phi_sg) {
             int pn[3] = {pos[0], pos[1], pos[2]};
             pn[a] += side ? 1 : -1;
@@ -277,17 +408,26 @@ __global__ void __launch_bounds__(LNT) k_reflux(Phys p, BH bh, OwnerLattice ol,
               phi_i += phi_sg[l];
               phi_n += phi_sg[B.off + ((long long)pn[2] * B.p[1] + pn[1]) * B.p[0] + pn[0]];
             }
-            U[4 * ntot + l] += sigma / (2.0 * p.dx[a]) * (-dI[0]) * (phi_n - phi_i);
+            U[4 * ntot + l] += sigma / (2.0 * dxa) * (-dI[0]) * (phi_n - phi_i);
           }
-          for (int q = 0; q < nvar; ++q) U[q * ntot + l] += -sigma * dI[q] / p.dx[a];
-          for (int q = 0; q < nvar; ++q) R[soo + q * ncell_o + co] = 0.0;
-        }
-        if (f[o] <= fb)
+          for (int q = 0; q < nvar; ++q) U[q * ntot + l] += -sigma * dI[q] / dxa;
           for (int q = 0; q < nvar; ++q) R[sos + q * ncell + cs] = 0.0;
+        }
       }
       __syncthreads();
     }
   }
+}
+
+cudaError_t launch_ghost_amr(tde_mesh *m, double *Udst, const double *Ucur, const double *Uold, int nvar,
+                             int nblk, const int32_t *ids, const int32_t *f, int flevel, int tau, int stage) {
+  if (!m->d_amr || nblk <= 0) return cudaSuccess;
+  ProfScope ps(m->ctx, TDE_K_GHOST);
+  const AmrSrc S{Udst, Ucur, Uold, f, flevel, tau, stage, (long long)m->ntot};
+  const unsigned gx = (unsigned)std::max(1, std::min((m->max_amr + LNT - 1) / LNT, 64));
+  k_ghost_amr<<<dim3(gx, (unsigned)nblk), LNT, 0, m->ctx->stream>>>(m->d_amr, m->d_amr_start, ids, m->d_blocks,
+                                                                   m->phys, S, Udst, nvar);
+  return cudaGetLastError();
 }
 
 // A captured LAT window is stale once the mesh's launch configuration changes.
@@ -394,7 +534,7 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
   }
   LCK(c, cudaMemsetAsync(m->d_freg, 0, sizeof(double) * m->freg_size, s));
   TimeArgs ta{m->d_dtb, 1, m->d_tstart, 1};
-  OwnerLattice ol{m->d_owner, {m->unit[0], m->unit[1], m->unit[2]}, {m->cn[0], m->cn[1], m->cn[2]}};
+  OwnerLattice ol{m->d_owner, {m->unit[0], m->unit[1], m->unit[2]}, {m->cn[0], m->cn[1], m->cn[2]}, m->lmax};
   const int fmax = m->lat_fmax;
   const unsigned gx_ghost = (unsigned)std::max(1, std::min((m->max_ghosts + 255) / 256, 64));
   const unsigned gx_copy = 64;
@@ -436,6 +576,7 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
                                                         stage, Udst, m->U, m->d_Uold, nvar, (long long)m->ntot);
         }
         LCK(c, cudaGetLastError());
+        LCK(c, launch_ghost_amr(m, Udst, m->U, m->d_Uold, nvar, n, ids, m->d_f, f, tau, stage));
         LCK(c, launch_c2p_padded(m, Udst, n, ids));
         LCK(c, launch_sweeps(m, stage, m->U, Udst, stage ? m->U : m->U1, n, ids, bh, ta, m->d_freg));
       }
@@ -450,6 +591,22 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
 }
 
 }  // namespace
+
+int tde::lat_step_all_ones(tde_mesh *m, const BH &bh) {
+  tde_ctx *c = m->ctx;
+  int r = ensure_factor_buffers(m);
+  if (r) return r;
+  bool ones = m->lat_ready && (int)m->h_f.size() == m->nb;
+  for (int b = 0; ones && b < m->nb; ++b) ones = m->h_f[b] == 1;
+  if (!ones) {
+    m->h_f.assign(m->nb, 1);
+    r = lat_build(m);
+    if (r) return r;
+  }
+  // dt0 = the step's dt, already on the device
+  LCK(c, cudaMemcpyAsync(m->d_scal + 3, m->d_scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return lat_enqueue_window(m, bh);
+}
 
 extern "C" int tde_lat_assign(tde_mesh *m, int n_lat, double merge_frac, double cfl,
                               const tde_bh_state *bhs, int32_t *factors, int *f_max, double *dt0) {
@@ -473,7 +630,7 @@ extern "C" int tde_lat_assign(tde_mesh *m, int n_lat, double merge_frac, double 
   {
     ProfScope ps(c, TDE_K_DT);
     k_lat_factors<<<1, 1024, 0, c->stream>>>(m->nb, m->d_dtb, n_lat, merge_frac, m->d_nbr_start, m->d_nbr,
-                                              m->d_f, m->d_f2, m->d_scal, m->d_flag);
+                                              m->d_blocks, m->d_f, m->d_f2, m->d_scal, m->d_flag);
   }
   LCK(c, cudaGetLastError());
   m->h_f.resize(m->nb);

@@ -32,7 +32,7 @@ struct NAScratch {
   unsigned long long minbits[NA_MAX_BLOCKS]; // per-block CFL minima (IEEE bits)
 };
 
-// The only scratch of this entry point (about 164 KB per device).
+// The only scratch of this entry point (about 176 KB per device).
 static __device__ __align__(256) NAScratch g_noalloc_scratch;
 
 // device address of g_noalloc_scratch, looked up once per device
@@ -88,10 +88,11 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
       for (int a = 0; a < 3; ++a) {
         int g = o[a] + c[a] - p.g[a];
         if (p.bc[a] == 1) {
-          g %= p.N[a];
-          if (g < 0) g += p.N[a];
+          const int N = p.active[a] ? p.N[a] << d.level : 1;
+          g %= N;
+          if (g < 0) g += N;
         }
-        x[a] = p.xmin[a] + (g + 0.5) * p.dx[a];
+        x[a] = p.xmin[a] + (g + 0.5) * (p.active[a] ? p.dx[a] * exp2i(-d.level) : p.dx[a]);
       }
       na_bh_pos(bh, t_block ? t_block[b] : 0.0, rb);
       const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
@@ -103,11 +104,11 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
       const double cs = sqrt(g1 * w[4] / w[0]);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        if (p.active[a]) best = fmin(best, p.dx[a] / (fabs(w[1 + a]) + cs));
+        if (p.active[a]) best = fmin(best, p.dx[a] * exp2i(-d.level) / (fabs(w[1 + a]) + cs));
       if (bh.on) {
         const double s2 = r2 + bh.rs2;
         const double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-        if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin / gmag));
+        if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin * exp2i(-d.level) / gmag));
       }
     }
   }
@@ -237,6 +238,7 @@ extern "C" int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block
   for (int b = 0; b < nblocks; ++b) {
     const tde_block_desc &d = blocks[b];
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: block size");
+    if (d.level < 0 || d.level > 8) return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: level");
     ntot += (long long)(d.nx + 2 * p.g[0]) * (d.ny + 2 * p.g[1]) * (d.nz + 2 * p.g[2]);
     const long long ni = (long long)d.nx * d.ny * d.nz;
     if (ni > max_int) max_int = ni;

@@ -30,10 +30,11 @@ __device__ __forceinline__ void cell_centre(const Phys &p, const DevBlock &B, co
   for (int a = 0; a < 3; ++a) {
     int g = o[a] + c[a] - p.g[a];
     if (p.bc[a] == 1) {
-      g %= p.N[a];
-      if (g < 0) g += p.N[a];
+      const int N = level_n(p, a, B.level);
+      g %= N;
+      if (g < 0) g += N;
     }
-    x[a] = p.xmin[a] + (g + 0.5) * p.dx[a];
+    x[a] = p.xmin[a] + (g + 0.5) * block_dx(p, B, a);
   }
 }
 
@@ -243,8 +244,8 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   __syncthreads();
 
   // ---- D: divergence, sources; the last direction completes the update
-  const double idx = p.idx[D];
-  const double hidx = 0.5 * p.idx[D];
+  const double idx = block_idx(p, B, D);
+  const double hidx = 0.5 * idx;
   for (int e = threadIdx.x; e < nd * M; e += NTS) {
     int c, lane;
     split(e, nd, c, lane);

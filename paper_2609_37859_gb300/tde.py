@@ -51,7 +51,12 @@ class GravParams(C.Structure):
 
 
 class BlockDesc(C.Structure):
-    _fields_ = [(n, C.c_int) for n in ("i0", "j0", "k0", "nx", "ny", "nz")]
+    _fields_ = [(n, C.c_int) for n in ("i0", "j0", "k0", "nx", "ny", "nz", "level")]
+
+
+def _block_descs(layout):
+    nb = layout.nb
+    return (BlockDesc * nb)(*[BlockDesc(*map(int, b), layout.level(q)) for q, b in enumerate(layout.blocks)])
 
 
 class GridDesc(C.Structure):
@@ -334,7 +339,7 @@ class Mesh:
         torch = ctx.torch
         self.ctx, self.layout, self.params, self.eos = ctx, layout, params, eos
         nb = layout.nb
-        blocks = (BlockDesc * nb)(*[BlockDesc(*map(int, b)) for b in layout.blocks])
+        blocks = _block_descs(layout)
         g = GridDesc((C.c_int * 3)(*layout.N), (C.c_double * 3)(*layout.xmin),
                      (C.c_double * 3)(*layout.dx), (C.c_int * 3)(*layout.bc), layout.ng)
         h = vp()
@@ -487,7 +492,7 @@ def compute_dt_noalloc(ctx, layout, params, U, cfl, dt_block=None, dt_min=None, 
     the library.  `table` is a (n_rho, n_T, lrho, lT, log10_e, log10_P, log10_cs2)
     tuple whose arrays are CUDA tensors the caller owns."""
     nb = layout.nb
-    blocks = (BlockDesc * nb)(*[BlockDesc(*map(int, b)) for b in layout.blocks])
+    blocks = _block_descs(layout)
     g = GridDesc((C.c_int * 3)(*layout.N), (C.c_double * 3)(*layout.xmin),
                  (C.c_double * 3)(*layout.dx), (C.c_int * 3)(*layout.bc), layout.ng)
     tv = None
