@@ -264,6 +264,8 @@ def run_gpu(args):
             line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
         if not args.no_remap:
             line["remap"] = remap_bench(ctx, tde, torch, dev, args)
+        if not args.no_smr:
+            line["lat_refined"] = smr_bench(ctx, tde, torch, dev, args)
         if not args.no_lat:
             line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_c5:
@@ -591,6 +593,88 @@ def gravity_bench(ctx, tde, torch, dev, args, n=256):
                              "levels, two V100s; AthenaK public solver 22.4 / 49.6 ms)"}
 
 
+def smr_bench(ctx, tde, torch, dev, args):
+    """LAT across coarse-fine interfaces (Sec. 7.1): a blast wave (ideal gas,
+    PLM + HLLE, dual energy) at the centre of a statically refined mesh, the
+    level-0 grid 128^3 in 16^3 MeshBlocks, refined twice (levels 1 and 2, 2:1
+    balanced) within r = 0.15 of the centre: 1912 blocks, 7.8 M cells.  Over the
+    same physical time f_max dt0: one LAT window (CUDA graph) against f_max
+    synchronised steps of dt0 (each one window with every factor 1), and the
+    density difference between the two (the paper's blast-wave comparison)."""
+    from paper_2609_37859_gb300 import workloads as wl
+
+    def sphere(lo, hi, L):
+        return sum(max(lo[a], 0.0, -hi[a]) ** 2 for a in range(3)) < 0.15 ** 2
+
+    lay = wl.smr_layout((128, 128, 128), (16, 16, 16), ((-0.5, 0.5),) * 3, (0, 0, 0), 2, sphere, 2)
+    x, y, z, _ = lay.interior_centres()
+    r2 = x * x + y * y + z * z
+    W = wl.prim_cells(lay, 1.0, 0.0, 0.0, 0.0, np.where(r2 < 0.04 ** 2, 10.0, 1e-2))
+    params = tde.make_params(dual=1, eta1=1e-3, eta2=1e-4, riemann=tde.RIEMANN_HLLE)
+    mesh = tde.Mesh(ctx, lay, params)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    del W
+    # let the blast develop before measuring
+    for _ in range(20):
+        mesh.step(cfl=CFL)
+    U0 = mesh.U.clone()
+    t0 = mesh.get_time()
+    fac, dt0, fmax = mesh.lat_assign(5, CFL, merge_frac=0.0)
+    cells = np.array([b[3] * b[4] * b[5] for b in lay.blocks], dtype=np.float64)
+    work = float((cells * (fmax // fac)).sum() / (cells.sum() * fmax))
+    by_level = {}
+    for L in range(3):
+        sel = lay.levels == L
+        by_level[str(L)] = {str(int(k)): int(((fac == k) & sel).sum()) for k in np.unique(fac[sel])}
+
+    def timed(fn, reps):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    # LAT window (graph)
+    mesh.lat_set_factors(fac, dt0)
+    mesh.lat_window(use_graph=True)
+    mesh.U.copy_(U0)
+    mesh.set_time(t0)
+    mesh.lat_set_factors(fac, dt0)
+    ms_lat = timed(lambda: mesh.lat_window(use_graph=True), 1)
+    rho_lat = mesh.U[0].clone()
+    # synchronised steps of dt0 over the same time
+    mesh.U.copy_(U0)
+    mesh.set_time(t0)
+    mesh.step(dt=dt0)   # warm-up (one-factor assignment)
+    mesh.U.copy_(U0)
+    mesh.set_time(t0)
+
+    def sync_window():
+        for _ in range(fmax):
+            mesh.step(dt=dt0)
+    ms_sync = timed(sync_window, 1)
+    flat = torch.from_numpy(lay.interior_flat()).to(dev)
+    rl, rs = rho_lat[flat], mesh.U[0][flat]
+    drel = (rl - rs).abs() / rs
+    ncell = float(cells.sum())
+    out = {"workload": "blast wave, 128^3 level-0 grid in 16^3 blocks refined to level 2 within r = 0.15: "
+                       "%d blocks (levels 0/1/2: %s), %.2f M cells, PLM + HLLE, dual energy, N_LAT = 5"
+                       % (lay.nb, "/".join(str(int(v)) for v in np.bincount(lay.levels)), ncell / 1e6),
+           "f_max": int(fmax), "factors_by_level": by_level, "work_fraction": work,
+           "ms_lat_window": ms_lat, "ms_sync_same_time": ms_sync, "speedup": ms_sync / ms_lat,
+           "ideal_speedup": 1.0 / work,
+           "effective_cell_updates_per_s": ncell * fmax / (ms_lat * 1e-3),
+           "sync_cell_updates_per_s": ncell * fmax / (ms_sync * 1e-3),
+           "rho_lat_vs_sync": {"max_rel": float(drel.max()), "mean_rel": float(drel.mean())},
+           "finite": bool(torch.isfinite(mesh.U).all().item())}
+    del mesh, U0
+    torch.cuda.empty_cache()
+    return out
+
+
 def remap_bench(ctx, tde, torch, dev, args, n=256, reps=5):
     """Domain remap (Sec. 5.2) of an n^3 dual-energy state in 32^3 MeshBlocks:
     (a) onto an n^3 grid over a domain twice as wide (the debris outgrowing its
@@ -811,6 +895,7 @@ def main():
     ap.add_argument("--no-c5", action="store_true", help="skip the production-shaped LAT run")
     ap.add_argument("--no-grav", action="store_true", help="skip the self-gravity multigrid")
     ap.add_argument("--no-remap", action="store_true", help="skip the domain remap")
+    ap.add_argument("--no-smr", action="store_true", help="skip LAT on the refined blast-wave mesh")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -187,13 +187,19 @@ __host__ __device__ __forceinline__ double exp2i(int e) {
   return r;
 }
 
+// x 2^e for a normal x whose result is normal: an integer add on the exponent
+// field (exact, and no FP64 instruction)
+__device__ __forceinline__ double scale2i(double x, int e) {
+  return __longlong_as_double(__double_as_longlong(x) + ((long long)e << 52));
+}
+
 // cell width, its reciprocal and the grid size along a on block B's level
 // (refinement halves the cells of the active directions only)
 __device__ __forceinline__ double block_dx(const Phys &p, const DevBlock &B, int a) {
-  return p.active[a] ? p.dx[a] * exp2i(-B.level) : p.dx[a];
+  return p.active[a] ? scale2i(p.dx[a], -B.level) : p.dx[a];
 }
 __device__ __forceinline__ double block_idx(const Phys &p, const DevBlock &B, int a) {
-  return p.active[a] ? p.idx[a] * exp2i(B.level) : p.idx[a];
+  return p.active[a] ? scale2i(p.idx[a], B.level) : p.idx[a];
 }
 __device__ __forceinline__ int level_n(const Phys &p, int a, int L) {
   return p.active[a] ? p.N[a] << L : 1;

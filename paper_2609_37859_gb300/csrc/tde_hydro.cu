@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         if (bh.on) {
           double s2 = r2 + bh.rs2;
           double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-          if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin * exp2i(-B.level) / gmag));
+          if (gmag > 0.0) best = fmin(best, sqrt(scale2i(p.dxmin, -B.level) / gmag));
         }
       }
     }

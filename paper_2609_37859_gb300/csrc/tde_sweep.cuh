@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   __syncthreads();
 
   // ---- D: divergence, sources; the last direction completes the update
-  const double idx = block_idx(p, B, D);
+  // the level read where it is needed (keeps it out of the live registers)
+  const double idx = scale2i(p.idx[D], __ldg(&a.blocks[b].level));
   const double hidx = 0.5 * idx;
   for (int e = threadIdx.x; e < nd * M; e += NTS) {
     int c, lane;
