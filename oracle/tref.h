@@ -207,6 +207,16 @@ void tref_boost(const tref_mesh *m, double *U, const double *V, double rho_min);
 int tref_mg_solve(int nx, int ny, int nz, const double *dx, const double *src, double *phi,
                   int max_cycles, double tol, int npre, int npost, double omega, double *defect);
 double tref_mg_defect_rms(int nx, int ny, int nz, const double *dx, const double *src, const double *phi);
+/* The same on a periodic (isolated = 0) or isolated grid (lower corner xmin):
+ * isolated boundary values from the multipole expansion of the source to order
+ * lmax (<= 8) about centre (NULL: the source-weighted centroid); fmg = 1 starts
+ * with full multigrid instead of phi.  *defect_start (may be NULL) = the rms
+ * defect before the V-cycles; phiq[q] = the expansion at the nq points xq[3q..]
+ * (isolated only). */
+int tref_mg_solve_bc(int nx, int ny, int nz, const double *dx, const double *xmin, int isolated, int lmax,
+                     const double *centre, int fmg, const double *src, double *phi, int max_cycles,
+                     double tol, int npre, int npost, double omega, double *defect, double *defect_start,
+                     int nq, const double *xq, double *phiq);
 
 /* Self-gravity potential of the hydro sources, in the mesh's padded layout
  * (ghosts included; the caller keeps the array), NULL to switch it off.  It is

@@ -94,6 +94,9 @@ def lib():
             "tref_mg_solve": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_double,
                                         C.c_int, C.c_int, C.c_double, dp]),
             "tref_mg_defect_rms": (C.c_double, [C.c_int, C.c_int, C.c_int, dp, dp, dp]),
+            "tref_mg_solve_bc": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, dp, C.c_int,
+                                           dp, dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double, dp, dp,
+                                           C.c_int, dp, dp]),
             "tref_frame_acceleration": (None, [C.c_void_p, dp, C.c_double, C.c_double, dp, dp]),
             "tref_boost": (None, [C.c_void_p, dp, dp, C.c_double]),
             "tref_saha_state": (None, [C.c_double, C.c_double, C.c_double, C.c_double, dp]),
@@ -378,6 +381,25 @@ def mg_solve(src, dx, phi=None, max_cycles=20, tol=0.0, npre=2, npost=2, omega=1
     dxa = np.ascontiguousarray(dx, dtype=np.float64)
     n = lib().tref_mg_solve(nx, ny, nz, P(dxa), P(src), P(phi), max_cycles, tol, npre, npost, omega, P(d))
     return phi, n, float(d[0])
+
+
+def mg_solve_bc(src, dx, xmin=(0.0, 0.0, 0.0), isolated=True, lmax=4, centre=None, fmg=True, phi=None,
+                max_cycles=20, tol=0.0, npre=2, npost=2, omega=1.15, query=None):
+    """Multigrid on a periodic or isolated grid (multipole boundary values), with
+    a full-multigrid start.  Returns (phi, cycles, rms defect, rms defect before
+    the V-cycles, the expansion at the query points [n][3])."""
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    nz, ny, nx = src.shape
+    phi = np.zeros_like(src) if phi is None else np.ascontiguousarray(phi, dtype=np.float64).copy()
+    d, d0 = np.zeros(1), np.zeros(1)
+    q = np.zeros((0, 3)) if query is None else np.ascontiguousarray(query, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(len(q))
+    c = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
+    n = lib().tref_mg_solve_bc(nx, ny, nz, P(np.ascontiguousarray(dx, dtype=np.float64)),
+                               P(np.ascontiguousarray(xmin, dtype=np.float64)), 1 if isolated else 0, lmax,
+                               P(c) if c is not None else None, 1 if fmg else 0, P(src), P(phi), max_cycles, tol,
+                               npre, npost, omega, P(d), P(d0), len(q), P(q), P(out))
+    return phi, n, float(d[0]), float(d0[0]), out
 
 
 def mg_defect(src, phi, dx):
