@@ -580,11 +580,35 @@ def gravity_bench(ctx, tde, torch, dev, args, n=256):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
+    # the full-multigrid start (the paper's start for a first or remapped solve)
+    ms_fmg, (nfmg, dfmg) = timed(lambda: mesh.gravity_solve(G, 0.0, tol=1e-9, max_cycles=30, warm=False, fmg=True))
+    del mesh
+    torch.cuda.empty_cache()
+    # isolated boundaries (multipole, l_max = 4): a centrally condensed cloud on
+    # an outflow mesh, from the full-multigrid start
+    lay_i = wl.uniform_layout((n, n, n), (32, 32, 32), domain=((-1, 1),) * 3, bc=(0, 0, 0), ng=2)
+    xi, yi, zi = lay_i.cell_centres()
+    rho_i = 1e-4 + np.exp(-((xi - 0.1) ** 2 + yi ** 2 + (zi + 0.05) ** 2) / (2 * 0.2 ** 2))
+    Wi = wl.prim_state(lay_i, rho_i, 0.0, 0.0, 0.0, 0.1 * rho_i)
+    del xi, yi, zi, rho_i
+    mesh = tde.Mesh(ctx, lay_i, tde.make_params())
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(Wi)).to(dev))
+    del Wi
+    mesh.gravity_solve(G, 0.0, tol=0.0, max_cycles=2, warm=False, isolated=True, fmg=True)   # warm-up
+    ms6i, _ = timed(lambda: mesh.gravity_solve(G, 0.0, tol=0.0, max_cycles=6, warm=True, isolated=True))
+    ms2i, _ = timed(lambda: mesh.gravity_solve(G, 0.0, tol=0.0, max_cycles=2, warm=True, isolated=True))
+    ms_iso, (niso, diso) = timed(lambda: mesh.gravity_solve(G, 0.0, tol=1e-9, max_cycles=30, warm=False,
+                                                            isolated=True, lmax=4, fmg=True))
     del mesh
     torch.cuda.empty_cache()
     return {"workload": "%d^3 periodic, %d MeshBlocks of 32^3, random smooth density, G = 1/(4 pi)" %
                         (n, lay.nb),
             "ms_per_vcycle": per_cycle, "cold": {"vcycles": ncold, "defect": dcold, "ms": ms_cold},
+            "fmg_start": {"vcycles_after": nfmg, "defect": dfmg, "ms": ms_fmg},
+            "isolated": {"workload": "%d^3 on [-1, 1]^3, outflow mesh, Gaussian cloud (sigma 0.2) over a "
+                                     "1e-4 floor, multipole boundary values to l_max = 4" % n,
+                         "ms_per_vcycle": (ms6i - ms2i) / 4.0,
+                         "fmg_solve": {"vcycles_after": niso, "defect": diso, "ms": ms_iso}},
             "warm_after_one_step": {"vcycles": nwarm, "defect": dwarm, "ms": ms_warm},
             "hbm": {"algorithmic_bytes_per_vcycle": bytes_cycle,
                     "achieved_gbs": bytes_cycle / (per_cycle * 1e-3) * 1e-9, "peak_gbs": hbm,

@@ -430,13 +430,20 @@ TDE_API int tde_mesh_boost(tde_mesh *mesh, const double *V, double rho_min);
  * Geometric multigrid for A_h phi = S_h, A_h = -lap_h (seven-point, weights
  * (dx/dy)^2 and (dx/dz)^2, Eq. selfgrav-poisson), S_h = -4 pi G rho_sg with
  * rho_sg = rho where rho > rho_min (floor gas excluded), on the mesh's uniform
- * grid with periodic boundaries in every direction (each N a power of two; the
- * mean of S is removed in two passes).  V-cycles of npre / npost red-black
- * Gauss-Seidel sweeps with over-relaxation omega (the paper: 2, 2, 1.15), a
- * full-approximation coarse correction, trilinear prolongation, post-smoothing
- * on every level and one extra fine sweep, until the rms defect (Eq.
- * selfgrav-defect) is below tol or max_cycles are done; warm = 1 starts from the
- * previous potential. */
+ * grid (each active N a power of two).  Boundaries: TDE_GRAV_PERIODIC (every
+ * active direction of the mesh periodic; the mean of S removed in two passes)
+ * or TDE_GRAV_ISOLATED (the paper's multipole boundary conditions: phi on every
+ * boundary face is the exterior multipole expansion of S to order lmax <= 4
+ * about its S-weighted centroid, a Dirichlet condition at the face on every
+ * level).  V-cycles of npre / npost red-black Gauss-Seidel sweeps with
+ * over-relaxation omega (the paper: 2, 2, 1.15), a full-approximation coarse
+ * correction, trilinear prolongation, post-smoothing on every level and one
+ * extra fine sweep, until the rms defect (Eq. selfgrav-defect) is below tol or
+ * max_cycles are done.  The start: fmg = 1 full multigrid (the paper's start for
+ * a first or remapped solve: the source on every level, the coarsest solved,
+ * then per finer level the prolonged solution and one V-cycle), else warm = 1
+ * the previous potential, else zero. */
+enum { TDE_GRAV_PERIODIC = 0, TDE_GRAV_ISOLATED = 1 };
 typedef struct {
   double G;            /* gravitational constant in code units (1 / (4 pi) for Table 1's) */
   double rho_min;      /* density above which gas is a source */
@@ -444,11 +451,17 @@ typedef struct {
   int max_cycles, npre, npost;
   double omega;        /* over-relaxation of the Gauss-Seidel sweeps */
   int warm;            /* start from the previous potential */
+  int boundary;        /* TDE_GRAV_PERIODIC or TDE_GRAV_ISOLATED */
+  int lmax;            /* isolated: multipole order 0..4 */
+  int fmg;             /* start with full multigrid */
 } tde_grav_params;
 /* Solve for phi_sg from the bound state's density; the potential is kept by the
- * mesh (also in the MeshBlock layout, ghosts included).  cycles and defect (may
- * be NULL) receive the V-cycles run and the final rms defect.  TDE_EINVAL unless
- * every active direction is periodic with a power-of-two size.  Synchronises. */
+ * mesh (also in the MeshBlock layout, ghosts included: periodic images, or
+ * beyond an isolated boundary the expansion at the ghost centre).  cycles and
+ * defect (may be NULL) receive the V-cycles run after the start and the final
+ * rms defect.  TDE_EINVAL for an active size that is not a power of two, a
+ * periodic solve on a mesh with a non-periodic active direction, lmax outside
+ * 0..4 or a refined mesh.  Synchronises. */
 TDE_API int tde_gravity_solve(tde_mesh *mesh, const tde_grav_params *params, int *cycles,
                               double *defect);
 /* on = 1: the hydro stage adds the kept phi_sg (frozen between solves) to the

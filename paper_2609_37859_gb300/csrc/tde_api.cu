@@ -920,11 +920,14 @@ static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 extern "C" int tde_gravity_solve(tde_mesh *m, const tde_grav_params *gp, int *cycles, double *defect) {
   if (!m) return TDE_EINVAL;
-  if (!m->U || !gp || gp->max_cycles < 0 || gp->npre < 0 || gp->npost < 0)
+  if (!m->U || !gp || gp->max_cycles < 0 || gp->npre < 0 || gp->npost < 0 ||
+      (gp->boundary != TDE_GRAV_PERIODIC && gp->boundary != TDE_GRAV_ISOLATED) ||
+      (gp->boundary == TDE_GRAV_ISOLATED && (gp->lmax < 0 || gp->lmax > 4)))
     return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: arguments");
   for (int a = 0; a < 3; ++a)
-    if (m->phys.N[a] > 1 && (m->phys.bc[a] != TDE_BC_PERIODIC || !pow2(m->phys.N[a])))
-      return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: needs periodic power-of-two directions");
+    if (m->phys.N[a] > 1 && (!pow2(m->phys.N[a]) ||
+                             (gp->boundary == TDE_GRAV_PERIODIC && m->phys.bc[a] != TDE_BC_PERIODIC)))
+      return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: needs power-of-two directions (periodic ones for a periodic solve)");
   if (m->lmax > 0) return fail(m->ctx, TDE_EINVAL, "tde_gravity_solve: refined mesh");
   CK(m->ctx, gravity_solve(m, *gp, cycles, defect));
   invalidate_graph(m);

@@ -1,7 +1,7 @@
 // tde_grav.cu -- self-gravity (Sec. 3.2): a geometric multigrid for
 // A_h phi = S_h, A_h = -lap_h (seven-point, anisotropic weights
 // w_y = (dx/dy)^2, w_z = (dx/dz)^2), S_h = -4 pi G rho_sg (Eq. selfgrav-poisson),
-// on the mesh's uniform grid with periodic boundaries, and the coupling of the
+// on the mesh's uniform grid, periodic or isolated, and the coupling of the
 // potential to the hydro sources (the sweeps add the stored phi_sg to the point
 // mass's potential in Eqs. lat-grav-momentum and lat-grav-energy).
 //
@@ -11,6 +11,19 @@
 // extra fine sweep per cycle; each direction halved while it has more than one
 // cell.  The levels are global arrays (x fastest); the MeshBlock layout is
 // gathered into level 0 and the potential scattered back (ghosts included).
+//
+// Isolated boundaries (the paper's multipole boundary conditions): phi on every
+// boundary face is the exterior multipole expansion of the source to order
+// l_max <= 4 about its source-weighted centroid, a Dirichlet condition at the
+// face (the cell beyond it is 2 phi_face - phi_inside; a coarse correction's is
+// -e_inside); the Gauss-Seidel update is implicit in those mirror cells and the
+// single-cell level is solved exactly.  The expansion uses the regular solid
+// harmonics R_l^m = r^l P_l^m(cos t) e^(i m p), built by their polynomial
+// recurrences in (x, y, z) (no trigonometry): the moments are sums of
+// S dV R_l^m(x'), the potential sum_lm Re(conj-free) (A R_re + B R_im) / r^(2l+1).
+//
+// Full multigrid start: the source restricted to every level, the coarsest
+// solved, then per finer level the prolonged solution and one V-cycle.
 #include <math.h>
 #include <string.h>
 
@@ -23,6 +36,8 @@ namespace tde {
 namespace {
 
 constexpr int GT = 256;
+constexpr int MP_LMAX = 4;                                       // largest expansion order
+constexpr int MP_NC = (MP_LMAX + 1) * (MP_LMAX + 2) / 2;        // (l, m) pairs, m <= l
 
 struct Lev {
   int n[3];
@@ -30,8 +45,18 @@ struct Lev {
   double *phi, *src, *tmp;
   // seven-point operator, per level: (A phi)_c = aw . (2 phi_c - phi_{c+a} - phi_{c-a});
   // Gauss-Seidel value = cs src + cw . (phi_{c+a} + phi_{c-a}) (cw = w_a / diag,
-  // cs = dx^2 / diag); zero weights in directions with one cell
+  // cs = dx^2 / diag); zero weights in directions with one cell (periodic) or
+  // inactive on the finest level (isolated)
   double aw[3], cw[3], cs;
+  int iso;                  // isolated boundaries
+  double x0[3];             // lower domain corner
+  const double *gf[6];      // isolated: phi on the boundary faces x-, x+, y-, y+, z-, z+
+};
+
+// the expansion: order, centre, coefficients (A_lm, B_lm) at 2 (l (l + 1) / 2 + m)
+struct MP {
+  int lmax;
+  const double *cc;         // [0..2] centre, then the coefficients
 };
 
 // 32-bit index arithmetic throughout (levels have < 2^31 cells; 64-bit integer
@@ -43,6 +68,10 @@ __device__ __forceinline__ unsigned wrap_idx(const Lev &L, int i, int j, int k) 
   return ((unsigned)k * L.n[1] + j) * L.n[0] + i;
 }
 
+__device__ __forceinline__ unsigned lin(const Lev &L, int i, int j, int k) {
+  return ((unsigned)k * L.n[1] + j) * L.n[0] + i;
+}
+
 __device__ __forceinline__ void decompose(const Lev &L, unsigned c, int &i, int &j, int &k) {
   const unsigned r = c / (unsigned)L.n[0];
   i = (int)(c - r * L.n[0]);
@@ -50,12 +79,133 @@ __device__ __forceinline__ void decompose(const Lev &L, unsigned c, int &i, int 
   j = (int)(r - (unsigned)k * L.n[1]);
 }
 
+// isolated: phi on the boundary face (a, side) of boundary cell c
+__device__ __forceinline__ double face_phi(const Lev &L, int a, int side, const int c[3]) {
+  const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+  return L.gf[2 * a + side][(unsigned)c[t2] * L.n[t1] + c[t1]];
+}
+
+// the regular solid harmonics R_l^m(d) (re, im) for l <= lmax, at 2 (l (l+1)/2 + m)
+__device__ __forceinline__ void solid_harmonics(int lmax, const double d[3], double *R) {
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double mre = 1.0, mim = 0.0;   // (2m - 1)!! (x + i y)^m
+  for (int m = 0; m <= lmax; ++m) {
+    if (m > 0) {
+      const double f = 2.0 * m - 1.0;
+      const double re = f * (mre * d[0] - mim * d[1]), im = f * (mre * d[1] + mim * d[0]);
+      mre = re;
+      mim = im;
+    }
+    int q = m * (m + 1) / 2 + m;
+    R[2 * q] = mre;
+    R[2 * q + 1] = mim;
+    if (m + 1 <= lmax) {
+      q = (m + 1) * (m + 2) / 2 + m;
+      R[2 * q] = (2.0 * m + 1.0) * d[2] * mre;
+      R[2 * q + 1] = (2.0 * m + 1.0) * d[2] * mim;
+    }
+    for (int l = m + 2; l <= lmax; ++l) {
+      const int q0 = l * (l + 1) / 2 + m, q1 = (l - 1) * l / 2 + m, q2 = (l - 2) * (l - 1) / 2 + m;
+      const double a = (2.0 * l - 1.0) * d[2], b = (l + m - 1.0) * r2, inv = 1.0 / (l - m);
+      R[2 * q0] = (a * R[2 * q1] - b * R[2 * q2]) * inv;
+      R[2 * q0 + 1] = (a * R[2 * q1 + 1] - b * R[2 * q2 + 1]) * inv;
+    }
+  }
+}
+
+// the exterior expansion at x
+__device__ double mp_eval(const MP &mp, const double x[3]) {
+  const double d[3] = {x[0] - mp.cc[0], x[1] - mp.cc[1], x[2] - mp.cc[2]};
+  double R[2 * MP_NC];
+  solid_harmonics(mp.lmax, d, R);
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double ir = 1.0 / sqrt(r2), ir2 = 1.0 / r2;
+  double s = 0.0, rp = ir;   // r^-(2l+1)
+  for (int l = 0; l <= mp.lmax; ++l) {
+    double t = 0.0;
+    for (int m = 0; m <= l; ++m) {
+      const int q = l * (l + 1) / 2 + m;
+      t += mp.cc[3 + 2 * q] * R[2 * q] + mp.cc[3 + 2 * q + 1] * R[2 * q + 1];
+    }
+    s += t * rp;
+    rp *= ir2;
+  }
+  return s;
+}
+
+// isolated: a cell with a neighbour beyond a boundary face
+__device__ __forceinline__ bool on_boundary(const Lev &L, int i, int j, int k) {
+  return (L.aw[0] != 0.0 && (i == 0 || i == L.n[0] - 1)) || (L.aw[1] != 0.0 && (j == 0 || j == L.n[1] - 1)) ||
+         (L.aw[2] != 0.0 && (k == 0 || k == L.n[2] - 1));
+}
+
+// the cell of thread e: x fastest; on an isolated grid of at least three cells
+// along x the cells at the two x faces come after all others, so that warps of
+// inner cells do not diverge into the boundary path (y and z boundary cells
+// fill whole rows)
+__device__ __forceinline__ void cell_of(const Lev &L, unsigned e, int &i, int &j, int &k) {
+  if (!L.iso || L.n[0] < 3) {
+    decompose(L, e, i, j, k);
+    return;
+  }
+  const unsigned nin = (unsigned)L.n[0] - 2, nrow = (unsigned)L.n[1] * L.n[2];
+  unsigned row;
+  if (e < nrow * nin) {
+    row = e / nin;
+    i = 1 + (int)(e - row * nin);
+  } else {
+    const unsigned r = e - nrow * nin;
+    row = r >> 1;
+    i = (r & 1) ? L.n[0] - 1 : 0;
+  }
+  k = (int)(row / (unsigned)L.n[1]);
+  j = (int)(row - (unsigned)k * L.n[1]);
+}
+
 __device__ __forceinline__ double apply_A(const Lev &L, const double *phi, int i, int j, int k) {
+  if (L.iso && on_boundary(L, i, j, k)) {
+    const int c[3] = {i, j, k};
+    const double pc = phi[lin(L, i, j, k)];
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      if (L.aw[a] == 0.0) continue;
+      double nb = 0.0;
+      for (int side = 0; side < 2; ++side) {
+        int q[3] = {i, j, k};
+        q[a] += side ? 1 : -1;
+        nb += (q[a] >= 0 && q[a] < L.n[a]) ? phi[lin(L, q[0], q[1], q[2])] : 2.0 * face_phi(L, a, side, c) - pc;
+      }
+      s = fma(L.aw[a], 2.0 * pc - nb, s);
+    }
+    return s;
+  }
+  // (periodic, or an isolated grid's inner cell, whose wrapped neighbours are its own)
   const double c2 = 2.0 * phi[wrap_idx(L, i, j, k)];
   double s = L.aw[0] * (c2 - phi[wrap_idx(L, i + 1, j, k)] - phi[wrap_idx(L, i - 1, j, k)]);
   s = fma(L.aw[1], c2 - phi[wrap_idx(L, i, j + 1, k)] - phi[wrap_idx(L, i, j - 1, k)], s);
   s = fma(L.aw[2], c2 - phi[wrap_idx(L, i, j, k + 1)] - phi[wrap_idx(L, i, j, k - 1)], s);
   return s;
+}
+
+// isolated Gauss-Seidel value of a boundary cell: the mirror cells 2 phi_face -
+// phi_c move to the diagonal (w_a / diag per mirror)
+__device__ __forceinline__ double gs_iso(const Lev &L, int i, int j, int k) {
+  const int c[3] = {i, j, k};
+  double nb = 0.0, dg = 1.0;   // in units of the inner cells' diagonal
+  for (int a = 0; a < 3; ++a) {
+    if (L.cw[a] == 0.0) continue;
+    for (int side = 0; side < 2; ++side) {
+      int q[3] = {i, j, k};
+      q[a] += side ? 1 : -1;
+      if (q[a] >= 0 && q[a] < L.n[a]) {
+        nb = fma(L.cw[a], L.phi[lin(L, q[0], q[1], q[2])], nb);
+      } else {
+        nb = fma(L.cw[a], 2.0 * face_phi(L, a, side, c), nb);
+        dg += L.cw[a];
+      }
+    }
+  }
+  return fma(L.cs, L.src[lin(L, i, j, k)], nb) / dg;
 }
 
 // level-0 source from the MeshBlock density: S = -4 pi G rho where rho > rho_min
@@ -82,8 +232,8 @@ __global__ void __launch_bounds__(GT) k_mg_partial(Lev L, int sq, double *part) 
   for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
     if (sq) {
       int i, j, k;
-      decompose(L, c, i, j, k);
-      const double d = L.src[c] - apply_A(L, L.phi, i, j, k);
+      cell_of(L, c, i, j, k);
+      const double d = L.src[lin(L, i, j, k)] - apply_A(L, L.phi, i, j, k);
       s += d * d;
     } else {
       s += L.src[c];
@@ -125,21 +275,47 @@ __global__ void __launch_bounds__(GT) k_mg_sub_mean(Lev L, const double *__restr
 __global__ void __launch_bounds__(GT) k_mg_smooth(Lev L, int colour, double omega) {
   const unsigned hx = (unsigned)(L.n[0] + 1) / 2;   // cells of one colour per row (n[0] even, or 1)
   const unsigned nrow = (unsigned)L.n[1] * L.n[2];
+  // isolated, at least four cells along x: each row's one x-face cell of this
+  // colour comes after all inner ones (no warp mixes the two paths)
+  const bool split = L.iso && L.n[0] >= 4;
   for (unsigned e = blockIdx.x * GT + threadIdx.x; e < nrow * hx; e += gridDim.x * GT) {
-    const unsigned row = e / hx;
-    const int k = (int)(row / (unsigned)L.n[1]), j = (int)(row - (unsigned)k * L.n[1]);
-    int i;
-    if (L.n[0] > 1) {
-      i = 2 * (int)(e - row * hx) + ((j + k + colour) & 1);
+    unsigned row;
+    int i, j, k;
+    if (split) {
+      const unsigned nin = hx - 1;
+      if (e < nrow * nin) {
+        row = e / nin;
+        k = (int)(row / (unsigned)L.n[1]);
+        j = (int)(row - (unsigned)k * L.n[1]);
+        const int par = (j + k + colour) & 1;
+        i = 2 * (int)(e - row * nin) + 2 - par;
+      } else {
+        row = e - nrow * nin;
+        k = (int)(row / (unsigned)L.n[1]);
+        j = (int)(row - (unsigned)k * L.n[1]);
+        i = ((j + k + colour) & 1) ? L.n[0] - 1 : 0;
+      }
     } else {
-      if (((j + k) & 1) != colour) continue;
-      i = 0;
+      row = e / hx;
+      k = (int)(row / (unsigned)L.n[1]);
+      j = (int)(row - (unsigned)k * L.n[1]);
+      if (L.n[0] > 1) {
+        i = 2 * (int)(e - row * hx) + ((j + k + colour) & 1);
+      } else {
+        if (((j + k) & 1) != colour) continue;
+        i = 0;
+      }
     }
     const unsigned c = row * L.n[0] + i;
-    double nb = L.cw[0] * (L.phi[wrap_idx(L, i + 1, j, k)] + L.phi[wrap_idx(L, i - 1, j, k)]);
-    nb = fma(L.cw[1], L.phi[wrap_idx(L, i, j + 1, k)] + L.phi[wrap_idx(L, i, j - 1, k)], nb);
-    nb = fma(L.cw[2], L.phi[wrap_idx(L, i, j, k + 1)] + L.phi[wrap_idx(L, i, j, k - 1)], nb);
-    const double gs = fma(L.cs, L.src[c], nb);
+    double gs;
+    if (L.iso && on_boundary(L, i, j, k)) {
+      gs = gs_iso(L, i, j, k);
+    } else {
+      double nb = L.cw[0] * (L.phi[wrap_idx(L, i + 1, j, k)] + L.phi[wrap_idx(L, i - 1, j, k)]);
+      nb = fma(L.cw[1], L.phi[wrap_idx(L, i, j + 1, k)] + L.phi[wrap_idx(L, i, j - 1, k)], nb);
+      nb = fma(L.cw[2], L.phi[wrap_idx(L, i, j, k + 1)] + L.phi[wrap_idx(L, i, j, k - 1)], nb);
+      gs = fma(L.cs, L.src[c], nb);
+    }
     const double p0 = L.phi[c];
     L.phi[c] = fma(omega, gs - p0, p0);
   }
@@ -150,9 +326,10 @@ __global__ void __launch_bounds__(GT) k_mg_smooth(Lev L, int colour, double omeg
 __global__ void __launch_bounds__(GT) k_mg_restrict(Lev F, Lev C, double inv) {
   const int r0 = F.n[0] / C.n[0], r1 = F.n[1] / C.n[1], r2 = F.n[2] / C.n[2];
   const unsigned n = (unsigned)C.n[0] * C.n[1] * C.n[2];
-  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+  for (unsigned e = blockIdx.x * GT + threadIdx.x; e < n; e += gridDim.x * GT) {
     int I, J, K;
-    decompose(C, c, I, J, K);
+    cell_of(C, e, I, J, K);
+    const unsigned c = lin(C, I, J, K);
     double sp = 0.0, sd = 0.0;
     for (int cz = 0; cz < r2; ++cz)
       for (int by = 0; by < r1; ++by)
@@ -171,10 +348,10 @@ __global__ void __launch_bounds__(GT) k_mg_restrict(Lev F, Lev C, double inv) {
 // coarse source of the full-approximation equation: S_C = R d_f + A_C (R phi_f)
 __global__ void __launch_bounds__(GT) k_mg_fas(Lev C) {
   const unsigned n = (unsigned)C.n[0] * C.n[1] * C.n[2];
-  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+  for (unsigned e = blockIdx.x * GT + threadIdx.x; e < n; e += gridDim.x * GT) {
     int I, J, K;
-    decompose(C, c, I, J, K);
-    C.src[c] += apply_A(C, C.tmp, I, J, K);
+    cell_of(C, e, I, J, K);
+    C.src[lin(C, I, J, K)] += apply_A(C, C.tmp, I, J, K);
   }
 }
 
@@ -213,7 +390,21 @@ __global__ void __launch_bounds__(GT) k_mg_prolong(Lev F, Lev C) {
           if ((ax && !h[0]) || (by && !h[1]) || (cz && !h[2])) continue;
           const int np = (h[0] && !ax) + (h[1] && !by) + (h[2] && !cz);
           const double w = np == 3 ? 27.0 : (np == 2 ? 9.0 : (np == 1 ? 3.0 : 1.0));
-          s = fma(w, C.tmp[wrap_idx(C, ax ? q[0] : p[0], by ? q[1] : p[1], cz ? q[2] : p[2])], s);
+          int u[3] = {ax ? q[0] : p[0], by ? q[1] : p[1], cz ? q[2] : p[2]};
+          double e;
+          if (C.iso) {   // beyond a face the correction is its odd mirror image
+            double sg = 1.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+              if (u[a] < 0 || u[a] >= C.n[a]) {
+                u[a] = u[a] < 0 ? -1 - u[a] : 2 * C.n[a] - 1 - u[a];
+                sg = -sg;
+              }
+            e = sg * C.tmp[lin(C, u[0], u[1], u[2])];
+          } else {
+            e = C.tmp[wrap_idx(C, u[0], u[1], u[2])];
+          }
+          s = fma(w, e, s);
         }
     F.phi[c] = fma(scale, s, F.phi[c]);
   }
@@ -222,14 +413,213 @@ __global__ void __launch_bounds__(GT) k_mg_prolong(Lev F, Lev C) {
 // the potential into the MeshBlock layout, every padded cell (ghosts by the
 // periodic image of their global position)
 __global__ void __launch_bounds__(GT) k_mg_scatter(Phys p, const DevBlock *__restrict__ blocks, Lev L,
-                                                   double *phi_pad) {
+                                                   MP mp, double *phi_pad) {
   const int b = blockIdx.y;
   const DevBlock B = blocks[b];
   const int npad = B.p[0] * B.p[1] * B.p[2];
   for (int e = blockIdx.x * GT + threadIdx.x; e < npad; e += gridDim.x * GT) {
     const int i = e % B.p[0], r = e / B.p[0];
     const int j = r % B.p[1], k = r / B.p[1];
-    phi_pad[B.off + e] = L.phi[wrap_idx(L, B.i0 + i - p.g[0], B.j0 + j - p.g[1], B.k0 + k - p.g[2])];
+    const int g[3] = {B.i0 + i - p.g[0], B.j0 + j - p.g[1], B.k0 + k - p.g[2]};
+    if (L.iso && (g[0] < 0 || g[1] < 0 || g[2] < 0 || g[0] >= L.n[0] || g[1] >= L.n[1] || g[2] >= L.n[2])) {
+      // a ghost cell beyond an isolated boundary: the expansion at its centre
+      double x[3];
+      for (int a = 0; a < 3; ++a) x[a] = L.x0[a] + (g[a] + 0.5) * L.dx[a];
+      phi_pad[B.off + e] = mp_eval(mp, x);
+    } else {
+      phi_pad[B.off + e] = L.phi[wrap_idx(L, g[0], g[1], g[2])];
+    }
+  }
+}
+
+// full multigrid: the source of coarse cell (volume average of the children)
+__global__ void __launch_bounds__(GT) k_mg_restrict_src(Lev F, Lev C, double inv) {
+  const int r0 = F.n[0] / C.n[0], r1 = F.n[1] / C.n[1], r2 = F.n[2] / C.n[2];
+  const unsigned n = (unsigned)C.n[0] * C.n[1] * C.n[2];
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    int I, J, K;
+    decompose(C, c, I, J, K);
+    double sd = 0.0;
+    for (int cz = 0; cz < r2; ++cz)
+      for (int by = 0; by < r1; ++by)
+        for (int ax = 0; ax < r0; ++ax) sd += F.src[lin(F, r0 * I + ax, r1 * J + by, r2 * K + cz)];
+    C.src[c] = sd * inv;
+  }
+}
+
+// the solution's value at coarse cell u, beyond isolated faces by repeated
+// mirror images (2 phi_face - phi_inside per face crossed; a face of a cell
+// outside the grid in another direction takes the expansion directly)
+__device__ double full_value(const Lev &C, const MP &mp, int u0, int u1, int u2) {
+  int u[3] = {u0, u1, u2};
+  if (!C.iso) return C.phi[wrap_idx(C, u[0], u[1], u[2])];
+  double acc = 0.0, sg = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    if (u[a] >= 0 && u[a] < C.n[a]) continue;
+    const int side = u[a] < 0 ? 0 : 1;
+    u[a] = u[a] < 0 ? -1 - u[a] : 2 * C.n[a] - 1 - u[a];
+    bool in = true;
+    for (int b = 0; b < 3; ++b)
+      if (u[b] < 0 || u[b] >= C.n[b]) in = false;
+    double g;
+    if (in) {
+      g = face_phi(C, a, side, u);
+    } else {
+      double x[3];
+      for (int b = 0; b < 3; ++b) x[b] = C.x0[b] + (u[b] + 0.5) * C.dx[b];
+      x[a] += (side ? 0.5 : -0.5) * C.dx[a];
+      g = mp_eval(mp, x);
+    }
+    acc = fma(sg, 2.0 * g, acc);
+    sg = -sg;
+  }
+  return fma(sg, C.phi[lin(C, u[0], u[1], u[2])], acc);
+}
+
+// full multigrid: F.phi = P phi_C (the solution itself, trilinear)
+__global__ void __launch_bounds__(GT) k_mg_prolong_full(Lev F, Lev C, MP mp) {
+  const unsigned n = (unsigned)F.n[0] * F.n[1] * F.n[2];
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    int f[3];
+    decompose(F, c, f[0], f[1], f[2]);
+    int p[3], q[3];
+    bool h[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      h[a] = F.n[a] != C.n[a];
+      p[a] = h[a] ? f[a] >> 1 : f[a];
+      q[a] = h[a] ? ((f[a] & 1) ? p[a] + 1 : p[a] - 1) : p[a];
+    }
+    const int nh = (int)h[0] + (int)h[1] + (int)h[2];
+    const double scale = nh == 3 ? 1.0 / 64.0 : (nh == 2 ? 1.0 / 16.0 : (nh == 1 ? 0.25 : 1.0));
+    double s = 0.0;
+    for (int cz = 0; cz < 2; ++cz)
+      for (int by = 0; by < 2; ++by)
+        for (int ax = 0; ax < 2; ++ax) {
+          if ((ax && !h[0]) || (by && !h[1]) || (cz && !h[2])) continue;
+          const int np = (h[0] && !ax) + (h[1] && !by) + (h[2] && !cz);
+          const double w = np == 3 ? 27.0 : (np == 2 ? 9.0 : (np == 1 ? 3.0 : 1.0));
+          s = fma(w, full_value(C, mp, ax ? q[0] : p[0], by ? q[1] : p[1], cz ? q[2] : p[2]), s);
+        }
+    F.phi[c] = scale * s;
+  }
+}
+
+// isolated single-cell level: its equation solved exactly
+__global__ void k_mg_exact1(Lev L) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) L.phi[0] = gs_iso(L, 0, 0, 0);
+}
+
+// partial sums per CTA of (S, S x, S y, S z) over level 0 (the centroid)
+__global__ void __launch_bounds__(GT) k_mp_centroid(Lev L, double *part) {
+  __shared__ double red[4][GT / 32];
+  const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    int i, j, k;
+    decompose(L, c, i, j, k);
+    const double S = L.src[c];
+    s[0] += S;
+    s[1] += S * (L.x0[0] + (i + 0.5) * L.dx[0]);
+    s[2] += S * (L.x0[1] + (j + 0.5) * L.dx[1]);
+    s[3] += S * (L.x0[2] + (k + 0.5) * L.dx[2]);
+  }
+  for (int q = 0; q < 4; ++q) {
+    double v = s[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < GT / 32; ++w) t += red[threadIdx.x][w];
+    part[4 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// the centroid from the partial sums (fixed order; the domain centre for a
+// source summing to zero)
+__global__ void k_mp_centre(const double *__restrict__ part, int np, Lev L, double *cc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < np; ++b)
+    for (int q = 0; q < 4; ++q) t[q] += part[4 * b + q];
+  for (int a = 0; a < 3; ++a) cc[a] = t[0] != 0.0 ? t[1 + a] / t[0] : L.x0[a] + 0.5 * L.n[a] * L.dx[a];
+}
+
+// partial moments per CTA: sum S dV R_l^m(x - c), 2 MP_NC values
+template <int LM>
+__global__ void __launch_bounds__(GT) k_mp_moments(Lev L, const double *__restrict__ cc, double *part) {
+  constexpr int NC = (LM + 1) * (LM + 2) / 2;
+  __shared__ double red[2 * NC][GT / 32];
+  const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
+  const double dV = L.dx[0] * L.dx[1] * L.dx[2];
+  double acc[2 * NC];
+#pragma unroll
+  for (int q = 0; q < 2 * NC; ++q) acc[q] = 0.0;
+  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
+    const double S = L.src[c];
+    if (S == 0.0) continue;
+    int i, j, k;
+    decompose(L, c, i, j, k);
+    const double d[3] = {L.x0[0] + (i + 0.5) * L.dx[0] - cc[0], L.x0[1] + (j + 0.5) * L.dx[1] - cc[1],
+                         L.x0[2] + (k + 0.5) * L.dx[2] - cc[2]};
+    double R[2 * MP_NC];
+    solid_harmonics(LM, d, R);
+    const double w = S * dV;
+#pragma unroll
+    for (int q = 0; q < 2 * NC; ++q) acc[q] = fma(w, R[q], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 2 * NC; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * NC; q += GT) {
+    double t = 0.0;
+    for (int w = 0; w < GT / 32; ++w) t += red[q][w];
+    part[2 * MP_NC * blockIdx.x + q] = t;
+  }
+}
+
+// coefficients (A_lm, B_lm) = (2 - delta_m0) (l-m)! / (l+m)! / (4 pi) x the moments
+__global__ void k_mp_coef(const double *__restrict__ part, int np, int lmax, double *cc) {
+  const int q = threadIdx.x;
+  if (q >= 2 * MP_NC) return;
+  const int pair = q >> 1;
+  int l = 0;
+  while ((l + 1) * (l + 2) / 2 <= pair) ++l;
+  const int m = pair - l * (l + 1) / 2;
+  double t = 0.0;
+  for (int b = 0; b < np; ++b) t += part[2 * MP_NC * b + q];
+  double f = (m ? 2.0 : 1.0) / (4.0 * M_PI);
+  for (int v = l - m + 1; v <= l + m; ++v) f /= v;   // (l-m)! / (l+m)!
+  cc[3 + q] = l <= lmax ? t * f : 0.0;
+}
+
+// phi on the boundary faces of every level
+struct FaceJob {
+  Lev L;
+  int start[7];   // entries of the faces x-, x+, ..., z+ of this level
+};
+__global__ void __launch_bounds__(GT) k_mp_faces(FaceJob job, MP mp, double *out) {
+  const Lev &L = job.L;
+  for (int e = blockIdx.x * GT + threadIdx.x; e < job.start[6]; e += gridDim.x * GT) {
+    int f = 0;
+    while (e >= job.start[f + 1]) ++f;
+    const int a = f >> 1, side = f & 1;
+    const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+    const int r = e - job.start[f];
+    int c[3];
+    c[t1] = r % L.n[t1];
+    c[t2] = r / L.n[t1];
+    c[a] = side ? L.n[a] - 1 : 0;
+    double x[3];
+    for (int b = 0; b < 3; ++b) x[b] = L.x0[b] + (c[b] + 0.5) * L.dx[b];
+    x[a] += (side ? 0.5 : -0.5) * L.dx[a];
+    out[e] = mp_eval(mp, x);
   }
 }
 
@@ -245,11 +635,16 @@ struct GravState {
   long long launches = 0;   // kernels launched since the last count (for the profile)
   cudaGraphExec_t cycle = nullptr;   // one V-cycle + the extra sweep + the defect norm
   int cycle_launches = 0;
-  double cycle_key[4] = {0, 0, 0, 0};  // npre, npost, omega the graph was captured with
+  double cycle_key[5] = {0, 0, 0, 0, 0};  // npre, npost, omega, 1, boundary the graph was captured with
   int nl = 0;
+  int iso = -1;             // boundary kind the level weights were set for
   Lev lev[40];
   double *part = nullptr, *scal = nullptr;   // partial sums; [0] mean, [1] defect
   int npart = 0;
+  double *faces = nullptr;  // isolated: phi on the boundary faces of every level
+  int face_start[40][7];
+  double *mp = nullptr;     // centre (3) + coefficients (2 MP_NC)
+  double *mpart = nullptr;  // partial moments, 2 MP_NC per CTA
 };
 
 static void grav_free(GravState *g) {
@@ -262,6 +657,9 @@ static void grav_free(GravState *g) {
   }
   cudaFree(g->part);
   cudaFree(g->scal);
+  cudaFree(g->faces);
+  cudaFree(g->mp);
+  cudaFree(g->mpart);
   delete g;
 }
 
@@ -272,18 +670,15 @@ void gravity_release(tde_mesh *m) {
   m->d_phi_sg = nullptr;
 }
 
-static cudaError_t grav_init(tde_mesh *m) {
-  if (m->grav) return cudaSuccess;
-  GravState *g = new GravState;
-  int n[3] = {m->phys.N[0], m->phys.N[1], m->phys.N[2]};
-  double h[3] = {m->phys.dx[0], m->phys.dx[1], m->phys.dx[2]};
-  cudaError_t err = cudaSuccess;
-  for (;;) {
-    Lev &L = g->lev[g->nl++];
-    for (int a = 0; a < 3; ++a) { L.n[a] = n[a]; L.dx[a] = h[a]; }
+// the operator's weights of every level for the boundary kind
+static void set_weights(GravState *g, const Phys &p, int iso) {
+  for (int l = 0; l < g->nl; ++l) {
+    Lev &L = g->lev[l];
+    const double *h = L.dx;
     double w[3], wsum = 0.0;
     for (int a = 0; a < 3; ++a) {
-      w[a] = n[a] > 1 ? (h[0] / h[a]) * (h[0] / h[a]) : 0.0;
+      const bool on = iso ? p.N[a] > 1 : L.n[a] > 1;
+      w[a] = on ? (h[0] / h[a]) * (h[0] / h[a]) : 0.0;
       wsum += w[a];
     }
     const double diag = 2.0 * wsum;
@@ -292,6 +687,30 @@ static cudaError_t grav_init(tde_mesh *m) {
       L.cw[a] = diag > 0.0 ? w[a] / diag : 0.0;
     }
     L.cs = diag > 0.0 ? h[0] * h[0] / diag : 0.0;
+    L.iso = iso;
+    for (int f = 0; f < 6; ++f) L.gf[f] = iso ? g->faces + g->face_start[l][f] : nullptr;
+  }
+  g->iso = iso;
+}
+
+static cudaError_t grav_init(tde_mesh *m) {
+  if (m->grav) return cudaSuccess;
+  GravState *g = new GravState;
+  int n[3] = {m->phys.N[0], m->phys.N[1], m->phys.N[2]};
+  double h[3] = {m->phys.dx[0], m->phys.dx[1], m->phys.dx[2]};
+  cudaError_t err = cudaSuccess;
+  int nface = 0;
+  for (;;) {
+    Lev &L = g->lev[g->nl];
+    for (int a = 0; a < 3; ++a) { L.n[a] = n[a]; L.dx[a] = h[a]; L.x0[a] = m->phys.xmin[a]; }
+    int *fs = g->face_start[g->nl];
+    fs[0] = nface;
+    for (int f = 0; f < 6; ++f) {
+      const int a = f >> 1, t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+      nface += m->phys.N[a] > 1 ? n[t1] * n[t2] : 0;
+      fs[f + 1] = nface;
+    }
+    ++g->nl;
     const size_t nc = (size_t)n[0] * n[1] * n[2];
     L.phi = L.src = L.tmp = nullptr;
     if (err == cudaSuccess) err = cudaMalloc(&L.phi, sizeof(double) * nc);
@@ -303,10 +722,14 @@ static cudaError_t grav_init(tde_mesh *m) {
       if (n[a] > 1) { n[a] /= 2; h[a] *= 2.0; }
   }
   g->npart = (int)grid_for((long long)m->phys.N[0] * m->phys.N[1] * m->phys.N[2]);
-  if (err == cudaSuccess) err = cudaMalloc(&g->part, sizeof(double) * g->npart);
+  if (err == cudaSuccess) err = cudaMalloc(&g->part, sizeof(double) * 4 * g->npart);
   if (err == cudaSuccess) err = cudaMalloc(&g->scal, sizeof(double) * 2);
+  if (err == cudaSuccess) err = cudaMalloc(&g->faces, sizeof(double) * std::max(nface, 1));
+  if (err == cudaSuccess) err = cudaMalloc(&g->mp, sizeof(double) * (3 + 2 * MP_NC));
+  if (err == cudaSuccess) err = cudaMalloc(&g->mpart, sizeof(double) * 2 * MP_NC * g->npart);
   if (err == cudaSuccess && !m->d_phi_sg) err = cudaMalloc(&m->d_phi_sg, sizeof(double) * m->ntot);
   if (err == cudaSuccess) err = cudaMemset(m->d_phi_sg, 0, sizeof(double) * m->ntot);
+  if (err == cudaSuccess) err = cudaMemset(g->mp, 0, sizeof(double) * (3 + 2 * MP_NC));
   if (err != cudaSuccess) {
     grav_free(g);
     return err;
@@ -332,7 +755,14 @@ static void smooth(GravState *g, const Lev &L, double omega, cudaStream_t s) {
 }
 
 static void vcycle(GravState *g, int l, const tde_grav_params &gp, cudaStream_t s) {
-  if (l == g->nl - 1) return;   // a single cell: the periodic correction is zero
+  if (l == g->nl - 1) {
+    // a single cell: periodic, the correction is zero; isolated, solved exactly
+    if (g->iso) {
+      k_mg_exact1<<<1, 32, 0, s>>>(g->lev[l]);
+      g->launches += 1;
+    }
+    return;
+  }
   const Lev &F = g->lev[l], &C = g->lev[l + 1];
   for (int q = 0; q < gp.npre; ++q) smooth(g, F, gp.omega, s);
   const long long nc = (long long)C.n[0] * C.n[1] * C.n[2];
@@ -346,23 +776,79 @@ static void vcycle(GravState *g, int l, const tde_grav_params &gp, cudaStream_t 
   for (int q = 0; q < gp.npost; ++q) smooth(g, F, gp.omega, s);
 }
 
+// isolated: the centroid, the moments, and phi on every level's boundary faces
+static void multipole_setup(GravState *g, int lmax, cudaStream_t s) {
+  const Lev &L0 = g->lev[0];
+  const long long n0 = (long long)L0.n[0] * L0.n[1] * L0.n[2];
+  const unsigned gr = std::min<unsigned>(grid_for(n0), (unsigned)g->npart);
+  k_mp_centroid<<<gr, GT, 0, s>>>(L0, g->part);
+  k_mp_centre<<<1, 32, 0, s>>>(g->part, (int)gr, L0, g->mp);
+  switch (lmax) {
+    case 0: k_mp_moments<0><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
+    case 1: k_mp_moments<1><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
+    case 2: k_mp_moments<2><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
+    case 3: k_mp_moments<3><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
+    default: k_mp_moments<4><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
+  }
+  k_mp_coef<<<1, 64, 0, s>>>(g->mpart, (int)gr, lmax, g->mp);
+  const MP mp{lmax, g->mp};
+  for (int l = 0; l < g->nl; ++l) {
+    FaceJob job;
+    job.L = g->lev[l];
+    for (int f = 0; f < 7; ++f) job.start[f] = g->face_start[l][f] - g->face_start[l][0];
+    if (job.start[6] == 0) continue;
+    k_mp_faces<<<grid_for(job.start[6]), GT, 0, s>>>(job, mp, g->faces + g->face_start[l][0]);
+    g->launches += 1;
+  }
+  g->launches += 4;
+}
+
+// full multigrid: the source on every level, the coarsest solved, then per finer
+// level the prolonged solution and one V-cycle (the extra sweep on the finest)
+static void full_multigrid(GravState *g, const tde_grav_params &gp, int lmax, cudaStream_t s) {
+  for (int l = 1; l < g->nl; ++l) {
+    const Lev &F = g->lev[l - 1], &C = g->lev[l];
+    const long long nc = (long long)C.n[0] * C.n[1] * C.n[2];
+    k_mg_restrict_src<<<grid_for(nc), GT, 0, s>>>(F, C, (double)nc / ((double)F.n[0] * F.n[1] * F.n[2]));
+    g->launches += 1;
+  }
+  cudaMemsetAsync(g->lev[g->nl - 1].phi, 0, sizeof(double), s);
+  vcycle(g, g->nl - 1, gp, s);
+  const MP mp{lmax, g->mp};
+  for (int l = g->nl - 2; l >= 0; --l) {
+    const Lev &F = g->lev[l];
+    k_mg_prolong_full<<<grid_for((long long)F.n[0] * F.n[1] * F.n[2]), GT, 0, s>>>(F, g->lev[l + 1], mp);
+    g->launches += 1;
+    vcycle(g, l, gp, s);
+    if (l == 0) smooth(g, F, gp.omega, s);
+  }
+}
+
 cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, double *defect) {
   tde_ctx *c = m->ctx;
   cudaStream_t s = c->stream;
   cudaError_t err = grav_init(m);
   if (err != cudaSuccess) return err;
   GravState *g = reinterpret_cast<GravState *>(m->grav);
+  const int iso = gp.boundary == TDE_GRAV_ISOLATED ? 1 : 0;
+  if (g->iso != iso) set_weights(g, m->phys, iso);
   Lev &L0 = g->lev[0];
   const long long n0 = (long long)L0.n[0] * L0.n[1] * L0.n[2];
   {
     ProfScope ps(c, TDE_K_GRAV, false);
     dim3 grid((unsigned)std::min<int64_t>((m->max_interior + GT - 1) / GT, 64), (unsigned)m->nb);
     k_mg_gather<<<grid, GT, 0, s>>>(m->phys, m->d_blocks, m->U, L0, 4.0 * M_PI * gp.G, gp.rho_min);
-    if (!gp.warm) cudaMemsetAsync(L0.phi, 0, sizeof(double) * n0, s);
-    for (int pass = 0; pass < 2; ++pass) {   // the source's mean, removed in two passes
-      reduce(g, L0, 0, g->scal, s);
-      k_mg_sub_mean<<<grid_for(n0), GT, 0, s>>>(L0, g->scal);
+    if (!gp.warm || gp.fmg) cudaMemsetAsync(L0.phi, 0, sizeof(double) * n0, s);
+    if (iso) {
+      multipole_setup(g, gp.lmax, s);
+    } else {
+      for (int pass = 0; pass < 2; ++pass) {   // the source's mean, removed in two passes
+        reduce(g, L0, 0, g->scal, s);
+        k_mg_sub_mean<<<grid_for(n0), GT, 0, s>>>(L0, g->scal);
+      }
+      g->launches += 2;
     }
+    if (gp.fmg) full_multigrid(g, gp, gp.lmax, s);
   }
   int ncyc = 0;
   double d = 0.0;
@@ -372,7 +858,7 @@ cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, d
   }
   // one cycle (V-cycle, the extra fine sweep, the defect norm) as a CUDA graph:
   // about a hundred small launches on the coarse levels replayed as one
-  const double key[4] = {(double)gp.npre, (double)gp.npost, gp.omega, 1.0};
+  const double key[5] = {(double)gp.npre, (double)gp.npost, gp.omega, 1.0, (double)iso};
   if (g->cycle && memcmp(key, g->cycle_key, sizeof key) != 0) {
     cudaGraphExecDestroy(g->cycle);
     g->cycle = nullptr;
@@ -420,9 +906,10 @@ cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, d
   {
     ProfScope ps(c, TDE_K_GRAV, false);
     dim3 grid((unsigned)std::min<int64_t>((m->max_interior + GT - 1) / GT, 64), (unsigned)m->nb);
-    k_mg_scatter<<<grid, GT, 0, s>>>(m->phys, m->d_blocks, L0, m->d_phi_sg);
+    const MP mp{gp.lmax, g->mp};
+    k_mg_scatter<<<grid, GT, 0, s>>>(m->phys, m->d_blocks, L0, mp, m->d_phi_sg);
   }
-  g->launches += 4;   // gather, scatter and the two mean subtractions (the rest count at launch)
+  g->launches += 2;   // gather and scatter (the rest count at launch)
   c->launches[TDE_K_GRAV] += g->launches;
   g->launches = 0;
   if (cycles) *cycles = ncyc;

@@ -21,6 +21,7 @@ BC_OUTFLOW, BC_PERIODIC = 0, 1
 RIEMANN_HLLC, RIEMANN_HLLE = 0, 1
 INVERT_BISECT, INVERT_SURROGATE, INVERT_BISECT_PLAIN = 0, 1, 2
 REMAP_THERMAL, REMAP_TOTAL = 0, 1
+GRAV_PERIODIC, GRAV_ISOLATED = 0, 1
 STATUS = {0: "TDE_OK", 1: "TDE_EINVAL", 2: "TDE_ENOMEM", 3: "TDE_ECUDA", 4: "TDE_ERANGE",
           5: "TDE_ENUMERIC", 6: "TDE_ETIMEOUT"}
 
@@ -47,7 +48,8 @@ class BHState(C.Structure):
 
 class GravParams(C.Structure):
     _fields_ = [("G", C.c_double), ("rho_min", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("npre", C.c_int), ("npost", C.c_int), ("omega", C.c_double), ("warm", C.c_int)]
+                ("npre", C.c_int), ("npost", C.c_int), ("omega", C.c_double), ("warm", C.c_int),
+                ("boundary", C.c_int), ("lmax", C.c_int), ("fmg", C.c_int)]
 
 
 class BlockDesc(C.Structure):
@@ -421,9 +423,11 @@ class Mesh:
         self.ctx.check(lib().tde_frame_acceleration(self.h, C.byref(bh), rho_min, A, C.byref(mass)))
         return list(A), mass.value
 
-    def gravity_solve(self, G, rho_min, tol=1e-10, max_cycles=20, npre=2, npost=2, omega=1.15, warm=True):
+    def gravity_solve(self, G, rho_min, tol=1e-10, max_cycles=20, npre=2, npost=2, omega=1.15, warm=True,
+                      isolated=False, lmax=4, fmg=False):
         """Self-gravity potential from the bound state's density; returns (cycles, rms defect)."""
-        gp = GravParams(G, rho_min, tol, max_cycles, npre, npost, omega, 1 if warm else 0)
+        gp = GravParams(G, rho_min, tol, max_cycles, npre, npost, omega, 1 if warm else 0,
+                        GRAV_ISOLATED if isolated else GRAV_PERIODIC, lmax, 1 if fmg else 0)
         n, d = C.c_int(), C.c_double()
         self.ctx.check(lib().tde_gravity_solve(self.h, C.byref(gp), C.byref(n), C.byref(d)))
         return n.value, d.value

@@ -122,3 +122,104 @@ def test_gravity_needs_periodic_power_of_two(tde, ctx):
     assert ei.value.code == tde.TDE_EINVAL
     with pytest.raises(tde.TDEError):
         m.gravity_enable(True)
+
+
+# ------------------------------------------- isolated boundaries and FMG ----
+
+def isolated_pair(oracle, tde, ctx, n=32, **scheme):
+    lay = wl.uniform_layout((n, n, n), (16, 16, 16), domain=((-1, 1),) * 3, bc=(0, 0, 0), ng=2)
+    x, y, z = lay.cell_centres()
+    rho = (1e-3 + np.exp(-((x - 0.2) ** 2 + (y + 0.1) ** 2 + (z - 0.05) ** 2) / (2 * 0.15 ** 2)) +
+           0.6 * np.exp(-((x + 0.25) ** 2 + (y - 0.2) ** 2 + (z + 0.1) ** 2) / (2 * 0.1 ** 2)))
+    W = wl.prim_state(lay, rho, 0.0, 0.0, 0.0, 0.1 * rho)
+    return Pair(oracle, tde, ctx, lay, W, **scheme)
+
+
+def oracle_phi_iso(oracle, P, cycles, fmg, lmax=4, rho_min=0.0):
+    rho = P.layout.to_global(P.U)[0]
+    S = np.where(rho > rho_min, -4.0 * np.pi * G * rho, 0.0)
+    return oracle.mg_solve_bc(S, list(P.layout.dx), xmin=P.layout.xmin, isolated=True, lmax=lmax, fmg=fmg,
+                              max_cycles=cycles, tol=0.0)
+
+
+@pytest.mark.parametrize("fmg", [False, True])
+def test_isolated_multigrid_matches_oracle_cycle_for_cycle(oracle, tde, ctx, fmg):
+    P = isolated_pair(oracle, tde, ctx)
+    for cycles in (0, 1, 3) if fmg else (1, 3):
+        n, d = P.gm.gravity_solve(G, 0.0, tol=0.0, max_cycles=cycles, warm=False, isolated=True, lmax=4, fmg=fmg)
+        phi_o, _, d_o, _, _ = oracle_phi_iso(oracle, P, cycles, fmg)
+        phi_g = P.gm.gravity_phi().cpu().numpy()
+        assert n == cycles
+        assert np.allclose(phi_g, phi_o, rtol=0, atol=1e-12 * np.abs(phi_o).max()), cycles
+        assert d == pytest.approx(d_o, rel=1e-7)
+
+
+def test_isolated_full_multigrid_convergence(oracle, tde, ctx):
+    """From the full-multigrid start a handful of V-cycles reach 1e-12 of the
+    source's scale (the paper: five V-cycles to 1e-12, contraction about 0.1)."""
+    P = isolated_pair(oracle, tde, ctx, n=64)
+    n0, d0 = P.gm.gravity_solve(G, 0.0, tol=0.0, max_cycles=0, warm=False, isolated=True, fmg=True)
+    n, d = P.gm.gravity_solve(G, 0.0, tol=1e-12, max_cycles=30, warm=False, isolated=True, fmg=True)
+    print("isolated 64^3: defect after FMG %.2e, %d V-cycles to %.2e" % (d0, n, d))
+    assert d < 1e-12 and n <= 9
+
+
+def test_steps_with_isolated_self_gravity(oracle, tde, ctx):
+    """The hydro stage with the isolated potential, ghosts beyond the outflow
+    boundary taking the expansion at their centres, against the oracle."""
+    P = isolated_pair(oracle, tde, ctx, dual=1, eta1=1e-3, eta2=1e-4)
+    P.gm.gravity_solve(G, 0.0, tol=0.0, max_cycles=8, warm=False, isolated=True, fmg=True)
+    P.gm.gravity_enable(True)
+    lay = P.layout
+    # the oracle's padded potential: interior and in-domain ghosts from the solve,
+    # ghosts beyond the boundary from the expansion
+    ghosts = []
+    for b in range(lay.nb):
+        i0, j0, k0, nx, ny, nz = lay.blocks[b]
+        px, py, pz = lay.pd[b]
+        k, j, i = np.meshgrid(np.arange(pz), np.arange(py), np.arange(px), indexing="ij")
+        gi, gj, gk = i0 + i - 2, j0 + j - 2, k0 + k - 2
+        out = (gi < 0) | (gj < 0) | (gk < 0) | (gi >= lay.N[0]) | (gj >= lay.N[1]) | (gk >= lay.N[2])
+        flat = lay.off[b] + (k * py + j) * px + i
+        xs = np.stack([lay.xmin[0] + (gi + 0.5) * lay.dx[0], lay.xmin[1] + (gj + 0.5) * lay.dx[1],
+                       lay.xmin[2] + (gk + 0.5) * lay.dx[2]], axis=-1)
+        ghosts.append((flat[out], xs[out]))
+    gq = np.concatenate([g[1] for g in ghosts])
+    rho = lay.to_global(P.U)[0]
+    phi_o, _, _, _, phiq = oracle.mg_solve_bc(-4.0 * np.pi * G * rho, list(lay.dx), xmin=lay.xmin, isolated=True,
+                                              lmax=4, fmg=True, max_cycles=8, tol=0.0, query=gq)
+    A = padded(oracle, P, phi_o)
+    A[np.concatenate([g[0] for g in ghosts])] = phiq
+    P.om.set_phi_sg(A)
+    U = P.U.copy()
+    for _ in range(3):
+        d = P.om.cfl_dt(U, 0.3).min()
+        P.om.step(U, d, 0.0)
+        P.gm.step(cfl=0.3)
+    assert_parity(lay.to_global(P.gpu("U")), lay.to_global(U), STEPS_TOL, "isolated self-gravity steps")
+
+
+def test_isolated_argument_checks(tde, ctx):
+    lay = wl.uniform_layout((16, 16, 16), (8, 8, 8), bc=(0, 0, 0), ng=2)
+    m = tde.Mesh(ctx, lay, tde.make_params())
+    with pytest.raises(tde.TDEError):
+        m.gravity_solve(G, 0.0, isolated=True, lmax=5)
+    m.gravity_solve(G, 0.0, isolated=True, lmax=2, max_cycles=2)   # outflow mesh, isolated: fine
+    lay = wl.uniform_layout((24, 16, 16), (8, 8, 8), bc=(0, 0, 0), ng=2)
+    m = tde.Mesh(ctx, lay, tde.make_params())
+    with pytest.raises(tde.TDEError):
+        m.gravity_solve(G, 0.0, isolated=True)   # 24 is not a power of two
+
+
+def test_isolated_two_dimensional_grid(oracle, tde, ctx):
+    """A one-cell-thick grid (z inactive: no faces, no weight along z) against the oracle."""
+    lay = wl.uniform_layout((32, 32, 1), (16, 16, 1), domain=((-1, 1), (-1, 1), (0, 0.0625)), bc=(0, 0, 0), ng=2)
+    x, y, z = lay.cell_centres()
+    rho = 1e-3 + np.exp(-((x - 0.2) ** 2 + (y + 0.1) ** 2) / (2 * 0.2 ** 2))
+    P = Pair(oracle, tde, ctx, lay, wl.prim_state(lay, rho, 0.0, 0.0, 0.0, 0.1 * rho))
+    for fmg, cycles in ((True, 0), (True, 2), (False, 3)):
+        n, d = P.gm.gravity_solve(G, 0.0, tol=0.0, max_cycles=cycles, warm=False, isolated=True, lmax=3, fmg=fmg)
+        phi_o, _, d_o, _, _ = oracle_phi_iso(oracle, P, cycles, fmg, lmax=3)
+        phi_g = P.gm.gravity_phi().cpu().numpy()
+        assert np.allclose(phi_g, phi_o, rtol=0, atol=1e-12 * np.abs(phi_o).max())
+        assert d == pytest.approx(d_o, rel=1e-7)
