@@ -821,9 +821,10 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
     ncell = lay.ncells
     del mesh, U0
     torch.cuda.empty_cache()
-    return {"workload": "stretched n=1.5 polytrope (1 Msun, 1 Rsun, 4:1) passing a moving 1e3 Msun point "
-                        "mass with excision, 2048 x 32^3 MeshBlocks, PPM+HLLC, Saha table, learned-guess "
-                        "closure, dual energy, Table 1 floors, N_LAT 6",
+    return {"workload": "stretched n=1.5 polytrope (1 Msun, 1 Rsun, 4:1) in its own frame, a 1e3 Msun point "
+                        "mass with excision passing at the parabolic speed through free-falling ambient gas, "
+                        "2048 x 32^3 MeshBlocks, PPM+HLLC, Saha table, learned-guess closure, dual energy, "
+                        "floors 100x Table 1's, N_LAT 6",
             "cells": ncell, "meshblocks": lay.nb, "f_max": int(fmax), "blocks_per_factor": levels,
             "work_fraction": work, "windows": nwin, "fine_steps": nwin * int(fmax),
             "autotune": autotune_report(tiles, tile_ms),
