@@ -263,7 +263,7 @@ def run_gpu(args):
         if not args.no_grav:
             line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
         if not args.no_remap:
-            line["remap"] = remap_bench(ctx, tde, torch, dev, args)
+            line["remap"] = remap_bench(ctx, tde, torch, dev, args, n=args.remap_n)
         if not args.no_smr:
             line["lat_refined"] = smr_bench(ctx, tde, torch, dev, args)
         if not args.no_lat:
@@ -920,6 +920,7 @@ def main():
     ap.add_argument("--no-c5", action="store_true", help="skip the production-shaped LAT run")
     ap.add_argument("--no-grav", action="store_true", help="skip the self-gravity multigrid")
     ap.add_argument("--no-remap", action="store_true", help="skip the domain remap")
+    ap.add_argument("--remap-n", type=int, default=256, help="source grid of the remap section (n^3)")
     ap.add_argument("--no-smr", action="store_true", help="skip LAT on the refined blast-wave mesh")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
