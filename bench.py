@@ -881,9 +881,22 @@ def cpu_baseline(seconds):
         if el >= seconds:
             break
     cells = n * len(ids) * BLOCK ** 3
-    return {"value": cells / el, "unit": UNIT, "cores": tref.num_threads(), "kind": "oracle",
+    cores = tref.num_threads()
+    # the same sample on one thread, for a third of the time
+    tref.set_num_threads(1)
+    n1, t1 = 0, time.perf_counter()
+    while True:
+        oracle_step(tref, m, U, S, ids, lay)
+        n1 += 1
+        el1 = time.perf_counter() - t1
+        if el1 >= seconds / 3.0:
+            break
+    tref.set_num_threads(cores)
+    return {"value": cells / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d RK2 steps of %d of the 64 MeshBlocks (32^3) of the workload, %.1f s" %
-                      (n, len(ids), el)}
+                      (n, len(ids), el),
+            "single_thread": {"value": n1 * len(ids) * BLOCK ** 3 / el1, "unit": UNIT, "steps": n1,
+                              "seconds": el1}}
 
 
 def run_reference(args):

@@ -126,6 +126,7 @@ int64_t tref_mesh_ntot(const tref_mesh *m);            /* padded cells of all bl
 int64_t tref_mesh_block_offset(const tref_mesh *m, int b);
 int tref_nvar(const tref_mesh *m);
 int tref_num_threads(void);   /* OpenMP threads of the block loops */
+void tref_set_num_threads(int n);
 void tref_set_params(tref_mesh *m, const tref_params *p);
 
 /* a1: fill the ghost cells of the listed blocks (all blocks if ids == NULL) from

@@ -112,6 +112,7 @@ def lib():
             "tref_mesh_free": (None, [C.c_void_p]),
             "tref_mesh_ntot": (C.c_int64, [C.c_void_p]),
             "tref_mesh_block_offset": (C.c_int64, [C.c_void_p, C.c_int]),
+            "tref_set_num_threads": (None, [C.c_int]),
             "tref_nvar": (C.c_int, [C.c_void_p]),
             "tref_set_params": (None, [C.c_void_p, C.POINTER(Params)]),
             "tref_ghost_fill": (None, [C.c_void_p, dp, C.c_int, C.c_int, ip]),
@@ -364,6 +365,10 @@ def mlp_loss_grad(params, x, target):
     loss = lib().tref_mlp_loss_grad(P(np.ascontiguousarray(params, dtype=np.float64)), len(x),
                                     P(x), P(t), P(g))
     return loss, g
+
+
+def set_num_threads(n):
+    lib().tref_set_num_threads(int(n))
 
 
 def num_threads():

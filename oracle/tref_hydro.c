@@ -206,6 +206,14 @@ int tref_num_threads(void) {
   return 1;
 #endif
 }
+/* Threads of the block loops from now on (n >= 1; no effect without OpenMP). */
+void tref_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
 void tref_set_params(tref_mesh *m, const tref_params *p) { m->p = *p; }
 
 static int gofs(const tref_mesh *m, int a) { return m->active[a] ? m->d.ng : 0; }
