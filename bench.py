@@ -283,11 +283,11 @@ def run_gpu(args):
 # DRAM bytes of one launch; profiles/k_sweep_c2_entropy_wave_ncu.md holds the
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
 # False (traffic reported as null) whenever a sweep kernel changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 228.5, "sweep_y": 193.4, "sweep_z": 319.4}
-DRAM_BYTES_SWEEP = {"sweep_x": 266.6e6, "sweep_y": 399.3e6, "sweep_z": 543.4e6}
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 226.4, "sweep_y": 191.4, "sweep_z": 317.4}
+DRAM_BYTES_SWEEP = {"sweep_x": 266.6e6, "sweep_y": 400.9e6, "sweep_z": 542.8e6}
 # FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
 # holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
-FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 199.6, "sweep_y": 199.6, "sweep_z": 287.6}
+FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 201.9, "sweep_y": 201.9, "sweep_z": 289.9}
 KERNELS_AS_CAPTURED = True
 
 
