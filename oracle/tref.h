@@ -106,6 +106,8 @@ void tref_eos_build(int n_rho, int n_T, double lrho_min, double lrho_max, double
                     double *log10_cs2, double *gamma1);
 /* Bilinear evaluation at (rho, T) (cgs): out P, e, cs2. */
 void tref_eos_eval_rhoT(const tref_table *t, double rho, double T, double *P, double *e, double *cs2);
+void tref_eos_eval_rhoT_n(const tref_table *t, int64_t n, const double *rho, const double *T, double *P,
+                          double *e, double *cs2);
 /* Inversion (rho, e) -> (T, P, cs2), cgs.  Returns 1 if clamped to the table edge. */
 int tref_eos_invert(const tref_table *t, double rho, double e, double *T, double *P, double *cs2,
                     double *e_used);

@@ -104,6 +104,7 @@ def lib():
             "tref_eos_build": (None, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_double, dp, dp, dp, dp]),
             "tref_eos_eval_rhoT": (None, [C.POINTER(Table), C.c_double, C.c_double, dp, dp, dp]),
+            "tref_eos_eval_rhoT_n": (None, [C.POINTER(Table), C.c_int64, dp, dp, dp, dp, dp]),
             "tref_eos_invert": (C.c_int, [C.POINTER(Table), C.c_double, C.c_double, dp, dp, dp, dp]),
             "tref_eos_T_from_P": (C.c_double, [C.POINTER(Table), C.c_double, C.c_double]),
             "tref_eos_invert_guess": (C.c_int, [C.POINTER(Table), C.c_double, C.c_double, C.c_double,
@@ -190,6 +191,14 @@ class EOSTable:
         Pr, e, c2 = C.c_double(), C.c_double(), C.c_double()
         lib().tref_eos_eval_rhoT(C.byref(self.c), rho, T, C.byref(Pr), C.byref(e), C.byref(c2))
         return Pr.value, e.value, c2.value
+
+    def eval_rhoT_n(self, rho, T):
+        """(P, e, cs2) arrays at arrays (rho, T), cgs."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+        T = np.ascontiguousarray(T, dtype=np.float64).ravel()
+        out = [np.empty_like(rho) for _ in range(3)]
+        lib().tref_eos_eval_rhoT_n(C.byref(self.c), rho.size, P(rho), P(T), P(out[0]), P(out[1]), P(out[2]))
+        return out
 
     def invert_guess(self, rho, e, log10_T_guess):
         T, Pr, c2 = C.c_double(), C.c_double(), C.c_double()

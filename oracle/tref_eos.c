@@ -168,6 +168,19 @@ void tref_eos_eval_rhoT(const tref_table *t, double rho, double T, double *P, do
   *cs2 = pow(10.0, bilin(t->log10_cs2, t->n_T, i, w, j, s));
 }
 
+/* tref_eos_eval_rhoT on n cells (arrays; outputs may be NULL), OpenMP over cells. */
+void tref_eos_eval_rhoT_n(const tref_table *t, int64_t n, const double *rho, const double *T, double *P,
+                          double *e, double *cs2) {
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < n; ++q) {
+    double p, en, c2;
+    tref_eos_eval_rhoT(t, rho[q], T[q], &p, &en, &c2);
+    if (P) P[q] = p;
+    if (e) e[q] = en;
+    if (cs2) cs2[q] = c2;
+  }
+}
+
 int tref_eos_invert(const tref_table *t, double rho, double e, double *T, double *P, double *cs2,
                     double *e_used) {
   int i; double w;

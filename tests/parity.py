@@ -36,3 +36,41 @@ def assert_parity(G, O, tol, what=""):
     assert np.all(np.isfinite(G)), "non-finite GPU values " + what
     assert e.max() <= tol, "%s: per-variable max error %s > %g" % (what, e, tol)
     return e
+
+
+def stencil_scale(Uin_block, active, radius):
+    """Per interior cell and variable: the largest input magnitude within `radius`
+    cells (the reconstruction stencil) of a padded, ghost-filled block
+    [nvar, pz, py, px], for the momentum the largest sqrt(2 rho E).  A stage's
+    output is a combination of these inputs with coefficients of order one (the
+    time step obeys the CFL condition), so its rounding is a few ulps of this
+    scale: where inflow multiplies a cell's density by 1e4 in one stage, its own
+    value is the wrong yardstick."""
+    from scipy.ndimage import maximum_filter
+    U = np.abs(np.asarray(Uin_block, dtype=np.float64))
+    size = tuple((2 * radius + 1) if active[a] else 1 for a in (2, 1, 0))
+    sm = np.sqrt(2.0 * U[0] * U[4])
+    out = []
+    for v in range(U.shape[0]):
+        out.append(maximum_filter(sm if v in (1, 2, 3) else U[v], size=size, mode="nearest"))
+    return np.stack(out)
+
+
+def assert_parity_stencil(G, O, scale, tol, what=""):
+    """assert_parity with the denominators raised to `scale` (stencil_scale of the
+    stage's input, interior cells, same shape as G and O)."""
+    G = np.asarray(G, dtype=np.float64)
+    O = np.asarray(O, dtype=np.float64)
+    assert np.all(np.isfinite(G)), "non-finite GPU values " + what
+    rho, E = O[0], O[4]
+    own = np.sqrt(2.0 * np.abs(rho) * np.abs(E))
+    errs = []
+    for v in range(O.shape[0]):
+        den = np.maximum(own if v in (1, 2, 3) else np.abs(O[v]), scale[v])
+        d = np.abs(G[v] - O[v])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            e = np.where(d == 0, 0.0, d / den)
+        errs.append(float(np.max(e)) if e.size else 0.0)
+    errs = np.array(errs)
+    assert errs.max() <= tol, "%s: per-variable max error %s > %g" % (what, errs, tol)
+    return errs
