@@ -182,3 +182,29 @@ def test_refused_layouts(tde, ctx):
     m = tde.Mesh(ctx, lay, tde.make_params())
     with pytest.raises(tde.TDEError):
         m.hydro_stage(0, torch.ones(lay.nb, dtype=torch.float64, device="cuda"))
+
+
+def test_frame_reduction_and_excision_on_a_refined_mesh(oracle, tde, ctx):
+    """The frame acceleration (Eq. frame-acceleration) weighs each cell by its
+    volume; LAT windows with the point mass's excision sphere inside the finest
+    level; both against the oracle."""
+    lay = smr(bc=(0, 0, 0), r=0.12, centre=(0.5, 0.45, 0.5))
+    bh = dict(on=1, excise=1, GM=0.01, r_soft=0.04, r_exc=0.05, x0=(0.52, 0.45, 0.5), v0=(0.1, 0.0, 0.0))
+    P = Pair(oracle, tde, ctx, lay, smooth_W(lay, seed=9), bh=bh, dual=1, eta1=1e-3, eta2=1e-4,
+             rho_floor=1e-6, p_floor=1e-8, u_floor=1.5e-8)
+    P.gm.set_time(0.0)
+    Ao, mo = P.om.frame_acceleration(P.U, 0.0, 0.5)
+    Ag, mg = P.gm.frame_acceleration(P.bh, 0.5)
+    assert mg == pytest.approx(mo, rel=1e-13)
+    assert np.allclose(Ag, Ao, rtol=1e-12, atol=1e-14 * np.abs(Ao).max())
+    U = P.U.copy()
+    t = 0.0
+    for w in range(2):
+        dt = P.om.cfl_dt(U, 0.3, np.full(lay.nb, t))
+        f, dt0, fmax = P.om.lat_factors(dt, 3, 0.0)
+        P.gm.lat_set_factors(f, dt0)
+        P.om.lat_window(U, f, dt0, t)
+        P.gm.lat_window(bh=P.bh)
+        t += fmax * dt0
+    assert_parity(interior(lay, P.gpu("U")), interior(lay, U), 2e-11, "refined windows with excision")
+    assert P.gm.counts()["excised"] > 0

@@ -81,3 +81,28 @@ def test_noalloc_dt_with_point_mass_and_excision_then_size_limit(tde):
     with pytest.raises(tde.TDEError) as ei:
         tde.compute_dt_noalloc(ctx, big, params, mesh.U, 0.4, got)
     assert ei.value.code == tde.TDE_EINVAL and "4096" in str(ei.value)
+
+
+def test_noalloc_dt_on_a_refined_mesh(tde):
+    """Blocks on three refinement levels (cells dx / 2^level): the same per-block
+    CFL step as tde_compute_dt."""
+    ctx = tde.Context(0)
+    dev = torch.device("cuda", 0)
+
+    def ball(lo, hi, L):
+        c = (0.4, 0.5, 0.5)
+        return sum(max(lo[a] - c[a], 0.0, c[a] - hi[a]) ** 2 for a in range(3)) < 0.1 ** 2
+    lay = wl.smr_layout((16, 16, 16), (4, 4, 4), ((0, 1),) * 3, (1, 1, 1), 2, ball, 2)
+    assert lay.levels.max() == 2
+    params = tde.make_params(dual=1)
+    mesh = tde.Mesh(ctx, lay, params)
+    x, y, z, _ = lay.interior_centres()
+    W = wl.prim_cells(lay, 1.0 + 0.2 * np.sin(2 * np.pi * x), 0.3 * np.cos(2 * np.pi * y), 0.0, 0.1, 1.0)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    bh = tde.make_bh(on=1, excise=1, GM=0.05, r_soft=0.05, r_exc=0.08, x0=(0.4, 0.5, 0.5))
+    want = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
+    mesh.compute_dt(0.3, want, bh=bh)
+    got = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
+    tde.compute_dt_noalloc(ctx, lay, params, mesh.U, 0.3, got, bh=bh)
+    torch.cuda.synchronize()
+    assert np.allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-14, atol=0)
