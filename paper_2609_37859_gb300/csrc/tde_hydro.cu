@@ -134,6 +134,24 @@ __global__ void __launch_bounds__(NT) k_c2p_padded(Phys p, const DevBlock *__res
   }
 }
 
+// primitives of listed cells (LAT ghost cells whose conserved values were
+// interpolated in time, restricted or prolonged; nothing counted: ghost cells)
+template <int EOSK, int DUAL, int EOSB = 0>
+__global__ void __launch_bounds__(NT) k_c2p_list(Phys p, const int32_t *__restrict__ list, int n,
+                                                 const double *__restrict__ U, double *__restrict__ W,
+                                                 long long ntot, EOSBuf eb) {
+  for (int e = blockIdx.x * NT + threadIdx.x; e < n; e += gridDim.x * NT) {
+    const long long flat = list[e];
+    double u[6], w[8];
+#pragma unroll
+    for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
+    cons_to_prim<EOSK, DUAL, EOSB>(p, u, w, nullptr, &eb, flat);
+    constexpr int NWV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
+#pragma unroll
+    for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
+  }
+}
+
 // The table inputs (cgs rho, e) of the interior (PADDED = 0) or all padded
 // (PADDED = 1) cells of the listed blocks, by the same expressions as the
 // closure inside k_c2p, for the learned-guess inversion's launches; nothing is
@@ -155,6 +173,25 @@ __global__ void __launch_bounds__(NT) k_c2p_eosin(Phys p, const DevBlock *__rest
       const int j = r % B.n[1], k = r / B.n[1];
       flat = B.off + ((long long)(k + p.g[2]) * B.p[1] + (j + p.g[1])) * B.p[0] + (i + p.g[0]);
     }
+    double u[6];
+#pragma unroll
+    for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
+    double rho, vx, vy, vz, Ue;
+    c2p_energy<DUAL>(p, u, rho, vx, vy, vz, Ue, nullptr);
+    double rc, ec;
+    eos_inputs(p, rho, Ue, rc, ec);
+    rho_in[flat] = rc;
+    e_in[flat] = ec;
+  }
+}
+
+// table inputs of listed cells (the learned-guess closure over a cell list)
+template <int DUAL>
+__global__ void __launch_bounds__(NT) k_c2p_eosin_list(Phys p, const int32_t *__restrict__ list, int n,
+                                                       const double *__restrict__ U, double *rho_in,
+                                                       double *e_in, long long ntot) {
+  for (int e = blockIdx.x * NT + threadIdx.x; e < n; e += gridDim.x * NT) {
+    const long long flat = list[e];
     double u[6];
 #pragma unroll
     for (int v = 0; v < 5 + DUAL; ++v) u[v] = U[v * ntot + flat];
@@ -538,6 +575,40 @@ cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const in
     else k_c2p_padded<EOS_TABLE, 0><<<grid, NT, 0, m->ctx->stream>>>(C2PP_ARGS);
   }
 #undef C2PP_ARGS
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_list(tde_mesh *m, const double *Uin, const int32_t *list, int n) {
+  if (n <= 0) return cudaSuccess;
+  ProfScope _ps(m->ctx, TDE_K_C2P);
+  const Phys &p = m->phys;
+  cudaStream_t s = m->ctx->stream;
+  const unsigned grid = (unsigned)std::min<int64_t>(((int64_t)n + NT - 1) / NT, 8LL * n_sm());
+  EOSBuf eb{m->sb.P, m->sb.cs2, m->sb.eu};
+  if (surrogate_closure(m)) {
+    if (!m->sb.rho || !m->eos || !m->eos->has_net) return cudaErrorInvalidValue;
+    if (p.dual) k_c2p_eosin_list<1><<<grid, NT, 0, s>>>(p, list, n, Uin, m->sb.rho, m->sb.e, (long long)m->ntot);
+    else k_c2p_eosin_list<0><<<grid, NT, 0, s>>>(p, list, n, Uin, m->sb.rho, m->sb.e, (long long)m->ntot);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    CellMap cm{};
+    cm.nblk = 1;
+    cm.list = list;
+    err = launch_eos_surrogate_cells(m->eos, cm, n, m->sb, m->d_cnt, s);
+    if (err != cudaSuccess) return err;
+  }
+#define C2PL_ARGS p, list, n, Uin, m->d_W, (long long)m->ntot, eb
+  if (p.eos == EOS_IDEAL) {
+    if (p.dual) k_c2p_list<EOS_IDEAL, 1><<<grid, NT, 0, s>>>(C2PL_ARGS);
+    else k_c2p_list<EOS_IDEAL, 0><<<grid, NT, 0, s>>>(C2PL_ARGS);
+  } else if (surrogate_closure(m)) {
+    if (p.dual) k_c2p_list<EOS_TABLE, 1, 1><<<grid, NT, 0, s>>>(C2PL_ARGS);
+    else k_c2p_list<EOS_TABLE, 0, 1><<<grid, NT, 0, s>>>(C2PL_ARGS);
+  } else {
+    if (p.dual) k_c2p_list<EOS_TABLE, 1><<<grid, NT, 0, s>>>(C2PL_ARGS);
+    else k_c2p_list<EOS_TABLE, 0><<<grid, NT, 0, s>>>(C2PL_ARGS);
+  }
+#undef C2PL_ARGS
   return cudaGetLastError();
 }
 

@@ -98,6 +98,7 @@ struct CellMap {
   const int32_t *ids;
   int nblk, padded;
   int g[3];
+  const int32_t *list;   // blocks == NULL: the cells' flat indices (NULL: cells 0..n-1)
 };
 // Buffers of the learned-guess closure, each indexed like the state (ntot):
 // table inputs, results (eu = clamped table energy or 0), guess and queue.
@@ -146,6 +147,11 @@ struct tde_mesh {
   int32_t *d_nbr_start = nullptr, *d_nbr = nullptr;
   int32_t *d_gsrcb = nullptr;          // source block of each ghost entry
   int unit[3] = {1, 1, 1}, cn[3] = {1, 1, 1};
+  // host copies of the ghost map (copy entries: dst, src, source block; ops' dst)
+  std::vector<int32_t> h_gmap, h_gsrcb, h_gstart, h_amr_dst, h_amr_start;
+  // LAT: per level, the ghost cells whose primitives are converted (not copied)
+  int32_t *d_lat_glist = nullptr;
+  std::vector<int32_t> h_lat_glist_off;   // [levels + 1]
   int32_t *d_owner = nullptr;          // owner block per unit cube of the finest level's grid
   int lmax = 0;                        // finest refinement level
   tde::AmrOp *d_amr = nullptr;         // refined-mesh ghost ops, grouped by block
@@ -191,6 +197,8 @@ cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double
                           double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta,
                           double *freg = nullptr);
 cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids);
+// primitives of n listed cells (flat indices, device), nothing counted
+cudaError_t launch_c2p_list(tde_mesh *m, const double *Uin, const int32_t *list, int n);
 size_t sweep_smem_max(const tde_mesh *m);
 size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
 constexpr int N_SWEEP_SHAPES = 3;

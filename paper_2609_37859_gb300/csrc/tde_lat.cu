@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(LNT) k_ghost_lat(const int32_t *__restrict__ m
     const int2 mp = reinterpret_cast<const int2 *>(map)[e];
     const int fn = f[gsrcb[e]];
     if (fn == flevel) {
-      for (int v = 0; v < nvar; ++v) Udst[v * ntot + mp.x] = Udst[v * ntot + mp.y];
+      // same schedule: the primitives are copied instead (k_ghost_w_lat), and
+      // nothing after reads a conserved ghost value
     } else if (fn < flevel) {
       for (int v = 0; v < nvar; ++v) Udst[v * ntot + mp.x] = Ucur[v * ntot + mp.y];
     } else {
@@ -262,6 +263,25 @@ __global__ void __launch_bounds__(LNT) k_ghost_amr(const AmrOp *__restrict__ ops
         }
       Udst[voff + op.dst] = out;
     }
+  }
+}
+
+// ghost cells whose source block is on the same schedule: the primitives of the
+// source interior cell, converted in the same launch sequence (the conversion
+// is a function of the cell's conserved values alone, so the copy equals the
+// conversion of the copied conserved values bit for bit)
+__global__ void __launch_bounds__(LNT) k_ghost_w_lat(const int32_t *__restrict__ map,
+                                                     const int32_t *__restrict__ gstart,
+                                                     const int32_t *__restrict__ gsrcb,
+                                                     const int32_t *__restrict__ ids,
+                                                     const int32_t *__restrict__ f, int flevel, double *W,
+                                                     int nwv, long long ntot) {
+  const int b = ids[blockIdx.y];
+  const int s0 = gstart[b], s1 = gstart[b + 1];
+  for (int e = s0 + blockIdx.x * LNT + threadIdx.x; e < s1; e += gridDim.x * LNT) {
+    if (f[gsrcb[e]] != flevel) continue;
+    const int2 mp = reinterpret_cast<const int2 *>(map)[e];
+    for (int v = 0; v < nwv; ++v) W[v * ntot + mp.x] = W[v * ntot + mp.y];
   }
 }
 
@@ -503,6 +523,30 @@ int lat_build(tde_mesh *m) {
     m->freg_size = fo[nb];
   }
   if (!m->d_sorted) LCK(c, cudaMalloc(&m->d_sorted, sizeof(int32_t) * nb));
+  // per level, the ghost cells whose primitives are converted: copies from a
+  // block on another schedule (time-interpolated or frozen) and the refined-mesh
+  // ops; the others take their source's primitives
+  const std::vector<int32_t> old_goff = m->h_lat_glist_off;
+  std::vector<int32_t> glist;
+  m->h_lat_glist_off.assign(1, 0);
+  for (size_t L = 0; L < m->h_levels.size(); ++L) {
+    const int f = m->h_levels[L];
+    for (int q = m->h_level_start[L]; q < m->h_level_start[L + 1]; ++q) {
+      const int b = m->h_sorted[q];
+      for (int e = m->h_gstart[b]; e < m->h_gstart[b + 1]; ++e)
+        if (m->h_f[m->h_gsrcb[e]] != f) glist.push_back(m->h_gmap[2 * e]);
+      if (!m->h_amr_start.empty() && !m->h_amr_dst.empty())
+        for (int e = m->h_amr_start[b]; e < m->h_amr_start[b + 1]; ++e) glist.push_back(m->h_amr_dst[e]);
+    }
+    m->h_lat_glist_off.push_back((int32_t)glist.size());
+  }
+  if (!m->d_lat_glist) {
+    const size_t cap = m->h_gsrcb.size() + m->h_amr_dst.size();
+    LCK(c, cudaMalloc(&m->d_lat_glist, sizeof(int32_t) * std::max<size_t>(cap, 1)));
+  }
+  if (!glist.empty())
+    LCK(c, cudaMemcpyAsync(m->d_lat_glist, glist.data(), sizeof(int32_t) * glist.size(), cudaMemcpyHostToDevice,
+                           c->stream));
   LCK(c, cudaMemcpyAsync(m->d_sorted, m->h_sorted.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice,
                          c->stream));
   LCK(c, cudaMemcpyAsync(m->d_f, m->h_f.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, c->stream));
@@ -510,7 +554,8 @@ int lat_build(tde_mesh *m) {
   m->lat_ready = true;
   // a captured window reads the block lists, factors and dt0 from device memory
   // when it is replayed; it stays valid while the levels and their sizes do
-  if (m->h_levels != old_levels || m->h_level_start != old_start) invalidate_graph(m);
+  if (m->h_levels != old_levels || m->h_level_start != old_start || m->h_lat_glist_off != old_goff)
+    invalidate_graph(m);
   return TDE_OK;
 }
 
@@ -577,7 +622,16 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
         }
         LCK(c, cudaGetLastError());
         LCK(c, launch_ghost_amr(m, Udst, m->U, m->d_Uold, nvar, n, ids, m->d_f, f, tau, stage));
-        LCK(c, launch_c2p_padded(m, Udst, n, ids));
+        // primitives: the interiors, the converted ghost cells, then the copies
+        LCK(c, launch_c2p(m, Udst, n, ids, false, bh, ta));
+        LCK(c, launch_c2p_list(m, Udst, m->d_lat_glist + m->h_lat_glist_off[L],
+                               m->h_lat_glist_off[L + 1] - m->h_lat_glist_off[L]));
+        {
+          ProfScope ps(c, TDE_K_GHOST);
+          k_ghost_w_lat<<<dim3(gx_ghost, n), LNT, 0, s>>>(m->d_ghost, m->d_gstart, m->d_gsrcb, ids, m->d_f, f,
+                                                          m->d_W, p.nwv, (long long)m->ntot);
+        }
+        LCK(c, cudaGetLastError());
         LCK(c, launch_sweeps(m, stage, m->U, Udst, stage ? m->U : m->U1, n, ids, bh, ta, m->d_freg));
       }
     }

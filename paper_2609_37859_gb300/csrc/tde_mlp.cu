@@ -257,7 +257,7 @@ __device__ __forceinline__ long long cm_cells(const CellMap &cm, long long n, in
   return cm.padded ? (long long)B.p[0] * B.p[1] * B.p[2] : (long long)B.n[0] * B.n[1] * B.n[2];
 }
 __device__ __forceinline__ long long cm_flat(const CellMap &cm, int bp, long long local) {
-  if (!cm.blocks) return local;
+  if (!cm.blocks) return cm.list ? (long long)cm.list[local] : local;
   const DevBlock &B = cm.blocks[cm.ids[bp]];
   if (cm.padded) return B.off + local;
   // 32-bit division only (a block has < 2^31 cells; 64-bit division would
