@@ -175,27 +175,53 @@ def run_gpu(args):
     ms = max_over_ranks(ms, dist, dev)
     counts = mesh.counts()
 
-    # ---- end-to-end through the C ABI with host buffers: every step copies the
-    # state in from pinned host memory and the result back out
+    # ---- end-to-end through the C ABI with host buffers: every step copies its
+    # state in from pinned host memory and its result back out.  Three device
+    # states rotate so that step k + 1's input copy and step k - 1's output copy
+    # (each on its own stream) overlap step k's kernels.
     host_in = U_init.cpu().pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
+    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(3)]
     nbytes = host_in.numel() * 8
-    mesh.U.copy_(U_init)
+    U_main = mesh.U
+    bufs = [U_main, torch.empty_like(U_main), torch.empty_like(U_main)]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event() for _ in range(3)]
+    ev_done = [torch.cuda.Event() for _ in range(3)]
+    ev_out = [torch.cuda.Event() for _ in range(3)]
     mesh.set_time(0.0)
-    for _ in range(max(1, args.warmup)):
-        mesh.U.copy_(host_in, non_blocking=True)
-        mesh.step(cfl=CFL)
-        host_out.copy_(mesh.U, non_blocking=True)
+
+    def e2e_run(n):
+        with torch.cuda.stream(s_in):
+            bufs[0].copy_(host_in, non_blocking=True)
+            ev_in[0].record(s_in)
+        for k in range(n):
+            b, nx = k % 3, (k + 1) % 3
+            if k + 1 < n:
+                with torch.cuda.stream(s_in):
+                    if k >= 2:
+                        s_in.wait_event(ev_out[nx])   # that buffer's result is out
+                    bufs[nx].copy_(host_in, non_blocking=True)
+                    ev_in[nx].record(s_in)
+            stream.wait_event(ev_in[b])
+            mesh.bind(bufs[b])
+            mesh.step(cfl=CFL)
+            ev_done[b].record(stream)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_done[b])
+                host_out[b].copy_(bufs[b], non_blocking=True)
+                ev_out[b].record(s_out)
+        stream.wait_event(ev_out[(n - 1) % 3])
+
+    e2e_run(max(1, args.warmup))
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(args.steps):
-        mesh.U.copy_(host_in, non_blocking=True)
-        mesh.step(cfl=CFL)
-        host_out.copy_(mesh.U, non_blocking=True)
+    e2e_run(args.steps)
     f1.record(stream)
     barrier()
     ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+    mesh.bind(U_main)
+    del bufs
 
     fp64_peak = ctx.probe_fp64()
     if rank == 0:
@@ -258,7 +284,7 @@ def run_gpu(args):
             line["closure_modes"] = closure_bench(mesh, U_init, tde, torch, dev, args)
         elif not (args.no_lat and args.no_c5):   # their learned arms need the network
             eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
-        del mesh, U_init, host_in, host_out
+        del mesh, U_init, host_in, host_out, U_main
         torch.cuda.empty_cache()
         if not args.no_grav:
             line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)

@@ -362,6 +362,13 @@ class Mesh:
         self.ctx.check(lib().tde_mesh_set_params(self.h, C.byref(params)))
         self.params = params
 
+    def bind(self, U, U1=None):
+        """Bind other caller-owned device states (nvar x ntot each) as U (and U1)."""
+        self.U = U
+        if U1 is not None:
+            self.U1 = U1
+        self.ctx.check(lib().tde_mesh_bind_state(self.h, _ptr(self.U), _ptr(self.U1)))
+
     def prim_to_cons(self, W):
         self.ctx.check(lib().tde_prim_to_cons(self.h, _ptr(W), _ptr(self.U)))
 
