@@ -49,6 +49,8 @@ struct Lev {
   // inactive on the finest level (isolated)
   double aw[3], cw[3], cs;
   int iso;                  // isolated boundaries
+  int act[3];               // weight along a nonzero (an integer test: an FP64
+                            // comparison would take the FP64 pipe)
   double x0[3];             // lower domain corner
   const double *gf[6];      // isolated: phi on the boundary faces x-, x+, y-, y+, z-, z+
 };
@@ -135,8 +137,8 @@ __device__ double mp_eval(const MP &mp, const double x[3]) {
 
 // isolated: a cell with a neighbour beyond a boundary face
 __device__ __forceinline__ bool on_boundary(const Lev &L, int i, int j, int k) {
-  return (L.aw[0] != 0.0 && (i == 0 || i == L.n[0] - 1)) || (L.aw[1] != 0.0 && (j == 0 || j == L.n[1] - 1)) ||
-         (L.aw[2] != 0.0 && (k == 0 || k == L.n[2] - 1));
+  return (L.act[0] && (i == 0 || i == L.n[0] - 1)) || (L.act[1] && (j == 0 || j == L.n[1] - 1)) ||
+         (L.act[2] && (k == 0 || k == L.n[2] - 1));
 }
 
 // the cell of thread e: x fastest; on an isolated grid of at least three cells
@@ -162,21 +164,41 @@ __device__ __forceinline__ void cell_of(const Lev &L, unsigned e, int &i, int &j
   j = (int)(row - (unsigned)k * L.n[1]);
 }
 
+// isolated boundary cell: its six neighbours, one beyond a face replaced by twice
+// the face value (its mirror image is 2 phi_face - phi_c, whose -phi_c part the
+// caller moves to the centre); out[a] = faces crossed along a.  Unrolled selects:
+// only boundary cells come here, so computing both sides costs little.
+struct Nb6 {
+  double m[3], p[3];
+  double out[3];
+};
+__device__ __forceinline__ Nb6 nbrs_iso(const Lev &L, const double *phi, int i, int j, int k, unsigned l) {
+  Nb6 r;
+  const unsigned sy = (unsigned)L.n[0], sz = (unsigned)L.n[0] * L.n[1];
+  const bool xl = i > 0, xh = i < L.n[0] - 1, yl = j > 0, yh = j < L.n[1] - 1, zl = k > 0, zh = k < L.n[2] - 1;
+  // (a direction inactive on the finest grid has no faces and weight 0: nothing read)
+  const bool ax = L.act[0], ay = L.act[1], az = L.act[2];
+  const unsigned fx = (unsigned)k * L.n[1] + j, fy = (unsigned)k * L.n[0] + i, fz = (unsigned)j * L.n[0] + i;
+  r.m[0] = !ax ? 0.0 : (xl ? phi[l - 1] : 2.0 * L.gf[0][fx]);
+  r.p[0] = !ax ? 0.0 : (xh ? phi[l + 1] : 2.0 * L.gf[1][fx]);
+  r.m[1] = !ay ? 0.0 : (yl ? phi[l - sy] : 2.0 * L.gf[2][fy]);
+  r.p[1] = !ay ? 0.0 : (yh ? phi[l + sy] : 2.0 * L.gf[3][fy]);
+  r.m[2] = !az ? 0.0 : (zl ? phi[l - sz] : 2.0 * L.gf[4][fz]);
+  r.p[2] = !az ? 0.0 : (zh ? phi[l + sz] : 2.0 * L.gf[5][fz]);
+  r.out[0] = (xl ? 0.0 : 1.0) + (xh ? 0.0 : 1.0);
+  r.out[1] = (yl ? 0.0 : 1.0) + (yh ? 0.0 : 1.0);
+  r.out[2] = (zl ? 0.0 : 1.0) + (zh ? 0.0 : 1.0);
+  return r;
+}
+
 __device__ __forceinline__ double apply_A(const Lev &L, const double *phi, int i, int j, int k) {
   if (L.iso && on_boundary(L, i, j, k)) {
-    const int c[3] = {i, j, k};
-    const double pc = phi[lin(L, i, j, k)];
+    const unsigned l = lin(L, i, j, k);
+    const double pc = phi[l];
+    const Nb6 q = nbrs_iso(L, phi, i, j, k, l);
     double s = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      if (L.aw[a] == 0.0) continue;
-      double nb = 0.0;
-      for (int side = 0; side < 2; ++side) {
-        int q[3] = {i, j, k};
-        q[a] += side ? 1 : -1;
-        nb += (q[a] >= 0 && q[a] < L.n[a]) ? phi[lin(L, q[0], q[1], q[2])] : 2.0 * face_phi(L, a, side, c) - pc;
-      }
-      s = fma(L.aw[a], 2.0 * pc - nb, s);
-    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s = fma(L.aw[a], (2.0 + q.out[a]) * pc - q.m[a] - q.p[a], s);
     return s;
   }
   // (periodic, or an isolated grid's inner cell, whose wrapped neighbours are its own)
@@ -187,25 +209,18 @@ __device__ __forceinline__ double apply_A(const Lev &L, const double *phi, int i
   return s;
 }
 
-// isolated Gauss-Seidel value of a boundary cell: the mirror cells 2 phi_face -
-// phi_c move to the diagonal (w_a / diag per mirror)
+// isolated Gauss-Seidel value of a boundary cell: the mirror cells' -phi_c parts
+// move to the diagonal (w_a / diag per face crossed)
 __device__ __forceinline__ double gs_iso(const Lev &L, int i, int j, int k) {
-  const int c[3] = {i, j, k};
+  const unsigned l = lin(L, i, j, k);
+  const Nb6 q = nbrs_iso(L, L.phi, i, j, k, l);
   double nb = 0.0, dg = 1.0;   // in units of the inner cells' diagonal
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (L.cw[a] == 0.0) continue;
-    for (int side = 0; side < 2; ++side) {
-      int q[3] = {i, j, k};
-      q[a] += side ? 1 : -1;
-      if (q[a] >= 0 && q[a] < L.n[a]) {
-        nb = fma(L.cw[a], L.phi[lin(L, q[0], q[1], q[2])], nb);
-      } else {
-        nb = fma(L.cw[a], 2.0 * face_phi(L, a, side, c), nb);
-        dg += L.cw[a];
-      }
-    }
+    nb = fma(L.cw[a], q.m[a] + q.p[a], nb);
+    dg = fma(L.cw[a], q.out[a], dg);
   }
-  return fma(L.cs, L.src[lin(L, i, j, k)], nb) / dg;
+  return fma(L.cs, L.src[l], nb) / dg;
 }
 
 // level-0 source from the MeshBlock density: S = -4 pi G rho where rho > rho_min
@@ -227,17 +242,18 @@ __global__ void __launch_bounds__(GT) k_mg_gather(Phys p, const DevBlock *__rest
 // partial sums (one per CTA) of f, or of the squared defect if sq
 __global__ void __launch_bounds__(GT) k_mg_partial(Lev L, int sq, double *part) {
   __shared__ double red[GT / 32];
-  const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
   double s = 0.0;
-  for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
-    if (sq) {
+  if (sq) {
+    const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
+    for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) {
       int i, j, k;
       cell_of(L, c, i, j, k);
       const double d = L.src[lin(L, i, j, k)] - apply_A(L, L.phi, i, j, k);
       s += d * d;
-    } else {
-      s += L.src[c];
     }
+  } else {
+    const unsigned n = (unsigned)L.n[0] * L.n[1] * L.n[2];
+    for (unsigned c = blockIdx.x * GT + threadIdx.x; c < n; c += gridDim.x * GT) s += L.src[c];
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -392,7 +408,8 @@ __global__ void __launch_bounds__(GT) k_mg_prolong(Lev F, Lev C) {
           const double w = np == 3 ? 27.0 : (np == 2 ? 9.0 : (np == 1 ? 3.0 : 1.0));
           int u[3] = {ax ? q[0] : p[0], by ? q[1] : p[1], cz ? q[2] : p[2]};
           double e;
-          if (C.iso) {   // beyond a face the correction is its odd mirror image
+          if (C.iso && ((unsigned)u[0] >= (unsigned)C.n[0] || (unsigned)u[1] >= (unsigned)C.n[1] ||
+                        (unsigned)u[2] >= (unsigned)C.n[2])) {   // beyond a face: the odd mirror image
             double sg = 1.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -421,14 +438,21 @@ __global__ void __launch_bounds__(GT) k_mg_scatter(Phys p, const DevBlock *__res
     const int i = e % B.p[0], r = e / B.p[0];
     const int j = r % B.p[1], k = r / B.p[1];
     const int g[3] = {B.i0 + i - p.g[0], B.j0 + j - p.g[1], B.k0 + k - p.g[2]};
-    if (L.iso && (g[0] < 0 || g[1] < 0 || g[2] < 0 || g[0] >= L.n[0] || g[1] >= L.n[1] || g[2] >= L.n[2])) {
-      // a ghost cell beyond an isolated boundary: the expansion at its centre
-      double x[3];
-      for (int a = 0; a < 3; ++a) x[a] = L.x0[a] + (g[a] + 0.5) * L.dx[a];
-      phi_pad[B.off + e] = mp_eval(mp, x);
-    } else {
-      phi_pad[B.off + e] = L.phi[wrap_idx(L, g[0], g[1], g[2])];
-    }
+    // (isolated: the ghost cells beyond the boundary are k_mg_scatter_out's)
+    if (L.iso && (g[0] < 0 || g[1] < 0 || g[2] < 0 || g[0] >= L.n[0] || g[1] >= L.n[1] || g[2] >= L.n[2])) continue;
+    phi_pad[B.off + e] = L.phi[wrap_idx(L, g[0], g[1], g[2])];
+  }
+}
+
+// isolated: the ghost cells beyond the boundary (a list built once per mesh)
+// take the expansion at their centres
+__global__ void __launch_bounds__(GT) k_mg_scatter_out(const long long *__restrict__ flat,
+                                                       const int *__restrict__ gidx, int n, Lev L, MP mp,
+                                                       double *phi_pad) {
+  for (int e = blockIdx.x * GT + threadIdx.x; e < n; e += gridDim.x * GT) {
+    double x[3];
+    for (int a = 0; a < 3; ++a) x[a] = L.x0[a] + (gidx[3 * e + a] + 0.5) * L.dx[a];
+    phi_pad[flat[e]] = mp_eval(mp, x);
   }
 }
 
@@ -537,14 +561,24 @@ __global__ void __launch_bounds__(GT) k_mp_centroid(Lev L, double *part) {
   }
 }
 
-// the centroid from the partial sums (fixed order; the domain centre for a
-// source summing to zero)
-__global__ void k_mp_centre(const double *__restrict__ part, int np, Lev L, double *cc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// the centroid from the partial sums (a fixed-order tree over GT threads; the
+// domain centre for a source summing to zero)
+__global__ void __launch_bounds__(GT) k_mp_centre(const double *__restrict__ part, int np, Lev L, double *cc) {
+  __shared__ double red[4][GT];
   double t[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = 0; b < np; ++b)
+  for (int b = threadIdx.x; b < np; b += GT)
     for (int q = 0; q < 4; ++q) t[q] += part[4 * b + q];
-  for (int a = 0; a < 3; ++a) cc[a] = t[0] != 0.0 ? t[1 + a] / t[0] : L.x0[a] + 0.5 * L.n[a] * L.dx[a];
+  for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = t[q];
+  __syncthreads();
+  for (int h = GT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    const int a = threadIdx.x;
+    cc[a] = red[0][0] != 0.0 ? red[1 + a][0] / red[0][0] : L.x0[a] + 0.5 * L.n[a] * L.dx[a];
+  }
 }
 
 // partial moments per CTA: sum S dV R_l^m(x - c), 2 MP_NC values
@@ -584,19 +618,28 @@ __global__ void __launch_bounds__(GT) k_mp_moments(Lev L, const double *__restri
   }
 }
 
-// coefficients (A_lm, B_lm) = (2 - delta_m0) (l-m)! / (l+m)! / (4 pi) x the moments
-__global__ void k_mp_coef(const double *__restrict__ part, int np, int lmax, double *cc) {
-  const int q = threadIdx.x;
-  if (q >= 2 * MP_NC) return;
-  const int pair = q >> 1;
-  int l = 0;
-  while ((l + 1) * (l + 2) / 2 <= pair) ++l;
-  const int m = pair - l * (l + 1) / 2;
+// coefficients (A_lm, B_lm) = (2 - delta_m0) (l-m)! / (l+m)! / (4 pi) x the
+// moments; one CTA per coefficient, a fixed-order tree over the partial sums
+__global__ void __launch_bounds__(GT) k_mp_coef(const double *__restrict__ part, int np, int lmax, double *cc) {
+  __shared__ double red[GT];
+  const int q = blockIdx.x;
   double t = 0.0;
-  for (int b = 0; b < np; ++b) t += part[2 * MP_NC * b + q];
-  double f = (m ? 2.0 : 1.0) / (4.0 * M_PI);
-  for (int v = l - m + 1; v <= l + m; ++v) f /= v;   // (l-m)! / (l+m)!
-  cc[3 + q] = l <= lmax ? t * f : 0.0;
+  for (int b = threadIdx.x; b < np; b += GT) t += part[2 * MP_NC * b + q];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = GT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int pair = q >> 1;
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= pair) ++l;
+    const int m = pair - l * (l + 1) / 2;
+    double f = (m ? 2.0 : 1.0) / (4.0 * M_PI);
+    for (int v = l - m + 1; v <= l + m; ++v) f /= v;   // (l-m)! / (l+m)!
+    cc[3 + q] = l <= lmax ? red[0] * f : 0.0;
+  }
 }
 
 // phi on the boundary faces of every level
@@ -645,6 +688,9 @@ struct GravState {
   int face_start[40][7];
   double *mp = nullptr;     // centre (3) + coefficients (2 MP_NC)
   double *mpart = nullptr;  // partial moments, 2 MP_NC per CTA
+  long long *out_flat = nullptr;   // isolated: MeshBlock ghost cells beyond the boundary
+  int *out_g = nullptr;            // their global indices (3 per cell)
+  int nout = -1;                   // -1: list not built
 };
 
 static void grav_free(GravState *g) {
@@ -660,6 +706,8 @@ static void grav_free(GravState *g) {
   cudaFree(g->faces);
   cudaFree(g->mp);
   cudaFree(g->mpart);
+  cudaFree(g->out_flat);
+  cudaFree(g->out_g);
   delete g;
 }
 
@@ -687,6 +735,7 @@ static void set_weights(GravState *g, const Phys &p, int iso) {
       L.cw[a] = diag > 0.0 ? w[a] / diag : 0.0;
     }
     L.cs = diag > 0.0 ? h[0] * h[0] / diag : 0.0;
+    for (int a = 0; a < 3; ++a) L.act[a] = w[a] != 0.0;
     L.iso = iso;
     for (int f = 0; f < 6; ++f) L.gf[f] = iso ? g->faces + g->face_start[l][f] : nullptr;
   }
@@ -782,7 +831,7 @@ static void multipole_setup(GravState *g, int lmax, cudaStream_t s) {
   const long long n0 = (long long)L0.n[0] * L0.n[1] * L0.n[2];
   const unsigned gr = std::min<unsigned>(grid_for(n0), (unsigned)g->npart);
   k_mp_centroid<<<gr, GT, 0, s>>>(L0, g->part);
-  k_mp_centre<<<1, 32, 0, s>>>(g->part, (int)gr, L0, g->mp);
+  k_mp_centre<<<1, GT, 0, s>>>(g->part, (int)gr, L0, g->mp);
   switch (lmax) {
     case 0: k_mp_moments<0><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
     case 1: k_mp_moments<1><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
@@ -790,7 +839,7 @@ static void multipole_setup(GravState *g, int lmax, cudaStream_t s) {
     case 3: k_mp_moments<3><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
     default: k_mp_moments<4><<<gr, GT, 0, s>>>(L0, g->mp, g->mpart); break;
   }
-  k_mp_coef<<<1, 64, 0, s>>>(g->mpart, (int)gr, lmax, g->mp);
+  k_mp_coef<<<2 * MP_NC, GT, 0, s>>>(g->mpart, (int)gr, lmax, g->mp);
   const MP mp{lmax, g->mp};
   for (int l = 0; l < g->nl; ++l) {
     FaceJob job;
@@ -903,11 +952,44 @@ cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, d
     g->launches += g->cycle_launches;
     ++ncyc;
   }
+  if (iso && g->nout < 0) {
+    // the MeshBlock ghost cells beyond the boundary, once per mesh
+    std::vector<long long> fl;
+    std::vector<int> gi;
+    const Phys &p = m->phys;
+    for (int b = 0; b < m->nb; ++b) {
+      const DevBlock &B = m->hblocks[b];
+      for (int k = 0; k < B.p[2]; ++k)
+        for (int j = 0; j < B.p[1]; ++j)
+          for (int i = 0; i < B.p[0]; ++i) {
+            const int gg[3] = {B.i0 + i - p.g[0], B.j0 + j - p.g[1], B.k0 + k - p.g[2]};
+            bool out = false;
+            for (int a = 0; a < 3; ++a)
+              if (gg[a] < 0 || gg[a] >= p.N[a]) out = true;
+            if (!out) continue;
+            fl.push_back(B.off + ((long long)k * B.p[1] + j) * B.p[0] + i);
+            gi.insert(gi.end(), gg, gg + 3);
+          }
+    }
+    g->nout = (int)fl.size();
+    if (g->nout > 0) {
+      err = cudaMalloc(&g->out_flat, sizeof(long long) * fl.size());
+      if (err == cudaSuccess) err = cudaMalloc(&g->out_g, sizeof(int) * gi.size());
+      if (err == cudaSuccess)
+        err = cudaMemcpy(g->out_flat, fl.data(), sizeof(long long) * fl.size(), cudaMemcpyHostToDevice);
+      if (err == cudaSuccess) err = cudaMemcpy(g->out_g, gi.data(), sizeof(int) * gi.size(), cudaMemcpyHostToDevice);
+      if (err != cudaSuccess) return err;
+    }
+  }
   {
     ProfScope ps(c, TDE_K_GRAV, false);
     dim3 grid((unsigned)std::min<int64_t>((m->max_interior + GT - 1) / GT, 64), (unsigned)m->nb);
     const MP mp{gp.lmax, g->mp};
     k_mg_scatter<<<grid, GT, 0, s>>>(m->phys, m->d_blocks, L0, mp, m->d_phi_sg);
+    if (iso && g->nout > 0) {
+      k_mg_scatter_out<<<grid_for(g->nout), GT, 0, s>>>(g->out_flat, g->out_g, g->nout, L0, mp, m->d_phi_sg);
+      g->launches += 1;
+    }
   }
   g->launches += 2;   // gather and scatter (the rest count at launch)
   c->launches[TDE_K_GRAV] += g->launches;
