@@ -638,13 +638,8 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
     cudaMemcpy(m->d_amr, amr.data(), sizeof(AmrOp) * amr.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(m->d_amr_start, amr_start.data(), sizeof(int32_t) * (nblocks + 1), cudaMemcpyHostToDevice);
   }
-  // host copies for the LAT ghost lists
-  m->h_gmap = gmap;
-  m->h_gsrcb = gsrcb;
-  m->h_gstart = gstart;
-  m->h_amr_start = amr_start;
-  m->h_amr_dst.resize(amr.size());
-  for (size_t q = 0; q < amr.size(); ++q) m->h_amr_dst[q] = amr[q].dst;
+  m->n_gcopy = (int64_t)gsrcb.size();
+  m->n_amr = (int64_t)amr.size();
   for (int a = 0; a < 3; ++a) {
     m->unit[a] = unit[a];
     m->cn[a] = cn[a];
@@ -685,6 +680,7 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_amr);
   cudaFree(m->d_amr_start);
   cudaFree(m->d_lat_glist);
+  cudaFree(m->d_lat_gstart);
   cudaFree(m->sb.rho);
   cudaFree(m->sb.lTg);
   cudaFree(m->sb.queue);

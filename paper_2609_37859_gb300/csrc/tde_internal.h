@@ -147,10 +147,10 @@ struct tde_mesh {
   int32_t *d_nbr_start = nullptr, *d_nbr = nullptr;
   int32_t *d_gsrcb = nullptr;          // source block of each ghost entry
   int unit[3] = {1, 1, 1}, cn[3] = {1, 1, 1};
-  // host copies of the ghost map (copy entries: dst, src, source block; ops' dst)
-  std::vector<int32_t> h_gmap, h_gsrcb, h_gstart, h_amr_dst, h_amr_start;
+  int64_t n_gcopy = 0, n_amr = 0;      // ghost copy entries, refined-mesh ghost ops
   // LAT: per level, the ghost cells whose primitives are converted (not copied)
   int32_t *d_lat_glist = nullptr;
+  int32_t *d_lat_gstart = nullptr;        // list offset of each block in factor order [nb + 1]
   std::vector<int32_t> h_lat_glist_off;   // [levels + 1]
   int32_t *d_owner = nullptr;          // owner block per unit cube of the finest level's grid
   int lmax = 0;                        // finest refinement level

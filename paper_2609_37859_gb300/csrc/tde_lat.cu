@@ -450,6 +450,114 @@ cudaError_t launch_ghost_amr(tde_mesh *m, double *Udst, const double *Ucur, cons
   return cudaGetLastError();
 }
 
+// ---- per level, the ghost cells a window converts (not copies) -------------
+// Built on the device whenever the factors change: for the q-th block of the
+// factor-sorted order, its copy entries whose source block is on another
+// schedule, in map order, then its refined-mesh ops.  Blocks in sorted order
+// make every level a contiguous segment of the list.
+constexpr int GLT = 256;
+
+__global__ void __launch_bounds__(GLT) k_glist_count(const int32_t *__restrict__ sorted,
+                                                     const int32_t *__restrict__ f,
+                                                     const int32_t *__restrict__ gstart,
+                                                     const int32_t *__restrict__ gsrcb,
+                                                     const int32_t *__restrict__ amr_start,
+                                                     int32_t *__restrict__ cnt) {
+  __shared__ int ws[GLT / 32];
+  const int b = sorted[blockIdx.x], fb = f[b];
+  int n = 0;
+  for (int e = gstart[b] + threadIdx.x; e < gstart[b + 1]; e += GLT) n += f[gsrcb[e]] != fb;
+  n = __reduce_add_sync(0xffffffffu, n);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = amr_start ? amr_start[b + 1] - amr_start[b] : 0;
+    for (int w = 0; w < GLT / 32; ++w) t += ws[w];
+    cnt[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the nb counts in place: cnt[q] -> start of block q, cnt[nb] = total
+__global__ void __launch_bounds__(1024) k_glist_scan(int32_t *cnt, int nb) {
+  __shared__ int ws[32];
+  const int per = (nb + 1023) / 1024, q0 = threadIdx.x * per, q1 = min(nb, q0 + per);
+  int s = 0;
+  for (int q = q0; q < q1; ++q) s += cnt[q];
+  // inclusive scan of the thread sums: within warps, then over warp totals
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int v = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    ws[lane] = v;
+  }
+  __syncthreads();
+  int run = x - s + (w ? ws[w - 1] : 0);
+  for (int q = q0; q < q1; ++q) {
+    const int c = cnt[q];
+    cnt[q] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) cnt[nb] = ws[31];
+}
+
+__global__ void __launch_bounds__(GLT) k_glist_fill(const int32_t *__restrict__ sorted,
+                                                    const int32_t *__restrict__ f,
+                                                    const int32_t *__restrict__ gstart,
+                                                    const int32_t *__restrict__ gsrcb,
+                                                    const int32_t *__restrict__ map,
+                                                    const AmrOp *__restrict__ amr,
+                                                    const int32_t *__restrict__ amr_start,
+                                                    const int32_t *__restrict__ start,
+                                                    int32_t *__restrict__ out) {
+  __shared__ int ws[GLT / 32];
+  const int b = sorted[blockIdx.x], fb = f[b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s1 = gstart[b + 1];
+  int base = start[blockIdx.x];
+  // ordered compaction, GLT entries per pass (the pass count is uniform over the CTA)
+  for (int e0 = gstart[b]; e0 < s1; e0 += GLT) {
+    const int e = e0 + threadIdx.x;
+    const bool take = e < s1 && f[gsrcb[e]] != fb;
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) ws[w] = __popc(bal);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int k = 0; k < GLT / 32; ++k) {
+      before += k < w ? ws[k] : 0;
+      tot += ws[k];
+    }
+    if (take) out[base + before + __popc(bal & ((1u << lane) - 1u))] = map[2 * e];
+    base += tot;
+    __syncthreads();
+  }
+  if (amr_start)
+    for (int e = amr_start[b] + threadIdx.x; e < amr_start[b + 1]; e += GLT)
+      out[base + e - amr_start[b]] = amr[e].dst;
+}
+
+// Enqueues the list build on the mesh's stream; starts[q] (q = 0..nb) are the
+// list offsets of the sorted blocks, read back by the caller after a sync.
+cudaError_t launch_glist(tde_mesh *m, int32_t *starts) {
+  const int nb = m->nb;
+  cudaStream_t s = m->ctx->stream;
+  ProfScope ps(m->ctx, TDE_K_SCALAR);
+  k_glist_count<<<nb, GLT, 0, s>>>(m->d_sorted, m->d_f, m->d_gstart, m->d_gsrcb, m->d_amr_start, starts);
+  k_glist_scan<<<1, 1024, 0, s>>>(starts, nb);
+  k_glist_fill<<<nb, GLT, 0, s>>>(m->d_sorted, m->d_f, m->d_gstart, m->d_gsrcb, m->d_ghost, m->d_amr,
+                                  m->d_amr_start, starts, m->d_lat_glist);
+  return cudaGetLastError();
+}
+
 // A captured LAT window is stale once the mesh's launch configuration changes.
 void invalidate_graph(tde_mesh *m) {
   if (m->lat_graph) {
@@ -523,34 +631,23 @@ int lat_build(tde_mesh *m) {
     m->freg_size = fo[nb];
   }
   if (!m->d_sorted) LCK(c, cudaMalloc(&m->d_sorted, sizeof(int32_t) * nb));
-  // per level, the ghost cells whose primitives are converted: copies from a
-  // block on another schedule (time-interpolated or frozen) and the refined-mesh
-  // ops; the others take their source's primitives
-  const std::vector<int32_t> old_goff = m->h_lat_glist_off;
-  std::vector<int32_t> glist;
-  m->h_lat_glist_off.assign(1, 0);
-  for (size_t L = 0; L < m->h_levels.size(); ++L) {
-    const int f = m->h_levels[L];
-    for (int q = m->h_level_start[L]; q < m->h_level_start[L + 1]; ++q) {
-      const int b = m->h_sorted[q];
-      for (int e = m->h_gstart[b]; e < m->h_gstart[b + 1]; ++e)
-        if (m->h_f[m->h_gsrcb[e]] != f) glist.push_back(m->h_gmap[2 * e]);
-      if (!m->h_amr_start.empty() && !m->h_amr_dst.empty())
-        for (int e = m->h_amr_start[b]; e < m->h_amr_start[b + 1]; ++e) glist.push_back(m->h_amr_dst[e]);
-    }
-    m->h_lat_glist_off.push_back((int32_t)glist.size());
-  }
-  if (!m->d_lat_glist) {
-    const size_t cap = m->h_gsrcb.size() + m->h_amr_dst.size();
-    LCK(c, cudaMalloc(&m->d_lat_glist, sizeof(int32_t) * std::max<size_t>(cap, 1)));
-  }
-  if (!glist.empty())
-    LCK(c, cudaMemcpyAsync(m->d_lat_glist, glist.data(), sizeof(int32_t) * glist.size(), cudaMemcpyHostToDevice,
-                           c->stream));
+  if (!m->d_lat_gstart) LCK(c, cudaMalloc(&m->d_lat_gstart, sizeof(int32_t) * (nb + 1)));
+  if (!m->d_lat_glist)
+    LCK(c, cudaMalloc(&m->d_lat_glist, sizeof(int32_t) * std::max<int64_t>(m->n_gcopy + m->n_amr, 1)));
   LCK(c, cudaMemcpyAsync(m->d_sorted, m->h_sorted.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice,
                          c->stream));
   LCK(c, cudaMemcpyAsync(m->d_f, m->h_f.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, c->stream));
+  // per level, the ghost cells whose primitives are converted: copies from a
+  // block on another schedule (time-interpolated or frozen) and the refined-mesh
+  // ops; the others take their source's primitives
+  std::vector<int32_t> starts(nb + 1);
+  LCK(c, launch_glist(m, m->d_lat_gstart));
+  LCK(c, cudaMemcpyAsync(starts.data(), m->d_lat_gstart, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost,
+                         c->stream));
   LCK(c, cudaStreamSynchronize(c->stream));
+  const std::vector<int32_t> old_goff = m->h_lat_glist_off;
+  m->h_lat_glist_off.resize(m->h_levels.size() + 1);
+  for (size_t L = 0; L <= m->h_levels.size(); ++L) m->h_lat_glist_off[L] = starts[m->h_level_start[L]];
   m->lat_ready = true;
   // a captured window reads the block lists, factors and dt0 from device memory
   // when it is replayed; it stays valid while the levels and their sizes do
