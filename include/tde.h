@@ -500,10 +500,20 @@ TDE_API int tde_mesh_remap(tde_mesh *dst, double *Udst, const tde_mesh *src, con
  * device doubles: TDE_MATH_RCP out = 1/x (refined hardware seed, within one
  * ulp), TDE_MATH_SQRT_RATIO out = sqrt(x / y) (within about two ulps; x y and
  * x / y normal), TDE_MATH_RCP_SEED and TDE_MATH_RSQRT_SEED the raw hardware
- * approximations of 1/x and 1/sqrt(x) that the two refine.  y is read only by
- * TDE_MATH_SQRT_RATIO.  TDE_EINVAL for an unknown op or null arrays with n > 0;
- * asynchronous on the context's stream. */
-enum { TDE_MATH_RCP = 0, TDE_MATH_SQRT_RATIO = 1, TDE_MATH_RCP_SEED = 2, TDE_MATH_RSQRT_SEED = 3 };
+ * approximations of 1/x and 1/sqrt(x) that the two refine, TDE_MATH_RSQRT
+ * out = 1/sqrt(x) (refined seed, within about two ulps; the point-mass
+ * potential), TDE_MATH_INSIDE out = 1 if sqrt(x) < y else 0 (the excision test,
+ * decided as with the correctly rounded square root, x >= 0).  y is read only by
+ * TDE_MATH_SQRT_RATIO and TDE_MATH_INSIDE.  TDE_EINVAL for an unknown op or null
+ * arrays with n > 0; asynchronous on the context's stream. */
+enum {
+  TDE_MATH_RCP = 0,
+  TDE_MATH_SQRT_RATIO = 1,
+  TDE_MATH_RCP_SEED = 2,
+  TDE_MATH_RSQRT_SEED = 3,
+  TDE_MATH_RSQRT = 4,
+  TDE_MATH_INSIDE = 5
+};
 TDE_API int tde_math_probe(tde_ctx *ctx, int op, int64_t n, const double *x, const double *y,
                            double *out);
 

@@ -1076,6 +1076,8 @@ __global__ void k_math_probe(int op, long long n, const double *x, const double 
       case TDE_MATH_RCP: r = rcp_nr(a); break;
       case TDE_MATH_SQRT_RATIO: r = sqrt_ratio(a, y[i]); break;
       case TDE_MATH_RCP_SEED: r = rcp_seed(a); break;
+      case TDE_MATH_RSQRT: r = rsqrt_nr(a); break;
+      case TDE_MATH_INSIDE: r = inside_radius(a, y[i]) ? 1.0 : 0.0; break;
       default: r = rsqrt_seed(a); break;
     }
     out[i] = r;
@@ -1086,8 +1088,8 @@ __global__ void k_math_probe(int op, long long n, const double *x, const double 
 extern "C" int tde_math_probe(tde_ctx *c, int op, int64_t n, const double *x, const double *y,
                               double *out) {
   if (!c) return TDE_EINVAL;
-  if (op < TDE_MATH_RCP || op > TDE_MATH_RSQRT_SEED || n < 0 || (n > 0 && (!x || !out)) ||
-      (n > 0 && op == TDE_MATH_SQRT_RATIO && !y))
+  if (op < TDE_MATH_RCP || op > TDE_MATH_INSIDE || n < 0 || (n > 0 && (!x || !out)) ||
+      (n > 0 && (op == TDE_MATH_SQRT_RATIO || op == TDE_MATH_INSIDE) && !y))
     return fail(c, TDE_EINVAL, "tde_math_probe: arguments");
   if (n == 0) return TDE_OK;
   ProfScope ps(c, TDE_K_PROBE);

@@ -252,7 +252,38 @@ __device__ __forceinline__ double sqrt_ratio(double a, double b) {
   return a * y1;
 }
 
+// 1/sqrt(t) for t > 0: the hardware seed refined to second order as in
+// sqrt_ratio, within about two ulps; the IEEE form outside the seed's normal range
+__device__ __forceinline__ double rsqrt_nr(double t) {
+  if ((unsigned long long)(((dbits(t) >> 52) & 0x7ff) - 2) >= 0x7fcull) return 1.0 / sqrt(t);
+  const double y = rsqrt_seed(t);
+  const double e = fma(-t, y * y, 1.0);
+  return fma(y, e * fma(e, 0.375, 0.5), y);
+}
+
+// sqrt(r2) < r for r2 >= 0, decided as with the correctly rounded square root:
+// away from the boundary the comparison of r2 with r^2 (1 -+ 2^-40) gives the
+// same answer (the roundings of r^2 and of the square root are below 2^-51
+// relative), and only within that band is the square root taken.  A negative
+// or NaN r gives false, as the comparison does.
+__device__ __forceinline__ bool inside_radius(double r2, double r) {
+  if ((unsigned long long)dbits(r) > 0x7ff0000000000000ull) return false;
+  const double r2b = r * r;
+  if (((dbits(r2b) >> 52) & 0x7ff) < 64) return dlt(sqrt(r2), r);   // r^2 near the subnormals
+  if (dlt(r2, r2b * (1.0 - 0x1p-40))) return true;
+  if (dlt(r2b * (1.0 + 0x1p-40), r2)) return false;
+  return dlt(sqrt(r2), r);
+}
+
 // ---------------------------------------------------------------- EOS ----
+
+// floor(x) for 0 <= x < 2^31 (also -0) from the bit fields, on the integer pipe
+__device__ __forceinline__ int ifloor_nonneg(double x) {
+  const long long b = dbits(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < 0) return 0;
+  return (int)(((b & 0xfffffffffffffLL) | 0x10000000000000LL) >> (52 - e));
+}
 
 // Density cell i and weight w of log10 rho (clamped to the table).
 __device__ __forceinline__ bool rho_cell(const DTable &t, double rho, int &i, double &w) {
@@ -404,7 +435,7 @@ __device__ __forceinline__ void eos_closure(const Phys &p, double rho, double U,
       Pc = eb->P[flat];
       c2c = eb->cs2[flat];
       eu = eb->eu[flat];
-      cl = eu > 0.0;
+      cl = dgt0(eu);
     } else {
       double rc, ec;
       eos_inputs(p, rho, U, rc, ec);

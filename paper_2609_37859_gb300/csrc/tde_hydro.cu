@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
       }
       double r2 = 0.0;
       if (bh.on || bh.excise) r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      if (bh.excise && sqrt(r2) < bh.rexc) skip = true;
+      if (bh.excise && inside_radius(r2, bh.rexc)) skip = true;
       if (!skip) {
         const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
         const double cs = sqrt_ratio(g1 * w[4], w[0]);
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         if (bh.on) {
           double s2 = r2 + bh.rs2;
           double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-          if (gmag > 0.0) best = fmin(best, sqrt(scale2i(p.dxmin, -B.level) / gmag));
+          if (dgt0(gmag)) best = dmin(best, sqrt(scale2i(p.dxmin, -B.level) / gmag));
         }
       }
     }
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NT) k_excise(Phys p, BH bh, TimeArgs ta,
   cell_centre(p, B, c, x);
   bh_pos(bh, ta_t(ta, b) + ta_dt(ta, b), rb);
   const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
-  if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) < bh.rexc)) return;
+  if (!inside_radius(d0 * d0 + d1 * d1 + d2 * d2, bh.rexc)) return;
   const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
   U[flat] = p.rho_floor;
   U[ntot + flat] = 0.0;
@@ -288,15 +288,21 @@ __global__ void __launch_bounds__(NT) k_sync(Phys p, const DevBlock *__restrict_
   const long long flat = B.off + c[2] * sz + c[1] * sy + c[0];
   const double *E = U + 4 * ntot;
   const int ax = p.active[0], ay = p.active[1], az = p.active[2];
-  double emax = -INFINITY;
+  // the neighbourhood maximum on the integer pipe: order keys of the bit
+  // patterns (the key map is its own inverse), 27 FP64 max operations saved
+  long long kmax = dkey(-INFINITY);
   for (int dk = -az; dk <= az; ++dk)
     for (int dj = -ay; dj <= ay; ++dj)
-      for (int di = -ax; di <= ax; ++di) emax = fmax(emax, E[flat + dk * sz + dj * sy + di]);
+      for (int di = -ax; di <= ax; ++di) {
+        const long long k = dkey(E[flat + dk * sz + dj * sy + di]);
+        kmax = k > kmax ? k : kmax;
+      }
+  const double emax = __longlong_as_double(kmax ^ ((kmax >> 63) & 0x7fffffffffffffffLL));
   const double u0 = U[flat], u1 = U[ntot + flat], u2 = U[2 * ntot + flat], u3 = U[3 * ntot + flat];
-  const double rho = u0 < p.rho_floor ? p.rho_floor : u0;
-  const double ir = 1.0 / rho;
+  const double rho = dlt(u0, p.rho_floor) ? p.rho_floor : u0;
+  const double ir = rcp_nr(rho);
   const double Uc = E[flat] - 0.5 * (u1 * (u1 * ir) + u2 * (u2 * ir) + u3 * (u3 * ir));
-  if (Uc > 0.0 && Uc > eta2 * emax) {
+  if (dgt0(Uc) && dlt(eta2 * emax, Uc)) {
     U[5 * ntot + flat] = Uc;
     count(&cnt->synced);
   }
@@ -415,7 +421,7 @@ __global__ void __launch_bounds__(NT) k_frame_partial(Phys p, BH bh, const doubl
     cell_centre(p, B, c, x);
     const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    if (bh.excise && sqrt(r2) < bh.rexc) continue;
+    if (bh.excise && inside_radius(r2, bh.rexc)) continue;
     const double q2 = r2 + bh.rs2;
     const double gfac = -bh.GM / (q2 * sqrt(q2));   // g = -grad Phi_bh = -GM d / q^3
     const double rw = rho * vw;   // mass in level-0 cell volumes

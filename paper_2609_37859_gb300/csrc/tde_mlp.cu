@@ -495,33 +495,36 @@ __global__ void __launch_bounds__(256) k_eos_newton(DTable t, CellMap cm, const 
       double w;
       const bool cl = rho_cell(t, rho[c], i, w);
       const double e = en[c];
-      const double ly = e > 0.0 ? tlog10(t, e) : -INFINITY;
+      // the decisions below compare on the integer pipe (dgt0, dle, dlt: the
+      // same outcomes as the FP64 comparisons for every non-NaN value)
+      const bool pos = dgt0(e);
+      const double ly = pos ? tlog10(t, e) : -INFINITY;
       const double *__restrict__ ra = t.le + (size_t)i * nt;
       const double *__restrict__ rb = ra + nt;
       ok = false;
-      if (!cl && ly > -INFINITY) {
+      if (!cl && pos) {
         const float xg = (lTg[c] - (float)t.lt0) * idlt;
         int j = (int)floorf(fminf(fmaxf(xg, 0.f), (float)(nt - 2)));
         j = min(max(j, 0), nt - 2);
         double g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
         double g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
         double sc = cell_solve(ly, g0, g1);
-        bool in = g0 <= ly && ly < g1;
+        bool in = dle(g0, ly) && dlt(ly, g1);
         if (!in) {
-          const double xn = (double)j + sc;   // the Newton result, in cell units
-          if (xn >= 0.0 && xn < (double)(nt - 1)) {
-            const int j2 = (int)floor(xn);
+          const double xn = __dadd_rn(dint(j), sc);   // the Newton result, in cell units
+          if (dge0(xn) && dlt(xn, dint(nt - 1))) {
+            const int j2 = ifloor_nonneg(xn);
             if (j2 != j) {
               j = j2;
               g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
               g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
-              in = g0 <= ly && ly < g1;
+              in = dle(g0, ly) && dlt(ly, g1);
               if (in) sc = cell_solve(ly, g0, g1);
             }
           }
         }
         // at the coldest node bisection clamps (y <= g_0): leave that to it
-        ok = in && (j > 0 || ly > g0);
+        ok = in && (j > 0 || dlt(g0, ly));
         if (ok) {
           if (P) P[c] = texp10(t, bilin(t.lp, nt, i, w, j, sc));
           if (cs2) cs2[c] = texp10(t, bilin(t.lc, nt, i, w, j, sc));

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
       na_bh_pos(bh, t_block ? t_block[b] : 0.0, rb);
       const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
       r2 = d0 * d0 + d1 * d1 + d2 * d2;
-      if (bh.excise && sqrt(r2) < bh.rexc) skip = true;
+      if (bh.excise && inside_radius(r2, bh.rexc)) skip = true;
     }
     if (!skip) {
       const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;

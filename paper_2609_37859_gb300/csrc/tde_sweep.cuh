@@ -145,11 +145,11 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       const double r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
       const int idx = D == 0 ? lane * NF + c : c * M + lane;
       if (grav) {
-        double ph = a.bh.on ? -a.bh.GM / sqrt(r2 + a.bh.rs2) : 0.0;
+        double ph = a.bh.on ? -a.bh.GM * rsqrt_nr(r2 + a.bh.rs2) : 0.0;
         if (a.phi_sg) ph += a.phi_sg[base + (long long)(g - 1 + c) * sD + lane * sL];   // Phi_bh + Phi_sg
         Ph[idx] = ph;
       }
-      if (exc) Ex[idx] = sqrt(r2) < a.bh.rexc ? 1 : 0;
+      if (exc) Ex[idx] = inside_radius(r2, a.bh.rexc) ? 1 : 0;
     }
   }
   __syncthreads();

@@ -13,7 +13,7 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
-MATH_RCP, MATH_SQRT_RATIO, MATH_RCP_SEED, MATH_RSQRT_SEED = range(4)
+MATH_RCP, MATH_SQRT_RATIO, MATH_RCP_SEED, MATH_RSQRT_SEED, MATH_RSQRT, MATH_INSIDE = range(6)
 TDE_OK, TDE_EINVAL, TDE_ENOMEM, TDE_ECUDA, TDE_ERANGE, TDE_ENUMERIC, TDE_ETIMEOUT = range(7)
 EOS_IDEAL, EOS_TABLE = 0, 1
 RECON_PLM, RECON_PPM = 0, 1

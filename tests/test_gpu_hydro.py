@@ -433,6 +433,40 @@ def test_reciprocal_and_sqrt_ratio_against_correct_rounding(tde, ctx):
     assert u.max() <= 1.0, u.max()
     u = _ulps(run(tde.MATH_SQRT_RATIO, yd), np.sqrt(x / y))
     assert u.max() <= 2.0, u.max()
+    u = _ulps(run(tde.MATH_RSQRT), 1.0 / np.sqrt(x))
+    assert u.max() <= 2.0, u.max()
+
+
+def test_excision_radius_test_is_exact(tde, ctx):
+    """The excision test sqrt(r2) < r taken without the square root away from
+    the boundary: identical decisions to numpy's correctly rounded sqrt, on
+    squared radii a few ulps either side of r^2, exact squares, random values,
+    zero, and radii of zero, near the subnormals, negative and NaN."""
+    rng = np.random.default_rng(31)
+    r = np.concatenate([10 ** rng.uniform(-150, 150, 20000), rng.uniform(0.01, 0.1, 20000)])
+    r2 = r * r
+    cases_x, cases_y = [], []
+    for k in range(-6, 7):   # r2 nudged k ulps from r^2
+        v = r2.copy()
+        for _ in range(abs(k)):
+            v = np.nextafter(v, np.inf if k > 0 else 0.0)
+        cases_x.append(v)
+        cases_y.append(r)
+    rs = np.nextafter(r, np.inf)   # squares of the neighbouring radii
+    cases_x += [rs * rs, r2 * (1 + 2.0 ** -40), r2 * (1 - 2.0 ** -40), 10 ** rng.uniform(-300, 300, 20000)]
+    cases_y += [r, r, r, 10 ** rng.uniform(-150, 150, 20000)]
+    cases_x.append(np.array([0.0, 0.0, 1.0, 0.0, 1e-310, 4e-320, 1.0, 1.0, np.inf, 1.0]))
+    cases_y.append(np.array([0.0, 1.0, 0.0, -1.0, 1e-155, 2e-160, np.nan, np.inf, 1.0, -0.0]))
+    x, y = np.concatenate(cases_x), np.concatenate(cases_y)
+    with np.errstate(invalid="ignore"):
+        want = (np.sqrt(x) < y).astype(np.float64)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = torch.empty_like(xd)
+    ctx.math_probe(tde.MATH_INSIDE, xd, out, yd)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, list(zip(x[bad][:5], y[bad][:5]))
 
 
 # ------------------------------------------------ determinism, failure reporting ----
