@@ -587,7 +587,8 @@ int lat_fail(tde_ctx *c, int code, const char *msg) {
   } while (0)
 
 
-// host-side level lists from the factors; allocates the LAT buffers once
+// level lists from the factors (sorted on the host, the ghost-conversion list built
+// on the device); allocates the LAT buffers once
 int lat_build(tde_mesh *m) {
   tde_ctx *c = m->ctx;
   const int nb = m->nb;
