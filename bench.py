@@ -848,8 +848,23 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
     mesh.lat_set_factors(fac, dt0)
     mesh.lat_window(bh=bh, use_graph=False)   # warm-up: eager, then capture
     mesh.lat_window(bh=bh, use_graph=True)
+    # where the first window's time goes: an eager window with CUDA events around
+    # every launch, by kernel class, and a synchronised step the same way
+    by_kind = {}
+    for name, fn in (("lat_window", lambda: mesh.lat_window(bh=bh, use_graph=False)),
+                     ("sync_step", lambda: mesh.step(dt=dt0, bh=bh))):
+        mesh.U.copy_(U0)
+        mesh.set_time(0.0)
+        mesh.lat_set_factors(fac, dt0)
+        torch.cuda.synchronize(dev)
+        ctx.profile(True)
+        fn()
+        torch.cuda.synchronize(dev)
+        by_kind[name] = {k: round(v[1], 3) for k, v in ctx.profile_read().items() if v[0]}
+        ctx.profile(False)
     mesh.U.copy_(U0)
     mesh.set_time(0.0)
+    mesh.lat_set_factors(fac, dt0)
     mesh.counts(reset=True)
     fmaxes, structures = [], set()
 
@@ -884,6 +899,7 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
             "sync_cell_updates_per_s": ncell / (ms_step * 1e-3),
             "floors": {"rho_floor": floors[0], "p_floor": floors[1], "unit": "rho0, rho0 v0^2"},
             "counters_per_window": {k: v // nwin for k, v in c.items()},
+            "first_window_ms_by_kernel_class": by_kind,
             "host_setup_s": setup_s}
 
 
