@@ -164,10 +164,13 @@ def test_c2_entropy_wave_parity(oracle, tde, ctx, tables):
     assert_parity(lay.to_global(P.gpu("U1")), lay.to_global(O1), STAGE_TOL, "stage 0")
     U = P.U.copy()
     gm.set_time(0.0)
+    gm.counts(reset=True)
+    oc = {}
     t = 0.0
     for s in range(100):
         d = om.cfl_dt(U, 0.3).min()
-        om.step(U, d, t)
+        for k, v in om.step(U, d, t).as_dict().items():
+            oc[k] = oc.get(k, 0) + v
         gm.step(cfl=0.3)
         t += d
         if s + 1 in (20, 100):
@@ -175,6 +178,7 @@ def test_c2_entropy_wave_parity(oracle, tde, ctx, tables):
             assert_parity(G, lay.to_global(U), STEPS_TOL, "%d steps" % (s + 1))
     assert gm.get_time() == pytest.approx(t, rel=1e-13)
     c = gm.counts()
+    assert {k: c[k] for k in oc} == oc   # the same branch decisions (no flips)
     assert c["table_clamp"] == 0 and c["dual_aux_used"] > 0 and c["nonfinite"] == 0
 
 
@@ -288,16 +292,25 @@ def test_bh_excision_ppm_table_code_units(oracle, tde, ctx, tables):
              rho_floor=1e-10, p_floor=1e-16, u_floor=1.5e-16, unit_rho=rho0, unit_e=v0 * v0)
     U = P.U.copy()
     P.gm.set_time(0.0)
+    P.gm.counts(reset=True)
+    oc = {}
     t = 0.0
-    dtb = P.dvec(0.0)
-    for _ in range(5):
+    for s in range(100):
         d = P.om.cfl_dt(U, 0.3, np.full(P.nb, t)).min()
-        P.om.step(U, d, t)
+        for k, v in P.om.step(U, d, t).as_dict().items():
+            oc[k] = oc.get(k, 0) + v
         t += d
         P.gm.step(cfl=0.3, bh=P.bh)
-    assert P.gm.get_time() == pytest.approx(t, rel=1e-12)
-    G = lay.to_global(P.gpu("U"))
-    assert_parity(G, lay.to_global(U), STEPS_TOL, "bh")
+        if s + 1 in (5, 100):
+            assert P.gm.get_time() == pytest.approx(t, rel=1e-12)
+            G = lay.to_global(P.gpu("U"))
+            assert_parity(G, lay.to_global(U), STEPS_TOL, "bh, %d steps" % (s + 1))
+    # the branch decisions (floors, table clamps, excision, dual-energy switch and
+    # resync) taken the same number of times on both sides: no flips
+    gc = P.gm.counts()
+    print("decision counts, oracle", oc, "gpu", gc)
+    assert {k: gc[k] for k in oc} == oc
+    assert oc["excised"] > 0 and oc["dual_aux_used"] > 0
     c = P.gm.counts()
     assert c["excised"] > 0 and c["nonfinite"] == 0
 
