@@ -517,6 +517,18 @@ enum {
 TDE_API int tde_math_probe(tde_ctx *ctx, int op, int64_t n, const double *x, const double *y,
                            double *out);
 
+/* The Riemann solvers of the sweeps (a5, Sec. 2.1) on n face-state pairs, for a
+ * unit check against an independent implementation: solver TDE_RIEMANN_HLLC or
+ * TDE_RIEMANN_HLLE across a face normal to direction d (0, 1, 2).  wl, wr: device
+ * arrays [n][8] of the left and right face states (rho, vx, vy, vz, P, Gamma_e,
+ * Gamma_1, U_aux); with eos_table = 0 the two Gammas are ignored and gamma is
+ * used, with dual = 0 U_aux is ignored.  F: device [n][6], the mass, momentum (x, y,
+ * z), energy and U_aux fluxes (U_aux flux 0 unless dual); vf: device [n], the face
+ * velocity of Eq. dual-face-velocity (0 unless dual).  TDE_EINVAL for a bad solver,
+ * direction or gamma, or null arrays with n > 0; asynchronous on the context's stream. */
+TDE_API int tde_riemann_probe(tde_ctx *ctx, int solver, int d, int eos_table, int dual, double gamma,
+                              int64_t n, const double *wl, const double *wr, double *F, double *vf);
+
 /* Measured FP64 fused multiply-add throughput of the device (FLOP/s, an FMA
  * counted as 2), from a kernel of independent FMA chains on every SM.  The
  * hydro stage is bound by this rate on sm_103a.  Synchronises the stream. */

@@ -170,6 +170,12 @@ void tref_cfl_dt(const tref_mesh *m, const double *U, double cfl, const double *
 void tref_step(const tref_mesh *m, double *U, double *Uscr, double dt, double t, tref_counts *c);
 /* Primitive (rho, vx, vy, vz, P) per interior cell -> conserved state, U_aux = U. */
 void tref_prim_to_cons(const tref_mesh *m, const double *W, double *U);
+/* a5 on n face-state pairs: HLLC (solver 0) or HLLE (1) across a face normal to
+ * direction d; wl, wr [n][8] = (rho, vx, vy, vz, P, Gamma_e, Gamma_1, U_aux) (an
+ * ideal gas has Gamma_e = Gamma_1 = gamma); F [n][6] = mass, momentum, energy and
+ * U_aux fluxes (the last 0 unless dual), vf [n] = face velocity. */
+void tref_riemann(int solver, int d, int dual, int64_t n, const double *wl, const double *wr, double *F,
+                  double *vf);
 /* Softened point-mass potential at position x (Eq. bh-softened-gravity). */
 double tref_phi_bh(const tref_params *p, const double *x, double t);
 

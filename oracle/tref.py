@@ -128,6 +128,7 @@ def lib():
             "tref_step": (None, [C.c_void_p, dp, dp, C.c_double, C.c_double, C.POINTER(Counts)]),
             "tref_prim_to_cons": (None, [C.c_void_p, dp, dp]),
             "tref_phi_bh": (C.c_double, [C.POINTER(Params), dp, C.c_double]),
+            "tref_riemann": (None, [C.c_int, C.c_int, C.c_int, C.c_int64, dp, dp, dp, dp]),
             "tref_mlp_forward": (None, [dp, C.c_int64, dp, dp]),
             "tref_mlp_loss_grad": (C.c_double, [dp, C.c_int64, dp, dp, dp]),
         }
@@ -358,6 +359,18 @@ class Mesh:
     def interior(self, U, var=None):
         """Global-grid array [nvar][Nz][Ny][Nx] of the interior cells."""
         return self.layout.to_global(U if var is None else U[var:var + 1])
+
+
+def riemann(solver, d, dual, wl, wr):
+    """a5 on face-state pairs wl, wr [n][8] (rho, vx, vy, vz, P, Gamma_e, Gamma_1,
+    U_aux): fluxes [n][6] and face velocities [n]."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    n = len(wl)
+    F = np.zeros((n, 6))
+    vf = np.zeros(n)
+    lib().tref_riemann(solver, d, dual, n, P(wl), P(wr), P(F), P(vf))
+    return F, vf
 
 
 def mlp_forward(params, x):

@@ -553,6 +553,16 @@ static void hlle(const double *wl, const double *wr, int d, int dual, double *F,
   }
 }
 
+/* The Riemann solvers on n face-state pairs (a unit check of a5): wl, wr are
+ * [n][8] primitives (rho, vx, vy, vz, P, Gamma_e, Gamma_1, U_aux), F [n][6], vf [n]. */
+void tref_riemann(int solver, int d, int dual, int64_t n, const double *wl, const double *wr, double *F,
+                  double *vf) {
+  for (int64_t q = 0; q < n; ++q) {
+    if (solver == TREF_HLLE) hlle(wl + 8 * q, wr + 8 * q, d, dual, F + 6 * q, vf + q);
+    else hllc(wl + 8 * q, wr + 8 * q, d, dual, F + 6 * q, vf + q);
+  }
+}
+
 /* -------------------------------------------------------------- stage ----- */
 
 /* flux-register layout of one block: sides x-, x+, y-, y+, z-, z+; each

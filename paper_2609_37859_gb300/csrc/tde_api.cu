@@ -1083,6 +1083,53 @@ __global__ void k_math_probe(int op, long long n, const double *x, const double 
     out[i] = r;
   }
 }
+
+template <int D, int EOSK, int DUAL, int SOLVER>
+__global__ void k_riemann_probe(Phys p, long long n, const double *__restrict__ wl,
+                                const double *__restrict__ wr, double *F, double *vf) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double *a = wl + 8 * i, *b = wr + 8 * i;
+    FState L, R;
+    L.r = a[0]; R.r = b[0];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) { L.v[q] = a[1 + q]; R.v[q] = b[1 + q]; }
+    L.P = a[4]; R.P = b[4];
+    // as the sweeps assemble the states
+    if (EOSK == EOS_TABLE) {
+      L.ge = a[5]; L.g1 = a[6]; R.ge = b[5]; R.g1 = b[6];
+    } else {
+      L.ge = L.g1 = R.ge = R.g1 = p.gamma;
+    }
+    L.A = DUAL ? a[7] : 0.0;
+    R.A = DUAL ? b[7] : 0.0;
+    double f[6], v;
+    if (SOLVER == RIEMANN_HLLE) hlle<D, EOSK, DUAL>(p, L, R, f, v);
+    else hllc<D, EOSK, DUAL>(p, L, R, f, v);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) F[6 * i + q] = f[q];
+    vf[i] = v;
+  }
+}
+
+template <int D, int EOSK, int DUAL>
+void riemann_probe_solver(int solver, const Phys &p, long long n, const double *wl, const double *wr,
+                          double *F, double *vf, unsigned grid, cudaStream_t s) {
+  if (solver == RIEMANN_HLLE) k_riemann_probe<D, EOSK, DUAL, RIEMANN_HLLE><<<grid, 256, 0, s>>>(p, n, wl, wr, F, vf);
+  else k_riemann_probe<D, EOSK, DUAL, RIEMANN_HLLC><<<grid, 256, 0, s>>>(p, n, wl, wr, F, vf);
+}
+
+template <int D>
+void riemann_probe_dir(int solver, int table, int dual, const Phys &p, long long n, const double *wl,
+                       const double *wr, double *F, double *vf, unsigned grid, cudaStream_t s) {
+  if (table) {
+    if (dual) riemann_probe_solver<D, EOS_TABLE, 1>(solver, p, n, wl, wr, F, vf, grid, s);
+    else riemann_probe_solver<D, EOS_TABLE, 0>(solver, p, n, wl, wr, F, vf, grid, s);
+  } else {
+    if (dual) riemann_probe_solver<D, EOS_IDEAL, 1>(solver, p, n, wl, wr, F, vf, grid, s);
+    else riemann_probe_solver<D, EOS_IDEAL, 0>(solver, p, n, wl, wr, F, vf, grid, s);
+  }
+}
 }  // namespace tde
 
 extern "C" int tde_math_probe(tde_ctx *c, int op, int64_t n, const double *x, const double *y,
@@ -1095,6 +1142,28 @@ extern "C" int tde_math_probe(tde_ctx *c, int op, int64_t n, const double *x, co
   ProfScope ps(c, TDE_K_PROBE);
   k_math_probe<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(
       op, (long long)n, x, y, out);
+  CK(c, cudaGetLastError());
+  return TDE_OK;
+}
+
+extern "C" int tde_riemann_probe(tde_ctx *c, int solver, int d, int eos_table, int dual, double gamma,
+                                 int64_t n, const double *wl, const double *wr, double *F, double *vf) {
+  if (!c) return TDE_EINVAL;
+  if ((solver != RIEMANN_HLLC && solver != RIEMANN_HLLE) || d < 0 || d > 2 || !(gamma > 1.0) || n < 0 ||
+      (n > 0 && (!wl || !wr || !F || !vf)))
+    return fail(c, TDE_EINVAL, "tde_riemann_probe: arguments");
+  if (n == 0) return TDE_OK;
+  Phys p{};
+  p.gamma = gamma;
+  p.gm1 = gamma - 1.0;
+  p.inv_gm1 = 1.0 / (gamma - 1.0);
+  p.riemann = solver;
+  ProfScope ps(c, TDE_K_PROBE);
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  const int t = eos_table ? 1 : 0, du = dual ? 1 : 0;
+  if (d == 0) riemann_probe_dir<0>(solver, t, du, p, (long long)n, wl, wr, F, vf, grid, c->stream);
+  else if (d == 1) riemann_probe_dir<1>(solver, t, du, p, (long long)n, wl, wr, F, vf, grid, c->stream);
+  else riemann_probe_dir<2>(solver, t, du, p, (long long)n, wl, wr, F, vf, grid, c->stream);
   CK(c, cudaGetLastError());
   return TDE_OK;
 }

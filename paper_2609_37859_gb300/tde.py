@@ -128,6 +128,7 @@ _SIGS = {
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
     "tde_math_selftest": [vp, C.c_int64, dp, dp, dp],
     "tde_math_probe": [vp, C.c_int, C.c_int64, dp, dp, dp],
+    "tde_riemann_probe": [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64, dp, dp, dp, dp],
     "tde_mesh_autotune": [vp, C.POINTER(BHState), C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
     "tde_frame_acceleration": [vp, C.POINTER(BHState), C.c_double, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
@@ -225,6 +226,11 @@ class Context:
 
     def math_probe(self, op, x, out, y=None):
         self.check(lib().tde_math_probe(self.h, op, x.numel(), _ptr(x), _ptr(y), _ptr(out)))
+
+    def riemann_probe(self, solver, d, wl, wr, F, vf, eos_table=1, dual=1, gamma=5.0 / 3.0):
+        """The sweeps' Riemann solver on face-state pairs wl, wr [n][8] (device)."""
+        self.check(lib().tde_riemann_probe(self.h, solver, d, eos_table, dual, gamma, wl.shape[0], _ptr(wl),
+                                           _ptr(wr), _ptr(F), _ptr(vf)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -511,3 +511,85 @@ def test_boost_closed_form_and_inverse(oracle):
     assert floor_cells.any()
     m.boost(U, -V, rho_min)
     assert np.allclose(m.interior(U), G, rtol=1e-13, atol=1e-14)
+
+
+# ------------------------------------------ the Riemann solvers on face pairs ----
+
+def _face_states(rng, n, table=True):
+    w = np.empty((n, 8))
+    w[:, 0] = 10 ** rng.uniform(-2, 1, n)
+    w[:, 1:4] = rng.normal(0, 1, (n, 3))
+    w[:, 4] = 10 ** rng.uniform(-2, 1, n)
+    w[:, 5] = rng.uniform(1.1, 1.7, n) if table else 5.0 / 3.0
+    w[:, 6] = rng.uniform(1.1, 1.8, n) if table else 5.0 / 3.0
+    w[:, 7] = w[:, 4] / (w[:, 5] - 1.0) * rng.uniform(0.5, 1.5, n)
+    return w
+
+
+def _euler_flux(w, d):
+    """The Euler flux of one state (the value any consistent solver returns for
+    identical left and right states)."""
+    rho, un, P = w[:, 0], w[:, 1 + d], w[:, 4]
+    E = P / (w[:, 5] - 1.0) + 0.5 * rho * (w[:, 1:4] ** 2).sum(axis=1)
+    F = np.zeros((len(w), 6))
+    F[:, 0] = rho * un
+    for q in range(3):
+        F[:, 1 + q] = rho * un * w[:, 1 + q]
+    F[:, 1 + d] += P
+    F[:, 4] = (E + P) * un
+    F[:, 5] = rho * un * w[:, 7] / rho
+    return F
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_riemann_consistency_upwinding_and_mirror_symmetry(oracle, solver):
+    """a5 on face-state pairs: identical states give the Euler flux; states moving
+    supersonically to the right (left) give the left (right) state's flux; the
+    mirror image (left and right exchanged, normal velocity negated) negates the
+    mass, transverse-momentum, energy and U_aux fluxes and the face velocity and
+    keeps the normal-momentum flux; a stationary contact carries only the pressure
+    under HLLC and diffuses mass under HLLE."""
+    rng = np.random.default_rng(41)
+    n = 2000
+    for d in range(3):
+        wl = _face_states(rng, n)
+        F, vf = oracle.riemann(solver, d, 1, wl, wl)
+        Fe = _euler_flux(wl, d)
+        assert np.allclose(F, Fe, rtol=1e-13, atol=1e-13 * np.abs(Fe).max())
+        assert np.allclose(vf, wl[:, 1 + d], rtol=1e-13, atol=1e-15)
+        # supersonic both ways: |u| > c on both sides
+        wr = _face_states(rng, n)
+        c = np.sqrt(np.maximum(wl[:, 6] * wl[:, 4] / wl[:, 0], wr[:, 6] * wr[:, 4] / wr[:, 0]))
+        for sgn in (1.0, -1.0):
+            a, b = wl.copy(), wr.copy()
+            a[:, 1 + d] = sgn * (2.0 * c + np.abs(a[:, 1 + d]))
+            b[:, 1 + d] = sgn * (2.0 * c + np.abs(b[:, 1 + d]))
+            F, _ = oracle.riemann(solver, d, 1, a, b)
+            Fu = _euler_flux(a if sgn > 0 else b, d)
+            assert np.allclose(F, Fu, rtol=1e-13, atol=1e-13 * np.abs(Fu).max())
+        # mirror symmetry on general pairs
+        F, vf = oracle.riemann(solver, d, 1, wl, wr)
+        ml, mr = wr.copy(), wl.copy()
+        ml[:, 1 + d] *= -1
+        mr[:, 1 + d] *= -1
+        Fm, vfm = oracle.riemann(solver, d, 1, ml, mr)
+        sign = -np.ones(6)
+        sign[1 + d] = 1.0
+        scale = np.abs(F).max(axis=0) + 1e-300
+        assert np.all(np.abs(Fm - sign * F) <= 1e-13 * scale)
+        assert np.allclose(vfm, -vf, rtol=1e-12, atol=1e-14 * np.abs(vf).max())
+    # stationary contact: equal pressure, zero velocity, density jump
+    wl = _face_states(rng, n)
+    wr = wl.copy()
+    wl[:, 1:4] = 0.0
+    wr[:, 1:4] = 0.0
+    wr[:, 0] *= 10 ** rng.uniform(-2, 2, n)
+    F, vf = oracle.riemann(solver, 0, 1, wl, wr)
+    assert np.allclose(F[:, 1], wl[:, 4], rtol=1e-13)
+    if solver == 0:   # zero up to the rounding of rho (S - u) / (S - S_M) against rho
+        c = np.sqrt(np.maximum(wl[:, 6] * wl[:, 4] / wl[:, 0], wr[:, 6] * wr[:, 4] / wr[:, 0]))
+        sc = (wl[:, 0] + wr[:, 0] + wl[:, 4] / (wl[:, 5] - 1.0) + wl[:, 7]) * c
+        assert np.all(np.abs(F[:, [0, 2, 3, 4, 5]]) <= 1e-13 * sc[:, None])
+        assert np.all(np.abs(vf) <= 1e-13 * c)
+    else:
+        assert np.all(np.sign(F[:, 0]) == np.sign(wl[:, 0] - wr[:, 0]))   # mass diffuses downhill
