@@ -325,6 +325,23 @@ TDE_API int tde_lat_window(tde_mesh *mesh, const tde_bh_state *bh, int use_graph
  * optionally reset them. */
 TDE_API int tde_counts_read(tde_mesh *mesh, tde_counts *out, int reset);
 
+/* Health of the asynchronous work so far (synchronises the stream; changes no
+ * state but the expiry flag).  tde_mesh_check: TDE_ENUMERIC if a kernel counted a
+ * non-finite value or a non-positive density after the floors since the counters
+ * were last reset, else the result of tde_eos_check on the mesh's EOS.
+ * tde_eos_check: TDE_ETIMEOUT if a bounded device wait of the learned-guess
+ * inference expired since the last check (the cells of its tiles then took the
+ * bisection fallback, so the results stand), clearing the flag; else TDE_OK.
+ * tde_last_error() names the count or the wait. */
+TDE_API int tde_mesh_check(tde_mesh *mesh);
+TDE_API int tde_eos_check(tde_eos *eos);
+/* Failure-detection test hook: with on != 0 the learned-guess inference issues
+ * no tensor-core work, so that its bounded wait for the results expires and
+ * takes the timeout path (about two seconds per launch: one-second limits on the
+ * wait for the results and on the wait for work in flight); results stay those
+ * of bisection.  on = 0 restores normal operation. */
+TDE_API int tde_eos_inject_wait_expiry(tde_eos *eos, int on);
+
 /* ---- allocation-free variant ---------------------------------------------- */
 
 /* A tabulated EOS held in device arrays that the caller owns (same layout and

@@ -976,6 +976,20 @@ extern "C" int tde_counts_read(tde_mesh *m, tde_counts *out, int reset) {
   return TDE_OK;
 }
 
+extern "C" int tde_mesh_check(tde_mesh *m) {
+  if (!m) return TDE_EINVAL;
+  Counters h;
+  CK(m->ctx, cudaMemcpyAsync(&h, m->d_cnt, sizeof h, cudaMemcpyDeviceToHost, m->ctx->stream));
+  CK(m->ctx, cudaStreamSynchronize(m->ctx->stream));
+  if (h.nonfinite) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "tde_mesh_check: %llu non-finite or non-positive-density results",
+             (unsigned long long)h.nonfinite);
+    return fail(m->ctx, TDE_ENUMERIC, msg);
+  }
+  return m->eos ? tde_eos_check(m->eos) : TDE_OK;
+}
+
 // ====================================================== measurement ====
 
 extern "C" int tde_profile(tde_ctx *ctx, int enable) {

@@ -74,6 +74,7 @@ struct tde_eos {
   int64_t queue_cap = 0;
   unsigned long long *d_qcount = nullptr;
   int *d_status = nullptr;
+  int inject_wait_expiry = 0;        // test hook: inference issues no tensor-core work
 };
 
 namespace tde {

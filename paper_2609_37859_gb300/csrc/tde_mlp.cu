@@ -234,6 +234,25 @@ __device__ __forceinline__ uint32_t core_off(int r, int k) {
 
 constexpr int IT = 128;   // cells per tile = threads per CTA
 
+// Wait until the mbarrier's phase of the given parity completes, for at most one
+// second of the global nanosecond timer (try_wait may suspend the thread for a
+// while, so the limit is on time, not on polls); false if it expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t parity) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar_addr), "r"(parity));
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
 struct SurrogateArgs {
   DTable t;
   MLPNorm nm;
@@ -245,6 +264,7 @@ struct SurrogateArgs {
   const float *xin;   // optional: network inputs instead of (rho, e) [n][2]
   Counters *cnt;
   int *status;        // set to 1 if a bounded wait expired
+  int skip_mma;       // failure-detection test: issue no MMA, so the wait expires
   float *lTg;         // optional: the guessed log10 T of each cell
   CellMap cm;         // which cells: plain arrays (cm.blocks null) or cells of blocks
 };
@@ -373,7 +393,7 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     // ---- layer 2 on the tensor core: D[128 x 64] = h1[128 x 64] * W2^T
-    if (tid == 0) {
+    if (tid == 0 && !a.skip_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
       for (int ks = 0; ks < H / 16; ++ks) {
@@ -388,18 +408,8 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           mbar_addr));
     }
-    // bounded wait for the MMAs (about 1 s of polling at most)
-    {
-      uint32_t done = 0;
-      for (long long it = 0; it < (1ll << 22) && !done; ++it) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar_addr), "r"(phase));
-      }
-      if (!done) s_abort = 1;
-    }
+    // bounded wait for the MMAs (one second of the global timer at most)
+    if (!mbar_wait_bounded(mbar_addr, phase)) s_abort = 1;
     phase ^= 1u;
     __syncthreads();
     if (s_abort) break;
@@ -440,17 +450,7 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   }
   if (s_abort && tid == 0) atomicExch(a.status, 1);
   // wait (bounded) for any MMA still in flight before freeing tensor memory
-  if (s_abort) {
-    for (long long it = 0; it < (1ll << 22); ++it) {
-      uint32_t done;
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-          "selp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(done)
-          : "r"(mbar_addr), "r"(phase ^ 1u));
-      if (done) break;
-    }
-  }
+  if (s_abort) mbar_wait_bounded(mbar_addr, phase ^ 1u);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -675,6 +675,7 @@ cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, 
   a.xin = xin;
   a.cnt = e->d_cnt;
   a.status = e->d_status;
+  a.skip_mma = e->inject_wait_expiry;
   a.lTg = lTg;
   a.cm = cm ? *cm : CellMap{};
   int sms = 152;
@@ -770,6 +771,26 @@ extern "C" int tde_eos_surrogate_reset(tde_eos *e) {
   if (!e) return TDE_EINVAL;
   e->has_net = false;
   return TDE_OK;
+}
+
+extern "C" int tde_eos_inject_wait_expiry(tde_eos *e, int on) {
+  if (!e) return TDE_EINVAL;
+  e->inject_wait_expiry = on ? 1 : 0;
+  return TDE_OK;
+}
+
+extern "C" int tde_eos_check(tde_eos *e) {
+  if (!e) return TDE_EINVAL;
+  tde_ctx *c = e->ctx;
+  MCK(c, cudaStreamSynchronize(c->stream));
+  if (!e->d_status) return TDE_OK;
+  int st = 0;
+  MCK(c, cudaMemcpy(&st, e->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!st) return TDE_OK;
+  MCK(c, cudaMemset(e->d_status, 0, sizeof(int)));
+  return mlp_fail(c, TDE_ETIMEOUT,
+                  "learned-guess inference: a bounded wait for the tensor-core results expired (the cells "
+                  "took the bisection fallback)");
 }
 
 extern "C" int tde_eos_surrogate_norm(const tde_eos *e, double *out8) {

@@ -123,6 +123,9 @@ _SIGS = {
     "tde_mesh_get_time": [vp, C.POINTER(C.c_double)],
     "tde_step": [vp, C.c_double, C.c_double, C.POINTER(BHState), dp],
     "tde_counts_read": [vp, C.POINTER(Counts), C.c_int],
+    "tde_mesh_check": [vp],
+    "tde_eos_check": [vp],
+    "tde_eos_inject_wait_expiry": [vp, C.c_int],
     "tde_profile": [vp, C.c_int],
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
@@ -274,6 +277,15 @@ class EOS:
         self.ctx.check(lib().tde_eos_invert(self.h, INVERT_BISECT, 0, None, None, None, None, None,
                                             C.byref(c)))
         return c.as_dict()
+
+    def check(self):
+        """Raise TDEError (TDE_ETIMEOUT) if a bounded wait of the learned-guess
+        inference expired since the last check."""
+        self.ctx.check(lib().tde_eos_check(self.h))
+
+    def inject_wait_expiry(self, on=True):
+        """Failure-detection test hook: the inference's bounded wait expires."""
+        self.ctx.check(lib().tde_eos_inject_wait_expiry(self.h, 1 if on else 0))
 
     def set_weights(self, w):
         a = np.ascontiguousarray(w, dtype=np.float32)
@@ -490,6 +502,11 @@ class Mesh:
         c = Counts()
         self.ctx.check(lib().tde_counts_read(self.h, C.byref(c), 1 if reset else 0))
         return c.as_dict()
+
+    def check(self):
+        """Raise TDEError (TDE_ENUMERIC: non-finite results counted since the last
+        counter reset; TDE_ETIMEOUT: an expired wait of the learned guess)."""
+        self.ctx.check(lib().tde_mesh_check(self.h))
 
     def close(self):
         if getattr(self, "h", None):

@@ -520,10 +520,15 @@ def test_bad_state_is_reported_not_trapped(oracle, tde, ctx):
     c = P.gm.counts()
     assert c["rho_floor"] > 0 and c["p_floor"] + c["dual_aux_used"] > 0
     assert c["nonfinite"] > 0        # the NaN propagates into its neighbourhood and is counted
+    with pytest.raises(tde.TDEError) as ei:   # and reported through the ABI
+        P.gm.check()
+    assert ei.value.code == tde.TDE_ENUMERIC
     torch.cuda.synchronize()         # the context is still usable
     P.gm.U.copy_(torch.from_numpy(P.U))
+    P.gm.counts(reset=True)
     P.gm.step(dt=1e-4)
     assert np.isfinite(P.gpu("U")).all()
+    P.gm.check()                     # healthy again
 
 
 def test_excision_with_extreme_floors_stays_finite(oracle, tde, ctx):

@@ -186,3 +186,37 @@ def test_what_training_buys(tde, oracle, env, trained):
     assert acc_trained > 0.7
     assert acc_trained > max(acc_random, acc_random2) + 0.3
     assert acceptance() == acc_trained   # the trained weights are back
+
+
+def test_expired_wait_is_reported_and_results_stand(tde, oracle, env, trained):
+    """Failure detection without a fault: the test hook makes the inference issue
+    no tensor-core work, so its bounded wait for the results expires; the kernel
+    sets the status word and returns, tde_eos_check reports TDE_ETIMEOUT once, the
+    cells take the bisection fallback (results identical to bisection) and the
+    context stays usable."""
+    ctx, eos, _ = env
+    rng = np.random.default_rng(77)
+    n = 4096
+    rho = torch.tensor(10 ** rng.uniform(-14, 2, n), dtype=torch.float64, device="cuda")
+    T0 = torch.tensor(10 ** rng.uniform(3.4, 5.4, n), dtype=torch.float64, device="cuda")
+    e = torch.empty_like(rho)
+    eos.eval_rhoT(rho, T0, e=e)
+    Tb, Pb = torch.empty_like(rho), torch.empty_like(rho)
+    eos.invert(rho, e, T=Tb, P=Pb, mode=tde.INVERT_BISECT)
+    eos.check()   # nothing pending
+    T, P = torch.empty_like(rho), torch.empty_like(rho)
+    eos.inject_wait_expiry(True)
+    try:
+        eos.invert(rho, e, T=T, P=P, mode=tde.INVERT_SURROGATE)
+        with pytest.raises(tde.TDEError) as ei:
+            eos.check()
+        assert ei.value.code == tde.TDE_ETIMEOUT
+    finally:
+        eos.inject_wait_expiry(False)
+    assert torch.equal(T, Tb) and torch.equal(P, Pb)
+    eos.check()   # the flag was cleared by the report
+    before = eos.counts()["surrogate_accepted"]
+    eos.invert(rho, e, T=T, P=P, mode=tde.INVERT_SURROGATE)
+    eos.check()
+    assert torch.equal(T, Tb) and torch.equal(P, Pb)
+    assert eos.counts()["surrogate_accepted"] - before > n // 2
