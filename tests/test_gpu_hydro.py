@@ -353,6 +353,22 @@ def test_dual_sync_and_excise_parity(oracle, tde, ctx):
     assert P.gm.counts()["excised"] > 0
 
 
+# ------------------------------------------------------- ghost gather ----
+
+@pytest.mark.parametrize("bc", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+def test_ghost_gather_bit_exact(oracle, tde, ctx, bc):
+    """a1 alone on mixed 8^3 / 4^3 blocks (PPM width 3): every padded cell after
+    the ghost fill equals the oracle's bit for bit (the fill only copies)."""
+    lay = wl.mixed_layout((16, 16, 8), 8, {(0, 0, 0), (1, 1, 0)}, ((0, 1), (0, 1), (0, 0.5)), bc, 3)
+    P = Pair(oracle, tde, ctx, lay, wl.random_smooth(lay, seed=5), recon=1, dual=1)
+    U = P.U.copy()
+    P.om.ghost_fill(U)
+    P.gm.ghost_fill(P.gm.U)
+    G = P.gpu("U")
+    assert np.array_equal(G, U)
+    assert not np.array_equal(G, P.U)   # ghosts were written
+
+
 # ------------------------------------------------------ EOS inversion ----
 
 def test_eos_invert_parity(oracle, tde, ctx, tables):
