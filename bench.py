@@ -15,6 +15,7 @@ is reported.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -156,6 +157,15 @@ def run_gpu(args):
     for _ in range(args.warmup):
         mesh.step(cfl=CFL)
     barrier()
+    # conservation audit of the timed steps (outside the timed region): the
+    # interior sums of the conserved fields, correctly rounded (math.fsum)
+    flat_int = torch.from_numpy(lay.interior_flat()).to(dev)
+
+    def audit():
+        G = mesh.U[:5][:, flat_int].cpu().numpy()
+        return [math.fsum(G[q]) for q in range(5)], [math.fsum(np.abs(G[q])) for q in range(5)]
+    sums0, scale0 = audit()
+    barrier()
     ctx.profile(True)
     clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                     if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
@@ -174,6 +184,12 @@ def run_gpu(args):
     ctx.profile(False)
     ms = max_over_ranks(ms, dist, dev)
     counts = mesh.counts()
+    sums1, _ = audit()
+    conservation = {"steps": args.steps, "summation": "math.fsum (correctly rounded) over the interior cells",
+                    "rel_drift": {name: abs(sums1[q] - sums0[q]) / max(scale0[q], 1e-300)
+                                  for q, name in enumerate(("mass", "momentum_x", "momentum_y", "momentum_z",
+                                                            "total_energy"))}}
+    del flat_int
 
     # ---- end-to-end through the C ABI with host buffers: every step copies its
     # state in from pinned host memory and its result back out.  Three device
@@ -278,6 +294,7 @@ def run_gpu(args):
             "clocks": clk,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "counters": counts,
+            "conservation": conservation,
         }
         if not args.no_eos:
             line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
