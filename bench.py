@@ -880,7 +880,7 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
     mesh.set_time(0.0)
     mesh.lat_set_factors(fac, dt0)
     mesh.counts(reset=True)
-    fmaxes, structures = [], set()
+    fmaxes, structures, works = [], set(), []
 
     def window():
         # as in production: factors from the CFL condition at each window start
@@ -888,6 +888,7 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
         fw, _, fm = mesh.lat_assign(6, CFL, merge_frac=0.01, bh=bh)
         fmaxes.append(int(fm))
         structures.add(tuple(int((fw == k).sum()) for k in (1, 2, 4, 8, 16, 32, 64)))
+        works.append(float((cells * (fm // fw)).sum() / (cells.sum() * fm)))
         mesh.lat_window(bh=bh, use_graph=True)
     ms_win = timed(window, nwin)
     c = mesh.counts(reset=True)
@@ -907,6 +908,8 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
             "work_fraction": work, "windows": nwin, "fine_steps": nwin * int(fmax),
             "autotune": autotune_report(tiles, tile_ms),
             "window_f_max": fmaxes, "distinct_level_structures": len(structures),
+            "work_fraction_per_window": works,
+            "ideal_speedup_timed_windows": 1.0 / float(np.mean(works)),
             "lat_window_ms": ms_win, "sync_step_ms": ms_step, "sync_window_ms_est": ms_step * fmax,
             "lat_speedup_vs_sync": ms_step * np.mean(fmaxes) / ms_win,
             "effective_cell_updates_per_s": ncell * np.mean(fmaxes) / (ms_win * 1e-3),
