@@ -155,29 +155,65 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   __syncthreads();
 
   // ---- B: face values of every cell adjacent to a face of the tile
-  for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
-    int c, lane;
-    split(e, nd + 2, c, lane);
-    if (lane >= nlane) continue;
-    const int pos = g - 1 + c;
+  if (RECON == PLM) {
+    for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
+      int c, lane;
+      split(e, nd + 2, c, lane);
+      if (lane >= nlane) continue;
+      const int pos = g - 1 + c;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double lo, hi;
-      if (RECON == PLM) {
+      for (int v = 0; v < NV; ++v) {
+        double lo, hi;
         plm(Wt[sw(v, pos - 1, lane)], Wt[sw(v, pos, lane)], Wt[sw(v, pos + 1, lane)], lo, hi);
-      } else {
-        const double qm2 = Wt[sw(v, pos - 2, lane)], qm1 = Wt[sw(v, pos - 1, lane)];
-        const double q0 = Wt[sw(v, pos, lane)], qp1 = Wt[sw(v, pos + 1, lane)];
-        const double qp2 = Wt[sw(v, pos + 2, lane)];
-        lo = ppm_iface(qm2, qm1, q0, qp1);
-        hi = ppm_iface(qm1, q0, qp1, qp2);
-        ppm_limit(q0, lo, hi);
+        FMs[sf(v, c, lane)] = lo;
+        FPs[sf(v, c, lane)] = hi;
       }
-      FMs[sf(v, c, lane)] = lo;
-      FPs[sf(v, c, lane)] = hi;
+    }
+    __syncthreads();
+  } else {
+    // PPM: the interpolated value of each of the nd + 3 interfaces once (a cell's
+    // upper interface is its neighbour's lower one), four variables at a time in
+    // the flux area (free until phase C: 4 (NF + 1) M <= 7 (NF - 1) M doubles for
+    // NF >= 4), then the monotonicity limits per cell
+    double *If = Fl;
+    const int NI = NF + 1, nfc = nd + 3;
+    auto si = [&](int vv, int f, int lane) {
+      return D == 0 ? (vv * M + lane) * NI + f : (vv * NI + f) * M + lane;
+    };
+#pragma unroll
+    for (int h = 0; h < NV; h += 4) {
+      for (int e = threadIdx.x; e < nfc * M; e += NTS) {
+        int f, lane;
+        split(e, nfc, f, lane);
+        if (lane >= nlane) continue;
+        const int p0 = g - 3 + f;   // interface f lies between cells p0 + 1 and p0 + 2
+#pragma unroll
+        for (int vv = 0; vv < 4; ++vv) {
+          if (h + vv >= NV) break;
+          const int v = h + vv;
+          If[si(vv, f, lane)] = ppm_iface(Wt[sw(v, p0, lane)], Wt[sw(v, p0 + 1, lane)],
+                                          Wt[sw(v, p0 + 2, lane)], Wt[sw(v, p0 + 3, lane)]);
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
+        int c, lane;
+        split(e, nd + 2, c, lane);
+        if (lane >= nlane) continue;
+        const int pos = g - 1 + c;
+#pragma unroll
+        for (int vv = 0; vv < 4; ++vv) {
+          if (h + vv >= NV) break;
+          const int v = h + vv;
+          double lo = If[si(vv, c, lane)], hi = If[si(vv, c + 1, lane)];
+          ppm_limit(Wt[sw(v, pos, lane)], lo, hi);
+          FMs[sf(v, c, lane)] = lo;
+          FPs[sf(v, c, lane)] = hi;
+        }
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
 
   // ---- C: one HLLC solve per face
   for (int e = threadIdx.x; e < (nd + 1) * M; e += NTS) {
