@@ -305,6 +305,16 @@ class Mesh:
                           P(np.ascontiguousarray(t_end_b, dtype=np.float64)), C.byref(c))
         return c
 
+    def cons_to_prim(self, u, counts=None):
+        """a2 + a3 on one cell: conserved u (5 or 6 values) -> primitives w[8]
+        (rho, vx, vy, vz, P, Gamma_e, Gamma_1, U_aux)."""
+        uu = np.zeros(6)
+        uu[:len(u)] = u
+        w = np.zeros(8)
+        c = counts if counts is not None else Counts()
+        lib().tref_cons_to_prim(self.h, P(uu), P(w), C.byref(c))
+        return w
+
     def dual_sync(self, U, ids=None, counts=None):
         ids_a = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
         c = counts if counts is not None else Counts()

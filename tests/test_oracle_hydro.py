@@ -593,3 +593,44 @@ def test_riemann_consistency_upwinding_and_mirror_symmetry(oracle, solver):
         assert np.all(np.abs(vf) <= 1e-13 * c)
     else:
         assert np.all(np.sign(F[:, 0]) == np.sign(wl[:, 0] - wr[:, 0]))   # mass diffuses downhill
+
+
+def test_cons_to_prim_dual_switch_and_floors(oracle):
+    """a2 on single cells (Eq. dual-econs, Eq. dual-primitive-switch, the floors):
+    the pressure comes from E - |m|^2 / (2 rho) when that exceeds eta1 E and from the
+    auxiliary energy otherwise (told apart by giving U_aux a different value), a
+    round trip of primitives is exact to rounding, and the density and pressure
+    floors apply and are counted."""
+    g = 5.0 / 3.0
+    lay = wl.uniform_layout((8, 8, 8), (8, 8, 8), bc=(1, 1, 1), ng=2)
+    m = oracle.Mesh(lay, oracle.make_params(dual=1, eta1=1e-3, rho_floor=1e-6, p_floor=1e-9, u_floor=1.5e-9))
+
+    def cons(rho, v, P, U_aux=None):
+        U = P / (g - 1)
+        E = U + 0.5 * rho * sum(x * x for x in v)
+        return [rho, rho * v[0], rho * v[1], rho * v[2], E, U if U_aux is None else U_aux]
+
+    # subsonic: the conservative thermal energy is used (U_aux ignored)
+    w = m.cons_to_prim(cons(2.0, (0.3, -0.2, 0.1), 1.5, U_aux=99.0))
+    assert w[0] == 2.0 and np.allclose(w[1:4], (0.3, -0.2, 0.1), rtol=1e-15)
+    assert w[4] == pytest.approx(1.5, rel=1e-14)
+    assert w[5] == pytest.approx(g, rel=1e-14) and w[6] == pytest.approx(g, rel=1e-14)
+    # Mach 1e4: U_cons = 5e-9 E < eta1 E -> the pressure from U_aux
+    rho, P = 1.0, 1.0
+    cs = np.sqrt(g * P / rho)
+    u = cons(rho, (1e4 * cs, 0.0, 0.0), P, U_aux=3.0)
+    c = oracle.Counts()
+    w = m.cons_to_prim(u, counts=c)
+    assert w[4] == pytest.approx((g - 1) * 3.0, rel=1e-14) and c.dual_aux_used == 1
+    # just above the threshold the conservative energy is used again
+    u = cons(rho, (10.0, 0.0, 0.0), P, U_aux=3.0)    # U_cons / E = 1.5 / 51.5 > 1e-3
+    c = oracle.Counts()
+    w = m.cons_to_prim(u, counts=c)
+    assert w[4] == pytest.approx(P, rel=1e-12) and c.dual_aux_used == 0
+    # floors: density below rho_floor, pressure below p_floor
+    c = oracle.Counts()
+    w = m.cons_to_prim(cons(1e-9, (0.0, 0.0, 0.0), 1.0), counts=c)
+    assert w[0] == 1e-6 and c.rho_floor == 1
+    c = oracle.Counts()
+    w = m.cons_to_prim(cons(1.0, (0.0, 0.0, 0.0), 1e-12), counts=c)
+    assert w[4] == 1e-9 and c.p_floor == 1
