@@ -64,3 +64,23 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_lat_metrics_follow_their_definition():
+    """bench.py's LAT-vs-synchronised figures (Sec. 7.4) against the same
+    definitions written independently in the oracle's LAT tests, on seeded data
+    with a dense region, floor-level cells and a sign pattern in the differences."""
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import numpy as np
+    import bench
+    from test_oracle_lat import lat_metrics
+    rng = np.random.default_rng(8)
+    sync = 10 ** rng.uniform(-10, 0, 5000)
+    lat = sync * (1 + 1e-3 * rng.normal(size=5000))
+    lat[:50] = 1e-9 * rng.uniform(0.5, 2.0, 50)   # cells crossing the dense threshold
+    got = bench.lat_vs_sync_metrics(torch, torch.from_numpy(lat), torch.from_numpy(sync), 1e-11)
+    want = lat_metrics(lat, sync, 1e-11)
+    for k, w in zip(("L1", "L2", "Linf", "C_logrho", "J_dense"), want):
+        assert got[k] == pytest.approx(float(w), rel=1e-12), k
+    assert got["J_dense"] < 1.0
