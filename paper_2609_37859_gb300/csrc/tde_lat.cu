@@ -10,9 +10,12 @@
 //    f with tau mod f = 0 as ONE batched launch sequence over that level's block
 //    list (slow levels first).  The blocks sorted by factor make every level a
 //    contiguous segment and the set of blocks completing at tau a prefix.
-//  * k_ghost_lat fills ghost cells per source block: same level -> the stage
-//    input, faster -> frozen current state, slower -> linear interpolation in
-//    time between the stored start-of-step state and the end state.
+//  * k_ghost_lat fills conserved ghost cells per source block: faster -> frozen
+//    current state, slower -> linear interpolation in time between the stored
+//    start-of-step state and the end state; those cells (and the refined-mesh
+//    ghosts of k_ghost_amr) are then converted to primitives from a per-level
+//    list built on the device (k_glist_*), while ghost cells whose source block
+//    is on the same schedule take that block's primitives (k_ghost_w_lat).
 //  * The sweeps add dt (F^1 + F^2)/2 of every boundary face to per-face-cell
 //    registers; k_reflux corrects the slower side of every mixed face at its
 //    completion (Eq. lat-flux-impulse, Eq. lat-grav-reflux), one CTA per block,
