@@ -10,7 +10,7 @@
 //             every ghost cell;
 //   k_sweep   one launch per active direction: a CTA stages a tile of pencils
 //             (with ghosts) in shared memory, reconstructs every cell's two face
-//             states once, solves every face once (HLLC), and accumulates the
+//             states once, solves every face once (HLLC or HLLE), and accumulates the
 //             flux divergence, the gravity sources and div v; the last active
 //             direction also finishes the update (RK combination, dual-energy
 //             compression, floors) and writes the output state.
