@@ -413,7 +413,9 @@ def test_uniform_flow_stays_uniform(oracle):
 def test_entropy_wave_tabulated_eos_dual_energy(oracle, saha_table):
     """The bench workload's physics in 1D: Saha table in cgs, rho = 1e-8 g/cm^3,
     T = 1e3 K, advected at Mach 1e7 with dual energy.  Pressure stays uniform to
-    roundoff through the tabulated compression source (Eq. dual-tabulated-compression)."""
+    roundoff.  The flow is uniform, so div v is at roundoff and the compression
+    source (Eq. dual-tabulated-compression) is close to zero here; it is pinned
+    with div v != 0 in tests/test_oracle_compression.py."""
     t = saha_table
     rho0, T0 = 1e-8, 1e3
     P0, e0, cs2 = t.eval_rhoT(rho0, T0)
