@@ -345,7 +345,9 @@ TDE_API int tde_eos_inject_wait_expiry(tde_eos *eos, int on);
 /* ---- allocation-free variant ---------------------------------------------- */
 
 /* A tabulated EOS held in device arrays that the caller owns (same layout and
- * meaning as the host arrays of tde_eos_load_table; not validated). */
+ * meaning as the host arrays of tde_eos_load_table).  The call checks that the
+ * three pointers are non-null, n_rho, n_T >= 2 and both ranges increase
+ * (TDE_EINVAL otherwise); the table's values are not validated. */
 typedef struct {
   int n_rho, n_T;
   double log10_rho_min, log10_rho_max, log10_T_min, log10_T_max;
@@ -362,11 +364,16 @@ typedef struct {
  * and/or dt_min (device, 1).  The paper has no counterpart: this is a library
  * service.  It calls no cudaMalloc, cudaFree or other allocating routine; its
  * scratch (block list copy, offsets, per-block minima) is one fixed device
- * array of about 176 KB that every GPU loading the library holds until exit.
- * Limit: 1 <= nblocks <= 4096, else TDE_EINVAL.  The first call on a device
- * looks up that array's device address, so it should come before any stream
- * capture.  All calls share the array: calls whose GPU work overlaps race.
- * Uses ctx's stream; asynchronous. */
+ * array of about 176 KB that every GPU loading the library holds until exit,
+ * beside a constant 4.6 KB array of the log10 / exp10 tables that the mesh's
+ * EOS lookups use, so dt equals tde_compute_dt's bit for bit.
+ * Limit: 1 <= nblocks <= 4096, else TDE_EINVAL; each block is checked as by
+ * tde_mesh_create (edges of 1..32 cells, one cell across an inactive direction,
+ * inside its level's grid).  The first call on a device looks up the arrays'
+ * device addresses and copies the tables into the second, so it should come
+ * before any stream capture.  All calls share the scratch array: calls whose
+ * GPU work overlaps race.  The block list is read from host memory during the
+ * call.  Uses ctx's stream; asynchronous. */
 TDE_API int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block_desc *blocks,
                                    const tde_grid_desc *grid, const tde_params *params,
                                    const tde_table_view *table, const double *U, double cfl,

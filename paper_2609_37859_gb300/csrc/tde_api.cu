@@ -14,6 +14,18 @@
 
 using namespace tde;
 
+// tables of the table-driven log10 / exp10 (tde_device.cuh), computed in
+// extended precision on the host
+void tde::fill_math_tables(MathTables *h) {
+  for (int j = 0; j < 182; ++j) {
+    const long double F = j / 128.0L;
+    h->logF[j] = j > 0 ? (double)logl(F) : 0.0;
+    h->invF[j] = j > 0 ? (double)(1.0L / F) : 0.0;
+    h->F[j] = j / 128.0;
+  }
+  for (int j = 0; j < 128; ++j) h->exp2j[j] = (double)exp2l(j / 128.0L);
+}
+
 namespace {
 
 int fail(tde_ctx *c, int code, const char *msg) {
@@ -227,13 +239,7 @@ extern "C" int tde_eos_load_table(tde_ctx *ctx, int n_rho, int n_T, double lr_mi
   t.le32 = reinterpret_cast<const float *>(e->d_data + 3 * nn);
   {   // tables of the table-driven log10 / exp10, computed in extended precision
     MathTables h;
-    for (int j = 0; j < 182; ++j) {
-      const long double F = j / 128.0L;
-      h.logF[j] = j > 0 ? (double)logl(F) : 0.0;
-      h.invF[j] = j > 0 ? (double)(1.0L / F) : 0.0;
-      h.F[j] = j / 128.0;
-    }
-    for (int j = 0; j < 128; ++j) h.exp2j[j] = (double)exp2l(j / 128.0L);
+    fill_math_tables(&h);
     err = cudaMalloc(&e->d_mt, sizeof(MathTables));
     if (err == cudaSuccess) err = cudaMemcpy(e->d_mt, &h, sizeof h, cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {

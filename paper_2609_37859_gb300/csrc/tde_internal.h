@@ -24,6 +24,9 @@ struct tde_ctx {
 };
 
 namespace tde {
+// fills the tables of fast_log10 / fast_exp10 (host, extended precision)
+void fill_math_tables(MathTables *h);
+
 // brackets one kernel launch: counts it and, when profiling, records events
 struct ProfScope {
   tde_ctx *c;

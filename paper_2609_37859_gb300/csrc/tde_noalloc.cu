@@ -9,7 +9,9 @@
 // this entry point takes the block list, the grid and the state directly and
 // keeps all of its scratch -- a copy of the block list, the padded-block
 // offsets and the per-block CFL minima -- in one fixed file-scope device array
-// that exists in every process that loads the library.
+// that exists in every process that loads the library.  A second, constant
+// file-scope array holds the log10 / exp10 tables of the EOS lookups, so the
+// results equal tde_compute_dt's bit for bit.
 //
 // The scratch array is shared by every call in the process: calls whose GPU
 // work overlaps (on two streams, or from two threads) race on it and must be
@@ -34,9 +36,13 @@ struct NAScratch {
 
 // The only scratch of this entry point (about 176 KB per device).
 static __device__ __align__(256) NAScratch g_noalloc_scratch;
+// Tables of the table-driven log10 / exp10 that the mesh path's EOS lookups use
+// (4.6 KB, constant: written once per device at set-up, never by a kernel).
+static __device__ __align__(256) MathTables g_noalloc_mt;
 
-// device address of g_noalloc_scratch, looked up once per device
+// device addresses of the two arrays, looked up once per device
 NAScratch *g_scratch_ptr[64] = {};
+const MathTables *g_mt_ptr[64] = {};
 
 __device__ __forceinline__ void na_bh_pos(const BH &bh, double t, double r[3]) {
   const double s = t - bh.t0;
@@ -59,6 +65,8 @@ __global__ void k_na_setup(NAScratch *S, int nb, Phys p) {
     S->minbits[b] = (unsigned long long)__double_as_longlong(INFINITY);
 }
 
+// The CFL minimum of tde_compute_dt (k_c2p's want_dt path) with the same
+// expressions, so that both entry points give the same bits.
 template <int EOSK, int DUAL>
 __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
                                                   const double *__restrict__ U, long long ntot,
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
           g %= N;
           if (g < 0) g += N;
         }
-        x[a] = p.xmin[a] + (g + 0.5) * (p.active[a] ? p.dx[a] * exp2i(-d.level) : p.dx[a]);
+        x[a] = p.xmin[a] + (g + 0.5) * (p.active[a] ? scale2i(p.dx[a], -d.level) : p.dx[a]);
       }
       na_bh_pos(bh, t_block ? t_block[b] : 0.0, rb);
       const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
@@ -101,14 +109,18 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
     }
     if (!skip) {
       const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
-      const double cs = sqrt(g1 * w[4] / w[0]);
+      const double cs = sqrt_ratio(g1 * w[4], w[0]);
+      // min_d dx_d / (|v_d| + cs) as the reciprocal of the largest signal rate
+      double rate = 0.0;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        if (p.active[a]) best = fmin(best, p.dx[a] * exp2i(-d.level) / (fabs(w[1 + a]) + cs));
+        if (p.active[a])
+          rate = dmax(rate, (fabs(w[1 + a]) + cs) * scale2i(p.idx[a], d.level));
+      best = dmin(best, rcp_nr(rate));
       if (bh.on) {
         const double s2 = r2 + bh.rs2;
         const double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-        if (gmag > 0.0) best = fmin(best, sqrt(p.dxmin * exp2i(-d.level) / gmag));
+        if (dgt0(gmag)) best = dmin(best, sqrt(scale2i(p.dxmin, -d.level) / gmag));
       }
     }
   }
@@ -168,15 +180,32 @@ extern "C" int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block
     return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: tabulated EOS without a table view");
   if (params->eos != TDE_EOS_IDEAL && params->eos != TDE_EOS_TABLE)
     return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: eos kind");
+  if (params->eos == TDE_EOS_TABLE &&
+      (!table->log10_e || !table->log10_P || !table->log10_cs2 || table->n_rho < 2 ||
+       table->n_T < 2 || !(table->log10_rho_max > table->log10_rho_min) ||
+       !(table->log10_T_max > table->log10_T_min)))
+    return na_fail(ctx, TDE_EINVAL,
+                   "tde_compute_dt_noalloc: table view needs three arrays, n_rho, n_T >= 2 and "
+                   "increasing ranges");
   if (ctx->device < 0 || ctx->device >= 64) return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: device");
+  if (grid->ng < 0 || grid->ng > 8 || grid->N[0] < 1 || grid->N[1] < 1 || grid->N[2] < 1)
+    return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: grid (N >= 1, ghost width 0..8)");
 
   // one-time set-up per device (the first call on a device does it; that first
-  // call should therefore come before any stream capture)
+  // call should therefore come before any stream capture): the two arrays'
+  // device addresses, and the log10 / exp10 tables copied into the second
   cudaError_t err = cudaSetDevice(ctx->device);
   if (err == cudaSuccess && !g_scratch_ptr[ctx->device]) {
-    void *p = nullptr;
-    err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (err == cudaSuccess) g_scratch_ptr[ctx->device] = static_cast<NAScratch *>(p);
+    MathTables h;
+    fill_math_tables(&h);
+    void *ps = nullptr, *pm = nullptr;
+    err = cudaMemcpyToSymbol(g_noalloc_mt, &h, sizeof h);
+    if (err == cudaSuccess) err = cudaGetSymbolAddress(&pm, g_noalloc_mt);
+    if (err == cudaSuccess) err = cudaGetSymbolAddress(&ps, g_noalloc_scratch);
+    if (err == cudaSuccess) {
+      g_mt_ptr[ctx->device] = static_cast<const MathTables *>(pm);
+      g_scratch_ptr[ctx->device] = static_cast<NAScratch *>(ps);
+    }
   }
   if (err != cudaSuccess) {
     ctx->err = std::string("tde_compute_dt_noalloc: ") + cudaGetErrorString(err);
@@ -208,6 +237,7 @@ extern "C" int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block
     p.tab.le = table->log10_e;
     p.tab.lp = table->log10_P;
     p.tab.lc = table->log10_cs2;
+    p.tab.mt = g_mt_ptr[ctx->device];
   }
   p.dxmin = INFINITY;
   for (int a = 0; a < 3; ++a) {
@@ -218,6 +248,7 @@ extern "C" int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block
     p.g[a] = act ? grid->ng : 0;
     p.xmin[a] = grid->xmin[a];
     p.dx[a] = grid->dx[a];
+    p.idx[a] = 1.0 / grid->dx[a];
     if (act && grid->dx[a] < p.dxmin) p.dxmin = grid->dx[a];
   }
   BH bh{};
@@ -237,8 +268,16 @@ extern "C" int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block
   long long ntot = 0, max_int = 0;
   for (int b = 0; b < nblocks; ++b) {
     const tde_block_desc &d = blocks[b];
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: block size");
     if (d.level < 0 || d.level > 8) return na_fail(ctx, TDE_EINVAL, "tde_compute_dt_noalloc: level");
+    // the checks of tde_mesh_create on one block: edges of 1..32 cells, one
+    // cell across an inactive direction, the block inside its level's grid
+    const int o[3] = {d.i0, d.j0, d.k0}, nn[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+      const int N = p.active[a] ? p.N[a] << d.level : 1;
+      if (nn[a] < 1 || nn[a] > 32 || (!p.active[a] && nn[a] != 1) || o[a] < 0 || o[a] + nn[a] > N)
+        return na_fail(ctx, TDE_EINVAL,
+                       "tde_compute_dt_noalloc: block outside the grid or edge above 32 cells");
+    }
     ntot += (long long)(d.nx + 2 * p.g[0]) * (d.ny + 2 * p.g[1]) * (d.nz + 2 * p.g[2]);
     const long long ni = (long long)d.nx * d.ny * d.nz;
     if (ni > max_int) max_int = ni;

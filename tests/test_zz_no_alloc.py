@@ -1,7 +1,8 @@
 """tde_compute_dt_noalloc: the CFL step for callers that may not allocate device
 memory (their device memory belongs to another allocator, or allocation is
-forbidden after start-up).  It must give what tde_compute_dt gives, call after
-call, although its scratch is one fixed device array shared by all calls.
+forbidden after start-up).  It must give what tde_compute_dt gives, bit for
+bit, call after call, although its scratch is one fixed device array shared by
+all calls.
 
 This file is collected last so that a failure here leaves every other test run.
 """
@@ -54,8 +55,8 @@ def test_noalloc_dt_equals_compute_dt_on_two_calls(tde):
         got_min = torch.full((1,), -1.0, dtype=torch.float64, device=dev)
         tde.compute_dt_noalloc(ctx, lay, params, mesh.U, 0.3, got, got_min, table=view)
         torch.cuda.synchronize()
-        assert np.allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-14, atol=0), call
-        assert float(got_min) == pytest.approx(float(want_min), rel=1e-14)
+        assert np.array_equal(got.cpu().numpy(), want.cpu().numpy()), call
+        assert float(got_min) == float(want_min)
         mesh.step(cfl=0.3)    # a new state for the second call
 
 
@@ -75,7 +76,7 @@ def test_noalloc_dt_with_point_mass_and_excision_then_size_limit(tde):
         got = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
         tde.compute_dt_noalloc(ctx, lay, params, mesh.U, 0.4, got, t_block=tb, bh=bh)
         torch.cuda.synchronize()
-        assert np.allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-14, atol=0)
+        assert np.array_equal(got.cpu().numpy(), want.cpu().numpy())
         tb += 0.05
     big = wl.uniform_layout((8, 8, 4097), (8, 8, 1), bc=(1, 1, 1), ng=2)
     with pytest.raises(tde.TDEError) as ei:
@@ -105,4 +106,36 @@ def test_noalloc_dt_on_a_refined_mesh(tde):
     got = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
     tde.compute_dt_noalloc(ctx, lay, params, mesh.U, 0.3, got, bh=bh)
     torch.cuda.synchronize()
-    assert np.allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-14, atol=0)
+    assert np.array_equal(got.cpu().numpy(), want.cpu().numpy())
+
+
+def test_noalloc_rejects_bad_table_views_and_blocks(tde):
+    """The checks of tde_mesh_create, and the table view's shape, before any GPU work."""
+    from types import SimpleNamespace
+    ctx = tde.Context(0)
+    dev = torch.device("cuda", 0)
+    lay = wl.uniform_layout((32, 32, 32), (16, 16, 16), bc=(1, 1, 1), ng=2)
+    params = tde.make_params(dual=1)
+    U = torch.zeros((6, lay.ntot), dtype=torch.float64, device=dev)
+    out = torch.zeros(lay.nb, dtype=torch.float64, device=dev)
+
+    def fails(layout, prm=params, table=None, what=""):
+        with pytest.raises(tde.TDEError) as ei:
+            tde.compute_dt_noalloc(ctx, layout, prm, U, 0.3, out, table=table)
+        assert ei.value.code == tde.TDE_EINVAL and what in str(ei.value), str(ei.value)
+
+    def with_blocks(blocks, N=lay.N):
+        blocks = np.asarray(blocks, dtype=np.int32)
+        return SimpleNamespace(nb=len(blocks), blocks=blocks, N=N, xmin=lay.xmin, dx=lay.dx, bc=lay.bc,
+                               ng=lay.ng, level=lambda q: 0)
+    edge = "edge above 32 cells"
+    fails(with_blocks([(0, 0, 0, 33, 16, 16)], N=(64, 32, 32)), what=edge)        # edge > 32
+    fails(with_blocks([(24, 0, 0, 16, 16, 16)]), what=edge)                       # past the grid
+    fails(with_blocks([(-1, 0, 0, 16, 16, 16)]), what=edge)                       # negative origin
+    fails(with_blocks([(0, 0, 0, 16, 16, 2)], N=(32, 32, 1)), what=edge)          # inactive axis, 2 cells
+    tp = tde.make_params(eos=tde.EOS_TABLE, dual=1)
+    col = torch.zeros((4, 4), dtype=torch.float64, device=dev)
+    fails(lay, tp, table=(4, 4, (-14.0, 2.0), (2.0, 8.0), col, None, col), what="table view")
+    fails(lay, tp, table=(4, 1, (-14.0, 2.0), (2.0, 8.0), col, col, col), what="table view")
+    fails(lay, tp, table=(4, 4, (2.0, -14.0), (2.0, 8.0), col, col, col), what="table view")
+    fails(lay, tp, table=(4, 4, (-14.0, 2.0), (8.0, 8.0), col, col, col), what="table view")
