@@ -216,6 +216,10 @@ void tref_boost(const tref_mesh *m, double *U, const double *V, double rho_min);
 int tref_mg_solve(int nx, int ny, int nz, const double *dx, const double *src, double *phi,
                   int max_cycles, double tol, int npre, int npost, double omega, double *defect);
 double tref_mg_defect_rms(int nx, int ny, int nz, const double *dx, const double *src, const double *phi);
+/* Prolongation of the V-cycle on its own (tricubic, cell centred): the coarse
+ * field e (nc cells) onto the fine grid (nf, each direction equal to or twice
+ * nc); iso = 1 mirrors e about zero beyond the faces, iso = 0 wraps. */
+void tref_mg_prolong(const int *nf, const int *nc, int iso, const double *e, double *out);
 /* The same on a periodic (isolated = 0) or isolated grid (lower corner xmin):
  * isolated boundary values from the multipole expansion of the source to order
  * lmax (<= 8) about centre (NULL: the source-weighted centroid); fmg = 1 starts

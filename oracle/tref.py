@@ -94,6 +94,7 @@ def lib():
             "tref_mg_solve": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_double,
                                         C.c_int, C.c_int, C.c_double, dp]),
             "tref_mg_defect_rms": (C.c_double, [C.c_int, C.c_int, C.c_int, dp, dp, dp]),
+            "tref_mg_prolong": (None, [ip, ip, C.c_int, dp, dp]),
             "tref_mg_solve_bc": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, dp, C.c_int,
                                            dp, dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double, dp, dp,
                                            C.c_int, dp, dp]),
@@ -437,6 +438,17 @@ def mg_solve_bc(src, dx, xmin=(0.0, 0.0, 0.0), isolated=True, lmax=4, centre=Non
                                P(c) if c is not None else None, 1 if fmg else 0, P(src), P(phi), max_cycles, tol,
                                npre, npost, omega, P(d), P(d0), len(q), P(q), P(out))
     return phi, n, float(d[0]), float(d0[0]), out
+
+
+def mg_prolong(e, nf, isolated=False):
+    """The V-cycle's prolongation of a coarse field e [nz][ny][nx] onto a grid of
+    nf = (nx, ny, nz) cells (each equal to or twice the coarse count)."""
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    nc = np.array(e.shape[::-1], dtype=np.int32)
+    nfa = np.array(nf, dtype=np.int32)
+    out = np.zeros(tuple(nf[::-1]))
+    lib().tref_mg_prolong(IP(nfa), IP(nc), 1 if isolated else 0, P(e), P(out))
+    return out
 
 
 def mg_defect(src, phi, dx):

@@ -11,7 +11,8 @@
  * with over-relaxation omega; defect d_h = S_h - A_h phi_h (Eq. selfgrav-defect);
  * restriction of phi and d by volume averages over the child cells;
  * full-approximation coarse equation A_H phi_H = R d_h + A_H R phi_h; the
- * coarse correction phi_H - R phi_h prolonged (trilinear, cell centred) and
+ * coarse correction phi_H - R phi_h prolonged (tricubic: per halved direction
+ * the cubic through the four coarse cell centres nearest the fine cell's) and
  * added; post-smoothing on every level; one extra sweep on the finest level at
  * the end of the cycle.  Each direction is halved while it has more than one
  * cell, down to a single cell.
@@ -148,9 +149,11 @@ static double at(const level_t *L, const double *f, int i, int j, int k, int bva
       c[a] = c[a] < 0 ? -1 - c[a] : 2 * L->n[a] - 1 - c[a];
       double g = 0.0;
       if (bval) {
+        /* the mirror point on the face (a cell and its image are equally far
+         * from the face, at any distance) */
         double x[3];
         for (int b = 0; b < 3; ++b) x[b] = L->bc->x0[b] + (c[b] + 0.5) * L->dx[b];
-        x[a] += 0.5 * s * L->dx[a];
+        x[a] = L->bc->x0[a] + (s < 0 ? 0.0 : L->n[a] * L->dx[a]);
         g = 2.0 * multipole(L->bc, x);
       }
       return g - at(L, f, c[0], c[1], c[2], bval);
@@ -242,31 +245,52 @@ static double restrict_cell(const level_t *Lf, const level_t *Lc, const double *
   return s / (r[0] * r[1] * r[2]);
 }
 
-/* trilinear prolongation (cell centred) of the coarse field e at fine cell (i, j, k):
- * per halved direction weights 3/4 on the parent and 1/4 on its neighbour towards
- * the fine cell; beyond an isolated boundary e is its boundary value (bval) or 0 */
+/* tricubic prolongation (cell centred) of the coarse field e at fine cell
+ * (i, j, k): along each halved direction the cubic through the four coarse
+ * centres nearest the fine centre, which lies a quarter of a coarse cell from
+ * its parent's centre p.  Lagrange weights at -1/4 on the nodes p-2, p-1, p,
+ * p+1 (fine cell on the parent's low side): -5/128, 35/128, 105/128, -7/128;
+ * at +1/4 on p-1, p, p+1, p+2: -7/128, 105/128, 35/128, -5/128.  The weights
+ * of the three directions multiply.  Beyond an isolated boundary e is its
+ * mirror image (bval: about the face value, else about 0). */
+static void cubic_taps(int f, int halved, int *first, double w[4], int *ntap) {
+  if (!halved) { *first = f; w[0] = 1.0; *ntap = 1; return; }
+  const int p = f / 2;
+  *ntap = 4;
+  if (f & 1) {
+    *first = p - 1;
+    w[0] = -7.0 / 128.0; w[1] = 105.0 / 128.0; w[2] = 35.0 / 128.0; w[3] = -5.0 / 128.0;
+  } else {
+    *first = p - 2;
+    w[0] = -5.0 / 128.0; w[1] = 35.0 / 128.0; w[2] = 105.0 / 128.0; w[3] = -7.0 / 128.0;
+  }
+}
+
 static double prolong_cell(const level_t *Lf, const level_t *Lc, const double *e, int i, int j, int k, int bval) {
   const int f[3] = {i, j, k};
-  int p[3], q[3];
-  double wp[3];
-  for (int a = 0; a < 3; ++a) {
-    const int r = Lf->n[a] / Lc->n[a];
-    if (r == 1) { p[a] = f[a]; q[a] = f[a]; wp[a] = 1.0; continue; }
-    p[a] = f[a] / 2;
-    q[a] = (f[a] & 1) ? p[a] + 1 : p[a] - 1;
-    wp[a] = 0.75;
-  }
+  int first[3], nt[3];
+  double w[3][4];
+  for (int a = 0; a < 3; ++a) cubic_taps(f[a], Lf->n[a] != Lc->n[a], &first[a], w[a], &nt[a]);
   double s = 0.0;
-  for (int c = 0; c < 2; ++c)
-    for (int b = 0; b < 2; ++b)
-      for (int a = 0; a < 2; ++a) {
-        const double wa = a ? 1.0 - wp[0] : wp[0];
-        const double wb = b ? 1.0 - wp[1] : wp[1];
-        const double wc = c ? 1.0 - wp[2] : wp[2];
-        if (wa == 0.0 || wb == 0.0 || wc == 0.0) continue;
-        s += wa * wb * wc * at(Lc, e, a ? q[0] : p[0], b ? q[1] : p[1], c ? q[2] : p[2], bval);
-      }
+  for (int c = 0; c < nt[2]; ++c)
+    for (int b = 0; b < nt[1]; ++b)
+      for (int a = 0; a < nt[0]; ++a)
+        s += w[0][a] * w[1][b] * w[2][c] * at(Lc, e, first[0] + a, first[1] + b, first[2] + c, bval);
   return s;
+}
+
+/* test access: prolong the coarse field e (nc) onto the fine grid (nf, each
+ * direction equal or doubled), periodic (iso = 0) or with isolated zero-value
+ * faces (iso = 1, the correction's boundary) */
+void tref_mg_prolong(const int *nf, const int *nc, int iso, const double *e, double *out) {
+  bc_t bc;
+  memset(&bc, 0, sizeof bc);
+  bc.iso = iso;
+  level_t F = {{nf[0], nf[1], nf[2]}, {1.0, 1.0, 1.0}, NULL, NULL, NULL, &bc};
+  level_t C = {{nc[0], nc[1], nc[2]}, {1.0, 1.0, 1.0}, NULL, NULL, NULL, &bc};
+  for (int k = 0; k < nf[2]; ++k)
+    for (int j = 0; j < nf[1]; ++j)
+      for (int i = 0; i < nf[0]; ++i) out[idx3(&F, i, j, k)] = prolong_cell(&F, &C, e, i, j, k, 0);
 }
 
 static void vcycle(level_t *Ls, int l, int nl, int npre, int npost, double omega) {

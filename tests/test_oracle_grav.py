@@ -68,6 +68,56 @@ def test_vcycle_convergence_factor(oracle):
     assert rates.max() < 0.12, rates
 
 
+def test_tricubic_prolongation_exact_on_cubics(oracle):
+    """The V-cycle's prolongation is tricubic (Sec. 3.2): it reproduces any
+    product of cubic polynomials at the fine cell centres wherever its 4^3
+    stencil lies inside the coarse grid, in every combination of halved and
+    kept directions; beyond an isolated face it mirrors the field about zero,
+    which reproduces fields odd about that face."""
+    rng = np.random.default_rng(11)
+
+    def cubic():
+        c = rng.normal(size=4)
+        return lambda t: ((c[3] * t + c[2]) * t + c[1]) * t + c[0]
+    P, Q, R = cubic(), cubic(), cubic()
+    for nf, nc in (((16, 16, 16), (8, 8, 8)), ((16, 8, 1), (8, 8, 1)), ((8, 16, 16), (8, 8, 8))):
+        cen = [np.arange(n) + 0.5 for n in nc]          # coarse centres, coarse cell width 1
+        e = P(cen[0])[None, None, :] * Q(cen[1])[None, :, None] * R(cen[2])[:, None, None]
+        out = oracle.mg_prolong(e, nf)
+        fine = [(np.arange(m) + 0.5) * (n / m) for m, n in zip(nf, nc)]
+        want = P(fine[0])[None, None, :] * Q(fine[1])[None, :, None] * R(fine[2])[:, None, None]
+        ok = []
+        for a in range(3):
+            f = np.arange(nf[a])
+            if nf[a] == nc[a]:
+                ok.append(np.ones(nf[a], dtype=bool))
+            else:
+                p = f // 2
+                lo = np.where(f % 2 == 1, p - 1, p - 2)
+                ok.append((lo >= 0) & (lo + 3 < nc[a]))
+        m = ok[2][:, None, None] & ok[1][None, :, None] & ok[0][None, None, :]
+        assert m.sum() > 0
+        assert np.abs(out - want)[m].max() <= 1e-12 * np.abs(want).max(), nf
+        # a trilinear prolongation misses the cubic part by far more than that
+        assert np.abs(want).max() > 0
+    # isolated: x^3 - 2x is odd about the low x face (x = 0), so its mirror image
+    # beyond that face is the field itself and the cells next to the face are exact
+    nc, nf = (8, 8, 8), (16, 16, 16)
+    cen = [np.arange(n) + 0.5 for n in nc]
+    odd = lambda t: t ** 3 - 2.0 * t   # noqa: E731
+    e = odd(cen[0])[None, None, :] * Q(cen[1])[None, :, None] * R(cen[2])[:, None, None]
+    out = oracle.mg_prolong(e, nf, isolated=True)
+    fine = [(np.arange(m) + 0.5) / 2 for m in nf]
+    want = odd(fine[0])[None, None, :] * Q(fine[1])[None, :, None] * R(fine[2])[:, None, None]
+    inner = slice(4, 12)
+    assert np.abs(out - want)[inner, inner, :8].max() <= 1e-12 * np.abs(want).max()
+    # the even part's mirror is not the field: the face cells then differ
+    e2 = Q(cen[0])[None, None, :] * Q(cen[1])[None, :, None] * R(cen[2])[:, None, None]
+    want2 = Q(fine[0])[None, None, :] * Q(fine[1])[None, :, None] * R(fine[2])[:, None, None]
+    out2 = oracle.mg_prolong(e2, nf, isolated=True)
+    assert np.abs(out2 - want2)[inner, inner, 0].max() > 1e-3 * np.abs(want2).max()
+
+
 # ------------------------------------------------ isolated boundaries, FMG ----
 
 def centred_grid(n, half):
