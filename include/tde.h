@@ -341,6 +341,15 @@ TDE_API int tde_eos_check(tde_eos *eos);
  * wait for the results and on the wait for work in flight); results stay those
  * of bisection.  on = 0 restores normal operation. */
 TDE_API int tde_eos_inject_wait_expiry(tde_eos *eos, int on);
+/* Failure-detection test hook of the mesh: with on != 0 the sweeps arm their
+ * TMA completion barrier but issue no copy, so every sweep tile's bounded wait
+ * (one second of the global timer, then one more for copies in flight) expires:
+ * the tile is skipped, the state it would have written is left as it was (so
+ * the step's result is not the method's), and tde_mesh_check reports
+ * TDE_ETIMEOUT once.  on = 0 restores normal operation.  TDE_EINVAL for a mesh
+ * whose sweeps stage without TMA (a padded block row that is not a whole number
+ * of 16-byte units). */
+TDE_API int tde_mesh_inject_wait_expiry(tde_mesh *mesh, int on);
 
 /* ---- allocation-free variant ---------------------------------------------- */
 
@@ -461,7 +470,7 @@ TDE_API int tde_mesh_boost(tde_mesh *mesh, const double *V, double rho_min);
  * about its S-weighted centroid, a Dirichlet condition at the face on every
  * level).  V-cycles of npre / npost red-black Gauss-Seidel sweeps with
  * over-relaxation omega (the paper: 2, 2, 1.15), a full-approximation coarse
- * correction, trilinear prolongation, post-smoothing on every level and one
+ * correction, tricubic prolongation, post-smoothing on every level and one
  * extra fine sweep, until the rms defect (Eq. selfgrav-defect) is below tol or
  * max_cycles are done.  The start: fmg = 1 full multigrid (the paper's start for
  * a first or remapped solve: the source on every level, the coarsest solved,
