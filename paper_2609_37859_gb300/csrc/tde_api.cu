@@ -113,7 +113,6 @@ int ensure_surrogate_buffers(tde_mesh *m) {
   if (m->sb.rho || !(m->phys.eos == EOS_TABLE && m->phys.eos_mode == TDE_INVERT_SURROGATE)) return TDE_OK;
   const size_t nt = (size_t)m->ntot;
   cudaError_t err = cudaMalloc(&m->sb.rho, sizeof(double) * nt * 5);
-  if (err == cudaSuccess) err = cudaMalloc(&m->sb.lTg, sizeof(float) * nt);
   if (err == cudaSuccess) err = cudaMalloc(&m->sb.queue, sizeof(long long) * nt);
   if (err == cudaSuccess) err = cudaMalloc(&m->sb.qcount, sizeof(unsigned long long));
   if (err != cudaSuccess) return cuda_fail(m->ctx, err, "learned-guess closure buffers");
@@ -610,6 +609,7 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   A((void **)&m->d_dtb, sizeof(double) * nblocks);
   A((void **)&m->d_dtbits, sizeof(unsigned long long) * nblocks);
   A((void **)&m->d_cnt, sizeof(Counters));
+  A((void **)&m->d_status, sizeof(int));
   A((void **)&m->d_gsrcb, sizeof(int32_t) * gsrcb.size());
   A((void **)&m->d_nbr_start, sizeof(int32_t) * (nblocks + 1));
   A((void **)&m->d_nbr, sizeof(int32_t) * m->h_nbr.size());
@@ -653,7 +653,9 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   cudaMemset(m->d_dU, 0, sizeof(double) * nt * (p.nvar + 1));
   cudaMemset(m->d_W, 0, sizeof(double) * nt * p.nwv);
   err = cudaMemset(m->d_cnt, 0, sizeof(Counters));
+  if (err == cudaSuccess) err = cudaMemset(m->d_status, 0, sizeof(int));
   if (err == cudaSuccess) err = cudaDeviceSynchronize();
+  if (err == cudaSuccess) err = build_sweep_tmaps(m);
   if (err != cudaSuccess) {
     tde_mesh_destroy(m);
     return cuda_fail(ctx, err, "tde_mesh_create: upload");
@@ -678,6 +680,8 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_dtb);
   cudaFree(m->d_dtbits);
   cudaFree(m->d_cnt);
+  cudaFree(m->d_status);
+  cudaFree(m->d_tmaps);
   cudaFree(m->d_gsrcb);
   cudaFree(m->d_nbr_start);
   cudaFree(m->d_nbr);
@@ -993,7 +997,25 @@ extern "C" int tde_mesh_check(tde_mesh *m) {
              (unsigned long long)h.nonfinite);
     return fail(m->ctx, TDE_ENUMERIC, msg);
   }
+  int st = 0;
+  CK(m->ctx, cudaMemcpy(&st, m->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st) {
+    CK(m->ctx, cudaMemset(m->d_status, 0, sizeof st));
+    return fail(m->ctx, TDE_ETIMEOUT, "tde_mesh_check: a bounded device wait of a mesh kernel expired");
+  }
   return m->eos ? tde_eos_check(m->eos) : TDE_OK;
+}
+
+extern "C" int tde_mesh_inject_wait_expiry(tde_mesh *m, int on) {
+  if (!m) return TDE_EINVAL;
+  if (on && !m->d_tmaps)
+    return fail(m->ctx, TDE_EINVAL, "tde_mesh_inject_wait_expiry: this mesh stages its sweeps without TMA");
+  m->inject_tma_skip = on ? 1 : 0;
+  if (m->lat_graph) {   // captured launches hold the old flag
+    cudaGraphExecDestroy(m->lat_graph);
+    m->lat_graph = nullptr;
+  }
+  return TDE_OK;
 }
 
 // ====================================================== measurement ====

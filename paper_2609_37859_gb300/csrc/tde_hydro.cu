@@ -524,6 +524,7 @@ static cudaError_t surrogate_table_pass(tde_mesh *m, const double *Uin, int nblk
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
+  m->ctx->launches[TDE_K_C2P] += 3;   // table inputs, guess + Newton, bisection of the misses
   CellMap cm{m->d_blocks, ids, nblk, padded ? 1 : 0, {p.g[0], p.g[1], p.g[2]}};
   int64_t nmax = 0;
   for (const DevBlock &B : m->hblocks)
@@ -597,6 +598,7 @@ cudaError_t launch_c2p_list(tde_mesh *m, const double *Uin, const int32_t *list,
     else k_c2p_eosin_list<0><<<grid, NT, 0, s>>>(p, list, n, Uin, m->sb.rho, m->sb.e, (long long)m->ntot);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    m->ctx->launches[TDE_K_C2P] += 3;   // table inputs, guess + Newton, bisection of the misses
     CellMap cm{};
     cm.nblk = 1;
     cm.list = list;
@@ -634,17 +636,93 @@ cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int
   return cudaGetLastError();
 }
 
-// shared memory of one sweep CTA (doubles, then the excision bytes)
-static size_t sweep_smem(const Phys &p, int PD, int NF, int M) {
+// lanes per staged row of a y or z sweep tile and the column of lane 0: a TMA
+// row starts on a 16-byte boundary, so with an odd ghost width the row starts
+// one cell early and carries two extra columns
+static void sweep_lane_layout(const Phys &p, int D, int M, int &LS, int &XO) {
+  XO = D == 0 ? 0 : (p.g[0] & 1);
+  LS = D == 0 ? M : M + 2 * XO;
+}
+
+// The sweeps' TMA tensor maps: for every tile shape, direction and block, a
+// 4-D view (x, y, z, field) of the block's primitives in W whose box is one
+// tile's staging area (D = 0: PD x M lanes x 1 x NV; D = 1: LS x PD x 1 x NV;
+// D = 2: LS x 1 x PD x NV), copied in place by one cp.async.bulk.tensor.
+// Requires every padded x row to be a whole number of 16-byte units (even
+// padded widths; then every block offset and plane is one too); otherwise,
+// or if the driver entry point is unavailable, no maps are built and the
+// sweeps stage by a copy loop (same values).  Returns a CUDA error only for a
+// failed allocation or copy.
+cudaError_t build_sweep_tmaps(tde_mesh *m) {
+  const Phys &p = m->phys;
+  m->d_tmaps = nullptr;
+  if (m->ntot & 1) return cudaSuccess;
+  for (int b = 0; b < m->nb; ++b)
+    if (m->hblocks[b].p[0] & 1) return cudaSuccess;
+  for (int D = 0; D < 3; ++D)
+    if (p.active[D] && ((m->nmax[D] + 2 * p.g[D]) & 1)) return cudaSuccess;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  auto encode = reinterpret_cast<CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill)>(fn);
+  const int nb = m->nb, NV = p.nwv;
+  std::vector<CUtensorMap> maps((size_t)N_TILE_SHAPES * 3 * nb);
+  memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+  for (int shape = 0; shape < N_TILE_SHAPES; ++shape)
+    for (int D = 0; D < 3; ++D) {
+      if (!p.active[D]) continue;
+      const int M = kTileShapes[shape].M, PD = m->nmax[D] + 2 * p.g[D];
+      int LS, XO;
+      sweep_lane_layout(p, D, M, LS, XO);
+      const cuuint32_t box[4] = {(cuuint32_t)(D == 0 ? PD : LS), (cuuint32_t)(D == 0 ? M : (D == 1 ? PD : 1)),
+                                 (cuuint32_t)(D == 2 ? PD : 1), (cuuint32_t)NV};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      for (int b = 0; b < nb; ++b) {
+        const DevBlock &B = m->hblocks[b];
+        const cuuint64_t dims[4] = {(cuuint64_t)B.p[0], (cuuint64_t)B.p[1], (cuuint64_t)B.p[2], (cuuint64_t)NV};
+        const cuuint64_t strides[3] = {(cuuint64_t)B.p[0] * 8, (cuuint64_t)B.p[0] * B.p[1] * 8,
+                                       (cuuint64_t)m->ntot * 8};
+        CUtensorMap &t = maps[((size_t)shape * 3 + D) * nb + b];
+        if (encode(&t, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void *)(m->d_W + B.off), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+          return cudaSuccess;   // this layout stays on the copy loop
+      }
+    }
+  CUtensorMap *d = nullptr;
+  cudaError_t err = cudaMalloc(&d, sizeof(CUtensorMap) * maps.size());
+  if (err == cudaSuccess) err = cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(d);
+    return err;
+  }
+  m->d_tmaps = d;
+  return cudaSuccess;
+}
+
+// shared memory of one sweep CTA (doubles, then the excision bytes): the
+// staging / flux union, the face values, the PPM interface scratch, the
+// potential and the density of the tile's cells
+static size_t sweep_smem(const Phys &p, int D, int PD, int NF, int M) {
   const int NV = p.nwv;
-  size_t nd = (size_t)NV * PD * M + 2 * (size_t)NV * NF * M + 7 * (size_t)(NF - 1) * M +
-              (size_t)NF * M;
-  return nd * sizeof(double) + (size_t)NF * M;
+  int LS, XO;
+  sweep_lane_layout(p, D, M, LS, XO);
+  size_t nd = (size_t)sweep_union_len(D, NV, PD, NF, M, LS) + 2 * (size_t)NV * NF * M +
+              (p.recon == PPM ? 4 * (size_t)(NF + 1) * M : 0) + 2 * (size_t)NF * M;
+  // then the excision flags (NF M bytes, rounded up to doubles) and the TMA barrier
+  return (nd + ((size_t)NF * M + 7) / 8 + 1) * sizeof(double);
 }
 
 size_t sweep_smem_for(const tde_mesh *m, int D, int shape) {
   const int PD = m->nmax[D] + 2 * m->phys.g[D], NF = m->nmax[D] + 2;
-  return sweep_smem(m->phys, PD, NF, kTileShapes[shape].M);
+  return sweep_smem(m->phys, D, PD, NF, kTileShapes[shape].M);
 }
 
 size_t sweep_smem_max(const tde_mesh *m) {
@@ -683,6 +761,9 @@ static SweepArgs sweep_args(tde_mesh *m, int stage, const double *U0, const doub
   a.fo = m->d_fo;
   a.nvar = m->phys.nvar;
   a.phi_sg = m->grav_on ? m->d_phi_sg : nullptr;
+  a.tmap = nullptr;
+  a.status = m->d_status;
+  a.skip_tma = m->inject_tma_skip;
   return a;
 }
 
@@ -695,7 +776,9 @@ static cudaError_t sweep_dir(tde_mesh *m, SweepArgs &a, int D, int shape, bool f
   a.first = first;
   a.PD = m->nmax[D] + 2 * p.g[D];
   a.NF = m->nmax[D] + 2;
-  const size_t smem = sweep_smem(p, a.PD, a.NF, M);
+  sweep_lane_layout(p, D, M, a.LS, a.XO);
+  a.tmap = m->d_tmaps ? m->d_tmaps + ((size_t)shape * 3 + D) * m->nb : nullptr;
+  const size_t smem = sweep_smem(p, D, a.PD, a.NF, M);
   dim3 grid((unsigned)(((m->nmax[LA] + M - 1) / M) * m->nmax[OA]), (unsigned)nblk);
   return sweep_launch_by_shape(shape, a, D, last, grid, smem, m->ctx->stream);
 }

@@ -1,6 +1,7 @@
 // tde_internal.h -- host-side objects of libtde.so and the kernel launchers
 // shared between the C-ABI layer (tde_api.cu) and the kernels (tde_hydro.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -136,6 +137,12 @@ struct tde_mesh {
   std::vector<tde::DevBlock> hblocks;
   std::vector<int64_t> hoff;
   tde::DevBlock *d_blocks = nullptr;
+  // TMA tensor maps of the primitives W for the sweeps' staging, one per
+  // (tile shape, direction, block) at [(shape * 3 + D) * nb + b]; null when
+  // some block's rows are not 16-byte multiples (the sweeps then copy by loop)
+  CUtensorMap *d_tmaps = nullptr;
+  int *d_status = nullptr;           // 1 after a bounded device wait of a mesh kernel expired
+  int inject_tma_skip = 0;           // test hook: the sweeps issue no TMA copy (their waits expire)
   int32_t *d_ghost = nullptr;        // [n_ghost][2] (dst, src) flat padded indices
   int32_t *d_gstart = nullptr;       // [nb + 1]
   int32_t *d_allids = nullptr;       // 0..nb-1
@@ -204,6 +211,7 @@ cudaError_t launch_c2p_padded(tde_mesh *m, const double *Uin, int nblk, const in
 // primitives of n listed cells (flat indices, device), nothing counted
 cudaError_t launch_c2p_list(tde_mesh *m, const double *Uin, const int32_t *list, int n);
 size_t sweep_smem_max(const tde_mesh *m);
+cudaError_t build_sweep_tmaps(tde_mesh *m);
 size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
 constexpr int N_SWEEP_SHAPES = 3;
 cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3][N_SWEEP_SHAPES]);

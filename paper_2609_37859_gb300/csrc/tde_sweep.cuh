@@ -5,6 +5,8 @@
 #pragma once
 #include <math.h>
 
+#include <cuda.h>
+
 #include "tde_internal.h"
 
 namespace tde {
@@ -58,6 +60,14 @@ struct SweepArgs {
   const double *phi_sg;      // self-gravity potential (MeshBlock layout) or null
   const long long *fo;       // register offset per block
   int nvar;
+  // TMA staging of phase A: the tensor maps of this direction and tile shape,
+  // one per block (null: staged by a copy loop); LS = lanes per staged row of
+  // y and z tiles, XO = staged column of lane 0 (LS = M + 2 and XO = 1 when the
+  // ghost width is odd: a TMA row must start on a 16-byte boundary)
+  const CUtensorMap *tmap;
+  int LS, XO;
+  int *status;               // set to 1 if a bounded wait for the TMA expired
+  int skip_tma;              // failure-detection test: issue no copy, so the wait expires
 };
 
 // A sweep tile is M pencils (lanes) of one block along D; its CTA has NTS
@@ -72,12 +82,41 @@ struct SweepGeo {
   static constexpr int OA = D == 2 ? 1 : 2;   // other transverse axis (one CTA per index)
 };
 
+// Bounded wait on an mbarrier phase: at most one second of the global
+// nanosecond timer (try_wait may suspend the thread, so the limit is on time).
+__device__ __forceinline__ bool sweep_wait(uint32_t mbar, uint32_t parity) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
+// Shared memory of a sweep tile, in doubles (then the excision bytes):
+// the staged primitives, later reused for the fluxes; the face values; the
+// PPM interface scratch; the potential and the density of the tile's cells.
+__host__ __device__ __forceinline__ int sweep_stage_len(int D, int NV, int PD, int M, int LS) {
+  return D == 0 ? NV * PD * M : NV * PD * LS;
+}
+__host__ __device__ __forceinline__ int sweep_union_len(int D, int NV, int PD, int NF, int M, int LS) {
+  const int st = sweep_stage_len(D, NV, PD, M, LS), fl = 7 * (NF - 1) * M;
+  return st > fl ? st : fl;
+}
+
 template <int D, int RECON, int EOSK, int DUAL, int LAST, int M, int NTS, int MINB>
 __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   constexpr int LA = SweepGeo<D>::LA, OA = SweepGeo<D>::OA;
   constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;   // reconstructed primitives
   constexpr int NVAR = 5 + DUAL;                            // conserved variables
-  extern __shared__ double sm[];
+  extern __shared__ __align__(128) double sm[];
   const Phys &p = a.p;
   const int b = a.ids[blockIdx.y];
   const DevBlock B = a.blocks[b];
@@ -91,19 +130,25 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   const long long sD = st[D], sL = st[LA];
   const long long base = B.off + (long long)(p.g[LA] + l0) * sL + (long long)(p.g[OA] + o) * st[OA];
   const int PD = a.PD, NF = a.NF, NFF = a.NF - 1;
+  const int LS = D == 0 ? M : a.LS, XO = D == 0 ? 0 : a.XO;
   const long long ntot = a.ntot;
 
-  double *Wt = sm;                       // [NV][PD][M]  primitives of the tile
-  double *FMs = Wt + NV * PD * M;        // [NV][NF][M]  value at the low face of cells g-1 .. g+nd
-  double *FPs = FMs + NV * NF * M;       // [NV][NF][M]  value at the high face
-  double *Fl = FPs + NV * NF * M;        // [7][NFF][M]  fluxes and face velocity
-  double *Ph = Fl + 7 * NFF * M;         // [NF][M]      potential of cells g-1 .. g+nd
-  unsigned char *Ex = reinterpret_cast<unsigned char *>(Ph + NF * M);   // [NF][M] excised
+  // staged primitives (D = 0: [NV][M][PD], pencil contiguous as in global
+  // memory; D = 1, 2: [NV][PD][LS], lanes contiguous), reused for the fluxes
+  // [7][NFF][M] once the face values exist
+  double *Wt = sm;
+  double *Fl = sm;
+  double *FMs = sm + sweep_union_len(D, NV, PD, NF, M, LS);   // [NV][NF][M]  low face of cells g-1 .. g+nd
+  double *FPs = FMs + NV * NF * M;       // [NV][NF][M]  high face
+  double *If = FPs + NV * NF * M;        // PPM: [4][NF + 1][M] interface values
+  double *Ph = If + (RECON == PPM ? 4 * (NF + 1) * M : 0);   // [NF][M] potential of cells g-1 .. g+nd
+  double *Rh = Ph + NF * M;              // [NF][M] density of the same cells (gravity source)
+  unsigned char *Ex = reinterpret_cast<unsigned char *>(Rh + NF * M);   // [NF][M] excised
+  // the TMA completion barrier, 8-byte aligned after the excision flags
+  unsigned long long *mbar = reinterpret_cast<unsigned long long *>(Rh + NF * M + (NF * M + 7) / 8);
 
-  // shared-memory indices: D = 0 keeps the pencil axis contiguous (it is
-  // contiguous in global memory too), D = 1, 2 keep the lane axis contiguous
   auto sw = [&](int v, int pos, int lane) {
-    return D == 0 ? (v * M + lane) * PD + pos : (v * PD + pos) * M + lane;
+    return D == 0 ? (v * M + lane) * PD + pos : (v * PD + pos) * LS + lane + XO;
   };
   auto sf = [&](int v, int c, int lane) {
     return D == 0 ? (v * M + lane) * NF + c : (v * NF + c) * M + lane;
@@ -116,8 +161,31 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
     else { c = e / M; lane = e - c * M; }
   };
 
-  // ---- A: stage the tile's primitives (all pencil cells incl. ghosts)
-  {
+  // ---- A: stage the tile's primitives (all pencil cells incl. ghosts): one
+  // TMA tensor copy of the tile's box (out-of-block parts of the box are
+  // zero-filled and never read), or a copy loop
+  const uint32_t mbar_addr = (uint32_t)__cvta_generic_to_shared(mbar);
+  if (a.tmap) {
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_addr), "r"(1));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+      asm volatile("fence.proxy.async.shared::cta;");
+      const uint32_t bytes = (uint32_t)sweep_stage_len(D, NV, PD, M, LS) * 8u;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_addr), "r"(bytes)
+                   : "memory");
+      int c0, c1, c2;
+      if (D == 0) { c0 = 0; c1 = p.g[1] + l0; c2 = p.g[2] + o; }
+      else if (D == 1) { c0 = p.g[0] + l0 - XO; c1 = 0; c2 = p.g[2] + o; }
+      else { c0 = p.g[0] + l0 - XO; c1 = p.g[1] + o; c2 = 0; }
+      const unsigned long long tm = reinterpret_cast<unsigned long long>(a.tmap + b);
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Wt);
+      if (!a.skip_tma)
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+            ::"r"(dst), "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(mbar_addr)
+            : "memory");
+    }
+  } else {
     const int per = pd * M;
     for (int e = threadIdx.x; e < NV * per; e += NTS) {
       const int v = e / per;
@@ -152,9 +220,32 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       if (exc) Ex[idx] = inside_radius(r2, a.bh.rexc) ? 1 : 0;
     }
   }
-  __syncthreads();
+  __syncthreads();   // (also orders the barrier's initialisation before the waits)
+  if (a.tmap) {
+    // every thread waits for the copy (bounded); if it did not complete, the
+    // tile is skipped, the status word set, and thread 0 waits once more
+    // (bounded) so that no copy is in flight when the CTA exits
+    const bool ok = sweep_wait(mbar_addr, 0);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(a.status, 1);
+        sweep_wait(mbar_addr, 0);
+      }
+      return;
+    }
+  }
 
-  // ---- B: face values of every cell adjacent to a face of the tile
+  // ---- B: face values of every cell adjacent to a face of the tile; the
+  // density of those cells kept for the gravity source (the staged primitives
+  // become the flux area after this phase)
+  if (grav) {
+    for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
+      int c, lane;
+      split(e, nd + 2, c, lane);
+      if (lane >= nlane) continue;
+      Rh[D == 0 ? lane * NF + c : c * M + lane] = Wt[sw(0, g - 1 + c, lane)];
+    }
+  }
   if (RECON == PLM) {
     for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
       int c, lane;
@@ -172,10 +263,8 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
     __syncthreads();
   } else {
     // PPM: the interpolated value of each of the nd + 3 interfaces once (a cell's
-    // upper interface is its neighbour's lower one), four variables at a time in
-    // the flux area (free until phase C: 4 (NF + 1) M <= 7 (NF - 1) M doubles for
-    // NF >= 4), then the monotonicity limits per cell
-    double *If = Fl;
+    // upper interface is its neighbour's lower one), four variables at a time,
+    // then the monotonicity limits per cell
     const int NI = NF + 1, nfc = nd + 3;
     auto si = [&](int vv, int f, int lane) {
       return D == 0 ? (vv * M + lane) * NI + f : (vv * NI + f) * M + lane;
@@ -300,7 +389,7 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       const int i1 = D == 0 ? i0 + 1 : i0 + M;
       const int i2 = D == 0 ? i0 + 2 : i0 + 2 * M;
       const double phm = Ph[i0], ph0 = Ph[i1], php = Ph[i2];
-      const double rho = Wt[sw(0, g + c, lane)];
+      const double rho = Rh[i1];
       acc[1 + D] -= rho * (php - phm) * hidx;
       acc[4] -= (Fl[sfl(0, c + 1, lane)] * (php - ph0) + Fl[sfl(0, c, lane)] * (ph0 - phm)) * hidx;
     }

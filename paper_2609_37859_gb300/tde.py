@@ -126,6 +126,7 @@ _SIGS = {
     "tde_mesh_check": [vp],
     "tde_eos_check": [vp],
     "tde_eos_inject_wait_expiry": [vp, C.c_int],
+    "tde_mesh_inject_wait_expiry": [vp, C.c_int],
     "tde_profile": [vp, C.c_int],
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
@@ -498,6 +499,10 @@ class Mesh:
         self.ctx.check(lib().tde_mesh_get_tiles(self.h, t))
         return list(t)
 
+    def inject_wait_expiry(self, on=True):
+        """Failure-detection test hook: the sweeps' TMA waits expire (no copy issued)."""
+        self.ctx.check(lib().tde_mesh_inject_wait_expiry(self.h, 1 if on else 0))
+
     def counts(self, reset=False):
         c = Counts()
         self.ctx.check(lib().tde_counts_read(self.h, C.byref(c), 1 if reset else 0))
@@ -505,7 +510,8 @@ class Mesh:
 
     def check(self):
         """Raise TDEError (TDE_ENUMERIC: non-finite results counted since the last
-        counter reset; TDE_ETIMEOUT: an expired wait of the learned guess)."""
+        counter reset; TDE_ETIMEOUT: an expired wait of the sweeps' staging or of
+        the learned guess)."""
         self.ctx.check(lib().tde_mesh_check(self.h))
 
     def close(self):
