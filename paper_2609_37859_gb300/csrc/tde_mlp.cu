@@ -267,6 +267,12 @@ struct SurrogateArgs {
   int skip_mma;       // failure-detection test: issue no MMA, so the wait expires
   float *lTg;         // optional: the guessed log10 T of each cell
   CellMap cm;         // which cells: plain arrays (cm.blocks null) or cells of blocks
+  // the fused Newton step (k_eos_surrogate<1>): results of accepted cells, the
+  // closure's clamped energy (eu, or null), the queue of cells left for
+  // bisection and its length
+  double *eu;
+  long long *queue;
+  unsigned long long *qcount;
 };
 
 // Cells of a cell map: block position bp's cell count, and the array index of
@@ -303,13 +309,74 @@ __device__ __forceinline__ void cm_split(const CellMap &cm, long long t, long lo
   first = (long long)((unsigned)t - q * (unsigned)per) * size;
 }
 
-__global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
+// One FP64 Newton step from the guessed log10 T, judged by the table bracket.
+// The column g is linear inside a temperature cell, so the step from the
+// guess's cell j lands on x = j + s with s the cell solve; if the root is in
+// cell j that is the root itself, otherwise x lies in the cell j' the linear
+// extension points to, and the root is taken there when j' brackets it.  An
+// accepted cell is the one bisection finds (g_j <= y < g_{j+1} is unique) and the
+// state is evaluated with the same formulas, so the result is the bisection
+// result bit for bit.  Returns false for the cells left to bisection (clamped
+// inputs, a step that misses).
+__device__ __forceinline__ bool newton_cell(const DTable &t, double rho_c, double e, float lTg, float idlt,
+                                            long long c, double *T, double *P, double *cs2, double *eu) {
+  const int nt = t.nt;
+  int i;
+  double w;
+  const bool cl = rho_cell(t, rho_c, i, w);
+  // the decisions below compare on the integer pipe (dgt0, dle, dlt: the
+  // same outcomes as the FP64 comparisons for every non-NaN value)
+  const bool pos = dgt0(e);
+  if (cl || !pos) return false;
+  const double ly = tlog10(t, e);
+  const double *__restrict__ ra = t.le + (size_t)i * nt;
+  const double *__restrict__ rb = ra + nt;
+  const float xg = (lTg - (float)t.lt0) * idlt;
+  int j = (int)floorf(fminf(fmaxf(xg, 0.f), (float)(nt - 2)));
+  j = min(max(j, 0), nt - 2);
+  double g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
+  double g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
+  double sc = cell_solve(ly, g0, g1);
+  bool in = dle(g0, ly) && dlt(ly, g1);
+  if (!in) {
+    const double xn = __dadd_rn(dint(j), sc);   // the Newton result, in cell units
+    if (dge0(xn) && dlt(xn, dint(nt - 1))) {
+      const int j2 = ifloor_nonneg(xn);
+      if (j2 != j) {
+        j = j2;
+        g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
+        g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
+        in = dle(g0, ly) && dlt(ly, g1);
+        if (in) sc = cell_solve(ly, g0, g1);
+      }
+    }
+  }
+  // at the coldest node bisection clamps (y <= g_0): leave that to it
+  if (!(in && (j > 0 || dlt(g0, ly)))) return false;
+  if (P) P[c] = texp10(t, bilin(t.lp, nt, i, w, j, sc));
+  if (cs2) cs2[c] = texp10(t, bilin(t.lc, nt, i, w, j, sc));
+  if (T) T[c] = texp10(t, cell_log10T(t, j, sc));
+  if (eu) eu[c] = 0.0;   // inside the table
+  return true;
+}
+
+// The learned guess.  NEWTON = 0: the network alone (raw outputs, the guess);
+// NEWTON = 1: the guess goes straight into the FP64 Newton step in the same
+// thread (newton_cell), accepted cells are written and the rest queued for
+// k_eos_fallback (one atomic per tile reserves the tile's queue slots; the
+// accepted count is added once per CTA).
+template <int NEWTON>
+__global__ void __launch_bounds__(IT, NEWTON ? 4 : 8) k_eos_surrogate(SurrogateArgs a) {
   __shared__ __align__(1024) unsigned char sA[IT * H * 2];   // h1, BF16, core-matrix layout
   __shared__ __align__(1024) unsigned char sB[H * H * 2];    // W2, BF16, core-matrix layout
   __shared__ float sW1[2 * H], sb1[H], sb2[H], sW3[2 * H], sb3[2];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
+  __shared__ unsigned s_wc[IT / 32];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned s_acc;
+  unsigned n_acc = 0;
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t sA_addr = (uint32_t)__cvta_generic_to_shared(sA);
   const uint32_t sB_addr = (uint32_t)__cvta_generic_to_shared(sB);
@@ -354,99 +421,138 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
     const long long local = first + tid;
     const bool live = local < ncell;
     const long long c = live ? cm_flat(a.cm, bp, local) : 0;
-    // ---- inputs and layer 1, FP32 only: the network needs log10 rho and the
-    // position z of log10 e in its column to FP32 accuracy (the FP64 work of
-    // the inversion is k_eos_newton's)
-    float x0 = 0.f, x1 = 0.f;
-    if (live) {
-      if (a.xin) {
-        x0 = a.xin[2 * c];
-        x1 = a.xin[2 * c + 1];
-      } else {
-        const DTable &t = a.t;
-        const float lr = __log2f((float)a.rho[c]) * 0.30102999566f;
-        const float ly = __log2f((float)a.e[c]) * 0.30102999566f;
-        const float xr = fminf(fmaxf((lr - (float)t.lr0) * (float)t.inv_dlr, 0.f), (float)(t.nr - 1));
-        const int ti = min((int)xr, t.nr - 2);
-        const float w32 = xr - (float)ti;
-        const float *__restrict__ ra = t.le32 + (size_t)ti * t.nt;
-        const float *__restrict__ rb = ra + t.nt;
-        const float glo = fmaf(w32, __ldg(rb) - __ldg(ra), __ldg(ra));
-        const float ghi = fmaf(w32, __ldg(rb + t.nt - 1) - __ldg(ra + t.nt - 1), __ldg(ra + t.nt - 1));
-        x0 = fminf(fmaxf((lr - a.nm.cr) * a.nm.isr, -2.f), 2.f);
-        const float z = __fdividef(ly - glo, ghi - glo);
-        x1 = (fminf(fmaxf(z, -1.f), 2.f) - a.nm.ce) * a.nm.ise;
+    // after an expired wait (s_abort, uniform) the network is skipped: the
+    // Newton kernel queues the remaining cells for bisection, the plain one stops
+    float y0 = 0.f, y1 = 0.f;
+    if (!s_abort) {
+      // ---- inputs and layer 1, FP32 only: the network needs log10 rho and the
+      // position z of log10 e in its column to FP32 accuracy (the FP64 work of
+      // the inversion is newton_cell's)
+      float x0 = 0.f, x1 = 0.f;
+      if (live) {
+        if (a.xin) {
+          x0 = a.xin[2 * c];
+          x1 = a.xin[2 * c + 1];
+        } else {
+          const DTable &t = a.t;
+          const float lr = __log2f((float)a.rho[c]) * 0.30102999566f;
+          const float ly = __log2f((float)a.e[c]) * 0.30102999566f;
+          const float xr = fminf(fmaxf((lr - (float)t.lr0) * (float)t.inv_dlr, 0.f), (float)(t.nr - 1));
+          const int ti = min((int)xr, t.nr - 2);
+          const float w32 = xr - (float)ti;
+          const float *__restrict__ ra = t.le32 + (size_t)ti * t.nt;
+          const float *__restrict__ rb = ra + t.nt;
+          const float glo = fmaf(w32, __ldg(rb) - __ldg(ra), __ldg(ra));
+          const float ghi = fmaf(w32, __ldg(rb + t.nt - 1) - __ldg(ra + t.nt - 1), __ldg(ra + t.nt - 1));
+          x0 = fminf(fmaxf((lr - a.nm.cr) * a.nm.isr, -2.f), 2.f);
+          const float z = __fdividef(ly - glo, ghi - glo);
+          x1 = (fminf(fmaxf(z, -1.f), 2.f) - a.nm.ce) * a.nm.ise;
+        }
       }
-    }
 #pragma unroll
-    for (int k8 = 0; k8 < H / 8; ++k8) {
-      __align__(16) __nv_bfloat16 hv[8];
+      for (int k8 = 0; k8 < H / 8; ++k8) {
+        __align__(16) __nv_bfloat16 hv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int o = 8 * k8 + u;
-        hv[u] = __float2bfloat16_rn(silu_tanh(sW1[2 * o] * x0 + sW1[2 * o + 1] * x1 + sb1[o]));
+        for (int u = 0; u < 8; ++u) {
+          const int o = 8 * k8 + u;
+          hv[u] = __float2bfloat16_rn(silu_tanh(sW1[2 * o] * x0 + sW1[2 * o + 1] * x1 + sb1[o]));
+        }
+        *reinterpret_cast<uint4 *>(sA + core_off(tid, 8 * k8)) = *reinterpret_cast<uint4 *>(hv);
       }
-      *reinterpret_cast<uint4 *>(sA + core_off(tid, 8 * k8)) = *reinterpret_cast<uint4 *>(hv);
+      // make the generic-proxy shared stores visible to the tensor core
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      // ---- layer 2 on the tensor core: D[128 x 64] = h1[128 x 64] * W2^T
+      if (tid == 0 && !a.skip_mma) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int ks = 0; ks < H / 16; ++ks) {
+          const unsigned long long ad = smem_desc(sA_addr + ks * 256, 128, 1024);
+          const unsigned long long bd = smem_desc(sB_addr + ks * 256, 128, 1024);
+          const uint32_t acc = ks > 0 ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tbase),
+              "l"(ad), "l"(bd), "r"(IDESC_BF16_M128_N64), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            mbar_addr));
+      }
+      // bounded wait for the MMAs (one second of the global timer at most)
+      if (!mbar_wait_bounded(mbar_addr, phase)) s_abort = 1;
+      phase ^= 1u;
+      __syncthreads();
+      if (!s_abort) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // ---- read the accumulator row of this thread (warp w owns TMEM lanes
+        // 32w..32w+31) in two halves of 32 columns, and apply layer 3 (FP32)
+        y0 = sb3[0];
+        y1 = sb3[1];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t r[32];
+          const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * hf);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+              "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int o = 32 * hf + q;
+            const float h2 = silu_tanh(__uint_as_float(r[q]) + sb2[o]);
+            y0 += sW3[o] * h2;
+            y1 += sW3[H + o] * h2;
+          }
+        }
+        if (live && a.yout) {
+          a.yout[2 * c] = y0;
+          a.yout[2 * c + 1] = y1;
+        }
+        if (live && a.lTg) a.lTg[c] = a.nm.cT + a.nm.sT * y0;
+      }
+      // every thread has its row in registers: the next tile may reuse sA and TMEM
+      asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    // make the generic-proxy shared stores visible to the tensor core
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    const bool have = !s_abort;   // uniform: set before the last barrier
+    if (!NEWTON && !have) break;
+    if (NEWTON) {
+      // the FP64 Newton step from this thread's guess; misses are queued
+      const bool ok = live ? (have && newton_cell(a.t, a.rho[c], a.e[c], a.nm.cT + a.nm.sT * y0, a.nm.idlt, c,
+                                                  a.T, a.P, a.cs2, a.eu))
+                           : true;
+      n_acc += (live && ok) ? 1u : 0u;
+      const int lane = tid & 31;
+      const unsigned rm = __ballot_sync(0xffffffffu, !ok);
+      if (lane == 0) s_wc[warp] = __popc(rm);
+      __syncthreads();
+      if (tid == 0) {
+        unsigned tot = 0;
+        for (int q = 0; q < IT / 32; ++q) {
+          const unsigned v = s_wc[q];
+          s_wc[q] = tot;   // exclusive prefix over the warps
+          tot += v;
+        }
+        s_base = tot ? atomicAdd(a.qcount, (unsigned long long)tot) : 0ull;
+      }
+      __syncthreads();
+      if (!ok) a.queue[s_base + s_wc[warp] + __popc(rm & ((1u << lane) - 1u))] = c;
+    }
     __syncthreads();
-    // ---- layer 2 on the tensor core: D[128 x 64] = h1[128 x 64] * W2^T
-    if (tid == 0 && !a.skip_mma) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-      for (int ks = 0; ks < H / 16; ++ks) {
-        const unsigned long long ad = smem_desc(sA_addr + ks * 256, 128, 1024);
-        const unsigned long long bd = smem_desc(sB_addr + ks * 256, 128, 1024);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tbase),
-            "l"(ad), "l"(bd), "r"(IDESC_BF16_M128_N64), "r"(acc));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          mbar_addr));
-    }
-    // bounded wait for the MMAs (one second of the global timer at most)
-    if (!mbar_wait_bounded(mbar_addr, phase)) s_abort = 1;
-    phase ^= 1u;
+  }
+  if (NEWTON) {   // accepted cells: one atomic per CTA
+    for (int o = 16; o > 0; o >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
+    if (tid == 0) s_acc = 0;
     __syncthreads();
-    if (s_abort) break;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // ---- read the accumulator row of this thread (warp w owns TMEM lanes
-    // 32w..32w+31) in two halves of 32 columns, and apply layer 3 (FP32)
-    float y0 = sb3[0], y1 = sb3[1];
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      uint32_t r[32];
-      const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * hf);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-          "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-            "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-            "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-            "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int o = 32 * hf + q;
-        const float h2 = silu_tanh(__uint_as_float(r[q]) + sb2[o]);
-        y0 += sW3[o] * h2;
-        y1 += sW3[H + o] * h2;
-      }
-    }
-    if (live && a.yout) {
-      a.yout[2 * c] = y0;
-      a.yout[2 * c + 1] = y1;
-    }
-    if (live && a.lTg) a.lTg[c] = a.nm.cT + a.nm.sT * y0;
-    // every thread has its row in registers: the next tile may reuse sA and TMEM
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    if ((tid & 31) == 0) atomicAdd(&s_acc, n_acc);
     __syncthreads();
+    if (tid == 0 && a.cnt && s_acc) atomicAdd(&a.cnt->surrogate_accepted, (unsigned long long)s_acc);
   }
   if (s_abort && tid == 0) atomicExch(a.status, 1);
   // wait (bounded) for any MMA still in flight before freeing tensor memory
@@ -455,109 +561,6 @@ __global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(64));
-}
-
-// One FP64 Newton step from the guessed log10 T, judged by the table bracket.
-// The column g is linear inside a temperature cell, so the step from the
-// guess's cell j lands on x = j + s with s the cell solve; if the root is in
-// cell j that is the root itself, otherwise x lies in the cell j' the linear
-// extension points to, and the root is taken there when j' brackets it.  An
-// accepted cell is the one bisection finds (g_j <= y < g_{j+1} is unique) and the
-// state is evaluated with the same formulas, so the result is the bisection
-// result bit for bit.  Cells not settled this way (clamped inputs, a step that
-// misses) are queued for k_eos_fallback; the queue slots of a CTA's 256 cells
-// are reserved with one atomic, and the accepted count is added once per CTA.
-__global__ void __launch_bounds__(256) k_eos_newton(DTable t, CellMap cm, const float *__restrict__ lTg,
-                                                    float idlt, long long n,
-                                                    const double *__restrict__ rho,
-                                                    const double *__restrict__ en, double *T, double *P,
-                                                    double *cs2, double *eu, Counters *cnt,
-                                                    long long *queue, unsigned long long *qcount) {
-  __shared__ unsigned s_wc[8];
-  __shared__ unsigned long long s_base;
-  __shared__ unsigned s_acc;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = t.nt;
-  const long long cpb = (n + 255) / 256;   // chunks of 256 cells per block
-  const long long nchunks = cpb * (cm.blocks ? cm.nblk : 1);
-  unsigned n_acc = 0;
-  // every thread of the CTA runs the same chunks (the CTA votes below)
-  for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    int bp;
-    long long local0;
-    cm_split(cm, ch, cpb, 256, bp, local0);
-    const long long ncell = cm_cells(cm, n, bp);
-    if (local0 >= ncell) continue;   // uniform over the CTA
-    const long long local = local0 + threadIdx.x;
-    const long long c = local < ncell ? cm_flat(cm, bp, local) : -1;
-    bool ok = true, acc = false;
-    if (c >= 0) {
-      int i;
-      double w;
-      const bool cl = rho_cell(t, rho[c], i, w);
-      const double e = en[c];
-      // the decisions below compare on the integer pipe (dgt0, dle, dlt: the
-      // same outcomes as the FP64 comparisons for every non-NaN value)
-      const bool pos = dgt0(e);
-      const double ly = pos ? tlog10(t, e) : -INFINITY;
-      const double *__restrict__ ra = t.le + (size_t)i * nt;
-      const double *__restrict__ rb = ra + nt;
-      ok = false;
-      if (!cl && pos) {
-        const float xg = (lTg[c] - (float)t.lt0) * idlt;
-        int j = (int)floorf(fminf(fmaxf(xg, 0.f), (float)(nt - 2)));
-        j = min(max(j, 0), nt - 2);
-        double g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
-        double g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
-        double sc = cell_solve(ly, g0, g1);
-        bool in = dle(g0, ly) && dlt(ly, g1);
-        if (!in) {
-          const double xn = __dadd_rn(dint(j), sc);   // the Newton result, in cell units
-          if (dge0(xn) && dlt(xn, dint(nt - 1))) {
-            const int j2 = ifloor_nonneg(xn);
-            if (j2 != j) {
-              j = j2;
-              g0 = lerp_rn(w, __ldg(ra + j), __ldg(rb + j));
-              g1 = lerp_rn(w, __ldg(ra + j + 1), __ldg(rb + j + 1));
-              in = dle(g0, ly) && dlt(ly, g1);
-              if (in) sc = cell_solve(ly, g0, g1);
-            }
-          }
-        }
-        // at the coldest node bisection clamps (y <= g_0): leave that to it
-        ok = in && (j > 0 || dlt(g0, ly));
-        if (ok) {
-          if (P) P[c] = texp10(t, bilin(t.lp, nt, i, w, j, sc));
-          if (cs2) cs2[c] = texp10(t, bilin(t.lc, nt, i, w, j, sc));
-          if (T) T[c] = texp10(t, cell_log10T(t, j, sc));
-          if (eu) eu[c] = 0.0;   // inside the table
-          acc = true;
-        }
-      }
-    }
-    n_acc += acc ? 1u : 0u;
-    const unsigned rm = __ballot_sync(0xffffffffu, !ok);
-    if (lane == 0) s_wc[warp] = __popc(rm);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned tot = 0;
-      for (int q = 0; q < 8; ++q) {
-        const unsigned v = s_wc[q];
-        s_wc[q] = tot;   // exclusive prefix over the warps
-        tot += v;
-      }
-      s_base = tot ? atomicAdd(qcount, (unsigned long long)tot) : 0ull;
-    }
-    __syncthreads();
-    if (!ok) queue[s_base + s_wc[warp] + __popc(rm & ((1u << lane) - 1u))] = c;
-    __syncthreads();   // s_wc and s_base are rewritten by the next chunk
-  }
-  // accepted cells: one atomic per CTA
-  for (int o = 16; o > 0; o >>= 1) n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
-  if (threadIdx.x == 0) s_acc = 0;
-  __syncthreads();
-  if (lane == 0) atomicAdd(&s_acc, n_acc);
-  __syncthreads();
-  if (threadIdx.x == 0 && cnt && s_acc) atomicAdd(&cnt->surrogate_accepted, (unsigned long long)s_acc);
 }
 
 // Table bisection for the cells the Newton step left (their indices in queue).
@@ -678,17 +681,57 @@ cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, 
   a.skip_mma = e->inject_wait_expiry;
   a.lTg = lTg;
   a.cm = cm ? *cm : CellMap{};
+  a.eu = nullptr;
+  a.queue = nullptr;
+  a.qcount = nullptr;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
   // one wave of resident CTAs: registers (64 x 128 threads) and shared memory
   // (26 KB, largest carveout) admit 8 per SM, and 8 x 64 TMEM columns fill the
   // SM's 512 exactly
-  cudaFuncSetAttribute(k_eos_surrogate, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaFuncSetAttribute(k_eos_surrogate<0>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
   const int per_sm = 8;
   const long long tiles = (n + IT - 1) / IT * (a.cm.blocks ? a.cm.nblk : 1);
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
-  k_eos_surrogate<<<grid, IT, 0, s>>>(a);
+  k_eos_surrogate<0><<<grid, IT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// the network and the Newton step in one pass (k_eos_surrogate<1>): 4 CTAs per
+// SM (the FP64 step's registers), 4 x 64 TMEM columns
+cudaError_t launch_surrogate_newton(tde_eos *e, const CellMap &cm, long long n, const double *rho,
+                                    const double *en, double *T, double *P, double *cs2, double *eu,
+                                    long long *queue, unsigned long long *qcount, Counters *cnt,
+                                    cudaStream_t s) {
+  SurrogateArgs a;
+  a.t = e->tab;
+  a.nm = norm_of(e);
+  a.wb = (const __nv_bfloat16 *)e->d_wb;
+  a.n = n;
+  a.rho = rho;
+  a.e = en;
+  a.T = T;
+  a.P = P;
+  a.cs2 = cs2;
+  a.yout = nullptr;
+  a.xin = nullptr;
+  a.cnt = cnt;
+  a.status = e->d_status;
+  a.skip_mma = e->inject_wait_expiry;
+  a.lTg = nullptr;
+  a.cm = cm;
+  a.eu = eu;
+  a.queue = queue;
+  a.qcount = qcount;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
+  cudaFuncSetAttribute(k_eos_surrogate<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+  const int per_sm = 4;
+  const long long tiles = (n + IT - 1) / IT * (cm.blocks ? cm.nblk : 1);
+  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
+  k_eos_surrogate<1><<<grid, IT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -701,16 +744,11 @@ cudaError_t surrogate_run(tde_eos *e, const CellMap &cm, long long n, const doub
                           cudaStream_t s) {
   cudaError_t r = cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), s);
   if (r != cudaSuccess) return r;
-  r = launch_surrogate_kernel(e, n, rho, en, nullptr, nullptr, nullptr, nullptr, nullptr, s, lTg, &cm);
+  (void)lTg;
+  r = launch_surrogate_newton(e, cm, n, rho, en, T, P, cs2, eu, queue, qcount, cnt, s);
   if (r != cudaSuccess) return r;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
-  const long long chunks = (n + 255) / 256 * (cm.blocks ? cm.nblk : 1);
-  const unsigned grid = (unsigned)std::min<long long>(chunks, (long long)sms * 8);
-  k_eos_newton<<<grid, 256, 0, s>>>(e->tab, cm, lTg, (float)(1.0 / e->tab.dlt), n, rho, en, T, P,
-                                    cs2, eu, cnt, queue, qcount);
-  r = cudaGetLastError();
-  if (r != cudaSuccess) return r;
   const long long ncell = n * (cm.blocks ? cm.nblk : 1);
   const unsigned gf = (unsigned)std::min<long long>((ncell + 255) / 256, (long long)sms * 8);
   k_eos_fallback<<<gf, 256, 0, s>>>(e->tab, queue, qcount, rho, en, T, P, cs2, eu, cnt);
@@ -730,7 +768,6 @@ cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const
     e->d_guess = nullptr;
     e->queue_cap = 0;
     cudaError_t r = cudaMalloc(&e->d_queue, sizeof(long long) * (size_t)n);
-    if (r == cudaSuccess) r = cudaMalloc(&e->d_guess, sizeof(float) * (size_t)n);
     if (r != cudaSuccess) return r;
     e->queue_cap = n;
   }
@@ -739,14 +776,15 @@ cudaError_t launch_eos_surrogate(tde_eos *e, int64_t n, const double *rho, const
     if (r != cudaSuccess) return r;
   }
   ProfScope ps(e->ctx, TDE_K_EOS);
-  return surrogate_run(e, CellMap{}, n, rho, en, T, P, cs2, nullptr, e->d_guess, e->d_queue,
+  e->ctx->launches[TDE_K_EOS] += 1;   // the guess with its Newton step, then the bisection of the misses
+  return surrogate_run(e, CellMap{}, n, rho, en, T, P, cs2, nullptr, nullptr, e->d_queue,
                        e->d_qcount, e->d_cnt, s);
 }
 
 cudaError_t launch_eos_surrogate_cells(tde_eos *e, const CellMap &cm, int64_t nmax,
                                        const SurrogateBuf &sb, Counters *cnt, cudaStream_t s) {
   if (nmax <= 0 || cm.nblk <= 0) return cudaSuccess;
-  return surrogate_run(e, cm, nmax, sb.rho, sb.e, nullptr, sb.P, sb.cs2, sb.eu, sb.lTg, sb.queue,
+  return surrogate_run(e, cm, nmax, sb.rho, sb.e, nullptr, sb.P, sb.cs2, sb.eu, nullptr, sb.queue,
                        sb.qcount, cnt, s);
 }
 }  // namespace tde
