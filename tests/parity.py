@@ -74,3 +74,33 @@ def assert_parity_stencil(G, O, scale, tol, what=""):
     errs = np.array(errs)
     assert errs.max() <= tol, "%s: per-variable max error %s > %g" % (what, errs, tol)
     return errs
+
+
+def error_report(G, O, scale=None, thresh=1e-12, mask=None):
+    """Both readings of a comparison, per conserved variable: the plain per-cell
+    error of cell_errors (max, and the number of cells above `thresh`), and, with
+    `scale` (stencil_scale of the input, same shape), the error against the larger
+    of the cell's own scale and its stencil's; plus the number of cells where
+    the two readings disagree about `thresh`.  `mask` (boolean, the grid's
+    shape) restricts the comparison to those cells."""
+    G = np.asarray(G, dtype=np.float64)
+    O = np.asarray(O, dtype=np.float64)
+    if mask is not None:
+        G, O = G[:, mask], O[:, mask]
+        scale = None if scale is None else scale[:, mask]
+    rho, E = O[0], O[4]
+    own_m = np.sqrt(2.0 * np.abs(rho) * np.abs(E))
+    out = {"plain_max": [], "plain_cells_above": [], "stencil_max": [], "disagree_cells": []}
+    for v in range(O.shape[0]):
+        own = own_m if v in (1, 2, 3) else np.abs(O[v])
+        d = np.abs(G[v] - O[v])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            e = np.where(d == 0, 0.0, d / own)
+        out["plain_max"].append(float(e.max()) if e.size else 0.0)
+        out["plain_cells_above"].append(int((e > thresh).sum()))
+        if scale is not None:
+            with np.errstate(divide="ignore", invalid="ignore"):
+                es = np.where(d == 0, 0.0, d / np.maximum(own, scale[v]))
+            out["stencil_max"].append(float(es.max()) if es.size else 0.0)
+            out["disagree_cells"].append(int(((e > thresh) != (es > thresh)).sum()))
+    return out

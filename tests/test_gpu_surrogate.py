@@ -90,11 +90,38 @@ def test_tensor_core_forward_matches_oracle_network(tde, oracle, env):
     eos.forward(dev(x), y)
     torch.cuda.synchronize()
     yo = oracle.mlp_forward(bf16_round(w), x.astype(np.float64))
-    yg = y.cpu().numpy()
-    # the hidden layer enters the tensor core as BF16 (relative rounding 2^-9)
-    err = np.abs(yg - yo)
-    assert err.max() < 0.05 * np.abs(yo).max() + 1e-3, err.max()
-    assert np.corrcoef(yg.ravel(), yo.ravel())[0, 1] > 0.9995
+    yg = y.cpu().numpy().astype(np.float64)
+    ye, bound = bf16_hidden_emulation(bf16_round(w), x.astype(np.float64))
+    # the emulation is the oracle network with the hidden layer rounded to BF16
+    assert np.abs(ye - yo).max() < 0.05 * np.abs(yo).max()
+    err = np.abs(yg - ye)
+    print("tensor-core forward: max |err| %.3e, max err/bound %.3f, mean err/bound %.4f" %
+          (err.max(), (err / bound).max(), (err / bound).mean()))
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def bf16_hidden_emulation(w, x):
+    """The network as the inference kernel computes it, in FP64: layer 1, SiLU,
+    the hidden values rounded to BF16 (the tensor core's operand type), the
+    64 x 64 layer, SiLU, layer 3.  Returns the outputs and a per-element
+    tolerance of 2^-9 (half a BF16 unit in the last place) of the sum of the
+    magnitudes of the output's 65 terms: both sides round the hidden layer to
+    BF16; they differ where the SiLU's one-MUFU tanh (relative error about
+    2^-11) moves a hidden value across a BF16 rounding midpoint (a change of one
+    unit, 2^-7 relative, with random sign, in a few of the 64 terms) and by FP32
+    rounding (2^-24 per operation)."""
+    H = 64
+    W1 = w[:2 * H].reshape(H, 2)
+    b1 = w[2 * H:3 * H]
+    W2 = w[3 * H:3 * H + H * H].reshape(H, H)
+    b2 = w[3 * H + H * H:4 * H + H * H]
+    W3 = w[4 * H + H * H:6 * H + H * H].reshape(2, H)
+    b3 = w[6 * H + H * H:]
+    silu = lambda a: a / (1.0 + np.exp(-a))   # noqa: E731
+    h1b = bf16_round(silu(x @ W1.T + b1).astype(np.float32))
+    h2 = silu(h1b @ W2.T + b2)
+    y = h2 @ W3.T + b3
+    return y, 2.0 ** -9 * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))
 
 
 @pytest.fixture(scope="module")
