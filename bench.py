@@ -1,17 +1,19 @@
-"""Benchmark of the GB300 hydro stage: FP64 cell-updates/s on the tabulated-EOS,
-dual-energy entropy-wave workload (128^3 cells as 64 MeshBlocks of 32^3, PLM +
-HLLC + SSP-RK2, Saha H/He table, periodic, Mach 1e7 on rho = 1e-8 g/cm^3,
-T = 1e3 K).
+"""Benchmark of the GB300 hydro stage: FP64 cell-updates/s on the production-shaped
+workload (a stretched n = 1.5 polytrope passing a moving 1e3 Msun point mass with
+excision; 2048 MeshBlocks of 32^3 = 67,108,864 cells, PPM + HLLC + SSP-RK2, Saha
+H/He table with the learned-guess closure, dual energy).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 One step = one synchronised RK2 step of every MeshBlock through the C ABI
-(tde_step: CFL dt, two stages, resync), i.e. 128^3 cell-updates.  Prints one
-JSON line (rank 0).  --impl reference times the CPU oracle on the host cores
-instead (a bounded sample of blocks per step).  Under torchrun each rank runs an
-independent replica on its own GPU (weak scaling, no collective on the data
-path); the timed region is bracketed by a barrier and the maximum over ranks
-is reported.
+(tde_step: CFL dt on the device, two stages, excision, resync).  Beside it: the
+same mesh under LAT (effective rate, work fraction), and as extras the
+entropy-wave workload (128^3), the EOS inversion, self-gravity, the remap and
+LAT on other meshes.  Prints one JSON line (rank 0).  --impl reference times the
+CPU oracle on the host cores instead, on a bounded sample of the workload.
+Under torchrun each rank runs an independent replica on its own GPU (weak
+scaling, no collective on the data path); the timed region is bracketed by a
+barrier and the maximum over ranks is reported.
 """
 import argparse
 import json
@@ -121,92 +123,29 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def run_gpu(args):
-    import torch
-    from paper_2609_37859_gb300 import tde, workloads as wl
-
-    rank, local, world = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    ctx = tde.Context(local, stream)
-    tab = np.load(TABLE)
-    eos = tde.EOS.from_file(ctx, TABLE)
-    Pw, cs2 = eos_point(tab)
-    lay = layout()
-    W, _ = wl.entropy_wave(lay, RHO0, Pw, MACH * np.sqrt(cs2), amp=AMP, seed=SEED + rank)
-    mesh = tde.Mesh(ctx, lay, tde.make_params(**SCHEME), eos)
-    W_d = torch.from_numpy(np.ascontiguousarray(W)).to(dev)
-    mesh.prim_to_cons(W_d)
-    U_init = mesh.U.clone()
-    del W_d
-    ncell = lay.ncells
-    # sweep tile shapes: timed per direction on this workload, fastest kept
-    tiles, tile_ms = mesh.autotune(reps=3)
-
+def barrier_fn(torch, dev, dist):
     def barrier():
         torch.cuda.synchronize(dev)
         if dist is not None:
             dist.barrier()
+    return barrier
 
-    # ---- device-resident timed region (value)
-    for _ in range(args.warmup):
-        mesh.step(cfl=CFL)
-    barrier()
-    # conservation audit of the timed steps (outside the timed region): the
-    # interior sums of the conserved fields, correctly rounded (math.fsum)
-    flat_int = torch.from_numpy(lay.interior_flat()).to(dev)
 
-    def audit():
-        G = mesh.U[:5][:, flat_int].cpu().numpy()
-        return [math.fsum(G[q]) for q in range(5)], [math.fsum(np.abs(G[q])) for q in range(5)]
-    sums0, scale0 = audit()
-    barrier()
-    ctx.profile(True)
-    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                    if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
-    clocks.start()
-    time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        mesh.step(cfl=CFL)
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1)
-    prof = ctx.profile_read()
-    clk = clocks.stop()
-    ctx.profile(False)
-    ms = max_over_ranks(ms, dist, dev)
-    counts = mesh.counts()
-    sums1, _ = audit()
-    conservation = {"steps": args.steps, "summation": "math.fsum (correctly rounded) over the interior cells",
-                    "rel_drift": {name: abs(sums1[q] - sums0[q]) / max(scale0[q], 1e-300)
-                                  for q, name in enumerate(("mass", "momentum_x", "momentum_y", "momentum_z",
-                                                            "total_energy"))}}
-    del flat_int
-
-    # ---- end-to-end through the C ABI with host buffers: every step copies its
-    # state in from pinned host memory and its result back out.  Three device
-    # states rotate so that step k + 1's input copy and step k - 1's output copy
-    # (each on its own stream) overlap step k's kernels.
-    host_in = U_init.cpu().pin_memory()
-    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(3)]
-    nbytes = host_in.numel() * 8
+def e2e_rotating(mesh, host_in, step_fn, torch, dev, stream):
+    """End to end through the C ABI with host buffers: every step copies its
+    state in from pinned host memory and its result back out.  Three device
+    states rotate so that step k + 1's input copy and step k - 1's output copy
+    (each on its own stream) overlap step k's kernels; the output copies go to
+    one pinned buffer in stream order.  Returns run(n) and the bytes per copy."""
+    host_out = torch.empty_like(host_in).pin_memory()
     U_main = mesh.U
     bufs = [U_main, torch.empty_like(U_main), torch.empty_like(U_main)]
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     ev_in = [torch.cuda.Event() for _ in range(3)]
     ev_done = [torch.cuda.Event() for _ in range(3)]
     ev_out = [torch.cuda.Event() for _ in range(3)]
-    mesh.set_time(0.0)
 
-    def e2e_run(n):
+    def run(n):
         with torch.cuda.stream(s_in):
             bufs[0].copy_(host_in, non_blocking=True)
             ev_in[0].record(s_in)
@@ -220,89 +159,124 @@ def run_gpu(args):
                     ev_in[nx].record(s_in)
             stream.wait_event(ev_in[b])
             mesh.bind(bufs[b])
-            mesh.step(cfl=CFL)
+            step_fn()
             ev_done[b].record(stream)
             with torch.cuda.stream(s_out):
                 s_out.wait_event(ev_done[b])
-                host_out[b].copy_(bufs[b], non_blocking=True)
+                host_out.copy_(bufs[b], non_blocking=True)
                 ev_out[b].record(s_out)
         stream.wait_event(ev_out[(n - 1) % 3])
 
-    e2e_run(max(1, args.warmup))
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    e2e_run(args.steps)
-    f1.record(stream)
-    barrier()
-    ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, dev)
-    mesh.bind(U_main)
-    del bufs
+    def close():
+        mesh.bind(U_main)
+        bufs.clear()
+    return run, close, host_in.numel() * 8
 
+
+def sweep_roofline(prof, cells, flop_per_cell, slots_per_cell, traffic, fp64_peak, kernel_note):
+    """roofline object of the dominant sweep: FP64 FLOP per cell (ncu SASS
+    counters of that kernel on this workload) x cells per launch / its average
+    CUDA-event launch time, against the FP64 FMA rate measured in this run."""
+    sweeps = {k: prof[k] for k in ("sweep_x", "sweep_y", "sweep_z") if prof[k][0]}
+    dom = max(sweeps, key=lambda k: sweeps[k][1])
+    n_dom, ms_dom = sweeps[dom]
+    avg_ms = ms_dom / max(n_dom, 1)
+    roof = {"bound": "alu", "kernel": "k_sweep (%s)" % dom.replace("sweep_", ""),
+            "unit": "TFLOP/s", "peak": fp64_peak * 1e-12,
+            "peak_source": "FP64 FMA probe measured in this run (tde_probe_fp64)",
+            "traffic": traffic.get(dom) if traffic else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
+            "avg_launch_ms": avg_ms, "launches": n_dom, "counters": kernel_note}
+    fpc = flop_per_cell.get(dom) if flop_per_cell else None
+    if fpc:
+        ach = fpc * cells / (avg_ms * 1e-3)
+        roof.update({"achieved": ach * 1e-12, "frac": ach / fp64_peak, "fp64_flop_per_cell": fpc})
+        slots = slots_per_cell.get(dom) if slots_per_cell else None
+        if slots:
+            # the same kernel counted in FP64-pipe issue slots (peak = FMA rate / 2)
+            rate = slots * cells / (avg_ms * 1e-3)
+            roof["fp64_issue"] = {"slots_per_cell": slots, "achieved_slots_per_s": rate,
+                                  "peak_slots_per_s": fp64_peak / 2, "frac": rate / (fp64_peak / 2)}
+    else:
+        roof.update({"achieved": None, "frac": None})
+    return roof
+
+
+def hbm_roofline(rate_per_gpu, peaks):
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    gbs = rate_per_gpu * BYTES_PER_CELL_UPDATE * 1e-9
+    return {"bytes_per_cell_update": BYTES_PER_CELL_UPDATE, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs", "frac": gbs / hbm_peak}
+
+
+def run_gpu(args):
+    import torch
+    from paper_2609_37859_gb300 import tde
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tde.Context(local, stream)
+    eos = tde.EOS.from_file(ctx, TABLE)
+    barrier = barrier_fn(torch, dev, dist)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    # the learned closure of the headline needs the trained network (device
+    # training: own forward / backward kernels and Adam, 2^20 table samples)
+    train = eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
+
+    # ---- the headline: synchronised RK2 steps of the production-shaped mesh
+    head = c5_headline(ctx, eos, tde, torch, dev, args, dist, world, barrier, stream)
     fp64_peak = ctx.probe_fp64()
     if rank == 0:
         steps = args.steps
-        value = whole_job_rate(ncell, world, steps, ms)
-        e2e = whole_job_rate(ncell, world, steps, ms_e2e)
-        sweeps = {k: prof[k] for k in ("sweep_x", "sweep_y", "sweep_z")}
-        dom = max(sweeps, key=lambda k: sweeps[k][1])
-        n_dom, ms_dom = sweeps[dom]
-        avg_ms = ms_dom / max(n_dom, 1)
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except OSError:
-            pass
-        hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        fp64_per_cell = FP64_FLOP_PER_CELL_SWEEP.get(dom)
-        roof = {"bound": "alu", "kernel": "k_sweep (%s)" % dom.replace("sweep_", ""),
-                "unit": "TFLOP/s", "peak": fp64_peak * 1e-12,
-                "peak_source": "FP64 FMA probe measured in this run (tde_probe_fp64)",
-                "traffic": DRAM_BYTES_SWEEP.get(dom) if KERNELS_AS_CAPTURED else None,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
-                "avg_launch_ms": avg_ms}
-        if fp64_per_cell:
-            ach = fp64_per_cell * ncell / (avg_ms * 1e-3)
-            roof.update({"achieved": ach * 1e-12, "frac": ach / fp64_peak,
-                         "fp64_flop_per_cell": fp64_per_cell})
-            slots = FP64_SLOTS_PER_CELL_SWEEP.get(dom)
-            if slots and KERNELS_AS_CAPTURED:
-                # the same kernel counted in FP64-pipe issue slots (peak = FMA rate / 2)
-                rate = slots * ncell / (avg_ms * 1e-3)
-                roof["fp64_issue"] = {"slots_per_cell": slots, "achieved_slots_per_s": rate,
-                                      "peak_slots_per_s": fp64_peak / 2, "frac": rate / (fp64_peak / 2)}
-        else:
-            roof.update({"achieved": None, "frac": None})
-        total_launches = sum(v[0] for v in prof.values())
+        ms = head["ms"]
+        value = whole_job_rate(head["cells"], world, steps, ms)
+        e2e = whole_job_rate(head["cells"], world, steps, head["ms_e2e"])
+        roof = sweep_roofline(head["prof"], head["cells"], FP64_FLOP_PER_CELL_C5, FP64_SLOTS_PER_CELL_C5,
+                              DRAM_BYTES_C5 if KERNELS_AS_CAPTURED_C5 else None, fp64_peak,
+                              C5_COUNTERS_NOTE)
+        prof = head["prof"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": ncell, "meshblocks": lay.nb,
-                       "global_batch": world * ncell, "parallelism": "replica per GPU" if world > 1 else "1 GPU",
-                       "l2": "working set %.2f GB per step > 129 MB L2 (no flush needed)" %
-                             ((mesh.U.numel() * 2 + mesh.ntot * (7 + 8)) * 8 / 1e9)},
-            "hbm_roofline": {"bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
-                             "achieved_gbs": value / world * BYTES_PER_CELL_UPDATE * 1e-9,
-                             "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                             "frac": value / world * BYTES_PER_CELL_UPDATE * 1e-9 / hbm_peak},
+            "config": {"workload": C5_WORKLOAD, "cells": head["cells"], "meshblocks": head["meshblocks"],
+                       "global_batch": world * head["cells"],
+                       "parallelism": "replica per GPU" if world > 1 else "1 GPU",
+                       "step": "one synchronised SSP-RK2 step of every MeshBlock (tde_step: CFL dt on "
+                               "the device, two stages with the learned closure, excision, resync)",
+                       "l2": "working set %.1f GB per step > 129 MB L2 (no flush needed)" % head["state_gb"]},
+            "hbm_roofline": hbm_roofline(value / world, peaks),
             "roofline": roof,
-            "autotune": autotune_report(tiles, tile_ms),
             "kernels_ms": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
             "kernels_launches": {k: v[0] for k, v in prof.items() if v[0]},
-            "gpu_launches": total_launches,
-            "clocks": clk,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "counters": counts,
-            "conservation": conservation,
+            "gpu_launches": sum(v[0] for v in prof.values()),
+            "clocks": head["clocks"],
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": head["copy_bytes"],
+                    "d2h_bytes_per_step": head["copy_bytes"]},
+            "counters": head["counts"],
+            "autotune": head["autotune"],
+            "lat": head["lat"],
+            "training": {k: train[k] for k in ("samples", "epochs", "ms", "loss_first", "loss_last")},
         }
+        if tuple(args.c5_grid) != (16, 16, 8):
+            line["config"]["workload"] += "; profiling case: %d x %d x %d MeshBlocks around the star" % \
+                tuple(args.c5_grid)
+        torch.cuda.empty_cache()
+        if not args.no_c2:
+            line["c2_entropy_wave"] = c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks)
+            torch.cuda.empty_cache()
         if not args.no_eos:
             line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
-            line["closure_modes"] = closure_bench(mesh, U_init, tde, torch, dev, args)
-        elif not (args.no_lat and args.no_c5):   # their learned arms need the network
-            eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
-        del mesh, U_init, host_in, host_out, U_main
-        torch.cuda.empty_cache()
         if not args.no_grav:
             line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
         if not args.no_remap:
@@ -311,14 +285,85 @@ def run_gpu(args):
             line["lat_refined"] = smr_bench(ctx, tde, torch, dev, args)
         if not args.no_lat:
             line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
-        if not args.no_c5:
-            line["c5_production"] = c5_bench(ctx, eos, tde, torch, dev, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks):
+    """The entropy-wave workload (C2: 128^3 as 64 x 32^3, PLM, Saha table in cgs,
+    dual energy, Mach 1e7): device rate, end to end, roofline of its dominant
+    sweep, conservation audit and the closure modes."""
+    from paper_2609_37859_gb300 import workloads as wl
+    tab = np.load(TABLE)
+    Pw, cs2 = eos_point(tab)
+    lay = layout()
+    W, _ = wl.entropy_wave(lay, RHO0, Pw, MACH * np.sqrt(cs2), amp=AMP, seed=SEED)
+    mesh = tde.Mesh(ctx, lay, tde.make_params(**SCHEME), eos)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(dev))
+    U_init = mesh.U.clone()
+    ncell = lay.ncells
+    tiles, tile_ms = mesh.autotune(reps=3)
+    steps = max(args.steps, 20)
+    for _ in range(args.warmup):
+        mesh.step(cfl=CFL)
+    torch.cuda.synchronize(dev)
+    flat_int = torch.from_numpy(lay.interior_flat()).to(dev)
+
+    def audit():
+        G = mesh.U[:5][:, flat_int].cpu().numpy()
+        return [math.fsum(G[q]) for q in range(5)], [math.fsum(np.abs(G[q])) for q in range(5)]
+    sums0, scale0 = audit()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        mesh.step(cfl=CFL)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    sums1, _ = audit()
+    conservation = {"steps": steps, "summation": "math.fsum (correctly rounded) over the interior cells",
+                    "rel_drift": {name: abs(sums1[q] - sums0[q]) / max(scale0[q], 1e-300)
+                                  for q, name in enumerate(("mass", "momentum_x", "momentum_y", "momentum_z",
+                                                            "total_energy"))}}
+    del flat_int
+    host_in = U_init.cpu().pin_memory()
+    mesh.set_time(0.0)
+    run, close, nbytes = e2e_rotating(mesh, host_in, lambda: mesh.step(cfl=CFL), torch, dev, stream)
+    run(max(1, args.warmup))
+    torch.cuda.synchronize(dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    run(steps)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = f0.elapsed_time(f1)
+    close()
+    value = ncell * steps / (ms * 1e-3)
+    out = {"workload": WORKLOAD, "cells": ncell, "steps": steps, "ms_per_step": ms / steps,
+           "value": value, "unit": UNIT,
+           "e2e": {"value": ncell * steps / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                   "d2h_bytes_per_step": nbytes},
+           "hbm_roofline": hbm_roofline(value, peaks),
+           "roofline": sweep_roofline(prof, ncell, FP64_FLOP_PER_CELL_SWEEP, FP64_SLOTS_PER_CELL_SWEEP,
+                                      DRAM_BYTES_SWEEP if KERNELS_AS_CAPTURED else None, fp64_peak,
+                                      "profiles/k_sweep_c2_entropy_wave_ncu.md"),
+           "kernels_ms": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
+           "autotune": autotune_report(tiles, tile_ms),
+           "counters": mesh.counts(),
+           "conservation": conservation}
+    if not args.no_eos:
+        out["closure_modes"] = closure_bench(mesh, U_init, tde, torch, dev, args)
+    del mesh, U_init, host_in
+    return out
 
 
 # FP64 operations (DADD + DMUL + 2 x DFMA thread-instructions, ncu SASS counters)
@@ -331,7 +376,18 @@ DRAM_BYTES_SWEEP = {"sweep_x": 266.6e6, "sweep_y": 400.9e6, "sweep_z": 542.8e6}
 # FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
 # holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
 FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 201.9, "sweep_y": 201.9, "sweep_z": 289.9}
-KERNELS_AS_CAPTURED = True
+KERNELS_AS_CAPTURED = False
+# The same for the headline's sweeps (production-shaped mesh, PPM, point mass),
+# from ncu on the 8 x 8 x 4 MeshBlocks around the star of that mesh (8.4 M
+# cells, the same cells and scheme; the full mesh holds ~36 GB on the device,
+# too much for a multi-pass capture), two launches of each sweep averaged,
+# DRAM bytes scaled to the full mesh by its cells (x 8); a one-pass capture of
+# the full mesh gives the same FP64 slots per cell within 2 %.
+FP64_FLOP_PER_CELL_C5 = {"sweep_x": 345.3, "sweep_y": 343.9, "sweep_z": 473.7}
+FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 299.6, "sweep_y": 295.4, "sweep_z": 387.1}
+DRAM_BYTES_C5 = {"sweep_x": 10.02e9, "sweep_y": 14.54e9, "sweep_z": 20.37e9}
+KERNELS_AS_CAPTURED_C5 = True
+C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 
 SHAPE_NAMES = ("8 lanes x 272 threads", "16 lanes x 288 threads", "4 lanes x 160 threads")
@@ -400,9 +456,8 @@ EOS_CELLS = 1 << 24
 
 def eos_bench(ctx, eos, tde, torch, dev, args):
     """2^24 (rho, e) cells -> (T, P, cs2): table bisection against the learned guess
-    plus one Newton step (identical results, checked), after training the network
-    on the device (2^20 table samples)."""
-    rep = eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
+    plus one Newton step (identical results, checked), with the network trained on
+    the device at the start of the run (2^20 table samples)."""
     from paper_2609_37859_gb300 import workloads as wl
     g = torch.Generator(device=dev)
     g.manual_seed(SEED)
@@ -440,9 +495,7 @@ def eos_bench(ctx, eos, tde, torch, dev, args):
             "surrogate_newton": res["surrogate"],
             "speedup_vs_plain": res["bisect_plain"]["ms"] / res["surrogate"]["ms"],
             "speedup_vs_fp32_guided": res["bisect"]["ms"] / res["surrogate"]["ms"],
-            "identical_results": bool(same),
-            "training": {"samples": rep["samples"], "epochs": rep["epochs"], "ms": rep["ms"],
-                         "loss_first": rep["loss_first"], "loss_last": rep["loss_last"]}}
+            "identical_results": bool(same)}
 
 
 # ------------------------------------------------------------- LAT stream (C4) ---
@@ -815,21 +868,26 @@ def remap_bench(ctx, tde, torch, dev, args, n=256, reps=5):
 # ------------------------------------------------------ production shape (C5) ---
 
 # rho_floor (rho0), p_floor (rho0 v0^2): 100x Table 1's.  With Table 1's floors
-# this unrelaxed star (no self-gravity, floor gas falling onto the point mass)
-# leaves ~7e4 non-finite cell-stages per window; with these, none.
+# this unrelaxed star (no self-gravity) leaves non-finite cells in LAT windows:
+# floor cells at the star's tip are heated within one step of a slow block (c_s
+# 0.13 -> 26) and its fixed step then runs at Courant number 2; with these, none.
 C5_FLOORS = (1e-8, 1e-10)
+C5_WORKLOAD = ("production-shaped: stretched n=1.5 polytrope (1 Msun, 1 Rsun, 4:1) in its own frame, a 1e3 Msun "
+               "point mass with excision passing at the parabolic speed through free-falling ambient gas; "
+               "2048 MeshBlocks of 32^3 (512x512x256 = 67,108,864 cells), ghost width 3, PPM+HLLC+SSP-RK2, "
+               "Saha H/He 256x256 table in the code units of Table 1, learned-guess closure (BF16 tensor-core "
+               "MLP + FP64 Newton, bisection fallback), dual energy, floors 100x Table 1's, CFL 0.3")
 
 
-def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
-    """The production-shaped run: 2048 x 32^3 MeshBlocks (67 M cells), PPM + HLLC,
-    Saha table in code units with the learned-guess closure, dual energy, the
-    floors of Table 1, a stretched n = 1.5 polytrope (1 Msun, 1 Rsun) passing a
-    moving 1e3 Msun point mass with excision; factors on N_LAT = 6 levels,
-    re-assigned at every window; LAT windows covering 200 fine steps (at most 4
-    windows), replayed as a CUDA graph, against synchronised steps of dt0."""
+def build_c5(ctx, eos, tde, torch, dev, floors=C5_FLOORS, grid=(16, 16, 8)):
+    """The production-shaped mesh; `grid` (blocks per axis) other than 16 x 16 x 8
+    keeps the cell size and takes the blocks around the star (a smaller case
+    of the same workload, for profiling)."""
     from paper_2609_37859_gb300 import workloads as wl
-    t_setup = time.time()
-    lay, f, bhp = wl.star_c5(seed=SEED, rho_floor=floors[0], p_floor=floors[1])
+    t0 = time.time()
+    half = tuple(n * 32 * 0.0625 / 2.0 for n in grid)   # Rsun: 32-cell blocks of 0.0625 Rsun
+    lay, f, bhp = wl.star_c5(seed=SEED, rho_floor=floors[0], p_floor=floors[1], n_blocks=tuple(grid),
+                             half_rsun=half)
     W = wl.prim_state(lay, f["rho"], f["vx"], f["vy"], f["vz"], f["P"])
     del f
     params = tde.make_params(eos=tde.EOS_TABLE, recon=tde.RECON_PPM, dual=1, eta1=1e-3, eta2=1e-4,
@@ -840,14 +898,86 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
     del W
     bh = tde.make_bh(on=1, excise=1, GM=bhp["GM"], r_soft=bhp["r_soft"], r_exc=bhp["r_exc"],
                      x0=bhp["x0"], v0=bhp["v0"])
-    setup_s = time.time() - t_setup
+    return lay, mesh, bh, time.time() - t0
+
+
+def c5_headline(ctx, eos, tde, torch, dev, args, dist, world, barrier, stream):
+    """Synchronised steps of the production-shaped mesh (the headline), then the
+    same mesh under LAT: windows of f_max fine steps on N_LAT = 6 levels,
+    factors re-assigned at every window, replayed as a CUDA graph."""
+    lay, mesh, bh, setup_s = build_c5(ctx, eos, tde, torch, dev, grid=args.c5_grid)
     tiles, tile_ms = mesh.autotune(bh=bh, reps=1)
+    U_init = mesh.U.clone()
+    step = lambda: mesh.step(cfl=CFL, bh=bh)   # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    # the end-to-end steps below start from the state the timed steps start from
+    U_t0 = mesh.U.clone()
+    mesh.counts(reset=True)
+    ctx.profile(True)
+    rank, local, _ = dist_env()
+    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                    if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select these launches
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    clk = clocks.stop()
+    ctx.profile(False)
+    ms = max_over_ranks(ms, dist, dev)
+    counts = mesh.counts(reset=True)
+    state_gb = (mesh.U.numel() * 2 + mesh.ntot * (8 + 7)) * 8 / 1e9
+
+    # end to end through the C ABI: the state in from pinned host memory and
+    # the result out, every step (each step starts from the initial state)
+    host_in = U_t0.cpu().pin_memory()
+    del U_t0
+    mesh.set_time(0.0)
+    run, close, nbytes = e2e_rotating(mesh, host_in, step, torch, dev, stream)
+    run(max(1, args.warmup))
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    run(args.steps)
+    f1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+    close()
+    del host_in
+    torch.cuda.empty_cache()
+
+    lat = c5_lat(ctx, mesh, lay, bh, U_init, torch, dev) if not args.no_c5 else None
+    if lat is not None:
+        lat["host_setup_s"] = setup_s
+    out = {"ms": ms, "ms_e2e": ms_e2e, "prof": prof, "clocks": clk, "counts": counts, "cells": lay.ncells,
+           "meshblocks": lay.nb, "copy_bytes": nbytes, "state_gb": state_gb,
+           "autotune": autotune_report(tiles, tile_ms), "lat": lat}
+    del mesh, U_init
+    torch.cuda.empty_cache()
+    return out
+
+
+def c5_lat(ctx, mesh, lay, bh, U0, torch, dev):
+    """LAT on the production-shaped mesh: windows covering 200 fine steps (at
+    most 4), factors from the CFL condition at each window start, the captured
+    window kept while the level sizes hold; against synchronised steps of dt0."""
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
     fac, dt0, fmax = mesh.lat_assign(6, CFL, merge_frac=0.01, bh=bh)
     cells = np.array([b[3] * b[4] * b[5] for b in lay.blocks], dtype=np.float64)
     work = float((cells * (fmax // fac)).sum() / (cells.sum() * fmax))
     levels = {int(k): int((fac == k).sum()) for k in np.unique(fac)}
     nwin = int(max(1, min(4, -(-200 // fmax))))
-    U0 = mesh.U.clone()
 
     def timed(fn, reps):
         torch.cuda.synchronize(dev)
@@ -884,7 +1014,6 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
 
     def window():
         # as in production: factors from the CFL condition at each window start
-        # (the captured window is kept while the levels keep their sizes)
         fw, _, fm = mesh.lat_assign(6, CFL, merge_frac=0.01, bh=bh)
         fmaxes.append(int(fm))
         structures.add(tuple(int((fw == k).sum()) for k in (1, 2, 4, 8, 16, 32, 64)))
@@ -892,21 +1021,14 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
         mesh.lat_window(bh=bh, use_graph=True)
     ms_win = timed(window, nwin)
     c = mesh.counts(reset=True)
-    # synchronised steps of dt0 (two timed) for the same physical time
     mesh.U.copy_(U0)
     mesh.set_time(0.0)
     mesh.step(dt=dt0, bh=bh)
     ms_step = timed(lambda: mesh.step(dt=dt0, bh=bh), 2)
     ncell = lay.ncells
-    del mesh, U0
-    torch.cuda.empty_cache()
-    return {"workload": "stretched n=1.5 polytrope (1 Msun, 1 Rsun, 4:1) in its own frame, a 1e3 Msun point "
-                        "mass with excision passing at the parabolic speed through free-falling ambient gas, "
-                        "2048 x 32^3 MeshBlocks, PPM+HLLC, Saha table, learned-guess closure, dual energy, "
-                        "floors 100x Table 1's, N_LAT 6",
-            "cells": ncell, "meshblocks": lay.nb, "f_max": int(fmax), "blocks_per_factor": levels,
+    return {"workload": "the headline mesh under LAT, N_LAT 6, windows covering 200 fine steps (at most 4)",
+            "f_max": int(fmax), "blocks_per_factor": levels,
             "work_fraction": work, "windows": nwin, "fine_steps": nwin * int(fmax),
-            "autotune": autotune_report(tiles, tile_ms),
             "window_f_max": fmaxes, "distinct_level_structures": len(structures),
             "work_fraction_per_window": works,
             "ideal_speedup_timed_windows": 1.0 / float(np.mean(works)),
@@ -914,95 +1036,110 @@ def c5_bench(ctx, eos, tde, torch, dev, args, floors=C5_FLOORS):
             "lat_speedup_vs_sync": ms_step * np.mean(fmaxes) / ms_win,
             "effective_cell_updates_per_s": ncell * np.mean(fmaxes) / (ms_win * 1e-3),
             "sync_cell_updates_per_s": ncell / (ms_step * 1e-3),
-            "floors": {"rho_floor": floors[0], "p_floor": floors[1], "unit": "rho0, rho0 v0^2"},
+            "floors": {"rho_floor": C5_FLOORS[0], "p_floor": C5_FLOORS[1], "unit": "rho0, rho0 v0^2"},
             "counters_per_window": {k: v // nwin for k, v in c.items()},
-            "first_window_ms_by_kernel_class": by_kind,
-            "host_setup_s": setup_s}
+            "first_window_ms_by_kernel_class": by_kind}
 
 
 # ------------------------------------------------------------------ oracle ---
 
-def oracle_setup(sample_blocks):
+# The oracle's bounded sample of the headline workload: the 4 x 4 x 2 MeshBlocks
+# of 32^3 around the star (the same cells, scheme, floors and point mass; the
+# point mass lies outside the sample, its potential acts on it).
+C5_SAMPLE = dict(n_blocks=(4, 4, 2), half_rsun=(4.0, 4.0, 2.0))
+
+
+def oracle_c5_sample():
     from oracle import tref
+    from paper_2609_37859_gb300 import workloads as wl
     d = np.load(TABLE)
     ot = tref.EOSTable(int(d["n_rho"]), int(d["n_T"]), tuple(d["lrho"]), tuple(d["lT"]),
                        d["log10_e"], d["log10_P"], d["log10_cs2"])
-    Pw, cs2 = eos_point(d)
-    from paper_2609_37859_gb300 import workloads as wl
-    lay = layout()
-    W, _ = wl.entropy_wave(lay, RHO0, Pw, MACH * np.sqrt(cs2), amp=AMP, seed=SEED)
-    m = tref.Mesh(lay, tref.make_params(**SCHEME), ot)
+    lay, f, bhp = wl.star_c5(seed=SEED, rho_floor=C5_FLOORS[0], p_floor=C5_FLOORS[1], **C5_SAMPLE)
+    W = wl.prim_state(lay, f["rho"], f["vx"], f["vy"], f["vz"], f["P"])
+    p = tref.make_params(eos=tref.EOS_TABLE, recon=tref.PPM, dual=1, eta1=1e-3, eta2=1e-4,
+                         rho_floor=C5_FLOORS[0], p_floor=C5_FLOORS[1], u_floor=1.5 * C5_FLOORS[1],
+                         unit_rho=wl.RHO0_CGS, unit_e=wl.V0_CGS ** 2, bh_on=1, excision_on=1,
+                         GM=bhp["GM"], r_soft=bhp["r_soft"], r_exc=bhp["r_exc"], bh_x0=bhp["x0"],
+                         bh_v0=bhp["v0"], bh_a0=(0.0, 0.0, 0.0))
+    m = tref.Mesh(lay, p, ot)
     U = m.prim_to_cons(W)
-    ids = np.linspace(0, lay.nb - 1, sample_blocks).astype(np.int32)
-    m.dt = float(m.cfl_dt(U, CFL).min())
-    return tref, m, U, ids, lay
+    return tref, m, U, lay
 
 
-def oracle_step(tref, m, U, S, ids, lay):
-    """One RK2 step of the sampled blocks (ghost fill, two stages, resync)."""
-    nb = lay.nb
-    dtb, tb = np.full(nb, m.dt), np.zeros(nb)
-    m.ghost_fill(U)
-    m.stage(0, U, U, S, dtb, tb, ids=ids)
-    m.ghost_fill(S)
-    m.stage(1, U, S, U, dtb, tb, ids=ids)
-    m.ghost_fill(U)
-    m.dual_sync(U, ids=ids)
+class OracleStepper:
+    """One step of the oracle on the sample: CFL dt over every block (as the
+    GPU step computes it), then the synchronised RK2 step (ghost fill, two
+    stages, excision, resync) of every block of the sample."""
+
+    def __init__(self):
+        self.tref, self.m, self.U, self.lay = oracle_c5_sample()
+        self.S = self.m.new_state()
+        self.t = 0.0
+        self.cells = self.lay.ncells
+
+    def __call__(self):
+        nb = self.lay.nb
+        dt = float(self.m.cfl_dt(self.U, CFL, np.full(nb, self.t)).min())
+        self.m.step(self.U, dt, self.t, self.S)
+        self.t += dt
+
+
+SAMPLE_NOTE = ("the 4x4x2 MeshBlocks of 32^3 (1,048,576 cells) around the star of the same workload, same "
+               "cells, scheme and floors; each step: CFL dt over the sample, then one synchronised RK2 step of "
+               "all its MeshBlocks (OpenMP over MeshBlocks, 32 blocks on the host's threads)")
 
 
 def cpu_baseline(seconds):
-    """The oracle as it stands, on the host cores, on a bounded sample (whole
-    RK2 steps of 8 of the 64 MeshBlocks, repeated for about `seconds`)."""
-    tref, m, U, ids, lay = oracle_setup(8)
-    S = m.new_state()
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    headline workload, for about `seconds`, then on one thread for a third of that."""
+    st = OracleStepper()
+    tref = st.tref
+    st()   # first touch
     n, t0 = 0, time.perf_counter()
     while True:
-        oracle_step(tref, m, U, S, ids, lay)
+        st()
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    cells = n * len(ids) * BLOCK ** 3
     cores = tref.num_threads()
-    # the same sample on one thread, for a third of the time
     tref.set_num_threads(1)
     n1, t1 = 0, time.perf_counter()
     while True:
-        oracle_step(tref, m, U, S, ids, lay)
+        st()
         n1 += 1
         el1 = time.perf_counter() - t1
         if el1 >= seconds / 3.0:
             break
     tref.set_num_threads(cores)
-    return {"value": cells / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d RK2 steps of %d of the 64 MeshBlocks (32^3) of the workload, %.1f s" %
-                      (n, len(ids), el),
-            "single_thread": {"value": n1 * len(ids) * BLOCK ** 3 / el1, "unit": UNIT, "steps": n1,
-                              "seconds": el1}}
+    v, v1 = n * st.cells / el, n1 * st.cells / el1
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d steps of %s, %.1f s" % (n, SAMPLE_NOTE, el),
+            "threads_busy": min(cores, st.lay.nb),
+            "single_thread": {"value": v1, "unit": UNIT, "steps": n1, "seconds": el1},
+            "all_thread_speedup": v / v1}
 
 
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    tref, m, U, ids, lay = oracle_setup(4)
-    S = m.new_state()
+    st = OracleStepper()
     for _ in range(args.warmup):
-        oracle_step(tref, m, U, S, ids, lay)
+        st()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(tref, m, U, S, ids, lay)
+        st()
     el = time.perf_counter() - t0
-    cells = args.steps * len(ids) * BLOCK ** 3
-    v = cells / el
-    sample = "each step: one RK2 step of %d of the 64 MeshBlocks (32^3) of the workload" % len(ids)
+    v = args.steps * st.cells / el
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "cells_per_step": len(ids) * BLOCK ** 3},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": tref.num_threads(), "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic", "config": {"workload": C5_WORKLOAD, "cells_per_step": st.cells},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": st.tref.num_threads(), "kind": "oracle",
+                         "sample": "each step: " + SAMPLE_NOTE},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -1010,9 +1147,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--no-c5", action="store_true", help="skip the production-shaped LAT run")
+    ap.add_argument("--no-c5", action="store_true", help="skip LAT windows on the headline mesh")
     ap.add_argument("--no-grav", action="store_true", help="skip the self-gravity multigrid")
     ap.add_argument("--no-remap", action="store_true", help="skip the domain remap")
     ap.add_argument("--remap-n", type=int, default=256, help="source grid of the remap section (n^3)")
@@ -1022,6 +1159,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-eos", action="store_true", help="skip the EOS-inversion comparison")
     ap.add_argument("--no-lat", action="store_true", help="skip the LAT stream comparison")
+    ap.add_argument("--no-c2", action="store_true", help="skip the entropy-wave (128^3) section")
+    ap.add_argument("--c5-grid", type=lambda v: tuple(int(x) for x in v.split(",")), default=(16, 16, 8),
+                    help="MeshBlocks per axis of the headline mesh (profiling cases; default 16,16,8)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
