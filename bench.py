@@ -234,6 +234,16 @@ def run_gpu(args):
     train = eos.train(seed=SEED, n_samples=1 << 20, epochs=120, batch=4096, lr=3e-3)
 
     # ---- the headline: synchronised RK2 steps of the production-shaped mesh
+    if args.no_headline:   # profiling runs of the other sections
+        if rank == 0:
+            line = {"metric": METRIC, "value": None, "unit": UNIT, "note": "headline skipped (--no-headline)"}
+            fp64_peak = ctx.probe_fp64()
+            if not args.no_eos:
+                line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
+            if not args.no_grav:
+                line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
+            print(json.dumps(line), flush=True)
+        return
     head = c5_headline(ctx, eos, tde, torch, dev, args, dist, world, barrier, stream)
     fp64_peak = ctx.probe_fp64()
     if rank == 0:
@@ -1160,6 +1170,8 @@ def main():
     ap.add_argument("--no-eos", action="store_true", help="skip the EOS-inversion comparison")
     ap.add_argument("--no-lat", action="store_true", help="skip the LAT stream comparison")
     ap.add_argument("--no-c2", action="store_true", help="skip the entropy-wave (128^3) section")
+    ap.add_argument("--no-headline", action="store_true",
+                    help="profiling: run only the EOS-inversion and self-gravity sections (no headline line)")
     ap.add_argument("--c5-grid", type=lambda v: tuple(int(x) for x in v.split(",")), default=(16, 16, 8),
                     help="MeshBlocks per axis of the headline mesh (profiling cases; default 16,16,8)")
     args = ap.parse_args()
