@@ -366,7 +366,7 @@ __device__ __forceinline__ bool newton_cell(const DTable &t, double rho_c, doubl
 // k_eos_fallback (one atomic per tile reserves the tile's queue slots; the
 // accepted count is added once per CTA).
 template <int NEWTON>
-__global__ void __launch_bounds__(IT, NEWTON ? 4 : 8) k_eos_surrogate(SurrogateArgs a) {
+__global__ void __launch_bounds__(IT, 8) k_eos_surrogate(SurrogateArgs a) {
   __shared__ __align__(1024) unsigned char sA[IT * H * 2];   // h1, BF16, core-matrix layout
   __shared__ __align__(1024) unsigned char sB[H * H * 2];    // W2, BF16, core-matrix layout
   __shared__ float sW1[2 * H], sb1[H], sb2[H], sW3[2 * H], sb3[2];
@@ -698,8 +698,8 @@ cudaError_t launch_surrogate_kernel(tde_eos *e, long long n, const double *rho, 
   return cudaGetLastError();
 }
 
-// the network and the Newton step in one pass (k_eos_surrogate<1>): 4 CTAs per
-// SM (the FP64 step's registers), 4 x 64 TMEM columns
+// the network and the Newton step in one pass (k_eos_surrogate<1>): 8 CTAs per
+// SM (64 registers, no spills), 8 x 64 TMEM columns fill the SM's 512
 cudaError_t launch_surrogate_newton(tde_eos *e, const CellMap &cm, long long n, const double *rho,
                                     const double *en, double *T, double *P, double *cs2, double *eu,
                                     long long *queue, unsigned long long *qcount, Counters *cnt,
@@ -728,7 +728,7 @@ cudaError_t launch_surrogate_newton(tde_eos *e, const CellMap &cm, long long n, 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->ctx->device);
   cudaFuncSetAttribute(k_eos_surrogate<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
-  const int per_sm = 4;
+  const int per_sm = 8;
   const long long tiles = (n + IT - 1) / IT * (cm.blocks ? cm.nblk : 1);
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
   k_eos_surrogate<1><<<grid, IT, 0, s>>>(a);
