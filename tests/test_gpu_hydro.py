@@ -217,6 +217,54 @@ def test_c2_full_size_sampled_stage_and_100_step_invariants(oracle, tde, ctx, ta
     assert gm.counts()["nonfinite"] == 0
 
 
+@pytest.mark.parametrize("eos", [0, 1])
+@pytest.mark.parametrize("stage", [0, 1])
+def test_compression_source_on_a_linear_flow(oracle, tde, ctx, tables, eos, stage):
+    """One stage of the GPU path on the linear velocity field of the oracle's
+    compression pins (tests/test_oracle_compression.py): the auxiliary energy
+    against the closed forms of Eq. dual-compression-continuous (ideal gas) and
+    Eq. dual-tabulated-compression (Saha table, partly ionised hydrogen, the
+    stage's updated density), Delta t_l = dt and dt/2, and against the oracle."""
+    from test_oracle_compression import SLOPES, advected, inner, linear_flow
+    lay = wl.uniform_layout((16, 16, 16), (8, 8, 8), bc=(0, 0, 0), ng=2)
+    if eos:
+        rho0, P0, scale, dt = 1e-8, tables[0].eval_rhoT(1e-8, 1e4)[0], 2e4, 0.04 / 2e4
+        kw = dict(eos=1, dual=1, eta1=1e-3, eta2=1e-4, rho_floor=1e-30, p_floor=1e-30, u_floor=1e-30)
+    else:
+        rho0, P0, scale, dt = 1.0, 1.0, 1.0, 0.02
+        kw = dict(dual=1, eta1=1e-3, eta2=1e-4)
+    Wi = linear_flow(lay, rho0, P0, scale)
+    P = Pair(oracle, tde, ctx, lay, Wi, tables if eos else None, **kw)
+    Uin = P.U.copy()
+    U0 = Uin.copy() if stage == 0 else P.om.prim_to_cons(linear_flow(lay, 1.25 * rho0, 1.5 * P0, 0.0))
+    if stage == 0:
+        P.gm.U.copy_(torch.from_numpy(Uin))
+        P.gm.hydro_stage(0, P.dvec(dt), P.dvec(0.0))
+        G = P.gpu("U1")
+    else:
+        P.gm.U.copy_(torch.from_numpy(U0))
+        P.gm.U1.copy_(torch.from_numpy(Uin))
+        P.gm.hydro_stage(1, P.dvec(dt), P.dvec(0.0))
+        G = P.gpu("U")
+    Gi = inner(lay.to_global(G))
+    D = scale * sum(SLOPES)
+    rho, Astar = advected(inner(lay.to_global(U0)), inner(lay.to_global(Uin)), stage, D * dt)
+    dtl = dt if stage == 0 else 0.5 * dt
+    if eos:
+        r, a = rho.ravel()[0], Astar.ravel()[0]
+        want = a - tables[0].invert(r, a / r)[1] * D * dtl
+    else:
+        want = Astar * np.exp(-(5.0 / 3.0 - 1.0) * D * dtl)
+    assert np.allclose(Gi[0], rho, rtol=1e-13, atol=0)
+    assert np.allclose(Gi[5], want, rtol=1e-12, atol=0), np.max(np.abs(Gi[5] / want - 1))
+    # and the oracle's stage on the same input
+    Uo = P.om.new_state()
+    Ug = Uin.copy()
+    P.om.ghost_fill(Ug)
+    P.om.stage(stage, U0, Ug, Uo, np.full(P.nb, dt), np.zeros(P.nb))
+    assert_parity(lay.to_global(G), lay.to_global(Uo), STAGE_TOL, "linear flow, stage %d" % stage)
+
+
 # ------------------------------------------ ragged blocks, PPM, 2D, subsets ----
 
 @pytest.mark.parametrize("recon,bc", [(0, (1, 0, 1)), (1, (1, 1, 1)), (1, (0, 0, 0))])
