@@ -610,6 +610,8 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   A((void **)&m->d_dtbits, sizeof(unsigned long long) * nblocks);
   A((void **)&m->d_cnt, sizeof(Counters));
   A((void **)&m->d_status, sizeof(int));
+  A((void **)&m->d_phic, sizeof(double) * nt);
+  A((void **)&m->d_excc, nt);
   A((void **)&m->d_gsrcb, sizeof(int32_t) * gsrcb.size());
   A((void **)&m->d_nbr_start, sizeof(int32_t) * (nblocks + 1));
   A((void **)&m->d_nbr, sizeof(int32_t) * m->h_nbr.size());
@@ -681,6 +683,8 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_dtbits);
   cudaFree(m->d_cnt);
   cudaFree(m->d_status);
+  cudaFree(m->d_phic);
+  cudaFree(m->d_excc);
   cudaFree(m->d_tmaps);
   cudaFree(m->d_gsrcb);
   cudaFree(m->d_nbr_start);

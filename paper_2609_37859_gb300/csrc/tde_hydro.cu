@@ -764,6 +764,8 @@ static SweepArgs sweep_args(tde_mesh *m, int stage, const double *U0, const doub
   a.tmap = nullptr;
   a.status = m->d_status;
   a.skip_tma = m->inject_tma_skip;
+  a.phic = m->d_phic;
+  a.exc_c = m->d_excc;
   return a;
 }
 

@@ -143,6 +143,8 @@ struct tde_mesh {
   CUtensorMap *d_tmaps = nullptr;
   int *d_status = nullptr;           // 1 after a bounded device wait of a mesh kernel expired
   int inject_tma_skip = 0;           // test hook: the sweeps issue no TMA copy (their waits expire)
+  double *d_phic = nullptr;          // potential of each interior cell at the stage time (sweep cache)
+  unsigned char *d_excc = nullptr;   // excision flag of each interior cell (sweep cache)
   int32_t *d_ghost = nullptr;        // [n_ghost][2] (dst, src) flat padded indices
   int32_t *d_gstart = nullptr;       // [nb + 1]
   int32_t *d_allids = nullptr;       // 0..nb-1

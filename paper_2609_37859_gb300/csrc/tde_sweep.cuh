@@ -68,6 +68,11 @@ struct SweepArgs {
   int LS, XO;
   int *status;               // set to 1 if a bounded wait for the TMA expired
   int skip_tma;              // failure-detection test: issue no copy, so the wait expires
+  // the potential and excision flag of every interior cell at the stage time,
+  // written by the stage's first sweep and read by the others (null: each
+  // sweep computes them)
+  double *phic;
+  unsigned char *exc_c;
 };
 
 // A sweep tile is M pencils (lanes) of one block along D; its CTA has NTS
@@ -199,10 +204,19 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
     const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
     double rb[3];
     bh_pos(a.bh, ts, rb);
+    const bool cached = a.phic != nullptr;
     for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
       int c, lane;
       split(e, nd + 2, c, lane);
       if (lane >= nlane) continue;
+      const int idx = D == 0 ? lane * NF + c : c * M + lane;
+      const bool inner = c > 0 && c <= nd;
+      const long long cflat = base + (long long)(g - 1 + c) * sD + lane * sL;
+      if (cached && inner && !a.first) {   // interior cell: the first sweep's value
+        if (grav) Ph[idx] = a.phic[cflat];
+        if (exc) Ex[idx] = a.exc_c[cflat];
+        continue;
+      }
       int cc[3];
       cc[D] = g - 1 + c;
       cc[LA] = p.g[LA] + l0 + lane;
@@ -211,13 +225,17 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       cell_centre(p, B, cc, x);
       const double dx0 = x[0] - rb[0], dx1 = x[1] - rb[1], dx2 = x[2] - rb[2];
       const double r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
-      const int idx = D == 0 ? lane * NF + c : c * M + lane;
       if (grav) {
         double ph = a.bh.on ? -a.bh.GM * rsqrt_nr(r2 + a.bh.rs2) : 0.0;
-        if (a.phi_sg) ph += a.phi_sg[base + (long long)(g - 1 + c) * sD + lane * sL];   // Phi_bh + Phi_sg
+        if (a.phi_sg) ph += a.phi_sg[cflat];   // Phi_bh + Phi_sg
         Ph[idx] = ph;
+        if (cached && inner) a.phic[cflat] = ph;
       }
-      if (exc) Ex[idx] = inside_radius(r2, a.bh.rexc) ? 1 : 0;
+      if (exc) {
+        const unsigned char x = inside_radius(r2, a.bh.rexc) ? 1 : 0;
+        Ex[idx] = x;
+        if (cached && inner) a.exc_c[cflat] = x;
+      }
     }
   }
   __syncthreads();   // (also orders the barrier's initialisation before the waits)
