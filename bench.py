@@ -242,6 +242,8 @@ def run_gpu(args):
                 line["eos_inversion"] = eos_bench(ctx, eos, tde, torch, dev, args)
             if not args.no_grav:
                 line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
+            if not args.no_lat:
+                line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
             print(json.dumps(line), flush=True)
         return
     head = c5_headline(ctx, eos, tde, torch, dev, args, dist, world, barrier, stream)
@@ -581,6 +583,13 @@ def lat_bench(ctx, eos, tde, torch, dev, args):
     ms_lat_sur, U_sur, sur_counts = lat_arm(tde.INVERT_SURROGATE)
     same_lat = bool(torch.equal(U_lat, U_sur))
     del U_sur
+    # the same windows with one persistent launch per level sub-step
+    set_mode(tde.INVERT_BISECT)
+    assert mesh.set_lat_mode(tde.LAT_PERSISTENT)
+    ms_lat_pers, U_pers, pers_counts = lat_arm(tde.INVERT_BISECT)
+    same_pers = bool(torch.equal(U_lat, U_pers)) and pers_counts == lat_counts
+    mesh.set_lat_mode(tde.LAT_SEQUENCE)
+    del U_pers
     set_mode(tde.INVERT_BISECT)
     # synchronised steps of dt0 over the same physical time
     mesh.U.copy_(U0)
@@ -622,6 +631,8 @@ def lat_bench(ctx, eos, tde, torch, dev, args):
             "work_fraction": work, "work_reduction": 1.0 - work,
             "autotune": autotune_report(tiles, tile_ms),
             "lat_window_ms": ms_lat, "sync_window_ms": ms_sync,
+            "persistent_level_window_ms": ms_lat_pers,
+            "persistent_level_identical_to_lat": same_pers,
             "learned_batched_window_ms": ms_lat_sur,
             "learned_batched_identical_to_lat": same_lat,
             "learned_accepted_per_window": sur_counts["surrogate_accepted"],

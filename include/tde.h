@@ -321,6 +321,22 @@ TDE_API int tde_lat_set_factors(tde_mesh *mesh, const int32_t *factors, double d
 TDE_API int tde_lat_window(tde_mesh *mesh, const tde_bh_state *bh, int use_graph,
                            int64_t *block_updates);
 
+/* How tde_lat_window runs one level sub-step (Sec. 7.1; the same results bit for
+ * bit in both modes).  TDE_LAT_SEQUENCE (the default): a sequence of batched
+ * launches over the level's blocks (save the start states; per RK stage the
+ * conserved ghosts from other schedules, the conversion to primitives, the
+ * primitive ghosts from the same schedule, the x, y, z sweeps).
+ * TDE_LAT_PERSISTENT: the same phases inside one cooperative launch whose CTAs
+ * stay resident and meet at grid barriers in device memory; a barrier wait is
+ * limited to one second of the global timer, after which the launch ends and
+ * tde_mesh_check reports TDE_ETIMEOUT.  It applies to 3-D meshes without
+ * refined-mesh ghost operations whose closure is not the learned guess; other
+ * meshes keep the sequence.  *active (host, may be NULL) = 1 if the mesh's
+ * current scheme takes the persistent form.  A captured window is discarded on
+ * a change of mode.  TDE_EINVAL for an unknown mode. */
+enum { TDE_LAT_SEQUENCE = 0, TDE_LAT_PERSISTENT = 1 };
+TDE_API int tde_mesh_set_lat_mode(tde_mesh *mesh, int mode, int *active);
+
 /* Copy the cumulative device counters to *out (synchronises the stream) and
  * optionally reset them. */
 TDE_API int tde_counts_read(tde_mesh *mesh, tde_counts *out, int reset);
@@ -350,6 +366,12 @@ TDE_API int tde_eos_inject_wait_expiry(tde_eos *eos, int on);
  * whose sweeps stage without TMA (a padded block row that is not a whole number
  * of 16-byte units). */
 TDE_API int tde_mesh_inject_wait_expiry(tde_mesh *mesh, int on);
+/* Failure-detection test hook of the persistent level launch: with on != 0 its
+ * CTA 0 does not arrive at the first grid barrier, so every CTA's bounded wait
+ * there expires after one second and the launch ends without doing the level's
+ * work; tde_mesh_check then reports TDE_ETIMEOUT once.  on = 0 restores normal
+ * operation.  Discards a captured window. */
+TDE_API int tde_mesh_inject_barrier_drop(tde_mesh *mesh, int on);
 
 /* ---- allocation-free variant ---------------------------------------------- */
 
@@ -408,6 +430,7 @@ enum {
   TDE_K_LATGRAPH = 12, /* replayed LAT window graphs (launches counted per kernel inside) */
   TDE_K_GRAV = 13,    /* self-gravity multigrid */
   TDE_K_REMAP = 14,   /* domain remap (the staging pass counts as scalar) */
+  TDE_K_LATLEVEL = 15, /* persistent LAT level sub-steps */
   TDE_K_NKIND = 16
 };
 

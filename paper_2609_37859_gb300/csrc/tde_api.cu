@@ -705,6 +705,7 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_f);
   cudaFree(m->d_f2);
   cudaFree(m->d_sorted);
+  cudaFree(m->d_lat_bar);
   cudaFree(m->d_Uold);
   cudaFree(m->d_freg);
   cudaFree(m->d_fo);
@@ -1019,6 +1020,23 @@ extern "C" int tde_mesh_inject_wait_expiry(tde_mesh *m, int on) {
     cudaGraphExecDestroy(m->lat_graph);
     m->lat_graph = nullptr;
   }
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_set_lat_mode(tde_mesh *m, int mode, int *active) {
+  if (!m) return TDE_EINVAL;
+  if (mode != TDE_LAT_SEQUENCE && mode != TDE_LAT_PERSISTENT)
+    return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_lat_mode: unknown mode");
+  if (mode != m->lat_mode) invalidate_graph(m);
+  m->lat_mode = mode;
+  if (active) *active = mode == TDE_LAT_PERSISTENT && lat_level_eligible(m) ? 1 : 0;
+  return TDE_OK;
+}
+
+extern "C" int tde_mesh_inject_barrier_drop(tde_mesh *m, int on) {
+  if (!m) return TDE_EINVAL;
+  m->inject_level_drop = on ? 1 : 0;
+  invalidate_graph(m);   // captured launches hold the old flag
   return TDE_OK;
 }
 

@@ -769,17 +769,31 @@ static SweepArgs sweep_args(tde_mesh *m, int stage, const double *U0, const doub
   return a;
 }
 
+// the direction's part of a sweep's arguments (tile shape `shape`)
+static void sweep_dir_fill(const tde_mesh *m, SweepArgs &a, int D, int shape, bool first) {
+  const Phys &p = m->phys;
+  a.first = first;
+  a.PD = m->nmax[D] + 2 * p.g[D];
+  a.NF = m->nmax[D] + 2;
+  sweep_lane_layout(p, D, kTileShapes[shape].M, a.LS, a.XO);
+  a.tmap = m->d_tmaps ? m->d_tmaps + ((size_t)shape * 3 + D) * m->nb : nullptr;
+}
+
+SweepArgs sweep_args_dir(tde_mesh *m, int stage, int D, int shape, bool first, const double *U0,
+                         const double *Uin, double *Uout, const int32_t *ids, const BH &bh, TimeArgs ta,
+                         double *freg) {
+  SweepArgs a = sweep_args(m, stage, U0, Uin, Uout, ids, bh, ta, freg);
+  sweep_dir_fill(m, a, D, shape, first);
+  return a;
+}
+
 // One direction's sweep over nblk blocks with tile shape `shape`.
 static cudaError_t sweep_dir(tde_mesh *m, SweepArgs &a, int D, int shape, bool first, bool last,
                              int nblk) {
   const Phys &p = m->phys;
   const int M = kTileShapes[shape].M;
   const int LA = D == 0 ? 1 : 0, OA = D == 2 ? 1 : 2;
-  a.first = first;
-  a.PD = m->nmax[D] + 2 * p.g[D];
-  a.NF = m->nmax[D] + 2;
-  sweep_lane_layout(p, D, M, a.LS, a.XO);
-  a.tmap = m->d_tmaps ? m->d_tmaps + ((size_t)shape * 3 + D) * m->nb : nullptr;
+  sweep_dir_fill(m, a, D, shape, first);
   const size_t smem = sweep_smem(p, D, a.PD, a.NF, M);
   dim3 grid((unsigned)(((m->nmax[LA] + M - 1) / M) * m->nmax[OA]), (unsigned)nblk);
   return sweep_launch_by_shape(shape, a, D, last, grid, smem, m->ctx->stream);

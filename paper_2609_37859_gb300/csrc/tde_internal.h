@@ -185,6 +185,9 @@ struct tde_mesh {
   long long freg_size = 0;
   double *d_tstart = nullptr;          // per-block step start time
   int *d_flag = nullptr;               // device status word of the factor kernel
+  int lat_mode = TDE_LAT_SEQUENCE;     // how a level sub-step is launched
+  unsigned *d_lat_bar = nullptr;       // grid barrier words of the persistent level kernel
+  int inject_level_drop = 0;           // test hook: its CTA 0 skips the first arrival
   cudaGraphExec_t lat_graph = nullptr;
   tde::BH lat_graph_bh{};
   const double *lat_graph_U = nullptr, *lat_graph_U1 = nullptr;
@@ -218,6 +221,13 @@ size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
 constexpr int N_SWEEP_SHAPES = 3;
 cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3][N_SWEEP_SHAPES]);
 void invalidate_graph(tde_mesh *m);
+// the persistent form of a LAT level sub-step (tde_lat_level.cu): whether the
+// mesh's scheme admits it, and one level sub-step (tau, level factor flevel, the
+// level's nglist converted ghost cells) as one launch
+bool lat_level_eligible(const tde_mesh *m);
+constexpr int LAT_BAR_WORDS = 8;   // barrier counter and generation, six sweep tile counters
+cudaError_t launch_lat_level(tde_mesh *m, const BH &bh, const int32_t *ids, int n, int flevel, int tau,
+                             const int32_t *glist, int nglist);
 cudaError_t launch_frame_acceleration(tde_mesh *m, const BH &bh, double rho_min, double *out4);
 cudaError_t launch_boost(tde_mesh *m, const double *V, double rho_min);
 cudaError_t gravity_solve(tde_mesh *m, const tde_grav_params &gp, int *cycles, double *defect);

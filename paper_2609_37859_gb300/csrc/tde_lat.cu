@@ -635,6 +635,7 @@ int lat_build(tde_mesh *m) {
     m->freg_size = fo[nb];
   }
   if (!m->d_sorted) LCK(c, cudaMalloc(&m->d_sorted, sizeof(int32_t) * nb));
+  if (!m->d_lat_bar) LCK(c, cudaMalloc(&m->d_lat_bar, LAT_BAR_WORDS * sizeof(unsigned)));
   if (!m->d_lat_gstart) LCK(c, cudaMalloc(&m->d_lat_gstart, sizeof(int32_t) * (nb + 1)));
   if (!m->d_lat_glist)
     LCK(c, cudaMalloc(&m->d_lat_glist, sizeof(int32_t) * std::max<int64_t>(m->n_gcopy + m->n_amr, 1)));
@@ -684,6 +685,7 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
   const int fmax = m->lat_fmax;
   const unsigned gx_ghost = (unsigned)std::max(1, std::min((m->max_ghosts + 255) / 256, 64));
   const unsigned gx_copy = 64;
+  const bool persistent = m->lat_mode == TDE_LAT_PERSISTENT && lat_level_eligible(m);
   for (int tau = 0; tau <= fmax; ++tau) {
     if (tau > 0) {
       const int p2 = tau & -tau;   // completing: every level f <= largest power of two dividing tau
@@ -708,6 +710,12 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
       if (tau % f) continue;
       const int32_t *ids = m->d_sorted + m->h_level_start[L];
       const int n = m->h_level_start[L + 1] - m->h_level_start[L];
+      if (persistent) {
+        ProfScope ps(c, TDE_K_LATLEVEL);
+        LCK(c, launch_lat_level(m, bh, ids, n, f, tau, m->d_lat_glist + m->h_lat_glist_off[L],
+                                m->h_lat_glist_off[L + 1] - m->h_lat_glist_off[L]));
+        continue;
+      }
       {
         ProfScope ps(c, TDE_K_SCALAR);
         k_copy_blocks<<<dim3(gx_copy, n), LNT, 0, s>>>(m->d_blocks, ids, m->U, m->d_Uold, nvar,

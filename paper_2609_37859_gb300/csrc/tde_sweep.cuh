@@ -116,19 +116,42 @@ __host__ __device__ __forceinline__ int sweep_union_len(int D, int NV, int PD, i
   return st > fl ? st : fl;
 }
 
-template <int D, int RECON, int EOSK, int DUAL, int LAST, int M, int NTS, int MINB>
-__global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
+// the TMA completion barrier of a sweep CTA: 8-byte aligned after the excision
+// flags (the last part of the tile's shared memory)
+template <int D, int RECON, int NV, int M>
+__device__ __forceinline__ unsigned long long *sweep_mbar(double *sm, int PD, int NF, int LS) {
+  double *Rh = sm + sweep_union_len(D, NV, PD, NF, M, LS) + 2 * NV * NF * M +
+               (RECON == PPM ? 4 * (NF + 1) * M : 0) + NF * M;
+  return reinterpret_cast<unsigned long long *>(Rh + NF * M + (NF * M + 7) / 8);
+}
+
+// initialise a CTA's TMA barrier (thread 0; the caller synchronises before use)
+__device__ __forceinline__ void sweep_mbar_init(unsigned long long *mbar) {
+  const uint32_t ma = (uint32_t)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ma), "r"(1));
+  asm volatile("fence.mbarrier_init.release.cluster;");
+  asm volatile("fence.proxy.async.shared::cta;");
+}
+
+// One sweep tile: tile `tile` of block ids[qb].  The TMA barrier (at `mbar`,
+// initialised) completes once per staged tile with the parity `parity`, which
+// the caller flips after every tile that returns staged = true.  Returns false
+// if the bounded wait for the staging copy expired (the tile is skipped and the
+// status word set).
+template <int D, int RECON, int EOSK, int DUAL, int LAST, int M, int NTS>
+__device__ __forceinline__ bool sweep_tile(const SweepArgs &a, int qb, int tile, double *sm,
+                                           unsigned long long *mbar, uint32_t parity, bool &staged) {
   constexpr int LA = SweepGeo<D>::LA, OA = SweepGeo<D>::OA;
   constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;   // reconstructed primitives
   constexpr int NVAR = 5 + DUAL;                            // conserved variables
-  extern __shared__ __align__(128) double sm[];
   const Phys &p = a.p;
-  const int b = a.ids[blockIdx.y];
+  const int b = a.ids[qb];
   const DevBlock B = a.blocks[b];
   const int nd = B.n[D], nl = B.n[LA], no = B.n[OA];
   const int nlc = (nl + M - 1) / M;
-  if ((int)blockIdx.x >= nlc * no) return;
-  const int l0 = (blockIdx.x % nlc) * M, o = blockIdx.x / nlc;
+  staged = false;
+  if (tile >= nlc * no) return true;   // uniform over the CTA
+  const int l0 = (tile % nlc) * M, o = tile / nlc;
   const int nlane = min(M, nl - l0);
   const int g = p.g[D], pd = B.p[D];
   const long long st[3] = {1, B.p[0], (long long)B.p[0] * B.p[1]};
@@ -149,8 +172,6 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   double *Ph = If + (RECON == PPM ? 4 * (NF + 1) * M : 0);   // [NF][M] potential of cells g-1 .. g+nd
   double *Rh = Ph + NF * M;              // [NF][M] density of the same cells (gravity source)
   unsigned char *Ex = reinterpret_cast<unsigned char *>(Rh + NF * M);   // [NF][M] excised
-  // the TMA completion barrier, 8-byte aligned after the excision flags
-  unsigned long long *mbar = reinterpret_cast<unsigned long long *>(Rh + NF * M + (NF * M + 7) / 8);
 
   auto sw = [&](int v, int pos, int lane) {
     return D == 0 ? (v * M + lane) * PD + pos : (v * PD + pos) * LS + lane + XO;
@@ -171,9 +192,9 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
   // zero-filled and never read), or a copy loop
   const uint32_t mbar_addr = (uint32_t)__cvta_generic_to_shared(mbar);
   if (a.tmap) {
+    staged = true;
     if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_addr), "r"(1));
-      asm volatile("fence.mbarrier_init.release.cluster;");
+      // earlier tiles' generic reads of the staging area before the async write
       asm volatile("fence.proxy.async.shared::cta;");
       const uint32_t bytes = (uint32_t)sweep_stage_len(D, NV, PD, M, LS) * 8u;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_addr), "r"(bytes)
@@ -238,18 +259,18 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       }
     }
   }
-  __syncthreads();   // (also orders the barrier's initialisation before the waits)
+  __syncthreads();
   if (a.tmap) {
     // every thread waits for the copy (bounded); if it did not complete, the
     // tile is skipped, the status word set, and thread 0 waits once more
-    // (bounded) so that no copy is in flight when the CTA exits
-    const bool ok = sweep_wait(mbar_addr, 0);
+    // (bounded) so that no copy is in flight when the CTA goes on or exits
+    const bool ok = sweep_wait(mbar_addr, parity);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(a.status, 1);
-        sweep_wait(mbar_addr, 0);
+        sweep_wait(mbar_addr, parity);
       }
-      return;
+      return false;
     }
   }
 
@@ -453,6 +474,18 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
       if (bad) count(&a.cnt->nonfinite);
     }
   }
+  return true;
+}
+
+template <int D, int RECON, int EOSK, int DUAL, int LAST, int M, int NTS, int MINB>
+__global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
+  constexpr int NV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
+  extern __shared__ __align__(128) double sm[];
+  unsigned long long *mbar =
+      sweep_mbar<D, RECON, NV, M>(sm, a.PD, a.NF, D == 0 ? M : a.LS);
+  if (a.tmap && threadIdx.x == 0) sweep_mbar_init(mbar);   // the tile's __syncthreads orders it
+  bool staged;
+  sweep_tile<D, RECON, EOSK, DUAL, LAST, M, NTS>(a, blockIdx.y, blockIdx.x, sm, mbar, 0, staged);
 }
 
 // ============================================================ launchers ====
@@ -513,5 +546,11 @@ constexpr TileShape kTileShapes[N_TILE_SHAPES] = {{8, 272, 3}, {16, 288, 3}, {4,
 cudaError_t sweep_launch_m8(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t sweep_launch_m16(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t sweep_launch_m4(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
+
+// A sweep's complete arguments for direction D and tile shape `shape` (the
+// launchers' own arguments, for kernels that run sweep tiles themselves).
+SweepArgs sweep_args_dir(tde_mesh *m, int stage, int D, int shape, bool first, const double *U0,
+                         const double *Uin, double *Uout, const int32_t *ids, const BH &bh, TimeArgs ta,
+                         double *freg);
 
 }  // namespace tde

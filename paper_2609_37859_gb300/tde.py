@@ -20,6 +20,7 @@ RECON_PLM, RECON_PPM = 0, 1
 BC_OUTFLOW, BC_PERIODIC = 0, 1
 RIEMANN_HLLC, RIEMANN_HLLE = 0, 1
 INVERT_BISECT, INVERT_SURROGATE, INVERT_BISECT_PLAIN = 0, 1, 2
+LAT_SEQUENCE, LAT_PERSISTENT = 0, 1
 REMAP_THERMAL, REMAP_TOTAL = 0, 1
 GRAV_PERIODIC, GRAV_ISOLATED = 0, 1
 STATUS = {0: "TDE_OK", 1: "TDE_EINVAL", 2: "TDE_ENOMEM", 3: "TDE_ECUDA", 4: "TDE_ERANGE",
@@ -127,6 +128,8 @@ _SIGS = {
     "tde_eos_check": [vp],
     "tde_eos_inject_wait_expiry": [vp, C.c_int],
     "tde_mesh_inject_wait_expiry": [vp, C.c_int],
+    "tde_mesh_inject_barrier_drop": [vp, C.c_int],
+    "tde_mesh_set_lat_mode": [vp, C.c_int, C.POINTER(C.c_int)],
     "tde_profile": [vp, C.c_int],
     "tde_profile_read": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
     "tde_probe_fp64": [vp, C.POINTER(C.c_double)],
@@ -152,7 +155,7 @@ _SIGS = {
                                C.POINTER(BHState), dp, dp],
 }
 KERNEL_KINDS = ("c2p", "dt", "ghost", "sweep_x", "sweep_y", "sweep_z", "sync", "excise", "scalar",
-                "p2c", "eos", "probe", "lat_graph", "grav", "remap")
+                "p2c", "eos", "probe", "lat_graph", "grav", "remap", "lat_level")
 NKIND = 16
 
 _lib = None
@@ -502,6 +505,19 @@ class Mesh:
     def inject_wait_expiry(self, on=True):
         """Failure-detection test hook: the sweeps' TMA waits expire (no copy issued)."""
         self.ctx.check(lib().tde_mesh_inject_wait_expiry(self.h, 1 if on else 0))
+
+    def set_lat_mode(self, mode):
+        """LAT_SEQUENCE or LAT_PERSISTENT (one cooperative launch per level
+        sub-step); returns whether the mesh's current scheme takes the
+        persistent form."""
+        active = C.c_int(0)
+        self.ctx.check(lib().tde_mesh_set_lat_mode(self.h, int(mode), C.byref(active)))
+        return bool(active.value)
+
+    def inject_barrier_drop(self, on=True):
+        """Failure-detection test hook: the persistent level launch's first grid
+        barrier is missing one arrival, so its bounded waits expire."""
+        self.ctx.check(lib().tde_mesh_inject_barrier_drop(self.h, 1 if on else 0))
 
     def counts(self, reset=False):
         c = Counts()
