@@ -634,6 +634,7 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   cudaMemcpy(m->d_blocks, m->hblocks.data(), sizeof(DevBlock) * nblocks, cudaMemcpyHostToDevice);
   if (!gmap.empty()) cudaMemcpy(m->d_ghost, gmap.data(), sizeof(int32_t) * gmap.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_gstart, gstart.data(), sizeof(int32_t) * (nblocks + 1), cudaMemcpyHostToDevice);
+  m->h_gstart = gstart;
   cudaMemcpy(m->d_allids, allids.data(), sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_scal, zeros, sizeof zeros, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_dtbits, inf_bits.data(), sizeof(unsigned long long) * nblocks, cudaMemcpyHostToDevice);
@@ -706,6 +707,7 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_f2);
   cudaFree(m->d_sorted);
   cudaFree(m->d_lat_bar);
+  cudaFree(m->d_lat_pre);
   cudaFree(m->d_Uold);
   cudaFree(m->d_freg);
   cudaFree(m->d_fo);

@@ -147,6 +147,7 @@ struct tde_mesh {
   unsigned char *d_excc = nullptr;   // excision flag of each interior cell (sweep cache)
   int32_t *d_ghost = nullptr;        // [n_ghost][2] (dst, src) flat padded indices
   int32_t *d_gstart = nullptr;       // [nb + 1]
+  std::vector<int32_t> h_gstart;     // its host copy
   int32_t *d_allids = nullptr;       // 0..nb-1
   double *d_W = nullptr;             // primitives, nwv * ntot
   double *d_dU = nullptr;            // accumulated L(U) and div v, (nvar + 1) * ntot
@@ -187,6 +188,10 @@ struct tde_mesh {
   int *d_flag = nullptr;               // device status word of the factor kernel
   int lat_mode = TDE_LAT_SEQUENCE;     // how a level sub-step is launched
   unsigned *d_lat_bar = nullptr;       // grid barrier words of the persistent level kernel
+  // its work items in factor order: prefix sums of the interior and ghost-map
+  // chunks (LAT_LEVEL_THREADS cells each) of the sorted blocks, [2][nb + 1]
+  int32_t *d_lat_pre = nullptr;
+  std::vector<int32_t> h_lat_pre;      // its host copy (the source of the upload)
   int inject_level_drop = 0;           // test hook: its CTA 0 skips the first arrival
   cudaGraphExec_t lat_graph = nullptr;
   tde::BH lat_graph_bh{};
@@ -226,6 +231,7 @@ void invalidate_graph(tde_mesh *m);
 // level's nglist converted ghost cells) as one launch
 bool lat_level_eligible(const tde_mesh *m);
 constexpr int LAT_BAR_WORDS = 8;   // barrier counter and generation, six sweep tile counters
+constexpr int LAT_LEVEL_THREADS = 272;   // CTA width of the persistent level kernel
 cudaError_t launch_lat_level(tde_mesh *m, const BH &bh, const int32_t *ids, int n, int flevel, int tau,
                              const int32_t *glist, int nglist);
 cudaError_t launch_frame_acceleration(tde_mesh *m, const BH &bh, double rho_min, double *out4);

@@ -636,6 +636,22 @@ int lat_build(tde_mesh *m) {
   }
   if (!m->d_sorted) LCK(c, cudaMalloc(&m->d_sorted, sizeof(int32_t) * nb));
   if (!m->d_lat_bar) LCK(c, cudaMalloc(&m->d_lat_bar, LAT_BAR_WORDS * sizeof(unsigned)));
+  if (!m->d_lat_pre) LCK(c, cudaMalloc(&m->d_lat_pre, 2 * sizeof(int32_t) * (nb + 1)));
+  {
+    // the persistent level kernel's work items: chunks of interior cells and of
+    // ghost-map entries, counted per block in factor order (lat_pre is read by
+    // the kernels when they run, so it is written before this call returns)
+    m->h_lat_pre.assign(2 * (size_t)(nb + 1), 0);
+    const int T = LAT_LEVEL_THREADS;
+    for (int q = 0; q < nb; ++q) {
+      const DevBlock &B = m->hblocks[m->h_sorted[q]];
+      const int b = m->h_sorted[q];
+      m->h_lat_pre[q + 1] = m->h_lat_pre[q] + (B.n[0] * B.n[1] * B.n[2] + T - 1) / T;
+      m->h_lat_pre[nb + 1 + q + 1] = m->h_lat_pre[nb + 1 + q] + (m->h_gstart[b + 1] - m->h_gstart[b] + T - 1) / T;
+    }
+    LCK(c, cudaMemcpyAsync(m->d_lat_pre, m->h_lat_pre.data(), sizeof(int32_t) * m->h_lat_pre.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+  }
   if (!m->d_lat_gstart) LCK(c, cudaMalloc(&m->d_lat_gstart, sizeof(int32_t) * (nb + 1)));
   if (!m->d_lat_glist)
     LCK(c, cudaMalloc(&m->d_lat_glist, sizeof(int32_t) * std::max<int64_t>(m->n_gcopy + m->n_amr, 1)));

@@ -35,7 +35,7 @@ namespace tde {
 
 namespace {
 
-constexpr int LM = 8, LNTS = 272, LMINB = 3;   // the sweeps' default tile shape (kTileShapes[0])
+constexpr int LM = 8, LNTS = LAT_LEVEL_THREADS, LMINB = 3;   // the sweeps' default tile shape
 static_assert(kTileShapes[0].M == LM && kTileShapes[0].NTS == LNTS && kTileShapes[0].MINB == LMINB,
               "the level kernel runs the default sweep tile shape");
 
@@ -59,7 +59,8 @@ struct LevelArgs {
   int *status;
   unsigned *bar;             // [0] arrivals, [1] generation, [2 + 3 stage + D] sweep tile counters
   int drop;                  // test hook: CTA 0 skips its first arrival
-  int cpb_pad, cpb_int, cpb_ghost;   // CTA-sized chunks per block of each cell range
+  const int32_t *pre_int;    // [n + 1] prefix sums of the blocks' interior chunks
+  const int32_t *pre_gh;     // [n + 1] prefix sums of their ghost-map chunks
   int tiles[3];              // sweep tiles per block and direction
   size_t mbar_off;           // byte offset of the TMA barrier in shared memory
 };
@@ -70,9 +71,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-// Grid barrier with a bounded wait.  gen counts the barriers this CTA has
-// passed.  Returns false (status set) if the wait expired.
-__device__ __forceinline__ bool grid_barrier(const LevelArgs &a, unsigned &gen, bool arrive) {
+// Grid barrier number idx (0, 1, ... in program order; the generation word
+// counts the completed ones) with a bounded wait.  Returns false (status set)
+// if the wait expired.
+__device__ __forceinline__ bool grid_barrier(const LevelArgs &a, unsigned idx, bool arrive) {
   __shared__ int s_ok;
   // generic-proxy writes of this phase (the primitives) before the sweeps'
   // tensor copies of other CTAs read them
@@ -90,7 +92,7 @@ __device__ __forceinline__ bool grid_barrier(const LevelArgs &a, unsigned &gen, 
     }
     unsigned long long t0, t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    while (ld_acquire(&a.bar[1]) == gen) {
+    while (ld_acquire(&a.bar[1]) <= idx) {
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
       if (t - t0 > 1000000000ull) {
         ok = 0;
@@ -100,7 +102,6 @@ __device__ __forceinline__ bool grid_barrier(const LevelArgs &a, unsigned &gen, 
     }
     __threadfence();
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    gen += 1;
     s_ok = ok;
   }
   __syncthreads();
@@ -112,7 +113,7 @@ __device__ __forceinline__ bool grid_barrier(const LevelArgs &a, unsigned &gen, 
 // excised cells), the next tile's index fetched while the current one runs
 template <int D, int RECON, int EOSK, int DUAL, int LAST>
 __device__ __forceinline__ bool level_sweep(const SweepArgs &s, int n, int tpb, unsigned *ctr, double *sm,
-                                            unsigned long long *mbar, uint32_t &parity) {
+                                            unsigned long long *mbar, uint32_t *s_par) {
   __shared__ unsigned s_item;
   const unsigned items = (unsigned)n * (unsigned)tpb;
   unsigned next = 0;
@@ -123,33 +124,73 @@ __device__ __forceinline__ bool level_sweep(const SweepArgs &s, int n, int tpb, 
     __syncthreads();
     const unsigned k = s_item;
     if (k >= items) return true;
+    // the TMA barrier's phase parity, kept in shared memory (thread 0 flips it
+    // after the tile, past the tile's own barriers)
+    const uint32_t parity = *s_par;
     if (threadIdx.x == 0) next = atomicAdd(ctr, 1u);
     bool staged;
     if (!sweep_tile<D, RECON, EOSK, DUAL, LAST, LM, LNTS>(s, (int)(k / tpb), (int)(k % tpb), sm, mbar, parity,
                                                           staged))
       return false;
-    if (staged) parity ^= 1u;
+    if (staged && threadIdx.x == 0) *s_par = parity ^ 1u;
   }
+}
+
+// The chunks (LNTS consecutive cells or ghost-map entries of one block) of a
+// level's blocks, strided over the CTAs: pre[0 .. n] are their prefix sums over
+// the level's blocks (offset by the earlier levels' chunks).  fn(q, c) runs
+// chunk c of the level's q-th block; q only grows along a CTA's items, so it
+// is found by walking forward.
+template <typename Fn>
+__device__ __forceinline__ void level_chunks(const int32_t *pre, int n, Fn fn) {
+  const int base = pre[0], items = pre[n] - base;
+  int q = 0;
+  for (int k = blockIdx.x; k < items; k += gridDim.x) {
+    while (pre[q + 1] <= base + k) ++q;
+    fn(q, base + k - pre[q]);
+  }
+}
+
+// interior cell e of block B: its flat index (-1 past the interior)
+__device__ __forceinline__ long long interior_flat(const Phys &p, const DevBlock &B, int e) {
+  if (e >= B.n[0] * B.n[1] * B.n[2]) return -1;
+  const int i = e % B.n[0], r = e / B.n[0];
+  const int j = r % B.n[1], k = r / B.n[1];
+  return B.off + ((long long)(k + p.g[2]) * B.p[1] + (j + p.g[1])) * B.p[0] + (i + p.g[0]);
 }
 
 // One RK stage of the level (STAGE a template parameter, so that every access to
 // the kernel's argument block has a constant offset).
 template <int STAGE, int RECON, int EOSK, int DUAL>
 __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsigned long long *mbar,
-                                            uint32_t &parity, unsigned &gen) {
+                                            uint32_t *s_par) {
+  constexpr unsigned B0 = 6 * STAGE;   // this stage's first grid barrier
   constexpr int NVAR = 5 + DUAL;
   constexpr int NWV = (EOSK == EOS_TABLE ? 7 : 5) + DUAL;
   const long long ntot = a.ntot;
   const Phys &p = a.sw[STAGE][0].p;
   double *Udst = STAGE ? a.U1 : a.U;
+  if (STAGE == 0) {
+    // ---- the start states of the level's blocks (the endpoints of the time
+    // interpolation read by faster neighbours later in the window; their
+    // interiors only: no ghost cell of Uold is read) and the step start time
+    level_chunks(a.pre_int, a.n, [&](int q, int c) {
+      const long long flat = interior_flat(p, a.blocks[a.ids[q]], c * LNTS + threadIdx.x);
+      if (flat < 0) return;
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) a.Uold[v * ntot + flat] = a.U[v * ntot + flat];
+    });
+    if (blockIdx.x == 0)
+      for (int q = threadIdx.x; q < a.n; q += LNTS) a.tstart[a.ids[q]] = a.scal[0] + a.tau * a.scal[3];
+  }
   // ---- conserved ghosts from neighbours on other schedules: a faster one's
   // current state, a slower one's state interpolated in time
-  for (long long k = blockIdx.x; k < (long long)a.n * a.cpb_ghost; k += gridDim.x) {
-    const int b = a.ids[k / a.cpb_ghost];
-    const int e = a.gstart[b] + (int)(k % a.cpb_ghost) * LNTS + threadIdx.x;
-    if (e >= a.gstart[b + 1]) continue;
+  level_chunks(a.pre_gh, a.n, [&](int q, int c) {
+    const int b = a.ids[q];
+    const int e = a.gstart[b] + c * LNTS + threadIdx.x;
+    if (e >= a.gstart[b + 1]) return;
     const int fn = a.f[a.gsrcb[e]];
-    if (fn == a.flevel) continue;   // same schedule: its primitives are copied below
+    if (fn == a.flevel) return;   // same schedule: its primitives are copied below
     const int2 mp = reinterpret_cast<const int2 *>(a.gmap)[e];
     if (fn < a.flevel) {
 #pragma unroll
@@ -162,24 +203,20 @@ __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsi
         Udst[v * ntot + mp.x] = o + s * (a.U[v * ntot + mp.y] - o);
       }
     }
-  }
-  if (!grid_barrier(a, gen, true)) return false;
+  });
+  if (!grid_barrier(a, B0, !(STAGE == 0 && a.drop && blockIdx.x == 0))) return false;
   // ---- primitives of the interiors (events counted) and of the converted
   // ghost cells (not counted)
-  for (long long k = blockIdx.x; k < (long long)a.n * a.cpb_int; k += gridDim.x) {
-    const DevBlock B = a.blocks[a.ids[k / a.cpb_int]];
-    const int e = (int)(k % a.cpb_int) * LNTS + threadIdx.x;
-    if (e >= B.n[0] * B.n[1] * B.n[2]) continue;
-    const int i = e % B.n[0], r = e / B.n[0];
-    const int j = r % B.n[1], kk = r / B.n[1];
-    const long long flat = B.off + ((long long)(kk + p.g[2]) * B.p[1] + (j + p.g[1])) * B.p[0] + (i + p.g[0]);
+  level_chunks(a.pre_int, a.n, [&](int q, int c) {
+    const long long flat = interior_flat(p, a.blocks[a.ids[q]], c * LNTS + threadIdx.x);
+    if (flat < 0) return;
     double u[6], w[8];
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) u[v] = Udst[v * ntot + flat];
     cons_to_prim<EOSK, DUAL>(p, u, w, a.cnt);
 #pragma unroll
     for (int v = 0; v < NWV; ++v) a.W[v * ntot + flat] = w[v];
-  }
+  });
   for (int e = blockIdx.x * LNTS + threadIdx.x; e < a.nglist; e += gridDim.x * LNTS) {
     const long long flat = a.glist[e];
     double u[6], w[8];
@@ -189,52 +226,37 @@ __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsi
 #pragma unroll
     for (int v = 0; v < NWV; ++v) a.W[v * ntot + flat] = w[v];
   }
-  if (!grid_barrier(a, gen, true)) return false;
+  if (!grid_barrier(a, B0 + 1, true)) return false;
   // ---- primitive ghosts of neighbours on the same schedule
-  for (long long k = blockIdx.x; k < (long long)a.n * a.cpb_ghost; k += gridDim.x) {
-    const int b = a.ids[k / a.cpb_ghost];
-    const int e = a.gstart[b] + (int)(k % a.cpb_ghost) * LNTS + threadIdx.x;
-    if (e >= a.gstart[b + 1] || a.f[a.gsrcb[e]] != a.flevel) continue;
+  level_chunks(a.pre_gh, a.n, [&](int q, int c) {
+    const int b = a.ids[q];
+    const int e = a.gstart[b] + c * LNTS + threadIdx.x;
+    if (e >= a.gstart[b + 1] || a.f[a.gsrcb[e]] != a.flevel) return;
     const int2 mp = reinterpret_cast<const int2 *>(a.gmap)[e];
 #pragma unroll
     for (int v = 0; v < NWV; ++v) a.W[v * ntot + mp.x] = a.W[v * ntot + mp.y];
-  }
-  if (!grid_barrier(a, gen, true)) return false;
+  });
+  if (!grid_barrier(a, B0 + 2, true)) return false;
   // ---- the sweeps; z completes the stage
   unsigned *ctr = a.bar + 2 + 3 * STAGE;
-  if (!level_sweep<0, RECON, EOSK, DUAL, 0>(a.sw[STAGE][0], a.n, a.tiles[0], ctr, sm, mbar, parity)) return false;
-  if (!grid_barrier(a, gen, true)) return false;
-  if (!level_sweep<1, RECON, EOSK, DUAL, 0>(a.sw[STAGE][1], a.n, a.tiles[1], ctr + 1, sm, mbar, parity))
+  if (!level_sweep<0, RECON, EOSK, DUAL, 0>(a.sw[STAGE][0], a.n, a.tiles[0], ctr, sm, mbar, s_par)) return false;
+  if (!grid_barrier(a, B0 + 3, true)) return false;
+  if (!level_sweep<1, RECON, EOSK, DUAL, 0>(a.sw[STAGE][1], a.n, a.tiles[1], ctr + 1, sm, mbar, s_par))
     return false;
-  if (!grid_barrier(a, gen, true)) return false;
-  return level_sweep<2, RECON, EOSK, DUAL, 1>(a.sw[STAGE][2], a.n, a.tiles[2], ctr + 2, sm, mbar, parity);
+  if (!grid_barrier(a, B0 + 4, true)) return false;
+  return level_sweep<2, RECON, EOSK, DUAL, 1>(a.sw[STAGE][2], a.n, a.tiles[2], ctr + 2, sm, mbar, s_par);
 }
 
 template <int RECON, int EOSK, int DUAL>
 __global__ void __launch_bounds__(LNTS, LMINB) k_lat_level(const LevelArgs a) {
-  constexpr int NVAR = 5 + DUAL;
   extern __shared__ __align__(128) double sm[];
   unsigned long long *mbar = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(sm) + a.mbar_off);
   if (a.sw[0][0].tmap && threadIdx.x == 0) sweep_mbar_init(mbar);   // ordered by the first barrier
-  uint32_t parity = 0;
-  unsigned gen = 0;
-  const long long ntot = a.ntot;
-  // ---- the start states of the level's blocks (read as the endpoints of the
-  // time interpolation by faster neighbours later in the window) and their
-  // step start time
-  for (long long k = blockIdx.x; k < (long long)a.n * a.cpb_pad; k += gridDim.x) {
-    const DevBlock B = a.blocks[a.ids[k / a.cpb_pad]];
-    const int e = (int)(k % a.cpb_pad) * LNTS + threadIdx.x;
-    if (e < B.p[0] * B.p[1] * B.p[2])
-#pragma unroll
-      for (int v = 0; v < NVAR; ++v) a.Uold[v * ntot + B.off + e] = a.U[v * ntot + B.off + e];
-  }
-  if (blockIdx.x == 0)
-    for (int q = threadIdx.x; q < a.n; q += LNTS) a.tstart[a.ids[q]] = a.scal[0] + a.tau * a.scal[3];
-  if (!grid_barrier(a, gen, !(a.drop && blockIdx.x == 0))) return;
-  if (!level_stage<0, RECON, EOSK, DUAL>(a, sm, mbar, parity, gen)) return;
-  if (!grid_barrier(a, gen, true)) return;
-  level_stage<1, RECON, EOSK, DUAL>(a, sm, mbar, parity, gen);
+  __shared__ uint32_t s_par;
+  if (threadIdx.x == 0) s_par = 0;   // ordered by the first barrier
+  if (!level_stage<0, RECON, EOSK, DUAL>(a, sm, mbar, &s_par)) return;
+  if (!grid_barrier(a, 5, true)) return;
+  level_stage<1, RECON, EOSK, DUAL>(a, sm, mbar, &s_par);
 }
 
 template <int RECON, int EOSK, int DUAL>
@@ -307,12 +329,13 @@ cudaError_t launch_lat_level(tde_mesh *m, const BH &bh, const int32_t *ids, int 
   a.status = m->d_status;
   a.bar = m->d_lat_bar;
   a.drop = m->inject_level_drop;
-  int64_t npad = 0;
-  for (const DevBlock &B : m->hblocks) npad = std::max<int64_t>(npad, (int64_t)B.p[0] * B.p[1] * B.p[2]);
-  a.cpb_pad = (int)((npad + LNTS - 1) / LNTS);
-  a.cpb_int = (int)((m->max_interior + LNTS - 1) / LNTS);
-  a.cpb_ghost = std::max(1, (m->max_ghosts + LNTS - 1) / LNTS);
-  int64_t items = std::max<int64_t>((int64_t)n * a.cpb_pad, (nglist + LNTS - 1) / LNTS);
+  // the level's blocks start at sorted position q0; its chunk prefix sums there
+  const int q0 = (int)(ids - m->d_sorted);
+  a.pre_int = m->d_lat_pre + q0;
+  a.pre_gh = m->d_lat_pre + (m->nb + 1) + q0;
+  const int64_t nint = m->h_lat_pre[q0 + n] - m->h_lat_pre[q0];
+  const int64_t ngh = m->h_lat_pre[m->nb + 1 + q0 + n] - m->h_lat_pre[m->nb + 1 + q0];
+  int64_t items = std::max<int64_t>(std::max(nint, ngh), (nglist + LNTS - 1) / LNTS);
   for (int D = 0; D < 3; ++D) {
     const int LA = D == 0 ? 1 : 0, OA = D == 2 ? 1 : 2;
     a.tiles[D] = ((m->nmax[LA] + LM - 1) / LM) * m->nmax[OA];
