@@ -398,7 +398,7 @@ KERNELS_AS_CAPTURED = False
 FP64_FLOP_PER_CELL_C5 = {"sweep_x": 345.3, "sweep_y": 315.9, "sweep_z": 445.7}
 FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 300.7, "sweep_y": 275.5, "sweep_z": 367.3}
 DRAM_BYTES_C5 = {"sweep_x": 10.91e9, "sweep_y": 15.29e9, "sweep_z": 21.10e9}
-KERNELS_AS_CAPTURED_C5 = True
+KERNELS_AS_CAPTURED_C5 = False
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 

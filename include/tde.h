@@ -401,8 +401,8 @@ typedef struct {
  * Limit: 1 <= nblocks <= 4096, else TDE_EINVAL; each block is checked as by
  * tde_mesh_create (edges of 1..32 cells, one cell across an inactive direction,
  * inside its level's grid).  The first call on a device looks up the arrays'
- * device addresses and copies the tables into the second, so it should come
- * before any stream capture.  All calls share the scratch array: calls whose
+ * device addresses and copies the tables into the second (a synchronous copy).
+ * All calls share the scratch array: calls whose
  * GPU work overlaps race.  The block list is read from host memory during the
  * call.  Uses ctx's stream; asynchronous. */
 TDE_API int tde_compute_dt_noalloc(tde_ctx *ctx, int nblocks, const tde_block_desc *blocks,

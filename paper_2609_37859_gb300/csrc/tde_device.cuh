@@ -34,6 +34,11 @@ __device__ __forceinline__ long long dkey(double x) {
   const long long b = dbits(x);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
+// the same with -0 and +0 equal (the IEEE order of non-NaN values)
+__device__ __forceinline__ long long dkey0(double x) {
+  const long long k = dkey(x);
+  return k < 0 ? k + 1 : k;
+}
 __device__ __forceinline__ bool dgt0(double x) { return dbits(x) > 0; }          // x > 0
 __device__ __forceinline__ bool dge0(double x) { return dkey(x) >= -1; }         // x >= 0 (incl. -0)
 __device__ __forceinline__ bool dle0(double x) { return dkey(x) <= 0; }          // x <= 0 (incl. +0)
@@ -514,17 +519,29 @@ __device__ __forceinline__ double ppm_iface(double qm1, double q0, double q1, do
   return dmin(dmax(a, lo), hi);
 }
 
-// Colella-Woodward (1984) monotonicity constraints on the parabola (aL, q0, aR)
+// Colella-Woodward (1984) monotonicity constraints on the parabola (aL, q0, aR).
+// The textbook tests (aR - q0)(q0 - aL) <= 0, da^2 < da q6 and da q6 < -da^2
+// (da = aR - aL, q6 = 6 (q0 - (aL + aR) / 2)) are taken in equivalent forms that
+// need no FP64 product: q0 not strictly between aL and aR; aL on the far side of
+// 3 q0 - 2 aR; aR on the far side of 3 q0 - 2 aL ("far" along the sign of da,
+// by which the textbook inequalities divide).  The comparisons run on the
+// integer pipe; the forms agree with the products except within rounding of a
+// tie, where both branches give the same interface value up to rounding (at the
+// tie of the second test 3 q0 - 2 aR equals aL), and for products that
+// underflow.  Three FP64 operations per variable and cell instead of about ten.
 __device__ __forceinline__ void ppm_limit(double q0, double &aL, double &aR) {
-  if (dle0((aR - q0) * (q0 - aL))) {
+  const long long kL = dkey0(aL), kR = dkey0(aR), kq = dkey0(q0);
+  const bool up = kL < kR;
+  if (up ? !(kL < kq && kq < kR) : !(kR < kq && kq < kL)) {
     aL = q0;
     aR = q0;
-  } else {
-    double da = aR - aL;
-    double q6 = 6.0 * (q0 - 0.5 * (aL + aR));
-    if (dlt(da * da, da * q6)) aL = 3.0 * q0 - 2.0 * aR;
-    else if (dlt(da * q6, -(da * da))) aR = 3.0 * q0 - 2.0 * aL;
+    return;
   }
+  const double t3 = 3.0 * q0;
+  const double nL = fma(-2.0, aR, t3), nR = fma(-2.0, aL, t3);
+  const long long knL = dkey0(nL), knR = dkey0(nR);
+  if (up ? kL < knL : knL < kL) aL = nL;
+  else if (up ? knR < kR : kR < knR) aR = nR;
 }
 
 // ------------------------------------------------------------------ HLLC ----
