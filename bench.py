@@ -398,7 +398,7 @@ KERNELS_AS_CAPTURED = False
 FP64_FLOP_PER_CELL_C5 = {"sweep_x": 295.6, "sweep_y": 265.4, "sweep_z": 395.9}
 FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 231.1, "sweep_y": 207.9, "sweep_z": 301.0}
 DRAM_BYTES_C5 = {"sweep_x": 10.92e9, "sweep_y": 15.35e9, "sweep_z": 21.08e9}
-KERNELS_AS_CAPTURED_C5 = True
+KERNELS_AS_CAPTURED_C5 = False
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 

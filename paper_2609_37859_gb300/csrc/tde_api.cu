@@ -402,7 +402,7 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   m->hoff[nblocks] = off;
   m->ntot = off;
   if (off >= (int64_t)INT32_MAX) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: more than 2^31 padded cells"); }
-  if (sweep_smem_max(m) > 227 * 1024) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: block too large for one sweep tile"); }
+  if (sweep_smem_max(m) > SWEEP_SMEM_LIMIT) { delete m; return fail(ctx, TDE_EINVAL, "tde_mesh_create: block too large for one sweep tile"); }
 
   // owner map of the finest level's grid, one entry per cube of unit cells that
   // every block edge lies on
@@ -887,7 +887,7 @@ extern "C" int tde_mesh_set_tiles(tde_mesh *m, const int32_t *tiles) {
   if (!m) return TDE_EINVAL;
   if (!tiles) return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_tiles: null");
   for (int D = 0; D < 3; ++D)
-    if (tiles[D] < 0 || tiles[D] >= N_SWEEP_SHAPES || sweep_smem_for(m, D, tiles[D]) > 227 * 1024)
+    if (tiles[D] < 0 || tiles[D] >= N_SWEEP_SHAPES || sweep_smem_for(m, D, tiles[D]) > SWEEP_SMEM_LIMIT)
       return fail(m->ctx, TDE_EINVAL, "tde_mesh_set_tiles: unknown shape or tile too large");
   for (int D = 0; D < 3; ++D) m->tile[D] = tiles[D];
   invalidate_graph(m);

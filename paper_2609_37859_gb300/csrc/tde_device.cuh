@@ -280,6 +280,25 @@ __device__ __forceinline__ bool inside_radius(double r2, double r) {
   return dlt(sqrt(r2), r);
 }
 
+// Squared distance of a cell centre from the point mass, in one fixed order of
+// roundings for every kernel (a cell's potential and excision flag then agree
+// wherever they are evaluated); d0 enters last, so the two transverse terms of
+// an x pencil can be summed once per pencil.
+__device__ __forceinline__ double bh_r2_yz(double d1, double d2) { return fma(d1, d1, d2 * d2); }
+__device__ __forceinline__ double bh_r2(double d0, double d1, double d2) { return fma(d0, d0, bh_r2_yz(d1, d2)); }
+
+// The square of the point mass's time-step limit (the CFL condition with the
+// point mass, Sec. 7.1): dt_g^2 = dx / |g| with |g| = GM r / (r^2 + r_s^2)^(3/2),
+// written as (dx / GM) s2^2 / (sqrt(s2) r) with s2 = r^2 + r_s^2 from refined
+// reciprocals (a few ulps); infinity where there is no limit (GM <= 0, r = 0).
+// Its square root is taken once per block, after the minimum (the square root
+// is monotonic, so the minimum of the roots is the root of the minimum).
+__device__ __forceinline__ double bh_dt2(double dx, double GM, double r2, double rs2) {
+  if (!dgt0(GM) || !dgt0(r2)) return INFINITY;
+  const double s2 = r2 + rs2;
+  return dx * rcp_nr(GM) * (s2 * s2) * (rsqrt_nr(s2) * rsqrt_nr(r2));
+}
+
 // ---------------------------------------------------------------- EOS ----
 
 // floor(x) for 0 <= x < 2^31 (also -0) from the bit fields, on the integer pipe

@@ -28,18 +28,42 @@ namespace tde {
 
 constexpr int NT = 256;   // threads per CTA
 
-__device__ __forceinline__ double block_min(double v) {
-  __shared__ double red[NT / 32];
+// minima of a and b over the CTA (valid in thread 0)
+__device__ __forceinline__ void block_min2(double &a, double &b) {
+  __shared__ double red[2][NT / 32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    v = threadIdx.x < NT / 32 ? red[threadIdx.x] : INFINITY;
+    a = threadIdx.x < NT / 32 ? red[0][threadIdx.x] : INFINITY;
+    b = threadIdx.x < NT / 32 ? red[1][threadIdx.x] : INFINITY;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
   }
-  return v;
+}
+
+// the point mass's position at time t, evaluated by one warp for the CTA
+__device__ __forceinline__ void cta_bh_pos(const BH &bh, double t, double rb[3]) {
+  __shared__ double s_rb[3];
+  if (threadIdx.x < 32) {
+    double r[3];
+    bh_pos(bh, t, r);
+    if (threadIdx.x < 3) s_rb[threadIdx.x] = r[threadIdx.x];
+  }
+  __syncthreads();
+  rb[0] = s_rb[0];
+  rb[1] = s_rb[1];
+  rb[2] = s_rb[2];
 }
 
 // ------------------------------------------------------------ k_c2p ----
@@ -56,7 +80,10 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
   const int nint = B.n[0] * B.n[1] * B.n[2];
   const int e = blockIdx.x * NT + threadIdx.x;
   if (blockIdx.x * NT >= nint) return;   // whole CTA past this block (uniform)
-  double best = INFINITY;
+  double best = INFINITY, best_g2 = INFINITY;   // the hydro limit; the point mass's, squared
+  double rb[3];
+  const bool near = want_dt && (bh.on || bh.excise);   // uniform over the CTA
+  if (near) cta_bh_pos(bh, ta_t(ta, b), rb);
   if (e < nint) {
     const int i = e % B.n[0], r = e / B.n[0];
     const int j = r % B.n[1], k = r / B.n[1];
@@ -71,15 +98,12 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
     for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
     if (want_dt) {
       bool skip = false;
-      double x[3], rb[3], d[3];
-      const double tb = ta_t(ta, b);
-      if (bh.on || bh.excise) {
-        cell_centre(p, B, c, x);
-        bh_pos(bh, tb, rb);
-        d[0] = x[0] - rb[0]; d[1] = x[1] - rb[1]; d[2] = x[2] - rb[2];
-      }
       double r2 = 0.0;
-      if (bh.on || bh.excise) r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (near) {
+        double x[3];
+        cell_centre(p, B, c, x);
+        r2 = bh_r2(x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]);
+      }
       if (bh.excise && inside_radius(r2, bh.rexc)) skip = true;
       if (!skip) {
         const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
@@ -90,18 +114,16 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         for (int a = 0; a < 3; ++a)
           if (p.active[a]) rate = dmax(rate, (fabs(w[1 + a]) + cs) * block_idx(p, B, a));
         best = dmin(best, rcp_nr(rate));
-        if (bh.on) {
-          double s2 = r2 + bh.rs2;
-          double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-          if (dgt0(gmag)) best = dmin(best, sqrt(scale2i(p.dxmin, -B.level) / gmag));
-        }
+        if (bh.on) best_g2 = bh_dt2(scale2i(p.dxmin, -B.level), bh.GM, r2, bh.rs2);
       }
     }
   }
   if (want_dt) {
-    best = block_min(best);
-    if (threadIdx.x == 0)
+    block_min2(best, best_g2);
+    if (threadIdx.x == 0) {
+      best = dmin(best, sqrt(best_g2));
       atomicMin(dtbits + b, (unsigned long long)__double_as_longlong(best));
+    }
   }
 }
 
@@ -248,30 +270,58 @@ __global__ void __launch_bounds__(NT) k_ghost(const int32_t *__restrict__ map,
 
 // ---------------------------------------------------- excision, resync ----
 
+// Excision reset of the interior cells within r_exc of the point mass.  A CTA
+// covers a slice of one block; one warp first tests the block's box of cell
+// centres against the sphere (with a margin of 2^-20 on r_exc^2, far above the
+// roundings of the centres and of r^2), and a block entirely outside it is
+// skipped, so the per-cell test (which decides as before) runs only near the
+// point mass.
 __global__ void __launch_bounds__(NT) k_excise(Phys p, BH bh, TimeArgs ta,
                                                const DevBlock *__restrict__ blocks,
                                                const int32_t *__restrict__ ids, double *U,
                                                long long ntot, Counters *cnt) {
+  __shared__ int s_far;
+  __shared__ double s_rb[3];
   const int b = ids[blockIdx.y];
   const DevBlock B = blocks[b];
   const int nint = B.n[0] * B.n[1] * B.n[2];
-  const int e = blockIdx.x * NT + threadIdx.x;
-  if (e >= nint) return;
-  const int i = e % B.n[0], r = e / B.n[0];
-  const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
-  double x[3], rb[3];
-  cell_centre(p, B, c, x);
-  bh_pos(bh, ta_t(ta, b) + ta_dt(ta, b), rb);
-  const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
-  if (!inside_radius(d0 * d0 + d1 * d1 + d2 * d2, bh.rexc)) return;
-  const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
-  U[flat] = p.rho_floor;
-  U[ntot + flat] = 0.0;
-  U[2 * ntot + flat] = 0.0;
-  U[3 * ntot + flat] = 0.0;
-  U[4 * ntot + flat] = p.u_floor;
-  if (p.dual) U[5 * ntot + flat] = p.u_floor;
-  count(&cnt->excised);
+  if ((int)blockIdx.x * NT >= nint) return;   // uniform over the CTA
+  if (threadIdx.x < 32) {
+    double rb[3];
+    bh_pos(bh, ta_t(ta, b) + ta_dt(ta, b), rb);
+    // nearest point of the box of interior cell centres, per direction
+    const int a = threadIdx.x < 3 ? threadIdx.x : 0;
+    const double lo = cell_coord(p, B, a, p.g[a]), hi = cell_coord(p, B, a, p.g[a] + B.n[a] - 1);
+    const double da = dlt(rb[a], lo) ? lo - rb[a] : (dlt(hi, rb[a]) ? rb[a] - hi : 0.0);
+    const double q = threadIdx.x < 3 ? da * da : 0.0;
+    const double d2 = __shfl_sync(0xffffffffu, q, 0) + __shfl_sync(0xffffffffu, q, 1) +
+                      __shfl_sync(0xffffffffu, q, 2);
+    if (threadIdx.x == 0) {
+      // (interior cell centres never wrap, so no periodic image enters either test)
+      s_far = dlt(bh.rexc * bh.rexc * (1.0 + 0x1p-20), d2);
+      s_rb[0] = rb[0];
+      s_rb[1] = rb[1];
+      s_rb[2] = rb[2];
+    }
+  }
+  __syncthreads();
+  if (s_far) return;
+  const double rb[3] = {s_rb[0], s_rb[1], s_rb[2]};
+  for (int e = blockIdx.x * NT + threadIdx.x; e < nint; e += gridDim.x * NT) {
+    const int i = e % B.n[0], r = e / B.n[0];
+    const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
+    double x[3];
+    cell_centre(p, B, c, x);
+    if (!inside_radius(bh_r2(x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]), bh.rexc)) continue;
+    const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
+    U[flat] = p.rho_floor;
+    U[ntot + flat] = 0.0;
+    U[2 * ntot + flat] = 0.0;
+    U[3 * ntot + flat] = 0.0;
+    U[4 * ntot + flat] = p.u_floor;
+    if (p.dual) U[5 * ntot + flat] = p.u_floor;
+    count(&cnt->excised);
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_sync(Phys p, const DevBlock *__restrict__ blocks,
@@ -420,7 +470,7 @@ __global__ void __launch_bounds__(NT) k_frame_partial(Phys p, BH bh, const doubl
     double x[3];
     cell_centre(p, B, c, x);
     const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
-    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const double r2 = bh_r2(d0, d1, d2);
     if (bh.excise && inside_radius(r2, bh.rexc)) continue;
     const double q2 = r2 + bh.rs2;
     const double gfac = -bh.GM / (q2 * sqrt(q2));   // g = -grad Phi_bh = -GM d / q^3
@@ -853,7 +903,7 @@ cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3]
     for (int t = 0; t < N_TILE_SHAPES; ++t) ms_out[D][t] = -1.f;
     if (!m->phys.active[D]) continue;
     for (int t = 0; t < N_TILE_SHAPES && err == cudaSuccess; ++t) {
-      if (sweep_smem_for(m, D, t) > 227 * 1024) continue;
+      if (sweep_smem_for(m, D, t) > SWEEP_SMEM_LIMIT) continue;
       SweepArgs a = sweep_args(m, 0, m->U, m->U, Uo, m->d_allids, bh, ta, nullptr);
       a.dU = dU;
       a.cnt = nullptr;
@@ -887,7 +937,7 @@ cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3]
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta) {
   ProfScope _ps(m->ctx, TDE_K_EXCISE);
-  dim3 grid((unsigned)((m->max_interior + NT - 1) / NT), (unsigned)nblk);
+  dim3 grid((unsigned)std::min<int64_t>((m->max_interior + NT - 1) / NT, 8), (unsigned)nblk);
   k_excise<<<grid, NT, 0, m->ctx->stream>>>(m->phys, bh, ta, m->d_blocks, ids, U,
                                              (long long)m->ntot, m->d_cnt);
   return cudaGetLastError();

@@ -224,6 +224,9 @@ size_t sweep_smem_max(const tde_mesh *m);
 cudaError_t build_sweep_tmaps(tde_mesh *m);
 size_t sweep_smem_for(const tde_mesh *m, int D, int shape);
 constexpr int N_SWEEP_SHAPES = 3;
+// the largest dynamic shared memory of a sweep tile: 227 KB less a reserve for
+// the sweep kernels' static shared memory (a few hundred bytes)
+constexpr size_t SWEEP_SMEM_LIMIT = 227 * 1024 - 1024;
 cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3][N_SWEEP_SHAPES]);
 void invalidate_graph(tde_mesh *m);
 // the persistent form of a LAT level sub-step (tde_lat_level.cu): whether the

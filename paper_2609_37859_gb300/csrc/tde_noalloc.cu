@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
   const int nint = n[0] * n[1] * n[2];
   if ((int)blockIdx.x * NA_NT >= nint) return;   // uniform over the CTA
   const int e = blockIdx.x * NA_NT + threadIdx.x;
-  double best = INFINITY;
+  double best = INFINITY, best_g2 = INFINITY;   // the hydro limit; the point mass's, squared
   if (e < nint) {
     const int i = e % n[0], r = e / n[0];
     const int c[3] = {i + p.g[0], r % n[1] + p.g[1], r / n[1] + p.g[2]};
@@ -103,8 +103,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
         x[a] = p.xmin[a] + (g + 0.5) * (p.active[a] ? scale2i(p.dx[a], -d.level) : p.dx[a]);
       }
       na_bh_pos(bh, t_block ? t_block[b] : 0.0, rb);
-      const double d0 = x[0] - rb[0], d1 = x[1] - rb[1], d2 = x[2] - rb[2];
-      r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      r2 = bh_r2(x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]);
       if (bh.excise && inside_radius(r2, bh.rexc)) skip = true;
     }
     if (!skip) {
@@ -117,23 +116,32 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
         if (p.active[a])
           rate = dmax(rate, (fabs(w[1 + a]) + cs) * scale2i(p.idx[a], d.level));
       best = dmin(best, rcp_nr(rate));
-      if (bh.on) {
-        const double s2 = r2 + bh.rs2;
-        const double gmag = bh.GM * sqrt(r2) / (s2 * sqrt(s2));
-        if (dgt0(gmag)) best = dmin(best, sqrt(scale2i(p.dxmin, -d.level) / gmag));
-      }
+      if (bh.on) best_g2 = bh_dt2(scale2i(p.dxmin, -d.level), bh.GM, r2, bh.rs2);
     }
   }
-  __shared__ double red[NA_NT / 32];
+  __shared__ double red[2][NA_NT / 32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  for (int o = 16; o > 0; o >>= 1) {
+    best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    best_g2 = fmin(best_g2, __shfl_xor_sync(0xffffffffu, best_g2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = best;
+    red[1][threadIdx.x >> 5] = best_g2;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    best = threadIdx.x < NA_NT / 32 ? red[threadIdx.x] : INFINITY;
+    best = threadIdx.x < NA_NT / 32 ? red[0][threadIdx.x] : INFINITY;
+    best_g2 = threadIdx.x < NA_NT / 32 ? red[1][threadIdx.x] : INFINITY;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (threadIdx.x == 0) atomicMin(S->minbits + b, (unsigned long long)__double_as_longlong(best));
+    for (int o = 16; o > 0; o >>= 1) {
+      best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+      best_g2 = fmin(best_g2, __shfl_xor_sync(0xffffffffu, best_g2, o));
+    }
+    if (threadIdx.x == 0) {
+      best = dmin(best, sqrt(best_g2));
+      atomicMin(S->minbits + b, (unsigned long long)__double_as_longlong(best));
+    }
   }
 }
 

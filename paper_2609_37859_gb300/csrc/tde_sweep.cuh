@@ -24,20 +24,24 @@ __device__ __forceinline__ void bh_pos(const BH &bh, double t, double r[3]) {
   for (int a = 0; a < 3; ++a) r[a] = bh.x0[a] + bh.v0[a] * s + 0.5 * bh.a0[a] * s * s;
 }
 
-// centre of padded cell c[] of block B; periodic directions wrap to the image
+// coordinate along direction a of padded cell index c of block B; periodic
+// directions wrap to the image
+__device__ __forceinline__ double cell_coord(const Phys &p, const DevBlock &B, int a, int c) {
+  const int o = a == 0 ? B.i0 : (a == 1 ? B.j0 : B.k0);
+  int g = o + c - p.g[a];
+  if (p.bc[a] == 1) {
+    const int N = level_n(p, a, B.level);
+    g %= N;
+    if (g < 0) g += N;
+  }
+  return p.xmin[a] + (g + 0.5) * block_dx(p, B, a);
+}
+
+// centre of padded cell c[] of block B
 __device__ __forceinline__ void cell_centre(const Phys &p, const DevBlock &B, const int c[3],
                                             double x[3]) {
-  const int o[3] = {B.i0, B.j0, B.k0};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int g = o[a] + c[a] - p.g[a];
-    if (p.bc[a] == 1) {
-      const int N = level_n(p, a, B.level);
-      g %= N;
-      if (g < 0) g += N;
-    }
-    x[a] = p.xmin[a] + (g + 0.5) * block_dx(p, B, a);
-  }
+  for (int a = 0; a < 3; ++a) x[a] = cell_coord(p, B, a, c[a]);
 }
 
 // ---------------------------------------------------------- k_sweep ----
@@ -222,9 +226,21 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs &a, int qb, int tile,
   }
   const bool grav = a.bh.on || a.phi_sg, exc = a.bh.excise;
   if (grav || exc) {
-    const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
-    double rb[3];
-    bh_pos(a.bh, ts, rb);
+    // one warp evaluates the point mass's position at the stage time and, for
+    // an x pencil, the transverse part of each lane's squared distance (the
+    // FP64 pipe charges a warp instruction whatever its active lanes)
+    __shared__ double s_rb[3], s_yz[M];
+    if (threadIdx.x < 32) {
+      const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
+      double rb[3];
+      bh_pos(a.bh, ts, rb);
+      if (threadIdx.x < 3) s_rb[threadIdx.x] = rb[threadIdx.x];
+      if (D == 0 && threadIdx.x < M)
+        s_yz[threadIdx.x] = bh_r2_yz(cell_coord(p, B, 1, p.g[1] + l0 + threadIdx.x) - rb[1],
+                                     cell_coord(p, B, 2, p.g[2] + o) - rb[2]);
+    }
+    __syncthreads();
+    const double rb0 = s_rb[0], rb1 = s_rb[1], rb2 = s_rb[2];
     const bool cached = a.phic != nullptr;
     for (int e = threadIdx.x; e < (nd + 2) * M; e += NTS) {
       int c, lane;
@@ -238,14 +254,19 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs &a, int qb, int tile,
         if (exc) Ex[idx] = a.exc_c[cflat];
         continue;
       }
-      int cc[3];
-      cc[D] = g - 1 + c;
-      cc[LA] = p.g[LA] + l0 + lane;
-      cc[OA] = p.g[OA] + o;
-      double x[3];
-      cell_centre(p, B, cc, x);
-      const double dx0 = x[0] - rb[0], dx1 = x[1] - rb[1], dx2 = x[2] - rb[2];
-      const double r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
+      double r2;
+      if (D == 0) {
+        const double d0 = cell_coord(p, B, 0, g - 1 + c) - rb0;
+        r2 = fma(d0, d0, s_yz[lane]);   // = bh_r2
+      } else {
+        int cc[3];
+        cc[D] = g - 1 + c;
+        cc[LA] = p.g[LA] + l0 + lane;
+        cc[OA] = p.g[OA] + o;
+        double x[3];
+        cell_centre(p, B, cc, x);
+        r2 = bh_r2(x[0] - rb0, x[1] - rb1, x[2] - rb2);
+      }
       if (grav) {
         double ph = a.bh.on ? -a.bh.GM * rsqrt_nr(r2 + a.bh.rs2) : 0.0;
         if (a.phi_sg) ph += a.phi_sg[cflat];   // Phi_bh + Phi_sg
@@ -492,17 +513,13 @@ __global__ void __launch_bounds__(NTS, MINB) k_sweep(const SweepArgs a) {
 
 template <int D, int RECON, int EOSK, int DUAL, int M, int NTS, int MINB>
 cudaError_t sweep_one(const SweepArgs &a, bool last, dim3 grid, size_t smem, cudaStream_t s) {
-  // the dynamic shared-memory limit is a per-function attribute (set on every
-  // launch: cheap, and correct on whichever device is current)
-  if (last) {
-    auto k = k_sweep<D, RECON, EOSK, DUAL, 1, M, NTS, MINB>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    k<<<grid, NTS, smem, s>>>(a);
-  } else {
-    auto k = k_sweep<D, RECON, EOSK, DUAL, 0, M, NTS, MINB>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    k<<<grid, NTS, smem, s>>>(a);
-  }
+  // the dynamic shared-memory limit is a per-function attribute (set to this
+  // launch's size on every launch: cheap, and correct on whichever device is
+  // current; the kernel's static shared memory counts against the same 227 KB)
+  auto k = last ? k_sweep<D, RECON, EOSK, DUAL, 1, M, NTS, MINB> : k_sweep<D, RECON, EOSK, DUAL, 0, M, NTS, MINB>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k<<<grid, NTS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
