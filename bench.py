@@ -402,7 +402,7 @@ KERNELS_AS_CAPTURED_C5 = False
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 
-SHAPE_NAMES = ("8 lanes x 272 threads", "16 lanes x 288 threads", "4 lanes x 160 threads")
+SHAPE_NAMES = ("8 lanes x 288 threads", "16 lanes x 288 threads", "4 lanes x 160 threads")
 
 
 def autotune_report(tiles, ms):

@@ -234,7 +234,7 @@ void invalidate_graph(tde_mesh *m);
 // level's nglist converted ghost cells) as one launch
 bool lat_level_eligible(const tde_mesh *m);
 constexpr int LAT_BAR_WORDS = 8;   // barrier counter and generation, six sweep tile counters
-constexpr int LAT_LEVEL_THREADS = 272;   // CTA width of the persistent level kernel
+constexpr int LAT_LEVEL_THREADS = 288;   // CTA width of the persistent level kernel
 cudaError_t launch_lat_level(tde_mesh *m, const BH &bh, const int32_t *ids, int n, int flevel, int tau,
                              const int32_t *glist, int nglist);
 cudaError_t launch_frame_acceleration(tde_mesh *m, const BH &bh, double rho_min, double *out4);

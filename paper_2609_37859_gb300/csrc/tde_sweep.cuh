@@ -80,9 +80,10 @@ struct SweepArgs {
 };
 
 // A sweep tile is M pencils (lanes) of one block along D; its CTA has NTS
-// threads.  NTS = (n + 2) M for pencils of n cells makes phases B (n + 2 cells),
-// C (n + 1 faces) and D (n cells) each a single pass, so no warp waits at a
-// barrier for another warp's second pass.  The shapes offered (tile_shapes)
+// threads.  NTS >= (n + 3) M for pencils of n cells makes every phase (the n + 3
+// PPM interfaces, n + 2 cells, n + 1 faces, n cells) a single pass, so no warp
+// waits at a barrier for another warp's second pass; for n = 32 and M = 8 that
+// is 280 threads, and 288 (nine whole warps) costs no more warps or registers.  The shapes offered (tile_shapes)
 // are chosen per direction by tde_mesh_autotune; every shape computes the same
 // operations on the same data, so results do not depend on the choice.
 template <int D>
@@ -558,7 +559,7 @@ struct TileShape {
   int M, NTS, MINB;
 };
 constexpr int N_TILE_SHAPES = N_SWEEP_SHAPES;
-constexpr TileShape kTileShapes[N_TILE_SHAPES] = {{8, 272, 3}, {16, 288, 3}, {4, 160, 5}};
+constexpr TileShape kTileShapes[N_TILE_SHAPES] = {{8, 288, 3}, {16, 288, 3}, {4, 160, 5}};
 
 cudaError_t sweep_launch_m8(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t sweep_launch_m16(const SweepArgs &a, int D, bool last, dim3 grid, size_t smem, cudaStream_t s);
