@@ -395,10 +395,10 @@ KERNELS_AS_CAPTURED = False
 # too much for a multi-pass capture), two launches of each sweep averaged,
 # DRAM bytes scaled to the full mesh by its cells (x 8); a one-pass capture of
 # the full mesh gives the same FP64 slots per cell within 2 %.
-FP64_FLOP_PER_CELL_C5 = {"sweep_x": 295.6, "sweep_y": 265.4, "sweep_z": 395.9}
-FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 231.1, "sweep_y": 207.9, "sweep_z": 301.0}
-DRAM_BYTES_C5 = {"sweep_x": 10.92e9, "sweep_y": 15.35e9, "sweep_z": 21.08e9}
-KERNELS_AS_CAPTURED_C5 = False
+FP64_FLOP_PER_CELL_C5 = {"sweep_x": 265.5, "sweep_y": 246.6, "sweep_z": 377.1}
+FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 203.1, "sweep_y": 189.9, "sweep_z": 283.0}
+DRAM_BYTES_C5 = {"sweep_x": 11.00e9, "sweep_y": 15.49e9, "sweep_z": 21.30e9}
+KERNELS_AS_CAPTURED_C5 = True
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 
