@@ -398,7 +398,7 @@ KERNELS_AS_CAPTURED = False
 FP64_FLOP_PER_CELL_C5 = {"sweep_x": 265.5, "sweep_y": 246.6, "sweep_z": 377.1}
 FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 203.1, "sweep_y": 189.9, "sweep_z": 283.0}
 DRAM_BYTES_C5 = {"sweep_x": 11.00e9, "sweep_y": 15.49e9, "sweep_z": 21.30e9}
-KERNELS_AS_CAPTURED_C5 = True
+KERNELS_AS_CAPTURED_C5 = False
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 

@@ -580,18 +580,17 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   const int t1 = D == 0 ? 1 : 0, t2 = D == 2 ? 1 : 2;
   double ul = L.v[D], ur = R.v[D];
   double cl = sqrt_ratio(L.g1 * L.P, L.r), cr = sqrt_ratio(R.g1 * R.P, R.r);
-  double Ul = EOSK == EOS_IDEAL ? L.P * p.inv_gm1 : L.P * rcp_nr(L.ge - 1.0);
-  double Ur = EOSK == EOS_IDEAL ? R.P * p.inv_gm1 : R.P * rcp_nr(R.ge - 1.0);
-  double El = Ul + 0.5 * L.r * (L.v[0] * L.v[0] + L.v[1] * L.v[1] + L.v[2] * L.v[2]);
-  double Er = Ur + 0.5 * R.r * (R.v[0] * R.v[0] + R.v[1] * R.v[1] + R.v[2] * R.v[2]);
   double SL = dmin(ul - cl, ur - cr);
   double SR = dmax(ul + cl, ur + cr);
   double al = L.r * (SL - ul), ar = R.r * (SR - ur);
   double SM = (R.P - L.P + al * ul - ar * ur) * rcp_nr(al - ar);
   bool supL = dge0(SL), supR = dle0(SR);
   bool useL = supL || (!supR && dge0(SM));
-  // chosen side K
-  double r = useL ? L.r : R.r, un = useL ? ul : ur, P = useL ? L.P : R.P, E = useL ? El : Er;
+  // chosen side K; its total energy only (the other side's enters no flux)
+  double r = useL ? L.r : R.r, un = useL ? ul : ur, P = useL ? L.P : R.P;
+  const double vK0 = useL ? L.v[0] : R.v[0], vK1 = useL ? L.v[1] : R.v[1], vK2 = useL ? L.v[2] : R.v[2];
+  const double UK = EOSK == EOS_IDEAL ? P * p.inv_gm1 : P * rcp_nr((useL ? L.ge : R.ge) - 1.0);
+  double E = UK + 0.5 * r * (vK0 * vK0 + vK1 * vK1 + vK2 * vK2);
   double vt1 = useL ? L.v[t1] : R.v[t1], vt2 = useL ? L.v[t2] : R.v[t2];
   double S = useL ? SL : SR;
   double Seff = (supL || supR) ? 0.0 : S;
