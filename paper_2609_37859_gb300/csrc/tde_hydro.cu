@@ -256,6 +256,10 @@ __global__ void __launch_bounds__(1024) k_dt_finalize(int nb, double cfl,
 
 // ---------------------------------------------------------- k_ghost ----
 
+// nf <= GHOST_NF_MAX fields per cell; every field of a cell is loaded before any
+// is stored (the sources are interior cells, the destinations ghost cells, so
+// they never overlap), which lets the loads of a cell overlap in flight
+constexpr int GHOST_NF_MAX = 8;
 __global__ void __launch_bounds__(NT) k_ghost(const int32_t *__restrict__ map,
                                               const int32_t *__restrict__ gstart,
                                               const int32_t *__restrict__ ids, double *f, int nf,
@@ -264,7 +268,13 @@ __global__ void __launch_bounds__(NT) k_ghost(const int32_t *__restrict__ map,
   const int s0 = gstart[b], s1 = gstart[b + 1];
   for (int e = s0 + blockIdx.x * NT + threadIdx.x; e < s1; e += gridDim.x * NT) {
     const int2 m = reinterpret_cast<const int2 *>(map)[e];
-    for (int v = 0; v < nf; ++v) f[v * ntot + m.x] = f[v * ntot + m.y];
+    double t[GHOST_NF_MAX];
+#pragma unroll
+    for (int v = 0; v < GHOST_NF_MAX; ++v)
+      if (v < nf) t[v] = f[v * ntot + m.y];
+#pragma unroll
+    for (int v = 0; v < GHOST_NF_MAX; ++v)
+      if (v < nf) f[v * ntot + m.x] = t[v];
   }
 }
 
@@ -679,6 +689,7 @@ cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double
 
 cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids) {
   if (m->max_ghosts == 0) return cudaSuccess;
+  if (nf < 1 || nf > GHOST_NF_MAX) return cudaErrorInvalidValue;
   ProfScope _ps(m->ctx, TDE_K_GHOST);
   unsigned gx = (unsigned)min((m->max_ghosts + NT - 1) / NT, 64);
   k_ghost<<<dim3(gx, (unsigned)nblk), NT, 0, m->ctx->stream>>>(m->d_ghost, m->d_gstart, ids, field,

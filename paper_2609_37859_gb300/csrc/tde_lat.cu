@@ -181,13 +181,27 @@ __global__ void __launch_bounds__(LNT) k_ghost_lat(const int32_t *__restrict__ m
       // same schedule: the primitives are copied instead (k_ghost_w_lat), and
       // nothing after reads a conserved ghost value
     } else if (fn < flevel) {
-      for (int v = 0; v < nvar; ++v) Udst[v * ntot + mp.x] = Ucur[v * ntot + mp.y];
+      // every field loaded before any is stored (sources are interior cells,
+      // destinations ghost cells), so the loads overlap in flight
+      double t[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        if (v < nvar) t[v] = Ucur[v * ntot + mp.y];
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        if (v < nvar) Udst[v * ntot + mp.x] = t[v];
     } else {
       const double s = (double)(tau % fn + stage * flevel) / (double)fn;
-      for (int v = 0; v < nvar; ++v) {
-        const double a = Uold[v * ntot + mp.y];
-        Udst[v * ntot + mp.x] = a + s * (Ucur[v * ntot + mp.y] - a);
-      }
+      double t[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        if (v < nvar) {
+          const double a = Uold[v * ntot + mp.y];
+          t[v] = a + s * (Ucur[v * ntot + mp.y] - a);
+        }
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        if (v < nvar) Udst[v * ntot + mp.x] = t[v];
     }
   }
 }
@@ -284,7 +298,13 @@ __global__ void __launch_bounds__(LNT) k_ghost_w_lat(const int32_t *__restrict__
   for (int e = s0 + blockIdx.x * LNT + threadIdx.x; e < s1; e += gridDim.x * LNT) {
     if (f[gsrcb[e]] != flevel) continue;
     const int2 mp = reinterpret_cast<const int2 *>(map)[e];
-    for (int v = 0; v < nwv; ++v) W[v * ntot + mp.x] = W[v * ntot + mp.y];
+    double t[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+      if (v < nwv) t[v] = W[v * ntot + mp.y];
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+      if (v < nwv) W[v * ntot + mp.x] = t[v];
   }
 }
 

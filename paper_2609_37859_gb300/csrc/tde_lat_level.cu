@@ -192,17 +192,20 @@ __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsi
     const int fn = a.f[a.gsrcb[e]];
     if (fn == a.flevel) return;   // same schedule: its primitives are copied below
     const int2 mp = reinterpret_cast<const int2 *>(a.gmap)[e];
+    double t[NVAR];   // every field loaded before any is stored (no overlap)
     if (fn < a.flevel) {
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) Udst[v * ntot + mp.x] = a.U[v * ntot + mp.y];
+      for (int v = 0; v < NVAR; ++v) t[v] = a.U[v * ntot + mp.y];
     } else {
       const double s = (double)(a.tau % fn + STAGE * a.flevel) / (double)fn;
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) {
         const double o = a.Uold[v * ntot + mp.y];
-        Udst[v * ntot + mp.x] = o + s * (a.U[v * ntot + mp.y] - o);
+        t[v] = o + s * (a.U[v * ntot + mp.y] - o);
       }
     }
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) Udst[v * ntot + mp.x] = t[v];
   });
   if (!grid_barrier(a, B0, !(STAGE == 0 && a.drop && blockIdx.x == 0))) return false;
   // ---- primitives of the interiors (events counted) and of the converted
@@ -233,8 +236,11 @@ __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsi
     const int e = a.gstart[b] + c * LNTS + threadIdx.x;
     if (e >= a.gstart[b + 1] || a.f[a.gsrcb[e]] != a.flevel) return;
     const int2 mp = reinterpret_cast<const int2 *>(a.gmap)[e];
+    double t[NWV];
 #pragma unroll
-    for (int v = 0; v < NWV; ++v) a.W[v * ntot + mp.x] = a.W[v * ntot + mp.y];
+    for (int v = 0; v < NWV; ++v) t[v] = a.W[v * ntot + mp.y];
+#pragma unroll
+    for (int v = 0; v < NWV; ++v) a.W[v * ntot + mp.x] = t[v];
   });
   if (!grid_barrier(a, B0 + 2, true)) return false;
   // ---- the sweeps; z completes the stage
