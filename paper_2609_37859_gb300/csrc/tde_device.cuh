@@ -293,10 +293,14 @@ __device__ __forceinline__ double bh_r2(double d0, double d1, double d2) { retur
 // reciprocals (a few ulps); infinity where there is no limit (GM <= 0, r = 0).
 // Its square root is taken once per block, after the minimum (the square root
 // is monotonic, so the minimum of the roots is the root of the minimum).
-__device__ __forceinline__ double bh_dt2(double dx, double GM, double r2, double rs2) {
-  if (!dgt0(GM) || !dgt0(r2)) return INFINITY;
+// dxg = bh_dxg(dx, GM), the per-block factor dx / GM (infinite without a limit).
+__device__ __forceinline__ double bh_dxg(double dx, double GM) {
+  return dgt0(GM) ? dx * rcp_nr(GM) : INFINITY;
+}
+__device__ __forceinline__ double bh_dt2(double dxg, double r2, double rs2) {
+  if (!dgt0(r2)) return INFINITY;
   const double s2 = r2 + rs2;
-  return dx * rcp_nr(GM) * (s2 * s2) * (rsqrt_nr(s2) * rsqrt_nr(r2));
+  return dxg * (s2 * s2) * (rsqrt_nr(s2) * rsqrt_nr(r2));
 }
 
 // ---------------------------------------------------------------- EOS ----

@@ -52,18 +52,21 @@ __device__ __forceinline__ void block_min2(double &a, double &b) {
   }
 }
 
-// the point mass's position at time t, evaluated by one warp for the CTA
-__device__ __forceinline__ void cta_bh_pos(const BH &bh, double t, double rb[3]) {
-  __shared__ double s_rb[3];
+// the point mass's position at time t and the block factor dx / GM of its
+// time-step limit, evaluated by one warp for the CTA
+__device__ __forceinline__ void cta_bh_pos(const BH &bh, double t, double dx, double rb[3], double &dxg) {
+  __shared__ double s_rb[4];
   if (threadIdx.x < 32) {
     double r[3];
     bh_pos(bh, t, r);
     if (threadIdx.x < 3) s_rb[threadIdx.x] = r[threadIdx.x];
+    if (threadIdx.x == 3) s_rb[3] = bh_dxg(dx, bh.GM);
   }
   __syncthreads();
   rb[0] = s_rb[0];
   rb[1] = s_rb[1];
   rb[2] = s_rb[2];
+  dxg = s_rb[3];
 }
 
 // ------------------------------------------------------------ k_c2p ----
@@ -81,9 +84,9 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
   const int e = blockIdx.x * NT + threadIdx.x;
   if (blockIdx.x * NT >= nint) return;   // whole CTA past this block (uniform)
   double best = INFINITY, best_g2 = INFINITY;   // the hydro limit; the point mass's, squared
-  double rb[3];
+  double rb[3], dxg = INFINITY;
   const bool near = want_dt && (bh.on || bh.excise);   // uniform over the CTA
-  if (near) cta_bh_pos(bh, ta_t(ta, b), rb);
+  if (near) cta_bh_pos(bh, ta_t(ta, b), scale2i(p.dxmin, -B.level), rb, dxg);
   if (e < nint) {
     const int i = e % B.n[0], r = e / B.n[0];
     const int j = r % B.n[1], k = r / B.n[1];
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         for (int a = 0; a < 3; ++a)
           if (p.active[a]) rate = dmax(rate, (fabs(w[1 + a]) + cs) * block_idx(p, B, a));
         best = dmin(best, rcp_nr(rate));
-        if (bh.on) best_g2 = bh_dt2(scale2i(p.dxmin, -B.level), bh.GM, r2, bh.rs2);
+        if (bh.on) best_g2 = bh_dt2(dxg, r2, bh.rs2);
       }
     }
   }

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_cfl(NAScratch *S, Phys p, BH bh,
         if (p.active[a])
           rate = dmax(rate, (fabs(w[1 + a]) + cs) * scale2i(p.idx[a], d.level));
       best = dmin(best, rcp_nr(rate));
-      if (bh.on) best_g2 = bh_dt2(scale2i(p.dxmin, -d.level), bh.GM, r2, bh.rs2);
+      if (bh.on) best_g2 = bh_dt2(bh_dxg(scale2i(p.dxmin, -d.level), bh.GM), r2, bh.rs2);
     }
   }
   __shared__ double red[2][NA_NT / 32];
