@@ -176,7 +176,9 @@ def e2e_rotating(mesh, host_in, step_fn, torch, dev, stream):
 def sweep_roofline(prof, cells, flop_per_cell, slots_per_cell, traffic, fp64_peak, kernel_note):
     """roofline object of the dominant sweep: FP64 FLOP per cell (ncu SASS
     counters of that kernel on this workload) x cells per launch / its average
-    CUDA-event launch time, against the FP64 FMA rate measured in this run."""
+    CUDA-event launch time, against the FP64 FMA rate measured in this run.
+    Counters of kernels that changed since their capture are passed as None:
+    achieved and frac are then null."""
     sweeps = {k: prof[k] for k in ("sweep_x", "sweep_y", "sweep_z") if prof[k][0]}
     dom = max(sweeps, key=lambda k: sweeps[k][1])
     n_dom, ms_dom = sweeps[dom]
@@ -244,6 +246,8 @@ def run_gpu(args):
                 line["self_gravity"] = gravity_bench(ctx, tde, torch, dev, args)
             if not args.no_lat:
                 line["lat_c4"] = lat_bench(ctx, eos, tde, torch, dev, args)
+            if not args.no_c2:
+                line["c2_entropy_wave"] = c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks)
             print(json.dumps(line), flush=True)
         return
     head = c5_headline(ctx, eos, tde, torch, dev, args, dist, world, barrier, stream)
@@ -253,9 +257,10 @@ def run_gpu(args):
         ms = head["ms"]
         value = whole_job_rate(head["cells"], world, steps, ms)
         e2e = whole_job_rate(head["cells"], world, steps, head["ms_e2e"])
-        roof = sweep_roofline(head["prof"], head["cells"], FP64_FLOP_PER_CELL_C5, FP64_SLOTS_PER_CELL_C5,
-                              DRAM_BYTES_C5 if KERNELS_AS_CAPTURED_C5 else None, fp64_peak,
-                              C5_COUNTERS_NOTE)
+        fresh = KERNELS_AS_CAPTURED_C5
+        roof = sweep_roofline(head["prof"], head["cells"], FP64_FLOP_PER_CELL_C5 if fresh else None,
+                              FP64_SLOTS_PER_CELL_C5 if fresh else None, DRAM_BYTES_C5 if fresh else None,
+                              fp64_peak, C5_COUNTERS_NOTE)
         prof = head["prof"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -333,11 +338,13 @@ def c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push("c2_timed_steps")   # lets a profiler select these launches
     e0.record(stream)
     for _ in range(steps):
         mesh.step(cfl=CFL)
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     prof = ctx.profile_read()
     ctx.profile(False)
@@ -365,7 +372,8 @@ def c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks):
            "e2e": {"value": ncell * steps / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                    "d2h_bytes_per_step": nbytes},
            "hbm_roofline": hbm_roofline(value, peaks),
-           "roofline": sweep_roofline(prof, ncell, FP64_FLOP_PER_CELL_SWEEP, FP64_SLOTS_PER_CELL_SWEEP,
+           "roofline": sweep_roofline(prof, ncell, FP64_FLOP_PER_CELL_SWEEP if KERNELS_AS_CAPTURED else None,
+                                      FP64_SLOTS_PER_CELL_SWEEP if KERNELS_AS_CAPTURED else None,
                                       DRAM_BYTES_SWEEP if KERNELS_AS_CAPTURED else None, fp64_peak,
                                       "profiles/k_sweep_c2_entropy_wave_ncu.md"),
            "kernels_ms": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
@@ -382,23 +390,24 @@ def c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks):
 # per interior cell in one launch of each sweep kernel on this workload, and the
 # DRAM bytes of one launch; profiles/k_sweep_c2_entropy_wave_ncu.md holds the
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
-# False (traffic reported as null) whenever a sweep kernel changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 226.4, "sweep_y": 191.4, "sweep_z": 317.4}
-DRAM_BYTES_SWEEP = {"sweep_x": 266.6e6, "sweep_y": 400.9e6, "sweep_z": 542.8e6}
+# False (achieved, frac and traffic reported as null) whenever a sweep kernel
+# changes.
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 210.3, "sweep_y": 174.9, "sweep_z": 300.9}
+DRAM_BYTES_SWEEP = {"sweep_x": 268.7e6, "sweep_y": 402.4e6, "sweep_z": 545.5e6}
 # FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
 # holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
-FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 201.9, "sweep_y": 201.9, "sweep_z": 289.9}
-KERNELS_AS_CAPTURED = False
+FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 190.6, "sweep_y": 190.6, "sweep_z": 278.6}
+KERNELS_AS_CAPTURED = True
 # The same for the headline's sweeps (production-shaped mesh, PPM, point mass),
 # from ncu on the 8 x 8 x 4 MeshBlocks around the star of that mesh (8.4 M
 # cells, the same cells and scheme; the full mesh holds ~36 GB on the device,
 # too much for a multi-pass capture), two launches of each sweep averaged,
 # DRAM bytes scaled to the full mesh by its cells (x 8); a one-pass capture of
 # the full mesh gives the same FP64 slots per cell within 2 %.
-FP64_FLOP_PER_CELL_C5 = {"sweep_x": 265.5, "sweep_y": 246.6, "sweep_z": 377.1}
-FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 203.1, "sweep_y": 189.9, "sweep_z": 283.0}
-DRAM_BYTES_C5 = {"sweep_x": 11.00e9, "sweep_y": 15.49e9, "sweep_z": 21.30e9}
-KERNELS_AS_CAPTURED_C5 = False
+FP64_FLOP_PER_CELL_C5 = {"sweep_x": 249.0, "sweep_y": 230.1, "sweep_z": 360.6}
+FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 191.8, "sweep_y": 178.7, "sweep_z": 271.8}
+DRAM_BYTES_C5 = {"sweep_x": 10.99e9, "sweep_y": 15.47e9, "sweep_z": 21.31e9}
+KERNELS_AS_CAPTURED_C5 = True
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 
