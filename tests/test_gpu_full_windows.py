@@ -185,3 +185,50 @@ def test_c5_subdomain_whole_lat_window_every_cell(oracle, tde, ctx, tables):
             assert abs(gc[k] - v) <= 1e-3 * v, (k, gc[k], v)
         else:
             assert gc[k] == v, (k, gc[k], v)
+
+
+def test_c5_subdomain_table1_floors(tde, ctx, tables):
+    """The same subdomain at Table 1's floors (1e-10 rho0, 1e-12 rho0 v0^2):
+    synchronised steps stay finite (the step is recomputed from the CFL
+    condition every step); the non-finite cells that this unrelaxed start
+    produces under LAT (a block's step is fixed for the window while a floor
+    cell next to the stellar surface is heated) are counted and reported, not
+    trapped, and the context stays usable."""
+    _, eos = tables
+    floors = (1e-10, 1e-12)
+    lay, W, bhp = c5_subdomain(floors)
+    bh = tde.make_bh(on=1, excise=1, GM=bhp["GM"], r_soft=bhp["r_soft"], r_exc=bhp["r_exc"], x0=bhp["x0"],
+                     v0=bhp["v0"])
+    params = tde.make_params(eos=1, recon=1, dual=1, eta1=1e-3, eta2=1e-4, rho_floor=floors[0],
+                             p_floor=floors[1], u_floor=1.5 * floors[1], unit_rho=wl.RHO0_CGS,
+                             unit_e=wl.V0_CGS ** 2)
+    mesh = tde.Mesh(ctx, lay, params, eos)
+    mesh.prim_to_cons(torch.from_numpy(np.ascontiguousarray(W)).to(mesh.U.device))
+    del W
+    U0 = mesh.U.clone()
+    mesh.set_time(0.0)
+    mesh.counts(reset=True)
+    for _ in range(64):
+        mesh.step(cfl=0.3, bh=bh)
+    c = mesh.counts(reset=True)
+    print("C5 subdomain, Table 1 floors, 64 synchronised steps:", c)
+    assert c["nonfinite"] == 0 and c["rho_floor"] > 0 and c["excised"] > 0
+    mesh.check()
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+    fac, dt0, fmax = mesh.lat_assign(6, 0.3, merge_frac=0.01, bh=bh)
+    mesh.lat_window(bh=bh)
+    c = mesh.counts()
+    print("C5 subdomain, Table 1 floors, one LAT window (f_max %d): %d non-finite cell-stages" %
+          (fmax, c["nonfinite"]))
+    if c["nonfinite"]:
+        with pytest.raises(tde.TDEError) as ei:
+            mesh.check()
+        assert ei.value.code == tde.TDE_ENUMERIC
+    # the context stays usable: the start again, one synchronised step
+    mesh.U.copy_(U0)
+    mesh.set_time(0.0)
+    mesh.counts(reset=True)
+    mesh.step(cfl=0.3, bh=bh)
+    assert mesh.counts(reset=True)["nonfinite"] == 0
+    mesh.check()
