@@ -28,48 +28,73 @@ namespace tde {
 
 constexpr int NT = 256;   // threads per CTA
 
-// minima of a and b over the CTA (valid in thread 0)
+// minima of a and b over the CTA (valid in thread 0) for values >= 0 (time
+// steps and their squares; NaN only if all are): the bit patterns of such
+// doubles order like the values, so the minima run on the integer pipe
+__device__ __forceinline__ unsigned long long umin64(unsigned long long x, unsigned long long y) {
+  return x < y ? x : y;
+}
 __device__ __forceinline__ void block_min2(double &a, double &b) {
-  __shared__ double red[2][NT / 32];
+  __shared__ unsigned long long red[2][NT / 32];
+  unsigned long long ka = (unsigned long long)dbits(a), kb = (unsigned long long)dbits(b);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-    b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+    ka = umin64(ka, __shfl_xor_sync(0xffffffffu, ka, o));
+    kb = umin64(kb, __shfl_xor_sync(0xffffffffu, kb, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = a;
-    red[1][threadIdx.x >> 5] = b;
+    red[0][threadIdx.x >> 5] = ka;
+    red[1][threadIdx.x >> 5] = kb;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    a = threadIdx.x < NT / 32 ? red[0][threadIdx.x] : INFINITY;
-    b = threadIdx.x < NT / 32 ? red[1][threadIdx.x] : INFINITY;
+    const unsigned long long inf = (unsigned long long)dbits(INFINITY);
+    ka = threadIdx.x < NT / 32 ? red[0][threadIdx.x] : inf;
+    kb = threadIdx.x < NT / 32 ? red[1][threadIdx.x] : inf;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-      b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+      ka = umin64(ka, __shfl_xor_sync(0xffffffffu, ka, o));
+      kb = umin64(kb, __shfl_xor_sync(0xffffffffu, kb, o));
     }
   }
+  a = __longlong_as_double((long long)ka);
+  b = __longlong_as_double((long long)kb);
 }
 
-// the point mass's position at time t and the block factor dx / GM of its
-// time-step limit, evaluated by one warp for the CTA
-__device__ __forceinline__ void cta_bh_pos(const BH &bh, double t, double dx, double rb[3], double &dxg) {
-  __shared__ double s_rb[4];
+// Squared distance from rb to the box of block B's interior cell centres: a
+// lower bound of every interior cell's bh_r2 up to rounding (warp-collective;
+// every lane of the calling warp gets it).  Interior centres never wrap, so no
+// periodic image enters.
+__device__ __forceinline__ double block_box_d2(const Phys &p, const DevBlock &B, const double rb[3]) {
+  const int l = threadIdx.x & 31, a = l < 3 ? l : 0;
+  const double lo = cell_coord(p, B, a, p.g[a]), hi = cell_coord(p, B, a, p.g[a] + B.n[a] - 1);
+  const double ra = a == 0 ? rb[0] : (a == 1 ? rb[1] : rb[2]);
+  const double da = dlt(ra, lo) ? lo - ra : (dlt(hi, ra) ? ra - hi : 0.0);
+  const double q = l < 3 ? da * da : 0.0;
+  return __shfl_sync(0xffffffffu, q, 0) + __shfl_sync(0xffffffffu, q, 1) + __shfl_sync(0xffffffffu, q, 2);
+}
+
+// The point mass's position at time t, the block factor dx / GM of its
+// time-step limit and the squared distance to the block's box of interior cell
+// centres, evaluated by one warp for the CTA.
+__device__ __forceinline__ void cta_bh_info(const BH &bh, double t, double dx, const Phys &p, const DevBlock &B,
+                                            double rb[3], double &dxg, double &d2box) {
+  __shared__ double s_rb[5];
   if (threadIdx.x < 32) {
     double r[3];
     bh_pos(bh, t, r);
+    const double d2 = block_box_d2(p, B, r);
     if (threadIdx.x < 3) s_rb[threadIdx.x] = r[threadIdx.x];
     if (threadIdx.x == 3) s_rb[3] = bh_dxg(dx, bh.GM);
+    if (threadIdx.x == 4) s_rb[4] = d2;
   }
   __syncthreads();
   rb[0] = s_rb[0];
   rb[1] = s_rb[1];
   rb[2] = s_rb[2];
   dxg = s_rb[3];
+  d2box = s_rb[4];
 }
-
-// ------------------------------------------------------------ k_c2p ----
 
 template <int EOSK, int DUAL, int EOSB = 0>
 __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
@@ -84,13 +109,18 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
   const int e = blockIdx.x * NT + threadIdx.x;
   if (blockIdx.x * NT >= nint) return;   // whole CTA past this block (uniform)
   double best = INFINITY, best_g2 = INFINITY;   // the hydro limit; the point mass's, squared
-  double rb[3], dxg = INFINITY;
+  double rb[3], dxg = INFINITY, d2box = 0.0;
   const bool near = want_dt && (bh.on || bh.excise);   // uniform over the CTA
-  if (near) cta_bh_pos(bh, ta_t(ta, b), scale2i(p.dxmin, -B.level), rb, dxg);
+  if (near) cta_bh_info(bh, ta_t(ta, b), scale2i(p.dxmin, -B.level), p, B, rb, dxg, d2box);
+  // some interior cell may lie within r_exc (else the per-cell test is false for
+  // all: a margin of 2^-20 on r_exc^2 is far above the roundings of the box and
+  // of the cells' r^2)
+  const bool exc_box = bh.excise && !dlt(bh.rexc * bh.rexc * (1.0 + 0x1p-20), d2box);
+  const int i = e % B.n[0], r = e / B.n[0];
+  const int c[3] = {i + p.g[0], r % B.n[1] + p.g[1], r / B.n[1] + p.g[2]};
+  bool skip = e >= nint;   // no CFL contribution (past the block, or excised)
+  double r2 = -1.0;        // the cell's squared distance, once computed
   if (e < nint) {
-    const int i = e % B.n[0], r = e / B.n[0];
-    const int j = r % B.n[1], k = r / B.n[1];
-    const int c[3] = {i + p.g[0], j + p.g[1], k + p.g[2]};
     const long long flat = B.off + ((long long)c[2] * B.p[1] + c[1]) * B.p[0] + c[0];
     double u[6], w[8];
 #pragma unroll
@@ -100,14 +130,12 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
 #pragma unroll
     for (int v = 0; v < NWV; ++v) W[v * ntot + flat] = w[v];
     if (want_dt) {
-      bool skip = false;
-      double r2 = 0.0;
-      if (near) {
+      if (exc_box) {
         double x[3];
         cell_centre(p, B, c, x);
         r2 = bh_r2(x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]);
+        skip = inside_radius(r2, bh.rexc);
       }
-      if (bh.excise && inside_radius(r2, bh.rexc)) skip = true;
       if (!skip) {
         const double g1 = EOSK == EOS_TABLE ? w[6] : p.gamma;
         const double cs = sqrt_ratio(g1 * w[4], w[0]);
@@ -117,11 +145,34 @@ __global__ void __launch_bounds__(NT) k_c2p(Phys p, BH bh, TimeArgs ta,
         for (int a = 0; a < 3; ++a)
           if (p.active[a]) rate = dmax(rate, (fabs(w[1 + a]) + cs) * block_idx(p, B, a));
         best = dmin(best, rcp_nr(rate));
-        if (bh.on) best_g2 = bh_dt2(dxg, r2, bh.rs2);
       }
     }
   }
   if (want_dt) {
+    if (bh.on) {
+      // The point mass's limit dt_g^2 grows with r beyond r_s / sqrt(2), so over a
+      // box at least that far its value at the box is a lower bound (less a
+      // margin of 2^-20 for the roundings); where that bound exceeds this CTA's
+      // hydro minimum squared (with the same margin) the point mass cannot set
+      // the CTA's minimum and is not evaluated per cell.  The result is the
+      // same as evaluating it everywhere.
+      __shared__ int s_grav;
+      double bmin = best, none = INFINITY;
+      block_min2(bmin, none);
+      if (threadIdx.x == 0) {
+        const double lb = dlt(0.5 * bh.rs2, d2box) ? bh_dt2(dxg, d2box, bh.rs2) * (1.0 - 0x1p-20) : 0.0;
+        s_grav = !dle(bmin * bmin * (1.0 + 0x1p-20), lb);
+      }
+      __syncthreads();
+      if (s_grav && !skip) {
+        if (r2 < 0.0) {
+          double x[3];
+          cell_centre(p, B, c, x);
+          r2 = bh_r2(x[0] - rb[0], x[1] - rb[1], x[2] - rb[2]);
+        }
+        best_g2 = bh_dt2(dxg, r2, bh.rs2);
+      }
+    }
     block_min2(best, best_g2);
     if (threadIdx.x == 0) {
       best = dmin(best, sqrt(best_g2));
@@ -302,13 +353,7 @@ __global__ void __launch_bounds__(NT) k_excise(Phys p, BH bh, TimeArgs ta,
   if (threadIdx.x < 32) {
     double rb[3];
     bh_pos(bh, ta_t(ta, b) + ta_dt(ta, b), rb);
-    // nearest point of the box of interior cell centres, per direction
-    const int a = threadIdx.x < 3 ? threadIdx.x : 0;
-    const double lo = cell_coord(p, B, a, p.g[a]), hi = cell_coord(p, B, a, p.g[a] + B.n[a] - 1);
-    const double da = dlt(rb[a], lo) ? lo - rb[a] : (dlt(hi, rb[a]) ? rb[a] - hi : 0.0);
-    const double q = threadIdx.x < 3 ? da * da : 0.0;
-    const double d2 = __shfl_sync(0xffffffffu, q, 0) + __shfl_sync(0xffffffffu, q, 1) +
-                      __shfl_sync(0xffffffffu, q, 2);
+    const double d2 = block_box_d2(p, B, rb);
     if (threadIdx.x == 0) {
       // (interior cell centres never wrap, so no periodic image enters either test)
       s_far = dlt(bh.rexc * bh.rexc * (1.0 + 0x1p-20), d2);
