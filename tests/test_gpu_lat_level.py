@@ -114,10 +114,25 @@ def test_persistent_level_launch_count(oracle, tde, ctx):
 
 
 def test_persistent_mode_applies_only_where_admitted(oracle, tde, ctx):
-    """2-D meshes keep the launch sequence; an unknown mode is refused."""
+    """2-D meshes and refined meshes keep the launch sequence (a window there
+    gives the sequence's bits in either mode); an unknown mode is refused."""
+    from test_gpu_smr import smr, smooth_W
     lay2 = wl.uniform_layout((32, 32, 1), (16, 16, 1), bc=(1, 1, 1), ng=2)
     Q = Pair(oracle, tde, ctx, lay2, wl.random_smooth(lay2, seed=3, P0=2.0), dual=1)
     assert Q.gm.set_lat_mode(tde.LAT_PERSISTENT) is False
+    lay3 = smr(r=0.1)
+    R = Pair(oracle, tde, ctx, lay3, smooth_W(lay3), dual=1, eta1=1e-3, eta2=1e-4)
+    f, dt0, fmax = R.gm.lat_assign(3, 0.3, 0.0)
+    assert fmax > 1
+    outs = []
+    for mode in (tde.LAT_SEQUENCE, tde.LAT_PERSISTENT):
+        assert R.gm.set_lat_mode(mode) is False
+        R.gm.U.copy_(torch.from_numpy(R.U))
+        R.gm.set_time(0.0)
+        R.gm.lat_set_factors(f, dt0)
+        R.gm.lat_window()
+        outs.append(R.gpu("U"))
+    assert np.array_equal(outs[0], outs[1])
     P = smooth(oracle, tde, ctx, (8, 8, 8))
     assert P.gm.set_lat_mode(tde.LAT_PERSISTENT) is True
     assert P.gm.set_lat_mode(tde.LAT_SEQUENCE) is False
