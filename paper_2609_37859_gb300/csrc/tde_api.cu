@@ -526,7 +526,8 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   // is a copy (gmap, source block gsrcb); on a refined mesh the others are
   // restriction or prolongation ops
   std::vector<int32_t> gmap, gsrcb;
-  std::vector<int32_t> gstart(nblocks + 1, 0);
+  std::vector<int32_t> gstart(nblocks + 1, 0), gend(nblocks, 0);
+  std::vector<int32_t> fmap, omap, fsrc, osrc;   // one block's face and other copies
   std::vector<AmrOp> amr;
   std::vector<int32_t> amr_start(nblocks + 1, 0);
   for (int b = 0; b < nblocks; ++b) {
@@ -549,9 +550,14 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
           const int64_t dst = B.off + ((int64_t)k * B.p[1] + j) * B.p[0] + i;
           const int Lo = m->hblocks[ob].level;
           if (Lo == L) {
-            gmap.push_back((int32_t)dst);
-            gmap.push_back((int32_t)padded(ob, gg));
-            gsrcb.push_back(ob);
+            // face ghosts (one direction outside the interior) first
+            int nout = 0;
+            for (int a = 0; a < 3; ++a)
+              if (c[a] < p.g[a] || c[a] >= p.g[a] + B.n[a]) ++nout;
+            std::vector<int32_t> &em = nout == 1 ? fmap : omap;
+            em.push_back((int32_t)dst);
+            em.push_back((int32_t)padded(ob, gg));
+            (nout == 1 ? fsrc : osrc).push_back(ob);
             ++cnt;
             continue;
           }
@@ -586,6 +592,12 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
           ++namr;
         }
     gstart[b + 1] = gstart[b] + cnt;
+    gend[b] = gstart[b] + (int32_t)fsrc.size();
+    gmap.insert(gmap.end(), fmap.begin(), fmap.end());
+    gmap.insert(gmap.end(), omap.begin(), omap.end());
+    gsrcb.insert(gsrcb.end(), fsrc.begin(), fsrc.end());
+    gsrcb.insert(gsrcb.end(), osrc.begin(), osrc.end());
+    fmap.clear(); omap.clear(); fsrc.clear(); osrc.clear();
     amr_start[b + 1] = amr_start[b] + namr;
     m->max_ghosts = std::max(m->max_ghosts, cnt);
     m->max_amr = std::max(m->max_amr, namr);
@@ -602,6 +614,7 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   A((void **)&m->d_blocks, sizeof(DevBlock) * nblocks);
   A((void **)&m->d_ghost, sizeof(int32_t) * gmap.size());
   A((void **)&m->d_gstart, sizeof(int32_t) * (nblocks + 1));
+  A((void **)&m->d_gend, sizeof(int32_t) * nblocks);
   A((void **)&m->d_allids, sizeof(int32_t) * nblocks);
   A((void **)&m->d_W, sizeof(double) * nt * p.nwv);
   A((void **)&m->d_dU, sizeof(double) * nt * (p.nvar + 1));
@@ -635,6 +648,10 @@ extern "C" int tde_mesh_create(tde_ctx *ctx, int nblocks, const tde_block_desc *
   if (!gmap.empty()) cudaMemcpy(m->d_ghost, gmap.data(), sizeof(int32_t) * gmap.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_gstart, gstart.data(), sizeof(int32_t) * (nblocks + 1), cudaMemcpyHostToDevice);
   m->h_gstart = gstart;
+  if (!amr.empty())   // refined meshes: every entry
+    for (int b = 0; b < nblocks; ++b) gend[b] = gstart[b + 1];
+  m->h_gend = gend;
+  cudaMemcpy(m->d_gend, gend.data(), sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_allids, allids.data(), sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_scal, zeros, sizeof zeros, cudaMemcpyHostToDevice);
   cudaMemcpy(m->d_dtbits, inf_bits.data(), sizeof(unsigned long long) * nblocks, cudaMemcpyHostToDevice);
@@ -676,6 +693,7 @@ extern "C" int tde_mesh_destroy(tde_mesh *m) {
   cudaFree(m->d_blocks);
   cudaFree(m->d_ghost);
   cudaFree(m->d_gstart);
+  cudaFree(m->d_gend);
   cudaFree(m->d_allids);
   cudaFree(m->d_W);
   cudaFree(m->d_dU);
@@ -796,7 +814,7 @@ static int run_stage(tde_mesh *m, int stage, int nblk, const int32_t *ids, const
     // every block advances: primitives of the interiors, then a copy of the
     // neighbours' primitives into the ghost layer
     if (!prims_ready) CK(c, launch_c2p(m, Uin, nblk, ids, false, bh, ta));
-    CK(c, launch_ghost(m, m->d_W, m->phys.nwv, nblk, ids));
+    CK(c, launch_ghost(m, m->d_W, m->phys.nwv, nblk, ids, true));
   } else {
     // a subset advances: refresh the conserved ghosts of the listed blocks from
     // the stage input and convert every padded cell of those blocks

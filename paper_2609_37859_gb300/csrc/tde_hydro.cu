@@ -316,10 +316,11 @@ __global__ void __launch_bounds__(1024) k_dt_finalize(int nb, double cfl,
 constexpr int GHOST_NF_MAX = 8;
 __global__ void __launch_bounds__(NT) k_ghost(const int32_t *__restrict__ map,
                                               const int32_t *__restrict__ gstart,
+                                              const int32_t *__restrict__ gend,
                                               const int32_t *__restrict__ ids, double *f, int nf,
                                               long long ntot) {
   const int b = ids[blockIdx.y];
-  const int s0 = gstart[b], s1 = gstart[b + 1];
+  const int s0 = gstart[b], s1 = gend ? gend[b] : gstart[b + 1];
   for (int e = s0 + blockIdx.x * NT + threadIdx.x; e < s1; e += gridDim.x * NT) {
     const int2 m = reinterpret_cast<const int2 *>(map)[e];
     double t[GHOST_NF_MAX];
@@ -735,12 +736,13 @@ cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids) {
+cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids, bool sweep_only) {
   if (m->max_ghosts == 0) return cudaSuccess;
   if (nf < 1 || nf > GHOST_NF_MAX) return cudaErrorInvalidValue;
   ProfScope _ps(m->ctx, TDE_K_GHOST);
   unsigned gx = (unsigned)min((m->max_ghosts + NT - 1) / NT, 64);
-  k_ghost<<<dim3(gx, (unsigned)nblk), NT, 0, m->ctx->stream>>>(m->d_ghost, m->d_gstart, ids, field,
+  k_ghost<<<dim3(gx, (unsigned)nblk), NT, 0, m->ctx->stream>>>(m->d_ghost, m->d_gstart,
+                                                                 sweep_only ? m->d_gend : nullptr, ids, field,
                                                                  nf, (long long)m->ntot);
   return cudaGetLastError();
 }
@@ -957,7 +959,7 @@ cudaError_t autotune_sweeps(tde_mesh *m, const BH &bh, int reps, float ms_out[3]
     err = cudaMemcpyAsync(cnt_save, m->d_cnt, sizeof(Counters), cudaMemcpyDeviceToDevice, s);
   TimeArgs ta{zero, 0, m->d_scal, 0};
   if (err == cudaSuccess) err = launch_c2p(m, m->U, m->nb, m->d_allids, false, bh, ta);
-  if (err == cudaSuccess) err = launch_ghost(m, m->d_W, m->phys.nwv, m->nb, m->d_allids);
+  if (err == cudaSuccess) err = launch_ghost(m, m->d_W, m->phys.nwv, m->nb, m->d_allids, true);
   for (int D = 0; D < 3 && err == cudaSuccess; ++D) {
     for (int t = 0; t < N_TILE_SHAPES; ++t) ms_out[D][t] = -1.f;
     if (!m->phys.active[D]) continue;

@@ -148,6 +148,12 @@ struct tde_mesh {
   int32_t *d_ghost = nullptr;        // [n_ghost][2] (dst, src) flat padded indices
   int32_t *d_gstart = nullptr;       // [nb + 1]
   std::vector<int32_t> h_gstart;     // its host copy
+  // [nb] end of each block's ghost entries that the sweeps read: the face ghosts
+  // (one direction outside the interior), listed first in each block's range;
+  // the sweeps never read an edge or corner ghost cell.  On a refined mesh every
+  // entry (gend[b] = gstart[b + 1]).
+  int32_t *d_gend = nullptr;
+  std::vector<int32_t> h_gend;
   int32_t *d_allids = nullptr;       // 0..nb-1
   double *d_W = nullptr;             // primitives, nwv * ntot
   double *d_dU = nullptr;            // accumulated L(U) and div v, (nvar + 1) * ntot
@@ -213,7 +219,9 @@ struct TimeArgs {
 cudaError_t launch_c2p(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids, bool want_dt,
                        const BH &bh, TimeArgs ta);
 cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double *dt_min);
-cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids);
+// every ghost cell of the listed blocks, or (sweep_only) the face ghosts the sweeps read
+cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids,
+                         bool sweep_only = false);
 cudaError_t launch_sweeps(tde_mesh *m, int stage, const double *U0, const double *Uin,
                           double *Uout, int nblk, const int32_t *ids, const BH &bh, TimeArgs ta,
                           double *freg = nullptr);

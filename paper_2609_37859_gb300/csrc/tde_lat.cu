@@ -36,7 +36,6 @@ namespace tde {
 cudaError_t launch_c2p(tde_mesh *m, const double *Uin, int nblk, const int32_t *ids, bool want_dt,
                        const BH &bh, TimeArgs ta);
 cudaError_t launch_dt_finalize(tde_mesh *m, double cfl, double *dt_block, double *dt_min);
-cudaError_t launch_ghost(tde_mesh *m, double *field, int nf, int nblk, const int32_t *ids);
 cudaError_t launch_excise(tde_mesh *m, double *U, int nblk, const int32_t *ids, const BH &bh,
                           TimeArgs ta);
 cudaError_t launch_sync(tde_mesh *m, double *U, int nblk, const int32_t *ids, double eta2);
@@ -165,6 +164,7 @@ __global__ void __launch_bounds__(LNT) k_copy_blocks(const DevBlock *__restrict_
 
 __global__ void __launch_bounds__(LNT) k_ghost_lat(const int32_t *__restrict__ map,
                                                    const int32_t *__restrict__ gstart,
+                                                   const int32_t *__restrict__ gend,
                                                    const int32_t *__restrict__ gsrcb,
                                                    const int32_t *__restrict__ ids,
                                                    const int32_t *__restrict__ f, int flevel,
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(LNT) k_ghost_lat(const int32_t *__restrict__ m
                                                    const double *__restrict__ Uold, int nvar,
                                                    long long ntot) {
   const int b = ids[blockIdx.y];
-  const int s0 = gstart[b], s1 = gstart[b + 1];
+  const int s0 = gstart[b], s1 = gend[b];   // the ghost cells the sweeps read
   for (int e = s0 + blockIdx.x * LNT + threadIdx.x; e < s1; e += gridDim.x * LNT) {
     const int2 mp = reinterpret_cast<const int2 *>(map)[e];
     const int fn = f[gsrcb[e]];
@@ -289,12 +289,13 @@ __global__ void __launch_bounds__(LNT) k_ghost_amr(const AmrOp *__restrict__ ops
 // conversion of the copied conserved values bit for bit)
 __global__ void __launch_bounds__(LNT) k_ghost_w_lat(const int32_t *__restrict__ map,
                                                      const int32_t *__restrict__ gstart,
+                                                     const int32_t *__restrict__ gend,
                                                      const int32_t *__restrict__ gsrcb,
                                                      const int32_t *__restrict__ ids,
                                                      const int32_t *__restrict__ f, int flevel, double *W,
                                                      int nwv, long long ntot) {
   const int b = ids[blockIdx.y];
-  const int s0 = gstart[b], s1 = gstart[b + 1];
+  const int s0 = gstart[b], s1 = gend[b];
   for (int e = s0 + blockIdx.x * LNT + threadIdx.x; e < s1; e += gridDim.x * LNT) {
     if (f[gsrcb[e]] != flevel) continue;
     const int2 mp = reinterpret_cast<const int2 *>(map)[e];
@@ -483,13 +484,14 @@ constexpr int GLT = 256;
 __global__ void __launch_bounds__(GLT) k_glist_count(const int32_t *__restrict__ sorted,
                                                      const int32_t *__restrict__ f,
                                                      const int32_t *__restrict__ gstart,
+                                                     const int32_t *__restrict__ gend,
                                                      const int32_t *__restrict__ gsrcb,
                                                      const int32_t *__restrict__ amr_start,
                                                      int32_t *__restrict__ cnt) {
   __shared__ int ws[GLT / 32];
   const int b = sorted[blockIdx.x], fb = f[b];
   int n = 0;
-  for (int e = gstart[b] + threadIdx.x; e < gstart[b + 1]; e += GLT) n += f[gsrcb[e]] != fb;
+  for (int e = gstart[b] + threadIdx.x; e < gend[b]; e += GLT) n += f[gsrcb[e]] != fb;
   n = __reduce_add_sync(0xffffffffu, n);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = n;
   __syncthreads();
@@ -536,6 +538,7 @@ __global__ void __launch_bounds__(1024) k_glist_scan(int32_t *cnt, int nb) {
 __global__ void __launch_bounds__(GLT) k_glist_fill(const int32_t *__restrict__ sorted,
                                                     const int32_t *__restrict__ f,
                                                     const int32_t *__restrict__ gstart,
+                                                    const int32_t *__restrict__ gend,
                                                     const int32_t *__restrict__ gsrcb,
                                                     const int32_t *__restrict__ map,
                                                     const AmrOp *__restrict__ amr,
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(GLT) k_glist_fill(const int32_t *__restrict__ 
   __shared__ int ws[GLT / 32];
   const int b = sorted[blockIdx.x], fb = f[b];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s1 = gstart[b + 1];
+  const int s1 = gend[b];   // the ghost cells the sweeps read
   int base = start[blockIdx.x];
   // ordered compaction, GLT entries per pass (the pass count is uniform over the CTA)
   for (int e0 = gstart[b]; e0 < s1; e0 += GLT) {
@@ -574,9 +577,9 @@ cudaError_t launch_glist(tde_mesh *m, int32_t *starts) {
   const int nb = m->nb;
   cudaStream_t s = m->ctx->stream;
   ProfScope ps(m->ctx, TDE_K_SCALAR);
-  k_glist_count<<<nb, GLT, 0, s>>>(m->d_sorted, m->d_f, m->d_gstart, m->d_gsrcb, m->d_amr_start, starts);
+  k_glist_count<<<nb, GLT, 0, s>>>(m->d_sorted, m->d_f, m->d_gstart, m->d_gend, m->d_gsrcb, m->d_amr_start, starts);
   k_glist_scan<<<1, 1024, 0, s>>>(starts, nb);
-  k_glist_fill<<<nb, GLT, 0, s>>>(m->d_sorted, m->d_f, m->d_gstart, m->d_gsrcb, m->d_ghost, m->d_amr,
+  k_glist_fill<<<nb, GLT, 0, s>>>(m->d_sorted, m->d_f, m->d_gstart, m->d_gend, m->d_gsrcb, m->d_ghost, m->d_amr,
                                   m->d_amr_start, starts, m->d_lat_glist);
   return cudaGetLastError();
 }
@@ -667,7 +670,7 @@ int lat_build(tde_mesh *m) {
       const DevBlock &B = m->hblocks[m->h_sorted[q]];
       const int b = m->h_sorted[q];
       m->h_lat_pre[q + 1] = m->h_lat_pre[q] + (B.n[0] * B.n[1] * B.n[2] + T - 1) / T;
-      m->h_lat_pre[nb + 1 + q + 1] = m->h_lat_pre[nb + 1 + q] + (m->h_gstart[b + 1] - m->h_gstart[b] + T - 1) / T;
+      m->h_lat_pre[nb + 1 + q + 1] = m->h_lat_pre[nb + 1 + q] + (m->h_gend[b] - m->h_gstart[b] + T - 1) / T;
     }
     LCK(c, cudaMemcpyAsync(m->d_lat_pre, m->h_lat_pre.data(), sizeof(int32_t) * m->h_lat_pre.size(),
                            cudaMemcpyHostToDevice, c->stream));
@@ -762,7 +765,7 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
         double *Udst = stage ? m->U1 : m->U;
         {
           ProfScope ps(c, TDE_K_GHOST);
-          k_ghost_lat<<<dim3(gx_ghost, n), LNT, 0, s>>>(m->d_ghost, m->d_gstart, m->d_gsrcb, ids, m->d_f, f, tau,
+          k_ghost_lat<<<dim3(gx_ghost, n), LNT, 0, s>>>(m->d_ghost, m->d_gstart, m->d_gend, m->d_gsrcb, ids, m->d_f, f, tau,
                                                         stage, Udst, m->U, m->d_Uold, nvar, (long long)m->ntot);
         }
         LCK(c, cudaGetLastError());
@@ -773,7 +776,7 @@ int lat_enqueue_window(tde_mesh *m, const BH &bh) {
                                m->h_lat_glist_off[L + 1] - m->h_lat_glist_off[L]));
         {
           ProfScope ps(c, TDE_K_GHOST);
-          k_ghost_w_lat<<<dim3(gx_ghost, n), LNT, 0, s>>>(m->d_ghost, m->d_gstart, m->d_gsrcb, ids, m->d_f, f,
+          k_ghost_w_lat<<<dim3(gx_ghost, n), LNT, 0, s>>>(m->d_ghost, m->d_gstart, m->d_gend, m->d_gsrcb, ids, m->d_f, f,
                                                           m->d_W, p.nwv, (long long)m->ntot);
         }
         LCK(c, cudaGetLastError());

@@ -50,6 +50,7 @@ struct LevelArgs {
   long long ntot;
   const int32_t *gmap;       // ghost (dst, src) pairs
   const int32_t *gstart;     // each block's range of them
+  const int32_t *gend;       // the end of its face entries (the ones the sweeps read)
   const int32_t *gsrcb;      // source block of each pair
   const int32_t *glist;      // the level's ghost cells that are converted
   int nglist;
@@ -188,7 +189,7 @@ __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsi
   level_chunks(a.pre_gh, a.n, [&](int q, int c) {
     const int b = a.ids[q];
     const int e = a.gstart[b] + c * LNTS + threadIdx.x;
-    if (e >= a.gstart[b + 1]) return;
+    if (e >= a.gend[b]) return;
     const int fn = a.f[a.gsrcb[e]];
     if (fn == a.flevel) return;   // same schedule: its primitives are copied below
     const int2 mp = reinterpret_cast<const int2 *>(a.gmap)[e];
@@ -234,7 +235,7 @@ __device__ __forceinline__ bool level_stage(const LevelArgs &a, double *sm, unsi
   level_chunks(a.pre_gh, a.n, [&](int q, int c) {
     const int b = a.ids[q];
     const int e = a.gstart[b] + c * LNTS + threadIdx.x;
-    if (e >= a.gstart[b + 1] || a.f[a.gsrcb[e]] != a.flevel) return;
+    if (e >= a.gend[b] || a.f[a.gsrcb[e]] != a.flevel) return;
     const int2 mp = reinterpret_cast<const int2 *>(a.gmap)[e];
     double t[NWV];
 #pragma unroll
@@ -326,6 +327,7 @@ cudaError_t launch_lat_level(tde_mesh *m, const BH &bh, const int32_t *ids, int 
   a.ntot = (long long)m->ntot;
   a.gmap = m->d_ghost;
   a.gstart = m->d_gstart;
+  a.gend = m->d_gend;
   a.gsrcb = m->d_gsrcb;
   a.glist = glist;
   a.nglist = nglist;
