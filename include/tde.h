@@ -451,8 +451,8 @@ TDE_API int tde_math_selftest(tde_eos *eos, int64_t n, const double *x, double *
 
 /* ---- sweep tile shapes and their autotuner (a9) -----------------------------
  * A sweep CTA works on a tile of pencils of one block along the sweep direction.
- * Shapes (index: lanes per tile, threads per CTA): 0: 8 x 272 (default), 1: 16 x
- * 288, 2: 4 x 160; a shape whose tile needs more than 227 KB of shared memory for
+ * Shapes (index: lanes per tile, threads per CTA): 0: 8 x 288 (default), 1: 16 x
+ * 288, 2: 4 x 160; a shape whose tile needs more than 226 KB of shared memory for
  * the mesh's block size is not available.  Results do not depend on the shape
  * (every face and cell is computed by the same operations); only the time does.
  *
