@@ -397,7 +397,7 @@ DRAM_BYTES_SWEEP = {"sweep_x": 268.7e6, "sweep_y": 402.4e6, "sweep_z": 545.5e6}
 # FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
 # holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
 FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 190.6, "sweep_y": 190.6, "sweep_z": 278.6}
-KERNELS_AS_CAPTURED = True
+KERNELS_AS_CAPTURED = False
 # The same for the headline's sweeps (production-shaped mesh, PPM, point mass),
 # from ncu on the 8 x 8 x 4 MeshBlocks around the star of that mesh (8.4 M
 # cells, the same cells and scheme; the full mesh holds ~36 GB on the device,
@@ -407,7 +407,7 @@ KERNELS_AS_CAPTURED = True
 FP64_FLOP_PER_CELL_C5 = {"sweep_x": 249.0, "sweep_y": 230.1, "sweep_z": 360.6}
 FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 191.8, "sweep_y": 178.7, "sweep_z": 271.8}
 DRAM_BYTES_C5 = {"sweep_x": 10.99e9, "sweep_y": 15.47e9, "sweep_z": 21.31e9}
-KERNELS_AS_CAPTURED_C5 = True
+KERNELS_AS_CAPTURED_C5 = False
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 

@@ -609,8 +609,10 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   double dn = fac * SM - mflux;
   double d1 = (fac - r) * vt1;
   double d2 = (fac - r) * vt2;
-  double Es = (E * (S - un) + (SM - un) * (rS * SM + P)) * inv;
-  double dE = Es - E;
+  // E*_K - E_K = [E (S - u) + (SM - u)(rS SM + P)] / (S - SM) - E
+  //            = (SM - u)(E + P + rS SM) / (S - SM): no cancellation, two fewer FP64 ops
+  const double EP = E + P;
+  double dE = (SM - un) * fma(rS, SM, EP) * inv;
   F[0] = mflux + Seff * d0;
   double Fn = mflux * un + P + Seff * dn;
   double F1 = mflux * vt1 + Seff * d1;
@@ -618,7 +620,7 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   F[1 + D] = Fn;
   F[1 + t1] = F1;
   F[1 + t2] = F2;
-  F[4] = (E + P) * un + Seff * dE;
+  F[4] = EP * un + Seff * dE;
   if (DUAL) {
     double f = F[0];
     bool up = dgt0(f);
