@@ -392,22 +392,22 @@ def c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks):
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
 # False (achieved, frac and traffic reported as null) whenever a sweep kernel
 # changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 210.3, "sweep_y": 174.9, "sweep_z": 300.9}
-DRAM_BYTES_SWEEP = {"sweep_x": 268.7e6, "sweep_y": 402.4e6, "sweep_z": 545.5e6}
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 207.2, "sweep_y": 171.8, "sweep_z": 297.8}
+DRAM_BYTES_SWEEP = {"sweep_x": 268.5e6, "sweep_y": 401.1e6, "sweep_z": 544.5e6}
 # FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
 # holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
-FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 190.6, "sweep_y": 190.6, "sweep_z": 278.6}
-KERNELS_AS_CAPTURED = False
+FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 189.5, "sweep_y": 189.5, "sweep_z": 277.5}
+KERNELS_AS_CAPTURED = True
 # The same for the headline's sweeps (production-shaped mesh, PPM, point mass),
 # from ncu on the 8 x 8 x 4 MeshBlocks around the star of that mesh (8.4 M
 # cells, the same cells and scheme; the full mesh holds ~36 GB on the device,
 # too much for a multi-pass capture), two launches of each sweep averaged,
 # DRAM bytes scaled to the full mesh by its cells (x 8); a one-pass capture of
 # the full mesh gives the same FP64 slots per cell within 2 %.
-FP64_FLOP_PER_CELL_C5 = {"sweep_x": 249.0, "sweep_y": 230.1, "sweep_z": 360.6}
-FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 191.8, "sweep_y": 178.7, "sweep_z": 271.8}
-DRAM_BYTES_C5 = {"sweep_x": 10.99e9, "sweep_y": 15.47e9, "sweep_z": 21.31e9}
-KERNELS_AS_CAPTURED_C5 = False
+FP64_FLOP_PER_CELL_C5 = {"sweep_x": 245.9, "sweep_y": 227.0, "sweep_z": 357.6}
+FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 190.7, "sweep_y": 177.5, "sweep_z": 270.6}
+DRAM_BYTES_C5 = {"sweep_x": 10.99e9, "sweep_y": 15.45e9, "sweep_z": 21.28e9}
+KERNELS_AS_CAPTURED_C5 = True
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 
 
