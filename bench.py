@@ -392,11 +392,11 @@ def c2_section(ctx, eos, tde, torch, dev, args, fp64_peak, peaks):
 # capture.  They describe the kernels as captured: set KERNELS_AS_CAPTURED to
 # False (achieved, frac and traffic reported as null) whenever a sweep kernel
 # changes.
-FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 207.2, "sweep_y": 171.8, "sweep_z": 297.8}
-DRAM_BYTES_SWEEP = {"sweep_x": 268.5e6, "sweep_y": 401.1e6, "sweep_z": 544.5e6}
+FP64_FLOP_PER_CELL_SWEEP = {"sweep_x": 205.2, "sweep_y": 169.7, "sweep_z": 295.7}
+DRAM_BYTES_SWEEP = {"sweep_x": 268.5e6, "sweep_y": 402.6e6, "sweep_z": 545.1e6}
 # FP64-pipe issue slots (warp instructions x 32) per interior cell: a DADD or DMUL
 # holds the pipe as long as a DFMA, so the pipe's busy fraction is slots / peak.
-FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 189.5, "sweep_y": 189.5, "sweep_z": 277.5}
+FP64_SLOTS_PER_CELL_SWEEP = {"sweep_x": 187.3, "sweep_y": 187.3, "sweep_z": 275.3}
 KERNELS_AS_CAPTURED = True
 # The same for the headline's sweeps (production-shaped mesh, PPM, point mass),
 # from ncu on the 8 x 8 x 4 MeshBlocks around the star of that mesh (8.4 M
@@ -404,9 +404,9 @@ KERNELS_AS_CAPTURED = True
 # too much for a multi-pass capture), two launches of each sweep averaged,
 # DRAM bytes scaled to the full mesh by its cells (x 8); a one-pass capture of
 # the full mesh gives the same FP64 slots per cell within 2 %.
-FP64_FLOP_PER_CELL_C5 = {"sweep_x": 245.9, "sweep_y": 227.0, "sweep_z": 357.6}
-FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 190.7, "sweep_y": 177.5, "sweep_z": 270.6}
-DRAM_BYTES_C5 = {"sweep_x": 10.99e9, "sweep_y": 15.45e9, "sweep_z": 21.28e9}
+FP64_FLOP_PER_CELL_C5 = {"sweep_x": 243.8, "sweep_y": 225.0, "sweep_z": 355.5}
+FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 188.5, "sweep_y": 175.3, "sweep_z": 268.4}
+DRAM_BYTES_C5 = {"sweep_x": 11.00e9, "sweep_y": 15.48e9, "sweep_z": 21.30e9}
 KERNELS_AS_CAPTURED_C5 = True
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 

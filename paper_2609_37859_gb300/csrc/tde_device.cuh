@@ -600,7 +600,7 @@ __device__ __forceinline__ void hllc(const Phys &p, const FState &L, const FStat
   double Seff = (supL || supR) ? 0.0 : S;
   double den = S - SM;
   if (dzero(den)) den = 1.0;   // only reachable when Seff == 0
-  double rS = r * (S - un);
+  double rS = useL ? al : ar;   // r (S - u) of side K: the same product as al / ar
   double inv = rcp_nr(den);
   double fac = rS * inv;
   double mflux = r * un;
