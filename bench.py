@@ -404,9 +404,9 @@ KERNELS_AS_CAPTURED = True
 # too much for a multi-pass capture), two launches of each sweep averaged,
 # DRAM bytes scaled to the full mesh by its cells (x 8); a one-pass capture of
 # the full mesh gives the same FP64 slots per cell within 2 %.
-FP64_FLOP_PER_CELL_C5 = {"sweep_x": 243.8, "sweep_y": 225.0, "sweep_z": 355.5}
-FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 188.5, "sweep_y": 175.3, "sweep_z": 268.4}
-DRAM_BYTES_C5 = {"sweep_x": 11.00e9, "sweep_y": 15.48e9, "sweep_z": 21.30e9}
+FP64_FLOP_PER_CELL_C5 = {"sweep_x": 240.7, "sweep_y": 224.8, "sweep_z": 355.3}
+FP64_SLOTS_PER_CELL_C5 = {"sweep_x": 185.5, "sweep_y": 174.9, "sweep_z": 268.0}
+DRAM_BYTES_C5 = {"sweep_x": 11.00e9, "sweep_y": 15.48e9, "sweep_z": 21.29e9}
 KERNELS_AS_CAPTURED_C5 = True
 C5_COUNTERS_NOTE = "profiles/k_sweep_c5_production_ncu.md (8x8x4-block case of the same mesh)"
 

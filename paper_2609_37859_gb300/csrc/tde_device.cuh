@@ -271,14 +271,30 @@ __device__ __forceinline__ double rsqrt_nr(double t) {
 // same answer (the roundings of r^2 and of the square root are below 2^-51
 // relative), and only within that band is the square root taken.  A negative
 // or NaN r gives false, as the comparison does.
-__device__ __forceinline__ bool inside_radius(double r2, double r) {
-  if ((unsigned long long)dbits(r) > 0x7ff0000000000000ull) return false;
+// The thresholds depend on r alone, so a kernel that tests many cells against one
+// sphere forms them once (sphere_of) and tests with inside_sphere; inside_radius
+// does both.
+struct Sphere {
+  double r, lo, hi;   // radius; r^2 (1 - 2^-40), r^2 (1 + 2^-40)
+  int mode;           // 0: the band test; 1: r^2 near the subnormals (root test); 2: never inside
+};
+__device__ __forceinline__ Sphere sphere_of(double r) {
+  Sphere s;
+  s.r = r;
   const double r2b = r * r;
-  if (((dbits(r2b) >> 52) & 0x7ff) < 64) return dlt(sqrt(r2), r);   // r^2 near the subnormals
-  if (dlt(r2, r2b * (1.0 - 0x1p-40))) return true;
-  if (dlt(r2b * (1.0 + 0x1p-40), r2)) return false;
-  return dlt(sqrt(r2), r);
+  s.lo = r2b * (1.0 - 0x1p-40);
+  s.hi = r2b * (1.0 + 0x1p-40);
+  s.mode = (unsigned long long)dbits(r) > 0x7ff0000000000000ull ? 2 : (((dbits(r2b) >> 52) & 0x7ff) < 64 ? 1 : 0);
+  return s;
 }
+__device__ __forceinline__ bool inside_sphere(double r2, const Sphere &s) {
+  if (s.mode == 2) return false;
+  if (s.mode == 1) return dlt(sqrt(r2), s.r);   // r^2 near the subnormals
+  if (dlt(r2, s.lo)) return true;
+  if (dlt(s.hi, r2)) return false;
+  return dlt(sqrt(r2), s.r);
+}
+__device__ __forceinline__ bool inside_radius(double r2, double r) { return inside_sphere(r2, sphere_of(r)); }
 
 // Squared distance of a cell centre from the point mass, in one fixed order of
 // roundings for every kernel (a cell's potential and excision flag then agree

@@ -231,11 +231,13 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs &a, int qb, int tile,
     // an x pencil, the transverse part of each lane's squared distance (the
     // FP64 pipe charges a warp instruction whatever its active lanes)
     __shared__ double s_rb[3], s_yz[M];
+    __shared__ Sphere s_exc;   // the excision sphere's thresholds
     if (threadIdx.x < 32) {
       const double ts = ta_t(a.ta, b) + (a.stage ? ta_dt(a.ta, b) : 0.0);
       double rb[3];
       bh_pos(a.bh, ts, rb);
       if (threadIdx.x < 3) s_rb[threadIdx.x] = rb[threadIdx.x];
+      if (threadIdx.x == 0 && exc) s_exc = sphere_of(a.bh.rexc);
       if (D == 0 && threadIdx.x < M)
         s_yz[threadIdx.x] = bh_r2_yz(cell_coord(p, B, 1, p.g[1] + l0 + threadIdx.x) - rb[1],
                                      cell_coord(p, B, 2, p.g[2] + o) - rb[2]);
@@ -275,7 +277,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs &a, int qb, int tile,
         if (cached && inner) a.phic[cflat] = ph;
       }
       if (exc) {
-        const unsigned char x = inside_radius(r2, a.bh.rexc) ? 1 : 0;
+        const unsigned char x = inside_sphere(r2, s_exc) ? 1 : 0;
         Ex[idx] = x;
         if (cached && inner) a.exc_c[cflat] = x;
       }
