@@ -9,7 +9,10 @@
 // Each phase does the per-cell work of the corresponding kernel with the same
 // device functions on the same data, so the results are the sequence's bit for
 // bit; only the distribution of the work over CTAs differs (sweep tiles of the
-// 8-lane shape, handed out round-robin).
+// default 8-lane shape taken from a work counter per phase, cells and ghost-map
+// entries in chunks of one CTA width strided over the CTAs).  The start states
+// are saved for their interiors only (no ghost cell of them is read), in the
+// first stage's ghost phase.
 //
 // A barrier is an arrival counter and a generation word in device memory,
 // zeroed before each launch (with the work counters from which the CTAs take
