@@ -3,7 +3,8 @@
 // One Runge-Kutta stage is four kinds of launches on the context's stream:
 //   k_c2p     conserved -> primitive (+ EOS, + optional per-block CFL minimum)
 //             on the interior cells only;
-//   k_ghost   the ghost layer of the primitives, gathered from the neighbours'
+//   k_ghost   the ghost layer of the primitives (the face ghosts, the only ones
+//             the sweeps read), gathered from the neighbours'
 //             interiors through a precomputed (dst, src) map (a1) -- the
 //             primitive recovery is pointwise, so copying primitives equals
 //             converting copied conserved variables and saves the EOS work of
